@@ -1,0 +1,134 @@
+"""Seeded synthetic inputs for the porosity-wave PT solver.
+
+This module is shared by the CPU oracle (tests, CPU baseline) and the CUDA path. It only builds
+*inputs*: parameter sets and initial fields. It holds none of the method's arithmetic: no
+rheology, no PT update, no derived coefficient (background density, pseudo-time steps and
+initial viscosities are computed by each implementation on its own side).
+
+Array convention: every field is a C-ordered ``numpy.float64`` array of shape
+``(nz_s, ny_s, nx_s)`` (x fastest), where ``(nx_s, ny_s, nz_s)`` is the staggered size of the
+field (``nx`` cells in x for cell-centred fields, ``nx + 1`` for x-faces, and so on).
+
+Workloads (thesis Art. 1, Sections 2.1-2.2, Table 2; nondimensional units):
+
+* ``c1_params`` — the 32^3 single-step case: phi0 = 0.01, one centred Gaussian anomaly of added
+  amplitude 2*phi0 and width 0.1, k0 = 1, mu0 = 1, eta0 = 1, weakening multiplier 0.01 where
+  Pf > Pt, power-law exponent 3 with tau0 = 0.04 (Table 2), Biot alpha = 0.9 and Skempton
+  B = 0.89 (Table 2), compressibilities beta_phi = 1e-2, beta_d = 1.3 beta_phi and shear modulus
+  G = 0.5 / beta_phi (ratios of the appendix two-phase script), rho_f g = 1, rho_s g = 2.
+* ``large_params`` — the same model at any n (511^3 is the benchmark grid) with a seeded
+  anomaly position (centre + U(-0.05, 0.05)^3).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "c1_params", "large_params", "gaussian_porosity", "perturbed_centre",
+    "field_shapes", "random_state", "PARAM_KEYS",
+]
+
+# Parameter names as used at both boundaries (C ABI struct members and the oracle's struct).
+PARAM_KEYS = (
+    # grid
+    "nx", "ny", "nz", "lx", "ly", "lz",
+    # physics
+    "phi0", "k0", "mu0", "eta0", "R_weak", "n_pow", "tau0", "alpha", "B", "beta_d", "beta_phi",
+    "G", "rhof_g", "rhos_g", "powerlaw_on", "compaction_on",
+    # numerics
+    "dt", "tol", "max_iter", "nup", "damp_x", "damp_y", "damp_z", "rho_i", "beta_n",
+    "rel_mu", "rel_eta", "cfl_v", "cfl_pf", "dtpt_scale", "xsi_w",
+)
+
+
+def c1_params(nx: int = 32, ny: int | None = None, nz: int | None = None) -> dict:
+    """Parameter set of the single-step 32^3 workload (any grid size may be passed)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    beta_phi = 1e-2
+    return dict(
+        nx=nx, ny=ny, nz=nz, lx=1.0, ly=1.0, lz=1.0,
+        phi0=0.01, k0=1.0, mu0=1.0, eta0=1.0, R_weak=0.01, n_pow=3.0, tau0=0.04,
+        alpha=0.9, B=0.89, beta_d=1.3 * beta_phi, beta_phi=beta_phi, G=0.5 / beta_phi,
+        rhof_g=1.0, rhos_g=2.0, powerlaw_on=1, compaction_on=1,
+        dt=1e-4 * (32.0 / max(nx, ny, nz)) ** 2, tol=1e-8, max_iter=20000, nup=15,
+        damp_x=1.0 - 1.0 / nx, damp_y=1.0 - 1.0 / ny, damp_z=1.0 - 1.0 / nz,
+        rho_i=1.0, beta_n=0.0, rel_mu=0.1, rel_eta=0.5,
+        cfl_v=1.0 / 6.1, cfl_pf=1.0 / 6.1, dtpt_scale=1.0, xsi_w=1.0,
+    )
+
+
+def large_params(n: int = 511, max_iter: int = 20000) -> dict:
+    """Same model and parameters on an n^3 grid (the benchmark uses n = 511)."""
+    p = c1_params(n)
+    p["max_iter"] = max_iter
+    return p
+
+
+def field_shapes(nx: int, ny: int, nz: int) -> dict:
+    """Staggered (z, y, x) shapes of every field (thesis Art. 1, Fig. 1 placement)."""
+    return dict(
+        centre=(nz, ny, nx),
+        Vx=(nz, ny, nx + 1), Vy=(nz, ny + 1, nx), Vz=(nz + 1, ny, nx),
+        txy=(nz, ny + 1, nx + 1), txz=(nz + 1, ny, nx + 1), tyz=(nz + 1, ny + 1, nx),
+    )
+
+
+def perturbed_centre(seed: int, base=(0.5, 0.5, 0.5), half_width: float = 0.05) -> tuple:
+    """Anomaly centre = base + U(-half_width, half_width)^3 from numpy's PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = rng.uniform(-half_width, half_width, size=3)
+    return tuple(float(b + x) for b, x in zip(base, d))
+
+
+def gaussian_porosity(p: dict, centres=((0.5, 0.5, 0.5),), amp: float | None = None,
+                      width: float = 0.1) -> np.ndarray:
+    """Initial porosity at cell centres: phi0 + sum_a amp * exp(-(|x - x_a| / width)^2).
+
+    Cell-centred grid on [0, lx] x [0, ly] x [0, lz] with dx = lx / nx; centres are given as
+    fractions of the box lengths. ``amp`` defaults to 2 * phi0 (added amplitude).
+    """
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    lx, ly, lz = p["lx"], p["ly"], p["lz"]
+    phi0 = p["phi0"]
+    amp = 2.0 * phi0 if amp is None else amp
+    x = (np.arange(nx) + 0.5) * (lx / nx)
+    y = (np.arange(ny) + 0.5) * (ly / ny)
+    z = (np.arange(nz) + 0.5) * (lz / nz)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    phi = np.full((nz, ny, nx), phi0, dtype=np.float64)
+    for (cx, cy, cz) in centres:
+        r2 = (X - cx * lx) ** 2 + (Y - cy * ly) ** 2 + (Z - cz * lz) ** 2
+        phi += amp * np.exp(-r2 / width ** 2)
+    return phi
+
+
+def random_state(p: dict, seed: int, scale: float = 1e-3) -> dict:
+    """A seeded, smooth-ish random mid-solve state (for parity tests that start off-rest).
+
+    Velocities on interior faces, pressures, stresses and old-step fields are uniform random of
+    the given scale; porosity is phi0 * (1 + 0.5 U(0,1)); boundary-normal velocities and
+    boundary-edge shear stresses are zero (free-slip). Viscosities are *not* produced: each
+    implementation initialises them from the porosity itself.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    sh = field_shapes(nx, ny, nz)
+    out = {}
+    for name in ("Vx", "Vy", "Vz"):
+        out[name] = scale * rng.standard_normal(sh[name])
+    out["Vx"][:, :, 0] = 0.0; out["Vx"][:, :, -1] = 0.0
+    out["Vy"][:, 0, :] = 0.0; out["Vy"][:, -1, :] = 0.0
+    out["Vz"][0, :, :] = 0.0; out["Vz"][-1, :, :] = 0.0
+    for name in ("Pt", "Pf"):
+        out[name] = scale * rng.standard_normal(sh["centre"])
+    out["phi"] = p["phi0"] * (1.0 + 0.5 * rng.uniform(size=sh["centre"]))
+    for name in ("txx", "tyy", "tzz"):
+        out[name] = scale * rng.standard_normal(sh["centre"])
+    out["txy"] = scale * rng.standard_normal(sh["txy"])
+    out["txy"][:, 0, :] = 0; out["txy"][:, -1, :] = 0; out["txy"][:, :, 0] = 0; out["txy"][:, :, -1] = 0
+    out["txz"] = scale * rng.standard_normal(sh["txz"])
+    out["txz"][0, :, :] = 0; out["txz"][-1, :, :] = 0; out["txz"][:, :, 0] = 0; out["txz"][:, :, -1] = 0
+    out["tyz"] = scale * rng.standard_normal(sh["tyz"])
+    out["tyz"][0, :, :] = 0; out["tyz"][-1, :, :] = 0; out["tyz"][:, 0, :] = 0; out["tyz"][:, -1, :] = 0
+    return out
