@@ -1,0 +1,170 @@
+/* porowave_pt.h — C ABI of the GB300 pseudo-transient (PT) + Picard solver for 3-D nonlinear
+ * poroviscoelastic two-phase flow (porosity waves).
+ *
+ * What it solves (thesis Art. 1): Biot poroelasticity extended with viscous compaction
+ * (Eqs. 1-2), total momentum balance (Eq. 3), Darcy flow (Eq. 4), Maxwell viscoelastic shear
+ * (Eq. 5), porosity evolution (Eq. 6), Carman-Kozeny permeability (Eq. 7), power-law shear
+ * viscosity (Eq. 8), decompaction weakening (Eq. 9) of the bulk viscosity (Eq. 10) and total
+ * density (Eq. 11), each physical time step solved implicitly by the PT iteration of
+ * Section 2.2 (Eqs. 12-16, in the form Eqs. 17-27) on the staggered grid of Fig. 1, with
+ * damped solid velocities, log-space porosity and Picard updates of the viscosities.
+ *
+ * Units are nondimensional; gravity acts along -z; pressures are excess over the lithostatic
+ * pressure of the background density phi0 rho_f + (1 - phi0) rho_s. Boundaries are free slip
+ * (zero normal velocity, zero shear stress) with zero normal Darcy flux (Eq. 34).
+ *
+ * ------------------------------------------------------------------------------------------
+ * Memory layout (all fields, device memory, owned by the caller):
+ *   Every staggered field is stored in the same padded box of dimensions
+ *       pitch_x  x  pitch_y  x  (nz + 1)            with pitch_x = roundup(nx + 1, 16),
+ *                                                        pitch_y = ny + 1,
+ *   element (i, j, k) at offset i + pitch_x * (j + pitch_y * k), x fastest
+ *   (pt_field_elems() gives the element count). Valid index ranges:
+ *       cell centres (Pt, Pf, phi, mu, eta, txx, tyy, tzz, logk)   i < nx,  j < ny,  k < nz
+ *       x-faces Vx (at x = i dx)                                    i <= nx, j < ny,  k < nz
+ *       y-faces Vy                                                  i < nx,  j <= ny, k < nz
+ *       z-faces Vz                                                  i < nx,  j < ny,  k <= nz
+ *       xy-edges txy (at x = i dx, y = j dy)                        i <= nx, j <= ny, k < nz
+ *       xz-edges txz                                                i <= nx, j < ny,  k <= nz
+ *       yz-edges tyz                                                i < nx,  j <= ny, k <= nz
+ *   Cell (i, j, k) is centred at ((i + 1/2) dx, (j + 1/2) dy, (k + 1/2) dz), dx = lx / nx.
+ *   Entries outside the valid ranges are padding: the library never reads them as data.
+ *   Field arrays must be 16-byte aligned and must not alias each other or the workspace.
+ *
+ * Threading and streams: every call is asynchronous on the stream given to pt_init except
+ * where a call returns a report (pt_step, pt_iterate, pt_residual), which synchronise that
+ * stream to read it. The library holds no global state; a context is used by one host thread
+ * at a time.
+ *
+ * Errors: functions return PT_OK (0) or a negative code (pt_strerror gives its text). On any
+ * error the fields hold the last complete iterate.
+ */
+#ifndef POROWAVE_PT_H
+#define POROWAVE_PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PT_OK = 0,
+  PT_EINVAL = -1,     /* bad argument: null pointer, size < 1, dt <= 0, misaligned, ...      */
+  PT_ENOTCONV = -2,   /* max_iter reached before the residual fell below tol                  */
+  PT_ENAN = -3,       /* a residual norm was not finite                                       */
+  PT_ETIMEOUT = -4,   /* a bounded device-side wait expired                                   */
+  PT_ECUDA = -5,      /* a CUDA call or kernel launch failed                                  */
+  PT_ESPACE = -6      /* workspace smaller than pt_workspace_size()                            */
+};
+
+enum { PT_FP64 = 0, PT_FP32 = 1 };
+
+/* Cell-centred grid on [0, lx] x [0, ly] x [0, lz]; dx = lx / nx. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double lx, ly, lz;
+} pt_grid;
+
+/* Physical parameters (Table 2 symbols, nondimensional). */
+typedef struct {
+  double phi0;      /* background porosity (sets the background density)                  */
+  double k0;        /* reference permeability over fluid viscosity, k = k0 e^logk (phi/phi0)^3 */
+  double mu0;       /* reference shear viscosity (Eq. 8)                                  */
+  double eta0;      /* reference bulk viscosity, eta = eta0 mu / phi (Eq. 10)             */
+  double R_weak;    /* bulk-viscosity multiplier where Pf > Pt (Eq. 9; 1 = no weakening)  */
+  double n_pow;     /* power-law exponent n (Eq. 8)                                       */
+  double tau0;      /* characteristic stress tau0 (Eq. 8)                                 */
+  double alpha;     /* Biot-Willis coefficient                                            */
+  double B;         /* Skempton coefficient                                               */
+  double beta_d;    /* drained compressibility 1 / K_d                                    */
+  double beta_phi;  /* effective bulk compressibility 1 / K_phi                           */
+  double G;         /* elastic shear modulus                                              */
+  double rhof_g;    /* fluid density times gravity                                        */
+  double rhos_g;    /* solid density times gravity                                        */
+  int32_t powerlaw_on;    /* 0: mu* = mu0 (no power law)                                  */
+  int32_t compaction_on;  /* 0: no viscous compaction term (1 / eta = 0)                  */
+} pt_phys;
+
+/* Numerical parameters of the PT iteration (Section 2.2 and the appendix two-phase script). */
+typedef struct {
+  double dt;              /* physical time step (> 0)                                      */
+  double tol;             /* convergence: max of the residual max-norms < tol               */
+  int32_t max_iter;       /* PT iteration cap per physical step                            */
+  int32_t nup;            /* Picard update and residual check every nup-th iteration       */
+  double damp[3];         /* velocity damping per direction, e.g. 1 - 1/n                  */
+  double rho_i;           /* inertial density of the velocity pseudo-time step            */
+  double beta_n;          /* numerical compressibility in the normal stresses               */
+  double rel_mu, rel_eta; /* log-space Picard relaxation of mu and eta                      */
+  double cfl_v;           /* dtau_V = cfl_v h^2 rho_i / (mu (1 + beta_n)),  h = min(dx,dy,dz) */
+  double cfl_pf;          /* dtau_Pf = cfl_pf h^2 (1 + beta_d B / alpha) / max local k      */
+  double dtpt_scale;      /* dtau_Pt = dtpt_scale mu (1 + beta_n) / nz                      */
+  double xsi_w;           /* stress sub-step dtS = max(mu) / (G xsi_w)                      */
+  int32_t precision;      /* PT_FP64 (all arithmetic FP64) or PT_FP32 (see pt_init)        */
+  int32_t iters_per_graph;/* PT iterations per CUDA-graph replay; 0 = nup                  */
+} pt_num;
+
+/* Caller-owned device fields, padded box layout above. logk may be NULL (logk = 0). */
+typedef struct {
+  double *Vx, *Vy, *Vz;                       /* solid velocity                (r/w)     */
+  double *Pt, *Pf, *phi;                      /* total, fluid pressure, porosity (r/w)    */
+  double *txx, *tyy, *tzz, *txy, *txz, *tyz;  /* deviatoric stress of the last step (r/w) */
+  double *mu, *eta;                           /* Picard shear and bulk viscosity (r/w)    */
+  const double *logk;                         /* log-permeability prefactor field (read)  */
+} pt_fields;
+
+/* Report of a step / iteration batch: residual max-norms of the last check. */
+typedef struct {
+  int32_t iters;      /* PT iterations taken                                                */
+  int32_t status;     /* PT_OK, PT_ENOTCONV, PT_ENAN, ...                                   */
+  double res_v;       /* max |F| momentum residual (Eq. 19 left side)                       */
+  double res_pt;      /* max |numerical div V| (Eq. 17 left side)                           */
+  double res_pf;      /* max |fluid-pressure residual| (Eq. 18 left side)                   */
+  double res_pic;     /* max |log mu* - log mu|, |log eta* - log eta| (Eqs. 24, 26)         */
+} pt_report;
+
+typedef struct pt_ctx pt_ctx;
+
+/* Elements per field array (padded box) for this grid; 0 if the grid is invalid. */
+size_t pt_field_elems(const pt_grid *grid);
+/* x pitch of the padded box (elements). */
+int32_t pt_pitch_x(const pt_grid *grid);
+/* Bytes of device workspace pt_init needs for this grid and numerics. */
+size_t pt_workspace_size(const pt_grid *grid, const pt_num *num);
+
+/* Create a solver context over caller-owned fields and workspace (device memory, at least
+ * pt_workspace_size() bytes, 256-byte aligned). Initialises the Picard state
+ * mu = mu0, eta = eta0 mu / phi (Eq. 26 with R = 1) unless keep_visc != 0, zeroes the damped
+ * residuals, and validates every argument. `stream` is a cudaStream_t (NULL = default stream).
+ * The context keeps the pointers: fields and workspace must outlive it. */
+int pt_init(pt_ctx **ctx, const pt_grid *grid, const pt_phys *phys, const pt_num *num,
+            const pt_fields *fields, void *workspace, size_t workspace_bytes, void *stream,
+            int32_t keep_visc);
+
+/* One physical time step (thesis Art. 1 Section 2.2): snapshot of the old state, PT + Picard
+ * iterations until the residual max-norm < tol (checked every nup iterations) or max_iter,
+ * then the step's final stresses. Returns PT_OK, PT_ENOTCONV (fields hold the last iterate,
+ * `rep` the last norms) or an error. */
+int pt_step(pt_ctx *ctx, pt_report *rep);
+
+/* Lower-level pieces of pt_step, for fixed-iteration-count runs (benchmarks, parity tests):
+ * pt_step_begin = old-state snapshot and stress sub-step; pt_iterate = `niter` PT iterations
+ * numbered it0+1 .. it0+niter (Picard and norms on multiples of nup; no convergence exit;
+ * `rep` may be NULL to skip the norm read-back); pt_step_end = final stresses and dt_cum. */
+int pt_step_begin(pt_ctx *ctx);
+int pt_iterate(pt_ctx *ctx, int32_t it0, int32_t niter, pt_report *rep);
+int pt_step_end(pt_ctx *ctx);
+
+/* Residual max-norms of the current state (no update). */
+int pt_residual(pt_ctx *ctx, pt_report *rep);
+
+/* Release the context (not the caller's memory). */
+void pt_destroy(pt_ctx *ctx);
+
+const char *pt_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

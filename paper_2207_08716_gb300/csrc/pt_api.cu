@@ -1,0 +1,433 @@
+// pt_api.cu — host side of the C ABI declared in include/porowave_pt.h.
+//
+// The context owns no device memory: fields belong to the caller, scratch lives in the
+// caller's workspace. Iterate k of the centre fields (Pt, Pf, phi) alternates between the
+// caller's arrays and their workspace partners (ping-pong); every API call that returns leaves
+// the current iterate in the caller's arrays.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "../../include/porowave_pt.h"
+#include "pt_common.cuh"
+#include "pt_kernels.cuh"
+
+using namespace pt;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kPitchMultiple = 16;
+constexpr int kWorkArrays = 23;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool grid_ok(const pt_grid* g) {
+  return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->nx < (1 << 20) && g->ny < (1 << 20) &&
+         g->nz < 65535 && g->lx > 0 && g->ly > 0 && g->lz > 0 && std::isfinite(g->lx) &&
+         std::isfinite(g->ly) && std::isfinite(g->lz);
+}
+
+Box make_box(const pt_grid* g) {
+  Box b;
+  b.nx = g->nx;
+  b.ny = g->ny;
+  b.nz = g->nz;
+  b.px = (g->nx + 1 + kPitchMultiple - 1) / kPitchMultiple * kPitchMultiple;
+  b.pxy = (long long)b.px * (g->ny + 1);
+  b.n = b.pxy * (g->nz + 1);
+  return b;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+struct pt_ctx {
+  Box box;
+  Coef coef;
+  pt_grid grid;
+  pt_phys phys;
+  pt_num num;
+  cudaStream_t stream;
+  // caller's fields
+  double *Vx, *Vy, *Vz, *txx, *tyy, *tzz, *txy, *txz, *tyz, *mu, *eta;
+  const double* logk;
+  double* Pt[2];
+  double* Pf[2];
+  double* phi[2];
+  int cur;  // 0: iterate k in the caller's arrays, 1: in the workspace partners
+  // workspace
+  double *Pto, *Pfo, *Lo, *txxo, *tyyo, *tzzo, *txyo, *txzo, *tyzo, *Rx, *Ry, *Rz, *perm, *rog;
+  double *s_txx, *s_tyy, *s_tzz, *s_txy, *s_txz, *s_tyz;
+  unsigned long long* red;       // device reduction block (RED_N slots)
+  unsigned long long* h_red;     // pinned host copy
+  // stress sub-stepping
+  double dtS, dt_cum;
+  int nsteps;
+  int checks_in_batch;
+};
+
+namespace {
+
+dim3 block_dims() { return dim3(32, 8, 1); }
+dim3 grid_dims(const Box& b) {
+  return dim3((unsigned)((b.nx + 1 + 31) / 32), (unsigned)((b.ny + 1 + 7) / 8), (unsigned)(b.nz + 1));
+}
+
+void fill_coef(pt_ctx* c) {
+  const pt_grid& g = c->grid;
+  const pt_phys& p = c->phys;
+  const pt_num& n = c->num;
+  Coef& k = c->coef;
+  const double dx = g.lx / g.nx, dy = g.ly / g.ny, dz = g.lz / g.nz;
+  const double h = std::fmin(dx, std::fmin(dy, dz));
+  k.rdx = 1.0 / dx;
+  k.rdy = 1.0 / dy;
+  k.rdz = 1.0 / dz;
+  k.h2 = h * h;
+  k.phi0 = p.phi0;
+  k.rphi0 = 1.0 / p.phi0;
+  k.k0 = p.k0;
+  k.mu0 = p.mu0;
+  k.eta0 = p.eta0;
+  k.R_weak = p.R_weak;
+  k.n_pow = p.n_pow;
+  k.tau0 = p.tau0;
+  k.alpha = p.alpha;
+  k.B = p.B;
+  k.beta_d = p.beta_d;
+  k.beta_phi = p.beta_phi;
+  k.G = p.G;
+  k.rhof_g = p.rhof_g;
+  k.rhos_g = p.rhos_g;
+  k.rho_bg_g = p.phi0 * p.rhof_g + (1.0 - p.phi0) * p.rhos_g;
+  k.powerlaw_on = p.powerlaw_on;
+  k.compaction_on = p.compaction_on;
+  k.dt = n.dt;
+  k.rdt = 1.0 / n.dt;
+  k.damp_x = n.damp[0];
+  k.damp_y = n.damp[1];
+  k.damp_z = n.damp[2];
+  k.rho_i = n.rho_i;
+  k.rrho_i = 1.0 / n.rho_i;
+  k.beta_n = n.beta_n;
+  k.rel_mu = n.rel_mu;
+  k.rel_eta = n.rel_eta;
+  k.dtauv_fac = n.cfl_v * k.h2 * n.rho_i / (1.0 + n.beta_n);
+  k.dtaupt_fac = n.dtpt_scale * (1.0 + n.beta_n) / g.nz;
+  k.dtaupf_fac = n.cfl_pf * k.h2 * (1.0 + p.beta_d * p.B / p.alpha);
+  k.rGdtS = c->dtS > 0 ? 1.0 / (p.G * c->dtS) : 0.0;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
+
+int sync_current_to_caller(pt_ctx* c) {
+  if (c->cur == 0) return PT_OK;
+  const size_t bytes = (size_t)c->box.n * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(c->Pt[0], c->Pt[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->Pf[0], c->Pf[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->phi[0], c->phi[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  c->cur = 0;
+  return cuda_status(e);
+}
+
+// One PT iteration number `it` (1-based); check = Picard update + norms.
+void launch_iteration(pt_ctx* c, int check) {
+  const Box& b = c->box;
+  const Coef& k = c->coef;
+  const dim3 bl = block_dims(), gr = grid_dims(b);
+  const int a = c->cur, n = 1 - c->cur;
+  if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[a], c->logk, c->perm, c->rog);
+  CentreIn ci{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->mu, c->eta, c->perm,
+              c->Pto, c->Pfo, c->txxo, c->tyyo, c->tzzo};
+  CentreOut co{c->Pt[n], c->Pf[n], c->s_txx, c->s_tyy, c->s_tzz};
+  k_centres<<<gr, bl, 0, c->stream>>>(b, k, ci, co, 1, c->red, check);
+  EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
+  EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
+  k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo);
+  k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[n], c->Pf[n],
+                                        c->Pto, c->Pfo, c->Lo, c->eta, c->phi[n]);
+  FaceIn fi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[n], c->rog, c->mu};
+  k_faces<<<gr, bl, 0, c->stream>>>(b, k, fi, c->Vx, c->Vy, c->Vz, c->Rx, c->Ry, c->Rz, c->red, check);
+  if (check) {
+    PicardIn pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[n], c->Pt[n], c->Pf[n]};
+    k_picard<<<gr, bl, 0, c->stream>>>(b, k, pi, c->mu, c->eta, c->red, 1);
+  }
+  c->cur = n;
+}
+
+int read_report(pt_ctx* c, pt_report* rep) {
+  cudaError_t e = cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  auto val = [&](int s) {
+    double d;
+    std::memcpy(&d, &c->h_red[s], sizeof d);
+    return d;
+  };
+  rep->res_v = val(RED_V);
+  rep->res_pt = val(RED_PT);
+  rep->res_pf = val(RED_PF);
+  rep->res_pic = val(RED_PIC);
+  const bool finite = std::isfinite(rep->res_v) && std::isfinite(rep->res_pt) &&
+                      std::isfinite(rep->res_pf) && std::isfinite(rep->res_pic);
+  return finite ? PT_OK : PT_ENAN;
+}
+
+double report_max(const pt_report* r) {
+  return std::fmax(std::fmax(r->res_v, r->res_pt), std::fmax(r->res_pf, r->res_pic));
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pt_field_elems(const pt_grid* grid) {
+  if (!grid_ok(grid)) return 0;
+  return (size_t)make_box(grid).n;
+}
+
+int32_t pt_pitch_x(const pt_grid* grid) {
+  if (!grid_ok(grid)) return 0;
+  return make_box(grid).px;
+}
+
+size_t pt_workspace_size(const pt_grid* grid, const pt_num* num) {
+  if (!grid_ok(grid) || !num) return 0;
+  const Box b = make_box(grid);
+  return kWorkArrays * align_up((size_t)b.n * sizeof(double), kAlign) + kAlign;
+}
+
+int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num* num,
+            const pt_fields* f, void* workspace, size_t workspace_bytes, void* stream,
+            int32_t keep_visc) {
+  if (!ctx) return PT_EINVAL;
+  *ctx = nullptr;
+  if (!grid_ok(grid) || !phys || !num || !f || !workspace) return PT_EINVAL;
+  if (!(num->dt > 0) || !std::isfinite(num->dt) || num->nup < 1 || num->max_iter < 0 || !(num->tol >= 0))
+    return PT_EINVAL;
+  if (!(num->rho_i > 0) || !(num->cfl_v > 0) || !(num->cfl_pf > 0) || !(num->dtpt_scale > 0) ||
+      !(num->xsi_w > 0))
+    return PT_EINVAL;
+  if (num->precision != PT_FP64) return PT_EINVAL;
+  if (!(phys->phi0 > 0 && phys->phi0 < 1) || !(phys->k0 > 0) || !(phys->mu0 > 0) || !(phys->eta0 > 0) ||
+      !(phys->G > 0) || !(phys->alpha > 0) || !(phys->B > 0) || !(phys->tau0 > 0) || !(phys->R_weak > 0))
+    return PT_EINVAL;
+  double* const ptrs[] = {f->Vx, f->Vy, f->Vz, f->Pt, f->Pf, f->phi, f->txx, f->tyy,
+                          f->tzz, f->txy, f->txz, f->tyz, f->mu, f->eta};
+  for (double* p : ptrs)
+    if (!p || !aligned16(p)) return PT_EINVAL;
+  if (f->logk && !aligned16(f->logk)) return PT_EINVAL;
+  if (((uintptr_t)workspace & (kAlign - 1)) != 0) return PT_EINVAL;
+  if (workspace_bytes < pt_workspace_size(grid, num)) return PT_ESPACE;
+
+  pt_ctx* c = new (std::nothrow) pt_ctx();
+  if (!c) return PT_ECUDA;
+  c->grid = *grid;
+  c->phys = *phys;
+  c->num = *num;
+  c->box = make_box(grid);
+  c->stream = (cudaStream_t)stream;
+  c->Vx = f->Vx; c->Vy = f->Vy; c->Vz = f->Vz;
+  c->Pt[0] = f->Pt; c->Pf[0] = f->Pf; c->phi[0] = f->phi;
+  c->txx = f->txx; c->tyy = f->tyy; c->tzz = f->tzz;
+  c->txy = f->txy; c->txz = f->txz; c->tyz = f->tyz;
+  c->mu = f->mu; c->eta = f->eta; c->logk = f->logk;
+  const size_t stride = align_up((size_t)c->box.n * sizeof(double), kAlign);
+  char* w = (char*)workspace;
+  double** slots[kWorkArrays] = {&c->Pt[1], &c->Pf[1], &c->phi[1], &c->Pto, &c->Pfo, &c->Lo,
+                                 &c->txxo, &c->tyyo, &c->tzzo, &c->txyo, &c->txzo, &c->tyzo,
+                                 &c->Rx, &c->Ry, &c->Rz, &c->perm, &c->rog, &c->s_txx,
+                                 &c->s_tyy, &c->s_tzz, &c->s_txy, &c->s_txz, &c->s_tyz};
+  for (int s = 0; s < kWorkArrays; ++s) *slots[s] = (double*)(w + s * stride);
+  c->red = (unsigned long long*)(w + kWorkArrays * stride);
+  if (cudaMallocHost(&c->h_red, RED_N * sizeof(unsigned long long)) != cudaSuccess) {
+    delete c;
+    return PT_ECUDA;
+  }
+  c->dtS = 0.0;
+  c->dt_cum = 0.0;
+  c->nsteps = 0;
+  c->cur = 0;
+  fill_coef(c);
+  // zero the whole workspace (damped residuals, old stresses, scratch padding)
+  cudaError_t e = cudaMemsetAsync(workspace, 0, pt_workspace_size(grid, num), c->stream);
+  if (e == cudaSuccess && !keep_visc) {
+    k_init_visc<<<grid_dims(c->box), block_dims(), 0, c->stream>>>(c->box, c->coef, c->phi[0], c->mu, c->eta);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFreeHost(c->h_red);
+    delete c;
+    return PT_ECUDA;
+  }
+  *ctx = c;
+  return PT_OK;
+}
+
+int pt_step_begin(pt_ctx* c) {
+  if (!c) return PT_EINVAL;
+  int rc = sync_current_to_caller(c);
+  if (rc != PT_OK) return rc;
+  const Box& b = c->box;
+  cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  k_begin_step<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->Pt[0], c->Pf[0], c->phi[0], c->mu,
+                                                             c->Pto, c->Pfo, c->Lo, c->red);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  double mu_max;
+  std::memcpy(&mu_max, &c->h_red[RED_MUMAX], sizeof mu_max);
+  if (!std::isfinite(mu_max) || !(mu_max > 0)) return PT_ENAN;
+  // stress sub-step of the appendix two-phase script: the largest xi = mu / (G dtS) is xsi_w;
+  // the old stresses are refreshed at the first step and when dt_cum reaches dtS
+  c->dtS = mu_max / (c->phys.G * c->num.xsi_w);
+  if (c->nsteps == 0 || c->dt_cum >= c->dtS) {
+    const size_t bytes = (size_t)b.n * sizeof(double);
+    const double* src[6] = {c->txx, c->tyy, c->tzz, c->txy, c->txz, c->tyz};
+    double* dst[6] = {c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
+    for (int s = 0; s < 6 && e == cudaSuccess; ++s)
+      e = cudaMemcpyAsync(dst[s], src[s], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    c->dt_cum = 0.0;
+  }
+  c->nsteps += 1;
+  fill_coef(c);
+  return cuda_status(e);
+}
+
+int pt_iterate(pt_ctx* c, int32_t it0, int32_t niter, pt_report* rep) {
+  if (!c || it0 < 0 || niter < 0) return PT_EINVAL;
+  if (c->nsteps == 0) return PT_EINVAL;  // pt_step_begin first
+  int checked = 0;
+  for (int32_t it = it0 + 1; it <= it0 + niter; ++it) {
+    const int check = (it % c->num.nup) == 0;
+    launch_iteration(c, check);
+    checked |= check;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return PT_ECUDA;
+  int rc = sync_current_to_caller(c);
+  if (rc != PT_OK) return rc;
+  if (rep) {
+    std::memset(rep, 0, sizeof *rep);
+    rep->iters = niter;
+    if (checked) {
+      rc = read_report(c, rep);
+    } else {
+      rc = cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    rep->status = rc;
+  }
+  return rc;
+}
+
+int pt_step_end(pt_ctx* c) {
+  if (!c) return PT_EINVAL;
+  int rc = sync_current_to_caller(c);
+  if (rc != PT_OK) return rc;
+  const Box& b = c->box;
+  CentreIn ci{c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->eta, c->perm,
+              c->Pto, c->Pfo, c->txxo, c->tyyo, c->tzzo};
+  CentreOut co{nullptr, nullptr, c->txx, c->tyy, c->tzz};
+  k_centres<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->coef, ci, co, 0, c->red, 0);
+  EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
+  EdgeOut eo{c->txy, c->txz, c->tyz};
+  k_edges<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->coef, ei, eo);
+  c->dt_cum += c->num.dt;
+  return cuda_status(cudaGetLastError());
+}
+
+int pt_step(pt_ctx* c, pt_report* rep) {
+  if (!c) return PT_EINVAL;
+  int rc = pt_step_begin(c);
+  if (rc != PT_OK) return rc;
+  pt_report r;
+  std::memset(&r, 0, sizeof r);
+  int it = 0;
+  bool converged = false;
+  const int nup = c->num.nup, cap = c->num.max_iter;
+  while (it < cap) {
+    const int n = std::min(nup - (it % nup), cap - it);
+    for (int s = 1; s <= n; ++s) launch_iteration(c, ((it + s) % nup) == 0);
+    it += n;
+    if (cudaGetLastError() != cudaSuccess) return PT_ECUDA;
+    if (it % nup == 0) {
+      rc = read_report(c, &r);
+      if (rc != PT_OK) break;
+      if (report_max(&r) < c->num.tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  int rc2 = sync_current_to_caller(c);
+  if (rc == PT_OK) rc = rc2;
+  if (rc == PT_OK) rc = pt_step_end(c);
+  if (rc == PT_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rc == PT_OK && !converged) rc = PT_ENOTCONV;
+  r.iters = it;
+  r.status = rc;
+  if (rep) *rep = r;
+  return rc;
+}
+
+int pt_residual(pt_ctx* c, pt_report* rep) {
+  if (!c || !rep) return PT_EINVAL;
+  if (c->nsteps == 0) return PT_EINVAL;
+  int rc = sync_current_to_caller(c);
+  if (rc != PT_OK) return rc;
+  const Box& b = c->box;
+  const Coef& k = c->coef;
+  const dim3 bl = block_dims(), gr = grid_dims(b);
+  cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[0], c->logk, c->perm, c->rog);
+  CentreIn ci{c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->eta, c->perm,
+              c->Pto, c->Pfo, c->txxo, c->tyyo, c->tzzo};
+  CentreOut co{c->Pt[1], c->Pf[1], c->s_txx, c->s_tyy, c->s_tzz};   // updates go to scratch
+  k_centres<<<gr, bl, 0, c->stream>>>(b, k, ci, co, 1, c->red, 1);
+  EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
+  EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
+  k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo);
+  FaceIn fi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[0], c->rog, c->mu};
+  k_residual_faces<<<gr, bl, 0, c->stream>>>(b, k, fi, c->red);
+  PicardIn pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[0], c->Pt[0], c->Pf[0]};
+  k_picard<<<gr, bl, 0, c->stream>>>(b, k, pi, c->mu, c->eta, c->red, 0);
+  if (cudaGetLastError() != cudaSuccess) return PT_ECUDA;
+  std::memset(rep, 0, sizeof *rep);
+  rc = read_report(c, rep);
+  rep->status = rc;
+  return rc;
+}
+
+void pt_destroy(pt_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  cudaFreeHost(c->h_red);
+  delete c;
+}
+
+const char* pt_strerror(int code) {
+  switch (code) {
+    case PT_OK: return "ok";
+    case PT_EINVAL: return "invalid argument";
+    case PT_ENOTCONV: return "PT iteration cap reached before the tolerance";
+    case PT_ENAN: return "non-finite residual";
+    case PT_ETIMEOUT: return "bounded device wait expired";
+    case PT_ECUDA: return "CUDA error";
+    case PT_ESPACE: return "workspace too small";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+"""Build and load the CUDA library (libpt_gb300.so) and declare its C ABI for ctypes.
+
+The library is compiled in-tree with nvcc for sm_103a (``build_library``). Loading never falls
+back to anything: if the shared object is missing or fails to load, ``load`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_CSRC = os.path.join(_PKG, "csrc")
+_INC = os.path.join(_ROOT, "include")
+_BUILD = os.path.join(_PKG, "_build")
+LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
+SOURCES = ("pt_api.cu", "pt_ref_kernels.cu")
+HEADERS = ("pt_common.cuh", "pt_kernels.cuh")
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+_lock = threading.Lock()
+_lib = None
+
+PT_OK, PT_EINVAL, PT_ENOTCONV, PT_ENAN, PT_ETIMEOUT, PT_ECUDA, PT_ESPACE = 0, -1, -2, -3, -4, -5, -6
+PT_FP64, PT_FP32 = 0, 1
+
+
+def _inputs():
+    files = [os.path.join(_CSRC, s) for s in SOURCES + HEADERS]
+    files.append(os.path.join(_INC, "porowave_pt.h"))
+    return files
+
+
+def build_library(force: bool = False, verbose: bool = False) -> str:
+    """Compile every .cu of the library into _build/libpt_gb300.so (objects in parallel)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(f) for f in _inputs())
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{_INC}"]
+    procs, objs = [], []
+    for s in SOURCES:
+        obj = os.path.join(_BUILD, s.replace(".cu", f".{os.getpid()}.o"))
+        objs.append(obj)
+        procs.append(subprocess.Popen(["nvcc", *flags, "-c", os.path.join(_CSRC, s), "-o", obj],
+                                      stdout=None if verbose else subprocess.PIPE,
+                                      stderr=subprocess.STDOUT))
+    for p, s in zip(procs, SOURCES):
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {s}:\n{(out or b'').decode(errors='replace')}")
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["nvcc", ARCH, "-shared", "-o", tmp, *objs], check=True)
+    os.replace(tmp, LIB_PATH)
+    for o in objs:
+        os.remove(o)
+    return LIB_PATH
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double)]
+
+
+class Phys(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("phi0", "k0", "mu0", "eta0", "R_weak", "n_pow", "tau0",
+                                          "alpha", "B", "beta_d", "beta_phi", "G", "rhof_g",
+                                          "rhos_g")] + \
+               [("powerlaw_on", C.c_int32), ("compaction_on", C.c_int32)]
+
+
+class Num(C.Structure):
+    _fields_ = [("dt", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("nup", C.c_int32), ("damp", C.c_double * 3), ("rho_i", C.c_double),
+                ("beta_n", C.c_double), ("rel_mu", C.c_double), ("rel_eta", C.c_double),
+                ("cfl_v", C.c_double), ("cfl_pf", C.c_double), ("dtpt_scale", C.c_double),
+                ("xsi_w", C.c_double), ("precision", C.c_int32), ("iters_per_graph", C.c_int32)]
+
+
+FIELD_NAMES = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi", "txx", "tyy", "tzz", "txy", "txz", "tyz",
+               "mu", "eta")
+
+
+class Fields(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in FIELD_NAMES] + [("logk", C.c_void_p)]
+
+
+class Report(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("res_v", C.c_double),
+                ("res_pt", C.c_double), ("res_pf", C.c_double), ("res_pic", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return dict(iters=self.iters, status=self.status, r_v=self.res_v, r_pt=self.res_pt,
+                    r_pf=self.res_pf, r_pic=self.res_pic)
+
+
+def grid_from(p: dict) -> Grid:
+    return Grid(p["nx"], p["ny"], p["nz"], p["lx"], p["ly"], p["lz"])
+
+
+def phys_from(p: dict) -> Phys:
+    ph = Phys()
+    for n, _ in Phys._fields_:
+        setattr(ph, n, p[n])
+    return ph
+
+
+def num_from(p: dict, precision: int = PT_FP64, iters_per_graph: int = 0) -> Num:
+    nm = Num()
+    for n, _ in Num._fields_:
+        if n == "damp":
+            nm.damp[0], nm.damp[1], nm.damp[2] = p["damp_x"], p["damp_y"], p["damp_z"]
+        elif n == "precision":
+            nm.precision = p.get("precision", precision)
+        elif n == "iters_per_graph":
+            nm.iters_per_graph = p.get("iters_per_graph", iters_per_graph)
+        else:
+            setattr(nm, n, p[n])
+    return nm
+
+
+# Every exported symbol of include/porowave_pt.h with its ctypes signature.
+SIGNATURES = {
+    "pt_field_elems": (C.c_size_t, [C.POINTER(Grid)]),
+    "pt_pitch_x": (C.c_int32, [C.POINTER(Grid)]),
+    "pt_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.POINTER(Num)]),
+    "pt_init": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Grid), C.POINTER(Phys), C.POINTER(Num),
+                          C.POINTER(Fields), C.c_void_p, C.c_size_t, C.c_void_p, C.c_int32]),
+    "pt_step": (C.c_int, [C.c_void_p, C.POINTER(Report)]),
+    "pt_step_begin": (C.c_int, [C.c_void_p]),
+    "pt_iterate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(Report)]),
+    "pt_step_end": (C.c_int, [C.c_void_p]),
+    "pt_residual": (C.c_int, [C.c_void_p, C.POINTER(Report)]),
+    "pt_destroy": (None, [C.c_void_p]),
+    "pt_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def load(build: bool = True) -> C.CDLL:
+    """Load libpt_gb300.so (building it first if `build`); raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build:
+                build_library()
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library {LIB_PATH} is missing; run "
+                                   "paper_2207_08716_gb300.native.build_library() on a machine with nvcc")
+            lib = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return load().pt_strerror(code).decode()

@@ -1,0 +1,139 @@
+"""Thin Python front end of the C ABI: device memory and the stream come from PyTorch, every
+step of the solve runs in the CUDA library (argument marshalling only here).
+
+Arrays at this level are in the natural staggered shapes (see ``pt_inputs.field_shapes``):
+numpy or torch, ``(nz_s, ny_s, nx_s)`` with x fastest. They are copied into the library's
+padded box layout on the device (``box[:nz_s, :ny_s, :nx_s] = a``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import native as N
+
+_SHAPE_OF = {"Vx": (0, 0, 1), "Vy": (0, 1, 0), "Vz": (1, 0, 0), "txy": (0, 1, 1),
+             "txz": (1, 0, 1), "tyz": (1, 1, 0)}
+
+
+def natural_shape(name: str, nx: int, ny: int, nz: int) -> tuple:
+    dz, dy, dx = _SHAPE_OF.get(name, (0, 0, 0))
+    return (nz + dz, ny + dy, nx + dx)
+
+
+class PTError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {N.strerror(code)} ({code})")
+        self.code = code
+
+
+class PTSolver:
+    """One solver context over device fields owned by this object (torch tensors).
+
+    params: dict with the keys of ``pt_inputs.PARAM_KEYS``; phi: initial porosity at cell
+    centres; logk: optional log-permeability prefactor field; fields: optional initial values of
+    any other field (natural shapes); keep_visc: keep given mu / eta instead of initialising
+    them from phi (Eq. 26).
+    """
+
+    def __init__(self, params: dict, phi, logk=None, fields: dict | None = None,
+                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None,
+                 keep_visc: bool = False):
+        self.lib = N.load()
+        self.params = dict(params)
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("PTSolver runs on a CUDA device only")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p = self.params
+        self.nx, self.ny, self.nz = p["nx"], p["ny"], p["nz"]
+        self._grid = N.grid_from(p)
+        self._phys = N.phys_from(p)
+        self._num = N.num_from(p)
+        n = self.lib.pt_field_elems(C.byref(self._grid))
+        if n == 0:
+            raise PTError(N.PT_EINVAL, "grid")
+        self.px = self.lib.pt_pitch_x(C.byref(self._grid))
+        self.box_shape = (self.nz + 1, self.ny + 1, self.px)
+        with torch.cuda.device(self.device):
+            self.f = {name: torch.zeros(self.box_shape, dtype=torch.float64, device=self.device)
+                      for name in N.FIELD_NAMES}
+            self.logk = None
+            if logk is not None:
+                self.logk = torch.zeros(self.box_shape, dtype=torch.float64, device=self.device)
+                self._put(self.logk, "centre", logk)
+            self._put(self.f["phi"], "phi", phi)
+            for k, v in (fields or {}).items():
+                self._put(self.f[k], k, v)
+            ws = self.lib.pt_workspace_size(C.byref(self._grid), C.byref(self._num))
+            self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        fs = N.Fields(*[self.f[k].data_ptr() for k in N.FIELD_NAMES],
+                      self.logk.data_ptr() if self.logk is not None else None)
+        ctx = C.c_void_p()
+        torch.cuda.synchronize(self.device)
+        rc = self.lib.pt_init(C.byref(ctx), C.byref(self._grid), C.byref(self._phys),
+                              C.byref(self._num), C.byref(fs), self.workspace.data_ptr(), ws,
+                              self.stream.cuda_stream, int(keep_visc))
+        if rc != N.PT_OK:
+            raise PTError(rc, "pt_init")
+        self.ctx = ctx
+
+    # -------------------------------------------------------------- layout marshalling
+    def _put(self, box: torch.Tensor, name: str, a) -> None:
+        t = torch.as_tensor(a, dtype=torch.float64).to(self.device)
+        sh = natural_shape(name, self.nx, self.ny, self.nz)
+        if tuple(t.shape) != sh:
+            raise ValueError(f"{name}: expected shape {sh}, got {tuple(t.shape)}")
+        box[: sh[0], : sh[1], : sh[2]].copy_(t)
+
+    def get(self, name: str) -> np.ndarray:
+        """Current field in its natural staggered shape, as a numpy array."""
+        torch.cuda.synchronize(self.device)
+        sh = natural_shape(name, self.nx, self.ny, self.nz)
+        return self.f[name][: sh[0], : sh[1], : sh[2]].cpu().numpy().copy()
+
+    def set(self, name: str, a) -> None:
+        self._put(self.f[name], name, a)
+        torch.cuda.synchronize(self.device)
+
+    # ------------------------------------------------------------------------ solve
+    def _check(self, rc: int, what: str, allow=(N.PT_OK,)) -> None:
+        if rc not in allow:
+            raise PTError(rc, what)
+
+    def step(self, raise_on_notconv: bool = False) -> dict:
+        rep = N.Report()
+        rc = self.lib.pt_step(self.ctx, C.byref(rep))
+        allow = (N.PT_OK,) if raise_on_notconv else (N.PT_OK, N.PT_ENOTCONV)
+        self._check(rc, "pt_step", allow)
+        return rep.as_dict()
+
+    def step_begin(self) -> None:
+        self._check(self.lib.pt_step_begin(self.ctx), "pt_step_begin")
+
+    def iterate(self, it0: int, niter: int, report: bool = True) -> dict | None:
+        rep = N.Report()
+        rc = self.lib.pt_iterate(self.ctx, it0, niter, C.byref(rep) if report else None)
+        self._check(rc, "pt_iterate")
+        return rep.as_dict() if report else None
+
+    def step_end(self) -> None:
+        self._check(self.lib.pt_step_end(self.ctx), "pt_step_end")
+
+    def residual(self) -> dict:
+        rep = N.Report()
+        self._check(self.lib.pt_residual(self.ctx, C.byref(rep)), "pt_residual")
+        return rep.as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            self.lib.pt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads and exports every symbol include/porowave_pt.h declares;
+host-only logic (sizes, layout, argument validation) is checked without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(pt_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2207_08716_gb300 import native
+    return native.load()
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    from paper_2207_08716_gb300 import native
+    declared = _declared_functions()
+    assert len(declared) >= 11, declared
+    for name in declared:
+        assert hasattr(lib, name), name                    # dlsym succeeds
+        assert name in native.SIGNATURES, name             # the binding declares it
+
+
+def test_layout_sizes(lib):
+    from paper_2207_08716_gb300 import native as N
+    for (nx, ny, nz), px in (((32, 32, 32), 48), ((511, 511, 511), 512), ((15, 3, 2), 16),
+                             ((1, 1, 1), 16), ((48, 40, 36), 64)):
+        g = N.Grid(nx, ny, nz, 1.0, 1.0, 1.0)
+        assert lib.pt_pitch_x(C.byref(g)) == px
+        assert lib.pt_field_elems(C.byref(g)) == px * (ny + 1) * (nz + 1)
+        num = N.num_from(__import__("pt_inputs").c1_params(nx, ny, nz))
+        ws = lib.pt_workspace_size(C.byref(g), C.byref(num))
+        assert ws >= 23 * px * (ny + 1) * (nz + 1) * 8
+    bad = N.Grid(0, 4, 4, 1.0, 1.0, 1.0)
+    assert lib.pt_field_elems(C.byref(bad)) == 0
+    assert lib.pt_pitch_x(C.byref(N.Grid(4, 4, 4, -1.0, 1.0, 1.0))) == 0
+
+
+def test_init_rejects_bad_arguments_before_touching_the_device(lib):
+    """Validation happens on the host: each bad argument returns PT_EINVAL / PT_ESPACE and
+    leaves the context null, without any CUDA call (this runs on a machine without a GPU)."""
+    import pt_inputs as I
+    from paper_2207_08716_gb300 import native as N
+    p = I.c1_params(8)
+    g, ph, num = N.grid_from(p), N.phys_from(p), N.num_from(p)
+    aligned = 1 << 20
+    fs = N.Fields(*([aligned] * 14), None)
+    ws = lib.pt_workspace_size(C.byref(g), C.byref(num))
+    ctx = C.c_void_p(1234)
+
+    def call(g=g, ph=ph, num=num, fs=fs, w=aligned * 2, wb=ws):
+        return lib.pt_init(C.byref(ctx), C.byref(g), C.byref(ph), C.byref(num), C.byref(fs), w, wb,
+                           None, 0)
+
+    assert call(g=N.Grid(0, 8, 8, 1, 1, 1)) == N.PT_EINVAL and ctx.value is None
+    nb = N.num_from(dict(p, dt=0.0))
+    assert call(num=nb) == N.PT_EINVAL
+    nb = N.num_from(dict(p, nup=0))
+    assert call(num=nb) == N.PT_EINVAL
+    pb = N.phys_from(dict(p, phi0=1.5))
+    assert call(ph=pb) == N.PT_EINVAL
+    assert call(fs=N.Fields(*([aligned] * 13), 0, None)) == N.PT_EINVAL      # null eta
+    assert call(fs=N.Fields(*([aligned + 8] + [aligned] * 13), None)) == N.PT_EINVAL  # misaligned
+    assert call(w=aligned * 2 + 16) == N.PT_EINVAL                            # workspace alignment
+    assert call(wb=ws - 1) == N.PT_ESPACE
+    assert lib.pt_step(None, None) == N.PT_EINVAL
+    assert lib.pt_iterate(None, 0, 1, None) == N.PT_EINVAL
+    assert lib.pt_strerror(N.PT_ENOTCONV).decode().startswith("PT iteration cap")
