@@ -1,0 +1,268 @@
+#!/usr/bin/env python3
+"""Benchmark: effective memory throughput T_eff (thesis Art. 1, Eqs. 28-29, 35-38) and PT
+iterations per second of the porosity-wave PT solver on one GB300, 511^3 cells.
+
+One benchmark step = one physical time step of the whole hot path: the old-state snapshot and
+stress sub-step, `--iters` PT iterations (coefficients, pressures, stresses, momentum, Darcy,
+porosity, velocities; Picard update and residual norms every 15th), and the end-of-step
+stresses. T_eff = A_eff / t_it with A_eff = 25 N p bytes and t_it = timed time / PT iterations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] ...
+Multi-GPU (torchrun, one rank per GPU) runs independent replicas (seed = rank): weak scaling,
+no data-path collective; only the timing max over ranks and a barrier are collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pt_inputs as I  # noqa: E402
+from paper_2207_08716_gb300 import measure as M  # noqa: E402
+
+METRIC = "T_eff GB/s (% of HBM peak) and PT iter/s at 511^3: FP64 vs FP32 vs batched"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK_GBS = 6800.0
+# FP64 FMA throughput measured on this machine's GB300 with a register-resident DFMA loop
+# (8 independent chains per thread, 152 x 8 blocks of 256 threads; FMA = 2 flops).
+FP64_PEAK_TFLOPS = 1.005
+
+# Algorithmic bytes per cell and launch of each kernel of the step-by-step FP64 path: the
+# arrays it must read and write once (8 B each), counted from its arguments.
+KERNEL_BYTES_PER_CELL = {
+    "k_perm": 3 * 8, "k_centres": 19 * 8, "k_edges": 10 * 8, "k_porosity": 11 * 8,
+    "k_faces": 21 * 8, "k_picard": 13 * 8, "k_begin_step": 6 * 8,
+}
+# FP64 flops per cell and launch counted by ncu (dfma x 2 + dadd + dmul) on the 128^3 case;
+# None until measured for the current kernel source.
+KERNEL_FP64_FLOPS_PER_CELL = {}
+# DRAM bytes per cell and launch from one ncu capture (dram__bytes_read + write), None if the
+# kernel changed since the capture.
+KERNEL_TRAFFIC_PER_CELL = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--n", type=int, default=511, help="cells per direction (511 = benchmark grid)")
+    ap.add_argument("--iters", type=int, default=30, help="PT iterations per physical step")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=191, help="sub-block edge of the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=6)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def workload_params(n: int, iters: int) -> dict:
+    p = I.large_params(n)
+    p["max_iter"] = iters
+    return p
+
+
+def workload_name(n: int, iters: int) -> str:
+    return (f"FP64 two-phase porosity-wave PT solver, {n}^3 cells, one seed-perturbed centred "
+            f"Gaussian anomaly, {iters} PT iterations per physical step")
+
+
+# ------------------------------------------------------------------------ CPU (oracle) leg
+def cpu_sample(n_sub: int, iters: int) -> dict:
+    """Oracle (as it stands) on a bounded sample of the benchmark workload: an n_sub^3 block of
+    the 511^3 grid around the anomaly (same spacing and parameters), `iters` PT iterations of
+    the first physical step. Returns T_eff over that sample."""
+    import oracle as O
+    p = workload_params(511, iters)
+    h = p["lx"] / p["nx"]
+    sub = dict(p, nx=n_sub, ny=n_sub, nz=n_sub, lx=n_sub * h, ly=n_sub * h, lz=n_sub * h)
+    sub["dtpt_scale"] = p["dtpt_scale"] * n_sub / p["nz"]
+    phi = I.gaussian_porosity(sub, centres=((0.5, 0.5, 0.5),), width=0.1)
+    st = O.make_state(sub, phi)
+    O.begin_step(st)
+    t0 = time.perf_counter()
+    rc, _ = O.iterate_n(st, 0, iters)
+    dt = time.perf_counter() - t0
+    if rc != 0:
+        raise RuntimeError(f"oracle rc {rc}")
+    ncell = n_sub ** 3
+    return {"value": M.t_eff_gbs(ncell, 8, dt / iters), "unit": "GB/s", "cores": O.max_threads(),
+            "kind": "oracle", "t_it_s": dt / iters, "seconds": dt,
+            "sample": (f"{n_sub}^3-cell block of the 511^3 workload (same spacing, parameters and "
+                       f"anomaly width), {iters} PT iterations of the first step, FP64 C oracle "
+                       f"with OpenMP; T_eff with A_eff = 25 N 8 B over the block")}
+
+
+def run_reference(args):
+    rank, _, world = M.rank_env()
+    if rank != 0:
+        return 0
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_sample(args.cpu_n, args.cpu_iters)
+        if s >= args.warmup:
+            vals.append(r)
+    v = float(np.median([r["value"] for r in vals]))
+    t_step = float(np.median([r["seconds"] for r in vals]))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(511, args.iters) +
+                                        f" (CPU oracle: bounded {args.cpu_n}^3 sample)",
+                                        "n": 511, "parallelism": "replicas"},
+        "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "GB/s"},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2207_08716_gb300.solver import PTSolver
+
+    rank, local_rank, world = M.rank_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+
+    n, iters = args.n, args.iters
+    p = workload_params(n, iters)
+    seed = M.replica_seed(rank)
+    phi = I.gaussian_porosity(p, centres=(I.perturbed_centre(seed),))
+    stream = torch.cuda.current_stream(dev)
+    s = PTSolver(p, phi, device=dev, stream=stream)
+    del phi
+
+    def one_step():
+        s.step_begin()
+        s.iterate(0, iters, report=False)
+        s.step_end()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region
+    clocks = M.ClockSampler(local_rank)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = s.launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    s.profile_begin()
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    kernels = s.profile_end()
+    clk = clocks.stop()
+    barrier()
+    t_local = e0.elapsed_time(e1) / 1e3
+    launches = s.launch_count() - launches0
+    t = M.max_over_ranks(t_local, dev)
+    ncell = n ** 3
+    total_iters = args.steps * iters
+    a_eff = M.a_eff_bytes(ncell, 8)
+    value = world * a_eff * total_iters / t / 1e9
+    t_it = t / total_iters
+
+    # ---- end to end: host-resident state, copies inside the timed region
+    host = s.host_mirror()
+    s.download(host)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(args.e2e_steps):
+        h2d = s.upload(host)
+        one_step()
+        d2h = s.download(host)
+        torch.cuda.synchronize(dev)
+    t_e2e = M.max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_val = world * a_eff * args.e2e_steps * iters / t_e2e / 1e9
+    del host
+
+    # ---- roofline of the dominant kernel (largest device time in the timed region)
+    hbm, hbm_kind = peaks()
+    dom = max(kernels.items(), key=lambda kv: kv[1][1])
+    name, (nl, ms) = dom
+    per_launch_s = ms / 1e3 / nl
+    bytes_launch = KERNEL_BYTES_PER_CELL.get(name, 0) * ncell
+    flops_cell = KERNEL_FP64_FLOPS_PER_CELL.get(name)
+    traffic_cell = KERNEL_TRAFFIC_PER_CELL.get(name)
+    gbs = bytes_launch / per_launch_s / 1e9
+    roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": gbs / hbm, "peak_source": f"{hbm_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": traffic_cell * ncell if traffic_cell else None,
+            "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": per_launch_s * 1e3}
+    if flops_cell:
+        tf = flops_cell * ncell / per_launch_s / 1e12
+        if tf / FP64_PEAK_TFLOPS > roof["frac"]:
+            roof.update(bound="alu", achieved=tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=tf / FP64_PEAK_TFLOPS,
+                        peak_source="measured FP64 DFMA throughput of this pool's GB300")
+        roof["fp64_tflops"] = tf
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample(args.cpu_n, args.cpu_iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(n, iters), "n": n, "iters_per_step": iters,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (every field 1.07 GB), no flush"},
+            "it_per_s": world * total_iters / t, "t_it_ms": t_it * 1e3,
+            "teff_frac_of_hbm": value / world / hbm,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+            "gpu_launches": launches, "clocks": clk,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()},
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

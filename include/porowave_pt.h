@@ -159,6 +159,20 @@ int pt_step_end(pt_ctx *ctx);
 /* Residual max-norms of the current state (no update). */
 int pt_residual(pt_ctx *ctx, pt_report *rep);
 
+/* Per-kernel device time, measured with CUDA events recorded on the context's stream around
+ * every kernel launch between pt_profile_begin and pt_profile_end (a benchmarking aid; the
+ * events are created on first use and kept by the context). pt_profile_end synchronises the
+ * stream, writes up to max_out entries (one per kernel that ran) and the entry count. */
+typedef struct {
+  char name[24];
+  int64_t launches;
+  double total_ms;
+} pt_kernel_time;
+int pt_profile_begin(pt_ctx *ctx);
+int pt_profile_end(pt_ctx *ctx, pt_kernel_time *out, int32_t max_out, int32_t *n_out);
+/* Kernel launches issued by this context since pt_init. */
+int64_t pt_launch_count(const pt_ctx *ctx);
+
 /* Release the context (not the caller's memory). */
 void pt_destroy(pt_ctx *ctx);
 

@@ -14,5 +14,5 @@ from .binding import (  # noqa: F401
     build, lib_path, OracleParams, OracleRes, State, make_state, init_viscosities,
     begin_step, iteration, iterate_n, end_step, step, system_residual, coefficients, darcy,
     divergence, stress, momentum, advection, tau_II, ORACLE_OK, ORACLE_EINVAL,
-    ORACLE_ENOTCONV, ORACLE_ENAN,
+    ORACLE_ENOTCONV, ORACLE_ENAN, max_threads,
 )

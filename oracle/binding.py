@@ -110,8 +110,15 @@ def _load():
                 f.argtypes = [P] + [_DP] * (n - 1)
                 f.restype = None
             lib.or_stress.argtypes = [P, C.c_double] + [_DP] * 18
+            lib.or_max_threads.argtypes = []
+            lib.or_max_threads.restype = C.c_int
             _lib = lib
     return _lib
+
+
+def max_threads() -> int:
+    """OpenMP threads the oracle uses."""
+    return int(_load().or_max_threads())
 
 
 def _shapes(p: dict) -> dict:

@@ -23,6 +23,7 @@
 #include "pt_oracle.h"
 
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -654,3 +655,5 @@ int or_system_residual(const or_params *p, const or_state *s,
   scratch_free(&w);
   return OR_OK;
 }
+
+int or_max_threads(void) { return omp_get_max_threads(); }

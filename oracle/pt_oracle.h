@@ -104,6 +104,9 @@ int or_system_residual(const or_params *p, const or_state *s,
                        double *out_Vx, double *out_Vy, double *out_Vz, double *out_pt,
                        double *out_pf, double *out_L, double *out_mu, double *out_eta);
 
+/* OpenMP threads the oracle's loops use. */
+int or_max_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

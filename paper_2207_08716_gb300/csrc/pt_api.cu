@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/porowave_pt.h"
 #include "pt_common.cuh"
@@ -70,10 +71,59 @@ struct pt_ctx {
   // stress sub-stepping
   double dtS, dt_cum;
   int nsteps;
-  int checks_in_batch;
+  // launch accounting and optional per-kernel event timing
+  long long launches;
+  bool profiling;
+  struct Rec { int kid; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used;
 };
 
 namespace {
+
+enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
+                K_RESIDUAL_FACES, K_COUNT };
+const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
+                                           "k_picard", "k_begin_step", "k_init_visc",
+                                           "k_residual_faces"};
+
+cudaEvent_t pooled_event(pt_ctx* c) {
+  if (c->pool_used == c->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_used++];
+}
+
+// Launch bracket: counts the launch and, while profiling, records an event pair around it.
+struct LaunchScope {
+  pt_ctx* c;
+  int kid;
+  cudaEvent_t b = nullptr;
+  LaunchScope(pt_ctx* ctx, int id) : c(ctx), kid(id) {
+    c->launches++;
+    if (c->profiling) {
+      cudaEvent_t a = pooled_event(c);
+      b = pooled_event(c);
+      if (a && b) {
+        cudaEventRecord(a, c->stream);
+        c->recs.push_back({kid, a, b});
+      } else {
+        b = nullptr;
+      }
+    }
+  }
+  ~LaunchScope() {
+    if (b) cudaEventRecord(b, c->stream);
+  }
+};
+#define PT_LAUNCH(ctx, kid, ...) \
+  do {                           \
+    LaunchScope scope_(ctx, kid); \
+    __VA_ARGS__;                 \
+  } while (0)
 
 dim3 block_dims() { return dim3(32, 8, 1); }
 dim3 grid_dims(const Box& b) {
@@ -144,21 +194,23 @@ void launch_iteration(pt_ctx* c, int check) {
   const dim3 bl = block_dims(), gr = grid_dims(b);
   const int a = c->cur, n = 1 - c->cur;
   if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-  k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[a], c->logk, c->perm, c->rog);
+  PT_LAUNCH(c, K_PERM, k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[a], c->logk, c->perm, c->rog));
   CentreIn ci{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->mu, c->eta, c->perm,
               c->Pto, c->Pfo, c->txxo, c->tyyo, c->tzzo};
   CentreOut co{c->Pt[n], c->Pf[n], c->s_txx, c->s_tyy, c->s_tzz};
-  k_centres<<<gr, bl, 0, c->stream>>>(b, k, ci, co, 1, c->red, check);
+  PT_LAUNCH(c, K_CENTRES, k_centres<<<gr, bl, 0, c->stream>>>(b, k, ci, co, 1, c->red, check));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
-  k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo);
-  k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[n], c->Pf[n],
-                                        c->Pto, c->Pfo, c->Lo, c->eta, c->phi[n]);
+  PT_LAUNCH(c, K_EDGES, k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo));
+  PT_LAUNCH(c, K_POROSITY,
+            k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[n],
+                                                  c->Pf[n], c->Pto, c->Pfo, c->Lo, c->eta, c->phi[n]));
   FaceIn fi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[n], c->rog, c->mu};
-  k_faces<<<gr, bl, 0, c->stream>>>(b, k, fi, c->Vx, c->Vy, c->Vz, c->Rx, c->Ry, c->Rz, c->red, check);
+  PT_LAUNCH(c, K_FACES,
+            k_faces<<<gr, bl, 0, c->stream>>>(b, k, fi, c->Vx, c->Vy, c->Vz, c->Rx, c->Ry, c->Rz, c->red, check));
   if (check) {
     PicardIn pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[n], c->Pt[n], c->Pf[n]};
-    k_picard<<<gr, bl, 0, c->stream>>>(b, k, pi, c->mu, c->eta, c->red, 1);
+    PT_LAUNCH(c, K_PICARD, k_picard<<<gr, bl, 0, c->stream>>>(b, k, pi, c->mu, c->eta, c->red, 1));
   }
   c->cur = n;
 }
@@ -257,11 +309,15 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   c->dt_cum = 0.0;
   c->nsteps = 0;
   c->cur = 0;
+  c->launches = 0;
+  c->profiling = false;
+  c->pool_used = 0;
   fill_coef(c);
   // zero the whole workspace (damped residuals, old stresses, scratch padding)
   cudaError_t e = cudaMemsetAsync(workspace, 0, pt_workspace_size(grid, num), c->stream);
   if (e == cudaSuccess && !keep_visc) {
-    k_init_visc<<<grid_dims(c->box), block_dims(), 0, c->stream>>>(c->box, c->coef, c->phi[0], c->mu, c->eta);
+    PT_LAUNCH(c, K_INIT_VISC, k_init_visc<<<grid_dims(c->box), block_dims(), 0, c->stream>>>(
+                                   c->box, c->coef, c->phi[0], c->mu, c->eta));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -280,8 +336,8 @@ int pt_step_begin(pt_ctx* c) {
   if (rc != PT_OK) return rc;
   const Box& b = c->box;
   cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-  k_begin_step<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->Pt[0], c->Pf[0], c->phi[0], c->mu,
-                                                             c->Pto, c->Pfo, c->Lo, c->red);
+  PT_LAUNCH(c, K_BEGIN, k_begin_step<<<grid_dims(b), block_dims(), 0, c->stream>>>(
+                             b, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->Pto, c->Pfo, c->Lo, c->red));
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
@@ -340,10 +396,10 @@ int pt_step_end(pt_ctx* c) {
   CentreIn ci{c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->eta, c->perm,
               c->Pto, c->Pfo, c->txxo, c->tyyo, c->tzzo};
   CentreOut co{nullptr, nullptr, c->txx, c->tyy, c->tzz};
-  k_centres<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->coef, ci, co, 0, c->red, 0);
+  PT_LAUNCH(c, K_CENTRES, k_centres<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->coef, ci, co, 0, c->red, 0));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->txy, c->txz, c->tyz};
-  k_edges<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->coef, ei, eo);
+  PT_LAUNCH(c, K_EDGES, k_edges<<<grid_dims(b), block_dims(), 0, c->stream>>>(b, c->coef, ei, eo));
   c->dt_cum += c->num.dt;
   return cuda_status(cudaGetLastError());
 }
@@ -391,18 +447,18 @@ int pt_residual(pt_ctx* c, pt_report* rep) {
   const Coef& k = c->coef;
   const dim3 bl = block_dims(), gr = grid_dims(b);
   cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-  k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[0], c->logk, c->perm, c->rog);
+  PT_LAUNCH(c, K_PERM, k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[0], c->logk, c->perm, c->rog));
   CentreIn ci{c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->eta, c->perm,
               c->Pto, c->Pfo, c->txxo, c->tyyo, c->tzzo};
   CentreOut co{c->Pt[1], c->Pf[1], c->s_txx, c->s_tyy, c->s_tzz};   // updates go to scratch
-  k_centres<<<gr, bl, 0, c->stream>>>(b, k, ci, co, 1, c->red, 1);
+  PT_LAUNCH(c, K_CENTRES, k_centres<<<gr, bl, 0, c->stream>>>(b, k, ci, co, 1, c->red, 1));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
-  k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo);
+  PT_LAUNCH(c, K_EDGES, k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo));
   FaceIn fi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[0], c->rog, c->mu};
-  k_residual_faces<<<gr, bl, 0, c->stream>>>(b, k, fi, c->red);
+  PT_LAUNCH(c, K_RESIDUAL_FACES, k_residual_faces<<<gr, bl, 0, c->stream>>>(b, k, fi, c->red));
   PicardIn pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[0], c->Pt[0], c->Pf[0]};
-  k_picard<<<gr, bl, 0, c->stream>>>(b, k, pi, c->mu, c->eta, c->red, 0);
+  PT_LAUNCH(c, K_PICARD, k_picard<<<gr, bl, 0, c->stream>>>(b, k, pi, c->mu, c->eta, c->red, 0));
   if (cudaGetLastError() != cudaSuccess) return PT_ECUDA;
   std::memset(rep, 0, sizeof *rep);
   rc = read_report(c, rep);
@@ -410,9 +466,49 @@ int pt_residual(pt_ctx* c, pt_report* rep) {
   return rc;
 }
 
+int pt_profile_begin(pt_ctx* c) {
+  if (!c) return PT_EINVAL;
+  c->recs.clear();
+  c->pool_used = 0;
+  c->profiling = true;
+  return PT_OK;
+}
+
+int pt_profile_end(pt_ctx* c, pt_kernel_time* out, int32_t max_out, int32_t* n_out) {
+  if (!c || (max_out > 0 && !out)) return PT_EINVAL;
+  c->profiling = false;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PT_ECUDA;
+  double ms[K_COUNT] = {0};
+  long long cnt[K_COUNT] = {0};
+  for (const auto& r : c->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return PT_ECUDA;
+    ms[r.kid] += t;
+    cnt[r.kid] += 1;
+  }
+  int32_t n = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (!cnt[k]) continue;
+    if (n < max_out) {
+      std::memset(out[n].name, 0, sizeof out[n].name);
+      std::strncpy(out[n].name, kKernelNames[k], sizeof out[n].name - 1);
+      out[n].launches = cnt[k];
+      out[n].total_ms = ms[k];
+    }
+    ++n;
+  }
+  if (n_out) *n_out = n < max_out ? n : max_out;
+  c->recs.clear();
+  c->pool_used = 0;
+  return PT_OK;
+}
+
+int64_t pt_launch_count(const pt_ctx* c) { return c ? (int64_t)c->launches : -1; }
+
 void pt_destroy(pt_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   cudaFreeHost(c->h_red);
   delete c;
 }

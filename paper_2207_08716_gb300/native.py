@@ -121,6 +121,10 @@ def num_from(p: dict, precision: int = PT_FP64, iters_per_graph: int = 0) -> Num
     return nm
 
 
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
 # Every exported symbol of include/porowave_pt.h with its ctypes signature.
 SIGNATURES = {
     "pt_field_elems": (C.c_size_t, [C.POINTER(Grid)]),
@@ -133,6 +137,9 @@ SIGNATURES = {
     "pt_iterate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(Report)]),
     "pt_step_end": (C.c_int, [C.c_void_p]),
     "pt_residual": (C.c_int, [C.c_void_p, C.POINTER(Report)]),
+    "pt_profile_begin": (C.c_int, [C.c_void_p]),
+    "pt_profile_end": (C.c_int, [C.c_void_p, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
+    "pt_launch_count": (C.c_int64, [C.c_void_p]),
     "pt_destroy": (None, [C.c_void_p]),
     "pt_strerror": (C.c_char_p, [C.c_int]),
 }

@@ -127,6 +127,43 @@ class PTSolver:
         self._check(self.lib.pt_residual(self.ctx, C.byref(rep)), "pt_residual")
         return rep.as_dict()
 
+    # ------------------------------------------------------------- measurement aids
+    def profile_begin(self) -> None:
+        self._check(self.lib.pt_profile_begin(self.ctx), "pt_profile_begin")
+
+    def profile_end(self) -> dict:
+        """{kernel name: (launches, total ms)} measured with CUDA events on the solver stream."""
+        out = (N.KernelTime * 32)()
+        n = C.c_int32(0)
+        self._check(self.lib.pt_profile_end(self.ctx, out, 32, C.byref(n)), "pt_profile_end")
+        return {out[i].name.decode(): (int(out[i].launches), float(out[i].total_ms)) for i in range(n.value)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.pt_launch_count(self.ctx))
+
+    # ------------------------------------------------ host-resident state (end to end)
+    def host_mirror(self) -> dict:
+        """Pinned host tensors in the padded box layout, one per field."""
+        return {k: torch.empty(self.box_shape, dtype=torch.float64, pin_memory=True)
+                for k in N.FIELD_NAMES}
+
+    def upload(self, host: dict) -> int:
+        """Copy host (pinned, box layout) fields to the device on the solver stream; bytes."""
+        nbytes = 0
+        with torch.cuda.stream(self.stream):
+            for k, h in host.items():
+                self.f[k].copy_(h, non_blocking=True)
+                nbytes += h.numel() * h.element_size()
+        return nbytes
+
+    def download(self, host: dict) -> int:
+        nbytes = 0
+        with torch.cuda.stream(self.stream):
+            for k, h in host.items():
+                h.copy_(self.f[k], non_blocking=True)
+                nbytes += h.numel() * h.element_size()
+        return nbytes
+
     def close(self) -> None:
         if getattr(self, "ctx", None):
             self.lib.pt_destroy(self.ctx)
