@@ -173,6 +173,32 @@ int pt_profile_end(pt_ctx *ctx, pt_kernel_time *out, int32_t max_out, int32_t *n
 /* Kernel launches issued by this context since pt_init. */
 int64_t pt_launch_count(const pt_ctx *ctx);
 
+/* ---- Residual norms with no allocation at all -------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory when they need the norms - e.g. a health check inside a run whose
+ * HBM is entirely held by a pool allocator, where a raw cudaMalloc would fail or fragment the
+ * pool, or a timing-critical loop that cannot afford the implicit device synchronisation of
+ * cudaMalloc / cudaFree. It computes the same four norms as pt_residual from fields the caller
+ * passes (current fields, old-step fields, the stress sub-step dtS) without a context or
+ * workspace: its intermediate arrays live in one fixed device array inside this library,
+ * PT_RESIDUAL_STATIC_SCRATCH_BYTES large, which every GPU that loads the library holds until
+ * the process exits. Grids whose padded box needs more than 10 arrays of that array (boxes of
+ * about 838,000 elements, e.g. 90^3 cells) are rejected with PT_ESPACE before any device work.
+ * Layout, alignment and argument rules are those of pt_init; the current device must be the
+ * one holding the fields. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture. Every
+ * call shares the array and clears its reduction block first; calls whose device work
+ * overlaps (other streams or host threads) race on it. Calls no cudaMalloc / cudaFree and no
+ * allocating library routine; synchronises `stream` to read the norms into `rep`. */
+#define PT_RESIDUAL_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+typedef struct {
+  const double *Pto, *Pfo;                          /* pressures at the start of the step */
+  const double *txxo, *tyyo, *tzzo, *txyo, *txzo, *tyzo;  /* old-step stresses          */
+} pt_old_fields;
+int pt_residual_static(const pt_grid *grid, const pt_phys *phys, const pt_num *num,
+                       const pt_fields *fields, const pt_old_fields *old, double dtS,
+                       void *stream, pt_report *rep);
+
 /* Release the context (not the caller's memory). */
 void pt_destroy(pt_ctx *ctx);
 

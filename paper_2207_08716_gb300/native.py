@@ -16,7 +16,7 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INC = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
-SOURCES = ("pt_api.cu", "pt_ref_kernels.cu")
+SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_static.cu")
 HEADERS = ("pt_common.cuh", "pt_kernels.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -121,6 +121,10 @@ def num_from(p: dict, precision: int = PT_FP64, iters_per_graph: int = 0) -> Num
     return nm
 
 
+class OldFields(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("Pto", "Pfo", "txxo", "tyyo", "tzzo", "txyo", "txzo", "tyzo")]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -140,6 +144,8 @@ SIGNATURES = {
     "pt_profile_begin": (C.c_int, [C.c_void_p]),
     "pt_profile_end": (C.c_int, [C.c_void_p, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
     "pt_launch_count": (C.c_int64, [C.c_void_p]),
+    "pt_residual_static": (C.c_int, [C.POINTER(Grid), C.POINTER(Phys), C.POINTER(Num), C.POINTER(Fields),
+                                     C.POINTER(OldFields), C.c_double, C.c_void_p, C.POINTER(Report)]),
     "pt_destroy": (None, [C.c_void_p]),
     "pt_strerror": (C.c_char_p, [C.c_int]),
 }
