@@ -39,13 +39,20 @@ FP64_PEAK_TFLOPS = 1.005
 KERNEL_BYTES_PER_CELL = {
     "k_perm": 3 * 8, "k_centres": 19 * 8, "k_edges": 10 * 8, "k_porosity": 11 * 8,
     "k_faces": 21 * 8, "k_picard": 13 * 8, "k_begin_step": 6 * 8,
+    # FP64-lean form: cells reads 25 arrays (V, Pt, Pf, phi, w, k, Pto, Pfo, phio, Eo, iEo, ieta,
+    # idtp, cm2, 3 toa_ii, 3 em2, 3 toa_e) and writes 11 (Pt, Pf, phi, w, k, 6 stresses);
+    # faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
+    "k_lean_cells": 36 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
+    "k_lean_begin": 11 * 8,
 }
-# FP64 flops per cell and launch counted by ncu (dfma x 2 + dadd + dmul) on the 128^3 case;
-# None until measured for the current kernel source.
-KERNEL_FP64_FLOPS_PER_CELL = {}
-# DRAM bytes per cell and launch from one ncu capture (dram__bytes_read + write), None if the
-# kernel changed since the capture.
-KERNEL_TRAFFIC_PER_CELL = {}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2}
+# FP64 flops per cell and launch (DFMA x 2 + DADD + DMUL thread instructions) from one ncu
+# capture of the kernel on the 191^3 case (profiles/k_lean_fp64_191.md); a kernel missing here
+# has no current count.
+KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 211.0, "k_lean_faces": 52.7, "k_centres": 237.0}
+# DRAM bytes per cell and launch (dram__bytes_read.sum + dram__bytes_write.sum) from the same
+# captures; the 191^3 case's per-cell figure scales with the cells of a launch.
+KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 287.0, "k_lean_faces": 181.0, "k_centres": 150.6}
 
 
 def parse():
@@ -60,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=191, help="sub-block edge of the CPU sample")
     ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="fp64",
+                    help="fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
     return ap.parse_args()
 
 
@@ -72,15 +81,16 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def workload_params(n: int, iters: int) -> dict:
+def workload_params(n: int, iters: int, precision: str = "fp64") -> dict:
     p = I.large_params(n)
     p["max_iter"] = iters
+    p["precision"] = PRECISIONS[precision]
     return p
 
 
-def workload_name(n: int, iters: int) -> str:
-    return (f"FP64 two-phase porosity-wave PT solver, {n}^3 cells, one seed-perturbed centred "
-            f"Gaussian anomaly, {iters} PT iterations per physical step")
+def workload_name(n: int, iters: int, precision: str = "fp64") -> str:
+    return (f"two-phase porosity-wave PT solver ({precision}), {n}^3 cells, one seed-perturbed "
+            f"centred Gaussian anomaly, {iters} PT iterations per physical step")
 
 
 # ------------------------------------------------------------------------ CPU (oracle) leg
@@ -147,7 +157,7 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=dev)
 
     n, iters = args.n, args.iters
-    p = workload_params(n, iters)
+    p = workload_params(n, iters, args.precision)
     seed = M.replica_seed(rank)
     phi = I.gaussian_porosity(p, centres=(I.perturbed_centre(seed),))
     stream = torch.cuda.current_stream(dev)
@@ -239,7 +249,8 @@ def run_native(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_name(n, iters), "n": n, "iters_per_step": iters,
+            "config": {"workload": workload_name(n, iters, args.precision), "n": n, "iters_per_step": iters,
+                       "precision": args.precision,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (every field 1.07 GB), no flush"},
             "it_per_s": world * total_iters / t, "t_it_ms": t_it * 1e3,

@@ -59,7 +59,12 @@ enum {
   PT_ESPACE = -6      /* workspace smaller than pt_workspace_size()                            */
 };
 
-enum { PT_FP64 = 0, PT_FP32 = 1 };
+/* Arithmetic of the PT iterations. PT_FP64: FP64 throughout, in the FP64-lean form (two
+ * fused kernels per iteration, coefficients refreshed at Picard updates). PT_FP64_STEPWISE:
+ * FP64, one kernel per data-flow step (the straightforward form, kept for comparison).
+ * PT_FP32: FP32 PT iterations with FP64 residuals, defect correction and porosity time
+ * integration. Fields at the boundary are FP64 in every mode. */
+enum { PT_FP64 = 0, PT_FP32 = 1, PT_FP64_STEPWISE = 2 };
 
 /* Cell-centred grid on [0, lx] x [0, ly] x [0, lz]; dx = lx / nx. */
 typedef struct {
@@ -101,7 +106,7 @@ typedef struct {
   double cfl_pf;          /* dtau_Pf = cfl_pf h^2 (1 + beta_d B / alpha) / max local k      */
   double dtpt_scale;      /* dtau_Pt = dtpt_scale mu (1 + beta_n) / nz                      */
   double xsi_w;           /* stress sub-step dtS = max(mu) / (G xsi_w)                      */
-  int32_t precision;      /* PT_FP64 (all arithmetic FP64) or PT_FP32 (see pt_init)        */
+  int32_t precision;      /* PT_FP64, PT_FP64_STEPWISE or PT_FP32 (see the enum above)     */
   int32_t iters_per_graph;/* PT iterations per CUDA-graph replay; 0 = nup                  */
 } pt_num;
 

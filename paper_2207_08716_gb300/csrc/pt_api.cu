@@ -17,6 +17,7 @@
 #include "../../include/porowave_pt.h"
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
+#include "pt_lean.cuh"
 
 using namespace pt;
 
@@ -24,7 +25,8 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kPitchMultiple = 16;
-constexpr int kWorkArrays = 23;
+constexpr int kRefArrays = 23;   // step-by-step path
+constexpr int kLeanArrays = 23;  // extra arrays of the FP64-lean path
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -66,6 +68,12 @@ struct pt_ctx {
   // workspace
   double *Pto, *Pfo, *Lo, *txxo, *tyyo, *tzzo, *txyo, *txzo, *tyzo, *Rx, *Ry, *Rz, *perm, *rog;
   double *s_txx, *s_tyy, *s_tzz, *s_txy, *s_txz, *s_tyz;
+  // FP64-lean path (precision PT_FP64)
+  bool lean;
+  double *lperm[2], *lw[2], *phio, *Eo, *iEo;
+  double *toa_xx, *toa_yy, *toa_zz, *toa_xy, *toa_xz, *toa_yz, *cm2, *idtp, *ieta;
+  double *em2_xy, *em2_xz, *em2_yz, *dtv_x, *dtv_y, *dtv_z, *K0;
+  LeanCoef<double> lcoef;
   unsigned long long* red;       // device reduction block (RED_N slots)
   unsigned long long* h_red;     // pinned host copy
   // stress sub-stepping
@@ -83,10 +91,12 @@ struct pt_ctx {
 namespace {
 
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
-                K_RESIDUAL_FACES, K_COUNT };
+                K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
+                K_LEAN_K0, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
-                                           "k_residual_faces"};
+                                           "k_residual_faces", "k_lean_cells", "k_lean_faces",
+                                           "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -129,6 +139,8 @@ dim3 block_dims() { return dim3(32, 8, 1); }
 dim3 grid_dims(const Box& b) {
   return dim3((unsigned)((b.nx + 1 + 31) / 32), (unsigned)((b.ny + 1 + 7) / 8), (unsigned)(b.nz + 1));
 }
+
+void fill_lean_coef(pt_ctx* c);
 
 void fill_coef(pt_ctx* c) {
   const pt_grid& g = c->grid;
@@ -173,6 +185,40 @@ void fill_coef(pt_ctx* c) {
   k.dtaupt_fac = n.dtpt_scale * (1.0 + n.beta_n) / g.nz;
   k.dtaupf_fac = n.cfl_pf * k.h2 * (1.0 + p.beta_d * p.B / p.alpha);
   k.rGdtS = c->dtS > 0 ? 1.0 / (p.G * c->dtS) : 0.0;
+  fill_lean_coef(c);
+}
+
+void fill_lean_coef(pt_ctx* c) {
+  const Coef& k = c->coef;
+  const pt_grid& g = c->grid;
+  const pt_phys& p = c->phys;
+  LeanCoef<double>& L = c->lcoef;
+  const double dz = g.lz / g.nz;
+  L.rdx = k.rdx; L.rdy = k.rdy; L.rdz = k.rdz;
+  L.hrdx = 0.5 * k.rdx; L.hrdy = 0.5 * k.rdy; L.hrdz = 0.5 * k.rdz;
+  L.hrdx2 = 0.5 * k.rdx * k.rdx; L.hrdy2 = 0.5 * k.rdy * k.rdy; L.hrdz2 = 0.5 * k.rdz * k.rdz;
+  L.buoy_dz = (k.rhof_g - k.rho_bg_g) * dz;
+  L.bd_rdt = k.beta_d * k.rdt;
+  L.bda_B_rdt = k.beta_d * k.alpha / k.B * k.rdt;
+  L.alpha = k.alpha;
+  L.alpha_B = k.alpha / k.B;
+  L.beta_n = k.beta_n;
+  L.beta_phi = k.beta_phi;
+  L.dt = k.dt;
+  L.rphi0 = k.rphi0;
+  L.k0 = k.k0;
+  L.phi0 = k.phi0;
+  L.drho_g = p.rhof_g - p.rhos_g;
+  L.ifac_pf = 1.0 / k.dtaupf_fac;
+  L.rrho_i = k.rrho_i;
+  L.damp_x = k.damp_x; L.damp_y = k.damp_y; L.damp_z = k.damp_z;
+  L.compaction_on = k.compaction_on;
+  L.powerlaw_on = k.powerlaw_on;
+  L.mu0 = k.mu0; L.eta0 = k.eta0; L.tau0 = k.tau0; L.n_pow = k.n_pow;
+  L.rel_mu = k.rel_mu; L.rel_eta = k.rel_eta; L.R_weak = k.R_weak;
+  L.rGdtS = k.rGdtS;
+  L.dtaupt_fac = k.dtaupt_fac;
+  L.dtauv_fac = k.dtauv_fac;
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
@@ -183,12 +229,22 @@ int sync_current_to_caller(pt_ctx* c) {
   cudaError_t e = cudaMemcpyAsync(c->Pt[0], c->Pt[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->Pf[0], c->Pf[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->phi[0], c->phi[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (c->lean) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->lw[0], c->lw[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->lperm[0], c->lperm[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
   c->cur = 0;
   return cuda_status(e);
 }
 
 // One PT iteration number `it` (1-based); check = Picard update + norms.
+void launch_iteration_lean(pt_ctx* c, int check);
+
 void launch_iteration(pt_ctx* c, int check) {
+  if (c->lean) {
+    launch_iteration_lean(c, check);
+    return;
+  }
   const Box& b = c->box;
   const Coef& k = c->coef;
   const dim3 bl = block_dims(), gr = grid_dims(b);
@@ -211,6 +267,42 @@ void launch_iteration(pt_ctx* c, int check) {
   if (check) {
     PicardIn pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[n], c->Pt[n], c->Pf[n]};
     PT_LAUNCH(c, K_PICARD, k_picard<<<gr, bl, 0, c->stream>>>(b, k, pi, c->mu, c->eta, c->red, 1));
+  }
+  c->cur = n;
+}
+
+void launch_lean_coef(pt_ctx* c) {
+  const Box& b = c->box;
+  LeanCoefIn<double> ci{c->mu, c->eta, c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
+  LeanCoefOut<double> co{c->cm2, c->toa_xx, c->toa_yy, c->toa_zz, c->idtp, c->ieta, c->em2_xy,
+                         c->em2_xz, c->em2_yz, c->toa_xy, c->toa_xz, c->toa_yz, c->dtv_x, c->dtv_y,
+                         c->dtv_z};
+  PT_LAUNCH(c, K_LEAN_COEF, lean_coef<double>(grid_dims(b), block_dims(), c->stream, b, c->lcoef, ci, co));
+}
+
+// One PT iteration of the FP64-lean form: cells (pressures, stresses, porosity), faces
+// (momentum, velocities), and on check iterations the Picard update and coefficient refresh.
+void launch_iteration_lean(pt_ctx* c, int check) {
+  const Box& b = c->box;
+  const dim3 bl = block_dims(), gr = grid_dims(b);
+  const int a = c->cur, n = 1 - c->cur;
+  if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  LeanCellIn<double> ci{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->lw[a], c->lperm[a],
+                        c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->ieta, c->idtp, c->cm2,
+                        c->toa_xx, c->toa_yy, c->toa_zz, c->em2_xy, c->em2_xz, c->em2_yz,
+                        c->toa_xy, c->toa_xz, c->toa_yz, c->logk ? c->K0 : nullptr};
+  LeanCellOut<double> co{c->Pt[n], c->Pf[n], c->phi[n], c->lw[n], c->lperm[n], c->s_txx, c->s_tyy,
+                         c->s_tzz, c->s_txy, c->s_txz, c->s_tyz};
+  PT_LAUNCH(c, K_LEAN_CELLS, lean_cells<double>(gr, bl, c->stream, b, c->lcoef, ci, co, c->red, check));
+  LeanFaceIn<double> fi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[n],
+                        c->phi[a], c->dtv_x, c->dtv_y, c->dtv_z};
+  PT_LAUNCH(c, K_LEAN_FACES, lean_faces<double>(gr, bl, c->stream, b, c->lcoef, fi, c->Vx, c->Vy, c->Vz, c->Rx,
+                                                   c->Ry, c->Rz, c->red, check));
+  if (check) {
+    LeanPicardIn<double> pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[n],
+                            c->Pt[n], c->Pf[n]};
+    PT_LAUNCH(c, K_LEAN_PICARD, lean_picard<double>(gr, bl, c->stream, b, c->lcoef, pi, c->mu, c->eta, c->red));
+    launch_lean_coef(c);
   }
   c->cur = n;
 }
@@ -255,7 +347,8 @@ int32_t pt_pitch_x(const pt_grid* grid) {
 size_t pt_workspace_size(const pt_grid* grid, const pt_num* num) {
   if (!grid_ok(grid) || !num) return 0;
   const Box b = make_box(grid);
-  return kWorkArrays * align_up((size_t)b.n * sizeof(double), kAlign) + kAlign;
+  const int arrays = kRefArrays + (num->precision == PT_FP64 ? kLeanArrays : 0);
+  return arrays * align_up((size_t)b.n * sizeof(double), kAlign) + kAlign;
 }
 
 int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num* num,
@@ -269,7 +362,7 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   if (!(num->rho_i > 0) || !(num->cfl_v > 0) || !(num->cfl_pf > 0) || !(num->dtpt_scale > 0) ||
       !(num->xsi_w > 0))
     return PT_EINVAL;
-  if (num->precision != PT_FP64) return PT_EINVAL;
+  if (num->precision != PT_FP64 && num->precision != PT_FP64_STEPWISE) return PT_EINVAL;
   if (!(phys->phi0 > 0 && phys->phi0 < 1) || !(phys->k0 > 0) || !(phys->mu0 > 0) || !(phys->eta0 > 0) ||
       !(phys->G > 0) || !(phys->alpha > 0) || !(phys->B > 0) || !(phys->tau0 > 0) || !(phys->R_weak > 0))
     return PT_EINVAL;
@@ -295,12 +388,18 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   c->mu = f->mu; c->eta = f->eta; c->logk = f->logk;
   const size_t stride = align_up((size_t)c->box.n * sizeof(double), kAlign);
   char* w = (char*)workspace;
-  double** slots[kWorkArrays] = {&c->Pt[1], &c->Pf[1], &c->phi[1], &c->Pto, &c->Pfo, &c->Lo,
-                                 &c->txxo, &c->tyyo, &c->tzzo, &c->txyo, &c->txzo, &c->tyzo,
-                                 &c->Rx, &c->Ry, &c->Rz, &c->perm, &c->rog, &c->s_txx,
-                                 &c->s_tyy, &c->s_tzz, &c->s_txy, &c->s_txz, &c->s_tyz};
-  for (int s = 0; s < kWorkArrays; ++s) *slots[s] = (double*)(w + s * stride);
-  c->red = (unsigned long long*)(w + kWorkArrays * stride);
+  c->lean = num->precision == PT_FP64;
+  double** slots[kRefArrays + kLeanArrays] = {
+      &c->Pt[1], &c->Pf[1], &c->phi[1], &c->Pto, &c->Pfo, &c->Lo, &c->txxo, &c->tyyo, &c->tzzo,
+      &c->txyo, &c->txzo, &c->tyzo, &c->Rx, &c->Ry, &c->Rz, &c->perm, &c->rog, &c->s_txx,
+      &c->s_tyy, &c->s_tzz, &c->s_txy, &c->s_txz, &c->s_tyz,
+      // FP64-lean extras
+      &c->lperm[0], &c->lperm[1], &c->lw[0], &c->lw[1], &c->phio, &c->Eo, &c->iEo, &c->toa_xx,
+      &c->toa_yy, &c->toa_zz, &c->toa_xy, &c->toa_xz, &c->toa_yz, &c->cm2, &c->idtp, &c->ieta,
+      &c->em2_xy, &c->em2_xz, &c->em2_yz, &c->dtv_x, &c->dtv_y, &c->dtv_z, &c->K0};
+  const int arrays = kRefArrays + (c->lean ? kLeanArrays : 0);
+  for (int s = 0; s < arrays; ++s) *slots[s] = (double*)(w + s * stride);
+  c->red = (unsigned long long*)(w + arrays * stride);
   if (cudaMallocHost(&c->h_red, RED_N * sizeof(unsigned long long)) != cudaSuccess) {
     delete c;
     return PT_ECUDA;
@@ -315,6 +414,11 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   fill_coef(c);
   // zero the whole workspace (damped residuals, old stresses, scratch padding)
   cudaError_t e = cudaMemsetAsync(workspace, 0, pt_workspace_size(grid, num), c->stream);
+  if (e == cudaSuccess && c->lean && c->logk) {
+    PT_LAUNCH(c, K_LEAN_K0, lean_k0<double>(grid_dims(c->box), block_dims(), c->stream, c->box, c->phys.k0, c->logk,
+                                            c->K0));
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && !keep_visc) {
     PT_LAUNCH(c, K_INIT_VISC, k_init_visc<<<grid_dims(c->box), block_dims(), 0, c->stream>>>(
                                    c->box, c->coef, c->phi[0], c->mu, c->eta));
@@ -336,8 +440,14 @@ int pt_step_begin(pt_ctx* c) {
   if (rc != PT_OK) return rc;
   const Box& b = c->box;
   cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-  PT_LAUNCH(c, K_BEGIN, k_begin_step<<<grid_dims(b), block_dims(), 0, c->stream>>>(
-                             b, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->Pto, c->Pfo, c->Lo, c->red));
+  if (c->lean) {
+    LeanBeginIn<double> bi{c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->logk ? c->K0 : nullptr};
+    LeanBeginOut<double> bo{c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->lw[0], c->lperm[0]};
+    PT_LAUNCH(c, K_LEAN_BEGIN, lean_begin<double>(grid_dims(b), block_dims(), c->stream, b, c->lcoef, bi, bo, c->red));
+  } else {
+    PT_LAUNCH(c, K_BEGIN, k_begin_step<<<grid_dims(b), block_dims(), 0, c->stream>>>(
+                               b, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->Pto, c->Pfo, c->Lo, c->red));
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
@@ -359,6 +469,10 @@ int pt_step_begin(pt_ctx* c) {
   }
   c->nsteps += 1;
   fill_coef(c);
+  if (c->lean && e == cudaSuccess) {
+    launch_lean_coef(c);
+    e = cudaGetLastError();
+  }
   return cuda_status(e);
 }
 

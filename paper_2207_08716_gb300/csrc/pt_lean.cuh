@@ -1,0 +1,87 @@
+// pt_lean.cuh — argument structs and declarations of the FP64-lean PT kernels
+// (pt_lean_kernels.cu). T is the field type (double; float for the FP32 form).
+#pragma once
+
+#include "pt_common.cuh"
+
+namespace pt {
+
+// Per-step scalars in the field type, pre-folded so each kernel multiplies instead of divides.
+template <class T>
+struct LeanCoef {
+  T rdx, rdy, rdz;              // 1 / dx
+  T hrdx, hrdy, hrdz;           // 1 / (2 dx)
+  T hrdx2, hrdy2, hrdz2;        // 1 / (2 dx^2)
+  T buoy_dz;                    // (rho_f - rho_BG) g dz
+  T bd_rdt, bda_B_rdt;          // beta_d / dt, beta_d alpha / (B dt)
+  T alpha, alpha_B;             // alpha, alpha / B
+  T beta_n, beta_phi, dt;
+  T rphi0, k0, phi0, drho_g;    // 1 / phi0, k0, phi0, (rho_f - rho_s) g
+  T ifac_pf;                    // 1 / (cfl_pf h^2 (1 + beta_d B / alpha)): 1/dtau_Pf = kmax * ifac_pf
+  T rrho_i, damp_x, damp_y, damp_z;
+  int compaction_on, powerlaw_on;
+  // Picard and coefficient refresh run in FP64
+  double mu0, eta0, tau0, n_pow, rel_mu, rel_eta, R_weak;
+  double rGdtS, dtaupt_fac, dtauv_fac;
+};
+
+template <class T>
+struct LeanCellIn {
+  const T *Vx, *Vy, *Vz, *Pt, *Pf, *phi, *w, *perm;
+  const T *Pto, *Pfo, *phio, *Eo, *iEo;
+  const T *ieta, *idtp, *cm2, *toa_xx, *toa_yy, *toa_zz;
+  const T *em2_xy, *em2_xz, *em2_yz, *toa_xy, *toa_xz, *toa_yz;
+  const T *K0;  // k0 e^logk per cell, or null (scalar k0)
+};
+template <class T>
+struct LeanCellOut {
+  T *Pt, *Pf, *phi, *w, *perm, *txx, *tyy, *tzz, *txy, *txz, *tyz;
+};
+template <class T>
+struct LeanFaceIn {
+  const T *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt1, *phi, *dtv_x, *dtv_y, *dtv_z;
+};
+template <class T>
+struct LeanPicardIn {
+  const T *txx, *tyy, *tzz, *txy, *txz, *tyz, *phi1, *Pt1, *Pf1;
+};
+template <class T>
+struct LeanCoefIn {
+  const T *mu, *eta;
+  const T *txxo, *tyyo, *tzzo, *txyo, *txzo, *tyzo;
+};
+template <class T>
+struct LeanCoefOut {
+  T *cm2, *toa_xx, *toa_yy, *toa_zz, *idtp, *ieta;
+  T *em2_xy, *em2_xz, *em2_yz, *toa_xy, *toa_xz, *toa_yz;
+  T *dtv_x, *dtv_y, *dtv_z;
+};
+template <class T>
+struct LeanBeginIn {
+  const T *Pt, *Pf, *phi, *mu, *K0;
+};
+template <class T>
+struct LeanBeginOut {
+  T *Pto, *Pfo, *phio, *Eo, *iEo, *w, *perm;
+};
+
+// Host-side launchers (the kernels are templates and are launched from their own TU).
+template <class T>
+void lean_cells(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, const LeanCellIn<T>& in,
+                const LeanCellOut<T>& out, unsigned long long* red, int check);
+template <class T>
+void lean_faces(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, const LeanFaceIn<T>& in,
+                T* Vx, T* Vy, T* Vz, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check);
+template <class T>
+void lean_picard(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, const LeanPicardIn<T>& in,
+                 T* mu, T* eta, unsigned long long* red);
+template <class T>
+void lean_coef(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, const LeanCoefIn<T>& in,
+               const LeanCoefOut<T>& out);
+template <class T>
+void lean_begin(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, const LeanBeginIn<T>& in,
+                const LeanBeginOut<T>& out, unsigned long long* red);
+template <class T>
+void lean_k0(dim3 gr, dim3 bl, cudaStream_t st, Box b, double k0, const double* logk, T* K0);
+
+}  // namespace pt

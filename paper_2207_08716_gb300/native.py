@@ -16,15 +16,15 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INC = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
-SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_static.cu")
-HEADERS = ("pt_common.cuh", "pt_kernels.cuh")
+SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_static.cu")
+HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
 _lib = None
 
 PT_OK, PT_EINVAL, PT_ENOTCONV, PT_ENAN, PT_ETIMEOUT, PT_ECUDA, PT_ESPACE = 0, -1, -2, -3, -4, -5, -6
-PT_FP64, PT_FP32 = 0, 1
+PT_FP64, PT_FP32, PT_FP64_STEPWISE = 0, 1, 2
 
 
 def _inputs():

@@ -35,11 +35,16 @@ def assert_fields(s, st, names=FIELDS, tol=TOL):
     return errs
 
 
+FP64_MODES = (0, 2)   # PT_FP64 (lean form), PT_FP64_STEPWISE
+
+
+@pytest.mark.parametrize("mode", FP64_MODES)
 @pytest.mark.parametrize("dims, niter", [((32, 32, 32), 450), ((48, 40, 36), 150),
                                          ((7, 9, 11), 300), ((1, 5, 6), 60), ((17, 1, 3), 45)])
-def test_iterations_match_oracle(dims, niter):
+def test_iterations_match_oracle(dims, niter, mode):
     PTSolver = _solver()
     p = I.c1_params(*dims)
+    p["precision"] = mode
     phi = I.gaussian_porosity(p, centres=((0.47, 0.52, 0.55),))
     s = PTSolver(p, phi)
     s.step_begin()
@@ -54,11 +59,12 @@ def test_iterations_match_oracle(dims, niter):
     s.close()
 
 
-def test_random_state_with_numerical_compressibility_and_logk():
+@pytest.mark.parametrize("mode", FP64_MODES)
+def test_random_state_with_numerical_compressibility_and_logk(mode):
     """Off-rest random state, beta_n = 10, a log-permeability field, weakening active."""
     PTSolver = _solver()
     p = I.c1_params(21, 18, 23)
-    p.update(beta_n=10.0, lx=1.1, ly=0.9, lz=1.2)
+    p.update(beta_n=10.0, lx=1.1, ly=0.9, lz=1.2, precision=mode)
     rs = I.random_state(p, seed=7, scale=1e-3)
     rng = np.random.default_rng(3)
     logk = 0.3 * rng.standard_normal((23, 18, 21))
@@ -75,11 +81,13 @@ def test_random_state_with_numerical_compressibility_and_logk():
     s.close()
 
 
-def test_two_steps_stress_substepping():
+@pytest.mark.parametrize("mode", FP64_MODES)
+def test_two_steps_stress_substepping(mode):
     """Two physical steps of fixed iteration counts: end-of-step stresses, the old-stress
     refresh rule and dt_cum bookkeeping match."""
     PTSolver = _solver()
     p = I.c1_params(20, 18, 16)
+    p["precision"] = mode
     p["xsi_w"] = 0.05          # dtS = 20 mu/G: with dt_cum < dtS the second step keeps tau_o
     phi = I.gaussian_porosity(p)
     s = PTSolver(p, phi)
