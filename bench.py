@@ -44,15 +44,21 @@ KERNEL_BYTES_PER_CELL = {
     # faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
     "k_lean_cells": 36 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
     "k_lean_begin": 11 * 8,
+    # mixed precision, FP32 correction iterations: cells reads 17 arrays (3 dV, dPt, dPf, cc, k,
+    # idtp, iden_pt, idtf, iden_pf, r_pt, r_pf, cm2, 3 em2) and writes 8 (dPt, dPf, 6 stresses);
+    # faces reads 19 (6 stresses, dPt, 3 dtv, 3 r_F, 3 R, 3 dV) and writes 6 (3 R, 3 dV)
+    "k_corr_cells": 25 * 4, "k_corr_faces": 25 * 4,
 }
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2}
 # FP64 flops per cell and launch (DFMA x 2 + DADD + DMUL thread instructions) from one ncu
 # capture of the kernel on the 191^3 case (profiles/k_lean_fp64_191.md); a kernel missing here
 # has no current count.
 KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 211.0, "k_lean_faces": 52.7, "k_centres": 237.0}
+# FP32 kernels are bound by HBM (their FP32 work is far below the FP32 pipe's rate).
 # DRAM bytes per cell and launch (dram__bytes_read.sum + dram__bytes_write.sum) from the same
 # captures; the 191^3 case's per-cell figure scales with the cells of a launch.
-KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 287.0, "k_lean_faces": 181.0, "k_centres": 150.6}
+KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 287.0, "k_lean_faces": 181.0, "k_centres": 150.6,
+                           "k_corr_cells": 99.5, "k_corr_faces": 98.7}
 
 
 def parse():
@@ -69,6 +75,9 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--precision", choices=tuple(PRECISIONS), default="fp64",
                     help="fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
+    ap.add_argument("--forms", default="fp32", help="extra forms measured after the headline one "
+                    "(comma list of fp32, fp64-stepwise, batched; '' for none)")
+    ap.add_argument("--fp32-iters", type=int, default=300, help="FP32 iterations per step of the fp32 form")
     return ap.parse_args()
 
 
@@ -145,19 +154,39 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def run_native(args):
+def roofline(kernels: dict, ncell: int) -> dict:
+    """Roofline of the dominant kernel (largest device time) from the live per-kernel events."""
+    hbm, hbm_kind = peaks()
+    name, (nl, ms) = max(kernels.items(), key=lambda kv: kv[1][1])
+    per_launch_s = ms / 1e3 / nl
+    bytes_launch = KERNEL_BYTES_PER_CELL.get(name, 0) * ncell
+    flops_cell = KERNEL_FP64_FLOPS_PER_CELL.get(name)
+    traffic_cell = KERNEL_TRAFFIC_PER_CELL.get(name)
+    gbs = bytes_launch / per_launch_s / 1e9
+    roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+            "frac": gbs / hbm, "peak_source": f"{hbm_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": traffic_cell * ncell if traffic_cell else None,
+            "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": per_launch_s * 1e3}
+    if flops_cell:
+        tf = flops_cell * ncell / per_launch_s / 1e12
+        if tf / FP64_PEAK_TFLOPS > roof["frac"]:
+            roof.update(bound="alu", achieved=tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=tf / FP64_PEAK_TFLOPS,
+                        peak_source="measured FP64 DFMA throughput of this pool's GB300 (FP64 pipe)")
+        roof["fp64_tflops"] = tf
+        roof["hbm_gbs"] = gbs
+    return roof
+
+
+def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_steps: int,
+                 dev, world: int, rank: int, local_rank: int) -> dict:
+    """Time `steps` physical steps (after `warmup`) of one form of the solver on this rank."""
     import torch
     import torch.distributed as dist
     from paper_2207_08716_gb300.solver import PTSolver
 
-    rank, local_rank, world = M.rank_env()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    if world > 1 and not dist.is_initialized():
-        dist.init_process_group("nccl", device_id=dev)
-
-    n, iters = args.n, args.iters
-    p = workload_params(n, iters, args.precision)
+    n = args.n
+    p = workload_params(n, iters, precision)
     seed = M.replica_seed(rank)
     phi = I.gaussian_porosity(p, centres=(I.perturbed_centre(seed),))
     stream = torch.cuda.current_stream(dev)
@@ -173,11 +202,9 @@ def run_native(args):
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one_step()
     torch.cuda.synchronize(dev)
-
-    # ---- device-resident timed region
     clocks = M.ClockSampler(local_rank)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = s.launch_count()
@@ -186,58 +213,64 @@ def run_native(args):
     clocks.start()
     s.profile_begin()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         one_step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     kernels = s.profile_end()
     clk = clocks.stop()
     barrier()
-    t_local = e0.elapsed_time(e1) / 1e3
+    t = M.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     launches = s.launch_count() - launches0
-    t = M.max_over_ranks(t_local, dev)
     ncell = n ** 3
-    total_iters = args.steps * iters
-    a_eff = M.a_eff_bytes(ncell, 8)
-    value = world * a_eff * total_iters / t / 1e9
-    t_it = t / total_iters
-
-    # ---- end to end: host-resident state, copies inside the timed region
-    host = s.host_mirror()
-    s.download(host)
-    torch.cuda.synchronize(dev)
-    barrier()
-    t0 = time.perf_counter()
-    h2d = d2h = 0
-    for _ in range(args.e2e_steps):
-        h2d = s.upload(host)
-        one_step()
-        d2h = s.download(host)
+    pbytes = 4 if precision == "fp32" else 8
+    total_iters = steps * iters
+    value = world * M.a_eff_bytes(ncell, pbytes) * total_iters / t / 1e9
+    out = {"precision": precision, "value": value, "unit": "GB/s", "p_bytes": pbytes,
+           "ms_per_step": t / steps * 1e3, "iters_per_step": iters, "it_per_s": world * total_iters / t,
+           "t_it_ms": t / total_iters * 1e3, "teff_frac_of_hbm": value / world / peaks()[0],
+           "roofline": roofline(kernels, ncell), "gpu_launches": launches, "clocks": clk,
+           "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()}}
+    if e2e_steps > 0:
+        host = s.host_mirror()
+        s.download(host)
         torch.cuda.synchronize(dev)
-    t_e2e = M.max_over_ranks(time.perf_counter() - t0, dev)
-    e2e_val = world * a_eff * args.e2e_steps * iters / t_e2e / 1e9
-    del host
+        barrier()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(e2e_steps):
+            h2d = s.upload(host)
+            one_step()
+            d2h = s.download(host)
+            torch.cuda.synchronize(dev)
+        t_e2e = M.max_over_ranks(time.perf_counter() - t0, dev)
+        out["e2e"] = {"value": world * M.a_eff_bytes(ncell, pbytes) * e2e_steps * iters / t_e2e / 1e9,
+                      "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "steps": e2e_steps}
+        del host
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return out
 
-    # ---- roofline of the dominant kernel (largest device time in the timed region)
-    hbm, hbm_kind = peaks()
-    dom = max(kernels.items(), key=lambda kv: kv[1][1])
-    name, (nl, ms) = dom
-    per_launch_s = ms / 1e3 / nl
-    bytes_launch = KERNEL_BYTES_PER_CELL.get(name, 0) * ncell
-    flops_cell = KERNEL_FP64_FLOPS_PER_CELL.get(name)
-    traffic_cell = KERNEL_TRAFFIC_PER_CELL.get(name)
-    gbs = bytes_launch / per_launch_s / 1e9
-    roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-            "frac": gbs / hbm, "peak_source": f"{hbm_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
-            "traffic": traffic_cell * ncell if traffic_cell else None,
-            "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": per_launch_s * 1e3}
-    if flops_cell:
-        tf = flops_cell * ncell / per_launch_s / 1e12
-        if tf / FP64_PEAK_TFLOPS > roof["frac"]:
-            roof.update(bound="alu", achieved=tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=tf / FP64_PEAK_TFLOPS,
-                        peak_source="measured FP64 DFMA throughput of this pool's GB300")
-        roof["fp64_tflops"] = tf
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, local_rank, world = M.rank_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+
+    head = measure_form(args, args.precision, args.fp32_iters if args.precision == "fp32" else args.iters,
+                        args.steps, args.warmup, args.e2e_steps, dev, world, rank, local_rank)
+    forms = {}
+    for f in [x for x in args.forms.split(",") if x and x != args.precision]:
+        if f in PRECISIONS:
+            it = args.fp32_iters if f == "fp32" else args.iters
+            forms[f] = measure_form(args, f, it, max(2, args.steps // 2), 2, 0, dev, world, rank, local_rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -245,24 +278,24 @@ def run_native(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": workload_name(n, iters, args.precision), "n": n, "iters_per_step": iters,
-                       "precision": args.precision,
+            "metric": METRIC, "value": head["value"], "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.n, head["iters_per_step"], args.precision),
+                       "n": args.n, "iters_per_step": head["iters_per_step"], "precision": args.precision,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (every field 1.07 GB), no flush"},
-            "it_per_s": world * total_iters / t, "t_it_ms": t_it * 1e3,
-            "teff_frac_of_hbm": value / world / hbm,
-            "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
-            "gpu_launches": launches, "clocks": clk,
-            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()},
+                       "l2": "inputs larger than L2 (every field >= 0.5 GB), no flush"},
+            "it_per_s": head["it_per_s"], "t_it_ms": head["t_it_ms"],
+            "teff_frac_of_hbm": head["teff_frac_of_hbm"], "roofline": head["roofline"],
+            "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"], "kernels": head["kernels"],
+            "forms": {k: {kk: v[kk] for kk in ("value", "unit", "p_bytes", "it_per_s", "t_it_ms",
+                                                 "teff_frac_of_hbm", "iters_per_step", "roofline",
+                                                 "gpu_launches", "clocks")}
+                      for k, v in forms.items()},
         }
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

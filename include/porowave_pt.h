@@ -108,6 +108,8 @@ typedef struct {
   double xsi_w;           /* stress sub-step dtS = max(mu) / (G xsi_w)                      */
   int32_t precision;      /* PT_FP64, PT_FP64_STEPWISE or PT_FP32 (see the enum above)     */
   int32_t iters_per_graph;/* PT iterations per CUDA-graph replay; 0 = nup                  */
+  double inner_rtol;      /* PT_FP32: each FP32 correction solve stops at this relative drop
+                           * of its residual (0 = 0.3)                                     */
 } pt_num;
 
 /* Caller-owned device fields, padded box layout above. logk may be NULL (logk = 0). */

@@ -18,6 +18,7 @@
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
 #include "pt_lean.cuh"
+#include "pt_mixed.cuh"
 
 using namespace pt;
 
@@ -27,6 +28,13 @@ constexpr size_t kAlign = 256;
 constexpr int kPitchMultiple = 16;
 constexpr int kRefArrays = 23;   // step-by-step path
 constexpr int kLeanArrays = 23;  // extra arrays of the FP64-lean path
+constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
+// Default relative drop at which the inner FP32 solves of the mixed-precision path stop. The
+// outer loop's convergence is bound by the log-space Picard relaxation of mu and eta (one
+// update per outer iteration), not by the inner accuracy: a drop of 0.3 per inner solve needs
+// about as many FP32 iterations in total as the FP64 path needs FP64 iterations (measured on
+// 32^3-96^3), while 1e-4 needs 3-4 times more.
+constexpr double kInnerRtol = 0.3;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -74,6 +82,13 @@ struct pt_ctx {
   double *toa_xx, *toa_yy, *toa_zz, *toa_xy, *toa_xz, *toa_yz, *cm2, *idtp, *ieta;
   double *em2_xy, *em2_xz, *em2_yz, *dtv_x, *dtv_y, *dtv_z, *K0;
   LeanCoef<double> lcoef;
+  // mixed-precision path (precision PT_FP32): FP32 correction problem
+  bool mixed;
+  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_iden_pt, *m_idtf, *m_iden_pf;
+  float *m_cm2, *m_em2_xy, *m_em2_xz, *m_em2_yz, *m_dtv_x, *m_dtv_y, *m_dtv_z;
+  float *m_dVx, *m_dVy, *m_dVz, *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
+  float *m_txx, *m_tyy, *m_tzz, *m_txy, *m_txz, *m_tyz;
+  CorrCoef<float> ccoef;
   unsigned long long* red;       // device reduction block (RED_N slots)
   unsigned long long* h_red;     // pinned host copy
   // stress sub-stepping
@@ -92,11 +107,14 @@ namespace {
 
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
-                K_LEAN_K0, K_COUNT };
+                K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_CELLS, K_CORR_FACES,
+                K_MIX_UPDATE, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
-                                           "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0"};
+                                           "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0",
+                                           "k_mix_prepare", "k_mix_res_faces", "k_mix_coef",
+                                           "k_corr_cells", "k_corr_faces", "k_mix_update"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -141,6 +159,7 @@ dim3 grid_dims(const Box& b) {
 }
 
 void fill_lean_coef(pt_ctx* c);
+void fill_corr_coef(pt_ctx* c);
 
 void fill_coef(pt_ctx* c) {
   const pt_grid& g = c->grid;
@@ -186,6 +205,7 @@ void fill_coef(pt_ctx* c) {
   k.dtaupf_fac = n.cfl_pf * k.h2 * (1.0 + p.beta_d * p.B / p.alpha);
   k.rGdtS = c->dtS > 0 ? 1.0 / (p.G * c->dtS) : 0.0;
   fill_lean_coef(c);
+  fill_corr_coef(c);
 }
 
 void fill_lean_coef(pt_ctx* c) {
@@ -219,6 +239,21 @@ void fill_lean_coef(pt_ctx* c) {
   L.rGdtS = k.rGdtS;
   L.dtaupt_fac = k.dtaupt_fac;
   L.dtauv_fac = k.dtauv_fac;
+}
+
+void fill_corr_coef(pt_ctx* c) {
+  const Coef& k = c->coef;
+  CorrCoef<float>& f = c->ccoef;
+  f.rdx = (float)k.rdx; f.rdy = (float)k.rdy; f.rdz = (float)k.rdz;
+  f.hrdx = (float)(0.5 * k.rdx); f.hrdy = (float)(0.5 * k.rdy); f.hrdz = (float)(0.5 * k.rdz);
+  f.hrdx2 = (float)(0.5 * k.rdx * k.rdx); f.hrdy2 = (float)(0.5 * k.rdy * k.rdy);
+  f.hrdz2 = (float)(0.5 * k.rdz * k.rdz);
+  f.bd_rdt = (float)(k.beta_d * k.rdt);
+  f.bd_rdt_a = (float)(k.beta_d * k.rdt * k.alpha);
+  f.bda_B_rdt = (float)(k.beta_d * k.alpha / k.B * k.rdt);
+  f.beta_n = (float)k.beta_n;
+  f.rrho_i = (float)k.rrho_i;
+  f.damp_x = (float)k.damp_x; f.damp_y = (float)k.damp_y; f.damp_z = (float)k.damp_z;
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
@@ -330,6 +365,86 @@ double report_max(const pt_report* r) {
   return std::fmax(std::fmax(r->res_v, r->res_pt), std::fmax(r->res_pf, r->res_pic));
 }
 
+// One outer iteration of the mixed-precision path (see pt_mixed_kernels.cu): FP64 residuals
+// and Picard update at u, then up to n_in FP32 PT iterations on the correction (stopping early
+// at a relative drop kInnerRtol when early_exit), u <- u + delta, FP64 porosity update.
+// `outer` receives the FP64 residual norms at u; *converged is set when they are below tol
+// (then no correction is run).
+int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* converged, int* inner_done) {
+  const Box& b = c->box;
+  const Coef& k = c->coef;
+  const dim3 bl = block_dims(), gr = grid_dims(b);
+  const int a = c->cur;
+  *converged = false;
+  *inner_done = 0;
+  cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  // (i) FP64 residuals at u, frozen coefficients of the correction problem
+  PT_LAUNCH(c, K_PERM, k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[a], c->logk, c->perm, c->rog));
+  MixPrepIn pin{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->mu, c->eta, c->perm, c->Pto,
+                c->Pfo, c->txxo, c->tyyo, c->tzzo};
+  MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_idtp,
+                  c->m_iden_pt, c->m_idtf, c->m_iden_pf};
+  PT_LAUNCH(c, K_MIX_PREP, mix_prepare(gr, bl, c->stream, b, k, pin, pout, c->red));
+  EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
+  EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
+  PT_LAUNCH(c, K_EDGES, k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo));
+  MixFaceIn fin{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[a], c->phi[a]};
+  PT_LAUNCH(c, K_MIX_FACES, mix_res_faces(gr, bl, c->stream, b, k, fin, c->m_rfx, c->m_rfy, c->m_rfz, c->red));
+  // (ii) Picard update of mu, eta from the stresses at u
+  LeanPicardIn<double> pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[a],
+                          c->Pt[a], c->Pf[a]};
+  PT_LAUNCH(c, K_LEAN_PICARD, lean_picard<double>(gr, bl, c->stream, b, c->lcoef, pi, c->mu, c->eta, c->red));
+  if (cudaGetLastError() != cudaSuccess) return PT_ECUDA;
+  int rc = read_report(c, outer);
+  if (rc != PT_OK) return rc;
+  if (early_exit && report_max(outer) < c->num.tol) {
+    *converged = true;
+    return PT_OK;
+  }
+  const double target = (c->num.inner_rtol > 0 ? c->num.inner_rtol : kInnerRtol) * report_max(outer);
+  // (iii) FP32 PT on the correction, from delta = 0, R = 0
+  MixCoefOut mco{c->m_cm2, c->m_em2_xy, c->m_em2_xz, c->m_em2_yz, c->m_dtv_x, c->m_dtv_y, c->m_dtv_z};
+  PT_LAUNCH(c, K_MIX_COEF, mix_coef(gr, bl, c->stream, b, k, c->mu, mco));
+  const size_t fb = (size_t)b.n * sizeof(float);
+  float* zero[] = {c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[0], c->m_dPf[0], c->m_Rx, c->m_Ry, c->m_Rz};
+  for (float* z : zero) cudaMemsetAsync(z, 0, fb, c->stream);
+  int d = 0;
+  const int nup = c->num.nup;
+  for (int it = 1; it <= n_in; ++it) {
+    const int check = early_exit && (it % nup) == 0;
+    if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+    CorrCellIn<float> ci{c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d], c->m_cc, c->m_perm,
+                         c->m_idtp, c->m_iden_pt, c->m_idtf, c->m_iden_pf, c->m_rpt, c->m_rpf,
+                         c->m_cm2, c->m_em2_xy, c->m_em2_xz, c->m_em2_yz};
+    CorrCellOut<float> co{c->m_dPt[1 - d], c->m_dPf[1 - d], c->m_txx, c->m_tyy, c->m_tzz, c->m_txy,
+                          c->m_txz, c->m_tyz};
+    PT_LAUNCH(c, K_CORR_CELLS, corr_cells<float>(gr, bl, c->stream, b, c->ccoef, ci, co, c->red, check));
+    CorrFaceIn<float> fi{c->m_txx, c->m_tyy, c->m_tzz, c->m_txy, c->m_txz, c->m_tyz, c->m_dPt[1 - d],
+                         c->m_dtv_x, c->m_dtv_y, c->m_dtv_z, c->m_rfx, c->m_rfy, c->m_rfz};
+    PT_LAUNCH(c, K_CORR_FACES, corr_faces<float>(gr, bl, c->stream, b, c->ccoef, fi, c->m_dVx, c->m_dVy,
+                                                 c->m_dVz, c->m_Rx, c->m_Ry, c->m_Rz, c->red, check));
+    d = 1 - d;
+    *inner_done = it;
+    if (check) {
+      pt_report ir;
+      rc = read_report(c, &ir);
+      if (rc != PT_OK) return rc;
+      if (std::fmax(std::fmax(ir.res_v, ir.res_pt), ir.res_pf) < target) break;
+    }
+  }
+  // (iv) u <- u + delta in FP64, then the FP64 porosity time integration (Eq. 22, log space)
+  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d]};
+  PT_LAUNCH(c, K_MIX_UPDATE, mix_update(gr, bl, c->stream, b, mu));
+  PT_LAUNCH(c, K_POROSITY,
+            k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[a], c->Pf[a],
+                                                  c->Pto, c->Pfo, c->Lo, c->eta, c->phi[1 - a]));
+  // Pt, Pf stay in buffer a; phi moves to 1 - a: copy the pressures along so cur stays paired
+  cudaMemcpyAsync(c->Pt[1 - a], c->Pt[a], (size_t)b.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->Pf[1 - a], c->Pf[a], (size_t)b.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  c->cur = 1 - a;
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace
 
 extern "C" {
@@ -348,7 +463,8 @@ size_t pt_workspace_size(const pt_grid* grid, const pt_num* num) {
   if (!grid_ok(grid) || !num) return 0;
   const Box b = make_box(grid);
   const int arrays = kRefArrays + (num->precision == PT_FP64 ? kLeanArrays : 0);
-  return arrays * align_up((size_t)b.n * sizeof(double), kAlign) + kAlign;
+  const size_t mixed = num->precision == PT_FP32 ? kMixArrays * align_up((size_t)b.n * sizeof(float), kAlign) : 0;
+  return arrays * align_up((size_t)b.n * sizeof(double), kAlign) + mixed + kAlign;
 }
 
 int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num* num,
@@ -362,7 +478,8 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   if (!(num->rho_i > 0) || !(num->cfl_v > 0) || !(num->cfl_pf > 0) || !(num->dtpt_scale > 0) ||
       !(num->xsi_w > 0))
     return PT_EINVAL;
-  if (num->precision != PT_FP64 && num->precision != PT_FP64_STEPWISE) return PT_EINVAL;
+  if (num->precision != PT_FP64 && num->precision != PT_FP64_STEPWISE && num->precision != PT_FP32)
+    return PT_EINVAL;
   if (!(phys->phi0 > 0 && phys->phi0 < 1) || !(phys->k0 > 0) || !(phys->mu0 > 0) || !(phys->eta0 > 0) ||
       !(phys->G > 0) || !(phys->alpha > 0) || !(phys->B > 0) || !(phys->tau0 > 0) || !(phys->R_weak > 0))
     return PT_EINVAL;
@@ -399,7 +516,20 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
       &c->em2_xy, &c->em2_xz, &c->em2_yz, &c->dtv_x, &c->dtv_y, &c->dtv_z, &c->K0};
   const int arrays = kRefArrays + (c->lean ? kLeanArrays : 0);
   for (int s = 0; s < arrays; ++s) *slots[s] = (double*)(w + s * stride);
-  c->red = (unsigned long long*)(w + arrays * stride);
+  char* wend = w + arrays * stride;
+  c->mixed = num->precision == PT_FP32;
+  if (c->mixed) {
+    const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
+    float** fslots[kMixArrays] = {
+        &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_idtp,
+        &c->m_iden_pt, &c->m_idtf, &c->m_iden_pf, &c->m_cm2, &c->m_em2_xy, &c->m_em2_xz, &c->m_em2_yz,
+        &c->m_dtv_x, &c->m_dtv_y, &c->m_dtv_z, &c->m_dVx, &c->m_dVy, &c->m_dVz, &c->m_dPt[0], &c->m_dPt[1],
+        &c->m_dPf[0], &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz, &c->m_txx, &c->m_tyy, &c->m_tzz,
+        &c->m_txy, &c->m_txz, &c->m_tyz};
+    for (int s = 0; s < kMixArrays; ++s) *fslots[s] = (float*)(wend + s * fstride);
+    wend += kMixArrays * fstride;
+  }
+  c->red = (unsigned long long*)wend;
   if (cudaMallocHost(&c->h_red, RED_N * sizeof(unsigned long long)) != cudaSuccess) {
     delete c;
     return PT_ECUDA;
@@ -479,6 +609,21 @@ int pt_step_begin(pt_ctx* c) {
 int pt_iterate(pt_ctx* c, int32_t it0, int32_t niter, pt_report* rep) {
   if (!c || it0 < 0 || niter < 0) return PT_EINVAL;
   if (c->nsteps == 0) return PT_EINVAL;  // pt_step_begin first
+  if (c->mixed) {
+    // one outer iteration with exactly niter FP32 iterations on the correction
+    pt_report outer;
+    bool conv = false;
+    int done = 0;
+    int rc = mixed_outer(c, niter, false, &outer, &conv, &done);
+    if (rc == PT_OK) rc = sync_current_to_caller(c);
+    if (rc == PT_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    if (rep) {
+      *rep = outer;
+      rep->iters = done;
+      rep->status = rc;
+    }
+    return rc;
+  }
   int checked = 0;
   for (int32_t it = it0 + 1; it <= it0 + niter; ++it) {
     const int check = (it % c->num.nup) == 0;
@@ -527,7 +672,13 @@ int pt_step(pt_ctx* c, pt_report* rep) {
   int it = 0;
   bool converged = false;
   const int nup = c->num.nup, cap = c->num.max_iter;
-  while (it < cap) {
+  while (c->mixed) {
+    int done = 0;
+    rc = mixed_outer(c, cap - it, true, &r, &converged, &done);
+    it += done;
+    if (rc != PT_OK || converged || it >= cap) break;
+  }
+  while (!c->mixed && it < cap) {
     const int n = std::min(nup - (it % nup), cap - it);
     for (int s = 1; s <= n; ++s) launch_iteration(c, ((it + s) % nup) == 0);
     it += n;

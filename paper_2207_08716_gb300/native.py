@@ -16,8 +16,8 @@ _CSRC = os.path.join(_PKG, "csrc")
 _INC = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
-SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_static.cu")
-HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh")
+SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu", "pt_static.cu")
+HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh", "pt_mixed.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -76,7 +76,8 @@ class Num(C.Structure):
                 ("nup", C.c_int32), ("damp", C.c_double * 3), ("rho_i", C.c_double),
                 ("beta_n", C.c_double), ("rel_mu", C.c_double), ("rel_eta", C.c_double),
                 ("cfl_v", C.c_double), ("cfl_pf", C.c_double), ("dtpt_scale", C.c_double),
-                ("xsi_w", C.c_double), ("precision", C.c_int32), ("iters_per_graph", C.c_int32)]
+                ("xsi_w", C.c_double), ("precision", C.c_int32), ("iters_per_graph", C.c_int32),
+                ("inner_rtol", C.c_double)]
 
 
 FIELD_NAMES = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi", "txx", "tyy", "tzz", "txy", "txz", "tyz",
@@ -116,6 +117,8 @@ def num_from(p: dict, precision: int = PT_FP64, iters_per_graph: int = 0) -> Num
             nm.precision = p.get("precision", precision)
         elif n == "iters_per_graph":
             nm.iters_per_graph = p.get("iters_per_graph", iters_per_graph)
+        elif n == "inner_rtol":
+            nm.inner_rtol = p.get("inner_rtol", 0.0)
         else:
             setattr(nm, n, p[n])
     return nm
