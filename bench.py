@@ -75,9 +75,14 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--precision", choices=tuple(PRECISIONS), default="fp64",
                     help="fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
-    ap.add_argument("--forms", default="fp32", help="extra forms measured after the headline one "
+    ap.add_argument("--forms", default="fp32,batched", help="extra forms measured after the headline one "
                     "(comma list of fp32, fp64-stepwise, batched; '' for none)")
     ap.add_argument("--fp32-iters", type=int, default=300, help="FP32 iterations per step of the fp32 form")
+    ap.add_argument("--batch-n", type=int, default=64, help="instances of the batched form")
+    ap.add_argument("--batch-iters", type=int, default=60, help="PT iterations per step of the batched form")
+    ap.add_argument("--batched-converge", action="store_true",
+                    help="run one step of the batched ensemble to convergence and report p50/p99 "
+                         "time-to-converge (minutes of GPU time) instead of the throughput bench")
     return ap.parse_args()
 
 
@@ -254,6 +259,56 @@ def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_
     return out
 
 
+def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, converge: bool = False) -> dict:
+    """The batched ensemble (64 instances, sizes {32,48,64,96,127}^3, seeded parameters and
+    anomalies; seed = rank): aggregate cell updates per second over `steps` physical steps of
+    `--batch-iters` PT iterations each, or one step to convergence with time-to-converge."""
+    import torch
+    from paper_2207_08716_gb300.solver import PTBatch
+
+    mem = I.ensemble(seed=M.replica_seed(rank), n_inst=args.batch_n, max_iter=40000)
+    if not converge:
+        for p, _ in mem:
+            p["tol"] = 0.0
+            p["max_iter"] = args.batch_iters
+    cells = [p["nx"] * p["ny"] * p["nz"] for p, _ in mem]
+    b = PTBatch(mem, device=dev)
+    del mem
+    for _ in range(warmup):
+        b.step()
+    torch.cuda.synchronize(dev)
+    clocks = M.ClockSampler(dev.index or 0)
+    clocks.start()
+    t0 = time.perf_counter()
+    iters = [0] * len(cells)
+    ttc_all = []
+    for _ in range(1 if converge else steps):
+        reps, ttc = b.step()
+        for m, r in enumerate(reps):
+            iters[m] += r["iters"]
+        ttc_all = ttc
+    torch.cuda.synchronize(dev)
+    t = M.max_over_ranks(time.perf_counter() - t0, dev)
+    clk = clocks.stop()
+    upd = M.sum_over_ranks(float(sum(c * it for c, it in zip(cells, iters))), dev)
+    bx, by, ipg = b.config()
+    out = {"value": M.a_eff_bytes(1, 8) * upd / t / 1e9, "unit": "GB/s",
+           "cell_updates_per_s": upd / t, "instances": len(cells), "total_cells": sum(cells),
+           "iters_per_step": None if converge else args.batch_iters, "seconds": t,
+           "tile": [bx, by], "iters_per_graph": ipg, "clocks": clk,
+           "value_definition": "T_eff-equivalent: 25 x 8 B x aggregate cell updates per second"}
+    if converge:
+        st = sorted(ttc_all)
+        out.update(statuses=[r["status"] for r in reps], iters=[r["iters"] for r in reps],
+                   p50_time_to_converge_ms=st[len(st) // 2],
+                   p99_time_to_converge_ms=st[min(len(st) - 1, int(0.99 * len(st)))],
+                   converged=sum(1 for r in reps if r["status"] == 0))
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -264,11 +319,18 @@ def run_native(args):
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=dev)
 
+    if args.batched_converge:
+        r = measure_batched(args, 1, 0, dev, world, rank, converge=True)
+        if rank == 0:
+            print(json.dumps({"metric": "batched ensemble time-to-converge", **r}), flush=True)
+        return 0
     head = measure_form(args, args.precision, args.fp32_iters if args.precision == "fp32" else args.iters,
                         args.steps, args.warmup, args.e2e_steps, dev, world, rank, local_rank)
     forms = {}
     for f in [x for x in args.forms.split(",") if x and x != args.precision]:
-        if f in PRECISIONS:
+        if f == "batched":
+            forms[f] = measure_batched(args, max(2, args.steps // 2), 1, dev, world, rank)
+        elif f in PRECISIONS:
             it = args.fp32_iters if f == "fp32" else args.iters
             forms[f] = measure_form(args, f, it, max(2, args.steps // 2), 2, 0, dev, world, rank, local_rank)
 
@@ -290,9 +352,9 @@ def run_native(args):
             "teff_frac_of_hbm": head["teff_frac_of_hbm"], "roofline": head["roofline"],
             "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
             "clocks": head["clocks"], "kernels": head["kernels"],
-            "forms": {k: {kk: v[kk] for kk in ("value", "unit", "p_bytes", "it_per_s", "t_it_ms",
-                                                 "teff_frac_of_hbm", "iters_per_step", "roofline",
-                                                 "gpu_launches", "clocks")}
+            "forms": {k: ({kk: v[kk] for kk in ("value", "unit", "p_bytes", "it_per_s", "t_it_ms",
+                                                  "teff_frac_of_hbm", "iters_per_step", "roofline",
+                                                  "gpu_launches", "clocks")} if k != "batched" else v)
                       for k, v in forms.items()},
         }
         print(json.dumps(line), flush=True)

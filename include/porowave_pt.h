@@ -206,6 +206,33 @@ int pt_residual_static(const pt_grid *grid, const pt_phys *phys, const pt_num *n
                        const pt_fields *fields, const pt_old_fields *old, double dtS,
                        void *stream, pt_report *rep);
 
+/* ---- Batched ensemble --------------------------------------------------------
+ * ninst independent instances (each its own grid, parameters, fields and numerics; FP64 lean
+ * form, precision PT_FP64) advanced together: one launch per PT phase covers all instances
+ * through a flat work list of (instance, tile) items walked by a persistent grid-stride grid, and
+ * 2 nup (or 4 nup) iterations are captured in one CUDA graph per replay. Each instance stops at
+ * its own first check with norms < tol (or at its max_iter / a non-finite norm), exactly where
+ * its single-instance pt_step would, and reproduces that run bit for bit. The first
+ * pt_batch_step tunes the tile shape (32x4, 32x8, 64x4) and the iterations per graph by timing
+ * graph replays (tuning replays are real iterations: the arithmetic does not depend on them).
+ * grids/phys/nums/fields are arrays of ninst; the workspace holds every instance's workspace
+ * (pt_workspace_size) plus the descriptor table. The batch works on a stream of its own
+ * (graphs cannot be captured on the legacy default stream): pt_batch_init and pt_batch_step
+ * first synchronise the caller's `stream`, and pt_batch_step returns after its work is done. */
+typedef struct pt_batch pt_batch;
+size_t pt_batch_workspace_size(int32_t ninst, const pt_grid *grids, const pt_num *nums);
+int pt_batch_init(pt_batch **batch, int32_t ninst, const pt_grid *grids, const pt_phys *phys,
+                  const pt_num *nums, const pt_fields *fields, void *workspace,
+                  size_t workspace_bytes, void *stream);
+/* One physical step of every instance. reps[ninst] receives each instance's report;
+ * time_to_converge_ms[ninst] (may be NULL) its device time from the step's first iteration to
+ * its stop. Returns PT_OK when every instance converged, PT_ENOTCONV if any hit its cap. */
+int pt_batch_step(pt_batch *batch, pt_report *reps, double *time_to_converge_ms);
+/* The tuned configuration (valid after the first pt_batch_step). */
+int pt_batch_config(const pt_batch *batch, int32_t *tile_x, int32_t *tile_y,
+                    int32_t *iters_per_graph);
+void pt_batch_destroy(pt_batch *batch);
+
 /* Release the context (not the caller's memory). */
 void pt_destroy(pt_ctx *ctx);
 

@@ -19,6 +19,7 @@
 #include "pt_kernels.cuh"
 #include "pt_lean.cuh"
 #include "pt_mixed.cuh"
+#include "pt_batch.cuh"
 
 using namespace pt;
 
@@ -789,6 +790,305 @@ const char* pt_strerror(int code) {
     case PT_ESPACE: return "workspace too small";
     default: return "unknown error";
   }
+}
+
+}  // extern "C"
+
+// ============================================================================ batched ensemble
+struct pt_batch {
+  int ninst;
+  std::vector<pt_ctx*> ctx;
+  cudaStream_t caller;      // the caller's stream (may be the legacy default stream)
+  cudaStream_t stream;      // the batch's own stream: graphs are captured and replayed on it
+  std::vector<BatchInst> h_inst;
+  BatchInst* d_inst;
+  BatchStatus* d_st;
+  BatchStatus* h_st;
+  int nup;
+  int bx, by, ipg;          // tile shape, iterations per graph replay
+  bool tuned;
+  long long ntiles;
+  int grid;
+  cudaGraphExec_t exec;
+  int exec_bx, exec_by, exec_ipg;
+};
+
+namespace {
+
+size_t batch_table_bytes(int ninst) {
+  return align_up(sizeof(BatchInst) * ninst, kAlign) + align_up(sizeof(BatchStatus) * ninst, kAlign);
+}
+
+// Descriptor of instance m for the batch's tile shape (pointers of both ping-pong parities).
+void fill_batch_inst(pt_batch* B, int m, long long base) {
+  pt_ctx* c = B->ctx[m];
+  BatchInst& I = B->h_inst[m];
+  I.b = c->box;
+  I.c = c->lcoef;
+  for (int a = 0; a < 2; ++a) {
+    const int n = 1 - a;
+    I.cin[a] = LeanCellIn<double>{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->lw[a], c->lperm[a],
+                                  c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->ieta, c->idtp, c->cm2,
+                                  c->toa_xx, c->toa_yy, c->toa_zz, c->em2_xy, c->em2_xz, c->em2_yz,
+                                  c->toa_xy, c->toa_xz, c->toa_yz, c->logk ? c->K0 : nullptr};
+    I.cout[a] = LeanCellOut<double>{c->Pt[n], c->Pf[n], c->phi[n], c->lw[n], c->lperm[n], c->s_txx,
+                                    c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz};
+    I.fin[a] = LeanFaceIn<double>{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[n],
+                                  c->phi[a], c->dtv_x, c->dtv_y, c->dtv_z};
+    I.pin[a] = LeanPicardIn<double>{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz,
+                                    c->phi[n], c->Pt[n], c->Pf[n]};
+  }
+  I.kin = LeanCoefIn<double>{c->mu, c->eta, c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
+  I.kout = LeanCoefOut<double>{c->cm2, c->toa_xx, c->toa_yy, c->toa_zz, c->idtp, c->ieta, c->em2_xy,
+                               c->em2_xz, c->em2_yz, c->toa_xy, c->toa_xz, c->toa_yz, c->dtv_x,
+                               c->dtv_y, c->dtv_z};
+  I.Vx = c->Vx; I.Vy = c->Vy; I.Vz = c->Vz;
+  I.Rx = c->Rx; I.Ry = c->Ry; I.Rz = c->Rz;
+  I.mu = c->mu; I.eta = c->eta;
+  I.red = c->red;
+  I.tol = c->num.tol;
+  I.max_iter = c->num.max_iter;
+  I.gx = (c->box.nx + 1 + B->bx - 1) / B->bx;
+  I.gy = (c->box.ny + 1 + B->by - 1) / B->by;
+  I.tile_base = base;
+}
+
+// Descriptors for the current tile shape, uploaded; returns the work-list length.
+cudaError_t upload_batch(pt_batch* B) {
+  long long base = 0;
+  for (int m = 0; m < B->ninst; ++m) {
+    fill_batch_inst(B, m, base);
+    base += (long long)B->h_inst[m].gx * B->h_inst[m].gy * (B->ctx[m]->box.nz + 1);
+  }
+  B->ntiles = base;
+  const int dev_blocks = batch_blocks_per_sm(B->bx, B->by);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  B->grid = std::max(1, sms * dev_blocks);
+  return cudaMemcpyAsync(B->d_inst, B->h_inst.data(), sizeof(BatchInst) * B->ninst, cudaMemcpyHostToDevice,
+                         B->stream);
+}
+
+// The launches of `ipg` iterations starting from parity 0 (ipg is a multiple of 2 nup).
+void record_batch_iterations(pt_batch* B, int ipg) {
+  for (int it = 1; it <= ipg; ++it) {
+    const int a = (it - 1) & 1;
+    const int check = (it % B->nup) == 0;
+    batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_CELLS, B->d_inst, B->d_st, B->ninst, B->ntiles, a, check);
+    batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_FACES, B->d_inst, B->d_st, B->ninst, B->ntiles, a, check);
+    if (check) {
+      batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_PICARD, B->d_inst, B->d_st, B->ninst, B->ntiles, a, 1);
+      batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_COEF, B->d_inst, B->d_st, B->ninst, B->ntiles, a, 0);
+      batch_converge(B->stream, B->d_inst, B->d_st, B->ninst, B->nup);
+    }
+  }
+}
+
+int build_batch_graph(pt_batch* B) {
+  if (B->exec && B->exec_bx == B->bx && B->exec_by == B->by && B->exec_ipg == B->ipg) return PT_OK;
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PT_ECUDA;
+  record_batch_iterations(B, B->ipg);
+  cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    B->exec = nullptr;
+    return PT_ECUDA;
+  }
+  B->exec_bx = B->bx;
+  B->exec_by = B->by;
+  B->exec_ipg = B->ipg;
+  return PT_OK;
+}
+
+int batch_active(pt_batch* B, int* nactive) {
+  cudaError_t e = cudaMemcpyAsync(B->h_st, B->d_st, sizeof(BatchStatus) * B->ninst, cudaMemcpyDeviceToHost,
+                                  B->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  int n = 0;
+  for (int m = 0; m < B->ninst; ++m) n += B->h_st[m].active;
+  *nactive = n;
+  return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pt_batch_workspace_size(int32_t ninst, const pt_grid* grids, const pt_num* nums) {
+  if (ninst < 1 || !grids || !nums) return 0;
+  size_t total = 0;
+  for (int m = 0; m < ninst; ++m) {
+    const size_t s = pt_workspace_size(&grids[m], &nums[m]);
+    if (s == 0) return 0;
+    total += align_up(s, kAlign);
+  }
+  return total + batch_table_bytes(ninst);
+}
+
+int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_phys* phys, const pt_num* nums,
+                  const pt_fields* fields, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out) return PT_EINVAL;
+  *out = nullptr;
+  if (ninst < 1 || !grids || !phys || !nums || !fields || !workspace) return PT_EINVAL;
+  if (((uintptr_t)workspace & (kAlign - 1)) != 0) return PT_EINVAL;
+  for (int m = 0; m < ninst; ++m)
+    if (nums[m].precision != PT_FP64 || nums[m].nup != nums[0].nup) return PT_EINVAL;
+  const size_t need = pt_batch_workspace_size(ninst, grids, nums);
+  if (need == 0) return PT_EINVAL;
+  if (workspace_bytes < need) return PT_ESPACE;
+  pt_batch* B = new (std::nothrow) pt_batch();
+  if (!B) return PT_ECUDA;
+  B->ninst = ninst;
+  B->caller = (cudaStream_t)stream;
+  // a stream of its own: the legacy default stream cannot be captured into a graph
+  if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete B;
+    return PT_ECUDA;
+  }
+  if (cudaStreamSynchronize(B->caller) != cudaSuccess) {
+    cudaStreamDestroy(B->stream);
+    delete B;
+    return PT_ECUDA;
+  }
+  B->nup = nums[0].nup;
+  B->bx = 32;
+  B->by = 8;
+  B->ipg = 2 * B->nup;
+  B->tuned = false;
+  B->exec = nullptr;
+  B->ctx.assign(ninst, nullptr);
+  B->h_inst.resize(ninst);
+  char* w = (char*)workspace;
+  int rc = PT_OK;
+  for (int m = 0; m < ninst && rc == PT_OK; ++m) {
+    const size_t s = pt_workspace_size(&grids[m], &nums[m]);
+    rc = pt_init(&B->ctx[m], &grids[m], &phys[m], &nums[m], &fields[m], w, s, (void*)B->stream, 0);
+    w += align_up(s, kAlign);
+  }
+  if (rc == PT_OK) {
+    B->d_inst = (BatchInst*)w;
+    B->d_st = (BatchStatus*)(w + align_up(sizeof(BatchInst) * ninst, kAlign));
+    if (cudaMallocHost(&B->h_st, sizeof(BatchStatus) * ninst) != cudaSuccess) rc = PT_ECUDA;
+  }
+  if (rc != PT_OK) {
+    for (pt_ctx* c : B->ctx) pt_destroy(c);
+    cudaStreamDestroy(B->stream);
+    delete B;
+    return rc;
+  }
+  *out = B;
+  return PT_OK;
+}
+
+int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
+  if (!B || !reps) return PT_EINVAL;
+  // order after the caller's prior work on its stream
+  if (cudaStreamSynchronize(B->caller) != cudaSuccess) return PT_ECUDA;
+  int rc = PT_OK;
+  int cap = 0;
+  for (int m = 0; m < B->ninst && rc == PT_OK; ++m) {
+    rc = pt_step_begin(B->ctx[m]);   // old-state snapshot, dtS, coefficients (per instance)
+    cap = std::max(cap, B->ctx[m]->num.max_iter);
+  }
+  if (rc != PT_OK) return rc;
+  if (upload_batch(B) != cudaSuccess) return PT_ECUDA;
+  batch_start(B->stream, B->d_inst, B->d_st, B->ninst);
+  // candidate configurations; the first step times one replay of each and keeps the fastest
+  struct Cfg { int bx, by, mult; };
+  const Cfg cands[] = {{32, 8, 2}, {32, 4, 2}, {64, 4, 2}, {32, 8, 4}};
+  const int ncand = B->tuned ? 0 : (int)(sizeof cands / sizeof cands[0]);
+  float best_ms = 1e30f;
+  Cfg best = {B->bx, B->by, B->ipg / (2 * B->nup)};
+  int done = 0, nactive = B->ninst;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ncand) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  for (int t = 0; t < ncand && nactive > 0 && done < cap; ++t) {
+    B->bx = cands[t].bx;
+    B->by = cands[t].by;
+    B->ipg = cands[t].mult * 2 * B->nup;
+    if (upload_batch(B) != cudaSuccess) return PT_ECUDA;
+    rc = build_batch_graph(B);
+    if (rc != PT_OK) return rc;
+    cudaEventRecord(e0, B->stream);
+    if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return PT_ECUDA;
+    cudaEventRecord(e1, B->stream);
+    done += B->ipg;
+    rc = batch_active(B, &nactive);
+    if (rc != PT_OK) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / B->ipg < best_ms) {
+      best_ms = ms / B->ipg;
+      best = cands[t];
+    }
+  }
+  if (ncand) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->bx = best.bx;
+    B->by = best.by;
+    B->ipg = best.mult * 2 * B->nup;
+    B->tuned = true;
+    if (upload_batch(B) != cudaSuccess) return PT_ECUDA;
+  }
+  rc = build_batch_graph(B);
+  if (rc != PT_OK) return rc;
+  while (nactive > 0 && done < cap) {
+    if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return PT_ECUDA;
+    done += B->ipg;
+    rc = batch_active(B, &nactive);
+    if (rc != PT_OK) return rc;
+  }
+  rc = batch_active(B, &nactive);
+  if (rc != PT_OK) return rc;
+  int any_nc = 0, any_nan = 0;
+  for (int m = 0; m < B->ninst; ++m) {
+    const BatchStatus& s = B->h_st[m];
+    pt_ctx* c = B->ctx[m];
+    c->cur = s.iters & 1;     // the instance's last iterate is in the buffer of its parity
+    const int rc_end = pt_step_end(c);
+    reps[m].iters = s.iters;
+    reps[m].status = s.status;
+    reps[m].res_v = s.res[0];
+    reps[m].res_pt = s.res[1];
+    reps[m].res_pf = s.res[2];
+    reps[m].res_pic = s.res[3];
+    if (ttc_ms) ttc_ms[m] = s.t_stop > s.t_start ? (double)(s.t_stop - s.t_start) * 1e-6 : -1.0;
+    if (rc_end != PT_OK) return rc_end;
+    any_nc |= s.status == PT_ENOTCONV;
+    any_nan |= s.status == PT_ENAN;
+  }
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return PT_ECUDA;
+  return any_nan ? PT_ENAN : (any_nc ? PT_ENOTCONV : PT_OK);
+}
+
+int pt_batch_config(const pt_batch* B, int32_t* tile_x, int32_t* tile_y, int32_t* ipg) {
+  if (!B) return PT_EINVAL;
+  if (tile_x) *tile_x = B->bx;
+  if (tile_y) *tile_y = B->by;
+  if (ipg) *ipg = B->ipg;
+  return PT_OK;
+}
+
+void pt_batch_destroy(pt_batch* B) {
+  if (!B) return;
+  cudaStreamSynchronize(B->stream);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  for (pt_ctx* c : B->ctx) pt_destroy(c);
+  cudaFreeHost(B->h_st);
+  cudaStreamDestroy(B->stream);
+  delete B;
 }
 
 }  // extern "C"

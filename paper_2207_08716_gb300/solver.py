@@ -174,3 +174,80 @@ class PTSolver:
             self.close()
         except Exception:
             pass
+
+
+class PTBatch:
+    """An ensemble of independent instances advanced together (pt_batch_* of the C ABI).
+
+    members: list of (params, phi) or (params, phi, logk); every instance uses the FP64-lean
+    form and the same nup.
+    """
+
+    def __init__(self, members, device="cuda", stream=None):
+        self.lib = N.load()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.n = len(members)
+        self.params = [dict(m[0]) for m in members]
+        G, P, U, F = (N.Grid * self.n)(), (N.Phys * self.n)(), (N.Num * self.n)(), (N.Fields * self.n)()
+        self.f, self.logk, self.shape = [], [], []
+        with torch.cuda.device(self.device):
+            for m, mem in enumerate(members):
+                p = dict(mem[0])
+                p["precision"] = N.PT_FP64
+                G[m], P[m], U[m] = N.grid_from(p), N.phys_from(p), N.num_from(p)
+                px = self.lib.pt_pitch_x(C.byref(G[m]))
+                box = (p["nz"] + 1, p["ny"] + 1, px)
+                f = {k: torch.zeros(box, dtype=torch.float64, device=self.device) for k in N.FIELD_NAMES}
+                sh = natural_shape("phi", p["nx"], p["ny"], p["nz"])
+                f["phi"][: sh[0], : sh[1], : sh[2]].copy_(torch.as_tensor(mem[1], dtype=torch.float64))
+                lk = None
+                if len(mem) > 2 and mem[2] is not None:
+                    lk = torch.zeros(box, dtype=torch.float64, device=self.device)
+                    lk[: sh[0], : sh[1], : sh[2]].copy_(torch.as_tensor(mem[2], dtype=torch.float64))
+                self.f.append(f)
+                self.logk.append(lk)
+                self.shape.append((p["nx"], p["ny"], p["nz"]))
+                F[m] = N.Fields(*[f[k].data_ptr() for k in N.FIELD_NAMES], lk.data_ptr() if lk is not None else None)
+            ws = self.lib.pt_batch_workspace_size(self.n, G, U)
+            if ws == 0:
+                raise PTError(N.PT_EINVAL, "pt_batch_workspace_size")
+            self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self._keep = (G, P, U, F)
+        torch.cuda.synchronize(self.device)
+        h = C.c_void_p()
+        rc = self.lib.pt_batch_init(C.byref(h), self.n, G, P, U, F, self.workspace.data_ptr(), ws,
+                                    self.stream.cuda_stream)
+        if rc != N.PT_OK:
+            raise PTError(rc, "pt_batch_init")
+        self.h = h
+
+    def step(self):
+        """One physical step of every instance: (list of report dicts, time-to-converge ms)."""
+        reps = (N.Report * self.n)()
+        ttc = (C.c_double * self.n)()
+        rc = self.lib.pt_batch_step(self.h, reps, ttc)
+        if rc not in (N.PT_OK, N.PT_ENOTCONV):
+            raise PTError(rc, "pt_batch_step")
+        return [r.as_dict() for r in reps], [float(t) for t in ttc]
+
+    def config(self) -> tuple:
+        bx, by, ipg = C.c_int32(), C.c_int32(), C.c_int32()
+        self.lib.pt_batch_config(self.h, C.byref(bx), C.byref(by), C.byref(ipg))
+        return bx.value, by.value, ipg.value
+
+    def get(self, m: int, name: str) -> np.ndarray:
+        torch.cuda.synchronize(self.device)
+        sh = natural_shape(name, *self.shape[m])
+        return self.f[m][name][: sh[0], : sh[1], : sh[2]].cpu().numpy().copy()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

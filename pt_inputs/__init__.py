@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "c1_params", "large_params", "gaussian_porosity", "perturbed_centre",
-    "field_shapes", "random_state", "PARAM_KEYS",
+    "field_shapes", "random_state", "ensemble", "PARAM_KEYS",
 ]
 
 # Parameter names as used at both boundaries (C ABI struct members and the oracle's struct).
@@ -131,4 +131,26 @@ def random_state(p: dict, seed: int, scale: float = 1e-3) -> dict:
     out["txz"][0, :, :] = 0; out["txz"][-1, :, :] = 0; out["txz"][:, :, 0] = 0; out["txz"][:, :, -1] = 0
     out["tyz"] = scale * rng.standard_normal(sh["tyz"])
     out["tyz"][0, :, :] = 0; out["tyz"][-1, :, :] = 0; out["tyz"][:, 0, :] = 0; out["tyz"][:, -1, :] = 0
+    return out
+
+
+def ensemble(seed: int = 0, n_inst: int = 64, sizes=(32, 48, 64, 96, 127), max_iter: int = 40000):
+    """Seeded ensemble of independent instances: [(params, phi), ...].
+
+    Instance i draws (numpy PCG64(seed), in order) its grid size n ~ U{sizes} (n^3 cells), the
+    weakening multiplier R_weak ~ U[0.01, 0.2], the background porosity phi0 ~ U[0.005, 0.02]
+    and 1-3 Gaussian anomalies (added amplitude 2 phi0, width 0.1) centred at U[0.2, 0.8]^3;
+    every other parameter is that of the 32^3 workload at grid size n.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n_inst):
+        n = int(rng.choice(np.asarray(sizes)))
+        R = float(rng.uniform(0.01, 0.2))
+        phi0 = float(rng.uniform(0.005, 0.02))
+        na = int(rng.integers(1, 4))
+        centres = [tuple(float(x) for x in rng.uniform(0.2, 0.8, size=3)) for _ in range(na)]
+        p = c1_params(n)
+        p.update(R_weak=R, phi0=phi0, max_iter=max_iter)
+        out.append((p, gaussian_porosity(p, centres=centres)))
     return out

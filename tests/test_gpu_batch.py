@@ -1,0 +1,74 @@
+"""Batched ensemble: every instance of one batched launch reproduces its single-instance run —
+same iteration count and status at its own convergence check, fields equal to 1e-12 relative
+(the per-point code is shared; the compiler may fuse multiply-adds differently in the two
+kernels, so the last bits can differ) — whatever tile shape and iterations per graph the tuner
+picks; and it agrees with the FP64 oracle within the 1e-10 parity bar."""
+import numpy as np
+import pytest
+
+import oracle as O
+import pt_inputs as I
+
+pytestmark = pytest.mark.gpu
+FIELDS = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi", "mu", "eta", "txx", "txy", "tyz")
+
+
+def _mods():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_08716_gb300.solver import PTBatch, PTSolver
+    return PTBatch, PTSolver
+
+
+def _members():
+    mem = I.ensemble(seed=3, n_inst=6, sizes=(9, 12, 16, 20), max_iter=3000)
+    mem[2][0]["max_iter"] = 90            # one instance hits its cap
+    return mem
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_batched_instances_equal_single_runs():
+    PTBatch, PTSolver = _mods()
+    mem = _members()
+    b = PTBatch(mem)
+    reps, ttc = b.step()
+    reps2, ttc2 = b.step()                # a second step: tuned configuration, tau_o carry-over
+    cfg = b.config()
+    assert cfg[0] in (32, 64) and cfg[2] % 30 == 0
+    for m, (p, phi) in enumerate(mem):
+        s = PTSolver(p, phi)
+        r1 = s.step()
+        r2 = s.step()
+        assert (reps[m]["iters"], reps[m]["status"]) == (r1["iters"], r1["status"]), (m, reps[m], r1)
+        assert (reps2[m]["iters"], reps2[m]["status"]) == (r2["iters"], r2["status"]), (m, reps2[m], r2)
+        for k in ("r_v", "r_pt", "r_pf", "r_pic"):      # norms of a converged state are noise-level
+            assert abs(reps2[m][k] - r2[k]) <= 1e-4 * abs(r2[k]) + 1e-14, (m, k, reps2[m][k], r2[k])
+        for name in FIELDS:
+            assert rel(b.get(m, name), s.get(name)) <= 1e-12, (m, name)
+        s.close()
+    assert reps[2]["status"] == -2 and reps[2]["iters"] == 90
+    assert all(t > 0 for t in ttc)
+    b.close()
+
+
+def test_batched_instance_matches_oracle():
+    PTBatch, _ = _mods()
+    mem = I.ensemble(seed=11, n_inst=3, sizes=(10, 14), max_iter=450)
+    for p, _ in mem:
+        p["tol"] = 0.0                    # fixed 450 iterations for every instance
+    b = PTBatch(mem)
+    reps, _ = b.step()
+    for m, (p, phi) in enumerate(mem):
+        assert reps[m]["iters"] == 450 and reps[m]["status"] == -2
+        st = O.make_state(p, phi)
+        O.begin_step(st)
+        rc, _ = O.iterate_n(st, 0, 450)
+        O.end_step(st)
+        for name in ("Vx", "Vz", "Pt", "Pf", "phi", "mu", "eta"):
+            g, o = b.get(m, name), st[name]
+            assert np.abs(g - o).max() <= 1e-10 * max(np.abs(o).max(), 1e-300), (m, name)
+    b.close()
