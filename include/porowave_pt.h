@@ -206,6 +206,26 @@ int pt_residual_static(const pt_grid *grid, const pt_phys *phys, const pt_num *n
                        const pt_fields *fields, const pt_old_fields *old, double dtS,
                        void *stream, pt_report *rep);
 
+/* ---- Adjoint -----------------------------------------------------------------
+ * Gradient of an objective J(phi^N) of the porosity after N physical steps with respect to the
+ * log-permeability field logk (k = k0 e^logk (phi/phi0)^3), by the discrete adjoint of the
+ * converged implicit steps: for n = N..1, J_F(u^n)^T lambda^n = g^n is solved with the same
+ * pseudo-transient scheme as the forward steps on the transposed staggered stencils, the
+ * gradient accumulates -(dF/dlogk)^T lambda^n and g^{n-1} = -(dF^n/du^{n-1})^T lambda^n.
+ * Scope: power law off (powerlaw_on = 0), no weakening (R_weak = 1), beta_n = 0, and no
+ * old-stress refresh inside the window (the window starts at the context's first step and the
+ * accumulated time stays below the stress sub-step dtS); other settings return PT_EINVAL.
+ * pt_adjoint_forward runs the N forward steps from the context's current state, keeping a
+ * checkpoint of the full state every ckpt_every steps in the adjoint workspace
+ * (pt_adjoint_workspace_size bytes, 256-byte aligned, device memory); pt_adjoint then sweeps
+ * back, re-running each segment from its checkpoint, writes dJ/dlogk (device, box layout) given
+ * dJ/dphi^N (device, box layout), and leaves the context at the state after step N.
+ * reps (pt_adjoint_forward: N entries; pt_adjoint: 1) report iterations and the last norms. */
+size_t pt_adjoint_workspace_size(const pt_grid *grid, int32_t nsteps, int32_t ckpt_every);
+int pt_adjoint_forward(pt_ctx *ctx, int32_t nsteps, int32_t ckpt_every, void *adj_workspace,
+                       size_t adj_bytes, pt_report *reps);
+int pt_adjoint(pt_ctx *ctx, const double *dJ_dphi, double *dJ_dlogk, pt_report *rep);
+
 /* ---- Batched ensemble --------------------------------------------------------
  * ninst independent instances (each its own grid, parameters, fields and numerics; FP64 lean
  * form, precision PT_FP64) advanced together: one launch per PT phase covers all instances

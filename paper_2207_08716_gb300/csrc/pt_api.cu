@@ -20,6 +20,7 @@
 #include "pt_lean.cuh"
 #include "pt_mixed.cuh"
 #include "pt_batch.cuh"
+#include "pt_adjoint.cuh"
 
 using namespace pt;
 
@@ -90,6 +91,12 @@ struct pt_ctx {
   float *m_dVx, *m_dVy, *m_dVz, *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
   float *m_txx, *m_tyy, *m_tzz, *m_txy, *m_txz, *m_tyz;
   CorrCoef<float> ccoef;
+  // adjoint recording (pt_adjoint_forward / pt_adjoint)
+  char* adj_ws;
+  size_t adj_bytes;
+  int adj_nsteps, adj_ckpt;
+  double adj_dtS[64], adj_dtcum[64];
+  int adj_nst[64];
   unsigned long long* red;       // device reduction block (RED_N slots)
   unsigned long long* h_red;     // pinned host copy
   // stress sub-stepping
@@ -109,13 +116,14 @@ namespace {
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
                 K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_CELLS, K_CORR_FACES,
-                K_MIX_UPDATE, K_COUNT };
+                K_MIX_UPDATE, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
                                            "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0",
                                            "k_mix_prepare", "k_mix_res_faces", "k_mix_coef",
-                                           "k_corr_cells", "k_corr_faces", "k_mix_update"};
+                                           "k_corr_cells", "k_corr_faces", "k_mix_update",
+                                           "k_adj_cells", "k_adj_faces", "k_adj_carry"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -542,6 +550,8 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   c->launches = 0;
   c->profiling = false;
   c->pool_used = 0;
+  c->adj_ws = nullptr;
+  c->adj_nsteps = 0;
   fill_coef(c);
   // zero the whole workspace (damped residuals, old stresses, scratch padding)
   cudaError_t e = cudaMemsetAsync(workspace, 0, pt_workspace_size(grid, num), c->stream);
@@ -1089,6 +1099,216 @@ void pt_batch_destroy(pt_batch* B) {
   cudaFreeHost(B->h_st);
   cudaStreamDestroy(B->stream);
   delete B;
+}
+
+}  // extern "C"
+
+// ============================================================================ adjoint
+namespace {
+
+constexpr int kCkptArrays = 23;   // 14 caller fields, R (3), old stresses (6)
+constexpr int kSegArrays = 6;     // converged Vx, Vy, Vz, Pt, Pf, phi per step of a segment
+constexpr int kAdjArrays = 22;    // multipliers, residual memory, stresses, right-hand sides
+
+int n_ckpts(int nsteps, int every) { return (nsteps + every - 1) / every + 1; }  // + final state
+
+double** ckpt_sources(pt_ctx* c, double** s) {
+  double* src[kCkptArrays] = {c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->txx, c->tyy, c->tzz,
+                              c->txy, c->txz, c->tyz, c->mu, c->eta, c->Rx, c->Ry, c->Rz, c->txxo,
+                              c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
+  for (int i = 0; i < kCkptArrays; ++i) s[i] = src[i];
+  return s;
+}
+
+double* adj_array(pt_ctx* c, size_t index) {
+  const size_t stride = align_up((size_t)c->box.n * sizeof(double), kAlign);
+  return (double*)(c->adj_ws + index * stride);
+}
+
+int ckpt_io(pt_ctx* c, int slot, bool save) {
+  double* s[kCkptArrays];
+  ckpt_sources(c, s);
+  const size_t bytes = (size_t)c->box.n * sizeof(double);
+  for (int i = 0; i < kCkptArrays; ++i) {
+    double* d = adj_array(c, (size_t)slot * kCkptArrays + i);
+    const cudaError_t e = save ? cudaMemcpyAsync(d, s[i], bytes, cudaMemcpyDeviceToDevice, c->stream)
+                               : cudaMemcpyAsync(s[i], d, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return PT_ECUDA;
+  }
+  if (save) {
+    c->adj_dtS[slot] = c->dtS;
+    c->adj_dtcum[slot] = c->dt_cum;
+    c->adj_nst[slot] = c->nsteps;
+  } else {
+    c->dtS = c->adj_dtS[slot];
+    c->dt_cum = c->adj_dtcum[slot];
+    c->nsteps = c->adj_nst[slot];
+    c->cur = 0;
+    fill_coef(c);
+  }
+  return PT_OK;
+}
+
+bool adjoint_scope_ok(const pt_ctx* c) {
+  return c->phys.powerlaw_on == 0 && c->phys.compaction_on != 0 && c->phys.R_weak == 1.0 &&
+         c->num.beta_n == 0.0 && !c->mixed && (c->lean || !c->logk);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pt_adjoint_workspace_size(const pt_grid* grid, int32_t nsteps, int32_t every) {
+  if (!grid_ok(grid) || nsteps < 1 || every < 1) return 0;
+  const int nck = n_ckpts(nsteps, every);
+  if (nck > 64) return 0;
+  const Box b = make_box(grid);
+  const size_t arrays = (size_t)nck * kCkptArrays + (size_t)(every + 1) * kSegArrays + kAdjArrays;
+  return arrays * align_up((size_t)b.n * sizeof(double), kAlign);
+}
+
+int pt_adjoint_forward(pt_ctx* c, int32_t nsteps, int32_t every, void* ws, size_t bytes, pt_report* reps) {
+  if (!c || !ws || nsteps < 1 || every < 1) return PT_EINVAL;
+  if (!adjoint_scope_ok(c) || c->nsteps != 0) return PT_EINVAL;
+  if (sync_current_to_caller(c) != PT_OK) return PT_ECUDA;
+  if (((uintptr_t)ws & (kAlign - 1)) != 0) return PT_EINVAL;
+  const size_t need = pt_adjoint_workspace_size(&c->grid, nsteps, every);
+  if (need == 0) return PT_EINVAL;
+  if (bytes < need) return PT_ESPACE;
+  c->adj_ws = (char*)ws;
+  c->adj_bytes = bytes;
+  c->adj_nsteps = nsteps;
+  c->adj_ckpt = every;
+  int rc = PT_OK;
+  for (int n = 0; n < nsteps && rc == PT_OK; ++n) {
+    if (n % every == 0) rc = ckpt_io(c, n / every, true);
+    if (rc != PT_OK) break;
+    pt_report r;
+    rc = pt_step(c, &r);
+    if (reps) reps[n] = r;
+    if (rc == PT_ENOTCONV) rc = PT_OK;   // reported per step; the adjoint uses the iterate reached
+    // the old stresses must not be refreshed after the first step inside the window
+    if (rc == PT_OK && c->dt_cum < (n + 0.5) * c->num.dt) rc = PT_EINVAL;
+  }
+  if (rc == PT_OK) rc = ckpt_io(c, n_ckpts(nsteps, every) - 1, true);   // final state
+  if (rc == PT_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rc != PT_OK) c->adj_nsteps = 0;
+  return rc;
+}
+
+int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
+  if (!c || !dJ_dphi || !grad || !c->adj_ws || c->adj_nsteps < 1) return PT_EINVAL;
+  const Box& b = c->box;
+  const dim3 bl = block_dims(), gr = grid_dims(b);
+  const int N = c->adj_nsteps, every = c->adj_ckpt, nck = n_ckpts(N, every);
+  const size_t bytes = (size_t)b.n * sizeof(double);
+  // adjoint arrays after the checkpoints and the segment states
+  const size_t seg0 = (size_t)nck * kCkptArrays, adj0 = seg0 + (size_t)(every + 1) * kSegArrays;
+  double* A[kAdjArrays];
+  for (int i = 0; i < kAdjArrays; ++i) A[i] = adj_array(c, adj0 + i);
+  double *Lx = A[0], *Ly = A[1], *Lz = A[2], *LRx = A[3], *LRy = A[4], *LRz = A[5];
+  double* lP[2] = {A[6], A[7]};
+  double* lF[2] = {A[8], A[9]};
+  double* lL[2] = {A[10], A[11]};
+  double *atxx = A[12], *atyy = A[13], *atzz = A[14], *atxy = A[15], *atxz = A[16], *atyz = A[17];
+  double *gP = A[18], *gF = A[19], *gphi = A[20], *gth = A[21];
+  auto seg = [&](int slot, int f) { return adj_array(c, seg0 + (size_t)slot * kSegArrays + f); };
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < kAdjArrays && e == cudaSuccess; ++i) e = cudaMemsetAsync(A[i], 0, bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gphi, dJ_dphi, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  // adjoint coefficients (mu = mu0 everywhere in scope)
+  const Coef& k = c->coef;
+  AdjCoef ac;
+  ac.rdx = k.rdx; ac.rdy = k.rdy; ac.rdz = k.rdz;
+  ac.m2 = 2.0 * c->phys.mu0 / (1.0 + c->phys.mu0 * k.rGdtS);   // d tau / d eps with fixed old stresses
+  ac.r_eta0mu0 = 1.0 / (c->phys.eta0 * c->phys.mu0);
+  ac.bd_rdt = k.beta_d * k.rdt;
+  ac.bd_rdt_a = k.beta_d * k.alpha * k.rdt;
+  ac.bda_B_rdt = k.beta_d * k.alpha / k.B * k.rdt;
+  ac.beta_phi = k.beta_phi;
+  ac.dt = k.dt;
+  ac.idtp = 1.0 / (k.dtaupt_fac * c->phys.mu0);
+  ac.ifac_pf = 1.0 / k.dtaupf_fac;
+  ac.rphi0 = k.rphi0;
+  ac.k0 = k.k0;
+  ac.buoy = k.rhof_g - k.rho_bg_g;
+  ac.drho_g = c->phys.rhof_g - c->phys.rhos_g;
+  ac.rrho_i = k.rrho_i;
+  ac.damp_x = k.damp_x; ac.damp_y = k.damp_y; ac.damp_z = k.damp_z;
+  ac.dtauv = k.dtauv_fac / c->phys.mu0;
+  const double* K0 = (c->lean && c->logk) ? c->K0 : nullptr;
+  long long total_iters = 0;
+  pt_report last;
+  std::memset(&last, 0, sizeof last);
+  int rc = PT_OK;
+  int cur = 0;   // parity of the multipliers' ping-pong
+  for (int s = nck - 2; s >= 0 && rc == PT_OK; --s) {
+    const int n0 = s * every, n1 = std::min(N, n0 + every);
+    // re-run the segment from its checkpoint, keeping every converged state
+    rc = ckpt_io(c, s, false);
+    double* src[kSegArrays] = {c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0]};
+    for (int f = 0; f < kSegArrays && rc == PT_OK; ++f)
+      if (cudaMemcpyAsync(seg(0, f), src[f], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) rc = PT_ECUDA;
+    for (int n = n0 + 1; n <= n1 && rc == PT_OK; ++n) {
+      pt_report r;
+      rc = pt_step(c, &r);
+      if (rc == PT_ENOTCONV) rc = PT_OK;
+      for (int f = 0; f < kSegArrays && rc == PT_OK; ++f)
+        if (cudaMemcpyAsync(seg(n - n0, f), src[f], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+          rc = PT_ECUDA;
+    }
+    // adjoint steps n1 .. n0+1, warm-started from the previous step's multipliers
+    for (int n = n1; n > n0 && rc == PT_OK; --n) {
+      AdjState u{seg(n - n0, 0), seg(n - n0, 1), seg(n - n0, 2), seg(n - n0, 3), seg(n - n0, 4), seg(n - n0, 5)};
+      // convergence: residual max-norms below tol times the largest right-hand side |g|
+      cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+      PT_LAUNCH(c, K_ADJ_CARRY, adj_gmax(gr, bl, c->stream, b, gP, gF, gphi, c->red));
+      double gscale = 0.0;
+      if (cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          c->stream) != cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        rc = PT_ECUDA;
+        break;
+      }
+      std::memcpy(&gscale, &c->h_red[RED_GMAX], sizeof gscale);
+      int it = 0;
+      const int nup = c->num.nup, cap = c->num.max_iter;
+      while (gscale > 0.0 && it < cap && rc == PT_OK) {
+        ++it;
+        const int check = (it % nup) == 0 || it == cap;
+        if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+        AdjCellIn ci{Lx, Ly, Lz, lP[cur], lF[cur], lL[cur], gP, gF, gphi, K0};
+        AdjCellOut co{atxx, atyy, atzz, atxy, atxz, atyz, lP[1 - cur], lF[1 - cur], lL[1 - cur],
+                      check ? gth : nullptr};
+        PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, ci, co, c->red, check));
+        AdjFaceIn fi{atxx, atyy, atzz, atxy, atxz, atyz, lP[1 - cur], lL[cur]};
+        PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, u, fi, Lx, Ly, Lz, LRx, LRy, LRz, c->red, check));
+        cur = 1 - cur;
+        if (check) {
+          rc = read_report(c, &last);
+          if (rc != PT_OK) break;
+          if (report_max(&last) < c->num.tol * gscale) break;
+        }
+      }
+      total_iters += it;
+      if (rc != PT_OK) break;
+      if (gscale == 0.0) cudaMemsetAsync(gth, 0, bytes, c->stream);   // g = 0: lambda = 0
+      // gradient and carry into step n-1 (phi_o = phi^{n-1})
+      AdjCarry ca{lP[cur], lF[cur], lL[cur], gth, seg(n - 1 - n0, 5), grad, gP, gF, gphi};
+      PT_LAUNCH(c, K_ADJ_CARRY, adj_carry(gr, bl, c->stream, b, ac, ca));
+      if (cudaGetLastError() != cudaSuccess) rc = PT_ECUDA;
+    }
+  }
+  if (rc == PT_OK) rc = ckpt_io(c, nck - 1, false);   // back to the state after step N
+  if (rc == PT_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+  if (rep) {
+    *rep = last;
+    rep->iters = (int32_t)std::min<long long>(total_iters, 0x7fffffff);
+    rep->status = rc;
+  }
+  return rc;
 }
 
 }  // extern "C"

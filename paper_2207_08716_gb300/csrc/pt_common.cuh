@@ -39,7 +39,7 @@ __host__ __device__ inline long long cidx(const Box& b, int i, int j, int k) {
 }
 
 // Indices of the residual max-norm slots in the device reduction block.
-enum { RED_V = 0, RED_PT = 1, RED_PF = 2, RED_PIC = 3, RED_MUMAX = 4, RED_N = 8 };
+enum { RED_V = 0, RED_PT = 1, RED_PF = 2, RED_PIC = 3, RED_MUMAX = 4, RED_GMAX = 5, RED_N = 8 };
 
 // Max-reduction of non-negative doubles through their bit patterns (monotone for x >= 0; a
 // NaN from fabs has the largest pattern and therefore surfaces in the norm). Every thread of

@@ -127,6 +127,30 @@ class PTSolver:
         self._check(self.lib.pt_residual(self.ctx, C.byref(rep)), "pt_residual")
         return rep.as_dict()
 
+    # ------------------------------------------------------------------- adjoint
+    def adjoint_forward(self, nsteps: int, ckpt_every: int | None = None) -> list:
+        """Run `nsteps` steps from the current (fresh) state keeping adjoint checkpoints."""
+        every = int(ckpt_every or nsteps)
+        need = self.lib.pt_adjoint_workspace_size(C.byref(self._grid), nsteps, every)
+        if need == 0:
+            raise PTError(N.PT_EINVAL, "pt_adjoint_workspace_size")
+        with torch.cuda.device(self.device):
+            self.adj_workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+        reps = (N.Report * nsteps)()
+        rc = self.lib.pt_adjoint_forward(self.ctx, nsteps, every, self.adj_workspace.data_ptr(), need, reps)
+        self._check(rc, "pt_adjoint_forward")
+        return [r.as_dict() for r in reps]
+
+    def adjoint(self, dJ_dphi) -> tuple:
+        """dJ/dlogk (cell-centred, natural shape, torch on the device) for dJ/dphi^N."""
+        g = torch.zeros(self.box_shape, dtype=torch.float64, device=self.device)
+        self._put(g, "phi", dJ_dphi)
+        out = torch.empty_like(g)
+        rep = N.Report()
+        torch.cuda.current_stream(self.device).synchronize()
+        self._check(self.lib.pt_adjoint(self.ctx, g.data_ptr(), out.data_ptr(), C.byref(rep)), "pt_adjoint")
+        return out[: self.nz, : self.ny, : self.nx].clone(), rep.as_dict()
+
     # ------------------------------------------------------------- measurement aids
     def profile_begin(self) -> None:
         self._check(self.lib.pt_profile_begin(self.ctx), "pt_profile_begin")

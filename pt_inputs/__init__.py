@@ -154,3 +154,18 @@ def ensemble(seed: int = 0, n_inst: int = 64, sizes=(32, 48, 64, 96, 127), max_i
         p.update(R_weak=R, phi0=phi0, max_iter=max_iter)
         out.append((p, gaussian_porosity(p, centres=centres)))
     return out
+
+
+def gaussian_random_field(shape, seed: int, corr_len: float = 0.1, std: float = 0.5) -> np.ndarray:
+    """Seeded Gaussian random field on the unit box (cell-centred, shape (nz, ny, nx)): white
+    noise filtered in Fourier space by a Gaussian of correlation length `corr_len`, rescaled to
+    standard deviation `std` (log-permeability prefactor fields for the adjoint's inputs)."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(shape)
+    ks = [np.fft.fftfreq(n, d=1.0 / n) for n in shape]
+    kz, ky, kx = np.meshgrid(*ks, indexing="ij")
+    filt = np.exp(-0.5 * (2 * np.pi * corr_len) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
+    f = np.real(np.fft.ifftn(np.fft.fftn(w) * filt))
+    f -= f.mean()
+    sd = f.std()
+    return f * (std / sd) if sd > 0 else f
