@@ -80,6 +80,13 @@ def parse():
     ap.add_argument("--fp32-iters", type=int, default=300, help="FP32 iterations per step of the fp32 form")
     ap.add_argument("--batch-n", type=int, default=64, help="instances of the batched form")
     ap.add_argument("--batch-iters", type=int, default=60, help="PT iterations per step of the batched form")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="measure the adjoint instead (127^3, 20 steps, checkpoint every 5): forward and "
+                         "backward wall time, cost multiple, optional finite-difference check")
+    ap.add_argument("--adjoint-n", type=int, default=127)
+    ap.add_argument("--adjoint-steps", type=int, default=20)
+    ap.add_argument("--adjoint-ckpt", type=int, default=5)
+    ap.add_argument("--adjoint-fd", type=int, default=0, help="finite-difference directions to check")
     ap.add_argument("--batched-converge", action="store_true",
                     help="run one step of the batched ensemble to convergence and report p50/p99 "
                          "time-to-converge (minutes of GPU time) instead of the throughput bench")
@@ -309,6 +316,85 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
     return out
 
 
+def measure_adjoint(args, dev) -> dict:
+    """Gradient of J = sum (phi^N - phi_target)^2 w.r.t. the log-permeability field: N converged
+    steps recorded with checkpoints, then the checkpointed reverse sweep (recompute + adjoint PT
+    per step). theta and the target's theta are Gaussian random fields (corr. length 0.1, std 0.5,
+    seeds 1 and 2); finite-difference directions use seeds 10, 11, ..."""
+    import torch
+    from paper_2207_08716_gb300.adjoint import adjoint_scope
+    from paper_2207_08716_gb300.solver import PTSolver
+
+    n, N, every = args.adjoint_n, args.adjoint_steps, args.adjoint_ckpt
+    p = adjoint_scope(I.c1_params(n))
+    p["precision"] = PRECISIONS["fp64"]
+    p["max_iter"] = 200000
+    phi = I.gaussian_porosity(p, centres=(I.perturbed_centre(0),))
+    theta = I.gaussian_random_field(phi.shape, seed=1, corr_len=0.1, std=0.5)
+    theta_t = I.gaussian_random_field(phi.shape, seed=2, corr_len=0.1, std=0.5)
+
+    def run_forward(th):
+        s = PTSolver(p, phi, logk=th, device=dev)
+        its = 0
+        for _ in range(N):
+            its += s.step()["iters"]
+        out = s.get("phi")
+        s.close()
+        return out, its
+
+    clocks = M.ClockSampler(dev.index or 0)
+    target, _ = run_forward(theta_t)
+    s = PTSolver(p, phi, logk=theta, device=dev)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t0 = time.perf_counter()
+    reps = s.adjoint_forward(N, every)
+    t_fwd = time.perf_counter() - t0
+    phiN = s.get("phi")
+    dJ = 2.0 * (phiN - target)
+    launches0 = s.launch_count()
+    s.profile_begin()
+    t0 = time.perf_counter()
+    grad, rep = s.adjoint(dJ)
+    torch.cuda.synchronize(dev)
+    t_bwd = time.perf_counter() - t0
+    kernels = s.profile_end()
+    clk = clocks.stop()
+    launches = s.launch_count() - launches0
+    grad = grad.cpu().numpy()
+    fwd_iters = sum(r["iters"] for r in reps)
+    adj_ms = sum(kernels.get(k, (0, 0.0))[1] for k in ("k_adj_cells", "k_adj_faces"))
+    ncell = n ** 3
+    out = {"n": n, "steps": N, "ckpt_every": every, "forward_s": t_fwd, "backward_s": t_bwd,
+           "cost_multiple": t_bwd / t_fwd, "forward_pt_iters": fwd_iters, "adjoint_pt_iters": rep["iters"],
+           "adjoint_ms_per_iter": adj_ms / max(rep["iters"], 1),
+           "forward_statuses": sorted({r["status"] for r in reps}), "adjoint_status": rep["status"],
+           "J": float(np.sum((phiN - target) ** 2)), "grad_max": float(np.abs(grad).max()),
+           "gpu_launches": launches, "clocks": clk,
+           "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()}}
+    # algorithmic bytes of one adjoint PT iteration: cells reads 16 arrays (3 lambda_V, 3 centre
+    # multipliers, 3 right-hand sides, K0, V (3), Pt, Pf, phi) and writes 9 (6 adjoint stresses, 3
+    # multipliers); faces reads 15 (6 stresses, lambda_P, lambda_L, phi, 3 lambda_V, 3 R) and
+    # writes 6 (3 R, 3 lambda_V)
+    if adj_ms > 0:
+        out["adjoint_gbs"] = (25 + 21) * 8 * ncell * rep["iters"] / (adj_ms / 1e3) / 1e9
+    s.close()
+    if args.adjoint_fd > 0:
+        eps = 1e-6 * float(np.abs(theta).max())
+        checks = []
+        for d in range(args.adjoint_fd):
+            v = I.gaussian_random_field(phi.shape, seed=10 + d, corr_len=0.1, std=1.0)
+            Jp = float(np.sum((run_forward(theta + eps * v)[0] - target) ** 2))
+            Jm = float(np.sum((run_forward(theta - eps * v)[0] - target) ** 2))
+            fd = (Jp - Jm) / (2 * eps)
+            ad = float(np.sum(grad * v))
+            checks.append({"seed": 10 + d, "adjoint": ad, "fd": fd, "rel": abs(ad - fd) / abs(fd)})
+        out["fd_checks"] = checks
+        out["fd_eps"] = eps
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -319,6 +405,12 @@ def run_native(args):
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=dev)
 
+    if args.adjoint:
+        if rank == 0:
+            r = measure_adjoint(args, dev)
+            print(json.dumps({"metric": "adjoint gradient dJ/dlogk: cost multiple of the forward", **r}),
+                  flush=True)
+        return 0
     if args.batched_converge:
         r = measure_batched(args, 1, 0, dev, world, rank, converge=True)
         if rank == 0:

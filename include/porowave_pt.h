@@ -217,7 +217,8 @@ int pt_residual_static(const pt_grid *grid, const pt_phys *phys, const pt_num *n
  * accumulated time stays below the stress sub-step dtS); other settings return PT_EINVAL.
  * pt_adjoint_forward runs the N forward steps from the context's current state, keeping a
  * checkpoint of the full state every ckpt_every steps in the adjoint workspace
- * (pt_adjoint_workspace_size bytes, 256-byte aligned, device memory); pt_adjoint then sweeps
+ * (pt_adjoint_workspace_size bytes, 256-byte aligned, device memory; ckpt_every = 1 stores every
+ * step and the reverse sweep then runs no forward step again); pt_adjoint then sweeps
  * back, re-running each segment from its checkpoint, writes dJ/dlogk (device, box layout) given
  * dJ/dphi^N (device, box layout), and leaves the context at the state after step N.
  * reps (pt_adjoint_forward: N entries; pt_adjoint: 1) report iterations and the last norms. */
@@ -225,6 +226,20 @@ size_t pt_adjoint_workspace_size(const pt_grid *grid, int32_t nsteps, int32_t ck
 int pt_adjoint_forward(pt_ctx *ctx, int32_t nsteps, int32_t ckpt_every, void *adj_workspace,
                        size_t adj_bytes, pt_report *reps);
 int pt_adjoint(pt_ctx *ctx, const double *dJ_dphi, double *dJ_dlogk, pt_report *rep);
+
+/* One application of the transposed operator: out = J_F(u)^T lam, J_F the Jacobian of the
+ * residual F = (F_V, F_Pt, F_Pf, F_L) of the implicit step (Eqs. 17-22, same scope as
+ * pt_adjoint) at the context's current fields u (k0 e^logk from pt_init). Components are in
+ * box layout on the device: lam/out Vx, Vy, Vz on faces (the wall-normal faces of lam must hold
+ * zero; those of out are set to zero), Pt, Pf, phi at centres (lam->Pt pairs with F_Pt, ... ,
+ * lam->phi with F_L; out->phi is dF/dphi^T lam). Requires a step begun (pt_step or
+ * pt_step_begin); workspace: pt_adjoint_workspace_size(grid, 0, 1) bytes of device memory,
+ * 256-byte aligned, used as scratch. Synchronises the stream. The thesis has no counterpart:
+ * this exists so that the transposed stencils can be checked against an independent Jacobian. */
+typedef struct {
+  double *Vx, *Vy, *Vz, *Pt, *Pf, *phi;
+} pt_adj_vec;
+int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *workspace, size_t bytes);
 
 /* ---- Batched ensemble --------------------------------------------------------
  * ninst independent instances (each its own grid, parameters, fields and numerics; FP64 lean

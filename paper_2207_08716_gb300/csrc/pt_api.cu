@@ -95,8 +95,8 @@ struct pt_ctx {
   char* adj_ws;
   size_t adj_bytes;
   int adj_nsteps, adj_ckpt;
-  double adj_dtS[64], adj_dtcum[64];
-  int adj_nst[64];
+  std::vector<double> adj_dtS, adj_dtcum;
+  std::vector<int> adj_nst;
   unsigned long long* red;       // device reduction block (RED_N slots)
   unsigned long long* h_red;     // pinned host copy
   // stress sub-stepping
@@ -116,14 +116,14 @@ namespace {
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
                 K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_CELLS, K_CORR_FACES,
-                K_MIX_UPDATE, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_COUNT };
+                K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
                                            "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0",
                                            "k_mix_prepare", "k_mix_res_faces", "k_mix_coef",
                                            "k_corr_cells", "k_corr_faces", "k_mix_update",
-                                           "k_adj_cells", "k_adj_faces", "k_adj_carry"};
+                                           "k_adj_prep", "k_adj_cells", "k_adj_faces", "k_adj_carry"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -1108,7 +1108,7 @@ namespace {
 
 constexpr int kCkptArrays = 23;   // 14 caller fields, R (3), old stresses (6)
 constexpr int kSegArrays = 6;     // converged Vx, Vy, Vz, Pt, Pf, phi per step of a segment
-constexpr int kAdjArrays = 22;    // multipliers, residual memory, stresses, right-hand sides
+constexpr int kAdjArrays = 40;    // multipliers, residual memory, stresses, right-hand sides, coefficients
 
 int n_ckpts(int nsteps, int every) { return (nsteps + every - 1) / every + 1; }  // + final state
 
@@ -1120,10 +1120,10 @@ double** ckpt_sources(pt_ctx* c, double** s) {
   return s;
 }
 
-double* adj_array(pt_ctx* c, size_t index) {
-  const size_t stride = align_up((size_t)c->box.n * sizeof(double), kAlign);
-  return (double*)(c->adj_ws + index * stride);
+double* ws_array(char* base, const Box& b, size_t index) {
+  return (double*)(base + index * align_up((size_t)b.n * sizeof(double), kAlign));
 }
+double* adj_array(pt_ctx* c, size_t index) { return ws_array(c->adj_ws, c->box, index); }
 
 int ckpt_io(pt_ctx* c, int slot, bool save) {
   double* s[kCkptArrays];
@@ -1154,31 +1154,93 @@ bool adjoint_scope_ok(const pt_ctx* c) {
          c->num.beta_n == 0.0 && !c->mixed && (c->lean || !c->logk);
 }
 
+// The adjoint's working arrays (kAdjArrays consecutive workspace arrays from `base`).
+struct AdjArrays {
+  double *Lx, *Ly, *Lz, *LRx, *LRy, *LRz, *lP[2], *lF[2], *lL[2], *mL[2];
+  double *txx, *tyy, *tzz, *txy, *txz, *tyz, *gP, *gF, *gphi, *gth;
+  AdjPrep prep;
+  double* all[kAdjArrays];
+  AdjArrays(char* base, const Box& b) {
+    for (int i = 0; i < kAdjArrays; ++i) all[i] = ws_array(base, b, i);
+    double** A = all;
+    Lx = A[0]; Ly = A[1]; Lz = A[2]; LRx = A[3]; LRy = A[4]; LRz = A[5];
+    lP[0] = A[6]; lP[1] = A[7]; lF[0] = A[8]; lF[1] = A[9]; lL[0] = A[10]; lL[1] = A[11];
+    mL[0] = A[12]; mL[1] = A[13];
+    txx = A[14]; tyy = A[15]; tzz = A[16]; txy = A[17]; txz = A[18]; tyz = A[19];
+    gP = A[20]; gF = A[21]; gphi = A[22]; gth = A[23];
+    prep = AdjPrep{A[24], A[25], A[26], A[27], A[28], A[29], A[30], A[31], A[32], A[33],
+                   A[34], A[35], A[36], A[37], A[38], A[39], nullptr, nullptr};
+  }
+  AdjPrep prep_for(int cur) const {
+    AdjPrep p = prep;
+    p.lL = lL[cur];
+    p.mL = mL[cur];
+    return p;
+  }
+  AdjCellIn cell_in(int cur, const double* K0) const {
+    return AdjCellIn{Lx, Ly, Lz, lP[cur], lF[cur], lL[cur], mL[cur], gP, gF, gphi, K0,
+                     prep.W, prep.cP, prep.cF, prep.Dg, prep.iD, prep.aPF, prep.a3k,
+                     prep.kfx, prep.kfy, prep.kfz, prep.gkx, prep.gky, prep.gkz};
+  }
+};
+
+// Scalars of the transposed system (mu = mu0 everywhere in the adjoint's scope).
+AdjCoef adjoint_coef(const pt_ctx* c) {
+  const Coef& k = c->coef;
+  AdjCoef ac;
+  ac.rdx = k.rdx; ac.rdy = k.rdy; ac.rdz = k.rdz;
+  ac.m2 = 2.0 * c->phys.mu0 / (1.0 + c->phys.mu0 * k.rGdtS);   // d tau / d eps, fixed old stresses
+  ac.third = 1.0 / 3.0;
+  ac.hm2rdx = 0.5 * ac.m2 * k.rdx; ac.hm2rdy = 0.5 * ac.m2 * k.rdy; ac.hm2rdz = 0.5 * ac.m2 * k.rdz;
+  ac.r_eta0mu0 = 1.0 / (c->phys.eta0 * c->phys.mu0);
+  ac.bd_rdt = k.beta_d * k.rdt;
+  ac.bd_rdt_a = k.beta_d * k.alpha * k.rdt;
+  ac.bda_B_rdt = k.beta_d * k.alpha / k.B * k.rdt;
+  ac.beta_phi = k.beta_phi;
+  ac.dt = k.dt;
+  ac.dt_r = k.dt * ac.r_eta0mu0;
+  ac.idtp = 1.0 / (k.dtaupt_fac * c->phys.mu0);
+  ac.ifac_pf = 1.0 / k.dtaupf_fac;
+  ac.rphi0 = k.rphi0;
+  ac.k0 = k.k0;
+  ac.buoy = k.rhof_g - k.rho_bg_g;
+  ac.hdrho_g = 0.5 * (c->phys.rhof_g - c->phys.rhos_g);
+  ac.hdt_rdx = 0.5 * k.dt * k.rdx; ac.hdt_rdy = 0.5 * k.dt * k.rdy; ac.hdt_rdz = 0.5 * k.dt * k.rdz;
+  ac.rrho_i = k.rrho_i;
+  ac.damp_x = k.damp_x; ac.damp_y = k.damp_y; ac.damp_z = k.damp_z;
+  ac.dtauv = k.dtauv_fac / c->phys.mu0;
+  return ac;
+}
+
 }  // namespace
 
 extern "C" {
 
 size_t pt_adjoint_workspace_size(const pt_grid* grid, int32_t nsteps, int32_t every) {
-  if (!grid_ok(grid) || nsteps < 1 || every < 1) return 0;
-  const int nck = n_ckpts(nsteps, every);
-  if (nck > 64) return 0;
+  if (!grid_ok(grid) || nsteps < 0 || every < 1) return 0;
   const Box b = make_box(grid);
-  const size_t arrays = (size_t)nck * kCkptArrays + (size_t)(every + 1) * kSegArrays + kAdjArrays;
-  return arrays * align_up((size_t)b.n * sizeof(double), kAlign);
+  const size_t stride = align_up((size_t)b.n * sizeof(double), kAlign);
+  if (nsteps == 0) return (size_t)kAdjArrays * stride;                    // pt_adjoint_apply
+  const int nck = n_ckpts(nsteps, every);
+  return ((size_t)nck * kCkptArrays + (size_t)(every + 1) * kSegArrays + kAdjArrays) * stride;
 }
 
 int pt_adjoint_forward(pt_ctx* c, int32_t nsteps, int32_t every, void* ws, size_t bytes, pt_report* reps) {
   if (!c || !ws || nsteps < 1 || every < 1) return PT_EINVAL;
   if (!adjoint_scope_ok(c) || c->nsteps != 0) return PT_EINVAL;
-  if (sync_current_to_caller(c) != PT_OK) return PT_ECUDA;
   if (((uintptr_t)ws & (kAlign - 1)) != 0) return PT_EINVAL;
   const size_t need = pt_adjoint_workspace_size(&c->grid, nsteps, every);
   if (need == 0) return PT_EINVAL;
   if (bytes < need) return PT_ESPACE;
+  if (sync_current_to_caller(c) != PT_OK) return PT_ECUDA;
   c->adj_ws = (char*)ws;
   c->adj_bytes = bytes;
   c->adj_nsteps = nsteps;
   c->adj_ckpt = every;
+  const int nck = n_ckpts(nsteps, every);
+  c->adj_dtS.assign(nck, 0.0);
+  c->adj_dtcum.assign(nck, 0.0);
+  c->adj_nst.assign(nck, 0);
   int rc = PT_OK;
   for (int n = 0; n < nsteps && rc == PT_OK; ++n) {
     if (n % every == 0) rc = ckpt_io(c, n / every, true);
@@ -1190,7 +1252,7 @@ int pt_adjoint_forward(pt_ctx* c, int32_t nsteps, int32_t every, void* ws, size_
     // the old stresses must not be refreshed after the first step inside the window
     if (rc == PT_OK && c->dt_cum < (n + 0.5) * c->num.dt) rc = PT_EINVAL;
   }
-  if (rc == PT_OK) rc = ckpt_io(c, n_ckpts(nsteps, every) - 1, true);   // final state
+  if (rc == PT_OK) rc = ckpt_io(c, nck - 1, true);   // final state
   if (rc == PT_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
   if (rc != PT_OK) c->adj_nsteps = 0;
   return rc;
@@ -1202,42 +1264,15 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
   const dim3 bl = block_dims(), gr = grid_dims(b);
   const int N = c->adj_nsteps, every = c->adj_ckpt, nck = n_ckpts(N, every);
   const size_t bytes = (size_t)b.n * sizeof(double);
-  // adjoint arrays after the checkpoints and the segment states
   const size_t seg0 = (size_t)nck * kCkptArrays, adj0 = seg0 + (size_t)(every + 1) * kSegArrays;
-  double* A[kAdjArrays];
-  for (int i = 0; i < kAdjArrays; ++i) A[i] = adj_array(c, adj0 + i);
-  double *Lx = A[0], *Ly = A[1], *Lz = A[2], *LRx = A[3], *LRy = A[4], *LRz = A[5];
-  double* lP[2] = {A[6], A[7]};
-  double* lF[2] = {A[8], A[9]};
-  double* lL[2] = {A[10], A[11]};
-  double *atxx = A[12], *atyy = A[13], *atzz = A[14], *atxy = A[15], *atxz = A[16], *atyz = A[17];
-  double *gP = A[18], *gF = A[19], *gphi = A[20], *gth = A[21];
+  AdjArrays A(c->adj_ws + adj0 * align_up(bytes, kAlign), b);
   auto seg = [&](int slot, int f) { return adj_array(c, seg0 + (size_t)slot * kSegArrays + f); };
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < kAdjArrays && e == cudaSuccess; ++i) e = cudaMemsetAsync(A[i], 0, bytes, c->stream);
+  for (int i = 0; i < kAdjArrays && e == cudaSuccess; ++i) e = cudaMemsetAsync(A.all[i], 0, bytes, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, bytes, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(gphi, dJ_dphi, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A.gphi, dJ_dphi, bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return PT_ECUDA;
-  // adjoint coefficients (mu = mu0 everywhere in scope)
-  const Coef& k = c->coef;
-  AdjCoef ac;
-  ac.rdx = k.rdx; ac.rdy = k.rdy; ac.rdz = k.rdz;
-  ac.m2 = 2.0 * c->phys.mu0 / (1.0 + c->phys.mu0 * k.rGdtS);   // d tau / d eps with fixed old stresses
-  ac.r_eta0mu0 = 1.0 / (c->phys.eta0 * c->phys.mu0);
-  ac.bd_rdt = k.beta_d * k.rdt;
-  ac.bd_rdt_a = k.beta_d * k.alpha * k.rdt;
-  ac.bda_B_rdt = k.beta_d * k.alpha / k.B * k.rdt;
-  ac.beta_phi = k.beta_phi;
-  ac.dt = k.dt;
-  ac.idtp = 1.0 / (k.dtaupt_fac * c->phys.mu0);
-  ac.ifac_pf = 1.0 / k.dtaupf_fac;
-  ac.rphi0 = k.rphi0;
-  ac.k0 = k.k0;
-  ac.buoy = k.rhof_g - k.rho_bg_g;
-  ac.drho_g = c->phys.rhof_g - c->phys.rhos_g;
-  ac.rrho_i = k.rrho_i;
-  ac.damp_x = k.damp_x; ac.damp_y = k.damp_y; ac.damp_z = k.damp_z;
-  ac.dtauv = k.dtauv_fac / c->phys.mu0;
+  const AdjCoef ac = adjoint_coef(c);
   const double* K0 = (c->lean && c->logk) ? c->K0 : nullptr;
   long long total_iters = 0;
   pt_report last;
@@ -1246,25 +1281,32 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
   int cur = 0;   // parity of the multipliers' ping-pong
   for (int s = nck - 2; s >= 0 && rc == PT_OK; --s) {
     const int n0 = s * every, n1 = std::min(N, n0 + every);
-    // re-run the segment from its checkpoint, keeping every converged state
-    rc = ckpt_io(c, s, false);
+    // re-run the segment from its checkpoint, keeping every converged state; its last state is
+    // the next checkpoint (no recompute at all when every step is checkpointed)
     double* src[kSegArrays] = {c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0]};
-    for (int f = 0; f < kSegArrays && rc == PT_OK; ++f)
-      if (cudaMemcpyAsync(seg(0, f), src[f], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) rc = PT_ECUDA;
-    for (int n = n0 + 1; n <= n1 && rc == PT_OK; ++n) {
+    auto keep = [&](int m) {
+      for (int f = 0; f < kSegArrays && rc == PT_OK; ++f)
+        if (cudaMemcpyAsync(seg(m, f), src[f], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+          rc = PT_ECUDA;
+    };
+    rc = ckpt_io(c, s, false);
+    if (rc == PT_OK) keep(0);
+    for (int n = n0 + 1; n < n1 && rc == PT_OK; ++n) {
       pt_report r;
       rc = pt_step(c, &r);
       if (rc == PT_ENOTCONV) rc = PT_OK;
-      for (int f = 0; f < kSegArrays && rc == PT_OK; ++f)
-        if (cudaMemcpyAsync(seg(n - n0, f), src[f], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
-          rc = PT_ECUDA;
+      if (rc == PT_OK) keep(n - n0);
     }
+    if (rc == PT_OK) rc = ckpt_io(c, s + 1, false);
+    if (rc == PT_OK) keep(n1 - n0);
     // adjoint steps n1 .. n0+1, warm-started from the previous step's multipliers
     for (int n = n1; n > n0 && rc == PT_OK; --n) {
-      AdjState u{seg(n - n0, 0), seg(n - n0, 1), seg(n - n0, 2), seg(n - n0, 3), seg(n - n0, 4), seg(n - n0, 5)};
+      const int m = n - n0;
+      const AdjState u{seg(m, 0), seg(m, 1), seg(m, 2), seg(m, 3), seg(m, 4), seg(m, 5)};
+      PT_LAUNCH(c, K_ADJ_PREP, adj_prep(gr, bl, c->stream, b, ac, u, K0, A.prep_for(cur)));
       // convergence: residual max-norms below tol times the largest right-hand side |g|
       cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-      PT_LAUNCH(c, K_ADJ_CARRY, adj_gmax(gr, bl, c->stream, b, gP, gF, gphi, c->red));
+      PT_LAUNCH(c, K_ADJ_CARRY, adj_gmax(gr, bl, c->stream, b, A.gP, A.gF, A.gphi, c->red));
       double gscale = 0.0;
       if (cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                           c->stream) != cudaSuccess ||
@@ -1279,12 +1321,13 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
         ++it;
         const int check = (it % nup) == 0 || it == cap;
         if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-        AdjCellIn ci{Lx, Ly, Lz, lP[cur], lF[cur], lL[cur], gP, gF, gphi, K0};
-        AdjCellOut co{atxx, atyy, atzz, atxy, atxz, atyz, lP[1 - cur], lF[1 - cur], lL[1 - cur],
-                      check ? gth : nullptr};
-        PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, ci, co, c->red, check));
-        AdjFaceIn fi{atxx, atyy, atzz, atxy, atxz, atyz, lP[1 - cur], lL[cur]};
-        PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, u, fi, Lx, Ly, Lz, LRx, LRy, LRz, c->red, check));
+        const AdjCellOut co{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[1 - cur], A.lF[1 - cur],
+                            A.lL[1 - cur], A.mL[1 - cur], check ? A.gth : nullptr, nullptr, nullptr, nullptr};
+        PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(cur, K0), co, c->red, check));
+        const AdjFaceIn fi{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[1 - cur], A.mL[1 - cur],
+                           A.prep.bfx, A.prep.bfy, A.prep.bfz, nullptr, nullptr, nullptr, 1};
+        PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz,
+                                            c->red, check));
         cur = 1 - cur;
         if (check) {
           rc = read_report(c, &last);
@@ -1294,9 +1337,9 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
       }
       total_iters += it;
       if (rc != PT_OK) break;
-      if (gscale == 0.0) cudaMemsetAsync(gth, 0, bytes, c->stream);   // g = 0: lambda = 0
+      if (gscale == 0.0) cudaMemsetAsync(A.gth, 0, bytes, c->stream);   // g = 0: lambda = 0
       // gradient and carry into step n-1 (phi_o = phi^{n-1})
-      AdjCarry ca{lP[cur], lF[cur], lL[cur], gth, seg(n - 1 - n0, 5), grad, gP, gF, gphi};
+      const AdjCarry ca{A.lP[cur], A.lF[cur], A.lL[cur], A.gth, seg(m - 1, 5), grad, A.gP, A.gF, A.gphi};
       PT_LAUNCH(c, K_ADJ_CARRY, adj_carry(gr, bl, c->stream, b, ac, ca));
       if (cudaGetLastError() != cudaSuccess) rc = PT_ECUDA;
     }
@@ -1309,6 +1352,45 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
     rep->status = rc;
   }
   return rc;
+}
+
+int pt_adjoint_apply(pt_ctx* c, const pt_adj_vec* lam, pt_adj_vec* out, void* ws, size_t wbytes) {
+  if (!c || !lam || !out || !ws) return PT_EINVAL;
+  if (!lam->Vx || !lam->Vy || !lam->Vz || !lam->Pt || !lam->Pf || !lam->phi) return PT_EINVAL;
+  if (!out->Vx || !out->Vy || !out->Vz || !out->Pt || !out->Pf || !out->phi) return PT_EINVAL;
+  if (!adjoint_scope_ok(c) || c->nsteps < 1) return PT_EINVAL;
+  if (((uintptr_t)ws & (kAlign - 1)) != 0) return PT_EINVAL;
+  if (wbytes < pt_adjoint_workspace_size(&c->grid, 0, 1)) return PT_ESPACE;
+  int rc = sync_current_to_caller(c);
+  if (rc != PT_OK) return rc;
+  const Box& b = c->box;
+  const dim3 bl = block_dims(), gr = grid_dims(b);
+  const size_t bytes = (size_t)b.n * sizeof(double);
+  AdjArrays A((char*)ws, b);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < kAdjArrays && e == cudaSuccess; ++i) e = cudaMemsetAsync(A.all[i], 0, bytes, c->stream);
+  const double* src[6] = {lam->Vx, lam->Vy, lam->Vz, lam->Pt, lam->Pf, lam->phi};
+  double* dst[6] = {A.Lx, A.Ly, A.Lz, A.lP[0], A.lF[0], A.lL[0]};
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  double* outs[6] = {out->Vx, out->Vy, out->Vz, out->Pt, out->Pf, out->phi};
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMemsetAsync(outs[i], 0, bytes, c->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  const AdjCoef ac = adjoint_coef(c);
+  const double* K0 = (c->lean && c->logk) ? c->K0 : nullptr;
+  const AdjState u{c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0]};
+  PT_LAUNCH(c, K_ADJ_PREP, adj_prep(gr, bl, c->stream, b, ac, u, K0, A.prep_for(0)));
+  // with g = 0 the residual rows of the iteration kernels are J^T lambda itself
+  const AdjCellOut co{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[1], A.lF[1], A.lL[1], A.mL[1],
+                      nullptr, out->Pt, out->Pf, out->phi};
+  PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(0, K0), co, c->red, 0));
+  const AdjFaceIn fi{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[0], A.mL[0],
+                     A.prep.bfx, A.prep.bfy, A.prep.bfz, out->Vx, out->Vy, out->Vz, 0};
+  PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz,
+                                      c->red, 0));
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_status(e);
 }
 
 }  // extern "C"

@@ -129,6 +129,10 @@ class OldFields(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("Pto", "Pfo", "txxo", "tyyo", "tzzo", "txyo", "txzo", "tyzo")]
 
 
+class AdjVec(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("Vx", "Vy", "Vz", "Pt", "Pf", "phi")]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -153,6 +157,7 @@ SIGNATURES = {
     "pt_adjoint_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.c_int32, C.c_int32]),
     "pt_adjoint_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(Report)]),
     "pt_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Report)]),
+    "pt_adjoint_apply": (C.c_int, [C.c_void_p, C.POINTER(AdjVec), C.POINTER(AdjVec), C.c_void_p, C.c_size_t]),
     "pt_batch_workspace_size": (C.c_size_t, [C.c_int32, C.POINTER(Grid), C.POINTER(Num)]),
     "pt_batch_init": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(Grid), C.POINTER(Phys),
                                 C.POINTER(Num), C.POINTER(Fields), C.c_void_p, C.c_size_t, C.c_void_p]),

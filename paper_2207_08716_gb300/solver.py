@@ -151,6 +151,28 @@ class PTSolver:
         self._check(self.lib.pt_adjoint(self.ctx, g.data_ptr(), out.data_ptr(), C.byref(rep)), "pt_adjoint")
         return out[: self.nz, : self.ny, : self.nx].clone(), rep.as_dict()
 
+    def adjoint_apply(self, lam: dict) -> dict:
+        """J_F(u)^T lam at the current fields (pt_adjoint_apply): lam and the result map
+        Vx, Vy, Vz, Pt, Pf, phi (natural shapes; wall-normal faces of lam must be zero)."""
+        keys = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi")
+        need = self.lib.pt_adjoint_workspace_size(C.byref(self._grid), 0, 1)
+        with torch.cuda.device(self.device):
+            ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+            lb = {k: torch.zeros(self.box_shape, dtype=torch.float64, device=self.device) for k in keys}
+            ob = {k: torch.empty(self.box_shape, dtype=torch.float64, device=self.device) for k in keys}
+        for k in keys:
+            self._put(lb[k], k, lam[k])
+        torch.cuda.current_stream(self.device).synchronize()
+        lv = N.AdjVec(*[lb[k].data_ptr() for k in keys])
+        ov = N.AdjVec(*[ob[k].data_ptr() for k in keys])
+        self._check(self.lib.pt_adjoint_apply(self.ctx, C.byref(lv), C.byref(ov), ws.data_ptr(), need),
+                    "pt_adjoint_apply")
+        out = {}
+        for k in keys:
+            sh = natural_shape(k, self.nx, self.ny, self.nz)
+            out[k] = ob[k][: sh[0], : sh[1], : sh[2]].cpu().numpy().copy()
+        return out
+
     # ------------------------------------------------------------- measurement aids
     def profile_begin(self) -> None:
         self._check(self.lib.pt_profile_begin(self.ctx), "pt_profile_begin")

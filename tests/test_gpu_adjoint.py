@@ -6,7 +6,9 @@ with respect to the log-permeability prefactor field (k = k0 e^logk (phi/phi0)^3
 Bars: the GPU gradient equals the dense-LU CPU adjoint to 1e-6 of its largest entry (both
 solve the same transposed systems; the GPU's by pseudo-transient iteration to 1e-12 of the
 right-hand side, its forward to 1e-12); directional derivatives match central differences of
-the GPU forward to 1e-4 relative; checkpoint spacing changes nothing (bitwise).
+the GPU forward to 1e-4 relative along 8 directions; one application of the transposed
+stencils equals the CPU residual's autograd vector-Jacobian product to 1e-12 element by
+element (and <J v, w> = <v, J^T w>); checkpoint spacing changes nothing (bitwise).
 """
 import numpy as np
 import pytest
@@ -89,16 +91,80 @@ def test_gpu_adjoint_matches_finite_differences_32():
     s.close()
     grad, _, _, rep = _gpu_gradient(p, phi, theta, target, N, 2)
     assert np.abs(grad).max() > 0
-    rng = np.random.default_rng(7)
     eps = 1e-3
-    for d in range(2):
+    for d in range(8):
         v = I.gaussian_random_field(phi.shape, seed=10 + d, corr_len=0.1, std=1.0)
         Jp = _gpu_misfit(p, phi, theta + eps * v, target, N)
         Jm = _gpu_misfit(p, phi, theta - eps * v, target, N)
         fd = (Jp - Jm) / (2 * eps)
         ad = float(np.sum(grad * v))
         assert abs(ad - fd) <= 1e-4 * abs(fd), (d, ad, fd, rep)
-    del rng
+
+
+def test_transposed_stencils_equal_cpu_vjp():
+    """pt_adjoint_apply (J_F^T lam on the GPU's transposed stencils) against the CPU adjoint's
+    residual differentiated by autograd: element by element, and the dot-product identity
+    <J v, w> = <v, J^T w> with J v from forward-mode differentiation."""
+    torch = _torch()
+    from oracle import adjoint as A
+    from paper_2207_08716_gb300.solver import PTSolver
+    dims = (13, 10, 9)
+    p = _params(dims, tol=1e-9)
+    nx, ny, nz = dims
+    phi = I.gaussian_porosity(p, centres=((0.4, 0.55, 0.5),), width=0.2)
+    theta = I.gaussian_random_field(phi.shape, seed=5, std=0.5)
+    s = PTSolver(p, phi, logk=theta)
+    s.step()
+    u = {k: A._t(s.get(k)) for k in A.U_KEYS}
+    rng = np.random.default_rng(11)
+    shapes = I.field_shapes(nx, ny, nz)
+
+    def rand_vec():
+        v = {k: rng.standard_normal(shapes.get(k, shapes["centre"])) for k in A.U_KEYS}
+        v["Vx"][:, :, 0] = v["Vx"][:, :, -1] = 0.0
+        v["Vy"][:, 0, :] = v["Vy"][:, -1, :] = 0.0
+        v["Vz"][0] = v["Vz"][-1] = 0.0
+        return v
+
+    w = rand_vec()
+    got = s.adjoint_apply(w)
+    old = dict(Pto=torch.zeros_like(u["Pt"]), Pfo=torch.zeros_like(u["Pt"]), Lo=torch.zeros_like(u["Pt"]))
+    uu = {k: v.clone().requires_grad_(True) for k, v in u.items()}
+    F = A.residual(p, uu, old, A._t(theta))
+    wi = {"Fx": w["Vx"][:, :, 1:-1], "Fy": w["Vy"][:, 1:-1, :], "Fz": w["Vz"][1:-1], "Fpt": w["Pt"],
+          "Fpf": w["Pf"], "FL": w["phi"]}
+    dot = sum((F[k] * A._t(wi[k])).sum() for k in A.F_KEYS)
+    grads = torch.autograd.grad(dot, [uu[k] for k in A.U_KEYS])
+    ref = dict(zip(A.U_KEYS, (g.numpy() for g in grads)))
+    inner = {"Vx": (slice(None), slice(None), slice(1, -1)), "Vy": (slice(None), slice(1, -1), slice(None)),
+             "Vz": (slice(1, -1),)}
+    for k in A.U_KEYS:
+        sl = inner.get(k, (slice(None),))
+        a, r = got[k][sl], ref[k][sl]
+        err = np.abs(a - r).max() / max(np.abs(r).max(), 1e-300)
+        assert err <= 1e-12, (k, err)
+    for k, sl in inner.items():                       # wall faces are not unknowns: zero
+        full = np.zeros_like(got[k])
+        full[sl] = got[k][sl]
+        np.testing.assert_array_equal(got[k], full)
+    # dot-product test with a forward-mode J v
+    v = rand_vec()
+
+    def Fu(*xs):
+        d = residual_in(xs)
+        return tuple(d[k] for k in A.F_KEYS)
+
+    def residual_in(xs):
+        return A.residual(p, dict(zip(A.U_KEYS, xs)), old, A._t(theta))
+
+    _, Jv = torch.autograd.functional.jvp(Fu, tuple(u[k] for k in A.U_KEYS), tuple(A._t(v[k]) for k in A.U_KEYS))
+    lhs = sum(float((Jv[i] * A._t(wi[k])).sum()) for i, k in enumerate(A.F_KEYS))
+    vi = {k: v[k][inner.get(k, (slice(None),))] for k in A.U_KEYS}
+    gi = {k: got[k][inner.get(k, (slice(None),))] for k in A.U_KEYS}
+    rhs = sum(float(np.sum(vi[k] * gi[k])) for k in A.U_KEYS)
+    scale = sum(float(np.sum(np.abs(vi[k] * gi[k]))) for k in A.U_KEYS)
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+    s.close()
 
 
 def test_checkpoint_spacing_changes_nothing():
