@@ -30,9 +30,6 @@ from paper_2207_08716_gb300 import measure as M  # noqa: E402
 METRIC = "T_eff GB/s (% of HBM peak) and PT iter/s at 511^3: FP64 vs FP32 vs batched"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6800.0
-# FP64 FMA throughput measured on this machine's GB300 with a register-resident DFMA loop
-# (8 independent chains per thread, 152 x 8 blocks of 256 threads; FMA = 2 flops).
-FP64_PEAK_TFLOPS = 1.005
 
 # Algorithmic bytes per cell and launch of each kernel of the step-by-step FP64 path: the
 # arrays it must read and write once (8 B each), counted from its arguments.
@@ -44,21 +41,26 @@ KERNEL_BYTES_PER_CELL = {
     # faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
     "k_lean_cells": 36 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
     "k_lean_begin": 11 * 8,
-    # mixed precision, FP32 correction iterations: cells reads 17 arrays (3 dV, dPt, dPf, cc, k,
-    # idtp, iden_pt, idtf, iden_pf, r_pt, r_pf, cm2, 3 em2) and writes 8 (dPt, dPf, 6 stresses);
-    # faces reads 19 (6 stresses, dPt, 3 dtv, 3 r_F, 3 R, 3 dV) and writes 6 (3 R, 3 dV)
-    "k_corr_cells": 25 * 4, "k_corr_faces": 25 * 4,
+    # mixed precision, one fused FP32 correction iteration: reads 18 arrays (3 dV, dPt, dPf, cc,
+    # k, iden_pt, iden_pf, r_pt, r_pf, mu, 3 r_F, 3 R) and writes 8 (3 dV, dPt, dPf, 3 R)
+    "k_corr": 26 * 4,
+    # adjoint PT iteration: cells reads 26 arrays and writes 10, faces reads 17 and writes 6
+    "k_adj_cells": 36 * 8, "k_adj_faces": 23 * 8,
 }
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2}
-# FP64 flops per cell and launch (DFMA x 2 + DADD + DMUL thread instructions) from one ncu
-# capture of the kernel on the 191^3 case (profiles/k_lean_fp64_191.md); a kernel missing here
-# has no current count.
-KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 211.0, "k_lean_faces": 52.7, "k_centres": 237.0}
+# FP64 thread instructions (DFMA + DADD + DMUL) and flops (DFMA x 2 + DADD + DMUL) per cell and
+# launch from one ncu capture of the kernel (profiles/k_lean_fp64_191.md, k_adj_cells_95.md,
+# k_centres_fp64_stepwise_191.md); a kernel missing here has no current count.
+KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 123.7, "k_adj_cells": 76.5, "k_centres": 152.0}
+KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 183.5, "k_adj_cells": 115.2, "k_centres": 237.0}
+# The FP64 pipe issues at most 304 thread-instructions per GPU clock (2 per SM; ncu's
+# sm__inst_executed_pipe_fp64 peak on this machine's GB300), i.e. 629 G/s at 2.07 GHz.
+FP64_PIPE_INST_PER_CLK = 304.0
 # FP32 kernels are bound by HBM (their FP32 work is far below the FP32 pipe's rate).
 # DRAM bytes per cell and launch (dram__bytes_read.sum + dram__bytes_write.sum) from the same
 # captures; the 191^3 case's per-cell figure scales with the cells of a launch.
-KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 287.0, "k_lean_faces": 181.0, "k_centres": 150.6,
-                           "k_corr_cells": 99.5, "k_corr_faces": 98.7}
+KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 287.2, "k_lean_faces": 181.0, "k_centres": 150.6,
+                           "k_adj_cells": 270.5}
 
 
 def parse():
@@ -85,7 +87,7 @@ def parse():
                          "backward wall time, cost multiple, optional finite-difference check")
     ap.add_argument("--adjoint-n", type=int, default=127)
     ap.add_argument("--adjoint-steps", type=int, default=20)
-    ap.add_argument("--adjoint-ckpt", type=int, default=5)
+    ap.add_argument("--adjoint-ckpt", default="5,1", help="checkpoint spacings to measure (comma list)")
     ap.add_argument("--adjoint-fd", type=int, default=0, help="finite-difference directions to check")
     ap.add_argument("--batched-converge", action="store_true",
                     help="run one step of the batched ensemble to convergence and report p50/p99 "
@@ -166,12 +168,15 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def roofline(kernels: dict, ncell: int) -> dict:
-    """Roofline of the dominant kernel (largest device time) from the live per-kernel events."""
+def roofline(kernels: dict, ncell: int, sm_mhz: float | None = None) -> dict:
+    """Roofline of the dominant kernel (largest device time) from the live per-kernel events.
+    FP64 kernels issue-bound on the FP64 pipe report FP64 thread-instructions per second
+    against the pipe's capacity (304 per clock at the SM clock measured during the run)."""
     hbm, hbm_kind = peaks()
     name, (nl, ms) = max(kernels.items(), key=lambda kv: kv[1][1])
     per_launch_s = ms / 1e3 / nl
     bytes_launch = KERNEL_BYTES_PER_CELL.get(name, 0) * ncell
+    inst_cell = KERNEL_FP64_INST_PER_CELL.get(name)
     flops_cell = KERNEL_FP64_FLOPS_PER_CELL.get(name)
     traffic_cell = KERNEL_TRAFFIC_PER_CELL.get(name)
     gbs = bytes_launch / per_launch_s / 1e9
@@ -179,13 +184,17 @@ def roofline(kernels: dict, ncell: int) -> dict:
             "frac": gbs / hbm, "peak_source": f"{hbm_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": traffic_cell * ncell if traffic_cell else None,
             "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": per_launch_s * 1e3}
-    if flops_cell:
-        tf = flops_cell * ncell / per_launch_s / 1e12
-        if tf / FP64_PEAK_TFLOPS > roof["frac"]:
-            roof.update(bound="alu", achieved=tf, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=tf / FP64_PEAK_TFLOPS,
-                        peak_source="measured FP64 DFMA throughput of this pool's GB300 (FP64 pipe)")
-        roof["fp64_tflops"] = tf
+    if inst_cell:
+        clk = (sm_mhz or 2070.0) * 1e6
+        peak = FP64_PIPE_INST_PER_CLK * clk / 1e9
+        ginst = inst_cell * ncell / per_launch_s / 1e9
+        if ginst / peak > roof["frac"]:
+            roof.update(bound="alu", achieved=ginst, peak=peak, unit="G FP64 inst/s", frac=ginst / peak,
+                        peak_source=f"FP64 pipe capacity, {FP64_PIPE_INST_PER_CLK:.0f} thread-instructions "
+                                    f"per clock at the measured {clk / 1e6:.0f} MHz (ncu pipe peak)")
+        roof["fp64_inst_per_cell"] = inst_cell
+        if flops_cell:
+            roof["fp64_tflops"] = flops_cell * ncell / per_launch_s / 1e12
         roof["hbm_gbs"] = gbs
     return roof
 
@@ -241,7 +250,8 @@ def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_
     out = {"precision": precision, "value": value, "unit": "GB/s", "p_bytes": pbytes,
            "ms_per_step": t / steps * 1e3, "iters_per_step": iters, "it_per_s": world * total_iters / t,
            "t_it_ms": t / total_iters * 1e3, "teff_frac_of_hbm": value / world / peaks()[0],
-           "roofline": roofline(kernels, ncell), "gpu_launches": launches, "clocks": clk,
+           "roofline": roofline(kernels, ncell, clk.get("sm_mhz") if clk else None),
+           "gpu_launches": launches, "clocks": clk,
            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()}}
     if e2e_steps > 0:
         host = s.host_mirror()
@@ -319,13 +329,15 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
 def measure_adjoint(args, dev) -> dict:
     """Gradient of J = sum (phi^N - phi_target)^2 w.r.t. the log-permeability field: N converged
     steps recorded with checkpoints, then the checkpointed reverse sweep (recompute + adjoint PT
-    per step). theta and the target's theta are Gaussian random fields (corr. length 0.1, std 0.5,
-    seeds 1 and 2); finite-difference directions use seeds 10, 11, ..."""
+    per step), once per checkpoint spacing. theta and the target's theta are Gaussian random
+    fields (corr. length 0.1, std 0.5, seeds 1 and 2); finite-difference directions use seeds
+    10, 11, ..."""
     import torch
     from paper_2207_08716_gb300.adjoint import adjoint_scope
     from paper_2207_08716_gb300.solver import PTSolver
 
-    n, N, every = args.adjoint_n, args.adjoint_steps, args.adjoint_ckpt
+    n, N = args.adjoint_n, args.adjoint_steps
+    spacings = [int(x) for x in str(args.adjoint_ckpt).split(",") if x]
     p = adjoint_scope(I.c1_params(n))
     p["precision"] = PRECISIONS["fp64"]
     p["max_iter"] = 200000
@@ -343,42 +355,53 @@ def measure_adjoint(args, dev) -> dict:
         return out, its
 
     clocks = M.ClockSampler(dev.index or 0)
+    t0 = time.perf_counter()
     target, _ = run_forward(theta_t)
-    s = PTSolver(p, phi, logk=theta, device=dev)
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    t0 = time.perf_counter()
-    reps = s.adjoint_forward(N, every)
-    t_fwd = time.perf_counter() - t0
-    phiN = s.get("phi")
-    dJ = 2.0 * (phiN - target)
-    launches0 = s.launch_count()
-    s.profile_begin()
-    t0 = time.perf_counter()
-    grad, rep = s.adjoint(dJ)
-    torch.cuda.synchronize(dev)
-    t_bwd = time.perf_counter() - t0
-    kernels = s.profile_end()
-    clk = clocks.stop()
-    launches = s.launch_count() - launches0
-    grad = grad.cpu().numpy()
-    fwd_iters = sum(r["iters"] for r in reps)
-    adj_ms = sum(kernels.get(k, (0, 0.0))[1] for k in ("k_adj_cells", "k_adj_faces"))
+    t_target = time.perf_counter() - t0
     ncell = n ** 3
-    out = {"n": n, "steps": N, "ckpt_every": every, "forward_s": t_fwd, "backward_s": t_bwd,
-           "cost_multiple": t_bwd / t_fwd, "forward_pt_iters": fwd_iters, "adjoint_pt_iters": rep["iters"],
-           "adjoint_ms_per_iter": adj_ms / max(rep["iters"], 1),
-           "forward_statuses": sorted({r["status"] for r in reps}), "adjoint_status": rep["status"],
-           "J": float(np.sum((phiN - target) ** 2)), "grad_max": float(np.abs(grad).max()),
-           "gpu_launches": launches, "clocks": clk,
-           "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()}}
-    # algorithmic bytes of one adjoint PT iteration: cells reads 16 arrays (3 lambda_V, 3 centre
-    # multipliers, 3 right-hand sides, K0, V (3), Pt, Pf, phi) and writes 9 (6 adjoint stresses, 3
-    # multipliers); faces reads 15 (6 stresses, lambda_P, lambda_L, phi, 3 lambda_V, 3 R) and
-    # writes 6 (3 R, 3 lambda_V)
-    if adj_ms > 0:
-        out["adjoint_gbs"] = (25 + 21) * 8 * ncell * rep["iters"] / (adj_ms / 1e3) / 1e9
-    s.close()
+    runs, grad = [], None
+    clocks.start()
+    for every in spacings:
+        s = PTSolver(p, phi, logk=theta, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        reps = s.adjoint_forward(N, every)
+        t_fwd = time.perf_counter() - t0
+        phiN = s.get("phi")
+        launches0 = s.launch_count()
+        s.profile_begin()
+        t0 = time.perf_counter()
+        g, rep = s.adjoint(2.0 * (phiN - target))
+        torch.cuda.synchronize(dev)
+        t_bwd = time.perf_counter() - t0
+        kernels = s.profile_end()
+        launches = s.launch_count() - launches0
+        g = g.cpu().numpy()
+        adj_ms = sum(kernels.get(k, (0, 0.0))[1] for k in ("k_adj_cells", "k_adj_faces"))
+        r = {"ckpt_every": every, "forward_s": t_fwd, "backward_s": t_bwd, "cost_multiple": t_bwd / t_fwd,
+             "forward_pt_iters": sum(x["iters"] for x in reps), "adjoint_pt_iters": rep["iters"],
+             "adjoint_ms_per_iter": adj_ms / max(rep["iters"], 1),
+             "forward_statuses": sorted({x["status"] for x in reps}), "adjoint_status": rep["status"],
+             "J": float(np.sum((phiN - target) ** 2)), "grad_max": float(np.abs(g).max()),
+             "gpu_launches": launches,
+             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()}}
+        # algorithmic bytes of one adjoint PT iteration: cells reads 26 arrays (3 lambda_V, 4 centre
+        # multipliers, 3 right-hand sides, phi, 1/(1-phi), 6 Darcy face factors, 5 row factors, V (3))
+        # and writes 10 (6 adjoint stresses, 4 multipliers); faces reads 17 (6 stresses, lambda_P,
+        # lambda_L/(1-phi), 3 advection factors, 3 lambda_V, 3 R) and writes 6 (3 R, 3 lambda_V)
+        if adj_ms > 0:
+            r["adjoint_gbs"] = (36 + 23) * 8 * ncell * rep["iters"] / (adj_ms / 1e3) / 1e9
+        if grad is not None:
+            r["max_rel_diff_vs_first"] = float(np.abs(g - grad).max() / np.abs(grad).max())
+        grad = g if grad is None else grad
+        runs.append(r)
+        s.close()
+    clk = clocks.stop()
+    for r in runs:
+        adj = {k: (v["launches"], v["ms"]) for k, v in r["kernels"].items() if k in ("k_adj_cells", "k_adj_faces")}
+        if adj:
+            r["roofline"] = roofline(adj, ncell, clk.get("sm_mhz") if clk else None)
+    out = {"n": n, "steps": N, "target_forward_s": t_target, "runs": runs, "clocks": clk}
     if args.adjoint_fd > 0:
         eps = 1e-6 * float(np.abs(theta).max())
         checks = []

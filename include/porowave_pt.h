@@ -268,6 +268,33 @@ int pt_batch_config(const pt_batch *batch, int32_t *tile_x, int32_t *tile_y,
                     int32_t *iters_per_graph);
 void pt_batch_destroy(pt_batch *batch);
 
+/* ---- Sub-domain (halo-exchange) form ---------------------------------------
+ * The distributed-memory decomposition of the thesis (Art. 1 Section 2.2; Art. 2: one
+ * sub-domain per GPU, halos exchanged every iteration), run on one GPU: the grid is split into
+ * parts[0] x parts[1] x parts[2] parts of near-equal size (at least 2 cells per part and
+ * direction), each an FP64-lean instance of the batched engine with its own padded box and a
+ * one-cell halo on every side that has a neighbour. After every PT iteration the halos of V,
+ * Pt, Pf, phi (with 1/(1-phi) and k) and after every Picard update those of mu, eta are copied
+ * from the owning parts; residual norms count owned points only; all parts stop together and
+ * share one stress sub-step from the largest mu of the whole grid. The result is bitwise that
+ * of the undivided grid run by the same kernels (parts = {1, 1, 1}).
+ * pt_dd_init copies the caller's global fields (device, box layout of `grid`) into the parts
+ * (workspace: pt_dd_workspace_size bytes of device memory, 256-byte aligned; precision must be
+ * PT_FP64; viscosities are initialised from phi as by pt_init); pt_dd_step advances one
+ * physical step to convergence (rep: iterations and the global norms); pt_dd_gather writes the
+ * parts' owned values back into the global fields. Errors: PT_EINVAL (sizes, parts, precision),
+ * PT_ESPACE, PT_ECUDA; pt_dd_step returns PT_ENOTCONV / PT_ENAN as pt_step does. */
+typedef struct pt_dd pt_dd;
+size_t pt_dd_workspace_size(const pt_grid *grid, const pt_num *num, const int32_t parts[3]);
+int pt_dd_init(pt_dd **dd, const pt_grid *grid, const pt_phys *phys, const pt_num *num,
+               const pt_fields *fields, const int32_t parts[3], void *workspace, size_t bytes,
+               void *stream);
+int pt_dd_step(pt_dd *dd, pt_report *rep);
+int pt_dd_gather(pt_dd *dd);
+/* Number of parts and the tuned configuration of the underlying batched engine. */
+int pt_dd_config(const pt_dd *dd, int32_t *nparts, int32_t *tile_x, int32_t *tile_y, int32_t *iters_per_graph);
+void pt_dd_destroy(pt_dd *dd);
+
 /* Release the context (not the caller's memory). */
 void pt_destroy(pt_ctx *ctx);
 

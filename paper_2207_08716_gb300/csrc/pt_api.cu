@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <array>
 #include <vector>
 
 #include "../../include/porowave_pt.h"
@@ -21,6 +22,7 @@
 #include "pt_mixed.cuh"
 #include "pt_batch.cuh"
 #include "pt_adjoint.cuh"
+#include "pt_dd.cuh"
 
 using namespace pt;
 
@@ -30,7 +32,7 @@ constexpr size_t kAlign = 256;
 constexpr int kPitchMultiple = 16;
 constexpr int kRefArrays = 23;   // step-by-step path
 constexpr int kLeanArrays = 23;  // extra arrays of the FP64-lean path
-constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
+constexpr int kMixArrays = 23;   // FP32 arrays of the mixed-precision path
 // Default relative drop at which the inner FP32 solves of the mixed-precision path stop. The
 // outer loop's convergence is bound by the log-space Picard relaxation of mu and eta (one
 // update per outer iteration), not by the inner accuracy: a drop of 0.3 per inner solve needs
@@ -65,6 +67,8 @@ struct pt_ctx {
   Box box;
   Coef coef;
   pt_grid grid;
+  pt_grid metric;   // grid whose spacing (and nz) define the coefficients: `grid`, or for a part
+                    // of a decomposed grid the whole grid
   pt_phys phys;
   pt_num num;
   cudaStream_t stream;
@@ -86,10 +90,8 @@ struct pt_ctx {
   LeanCoef<double> lcoef;
   // mixed-precision path (precision PT_FP32): FP32 correction problem
   bool mixed;
-  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_iden_pt, *m_idtf, *m_iden_pf;
-  float *m_cm2, *m_em2_xy, *m_em2_xz, *m_em2_yz, *m_dtv_x, *m_dtv_y, *m_dtv_z;
-  float *m_dVx, *m_dVy, *m_dVz, *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
-  float *m_txx, *m_tyy, *m_tzz, *m_txy, *m_txz, *m_tyz;
+  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_iden_pt, *m_iden_pf, *m_mu;
+  float *m_dVx[2], *m_dVy[2], *m_dVz[2], *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
   CorrCoef<float> ccoef;
   // adjoint recording (pt_adjoint_forward / pt_adjoint)
   char* adj_ws;
@@ -115,14 +117,14 @@ namespace {
 
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
-                K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_CELLS, K_CORR_FACES,
+                K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR,
                 K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
                                            "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0",
                                            "k_mix_prepare", "k_mix_res_faces", "k_mix_coef",
-                                           "k_corr_cells", "k_corr_faces", "k_mix_update",
+                                           "k_corr", "k_mix_update",
                                            "k_adj_prep", "k_adj_cells", "k_adj_faces", "k_adj_carry"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
@@ -171,7 +173,7 @@ void fill_lean_coef(pt_ctx* c);
 void fill_corr_coef(pt_ctx* c);
 
 void fill_coef(pt_ctx* c) {
-  const pt_grid& g = c->grid;
+  const pt_grid& g = c->metric;
   const pt_phys& p = c->phys;
   const pt_num& n = c->num;
   Coef& k = c->coef;
@@ -219,7 +221,7 @@ void fill_coef(pt_ctx* c) {
 
 void fill_lean_coef(pt_ctx* c) {
   const Coef& k = c->coef;
-  const pt_grid& g = c->grid;
+  const pt_grid& g = c->metric;
   const pt_phys& p = c->phys;
   LeanCoef<double>& L = c->lcoef;
   const double dz = g.lz / g.nz;
@@ -263,6 +265,8 @@ void fill_corr_coef(pt_ctx* c) {
   f.beta_n = (float)k.beta_n;
   f.rrho_i = (float)k.rrho_i;
   f.damp_x = (float)k.damp_x; f.damp_y = (float)k.damp_y; f.damp_z = (float)k.damp_z;
+  f.rG = (float)k.rGdtS;
+  f.hdtv = (float)(0.5 * k.dtauv_fac);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
@@ -391,8 +395,8 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   PT_LAUNCH(c, K_PERM, k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[a], c->logk, c->perm, c->rog));
   MixPrepIn pin{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->mu, c->eta, c->perm, c->Pto,
                 c->Pfo, c->txxo, c->tyyo, c->tzzo};
-  MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_idtp,
-                  c->m_iden_pt, c->m_idtf, c->m_iden_pf};
+  MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_iden_pt,
+                  c->m_iden_pf};
   PT_LAUNCH(c, K_MIX_PREP, mix_prepare(gr, bl, c->stream, b, k, pin, pout, c->red));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
@@ -412,26 +416,23 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   }
   const double target = (c->num.inner_rtol > 0 ? c->num.inner_rtol : kInnerRtol) * report_max(outer);
   // (iii) FP32 PT on the correction, from delta = 0, R = 0
-  MixCoefOut mco{c->m_cm2, c->m_em2_xy, c->m_em2_xz, c->m_em2_yz, c->m_dtv_x, c->m_dtv_y, c->m_dtv_z};
+  MixCoefOut mco{c->m_mu};
   PT_LAUNCH(c, K_MIX_COEF, mix_coef(gr, bl, c->stream, b, k, c->mu, mco));
   const size_t fb = (size_t)b.n * sizeof(float);
-  float* zero[] = {c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[0], c->m_dPf[0], c->m_Rx, c->m_Ry, c->m_Rz};
+  float* zero[] = {c->m_dVx[0], c->m_dVy[0], c->m_dVz[0], c->m_dVx[1], c->m_dVy[1], c->m_dVz[1],
+                   c->m_dPt[0], c->m_dPf[0], c->m_Rx, c->m_Ry, c->m_Rz};
   for (float* z : zero) cudaMemsetAsync(z, 0, fb, c->stream);
   int d = 0;
   const int nup = c->num.nup;
   for (int it = 1; it <= n_in; ++it) {
     const int check = early_exit && (it % nup) == 0;
     if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-    CorrCellIn<float> ci{c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d], c->m_cc, c->m_perm,
-                         c->m_idtp, c->m_iden_pt, c->m_idtf, c->m_iden_pf, c->m_rpt, c->m_rpf,
-                         c->m_cm2, c->m_em2_xy, c->m_em2_xz, c->m_em2_yz};
-    CorrCellOut<float> co{c->m_dPt[1 - d], c->m_dPf[1 - d], c->m_txx, c->m_tyy, c->m_tzz, c->m_txy,
-                          c->m_txz, c->m_tyz};
-    PT_LAUNCH(c, K_CORR_CELLS, corr_cells<float>(gr, bl, c->stream, b, c->ccoef, ci, co, c->red, check));
-    CorrFaceIn<float> fi{c->m_txx, c->m_tyy, c->m_tzz, c->m_txy, c->m_txz, c->m_tyz, c->m_dPt[1 - d],
-                         c->m_dtv_x, c->m_dtv_y, c->m_dtv_z, c->m_rfx, c->m_rfy, c->m_rfz};
-    PT_LAUNCH(c, K_CORR_FACES, corr_faces<float>(gr, bl, c->stream, b, c->ccoef, fi, c->m_dVx, c->m_dVy,
-                                                 c->m_dVz, c->m_Rx, c->m_Ry, c->m_Rz, c->red, check));
+    const CorrIn<float> ci{c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d], c->m_dPf[d], c->m_cc,
+                           c->m_perm, c->m_iden_pt, c->m_iden_pf, c->m_rpt, c->m_rpf, c->m_mu,
+                           c->m_rfx, c->m_rfy, c->m_rfz};
+    const CorrOut<float> co{c->m_dVx[1 - d], c->m_dVy[1 - d], c->m_dVz[1 - d], c->m_dPt[1 - d], c->m_dPf[1 - d]};
+    PT_LAUNCH(c, K_CORR, corr_iter<float>(gr, bl, c->stream, b, c->ccoef, ci, co, c->m_Rx, c->m_Ry, c->m_Rz,
+                                          c->red, check));
     d = 1 - d;
     *inner_done = it;
     if (check) {
@@ -442,7 +443,8 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
     }
   }
   // (iv) u <- u + delta in FP64, then the FP64 porosity time integration (Eq. 22, log space)
-  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d]};
+  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d],
+               c->m_dPf[d]};
   PT_LAUNCH(c, K_MIX_UPDATE, mix_update(gr, bl, c->stream, b, mu));
   PT_LAUNCH(c, K_POROSITY,
             k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[a], c->Pf[a],
@@ -452,6 +454,58 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   cudaMemcpyAsync(c->Pf[1 - a], c->Pf[a], (size_t)b.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   c->cur = 1 - a;
   return cuda_status(cudaGetLastError());
+}
+
+// Step begin in three parts (a decomposed grid takes the largest mu over all its parts):
+// old-state snapshot and the largest mu into the reduction block; read it; stress sub-step,
+// old-stress refresh and coefficients from it.
+int step_begin_launch(pt_ctx* c) {
+  int rc = sync_current_to_caller(c);
+  if (rc != PT_OK) return rc;
+  const Box& b = c->box;
+  cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  if (c->lean) {
+    LeanBeginIn<double> bi{c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->logk ? c->K0 : nullptr};
+    LeanBeginOut<double> bo{c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->lw[0], c->lperm[0]};
+    PT_LAUNCH(c, K_LEAN_BEGIN, lean_begin<double>(grid_dims(b), block_dims(), c->stream, b, c->lcoef, bi, bo, c->red));
+  } else {
+    PT_LAUNCH(c, K_BEGIN, k_begin_step<<<grid_dims(b), block_dims(), 0, c->stream>>>(
+                               b, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->Pto, c->Pfo, c->Lo, c->red));
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+int step_begin_mumax(pt_ctx* c, double* mu_max) {
+  cudaError_t e =
+      cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  std::memcpy(mu_max, &c->h_red[RED_MUMAX], sizeof *mu_max);
+  return PT_OK;
+}
+
+int step_begin_finish(pt_ctx* c, double mu_max) {
+  if (!std::isfinite(mu_max) || !(mu_max > 0)) return PT_ENAN;
+  const Box& b = c->box;
+  cudaError_t e = cudaSuccess;
+  // stress sub-step of the appendix two-phase script: the largest xi = mu / (G dtS) is xsi_w;
+  // the old stresses are refreshed at the first step and when dt_cum reaches dtS
+  c->dtS = mu_max / (c->phys.G * c->num.xsi_w);
+  if (c->nsteps == 0 || c->dt_cum >= c->dtS) {
+    const size_t bytes = (size_t)b.n * sizeof(double);
+    const double* src[6] = {c->txx, c->tyy, c->tzz, c->txy, c->txz, c->tyz};
+    double* dst[6] = {c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
+    for (int s = 0; s < 6 && e == cudaSuccess; ++s)
+      e = cudaMemcpyAsync(dst[s], src[s], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    c->dt_cum = 0.0;
+  }
+  c->nsteps += 1;
+  fill_coef(c);
+  if (c->lean && e == cudaSuccess) {
+    launch_lean_coef(c);
+    e = cudaGetLastError();
+  }
+  return cuda_status(e);
 }
 
 }  // namespace
@@ -503,6 +557,7 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   pt_ctx* c = new (std::nothrow) pt_ctx();
   if (!c) return PT_ECUDA;
   c->grid = *grid;
+  c->metric = *grid;
   c->phys = *phys;
   c->num = *num;
   c->box = make_box(grid);
@@ -530,11 +585,9 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   if (c->mixed) {
     const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
     float** fslots[kMixArrays] = {
-        &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_idtp,
-        &c->m_iden_pt, &c->m_idtf, &c->m_iden_pf, &c->m_cm2, &c->m_em2_xy, &c->m_em2_xz, &c->m_em2_yz,
-        &c->m_dtv_x, &c->m_dtv_y, &c->m_dtv_z, &c->m_dVx, &c->m_dVy, &c->m_dVz, &c->m_dPt[0], &c->m_dPt[1],
-        &c->m_dPf[0], &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz, &c->m_txx, &c->m_tyy, &c->m_tzz,
-        &c->m_txy, &c->m_txz, &c->m_tyz};
+        &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_iden_pt,
+        &c->m_iden_pf, &c->m_mu, &c->m_dVx[0], &c->m_dVy[0], &c->m_dVz[0], &c->m_dVx[1], &c->m_dVy[1],
+        &c->m_dVz[1], &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0], &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz};
     for (int s = 0; s < kMixArrays; ++s) *fslots[s] = (float*)(wend + s * fstride);
     wend += kMixArrays * fstride;
   }
@@ -577,44 +630,11 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
 
 int pt_step_begin(pt_ctx* c) {
   if (!c) return PT_EINVAL;
-  int rc = sync_current_to_caller(c);
-  if (rc != PT_OK) return rc;
-  const Box& b = c->box;
-  cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-  if (c->lean) {
-    LeanBeginIn<double> bi{c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->logk ? c->K0 : nullptr};
-    LeanBeginOut<double> bo{c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->lw[0], c->lperm[0]};
-    PT_LAUNCH(c, K_LEAN_BEGIN, lean_begin<double>(grid_dims(b), block_dims(), c->stream, b, c->lcoef, bi, bo, c->red));
-  } else {
-    PT_LAUNCH(c, K_BEGIN, k_begin_step<<<grid_dims(b), block_dims(), 0, c->stream>>>(
-                               b, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->Pto, c->Pfo, c->Lo, c->red));
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return PT_ECUDA;
-  double mu_max;
-  std::memcpy(&mu_max, &c->h_red[RED_MUMAX], sizeof mu_max);
-  if (!std::isfinite(mu_max) || !(mu_max > 0)) return PT_ENAN;
-  // stress sub-step of the appendix two-phase script: the largest xi = mu / (G dtS) is xsi_w;
-  // the old stresses are refreshed at the first step and when dt_cum reaches dtS
-  c->dtS = mu_max / (c->phys.G * c->num.xsi_w);
-  if (c->nsteps == 0 || c->dt_cum >= c->dtS) {
-    const size_t bytes = (size_t)b.n * sizeof(double);
-    const double* src[6] = {c->txx, c->tyy, c->tzz, c->txy, c->txz, c->tyz};
-    double* dst[6] = {c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
-    for (int s = 0; s < 6 && e == cudaSuccess; ++s)
-      e = cudaMemcpyAsync(dst[s], src[s], bytes, cudaMemcpyDeviceToDevice, c->stream);
-    c->dt_cum = 0.0;
-  }
-  c->nsteps += 1;
-  fill_coef(c);
-  if (c->lean && e == cudaSuccess) {
-    launch_lean_coef(c);
-    e = cudaGetLastError();
-  }
-  return cuda_status(e);
+  int rc = step_begin_launch(c);
+  double mu_max = 0.0;
+  if (rc == PT_OK) rc = step_begin_mumax(c, &mu_max);
+  if (rc == PT_OK) rc = step_begin_finish(c, mu_max);
+  return rc;
 }
 
 int pt_iterate(pt_ctx* c, int32_t it0, int32_t niter, pt_report* rep) {
@@ -821,6 +841,12 @@ struct pt_batch {
   int grid;
   cudaGraphExec_t exec;
   int exec_bx, exec_by, exec_ipg;
+  // parts of one decomposed grid (pt_dd): coupled convergence, halo exchange, ownership
+  int coupled;
+  const HaloSlab* d_slabs;
+  int nslabs, slab_elems;
+  DDTables tables;
+  std::vector<std::array<int, 6>> own;   // per instance: own_lo[3], own_hi[3]
 };
 
 namespace {
@@ -855,7 +881,11 @@ void fill_batch_inst(pt_batch* B, int m, long long base) {
   I.Vx = c->Vx; I.Vy = c->Vy; I.Vz = c->Vz;
   I.Rx = c->Rx; I.Ry = c->Ry; I.Rz = c->Rz;
   I.mu = c->mu; I.eta = c->eta;
-  I.red = c->red;
+  I.red = B->coupled ? B->ctx[0]->red : c->red;   // parts of one grid share the norms
+  for (int d = 0; d < 3; ++d) {
+    I.own_lo[d] = B->own.empty() ? 0 : B->own[m][d];
+    I.own_hi[d] = B->own.empty() ? (d == 0 ? c->box.nx : d == 1 ? c->box.ny : c->box.nz) : B->own[m][3 + d];
+  }
   I.tol = c->num.tol;
   I.max_iter = c->num.max_iter;
   I.gx = (c->box.nx + 1 + B->bx - 1) / B->bx;
@@ -887,10 +917,14 @@ void record_batch_iterations(pt_batch* B, int ipg) {
     const int check = (it % B->nup) == 0;
     batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_CELLS, B->d_inst, B->d_st, B->ninst, B->ntiles, a, check);
     batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_FACES, B->d_inst, B->d_st, B->ninst, B->ntiles, a, check);
+    if (B->coupled)
+      dd_exchange(B->stream, B->d_inst, B->d_st, B->d_slabs, B->nslabs, B->slab_elems, B->tables, a, DD_STATE);
     if (check) {
       batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_PICARD, B->d_inst, B->d_st, B->ninst, B->ntiles, a, 1);
+      if (B->coupled)
+        dd_exchange(B->stream, B->d_inst, B->d_st, B->d_slabs, B->nslabs, B->slab_elems, B->tables, a, DD_VISC);
       batch_phase(B->bx, B->by, B->grid, B->stream, BATCH_COEF, B->d_inst, B->d_st, B->ninst, B->ntiles, a, 0);
-      batch_converge(B->stream, B->d_inst, B->d_st, B->ninst, B->nup);
+      batch_converge(B->stream, B->d_inst, B->d_st, B->ninst, B->nup, B->coupled);
     }
   }
 }
@@ -974,6 +1008,10 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   B->ipg = 2 * B->nup;
   B->tuned = false;
   B->exec = nullptr;
+  B->coupled = 0;
+  B->d_slabs = nullptr;
+  B->nslabs = 0;
+  B->slab_elems = 0;
   B->ctx.assign(ninst, nullptr);
   B->h_inst.resize(ninst);
   char* w = (char*)workspace;
@@ -1004,7 +1042,19 @@ int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
   if (cudaStreamSynchronize(B->caller) != cudaSuccess) return PT_ECUDA;
   int rc = PT_OK;
   int cap = 0;
-  for (int m = 0; m < B->ninst && rc == PT_OK; ++m) {
+  if (B->coupled) {
+    // parts of one grid: one stress sub-step from the largest mu over all parts
+    double mu_max = 0.0;
+    for (int m = 0; m < B->ninst && rc == PT_OK; ++m) rc = step_begin_launch(B->ctx[m]);
+    for (int m = 0; m < B->ninst && rc == PT_OK; ++m) {
+      double v = 0.0;
+      rc = step_begin_mumax(B->ctx[m], &v);
+      mu_max = std::fmax(mu_max, v);
+    }
+    for (int m = 0; m < B->ninst && rc == PT_OK; ++m) rc = step_begin_finish(B->ctx[m], mu_max);
+    cap = B->ctx[0]->num.max_iter;
+  }
+  for (int m = 0; m < B->ninst && rc == PT_OK && !B->coupled; ++m) {
     rc = pt_step_begin(B->ctx[m]);   // old-state snapshot, dtS, coefficients (per instance)
     cap = std::max(cap, B->ctx[m]->num.max_iter);
   }
@@ -1391,6 +1441,251 @@ int pt_adjoint_apply(pt_ctx* c, const pt_adj_vec* lam, pt_adj_vec* out, void* ws
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_status(e);
+}
+
+}  // extern "C"
+
+// ============================================================================ sub-domains
+struct pt_dd {
+  pt_grid grid;
+  Box gbox;
+  int nparts;
+  pt_batch* B;
+  std::vector<DDFields> h_parts;
+  DDFields* d_global;
+  DDFields* d_parts;
+  Box* d_boxes;
+  DDTables tables;
+};
+
+namespace {
+
+// Split of a grid into parts: part p of a direction owns cells [cut[p], cut[p+1]) and its box
+// adds one halo cell on each side that has a neighbour.
+struct DDPlan {
+  int parts[3];
+  std::vector<int> cut[3];
+  std::vector<pt_grid> grids;
+  std::vector<std::array<int, 3>> off;
+  std::vector<std::array<int, 6>> own;
+  std::vector<HaloSlab> slabs;
+  int slab_elems = 0;
+};
+
+bool dd_plan(const pt_grid* g, const int32_t* parts, DDPlan* P) {
+  if (!grid_ok(g) || !parts) return false;
+  const int n[3] = {g->nx, g->ny, g->nz};
+  const double h[3] = {g->lx / g->nx, g->ly / g->ny, g->lz / g->nz};
+  for (int d = 0; d < 3; ++d) {
+    if (parts[d] < 1 || (parts[d] > 1 && n[d] / parts[d] < 2)) return false;   // >= 2 cells per part
+    P->parts[d] = parts[d];
+    P->cut[d].resize(parts[d] + 1);
+    for (int p = 0; p <= parts[d]; ++p) P->cut[d][p] = (int)((long long)p * n[d] / parts[d]);
+  }
+  for (int pz = 0; pz < parts[2]; ++pz)
+    for (int py = 0; py < parts[1]; ++py)
+      for (int px = 0; px < parts[0]; ++px) {
+        const int pc[3] = {px, py, pz};
+        int nl[3];
+        std::array<int, 3> off;
+        std::array<int, 6> own;
+        for (int d = 0; d < 3; ++d) {
+          const int lo = P->cut[d][pc[d]], hi = P->cut[d][pc[d] + 1];
+          const int hl = pc[d] > 0, hr = pc[d] < parts[d] - 1;
+          nl[d] = hi - lo + hl + hr;
+          off[d] = lo - hl;
+          own[d] = hl;
+          own[3 + d] = hl + (hi - lo);
+        }
+        pt_grid lg{nl[0], nl[1], nl[2], nl[0] * h[0], nl[1] * h[1], nl[2] * h[2]};
+        const int m = (int)P->grids.size();
+        P->grids.push_back(lg);
+        P->off.push_back(off);
+        P->own.push_back(own);
+        for (int d = 0; d < 3; ++d)
+          for (int side = 0; side < 2; ++side) {
+            if (side == 0 ? pc[d] == 0 : pc[d] == parts[d] - 1) continue;
+            int r0[3], r1[3];
+            for (int e = 0; e < 3; ++e) {
+              r0[e] = 0;
+              r1[e] = nl[e] + 1;          // box indices include the upper face / edge plane
+            }
+            if (side == 0) {
+              r0[d] = 0;
+              r1[d] = 1;
+            } else {
+              r0[d] = nl[d] - 1;
+              r1[d] = nl[d] + 1;
+            }
+            P->slabs.push_back(HaloSlab{m, r0[0], r1[0], r0[1], r1[1], r0[2], r1[2]});
+            const long long el = (long long)(r1[0] - r0[0]) * (r1[1] - r0[1]) * (r1[2] - r0[2]);
+            P->slab_elems = (int)std::max<long long>(P->slab_elems, el);
+          }
+      }
+  return true;
+}
+
+size_t dd_part_bytes(const pt_grid& lg) {
+  return (size_t)kDDFields * align_up((size_t)make_box(&lg).n * sizeof(double), kAlign);
+}
+
+size_t dd_table_bytes(const pt_grid* g, const DDPlan& P) {
+  const size_t np = P.grids.size();
+  return align_up(sizeof(HaloSlab) * std::max<size_t>(1, P.slabs.size()), kAlign) +
+         align_up(sizeof(int) * (size_t)(g->nx + g->ny + g->nz + 3), kAlign) +
+         align_up(sizeof(int) * 3 * np, kAlign) + align_up(sizeof(DDFields) * (np + 1), kAlign) +
+         align_up(sizeof(Box) * np, kAlign);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pt_dd_workspace_size(const pt_grid* grid, const pt_num* num, const int32_t parts[3]) {
+  DDPlan P;
+  if (!num || !dd_plan(grid, parts, &P)) return 0;
+  size_t total = 0;
+  for (const pt_grid& lg : P.grids) total += dd_part_bytes(lg);
+  std::vector<pt_num> nums(P.grids.size(), *num);
+  const size_t bw = pt_batch_workspace_size((int32_t)P.grids.size(), P.grids.data(), nums.data());
+  if (bw == 0) return 0;
+  return total + align_up(bw, kAlign) + dd_table_bytes(grid, P);
+}
+
+int pt_dd_init(pt_dd** out, const pt_grid* grid, const pt_phys* phys, const pt_num* num, const pt_fields* fields,
+               const int32_t parts[3], void* workspace, size_t bytes, void* stream) {
+  if (!out) return PT_EINVAL;
+  *out = nullptr;
+  if (!grid || !phys || !num || !fields || !parts || !workspace) return PT_EINVAL;
+  if (num->precision != PT_FP64) return PT_EINVAL;
+  if (((uintptr_t)workspace & (kAlign - 1)) != 0) return PT_EINVAL;
+  DDPlan P;
+  if (!dd_plan(grid, parts, &P)) return PT_EINVAL;
+  const size_t need = pt_dd_workspace_size(grid, num, parts);
+  if (need == 0) return PT_EINVAL;
+  if (bytes < need) return PT_ESPACE;
+  const int np = (int)P.grids.size();
+  cudaStream_t s = (cudaStream_t)stream;
+  pt_dd* D = new (std::nothrow) pt_dd();
+  if (!D) return PT_ECUDA;
+  D->grid = *grid;
+  D->gbox = make_box(grid);
+  D->nparts = np;
+  // part fields, then the batch's workspace, then the tables
+  char* w = (char*)workspace;
+  D->h_parts.resize(np);
+  std::vector<pt_fields> pf(np);
+  for (int m = 0; m < np; ++m) {
+    const size_t stride = align_up((size_t)make_box(&P.grids[m]).n * sizeof(double), kAlign);
+    for (int f = 0; f < kDDFields; ++f) D->h_parts[m].f[f] = (double*)(w + f * stride);
+    if (!fields->logk) D->h_parts[m].f[kDDFields - 1] = nullptr;
+    double** F = D->h_parts[m].f;
+    pf[m] = pt_fields{F[0], F[1], F[2], F[3], F[4], F[5], F[6], F[7], F[8], F[9], F[10], F[11], F[12], F[13],
+                      F[14]};
+    w += dd_part_bytes(P.grids[m]);
+  }
+  std::vector<pt_num> nums(np, *num);
+  std::vector<pt_phys> phs(np, *phys);
+  const size_t bw = pt_batch_workspace_size(np, P.grids.data(), nums.data());
+  char* wb = w;
+  w += align_up(bw, kAlign);
+  HaloSlab* d_slabs = (HaloSlab*)w;
+  w += align_up(sizeof(HaloSlab) * std::max<size_t>(1, P.slabs.size()), kAlign);
+  int* d_own = (int*)w;
+  w += align_up(sizeof(int) * (size_t)(grid->nx + grid->ny + grid->nz + 3), kAlign);
+  int* d_off = (int*)w;
+  w += align_up(sizeof(int) * 3 * np, kAlign);
+  D->d_global = (DDFields*)w;
+  D->d_parts = D->d_global + 1;
+  w += align_up(sizeof(DDFields) * (np + 1), kAlign);
+  D->d_boxes = (Box*)w;
+  // host copies of the tables
+  std::vector<int> own;
+  const int n[3] = {grid->nx, grid->ny, grid->nz};
+  for (int d = 0; d < 3; ++d)
+    for (int G = 0; G <= n[d]; ++G) {
+      int p = 0;
+      while (p + 1 < P.parts[d] && G >= P.cut[d][p + 1]) ++p;
+      own.push_back(p);
+    }
+  std::vector<int> off;
+  std::vector<Box> boxes;
+  for (int m = 0; m < np; ++m) {
+    for (int d = 0; d < 3; ++d) off.push_back(P.off[m][d]);
+    boxes.push_back(make_box(&P.grids[m]));
+  }
+  DDFields g;
+  const double* gf[kDDFields] = {fields->Vx, fields->Vy, fields->Vz, fields->Pt, fields->Pf, fields->phi,
+                                 fields->txx, fields->tyy, fields->tzz, fields->txy, fields->txz, fields->tyz,
+                                 fields->mu, fields->eta, fields->logk};
+  for (int f = 0; f < kDDFields; ++f) g.f[f] = const_cast<double*>(gf[f]);
+  cudaError_t e = cudaSuccess;
+  if (!P.slabs.empty())
+    e = cudaMemcpyAsync(d_slabs, P.slabs.data(), sizeof(HaloSlab) * P.slabs.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_own, own.data(), sizeof(int) * own.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D->d_global, &g, sizeof g, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(D->d_parts, D->h_parts.data(), sizeof(DDFields) * np, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D->d_boxes, boxes.data(), sizeof(Box) * np, cudaMemcpyHostToDevice, s);
+  for (int m = 0; m < np && e == cudaSuccess; ++m) {
+    dd_scatter(s, D->gbox, boxes[m], P.off[m][0], P.off[m][1], P.off[m][2], D->d_global, D->d_parts + m);
+    e = cudaGetLastError();
+  }
+  // the host tables must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete D;
+    return PT_ECUDA;
+  }
+  int rc = pt_batch_init(&D->B, np, P.grids.data(), phs.data(), nums.data(), pf.data(), wb, bw, stream);
+  if (rc != PT_OK) {
+    delete D;
+    return rc;
+  }
+  pt_batch* B = D->B;
+  for (pt_ctx* c : B->ctx) {   // coefficients from the whole grid's spacing (and nz)
+    c->metric = *grid;
+    fill_coef(c);
+  }
+  B->coupled = 1;
+  B->own = P.own;
+  B->d_slabs = d_slabs;
+  B->nslabs = (int)P.slabs.size();
+  B->slab_elems = P.slab_elems;
+  D->tables = DDTables{d_own, d_own + grid->nx + 1, d_own + grid->nx + grid->ny + 2, d_off, P.parts[0],
+                       P.parts[1]};
+  B->tables = D->tables;
+  *out = D;
+  return PT_OK;
+}
+
+int pt_dd_step(pt_dd* D, pt_report* rep) {
+  if (!D || !rep) return PT_EINVAL;
+  std::vector<pt_report> reps(D->nparts);
+  const int rc = pt_batch_step(D->B, reps.data(), nullptr);
+  *rep = reps[0];
+  return rc;
+}
+
+int pt_dd_gather(pt_dd* D) {
+  if (!D) return PT_EINVAL;
+  dd_gather(D->B->stream, D->gbox, D->d_boxes, D->tables, D->d_global, D->d_parts);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(D->B->stream);
+  return cuda_status(e);
+}
+
+int pt_dd_config(const pt_dd* D, int32_t* nparts, int32_t* tile_x, int32_t* tile_y, int32_t* ipg) {
+  if (!D) return PT_EINVAL;
+  if (nparts) *nparts = D->nparts;
+  return pt_batch_config(D->B, tile_x, tile_y, ipg);
+}
+
+void pt_dd_destroy(pt_dd* D) {
+  if (!D) return;
+  pt_batch_destroy(D->B);
+  delete D;
 }
 
 }  // extern "C"

@@ -23,6 +23,7 @@ struct BatchInst {
   int max_iter;
   int gx, gy;                 // tiles per z-level for the current tile shape
   long long tile_base;        // first work item of this instance
+  int own_lo[3], own_hi[3];   // cells [own_lo, own_hi) per direction enter the residual norms
 };
 
 // Per-instance status written by the convergence kernel (device memory).
@@ -41,8 +42,9 @@ enum { BATCH_CELLS = 0, BATCH_FACES = 1, BATCH_PICARD = 2, BATCH_COEF = 3 };
 void batch_phase(int bx, int by, int grid, cudaStream_t s, int phase, const BatchInst* inst,
                  const BatchStatus* st, int ninst, long long ntiles, int a, int check);
 // After a check iteration: retire converged (or capped / non-finite) instances, add `nup` to
-// the iteration counter of the active ones, clear their reduction slots.
-void batch_converge(cudaStream_t s, const BatchInst* inst, BatchStatus* st, int ninst, int nup);
+// the iteration counter of the active ones, clear their reduction slots. coupled: the instances
+// are parts of one problem sharing instance 0's reduction slots and retire together.
+void batch_converge(cudaStream_t s, const BatchInst* inst, BatchStatus* st, int ninst, int nup, int coupled);
 // Start of a step: all instances active, counters zero, reduction slots clear, start time.
 void batch_start(cudaStream_t s, const BatchInst* inst, BatchStatus* st, int ninst);
 // Resident CTAs per SM of the batched cell kernel for a tile shape (occupancy of the widest phase).

@@ -46,21 +46,29 @@ __global__ void __launch_bounds__(BX * BY) k_batch_phase(const BatchInst* __rest
     const int r = (int)(local - (long long)k * per_z);
     const int ty = r / I.gx, tx = r - ty * I.gx;
     const int i = tx * BX + threadIdx.x, j = ty * BY + threadIdx.y;
+    // ownership of the cell (i, j, k) and of its lower faces: a face counts when one of its two
+    // cells is owned (halo cells of a sub-domain are recomputed by their owner)
+    const bool ox = i >= I.own_lo[0] && i < I.own_hi[0], oy = j >= I.own_lo[1] && j < I.own_hi[1];
+    const bool oz = k >= I.own_lo[2] && k < I.own_hi[2];
+    const bool own = ox && oy && oz;
     if (PHASE == BATCH_CELLS) {
       double r_pt = 0.0, r_pf = 0.0;
       lean_cell_point(I.b, I.c, I.cin[a], I.cout[a], i, j, k, check, r_pt, r_pf);
       if (check) {
-        block_max_atomic(r_pt, I.red + RED_PT);
-        block_max_atomic(r_pf, I.red + RED_PF);
+        block_max_atomic(own ? r_pt : 0.0, I.red + RED_PT);
+        block_max_atomic(own ? r_pf : 0.0, I.red + RED_PF);
       }
     } else if (PHASE == BATCH_FACES) {
       double r_v = 0.0;
-      lean_face_point(I.b, I.c, I.fin[a], I.Vx, I.Vy, I.Vz, I.Rx, I.Ry, I.Rz, i, j, k, check, r_v);
+      const bool fx = i >= I.own_lo[0] && i <= I.own_hi[0], fy = j >= I.own_lo[1] && j <= I.own_hi[1];
+      const bool fz = k >= I.own_lo[2] && k <= I.own_hi[2];
+      const int mask = (fx && oy && oz ? 1 : 0) | (ox && fy && oz ? 2 : 0) | (ox && oy && fz ? 4 : 0);
+      lean_face_point(I.b, I.c, I.fin[a], I.Vx, I.Vy, I.Vz, I.Rx, I.Ry, I.Rz, i, j, k, check, r_v, mask);
       if (check) block_max_atomic(r_v, I.red + RED_V);
     } else if (PHASE == BATCH_PICARD) {
       double rp = 0.0;
       lean_picard_point(I.b, I.c, I.pin[a], I.mu, I.eta, i, j, k, rp);
-      block_max_atomic(rp, I.red + RED_PIC);
+      block_max_atomic(own ? rp : 0.0, I.red + RED_PIC);
     } else {
       lean_coef_point(I.b, I.c, I.kin, I.kout, i, j, k);
     }
@@ -68,8 +76,35 @@ __global__ void __launch_bounds__(BX * BY) k_batch_phase(const BatchInst* __rest
 }
 
 __global__ void k_batch_converge(const BatchInst* __restrict__ inst, BatchStatus* __restrict__ st,
-                                 int ninst, int nup) {
+                                 int ninst, int nup, int coupled) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (coupled) {
+    // parts of one problem: instance 0's slots hold the global norms; one decision for all
+    if (m != 0 || !st[0].active) return;
+    unsigned long long* red = inst[0].red;
+    double v[4], worst = 0.0;
+    bool finite = true;
+    const int slot[4] = {RED_V, RED_PT, RED_PF, RED_PIC};
+    for (int s = 0; s < 4; ++s) {
+      v[s] = __longlong_as_double((long long)red[slot[s]]);
+      finite = finite && isfinite(v[s]);
+      worst = fmax(worst, v[s]);
+      red[slot[s]] = 0ull;
+    }
+    const int it = st[0].iters + nup;
+    const bool stop = !finite || worst < inst[0].tol || it >= inst[0].max_iter;
+    const unsigned long long now = global_ns();
+    for (int p = 0; p < ninst; ++p) {
+      for (int s = 0; s < 4; ++s) st[p].res[s] = v[s];
+      st[p].iters = it;
+      if (stop) {
+        st[p].active = 0;
+        st[p].status = !finite ? -3 : (worst < inst[0].tol ? 0 : -2);
+        st[p].t_stop = now;
+      }
+    }
+    return;
+  }
   if (m >= ninst || !st[m].active) return;
   unsigned long long* red = inst[m].red;
   double v[4];
@@ -123,8 +158,8 @@ void batch_phase(int bx, int by, int grid, cudaStream_t s, int phase, const Batc
   else launch_phase<32, 8>(grid, s, phase, inst, st, ninst, ntiles, a, check);
 }
 
-void batch_converge(cudaStream_t s, const BatchInst* inst, BatchStatus* st, int ninst, int nup) {
-  k_batch_converge<<<(ninst + 127) / 128, 128, 0, s>>>(inst, st, ninst, nup);
+void batch_converge(cudaStream_t s, const BatchInst* inst, BatchStatus* st, int ninst, int nup, int coupled) {
+  k_batch_converge<<<(ninst + 127) / 128, 128, 0, s>>>(inst, st, ninst, nup, coupled);
 }
 
 void batch_start(cudaStream_t s, const BatchInst* inst, BatchStatus* st, int ninst) {

@@ -49,6 +49,17 @@ __device__ inline float pos_max(float a, float b) {
 template <class T>
 __device__ inline T tabs(T x) { return x < T(0) ? -x : x; }
 
+// 1 / x for the local-implicit pseudo-step denominators (x > 0, far inside the normal range):
+// the hardware's approximate reciprocal refined by one Newton step, r' = r + r (1 - x r), whose
+// relative error is the square of the seed's (~2^-46 in FP64). It only scales the pseudo-time
+// step of the update P - res / x, so the fixed point of the iteration does not depend on it.
+__device__ inline double rcp_pseudo(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ inline float rcp_pseudo(float x) { return __frcp_rn(x); }
+
 
 }  // namespace lean_detail
 
@@ -132,13 +143,11 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       }
       // div qD = -1/2 sum_d rd^2 [(k + k_r)(Pf_r - Pf) - (k_l + k)(Pf - Pf_l)]
       const T divqD = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
-      // local-implicit pressure updates, Eqs. 17-18, written with 1 / dtau
-      const T idtp = in.idtp[q];
-      const T Pt1 = (Pt * idtp - (divV - c.bd_rdt * (Pto + c.alpha * dPf) - cc * Pf)) /
-                    (idtp + c.bd_rdt + cc);
-      const T idtf = kmax * c.ifac_pf;
-      const T Pf1 = (Pf * idtf - (divqD - c.bd_rdt * (c.alpha_B * Pfo + c.alpha * dPt) - cc * Pt)) /
-                    (idtf + c.bda_B_rdt + cc);
+      // local-implicit pressure updates, Eqs. 17-18: P1 = P - res / (1/dtau + d res/dP), the
+      // residuals being divVn (row Pt) and resF (row Pf)
+      const T resF = divqD + c.bda_B_rdt * dPf - c.bd_rdt * c.alpha * dPt + (Pf - Pt) * cc;
+      const T Pt1 = Pt - rcp_pseudo(in.idtp[q] + c.bd_rdt + cc) * divVn;
+      const T Pf1 = Pf - rcp_pseudo(kmax * c.ifac_pf + c.bda_B_rdt + cc) * resF;
       out.Pt[q] = Pt1;
       out.Pf[q] = Pf1;
       // normal deviatoric stresses (Eq. 21): tau = tau_o xi/(1+xi) + 2 mu/(1+xi) (edot + beta_n divVn)
@@ -171,18 +180,19 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       out.perm[q] = (in.K0 ? in.K0[q] : c.k0) * r * r * r;
       if (check) {
         r_pt = (double)tabs(divVn);
-        r_pf = (double)tabs(divqD + c.bda_B_rdt * dPf - c.bd_rdt * c.alpha * dPt + (Pf - Pt) * cc);
+        r_pf = (double)tabs(resF);
       }
     }
   }
 }
 
-// Momentum residual, damped R and velocity update of the three lower faces of (i, j, k).
+// Momentum residual, damped R and velocity update of the three lower faces of (i, j, k); bit d
+// of `mask` includes the face normal to direction d in the residual norm r_v.
 template <class T>
 __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>& c, const LeanFaceIn<T>& in,
                                                 T* __restrict__ Vx, T* __restrict__ Vy, T* __restrict__ Vz,
                                                 T* __restrict__ Rx, T* __restrict__ Ry, T* __restrict__ Rz,
-                                                int i, int j, int k, int check, double& r_v) {
+                                                int i, int j, int k, int check, double& r_v, int mask = 7) {
   using namespace lean_detail;
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
@@ -193,7 +203,7 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
       const T R = F * c.rrho_i + c.damp_x * Rx[q];
       Rx[q] = R;
       Vx[q] += in.dtv_x[q] * R;
-      if (check) r_v = fmax(r_v, (double)tabs(F));
+      if (check && (mask & 1)) r_v = fmax(r_v, (double)tabs(F));
     }
     if (j > 0 && j < b.ny && i < b.nx && k < b.nz) {
       const T F = (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
@@ -201,7 +211,7 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
       const T R = F * c.rrho_i + c.damp_y * Ry[q];
       Ry[q] = R;
       Vy[q] += in.dtv_y[q] * R;
-      if (check) r_v = fmax(r_v, (double)tabs(F));
+      if (check && (mask & 2)) r_v = fmax(r_v, (double)tabs(F));
     }
     if (k > 0 && k < b.nz && i < b.nx && j < b.ny) {
       // buoyancy -(rho g - rho_BG g) averaged to the face, rho g - rho_BG g = (phi - phi0) drho_g
@@ -211,7 +221,7 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
       const T R = F * c.rrho_i + c.damp_z * Rz[q];
       Rz[q] = R;
       Vz[q] += in.dtv_z[q] * R;
-      if (check) r_v = fmax(r_v, (double)tabs(F));
+      if (check && (mask & 4)) r_v = fmax(r_v, (double)tabs(F));
     }
   }
 }

@@ -11,13 +11,13 @@ struct MixPrepIn {
 };
 struct MixPrepOut {
   double *txx, *tyy, *tzz;                                  // FP64 stresses at u
-  float *r_pt, *r_pf, *cc, *perm, *idtp, *iden_pt, *idtf, *iden_pf;
+  float *r_pt, *r_pf, *cc, *perm, *iden_pt, *iden_pf;
 };
 struct MixFaceIn {
   const double *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt, *phi;
 };
 struct MixCoefOut {
-  float *cm2, *em2_xy, *em2_xz, *em2_yz, *dtv_x, *dtv_y, *dtv_z;
+  float *mu;                                                // FP32 copy of the Picard-updated mu
 };
 struct MixUpdate {
   double *Vx, *Vy, *Vz, *Pt, *Pf;
@@ -28,20 +28,19 @@ template <class T>
 struct CorrCoef {
   T rdx, rdy, rdz, hrdx, hrdy, hrdz, hrdx2, hrdy2, hrdz2;
   T bd_rdt, bd_rdt_a, bda_B_rdt, beta_n, rrho_i, damp_x, damp_y, damp_z;
+  T rG;                                            // 1 / (G dtS): xi = mu rG
+  T hdtv;                                          // dtau_V at a face = hdtv (1/mu_l + 1/mu_r)
+};
+// One FP32 PT iteration on the correction reads the current correction and the frozen
+// coefficients and writes the next correction (ping-pong); R is updated in place.
+template <class T>
+struct CorrIn {
+  const T *Vx, *Vy, *Vz, *Pt, *Pf;                 // current correction dV, dPt, dPf
+  const T *cc, *perm, *iden_pt, *iden_pf, *r_pt, *r_pf, *mu, *rfx, *rfy, *rfz;
 };
 template <class T>
-struct CorrCellIn {
-  const T *Vx, *Vy, *Vz, *Pt, *Pf;                 // current correction
-  const T *cc, *perm, *idtp, *iden_pt, *idtf, *iden_pf, *r_pt, *r_pf;
-  const T *cm2, *em2_xy, *em2_xz, *em2_yz;
-};
-template <class T>
-struct CorrCellOut {
-  T *Pt, *Pf, *txx, *tyy, *tzz, *txy, *txz, *tyz;
-};
-template <class T>
-struct CorrFaceIn {
-  const T *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt1, *dtv_x, *dtv_y, *dtv_z, *rfx, *rfy, *rfz;
+struct CorrOut {
+  T *Vx, *Vy, *Vz, *Pt, *Pf;                       // next correction
 };
 
 void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPrepIn& in,
@@ -51,10 +50,7 @@ void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const 
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out);
 void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u);
 template <class T>
-void corr_cells(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrCellIn<T>& in,
-                const CorrCellOut<T>& out, unsigned long long* red, int check);
-template <class T>
-void corr_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrFaceIn<T>& in,
-                T* Vx, T* Vy, T* Vz, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check);
+void corr_iter(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrIn<T>& in,
+               const CorrOut<T>& out, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check);
 
 }  // namespace pt

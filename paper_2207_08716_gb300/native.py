@@ -17,8 +17,8 @@ _INC = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
 SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu",
-           "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_static.cu")
-HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh")
+           "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu")
+HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -158,6 +158,14 @@ SIGNATURES = {
     "pt_adjoint_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(Report)]),
     "pt_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Report)]),
     "pt_adjoint_apply": (C.c_int, [C.c_void_p, C.POINTER(AdjVec), C.POINTER(AdjVec), C.c_void_p, C.c_size_t]),
+    "pt_dd_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.POINTER(Num), C.POINTER(C.c_int32)]),
+    "pt_dd_init": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Grid), C.POINTER(Phys), C.POINTER(Num),
+                             C.POINTER(Fields), C.POINTER(C.c_int32), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pt_dd_step": (C.c_int, [C.c_void_p, C.POINTER(Report)]),
+    "pt_dd_gather": (C.c_int, [C.c_void_p]),
+    "pt_dd_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32)]),
+    "pt_dd_destroy": (None, [C.c_void_p]),
     "pt_batch_workspace_size": (C.c_size_t, [C.c_int32, C.POINTER(Grid), C.POINTER(Num)]),
     "pt_batch_init": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(Grid), C.POINTER(Phys),
                                 C.POINTER(Num), C.POINTER(Fields), C.c_void_p, C.c_size_t, C.c_void_p]),

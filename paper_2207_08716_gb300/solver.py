@@ -297,3 +297,78 @@ class PTBatch:
             self.close()
         except Exception:
             pass
+
+
+class PTDomains:
+    """The grid split into parts x parts x parts sub-domains with halo exchange (pt_dd_* of the
+    C ABI): same arguments as PTSolver plus `parts` = (px, py, pz); FP64-lean form."""
+
+    def __init__(self, params: dict, phi, parts=(2, 2, 2), logk=None, device="cuda", stream=None):
+        self.lib = N.load()
+        p = dict(params)
+        p["precision"] = N.PT_FP64
+        self.params = p
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.nx, self.ny, self.nz = p["nx"], p["ny"], p["nz"]
+        self._grid, self._phys, self._num = N.grid_from(p), N.phys_from(p), N.num_from(p)
+        self._parts = (C.c_int32 * 3)(*[int(x) for x in parts])
+        px = self.lib.pt_pitch_x(C.byref(self._grid))
+        if px == 0:
+            raise PTError(N.PT_EINVAL, "grid")
+        self.box_shape = (self.nz + 1, self.ny + 1, px)
+        ws = self.lib.pt_dd_workspace_size(C.byref(self._grid), C.byref(self._num), self._parts)
+        if ws == 0:
+            raise PTError(N.PT_EINVAL, "pt_dd_workspace_size")
+        with torch.cuda.device(self.device):
+            self.f = {k: torch.zeros(self.box_shape, dtype=torch.float64, device=self.device) for k in N.FIELD_NAMES}
+            self.logk = None
+            if logk is not None:
+                self.logk = torch.zeros(self.box_shape, dtype=torch.float64, device=self.device)
+                self.logk[: self.nz, : self.ny, : self.nx].copy_(torch.as_tensor(logk, dtype=torch.float64))
+            self.f["phi"][: self.nz, : self.ny, : self.nx].copy_(torch.as_tensor(phi, dtype=torch.float64))
+            self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self._fields = N.Fields(*[self.f[k].data_ptr() for k in N.FIELD_NAMES],
+                                self.logk.data_ptr() if self.logk is not None else None)
+        torch.cuda.synchronize(self.device)
+        h = C.c_void_p()
+        rc = self.lib.pt_dd_init(C.byref(h), C.byref(self._grid), C.byref(self._phys), C.byref(self._num),
+                                 C.byref(self._fields), self._parts, self.workspace.data_ptr(), ws,
+                                 self.stream.cuda_stream)
+        if rc != N.PT_OK:
+            raise PTError(rc, "pt_dd_init")
+        self.h = h
+
+    def step(self) -> dict:
+        rep = N.Report()
+        rc = self.lib.pt_dd_step(self.h, C.byref(rep))
+        if rc not in (N.PT_OK, N.PT_ENOTCONV):
+            raise PTError(rc, "pt_dd_step")
+        return rep.as_dict()
+
+    def gather(self) -> None:
+        rc = self.lib.pt_dd_gather(self.h)
+        if rc != N.PT_OK:
+            raise PTError(rc, "pt_dd_gather")
+
+    def get(self, name: str) -> np.ndarray:
+        """Field in its natural staggered shape (call gather() first)."""
+        torch.cuda.synchronize(self.device)
+        sh = natural_shape(name, self.nx, self.ny, self.nz)
+        return self.f[name][: sh[0], : sh[1], : sh[2]].cpu().numpy().copy()
+
+    def config(self) -> tuple:
+        n, bx, by, ipg = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self.lib.pt_dd_config(self.h, C.byref(n), C.byref(bx), C.byref(by), C.byref(ipg))
+        return n.value, bx.value, by.value, ipg.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pt_dd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

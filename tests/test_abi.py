@@ -80,3 +80,31 @@ def test_init_rejects_bad_arguments_before_touching_the_device(lib):
     assert lib.pt_step(None, None) == N.PT_EINVAL
     assert lib.pt_iterate(None, 0, 1, None) == N.PT_EINVAL
     assert lib.pt_strerror(N.PT_ENOTCONV).decode().startswith("PT iteration cap")
+
+
+def test_decomposition_sizes_are_validated_on_the_host(lib):
+    """pt_dd_workspace_size / pt_dd_init reject splits with fewer than 2 cells per part, bad part
+    counts and FP32 precision before any CUDA call (runs without a GPU)."""
+    import pt_inputs as I
+    from paper_2207_08716_gb300 import native as N
+    p = I.c1_params(10, 9, 8)
+    g, ph, num = N.grid_from(p), N.phys_from(p), N.num_from(p)
+    parts = lambda *v: (C.c_int32 * 3)(*v)
+    assert lib.pt_dd_workspace_size(C.byref(g), C.byref(num), parts(1, 1, 1)) > 0
+    assert lib.pt_dd_workspace_size(C.byref(g), C.byref(num), parts(5, 4, 4)) > 0
+    assert lib.pt_dd_workspace_size(C.byref(g), C.byref(num), parts(6, 1, 1)) == 0   # 10 / 6 < 2 cells
+    assert lib.pt_dd_workspace_size(C.byref(g), C.byref(num), parts(0, 1, 1)) == 0
+    one = lib.pt_dd_workspace_size(C.byref(g), C.byref(num), parts(1, 1, 1))
+    eight = lib.pt_dd_workspace_size(C.byref(g), C.byref(num), parts(2, 2, 2))
+    assert eight > one                                   # halos and per-part boxes cost memory
+    fs = N.Fields(*([None] * 15))
+    h = C.c_void_p()
+    aligned = 1 << 20
+    num32 = N.num_from(dict(p, precision=N.PT_FP32))
+    assert lib.pt_dd_init(C.byref(h), C.byref(g), C.byref(ph), C.byref(num32), C.byref(fs), parts(2, 2, 2),
+                          aligned, eight, None) == N.PT_EINVAL
+    assert lib.pt_dd_init(C.byref(h), C.byref(g), C.byref(ph), C.byref(num), C.byref(fs), parts(6, 1, 1),
+                          aligned, eight, None) == N.PT_EINVAL
+    assert lib.pt_dd_init(C.byref(h), C.byref(g), C.byref(ph), C.byref(num), C.byref(fs), parts(2, 2, 2),
+                          aligned, 16, None) == N.PT_ESPACE
+    assert not h.value
