@@ -41,9 +41,10 @@ KERNEL_BYTES_PER_CELL = {
     # faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
     "k_lean_cells": 36 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
     "k_lean_begin": 11 * 8,
-    # mixed precision, one fused FP32 correction iteration: reads 18 arrays (3 dV, dPt, dPf, cc,
-    # k, iden_pt, iden_pf, r_pt, r_pf, mu, 3 r_F, 3 R) and writes 8 (3 dV, dPt, dPf, 3 R)
-    "k_corr": 26 * 4,
+    # mixed precision, FP32 correction iterations: cells reads 15 arrays (3 dV, dPt, dPf, cc, k,
+    # iden_pt, iden_pf, r_pt, r_pf, cm2, 3 em2) and writes 8 (dPt, dPf, 6 stresses); faces reads 19
+    # (6 stresses, dPt, 3 dtv, 3 r_F, 3 R, 3 dV) and writes 6 (3 R, 3 dV)
+    "k_corr_cells": 23 * 4, "k_corr_faces": 25 * 4,
     # adjoint PT iteration: cells reads 26 arrays and writes 10, faces reads 17 and writes 6
     "k_adj_cells": 36 * 8, "k_adj_faces": 23 * 8,
 }

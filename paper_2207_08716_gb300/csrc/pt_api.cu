@@ -32,7 +32,7 @@ constexpr size_t kAlign = 256;
 constexpr int kPitchMultiple = 16;
 constexpr int kRefArrays = 23;   // step-by-step path
 constexpr int kLeanArrays = 23;  // extra arrays of the FP64-lean path
-constexpr int kMixArrays = 23;   // FP32 arrays of the mixed-precision path
+constexpr int kMixArrays = 32;   // FP32 arrays of the mixed-precision path
 // Default relative drop at which the inner FP32 solves of the mixed-precision path stop. The
 // outer loop's convergence is bound by the log-space Picard relaxation of mu and eta (one
 // update per outer iteration), not by the inner accuracy: a drop of 0.3 per inner solve needs
@@ -90,8 +90,10 @@ struct pt_ctx {
   LeanCoef<double> lcoef;
   // mixed-precision path (precision PT_FP32): FP32 correction problem
   bool mixed;
-  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_iden_pt, *m_iden_pf, *m_mu;
-  float *m_dVx[2], *m_dVy[2], *m_dVz[2], *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
+  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_iden_pt, *m_iden_pf;
+  float *m_cm2, *m_em2_xy, *m_em2_xz, *m_em2_yz;
+  float *m_dVx, *m_dVy, *m_dVz, *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
+  float *m_txx, *m_tyy, *m_tzz, *m_txy, *m_txz, *m_tyz, *m_dtv_x, *m_dtv_y, *m_dtv_z;
   CorrCoef<float> ccoef;
   // adjoint recording (pt_adjoint_forward / pt_adjoint)
   char* adj_ws;
@@ -117,14 +119,14 @@ namespace {
 
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
-                K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR,
+                K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_CELLS, K_CORR_FACES,
                 K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
                                            "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0",
                                            "k_mix_prepare", "k_mix_res_faces", "k_mix_coef",
-                                           "k_corr", "k_mix_update",
+                                           "k_corr_cells", "k_corr_faces", "k_mix_update",
                                            "k_adj_prep", "k_adj_cells", "k_adj_faces", "k_adj_carry"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
@@ -265,8 +267,6 @@ void fill_corr_coef(pt_ctx* c) {
   f.beta_n = (float)k.beta_n;
   f.rrho_i = (float)k.rrho_i;
   f.damp_x = (float)k.damp_x; f.damp_y = (float)k.damp_y; f.damp_z = (float)k.damp_z;
-  f.rG = (float)k.rGdtS;
-  f.hdtv = (float)(0.5 * k.dtauv_fac);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
@@ -416,23 +416,26 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   }
   const double target = (c->num.inner_rtol > 0 ? c->num.inner_rtol : kInnerRtol) * report_max(outer);
   // (iii) FP32 PT on the correction, from delta = 0, R = 0
-  MixCoefOut mco{c->m_mu};
+  MixCoefOut mco{c->m_cm2, c->m_em2_xy, c->m_em2_xz, c->m_em2_yz, c->m_dtv_x, c->m_dtv_y, c->m_dtv_z};
   PT_LAUNCH(c, K_MIX_COEF, mix_coef(gr, bl, c->stream, b, k, c->mu, mco));
   const size_t fb = (size_t)b.n * sizeof(float);
-  float* zero[] = {c->m_dVx[0], c->m_dVy[0], c->m_dVz[0], c->m_dVx[1], c->m_dVy[1], c->m_dVz[1],
-                   c->m_dPt[0], c->m_dPf[0], c->m_Rx, c->m_Ry, c->m_Rz};
+  float* zero[] = {c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[0], c->m_dPf[0], c->m_Rx, c->m_Ry, c->m_Rz};
   for (float* z : zero) cudaMemsetAsync(z, 0, fb, c->stream);
   int d = 0;
   const int nup = c->num.nup;
   for (int it = 1; it <= n_in; ++it) {
     const int check = early_exit && (it % nup) == 0;
     if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-    const CorrIn<float> ci{c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d], c->m_dPf[d], c->m_cc,
-                           c->m_perm, c->m_iden_pt, c->m_iden_pf, c->m_rpt, c->m_rpf, c->m_mu,
-                           c->m_rfx, c->m_rfy, c->m_rfz};
-    const CorrOut<float> co{c->m_dVx[1 - d], c->m_dVy[1 - d], c->m_dVz[1 - d], c->m_dPt[1 - d], c->m_dPf[1 - d]};
-    PT_LAUNCH(c, K_CORR, corr_iter<float>(gr, bl, c->stream, b, c->ccoef, ci, co, c->m_Rx, c->m_Ry, c->m_Rz,
-                                          c->red, check));
+    const CorrIn<float> ci{c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d], c->m_cc, c->m_perm,
+                           c->m_iden_pt, c->m_iden_pf, c->m_rpt, c->m_rpf, c->m_cm2, c->m_em2_xy,
+                           c->m_em2_xz, c->m_em2_yz};
+    const CorrCellOut<float> co{c->m_dPt[1 - d], c->m_dPf[1 - d], c->m_txx, c->m_tyy, c->m_tzz,
+                                c->m_txy, c->m_txz, c->m_tyz};
+    PT_LAUNCH(c, K_CORR_CELLS, corr_cells<float>(gr, bl, c->stream, b, c->ccoef, ci, co, c->red, check));
+    const CorrFaceIn<float> fi{c->m_txx, c->m_tyy, c->m_tzz, c->m_txy, c->m_txz, c->m_tyz, c->m_dPt[1 - d],
+                               c->m_dtv_x, c->m_dtv_y, c->m_dtv_z, c->m_rfx, c->m_rfy, c->m_rfz};
+    PT_LAUNCH(c, K_CORR_FACES, corr_faces<float>(gr, bl, c->stream, b, c->ccoef, fi, c->m_dVx, c->m_dVy,
+                                                 c->m_dVz, c->m_Rx, c->m_Ry, c->m_Rz, c->red, check));
     d = 1 - d;
     *inner_done = it;
     if (check) {
@@ -443,8 +446,7 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
     }
   }
   // (iv) u <- u + delta in FP64, then the FP64 porosity time integration (Eq. 22, log space)
-  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d],
-               c->m_dPf[d]};
+  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d]};
   PT_LAUNCH(c, K_MIX_UPDATE, mix_update(gr, bl, c->stream, b, mu));
   PT_LAUNCH(c, K_POROSITY,
             k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[a], c->Pf[a],
@@ -586,8 +588,9 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
     const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
     float** fslots[kMixArrays] = {
         &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_iden_pt,
-        &c->m_iden_pf, &c->m_mu, &c->m_dVx[0], &c->m_dVy[0], &c->m_dVz[0], &c->m_dVx[1], &c->m_dVy[1],
-        &c->m_dVz[1], &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0], &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz};
+        &c->m_iden_pf, &c->m_cm2, &c->m_em2_xy, &c->m_em2_xz, &c->m_em2_yz, &c->m_dVx, &c->m_dVy, &c->m_dVz, &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0],
+        &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz, &c->m_txx, &c->m_tyy, &c->m_tzz, &c->m_txy, &c->m_txz,
+        &c->m_tyz, &c->m_dtv_x, &c->m_dtv_y, &c->m_dtv_z};
     for (int s = 0; s < kMixArrays; ++s) *fslots[s] = (float*)(wend + s * fstride);
     wend += kMixArrays * fstride;
   }

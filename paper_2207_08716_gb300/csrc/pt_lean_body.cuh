@@ -73,30 +73,20 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
     const bool cell = i < b.nx && j < b.ny && k < b.nz;
-    // ---- edges owned by this index: xy (i, j, k), xz (i, j, k), yz (i, j, k)
-    if (k < b.nz) {
-      T t = T(0);
-      if (i > 0 && i < b.nx && j > 0 && j < b.ny) {
-        const T e = (in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx;
-        t = in.toa_xy[q] + in.em2_xy[q] * e;
-      }
-      out.txy[q] = t;
+    // ---- edges owned by this index: xy (i, j, k), xz (i, j, k), yz (i, j, k); stored at the end
+    // with the cell's outputs, after every load (the arrays are not declared non-aliasing)
+    T t_xy = T(0), t_xz = T(0), t_yz = T(0);
+    if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
+      const T e = (in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx;
+      t_xy = in.toa_xy[q] + in.em2_xy[q] * e;
     }
-    if (j < b.ny) {
-      T t = T(0);
-      if (i > 0 && i < b.nx && k > 0 && k < b.nz) {
-        const T e = (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx;
-        t = in.toa_xz[q] + in.em2_xz[q] * e;
-      }
-      out.txz[q] = t;
+    if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
+      const T e = (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx;
+      t_xz = in.toa_xz[q] + in.em2_xz[q] * e;
     }
-    if (i < b.nx) {
-      T t = T(0);
-      if (j > 0 && j < b.ny && k > 0 && k < b.nz) {
-        const T e = (in.Vy[q] - in.Vy[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - px]) * c.hrdy;
-        t = in.toa_yz[q] + in.em2_yz[q] * e;
-      }
-      out.tyz[q] = t;
+    if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
+      const T e = (in.Vy[q] - in.Vy[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - px]) * c.hrdy;
+      t_yz = in.toa_yz[q] + in.em2_yz[q] * e;
     }
     if (cell) {
       const T Pt = in.Pt[q], Pf = in.Pf[q], Pto = in.Pto[q], Pfo = in.Pfo[q];
@@ -148,15 +138,13 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       const T resF = divqD + c.bda_B_rdt * dPf - c.bd_rdt * c.alpha * dPt + (Pf - Pt) * cc;
       const T Pt1 = Pt - rcp_pseudo(in.idtp[q] + c.bd_rdt + cc) * divVn;
       const T Pf1 = Pf - rcp_pseudo(kmax * c.ifac_pf + c.bda_B_rdt + cc) * resF;
-      out.Pt[q] = Pt1;
-      out.Pf[q] = Pf1;
       // normal deviatoric stresses (Eq. 21): tau = tau_o xi/(1+xi) + 2 mu/(1+xi) (edot + beta_n divVn)
       const T third = divV * T(1.0 / 3.0);
       const T bn = c.beta_n * divVn;
       const T cm2 = in.cm2[q];
-      out.txx[q] = in.toa_xx[q] + cm2 * (gx - third + bn);
-      out.tyy[q] = in.toa_yy[q] + cm2 * (gy - third + bn);
-      out.tzz[q] = in.toa_zz[q] + cm2 * (gz - third + bn);
+      const T sxx = in.toa_xx[q] + cm2 * (gx - third + bn);
+      const T syy = in.toa_yy[q] + cm2 * (gy - third + bn);
+      const T szz = in.toa_zz[q] + cm2 * (gz - third + bn);
       // porosity in log space (Eq. 22): L = Lo + delta,
       // delta = -[beta_phi ((Pf1 - Pfo) - (Pt1 - Pto)) + dt (Pf1 - Pt1) / eta + dt V.grad(1-phi)/(1-phi)]
       T ax = T(0), ay = T(0), az = T(0);
@@ -173,16 +161,26 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       T em_p, em_n;
       expm1_pair(delta, em_p, em_n);
       const T phio = in.phio[q], Eo = in.Eo[q], iEo = in.iEo[q];
+      const T K0 = in.K0 ? in.K0[q] : c.k0;
       const T ph1 = phio - Eo * em_p;
+      const T r = ph1 * c.rphi0;
+      // every load above precedes the stores (the arrays are not declared non-aliasing)
+      out.Pt[q] = Pt1;
+      out.Pf[q] = Pf1;
+      out.txx[q] = sxx;
+      out.tyy[q] = syy;
+      out.tzz[q] = szz;
       out.phi[q] = ph1;
       out.w[q] = iEo + iEo * em_n;
-      const T r = ph1 * c.rphi0;
-      out.perm[q] = (in.K0 ? in.K0[q] : c.k0) * r * r * r;
+      out.perm[q] = K0 * r * r * r;
       if (check) {
         r_pt = (double)tabs(divVn);
         r_pf = (double)tabs(resF);
       }
     }
+    if (k < b.nz) out.txy[q] = t_xy;
+    if (j < b.ny) out.txz[q] = t_xz;
+    if (i < b.nx) out.tyz[q] = t_yz;
   }
 }
 
@@ -197,31 +195,38 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
-    if (i > 0 && i < b.nx && j < b.ny && k < b.nz) {
-      const T F = (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
-                  (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - 1]) * c.rdx;
-      const T R = F * c.rrho_i + c.damp_x * Rx[q];
-      Rx[q] = R;
-      Vx[q] += in.dtv_x[q] * R;
-      if (check && (mask & 1)) r_v = fmax(r_v, (double)tabs(F));
+    const bool fx = i > 0 && i < b.nx && j < b.ny && k < b.nz;
+    const bool fy = j > 0 && j < b.ny && i < b.nx && k < b.nz;
+    const bool fz = k > 0 && k < b.nz && i < b.nx && j < b.ny;
+    // all loads before the first store (the arrays are not declared non-aliasing)
+    T Fx = T(0), Fy = T(0), Fz = T(0), Rx1 = T(0), Ry1 = T(0), Rz1 = T(0), Vx1 = T(0), Vy1 = T(0), Vz1 = T(0);
+    if (fx) {
+      Fx = (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
+           (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - 1]) * c.rdx;
+      Rx1 = Fx * c.rrho_i + c.damp_x * Rx[q];
+      Vx1 = Vx[q] + in.dtv_x[q] * Rx1;
     }
-    if (j > 0 && j < b.ny && i < b.nx && k < b.nz) {
-      const T F = (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
-                  (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - px]) * c.rdy;
-      const T R = F * c.rrho_i + c.damp_y * Ry[q];
-      Ry[q] = R;
-      Vy[q] += in.dtv_y[q] * R;
-      if (check && (mask & 2)) r_v = fmax(r_v, (double)tabs(F));
+    if (fy) {
+      Fy = (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
+           (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - px]) * c.rdy;
+      Ry1 = Fy * c.rrho_i + c.damp_y * Ry[q];
+      Vy1 = Vy[q] + in.dtv_y[q] * Ry1;
     }
-    if (k > 0 && k < b.nz && i < b.nx && j < b.ny) {
+    if (fz) {
       // buoyancy -(rho g - rho_BG g) averaged to the face, rho g - rho_BG g = (phi - phi0) drho_g
       const T rog = (T(0.5) * (in.phi[q - pxy] + in.phi[q]) - c.phi0) * c.drho_g;
-      const T F = (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
-                  (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.Pt1[q] - in.Pt1[q - pxy]) * c.rdz - rog;
-      const T R = F * c.rrho_i + c.damp_z * Rz[q];
-      Rz[q] = R;
-      Vz[q] += in.dtv_z[q] * R;
-      if (check && (mask & 4)) r_v = fmax(r_v, (double)tabs(F));
+      Fz = (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
+           (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.Pt1[q] - in.Pt1[q - pxy]) * c.rdz - rog;
+      Rz1 = Fz * c.rrho_i + c.damp_z * Rz[q];
+      Vz1 = Vz[q] + in.dtv_z[q] * Rz1;
+    }
+    if (fx) { Rx[q] = Rx1; Vx[q] = Vx1; }
+    if (fy) { Ry[q] = Ry1; Vy[q] = Vy1; }
+    if (fz) { Rz[q] = Rz1; Vz[q] = Vz1; }
+    if (check) {
+      if (fx && (mask & 1)) r_v = fmax(r_v, (double)tabs(Fx));
+      if (fy && (mask & 2)) r_v = fmax(r_v, (double)tabs(Fy));
+      if (fz && (mask & 4)) r_v = fmax(r_v, (double)tabs(Fz));
     }
   }
 }

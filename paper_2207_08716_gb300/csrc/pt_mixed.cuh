@@ -17,7 +17,8 @@ struct MixFaceIn {
   const double *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt, *phi;
 };
 struct MixCoefOut {
-  float *mu;                                                // FP32 copy of the Picard-updated mu
+  float *cm2, *em2_xy, *em2_xz, *em2_yz;                    // 2 mu / (1 + xi) at centres and edges
+  float *dtv_x, *dtv_y, *dtv_z;                             // velocity pseudo-steps at faces
 };
 struct MixUpdate {
   double *Vx, *Vy, *Vz, *Pt, *Pf;
@@ -28,19 +29,20 @@ template <class T>
 struct CorrCoef {
   T rdx, rdy, rdz, hrdx, hrdy, hrdz, hrdx2, hrdy2, hrdz2;
   T bd_rdt, bd_rdt_a, bda_B_rdt, beta_n, rrho_i, damp_x, damp_y, damp_z;
-  T rG;                                            // 1 / (G dtS): xi = mu rG
-  T hdtv;                                          // dtau_V at a face = hdtv (1/mu_l + 1/mu_r)
 };
-// One FP32 PT iteration on the correction reads the current correction and the frozen
-// coefficients and writes the next correction (ping-pong); R is updated in place.
+// FP32 PT iteration on the correction: current correction and frozen coefficients.
 template <class T>
 struct CorrIn {
   const T *Vx, *Vy, *Vz, *Pt, *Pf;                 // current correction dV, dPt, dPf
-  const T *cc, *perm, *iden_pt, *iden_pf, *r_pt, *r_pf, *mu, *rfx, *rfy, *rfz;
+  const T *cc, *perm, *iden_pt, *iden_pf, *r_pt, *r_pf, *cm2, *em2_xy, *em2_xz, *em2_yz;
 };
 template <class T>
-struct CorrOut {
-  T *Vx, *Vy, *Vz, *Pt, *Pf;                       // next correction
+struct CorrCellOut {
+  T *Pt, *Pf, *txx, *tyy, *tzz, *txy, *txz, *tyz;  // next dPt, dPf; stresses of the correction
+};
+template <class T>
+struct CorrFaceIn {
+  const T *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt1, *dtv_x, *dtv_y, *dtv_z, *rfx, *rfy, *rfz;
 };
 
 void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPrepIn& in,
@@ -50,7 +52,10 @@ void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const 
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out);
 void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u);
 template <class T>
-void corr_iter(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrIn<T>& in,
-               const CorrOut<T>& out, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check);
+void corr_cells(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrIn<T>& in,
+                const CorrCellOut<T>& out, unsigned long long* red, int check);
+template <class T>
+void corr_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrFaceIn<T>& in, T* Vx,
+                T* Vy, T* Vz, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check);
 
 }  // namespace pt

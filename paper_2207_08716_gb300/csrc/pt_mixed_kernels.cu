@@ -9,7 +9,7 @@
 //   (iii) FP32 PT on the correction delta = (dV, dPt, dPf) of the system linearised at u with
 //         frozen coefficients (k, 1/(eta(1-phi)), mu, pseudo-time steps): the same damped,
 //         local-implicit scheme as the FP64 iteration, iterating on the small correction so
-//         that FP32 keeps its relative precision on it (k_corr: one fused launch per iteration);
+//         that FP32 keeps its relative precision on it (k_corr_cells, k_corr_faces);
 //   (iv)  u <- u + delta in FP64 (k_mix_update), then the porosity time integration of
 //         Eq. 22 in FP64 (log space) from the corrected pressures and velocities.
 // Converged when the FP64 residual max-norms and the Picard change are below tol.
@@ -137,95 +137,71 @@ __global__ void __launch_bounds__(256) k_mix_res_faces(Box b, Coef c, MixFaceIn 
 
 // Frozen mu-dependent coefficients of the correction problem: 2 mu/(1+xi) at centres and
 // edges, dtau_V on faces (FP32).
-__global__ void __launch_bounds__(256) k_mix_coef(Box b, const double* __restrict__ mu, MixCoefOut out) {
+__global__ void __launch_bounds__(256) k_mix_coef(Box b, Coef c, const double* __restrict__ mu, MixCoefOut out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  if (i >= b.nx || j >= b.ny || k >= b.nz) return;
+  if (i > b.nx || j > b.ny || k > b.nz) return;
   const long long q = cidx(b, i, j, k);
-  out.mu[q] = (float)mu[q];
-}
-
-namespace {
-
-// Normal stresses and the updated total-pressure correction of cell p (the linearised Eqs. 17
-// and 21 with frozen coefficients, local-implicit dPt' = dPt - rho_Pt / (1/dtau + d rho/dPt)).
-template <class T>
-__device__ __forceinline__ void corr_cell(const Box& b, const CorrCoef<T>& c, const CorrIn<T>& in, long long p,
-                                          T& txx, T& tyy, T& tzz, T& dPt1, T& rho_pt) {
-  const T gx = (in.Vx[p + 1] - in.Vx[p]) * c.rdx;
-  const T gy = (in.Vy[p + b.px] - in.Vy[p]) * c.rdy;
-  const T gz = (in.Vz[p + b.pxy] - in.Vz[p]) * c.rdz;
-  const T divV = gx + gy + gz;
-  const T cc = in.cc[p], rpt = in.r_pt[p];
-  const T dPt = in.Pt[p], dPf = in.Pf[p];
-  rho_pt = rpt + divV + (c.bd_rdt + cc) * dPt - (c.bd_rdt_a + cc) * dPf;
-  dPt1 = dPt - in.iden_pt[p] * rho_pt;
-  const T m = in.mu[p];
-  const T cm2 = __fdividef(T(2) * m, T(1) + m * c.rG);      // 2 mu / (1 + xi)
-  const T third = divV * T(1.0 / 3.0), bn = c.beta_n * (rho_pt - rpt);
-  txx = cm2 * (gx - third + bn);
-  tyy = cm2 * (gy - third + bn);
-  tzz = cm2 * (gz - third + bn);
-}
-
-template <class T>
-__device__ __forceinline__ T edge_em2(const CorrCoef<T>& c, T m1, T m2, T m3, T m4) {
-  const T m = T(0.25) * ((m1 + m2) + (m3 + m4));
-  return __fdividef(T(2) * m, T(1) + m * c.rG);
-}
-// Shear stresses of the correction at the edge with box index e = (i, j, k); zero on the walls.
-template <class T>
-__device__ __forceinline__ T corr_txy(const Box& b, const CorrCoef<T>& c, const CorrIn<T>& in, long long e,
-                                      int i, int j, int k) {
-  if (!(i > 0 && i < b.nx && j > 0 && j < b.ny && k < b.nz)) return T(0);
-  const long long px = b.px;
-  return edge_em2(c, in.mu[e - 1 - px], in.mu[e - px], in.mu[e - 1], in.mu[e]) *
-         ((in.Vx[e] - in.Vx[e - px]) * c.hrdy + (in.Vy[e] - in.Vy[e - 1]) * c.hrdx);
-}
-template <class T>
-__device__ __forceinline__ T corr_txz(const Box& b, const CorrCoef<T>& c, const CorrIn<T>& in, long long e,
-                                      int i, int j, int k) {
-  if (!(i > 0 && i < b.nx && k > 0 && k < b.nz && j < b.ny)) return T(0);
-  const long long pxy = b.pxy;
-  return edge_em2(c, in.mu[e - 1 - pxy], in.mu[e - pxy], in.mu[e - 1], in.mu[e]) *
-         ((in.Vx[e] - in.Vx[e - pxy]) * c.hrdz + (in.Vz[e] - in.Vz[e - 1]) * c.hrdx);
-}
-template <class T>
-__device__ __forceinline__ T corr_tyz(const Box& b, const CorrCoef<T>& c, const CorrIn<T>& in, long long e,
-                                      int i, int j, int k) {
-  if (!(j > 0 && j < b.ny && k > 0 && k < b.nz && i < b.nx)) return T(0);
   const long long px = b.px, pxy = b.pxy;
-  return edge_em2(c, in.mu[e - px - pxy], in.mu[e - pxy], in.mu[e - px], in.mu[e]) *
-         ((in.Vy[e] - in.Vy[e - pxy]) * c.hrdz + (in.Vz[e] - in.Vz[e - px]) * c.hrdy);
+  const double rG = c.rGdtS;
+  // viscoelastic moduli 2 mu / (1 + xi) at centres and edges (mean of the four cells' mu)
+  if (i < b.nx && j < b.ny && k < b.nz) {
+    const double m = mu[q];
+    out.cm2[q] = (float)(2.0 * m / (1.0 + m * rG));
+  }
+  if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
+    const double m = 0.25 * (mu[q - 1 - px] + mu[q - px] + mu[q - 1] + mu[q]);
+    out.em2_xy[q] = (float)(2.0 * m / (1.0 + m * rG));
+  }
+  if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
+    const double m = 0.25 * (mu[q - 1 - pxy] + mu[q - pxy] + mu[q - 1] + mu[q]);
+    out.em2_xz[q] = (float)(2.0 * m / (1.0 + m * rG));
+  }
+  if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
+    const double m = 0.25 * (mu[q - px - pxy] + mu[q - pxy] + mu[q - px] + mu[q]);
+    out.em2_yz[q] = (float)(2.0 * m / (1.0 + m * rG));
+  }
+  // pseudo-time steps of the velocity correction, mean of the two centres' dtau_V = fac / mu
+  if (i > 0 && i < b.nx && j < b.ny && k < b.nz)
+    out.dtv_x[q] = (float)(0.5 * c.dtauv_fac * (1.0 / mu[q - 1] + 1.0 / mu[q]));
+  if (j > 0 && j < b.ny && i < b.nx && k < b.nz)
+    out.dtv_y[q] = (float)(0.5 * c.dtauv_fac * (1.0 / mu[q - px] + 1.0 / mu[q]));
+  if (k > 0 && k < b.nz && i < b.nx && j < b.ny)
+    out.dtv_z[q] = (float)(0.5 * c.dtauv_fac * (1.0 / mu[q - pxy] + 1.0 / mu[q]));
 }
 
-}  // namespace
-
-// (iii) one FP32 PT iteration on the correction, fused: the thread of box index (i, j, k)
-// updates the cell's dPt, dPf (local-implicit, linearised Eqs. 17-18 with right-hand sides
-// r_Pt, r_Pf) and the cell's three lower faces (linearised Eq. 19 with right-hand side r_F,
-// damped R, dV update). The stresses are recomputed from the current dV instead of stored, and
-// the pressure update of a face's other cell is recomputed where the face needs it, so one
-// launch reads each array once (26 FP32 arrays per cell instead of 50 for a cells + faces
-// pair); the arithmetic is the same iteration as updating cells then faces.
+// (iii) one FP32 PT iteration on the correction, cells: edge and centre stresses of dV (no
+// old-stress term, it is in r_F), local-implicit dPt, dPf updates of the linearised Eqs. 17-18
+// with right-hand sides r_Pt, r_Pf and frozen coefficients, written dP' = dP - rho / (1/dtau +
+// d rho/dP). Reads 15 FP32 arrays and writes 8; every load is issued before the first store
+// (the arrays are not declared non-aliasing, so a store would order the loads after it).
 template <class T>
-__global__ void __launch_bounds__(256) k_corr(Box b, CorrCoef<T> c, CorrIn<T> in, CorrOut<T> out,
-                                              T* __restrict__ Rx, T* __restrict__ Ry, T* __restrict__ Rz,
-                                              unsigned long long* red, int check) {
+__global__ void __launch_bounds__(256) k_corr_cells(Box b, CorrCoef<T> c, CorrIn<T> in, CorrCellOut<T> out,
+                                                    unsigned long long* red, int check) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  double r_pt = 0.0, r_pf = 0.0, r_v = 0.0;
+  double r_pt = 0.0, r_pf = 0.0;
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
+    T txy = T(0), txz = T(0), tyz = T(0);
+    if (i > 0 && i < b.nx && j > 0 && j < b.ny && k < b.nz)
+      txy = in.em2_xy[q] * ((in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx);
+    if (i > 0 && i < b.nx && k > 0 && k < b.nz && j < b.ny)
+      txz = in.em2_xz[q] * ((in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx);
+    if (j > 0 && j < b.ny && k > 0 && k < b.nz && i < b.nx)
+      tyz = in.em2_yz[q] * ((in.Vy[q] - in.Vy[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - px]) * c.hrdy);
     const bool cell = i < b.nx && j < b.ny && k < b.nz;
-    T txx = T(0), tyy = T(0), tzz = T(0), dPt1 = T(0), rho_pt = T(0);
+    T txx = T(0), tyy = T(0), tzz = T(0), dPt1 = T(0), dPf1 = T(0);
     if (cell) {
-      corr_cell(b, c, in, q, txx, tyy, tzz, dPt1, rho_pt);
-      // fluid-pressure correction: linearised Darcy (frozen k) with the current dPf
-      const T dPt = in.Pt[q], dPf = in.Pf[q], cc = in.cc[q], kc = in.perm[q];
+      const T dPt = in.Pt[q], dPf = in.Pf[q], cc = in.cc[q], rpt = in.r_pt[q], kc = in.perm[q];
+      const T gx = (in.Vx[q + 1] - in.Vx[q]) * c.rdx, gy = (in.Vy[q + px] - in.Vy[q]) * c.rdy;
+      const T gz = (in.Vz[q + pxy] - in.Vz[q]) * c.rdz;
+      const T divV = gx + gy + gz;
+      const T cpl = c.bd_rdt_a + cc;
+      const T rho_pt = rpt + divV + (c.bd_rdt + cc) * dPt - cpl * dPf;
       T sx = T(0), sy = T(0), sz = T(0);
       if (i > 0) sx -= (in.perm[q - 1] + kc) * (dPf - in.Pf[q - 1]);
       if (i < b.nx - 1) sx += (kc + in.perm[q + 1]) * (in.Pf[q + 1] - dPf);
@@ -234,54 +210,78 @@ __global__ void __launch_bounds__(256) k_corr(Box b, CorrCoef<T> c, CorrIn<T> in
       if (k > 0) sz -= (in.perm[q - pxy] + kc) * (dPf - in.Pf[q - pxy]);
       if (k < b.nz - 1) sz += (kc + in.perm[q + pxy]) * (in.Pf[q + pxy] - dPf);
       const T divq = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
-      const T rho_pf = in.r_pf[q] + divq + (c.bda_B_rdt + cc) * dPf - (c.bd_rdt_a + cc) * dPt;
-      out.Pt[q] = dPt1;
-      out.Pf[q] = dPf - in.iden_pf[q] * rho_pf;
+      const T rho_pf = in.r_pf[q] + divq + (c.bda_B_rdt + cc) * dPf - cpl * dPt;
+      dPt1 = dPt - in.iden_pt[q] * rho_pt;
+      dPf1 = dPf - in.iden_pf[q] * rho_pf;
+      const T cm2 = in.cm2[q];
+      const T third = divV * T(1.0 / 3.0), bn = c.beta_n * (rho_pt - rpt);
+      txx = cm2 * (gx - third + bn);
+      tyy = cm2 * (gy - third + bn);
+      tzz = cm2 * (gz - third + bn);
       if (check) {
         r_pt = (double)tabs(rho_pt);
         r_pf = (double)tabs(rho_pf);
       }
     }
-    const T txy0 = corr_txy(b, c, in, q, i, j, k);
-    const T txz0 = corr_txz(b, c, in, q, i, j, k);
-    const T tyz0 = corr_tyz(b, c, in, q, i, j, k);
-    if (i > 0 && i < b.nx && j < b.ny && k < b.nz) {
-      T lxx, lyy, lzz, lP1, lrho;
-      corr_cell(b, c, in, q - 1, lxx, lyy, lzz, lP1, lrho);
-      const T F = in.rfx[q] + (txx - lxx) * c.rdx + (corr_txy(b, c, in, q + px, i, j + 1, k) - txy0) * c.rdy +
-                  (corr_txz(b, c, in, q + pxy, i, j, k + 1) - txz0) * c.rdz - (dPt1 - lP1) * c.rdx;
-      const T R = F * c.rrho_i + c.damp_x * Rx[q];
-      Rx[q] = R;
-      out.Vx[q] = in.Vx[q] + c.hdtv * (__frcp_rn(in.mu[q - 1]) + __frcp_rn(in.mu[q])) * R;
-      if (check) r_v = fmax(r_v, (double)tabs(F));
-    }
-    if (j > 0 && j < b.ny && i < b.nx && k < b.nz) {
-      T lxx, lyy, lzz, lP1, lrho;
-      corr_cell(b, c, in, q - px, lxx, lyy, lzz, lP1, lrho);
-      const T F = in.rfy[q] + (corr_txy(b, c, in, q + 1, i + 1, j, k) - txy0) * c.rdx + (tyy - lyy) * c.rdy +
-                  (corr_tyz(b, c, in, q + pxy, i, j, k + 1) - tyz0) * c.rdz - (dPt1 - lP1) * c.rdy;
-      const T R = F * c.rrho_i + c.damp_y * Ry[q];
-      Ry[q] = R;
-      out.Vy[q] = in.Vy[q] + c.hdtv * (__frcp_rn(in.mu[q - px]) + __frcp_rn(in.mu[q])) * R;
-      if (check) r_v = fmax(r_v, (double)tabs(F));
-    }
-    if (k > 0 && k < b.nz && i < b.nx && j < b.ny) {
-      T lxx, lyy, lzz, lP1, lrho;
-      corr_cell(b, c, in, q - pxy, lxx, lyy, lzz, lP1, lrho);
-      const T F = in.rfz[q] + (corr_txz(b, c, in, q + 1, i + 1, j, k) - txz0) * c.rdx +
-                  (corr_tyz(b, c, in, q + px, i, j + 1, k) - tyz0) * c.rdy + (tzz - lzz) * c.rdz -
-                  (dPt1 - lP1) * c.rdz;
-      const T R = F * c.rrho_i + c.damp_z * Rz[q];
-      Rz[q] = R;
-      out.Vz[q] = in.Vz[q] + c.hdtv * (__frcp_rn(in.mu[q - pxy]) + __frcp_rn(in.mu[q])) * R;
-      if (check) r_v = fmax(r_v, (double)tabs(F));
+    if (k < b.nz) out.txy[q] = txy;
+    if (j < b.ny) out.txz[q] = txz;
+    if (i < b.nx) out.tyz[q] = tyz;
+    if (cell) {
+      out.Pt[q] = dPt1;
+      out.Pf[q] = dPf1;
+      out.txx[q] = txx;
+      out.tyy[q] = tyy;
+      out.tzz[q] = tzz;
     }
   }
   if (check) {
     block_max_atomic(r_pt, red + RED_PT);
     block_max_atomic(r_pf, red + RED_PF);
-    block_max_atomic(r_v, red + RED_V);
   }
+}
+
+// (iii) faces: linearised momentum residual r_F + div tau(dV) - grad dPt', damped R, dV update.
+// Reads 19 FP32 arrays and writes 6, all loads before the first store.
+template <class T>
+__global__ void __launch_bounds__(256) k_corr_faces(Box b, CorrCoef<T> c, CorrFaceIn<T> in,
+                                                    T* __restrict__ Vx, T* __restrict__ Vy, T* __restrict__ Vz,
+                                                    T* __restrict__ Rx, T* __restrict__ Ry, T* __restrict__ Rz,
+                                                    unsigned long long* red, int check) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double r_v = 0.0;
+  if (i <= b.nx && j <= b.ny && k <= b.nz) {
+    const long long q = cidx(b, i, j, k);
+    const long long px = b.px, pxy = b.pxy;
+    const bool fx = i > 0 && i < b.nx && j < b.ny && k < b.nz;
+    const bool fy = j > 0 && j < b.ny && i < b.nx && k < b.nz;
+    const bool fz = k > 0 && k < b.nz && i < b.nx && j < b.ny;
+    T Fx = T(0), Fy = T(0), Fz = T(0), Rx1 = T(0), Ry1 = T(0), Rz1 = T(0), Vx1 = T(0), Vy1 = T(0), Vz1 = T(0);
+    if (fx) {
+      Fx = in.rfx[q] + (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
+           (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - 1]) * c.rdx;
+      Rx1 = Fx * c.rrho_i + c.damp_x * Rx[q];
+      Vx1 = Vx[q] + in.dtv_x[q] * Rx1;
+    }
+    if (fy) {
+      Fy = in.rfy[q] + (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
+           (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - px]) * c.rdy;
+      Ry1 = Fy * c.rrho_i + c.damp_y * Ry[q];
+      Vy1 = Vy[q] + in.dtv_y[q] * Ry1;
+    }
+    if (fz) {
+      Fz = in.rfz[q] + (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
+           (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.Pt1[q] - in.Pt1[q - pxy]) * c.rdz;
+      Rz1 = Fz * c.rrho_i + c.damp_z * Rz[q];
+      Vz1 = Vz[q] + in.dtv_z[q] * Rz1;
+    }
+    if (fx) { Rx[q] = Rx1; Vx[q] = Vx1; }
+    if (fy) { Ry[q] = Ry1; Vy[q] = Vy1; }
+    if (fz) { Rz[q] = Rz1; Vz[q] = Vz1; }
+    if (check) r_v = fmax((double)tabs(Fx), fmax((double)tabs(Fy), (double)tabs(Fz)));
+  }
+  if (check) block_max_atomic(r_v, red + RED_V);
 }
 
 // (iv) u <- u + delta (FP64 += FP32 correction).
@@ -309,18 +309,24 @@ void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const 
   k_mix_res_faces<<<g, bl, 0, s>>>(b, c, in, rfx, rfy, rfz, red);
 }
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out) {
-  (void)c;
-  k_mix_coef<<<g, bl, 0, s>>>(b, mu, out);
+  k_mix_coef<<<g, bl, 0, s>>>(b, c, mu, out);
 }
 void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u) {
   k_mix_update<<<g, bl, 0, s>>>(b, u);
 }
 template <class T>
-void corr_iter(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrIn<T>& in,
-               const CorrOut<T>& out, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check) {
-  k_corr<T><<<g, bl, 0, s>>>(b, c, in, out, Rx, Ry, Rz, red, check);
+void corr_cells(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrIn<T>& in,
+                const CorrCellOut<T>& out, unsigned long long* red, int check) {
+  k_corr_cells<T><<<g, bl, 0, s>>>(b, c, in, out, red, check);
 }
-template void corr_iter<float>(dim3, dim3, cudaStream_t, Box, const CorrCoef<float>&, const CorrIn<float>&,
-                               const CorrOut<float>&, float*, float*, float*, unsigned long long*, int);
+template <class T>
+void corr_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrFaceIn<T>& in, T* Vx,
+                T* Vy, T* Vz, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check) {
+  k_corr_faces<T><<<g, bl, 0, s>>>(b, c, in, Vx, Vy, Vz, Rx, Ry, Rz, red, check);
+}
+template void corr_cells<float>(dim3, dim3, cudaStream_t, Box, const CorrCoef<float>&, const CorrIn<float>&,
+                                const CorrCellOut<float>&, unsigned long long*, int);
+template void corr_faces<float>(dim3, dim3, cudaStream_t, Box, const CorrCoef<float>&, const CorrFaceIn<float>&,
+                                float*, float*, float*, float*, float*, float*, unsigned long long*, int);
 
 }  // namespace pt
