@@ -41,10 +41,10 @@ KERNEL_BYTES_PER_CELL = {
     # faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
     "k_lean_cells": 36 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
     "k_lean_begin": 11 * 8,
-    # mixed precision, FP32 correction iterations: cells reads 15 arrays (3 dV, dPt, dPf, cc, k,
-    # iden_pt, iden_pf, r_pt, r_pf, cm2, 3 em2) and writes 8 (dPt, dPf, 6 stresses); faces reads 19
-    # (6 stresses, dPt, 3 dtv, 3 r_F, 3 R, 3 dV) and writes 6 (3 R, 3 dV)
-    "k_corr_cells": 23 * 4, "k_corr_faces": 25 * 4,
+    # mixed precision, FP32 correction iterations: cells reads 17 arrays (3 dV, dPt, dPf, cc, k,
+    # idtp, iden_pt, idtf, iden_pf, r_pt, r_pf, cm2, 3 em2) and writes 8 (dPt, dPf, 6 stresses);
+    # faces reads 19 (6 stresses, dPt, 3 dtv, 3 r_F, 3 R, 3 dV) and writes 6 (3 R, 3 dV)
+    "k_corr_cells": 25 * 4, "k_corr_faces": 25 * 4,
     # adjoint PT iteration: cells reads 26 arrays and writes 10, faces reads 17 and writes 6
     "k_adj_cells": 36 * 8, "k_adj_faces": 23 * 8,
 }
@@ -52,15 +52,17 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2}
 # FP64 thread instructions (DFMA + DADD + DMUL) and flops (DFMA x 2 + DADD + DMUL) per cell and
 # launch from one ncu capture of the kernel (profiles/k_lean_fp64_191.md, k_adj_cells_95.md,
 # k_centres_fp64_stepwise_191.md); a kernel missing here has no current count.
-KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 123.7, "k_adj_cells": 76.5, "k_centres": 152.0}
-KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 183.5, "k_adj_cells": 115.2, "k_centres": 237.0}
+KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 114.8, "k_lean_faces": 35.8, "k_adj_cells": 76.5,
+                             "k_centres": 152.0}
+KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 168.7, "k_lean_faces": 52.7, "k_adj_cells": 115.2,
+                              "k_centres": 237.0}
 # The FP64 pipe issues at most 304 thread-instructions per GPU clock (2 per SM; ncu's
 # sm__inst_executed_pipe_fp64 peak on this machine's GB300), i.e. 629 G/s at 2.07 GHz.
 FP64_PIPE_INST_PER_CLK = 304.0
 # FP32 kernels are bound by HBM (their FP32 work is far below the FP32 pipe's rate).
 # DRAM bytes per cell and launch (dram__bytes_read.sum + dram__bytes_write.sum) from the same
 # captures; the 191^3 case's per-cell figure scales with the cells of a launch.
-KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 287.2, "k_lean_faces": 181.0, "k_centres": 150.6,
+KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 286.8, "k_lean_faces": 180.6, "k_centres": 150.6,
                            "k_adj_cells": 270.5}
 
 

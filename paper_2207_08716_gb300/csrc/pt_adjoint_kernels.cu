@@ -233,42 +233,46 @@ __global__ void __launch_bounds__(256) k_adj_faces(Box b, AdjCoef c, AdjFaceIn i
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
-    if (i > 0 && i < b.nx && j < b.ny && k < b.nz) {
-      const double F = (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
-                       (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.lP1[q] - in.lP1[q - 1]) * c.rdx +
-                       in.bfx[q] * (in.mL[q - 1] + in.mL[q]);
+    const bool fx = i > 0 && i < b.nx && j < b.ny && k < b.nz;
+    const bool fy = j > 0 && j < b.ny && i < b.nx && k < b.nz;
+    const bool fz = k > 0 && k < b.nz && i < b.nx && j < b.ny;
+    double Fx = 0.0, Fy = 0.0, Fz = 0.0, Rx1 = 0.0, Ry1 = 0.0, Rz1 = 0.0, Lx1 = 0.0, Ly1 = 0.0, Lz1 = 0.0;
+    if (fx) {
+      Fx = (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
+           (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.lP1[q] - in.lP1[q - 1]) * c.rdx +
+           in.bfx[q] * (in.mL[q - 1] + in.mL[q]);
       if (in.update) {
-        const double R = F * c.rrho_i + c.damp_x * Rx[q];
-        Rx[q] = R;
-        Lx[q] += c.dtauv * R;
+        Rx1 = Fx * c.rrho_i + c.damp_x * Rx[q];
+        Lx1 = Lx[q] + c.dtauv * Rx1;
       }
-      if (in.rx) in.rx[q] = F;
-      r_v = fabs(F);
     }
-    if (j > 0 && j < b.ny && i < b.nx && k < b.nz) {
-      const double F = (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
-                       (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.lP1[q] - in.lP1[q - px]) * c.rdy +
-                       in.bfy[q] * (in.mL[q - px] + in.mL[q]);
+    if (fy) {
+      Fy = (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
+           (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.lP1[q] - in.lP1[q - px]) * c.rdy +
+           in.bfy[q] * (in.mL[q - px] + in.mL[q]);
       if (in.update) {
-        const double R = F * c.rrho_i + c.damp_y * Ry[q];
-        Ry[q] = R;
-        Ly[q] += c.dtauv * R;
+        Ry1 = Fy * c.rrho_i + c.damp_y * Ry[q];
+        Ly1 = Ly[q] + c.dtauv * Ry1;
       }
-      if (in.ry) in.ry[q] = F;
-      r_v = fmax(r_v, fabs(F));
     }
-    if (k > 0 && k < b.nz && i < b.nx && j < b.ny) {
-      const double F = (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
-                       (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.lP1[q] - in.lP1[q - pxy]) * c.rdz +
-                       in.bfz[q] * (in.mL[q - pxy] + in.mL[q]);
+    if (fz) {
+      Fz = (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
+           (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.lP1[q] - in.lP1[q - pxy]) * c.rdz +
+           in.bfz[q] * (in.mL[q - pxy] + in.mL[q]);
       if (in.update) {
-        const double R = F * c.rrho_i + c.damp_z * Rz[q];
-        Rz[q] = R;
-        Lz[q] += c.dtauv * R;
+        Rz1 = Fz * c.rrho_i + c.damp_z * Rz[q];
+        Lz1 = Lz[q] + c.dtauv * Rz1;
       }
-      if (in.rz) in.rz[q] = F;
-      r_v = fmax(r_v, fabs(F));
     }
+    if (in.update) {
+      if (fx) { Rx[q] = Rx1; Lx[q] = Lx1; }
+      if (fy) { Ry[q] = Ry1; Ly[q] = Ly1; }
+      if (fz) { Rz[q] = Rz1; Lz[q] = Lz1; }
+    }
+    if (fx && in.rx) in.rx[q] = Fx;
+    if (fy && in.ry) in.ry[q] = Fy;
+    if (fz && in.rz) in.rz[q] = Fz;
+    r_v = fmax(fabs(Fx), fmax(fabs(Fy), fabs(Fz)));
   }
   if (check) block_max_atomic(r_v, red + RED_V);
 }

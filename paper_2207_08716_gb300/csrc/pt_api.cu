@@ -32,7 +32,7 @@ constexpr size_t kAlign = 256;
 constexpr int kPitchMultiple = 16;
 constexpr int kRefArrays = 23;   // step-by-step path
 constexpr int kLeanArrays = 23;  // extra arrays of the FP64-lean path
-constexpr int kMixArrays = 32;   // FP32 arrays of the mixed-precision path
+constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
 // Default relative drop at which the inner FP32 solves of the mixed-precision path stop. The
 // outer loop's convergence is bound by the log-space Picard relaxation of mu and eta (one
 // update per outer iteration), not by the inner accuracy: a drop of 0.3 per inner solve needs
@@ -90,7 +90,7 @@ struct pt_ctx {
   LeanCoef<double> lcoef;
   // mixed-precision path (precision PT_FP32): FP32 correction problem
   bool mixed;
-  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_iden_pt, *m_iden_pf;
+  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_iden_pt, *m_idtf, *m_iden_pf;
   float *m_cm2, *m_em2_xy, *m_em2_xz, *m_em2_yz;
   float *m_dVx, *m_dVy, *m_dVz, *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
   float *m_txx, *m_tyy, *m_tzz, *m_txy, *m_txz, *m_tyz, *m_dtv_x, *m_dtv_y, *m_dtv_z;
@@ -395,8 +395,8 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   PT_LAUNCH(c, K_PERM, k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[a], c->logk, c->perm, c->rog));
   MixPrepIn pin{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->mu, c->eta, c->perm, c->Pto,
                 c->Pfo, c->txxo, c->tyyo, c->tzzo};
-  MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_iden_pt,
-                  c->m_iden_pf};
+  MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_idtp,
+                  c->m_iden_pt, c->m_idtf, c->m_iden_pf};
   PT_LAUNCH(c, K_MIX_PREP, mix_prepare(gr, bl, c->stream, b, k, pin, pout, c->red));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
@@ -427,8 +427,8 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
     const int check = early_exit && (it % nup) == 0;
     if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
     const CorrIn<float> ci{c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d], c->m_cc, c->m_perm,
-                           c->m_iden_pt, c->m_iden_pf, c->m_rpt, c->m_rpf, c->m_cm2, c->m_em2_xy,
-                           c->m_em2_xz, c->m_em2_yz};
+                           c->m_idtp, c->m_iden_pt, c->m_idtf, c->m_iden_pf, c->m_rpt, c->m_rpf, c->m_cm2,
+                           c->m_em2_xy, c->m_em2_xz, c->m_em2_yz};
     const CorrCellOut<float> co{c->m_dPt[1 - d], c->m_dPf[1 - d], c->m_txx, c->m_tyy, c->m_tzz,
                                 c->m_txy, c->m_txz, c->m_tyz};
     PT_LAUNCH(c, K_CORR_CELLS, corr_cells<float>(gr, bl, c->stream, b, c->ccoef, ci, co, c->red, check));
@@ -587,8 +587,8 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   if (c->mixed) {
     const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
     float** fslots[kMixArrays] = {
-        &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_iden_pt,
-        &c->m_iden_pf, &c->m_cm2, &c->m_em2_xy, &c->m_em2_xz, &c->m_em2_yz, &c->m_dVx, &c->m_dVy, &c->m_dVz, &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0],
+        &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_idtp,
+        &c->m_iden_pt, &c->m_idtf, &c->m_iden_pf, &c->m_cm2, &c->m_em2_xy, &c->m_em2_xz, &c->m_em2_yz, &c->m_dVx, &c->m_dVy, &c->m_dVz, &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0],
         &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz, &c->m_txx, &c->m_tyy, &c->m_tzz, &c->m_txy, &c->m_txz,
         &c->m_tyz, &c->m_dtv_x, &c->m_dtv_y, &c->m_dtv_z};
     for (int s = 0; s < kMixArrays; ++s) *fslots[s] = (float*)(wend + s * fstride);

@@ -8,11 +8,17 @@ namespace pt {
 namespace lean_detail {
 
 // exp(d) - 1 and exp(-d) - 1 from the Taylor series of exp split into its odd part
-// O = d + d^3/3! + ... and even part E = d^2/2! + d^4/4! + ... (both truncated after d^9 /
-// d^8: for |d| <= 2^-6 the first dropped term is below 2^-60 |d|). expm1(d) = E + O,
-// expm1(-d) = E - O.
+// O = d + d^3/3! + ... and even part E = d^2/2! + d^4/4! + ... (truncated after d^5 / d^4 for
+// |d| <= 2^-20 and after d^9 / d^8 for |d| <= 2^-6: in both cases the first dropped term is
+// below 2^-60 |d|). expm1(d) = E + O, expm1(-d) = E - O.
 __device__ inline void expm1_pair(double d, double& em_pos, double& em_neg) {
-  if (fabs(d) <= 0.015625) {
+  if (fabs(d) <= 0x1p-20) {
+    const double d2 = d * d;
+    const double E = d2 * fma(d2, 1.0 / 24.0, 0.5);
+    const double O = d * fma(d2, fma(d2, 1.0 / 120.0, 1.0 / 6.0), 1.0);
+    em_pos = E + O;
+    em_neg = E - O;
+  } else if (fabs(d) <= 0.015625) {
     const double d2 = d * d;
     const double E = d2 * fma(d2, fma(d2, fma(d2, 1.0 / 40320.0, 1.0 / 720.0), 1.0 / 24.0), 0.5);
     const double O = d * fma(d2, fma(d2, fma(d2, fma(d2, 1.0 / 362880.0, 1.0 / 5040.0), 1.0 / 120.0), 1.0 / 6.0), 1.0);

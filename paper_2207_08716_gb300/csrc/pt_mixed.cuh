@@ -11,7 +11,7 @@ struct MixPrepIn {
 };
 struct MixPrepOut {
   double *txx, *tyy, *tzz;                                  // FP64 stresses at u
-  float *r_pt, *r_pf, *cc, *perm, *iden_pt, *iden_pf;
+  float *r_pt, *r_pf, *cc, *perm, *idtp, *iden_pt, *idtf, *iden_pf;
 };
 struct MixFaceIn {
   const double *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt, *phi;
@@ -34,7 +34,7 @@ struct CorrCoef {
 template <class T>
 struct CorrIn {
   const T *Vx, *Vy, *Vz, *Pt, *Pf;                 // current correction dV, dPt, dPf
-  const T *cc, *perm, *iden_pt, *iden_pf, *r_pt, *r_pf, *cm2, *em2_xy, *em2_xz, *em2_yz;
+  const T *cc, *perm, *idtp, *iden_pt, *idtf, *iden_pf, *r_pt, *r_pf, *cm2, *em2_xy, *em2_xz, *em2_yz;
 };
 template <class T>
 struct CorrCellOut {

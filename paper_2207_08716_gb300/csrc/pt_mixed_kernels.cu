@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(256) k_mix_prepare(Box b, Coef c, MixPrepIn in
     out.r_pf[q] = (float)rpf;
     out.cc[q] = (float)cc;
     out.perm[q] = (float)kc;
+    out.idtp[q] = (float)idtp;
     out.iden_pt[q] = (float)(1.0 / (idtp + c.beta_d * c.rdt + cc));
+    out.idtf[q] = (float)idtf;
     out.iden_pf[q] = (float)(1.0 / (idtf + c.beta_d * c.alpha / c.B * c.rdt + cc));
     r_pt = fabs(divVn);
     r_pf = fabs(rpf);
@@ -172,13 +174,11 @@ __global__ void __launch_bounds__(256) k_mix_coef(Box b, Coef c, const double* _
 }
 
 // (iii) one FP32 PT iteration on the correction, cells: edge and centre stresses of dV (no
-// old-stress term, it is in r_F), local-implicit dPt, dPf updates of the linearised Eqs. 17-18
-// with right-hand sides r_Pt, r_Pf and frozen coefficients, written dP' = dP - rho / (1/dtau +
-// d rho/dP). Reads 15 FP32 arrays and writes 8; every load is issued before the first store
-// (the arrays are not declared non-aliasing, so a store would order the loads after it).
+// old-stress term, it is in r_F), local-implicit dPt and dPf updates of the linearised Eqs.
+// 17-18 with right-hand sides r_Pt, r_Pf and frozen coefficients.
 template <class T>
-__global__ void __launch_bounds__(256) k_corr_cells(Box b, CorrCoef<T> c, CorrIn<T> in, CorrCellOut<T> out,
-                                                    unsigned long long* red, int check) {
+__global__ void __launch_bounds__(256) k_corr_cells(Box b, CorrCoef<T> c, CorrIn<T> in,
+                                                    CorrCellOut<T> out, unsigned long long* red, int check) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -186,22 +186,32 @@ __global__ void __launch_bounds__(256) k_corr_cells(Box b, CorrCoef<T> c, CorrIn
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
-    T txy = T(0), txz = T(0), tyz = T(0);
-    if (i > 0 && i < b.nx && j > 0 && j < b.ny && k < b.nz)
-      txy = in.em2_xy[q] * ((in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx);
-    if (i > 0 && i < b.nx && k > 0 && k < b.nz && j < b.ny)
-      txz = in.em2_xz[q] * ((in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx);
-    if (j > 0 && j < b.ny && k > 0 && k < b.nz && i < b.nx)
-      tyz = in.em2_yz[q] * ((in.Vy[q] - in.Vy[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - px]) * c.hrdy);
-    const bool cell = i < b.nx && j < b.ny && k < b.nz;
-    T txx = T(0), tyy = T(0), tzz = T(0), dPt1 = T(0), dPf1 = T(0);
-    if (cell) {
-      const T dPt = in.Pt[q], dPf = in.Pf[q], cc = in.cc[q], rpt = in.r_pt[q], kc = in.perm[q];
+    if (k < b.nz) {
+      T t = T(0);
+      if (i > 0 && i < b.nx && j > 0 && j < b.ny)
+        t = in.em2_xy[q] * ((in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx);
+      out.txy[q] = t;
+    }
+    if (j < b.ny) {
+      T t = T(0);
+      if (i > 0 && i < b.nx && k > 0 && k < b.nz)
+        t = in.em2_xz[q] * ((in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx);
+      out.txz[q] = t;
+    }
+    if (i < b.nx) {
+      T t = T(0);
+      if (j > 0 && j < b.ny && k > 0 && k < b.nz)
+        t = in.em2_yz[q] * ((in.Vy[q] - in.Vy[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - px]) * c.hrdy);
+      out.tyz[q] = t;
+    }
+    if (i < b.nx && j < b.ny && k < b.nz) {
+      const T dPt = in.Pt[q], dPf = in.Pf[q], cc = in.cc[q];
       const T gx = (in.Vx[q + 1] - in.Vx[q]) * c.rdx, gy = (in.Vy[q + px] - in.Vy[q]) * c.rdy;
       const T gz = (in.Vz[q + pxy] - in.Vz[q]) * c.rdz;
       const T divV = gx + gy + gz;
-      const T cpl = c.bd_rdt_a + cc;
-      const T rho_pt = rpt + divV + (c.bd_rdt + cc) * dPt - cpl * dPf;
+      const T cpl = c.bd_rdt_a + cc;                 // beta_d alpha / dt + cc
+      const T rho_pt = in.r_pt[q] + divV + (c.bd_rdt + cc) * dPt - cpl * dPf;
+      const T kc = in.perm[q];
       T sx = T(0), sy = T(0), sz = T(0);
       if (i > 0) sx -= (in.perm[q - 1] + kc) * (dPf - in.Pf[q - 1]);
       if (i < b.nx - 1) sx += (kc + in.perm[q + 1]) * (in.Pf[q + 1] - dPf);
@@ -211,27 +221,21 @@ __global__ void __launch_bounds__(256) k_corr_cells(Box b, CorrCoef<T> c, CorrIn
       if (k < b.nz - 1) sz += (kc + in.perm[q + pxy]) * (in.Pf[q + pxy] - dPf);
       const T divq = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
       const T rho_pf = in.r_pf[q] + divq + (c.bda_B_rdt + cc) * dPf - cpl * dPt;
-      dPt1 = dPt - in.iden_pt[q] * rho_pt;
-      dPf1 = dPf - in.iden_pf[q] * rho_pf;
+      // dP' = dP - dtau rho(dP', ...) solved for dP' (local terms implicit)
+      const T dPt1 = (dPt * in.idtp[q] - (in.r_pt[q] + divV - cpl * dPf)) * in.iden_pt[q];
+      const T dPf1 = (dPf * in.idtf[q] - (in.r_pf[q] + divq - cpl * dPt)) * in.iden_pf[q];
+      out.Pt[q] = dPt1;
+      out.Pf[q] = dPf1;
+      const T third = divV * T(1.0 / 3.0);
+      const T bn = c.beta_n * (rho_pt - in.r_pt[q]);
       const T cm2 = in.cm2[q];
-      const T third = divV * T(1.0 / 3.0), bn = c.beta_n * (rho_pt - rpt);
-      txx = cm2 * (gx - third + bn);
-      tyy = cm2 * (gy - third + bn);
-      tzz = cm2 * (gz - third + bn);
+      out.txx[q] = cm2 * (gx - third + bn);
+      out.tyy[q] = cm2 * (gy - third + bn);
+      out.tzz[q] = cm2 * (gz - third + bn);
       if (check) {
         r_pt = (double)tabs(rho_pt);
         r_pf = (double)tabs(rho_pf);
       }
-    }
-    if (k < b.nz) out.txy[q] = txy;
-    if (j < b.ny) out.txz[q] = txz;
-    if (i < b.nx) out.tyz[q] = tyz;
-    if (cell) {
-      out.Pt[q] = dPt1;
-      out.Pf[q] = dPf1;
-      out.txx[q] = txx;
-      out.tyy[q] = tyy;
-      out.tzz[q] = tzz;
     }
   }
   if (check) {
