@@ -140,7 +140,7 @@ def old_from(st) -> dict:
 def adjoint_params(p: dict) -> dict:
     """The scope of the adjoint: power law off, no weakening, beta_n = 0."""
     q = dict(p)
-    q.update(powerlaw_on=0, R_weak=1.0, beta_n=0.0)
+    q.update(powerlaw_on=0, R_weak=1.0, beta_n=0.0, tau_bg=0.0)
     return q
 
 

@@ -51,16 +51,18 @@ class OracleParams(C.Structure):
         ("rho_i", C.c_double), ("beta_n", C.c_double), ("rel_mu", C.c_double),
         ("rel_eta", C.c_double), ("cfl_v", C.c_double), ("cfl_pf", C.c_double),
         ("dtpt_scale", C.c_double), ("xsi_w", C.c_double), ("mech_on", C.c_int),
+        ("tau_bg", C.c_double),
     ]
 
     @classmethod
     def from_dict(cls, d: dict, mech_on: int = 1) -> "OracleParams":
         p = cls()
         for name, _ in cls._fields_:
-            if name == "mech_on":
+            if name in ("mech_on", "tau_bg"):
                 continue
             setattr(p, name, d[name])
         p.mech_on = int(d.get("mech_on", mech_on))
+        p.tau_bg = float(d.get("tau_bg", 0.0))
         return p
 
 

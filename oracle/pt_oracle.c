@@ -208,7 +208,9 @@ static void pressure_update(const or_params *p, const or_state *s, const double 
  * tau = (tau_o xi + 2 mu (edot + beta_n divVn delta_ij)) / (1 + xi),  xi = mu / (G dtS), with
  * dtS the stress sub-step of the appendix two-phase script;
  * on edges mu and xi are the means of the 4 surrounding centres; boundary-edge shear
- * stresses are zero (free slip). */
+ * stresses are zero (free slip). With a background shear stress (Eqs. 32-33) the xy strain
+ * rate gains tau_bg / (2 mu0) at every xy-edge; on the wall edges the unknown velocity's part
+ * is zero and mu, xi are the means over the centres next to the edge. */
 void or_stress(const or_params *p, double dtS, const double *Vx, const double *Vy, const double *Vz,
                const double *divV, const double *divVn, const double *mu,
                const double *txxo, const double *tyyo, const double *tzzo,
@@ -229,6 +231,7 @@ void or_stress(const or_params *p, double dtS, const double *Vx, const double *V
         tyy[c] = (tyyo[c] * xi + 2.0 * m * (eyy + bn * divVn[c])) / (1.0 + xi);
         tzz[c] = (tzzo[c] * xi + 2.0 * m * (ezz + bn * divVn[c])) / (1.0 + xi);
       }
+  const double ebg = 0.5 * p->tau_bg / p->mu0;   /* background xy strain rate */
 #pragma omp parallel for
   for (int k = 0; k < NZ; ++k)
     for (int j = 0; j <= NY; ++j)
@@ -240,8 +243,20 @@ void or_stress(const or_params *p, double dtS, const double *Vx, const double *V
           const double xi = 0.25 * (mu[C_(i - 1, j - 1, k)] / Gdt + mu[C_(i, j - 1, k)] / Gdt +
                                     mu[C_(i - 1, j, k)] / Gdt + mu[C_(i, j, k)] / Gdt);
           const double e = 0.5 * ((Vx[FX_(i, j, k)] - Vx[FX_(i, j - 1, k)]) / dy +
-                                  (Vy[FY_(i, j, k)] - Vy[FY_(i - 1, j, k)]) / dx);
+                                  (Vy[FY_(i, j, k)] - Vy[FY_(i - 1, j, k)]) / dx) + ebg;
           t = (txyo[EXY_(i, j, k)] * xi + 2.0 * m * e) / (1.0 + xi);
+        } else if (p->tau_bg != 0.0) {
+          /* wall edge: the mean mu over the (two, or at a corner one) centres next to it */
+          double msum = 0.0;
+          int cnt = 0;
+          for (int dj = -1; dj <= 0; ++dj)
+            for (int di = -1; di <= 0; ++di)
+              if (i + di >= 0 && i + di < NX && j + dj >= 0 && j + dj < NY) {
+                msum += mu[C_(i + di, j + dj, k)];
+                cnt += 1;
+              }
+          const double m = msum / cnt, xi = m / Gdt;
+          t = (txyo[EXY_(i, j, k)] * xi + 2.0 * m * ebg) / (1.0 + xi);
         }
         txy[EXY_(i, j, k)] = t;
       }

@@ -41,6 +41,10 @@ typedef struct {
   /* oracle-only switch: 0 freezes the solid (no momentum, V stays as given). Used by the
    * linear-diffusion-limit pin, where the P-Pf system decouples from the mechanics. */
   int mech_on;
+  /* applied horizontal background shear stress (Eqs. 32-33; 0 = none): the background flow
+   * V_bg = (tau_bg / mu0) (y - ly/2) e_x adds tau_bg / (2 mu0) to the xy strain rate at every
+   * xy-edge, the wall edges included, where the unknown velocity's part is zero (free slip) */
+  double tau_bg;
 } or_params;
 
 typedef struct {

@@ -69,7 +69,7 @@ class Phys(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("phi0", "k0", "mu0", "eta0", "R_weak", "n_pow", "tau0",
                                           "alpha", "B", "beta_d", "beta_phi", "G", "rhof_g",
                                           "rhos_g")] + \
-               [("powerlaw_on", C.c_int32), ("compaction_on", C.c_int32)]
+               [("powerlaw_on", C.c_int32), ("compaction_on", C.c_int32), ("tau_bg", C.c_double)]
 
 
 class Num(C.Structure):
@@ -105,7 +105,7 @@ def grid_from(p: dict) -> Grid:
 def phys_from(p: dict) -> Phys:
     ph = Phys()
     for n, _ in Phys._fields_:
-        setattr(ph, n, p[n])
+        setattr(ph, n, p.get(n, 0.0) if n == "tau_bg" else p[n])
     return ph
 
 

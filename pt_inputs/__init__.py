@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "c1_params", "large_params", "gaussian_porosity", "perturbed_centre",
-    "field_shapes", "random_state", "ensemble", "PARAM_KEYS",
+    "field_shapes", "random_state", "ensemble", "PARAM_KEYS", "shear_params", "ellipsoid_porosity",
 ]
 
 # Parameter names as used at both boundaries (C ABI struct members and the oracle's struct).
@@ -34,7 +34,7 @@ PARAM_KEYS = (
     "nx", "ny", "nz", "lx", "ly", "lz",
     # physics
     "phi0", "k0", "mu0", "eta0", "R_weak", "n_pow", "tau0", "alpha", "B", "beta_d", "beta_phi",
-    "G", "rhof_g", "rhos_g", "powerlaw_on", "compaction_on",
+    "G", "rhof_g", "rhos_g", "powerlaw_on", "compaction_on", "tau_bg",
     # numerics
     "dt", "tol", "max_iter", "nup", "damp_x", "damp_y", "damp_z", "rho_i", "beta_n",
     "rel_mu", "rel_eta", "cfl_v", "cfl_pf", "dtpt_scale", "xsi_w",
@@ -50,7 +50,7 @@ def c1_params(nx: int = 32, ny: int | None = None, nz: int | None = None) -> dic
         nx=nx, ny=ny, nz=nz, lx=1.0, ly=1.0, lz=1.0,
         phi0=0.01, k0=1.0, mu0=1.0, eta0=1.0, R_weak=0.01, n_pow=3.0, tau0=0.04,
         alpha=0.9, B=0.89, beta_d=1.3 * beta_phi, beta_phi=beta_phi, G=0.5 / beta_phi,
-        rhof_g=1.0, rhos_g=2.0, powerlaw_on=1, compaction_on=1,
+        rhof_g=1.0, rhos_g=2.0, powerlaw_on=1, compaction_on=1, tau_bg=0.0,
         dt=1e-4 * (32.0 / max(nx, ny, nz)) ** 2, tol=1e-8, max_iter=20000, nup=15,
         damp_x=1.0 - 1.0 / nx, damp_y=1.0 - 1.0 / ny, damp_z=1.0 - 1.0 / nz,
         rho_i=1.0, beta_n=0.0, rel_mu=0.1, rel_eta=0.5,
@@ -169,3 +169,30 @@ def gaussian_random_field(shape, seed: int, corr_len: float = 0.1, std: float = 
     f -= f.mean()
     sd = f.std()
     return f * (std / sd) if sd > 0 else f
+
+
+def shear_params(nx: int = 64, ny: int | None = None, nz: int | None = None, dt: float = 1e-5) -> dict:
+    """The background-shear workload of thesis Art. 1 Section 3.1 (Table 2), scaled down: a
+    30 x 30 x 60 box sheared by tau_bg = 1, K_phi = 333.33 (beta_phi = 3e-3), G = 166.66,
+    decompaction weakening factor R0 = 2000 (bulk viscosity / 2000 where Pf > Pt), n = 3,
+    tau0 = 0.04; drained compressibility 1.3 beta_phi and phi0 = 1e-2 as in the appendix script."""
+    ny = nx if ny is None else ny
+    nz = 2 * nx if nz is None else nz
+    p = c1_params(nx, ny, nz)
+    beta_phi = 1.0 / 333.33
+    p.update(lx=30.0, ly=30.0, lz=60.0, R_weak=1.0 / 2000.0, beta_phi=beta_phi, beta_d=1.3 * beta_phi,
+             G=166.66, tau_bg=1.0, dt=dt)
+    return p
+
+
+def ellipsoid_porosity(p: dict, centre=(0.5, 0.5, 0.2), axes=(14.0, 14.0, 3.5), factor: float = 2.0):
+    """Porosity phi0 with an ellipsoid of `factor` phi0 (Table 2: axis lengths 14 x 14 x 3.5,
+    twice the background porosity), centred at `centre` in fractions of the box (one fifth of
+    the height), sampled at the cell centres; shape (nz, ny, nx)."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    x = (np.arange(nx) + 0.5) * p["lx"] / nx - centre[0] * p["lx"]
+    y = (np.arange(ny) + 0.5) * p["ly"] / ny - centre[1] * p["ly"]
+    z = (np.arange(nz) + 0.5) * p["lz"] / nz - centre[2] * p["lz"]
+    zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
+    r2 = (xx / (0.5 * axes[0])) ** 2 + (yy / (0.5 * axes[1])) ** 2 + (zz / (0.5 * axes[2])) ** 2
+    return np.where(r2 <= 1.0, factor * p["phi0"], p["phi0"])
