@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--fp32-iters", type=int, default=300, help="FP32 iterations per step of the fp32 form")
     ap.add_argument("--batch-n", type=int, default=64, help="instances of the batched form")
     ap.add_argument("--batch-iters", type=int, default=60, help="PT iterations per step of the batched form")
+    ap.add_argument("--workload", choices=("porosity", "shear"), default="porosity",
+                    help="porosity: n^3 box, Gaussian anomaly (the benchmark); shear: the background-shear "
+                         "setup of Table 2 on n x n x 2n cells (30 x 30 x 60 box, ellipsoidal anomaly)")
     ap.add_argument("--adjoint", action="store_true",
                     help="measure the adjoint instead (127^3, 20 steps, checkpoint every 5): forward and "
                          "backward wall time, cost multiple, optional finite-difference check")
@@ -107,14 +110,23 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def workload_params(n: int, iters: int, precision: str = "fp64") -> dict:
-    p = I.large_params(n)
+def workload_params(n: int, iters: int, precision: str = "fp64", workload: str = "porosity") -> dict:
+    p = I.shear_params(n) if workload == "shear" else I.large_params(n)
     p["max_iter"] = iters
     p["precision"] = PRECISIONS[precision]
     return p
 
 
-def workload_name(n: int, iters: int, precision: str = "fp64") -> str:
+def workload_phi(p: dict, seed: int, workload: str = "porosity"):
+    if workload == "shear":
+        return I.ellipsoid_porosity(p)
+    return I.gaussian_porosity(p, centres=(I.perturbed_centre(seed),))
+
+
+def workload_name(n: int, iters: int, precision: str = "fp64", workload: str = "porosity") -> str:
+    if workload == "shear":
+        return (f"two-phase porosity-wave PT solver ({precision}) under background shear (Table 2 setup), "
+                f"{n}x{n}x{2 * n} cells, 30x30x60 box, ellipsoidal anomaly, {iters} PT iterations per step")
     return (f"two-phase porosity-wave PT solver ({precision}), {n}^3 cells, one seed-perturbed "
             f"centred Gaussian anomaly, {iters} PT iterations per physical step")
 
@@ -210,9 +222,9 @@ def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_
     from paper_2207_08716_gb300.solver import PTSolver
 
     n = args.n
-    p = workload_params(n, iters, precision)
+    p = workload_params(n, iters, precision, args.workload)
     seed = M.replica_seed(rank)
-    phi = I.gaussian_porosity(p, centres=(I.perturbed_centre(seed),))
+    phi = workload_phi(p, seed, args.workload)
     stream = torch.cuda.current_stream(dev)
     s = PTSolver(p, phi, device=dev, stream=stream)
     del phi
@@ -246,7 +258,7 @@ def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_
     barrier()
     t = M.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     launches = s.launch_count() - launches0
-    ncell = n ** 3
+    ncell = p["nx"] * p["ny"] * p["nz"]
     pbytes = 4 if precision == "fp32" else 8
     total_iters = steps * iters
     value = world * M.a_eff_bytes(ncell, pbytes) * total_iters / t / 1e9
@@ -462,7 +474,7 @@ def run_native(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.n, head["iters_per_step"], args.precision),
+            "config": {"workload": workload_name(args.n, head["iters_per_step"], args.precision, args.workload),
                        "n": args.n, "iters_per_step": head["iters_per_step"], "precision": args.precision,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (every field >= 0.5 GB), no flush"},

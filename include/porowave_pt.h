@@ -90,6 +90,9 @@ typedef struct {
   double rhos_g;    /* solid density times gravity                                        */
   int32_t powerlaw_on;    /* 0: mu* = mu0 (no power law)                                  */
   int32_t compaction_on;  /* 0: no viscous compaction term (1 / eta = 0)                  */
+  double tau_bg;          /* applied horizontal background shear stress (Eqs. 32-33; 0 =
+                             none): tau_bg / (2 mu0) is added to the xy strain rate on every
+                             xy-edge, the wall edges included (free slip for the unknown V) */
 } pt_phys;
 
 /* Numerical parameters of the PT iteration (Section 2.2 and the appendix two-phase script). */

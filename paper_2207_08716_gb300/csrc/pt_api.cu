@@ -217,6 +217,8 @@ void fill_coef(pt_ctx* c) {
   k.dtaupt_fac = n.dtpt_scale * (1.0 + n.beta_n) / g.nz;
   k.dtaupf_fac = n.cfl_pf * k.h2 * (1.0 + p.beta_d * p.B / p.alpha);
   k.rGdtS = c->dtS > 0 ? 1.0 / (p.G * c->dtS) : 0.0;
+  k.ebg = 0.5 * p.tau_bg / p.mu0;
+  k.bg_on = p.tau_bg != 0.0;
   fill_lean_coef(c);
   fill_corr_coef(c);
 }
@@ -231,6 +233,8 @@ void fill_lean_coef(pt_ctx* c) {
   L.hrdx = 0.5 * k.rdx; L.hrdy = 0.5 * k.rdy; L.hrdz = 0.5 * k.rdz;
   L.hrdx2 = 0.5 * k.rdx * k.rdx; L.hrdy2 = 0.5 * k.rdy * k.rdy; L.hrdz2 = 0.5 * k.rdz * k.rdz;
   L.buoy_dz = (k.rhof_g - k.rho_bg_g) * dz;
+  L.ebg = k.ebg;
+  L.bg_on = k.bg_on;
   L.bd_rdt = k.beta_d * k.rdt;
   L.bda_B_rdt = k.beta_d * k.alpha / k.B * k.rdt;
   L.alpha = k.alpha;

@@ -32,7 +32,22 @@ struct Coef {
   double dtaupt_fac;           // dtpt_scale (1 + beta_n) / nz:     dtau_Pt = dtaupt_fac * mu
   double dtaupf_fac;           // cfl_pf h^2 (1 + beta_d B / alpha): dtau_Pf = dtaupf_fac / kmax
   double rGdtS;                // 1 / (G dtS): xi = mu / (G dtS)
+  double ebg;                  // background xy strain rate tau_bg / (2 mu0) (Eqs. 32-33)
+  int bg_on;                   // tau_bg != 0: wall xy-edges carry the background stress
 };
+
+// Mean shear viscosity over the centres next to the xy-edge with box index q = (i, j, .)
+// that lie inside the grid (four inside, two on a wall, one in a corner), in a fixed order.
+template <class T>
+__device__ inline double edge_mean_mu_xy(const Box& b, const T* mu, long long q, int i, int j) {
+  double s = 0.0;
+  int n = 0;
+  if (i > 0 && j > 0) { s += (double)mu[q - 1 - b.px]; ++n; }
+  if (i < b.nx && j > 0) { s += (double)mu[q - b.px]; ++n; }
+  if (i > 0 && j < b.ny) { s += (double)mu[q - 1]; ++n; }
+  if (i < b.nx && j < b.ny) { s += (double)mu[q]; ++n; }
+  return s / n;
+}
 
 __host__ __device__ inline long long cidx(const Box& b, int i, int j, int k) {
   return (long long)i + (long long)b.px * j + b.pxy * k;

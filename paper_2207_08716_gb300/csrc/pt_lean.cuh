@@ -20,6 +20,8 @@ struct LeanCoef {
   T ifac_pf;                    // 1 / (cfl_pf h^2 (1 + beta_d B / alpha)): 1/dtau_Pf = kmax * ifac_pf
   T rrho_i, damp_x, damp_y, damp_z;
   int compaction_on, powerlaw_on;
+  T ebg;                        // background xy strain rate tau_bg / (2 mu0) (Eqs. 32-33)
+  int bg_on;                    // tau_bg != 0: wall xy-edges carry the background stress
   // Picard and coefficient refresh run in FP64
   double mu0, eta0, tau0, n_pow, rel_mu, rel_eta, R_weak;
   double rGdtS, dtaupt_fac, dtauv_fac;

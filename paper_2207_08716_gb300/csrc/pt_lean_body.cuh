@@ -84,7 +84,9 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     T t_xy = T(0), t_xz = T(0), t_yz = T(0);
     if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
       const T e = (in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx;
-      t_xy = in.toa_xy[q] + in.em2_xy[q] * e;
+      t_xy = in.toa_xy[q] + in.em2_xy[q] * e;   // toa_xy holds the background part too
+    } else if (k < b.nz && c.bg_on) {   // wall xy-edge under background shear (Eqs. 32-33)
+      t_xy = in.toa_xy[q];
     }
     if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
       const T e = (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx;
@@ -291,7 +293,13 @@ __device__ __forceinline__ void lean_coef_point(const Box& b, const LeanCoef<T>&
     const double m = 0.25 * ((double)in.mu[q - 1 - px] + in.mu[q - px] + in.mu[q - 1] + in.mu[q]);
     const double s = 1.0 / (1.0 + m * rG);
     out.em2_xy[q] = (T)(2.0 * m * s);
-    out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s));
+    // the background shear's stress 2 mu/(1+xi) tau_bg/(2 mu0) (Eqs. 32-33) joins the old-stress part
+    out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
+  } else if (k < b.nz && c.bg_on) {   // wall xy-edges carry the background stress
+    const double m = edge_mean_mu_xy(b, in.mu, q, i, j);
+    const double s = 1.0 / (1.0 + m * rG);
+    out.em2_xy[q] = (T)(2.0 * m * s);
+    out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
   }
   if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
     const double m = 0.25 * ((double)in.mu[q - 1 - pxy] + in.mu[q - pxy] + in.mu[q - 1] + in.mu[q]);

@@ -5,7 +5,8 @@
 //   k_perm      k = k0 e^logk (phi/phi0)^3 (Eq. 23), rho g - rho_BG g (Eq. 27)   from phi^k
 //   k_centres   div V, numerical div V (Eq. 17), Pt^{k+1}, Pf^{k+1} local-implicit (Eqs. 17-18
 //               with div qD from Eq. 20), normal deviatoric stresses (Eq. 21)
-//   k_edges     shear stresses on edges (Eq. 21), zero on boundary edges (free slip)
+//   k_edges     shear stresses on edges (Eq. 21), zero on boundary edges (free slip) unless a
+//               background shear stress is applied (Eqs. 32-33)
 //   k_porosity  phi^{k+1} = 1 - exp(L), L from Eq. 22 in log(1 - phi) form
 //   k_faces     momentum residual (Eq. 19) with Pt^{k+1}, damped R, V^{k+1} = V + dtau R
 //   k_picard    every nup-th iteration: mu, eta towards Eqs. 24-26, log-space relaxation
@@ -126,13 +127,17 @@ __global__ void k_edges(Box b, Coef c, EdgeIn in, EdgeOut out) {
   if (i > b.nx || j > b.ny || k > b.nz) return;
   const long long q = cidx(b, i, j, k);
   const long long px = b.px, pxy = b.pxy;
-  if (k < b.nz) {  // xy-edge (i, j, k)
+  if (k < b.nz) {  // xy-edge (i, j, k); the background shear adds ebg to the strain rate
     double t = 0.0;
     if (i > 0 && i < b.nx && j > 0 && j < b.ny) {
       const double m = 0.25 * (in.mu[q - 1 - px] + in.mu[q - px] + in.mu[q - 1] + in.mu[q]);
       const double xi = m * c.rGdtS;
-      const double e = 0.5 * ((in.Vx[q] - in.Vx[q - px]) * c.rdy + (in.Vy[q] - in.Vy[q - 1]) * c.rdx);
+      const double e = 0.5 * ((in.Vx[q] - in.Vx[q - px]) * c.rdy + (in.Vy[q] - in.Vy[q - 1]) * c.rdx) + c.ebg;
       t = (in.txyo[q] * xi + 2.0 * m * e) / (1.0 + xi);
+    } else if (c.bg_on) {   // wall edge: background part only
+      const double m = edge_mean_mu_xy(b, in.mu, q, i, j);
+      const double xi = m * c.rGdtS;
+      t = (in.txyo[q] * xi + 2.0 * m * c.ebg) / (1.0 + xi);
     }
     out.txy[q] = t;
   }
