@@ -23,15 +23,19 @@ def lib_path() -> str:
     return _LIB
 
 
+_RX_SRC = os.path.join(_HERE, "rx_oracle.c")
+_RX_HDR = os.path.join(_HERE, "rx_oracle.h")
+
+
 def build(force: bool = False) -> str:
-    """Compile pt_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    """Compile pt_oracle.c and rx_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_LIB) or
-             os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _HDR, _RX_SRC, _RX_HDR))
+    stale = not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, _SRC, _RX_SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB

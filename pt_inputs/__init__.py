@@ -26,6 +26,7 @@ import numpy as np
 __all__ = [
     "c1_params", "large_params", "gaussian_porosity", "perturbed_centre",
     "field_shapes", "random_state", "ensemble", "PARAM_KEYS", "shear_params", "ellipsoid_porosity",
+    "rx_params", "rx_initial",
 ]
 
 # Parameter names as used at both boundaries (C ABI struct members and the oracle's struct).
@@ -196,3 +197,34 @@ def ellipsoid_porosity(p: dict, centre=(0.5, 0.5, 0.2), axes=(14.0, 14.0, 3.5), 
     zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
     r2 = (xx / (0.5 * axes[0])) ** 2 + (yy / (0.5 * axes[1])) ** 2 + (zz / (0.5 * axes[2])) ** 2
     return np.where(r2 <= 1.0, factor * p["phi0"], p["phi0"])
+
+
+def rx_params(nx: int = 32, ny: int | None = None, nz: int | None = None, Da: float = 100.0,
+              dt: float = 1e-6) -> dict:
+    """Reactive porosity-wave workload of thesis Art. 3 (appendix A.6 values, nondimensional in
+    the compaction length, compaction pressure and viscous time): box lz = 50, lx = ly = lz / 4
+    (nz = 4 nx by default), Deborah number 1e-3 (beta_d = 1e-3), beta_s = 11/12 beta_d,
+    beta_f = 6 beta_d, rho_s = 1.5, rho_f = 0.5, g = 1, Clapeyron slope -1 (d Xs_eq / d Pf = -0.2),
+    Delta X = 3, Xs_max = 0.05, phi0 = 0.01, Damkoehler number Da (reaction time 1 / Da)."""
+    ny = nx if ny is None else ny
+    nz = 4 * nx if nz is None else nz
+    beta_d = 1e-3
+    return dict(nx=nx, ny=ny, nz=nz, lx=12.5, ly=12.5, lz=50.0, phi0=0.01, k0=1.0, eta=1.0,
+                rhof=0.5, rhos=1.5, g=1.0, beta_d=beta_d, beta_s=beta_d * 11.0 / 12.0, beta_f=6.0 * beta_d,
+                beta_x=-0.2, dX=3.0, xs_max=0.05, tau=1.0 / Da, dt=dt, tol=2e-8, cfl_div=16.1,
+                pf_scale=10.0, max_iter=20000, nup=10)
+
+
+def rx_initial(p: dict):
+    """Two vertically stacked Gaussian porosity anomalies (amplitudes 1.5 phi0 at 0.1 lz and
+    0.75 phi0 at 0.23 lz, widths 0.12 lx horizontally and 0.03 lz vertically) on phi0, Xs at
+    half its maximum, zero fluid pressure: (Pf, phi, Xs), each (nz, ny, nx)."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    x = (np.arange(nx) + 0.5) * p["lx"] / nx - 0.5 * p["lx"]
+    y = (np.arange(ny) + 0.5) * p["ly"] / ny - 0.5 * p["ly"]
+    z = (np.arange(nz) + 0.5) * p["lz"] / nz
+    zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
+    rh, rv = 0.12 * p["lx"], 0.03 * p["lz"]
+    g = lambda zc: np.exp(-(xx / rh) ** 2 - (yy / rh) ** 2 - ((zz - zc * p["lz"]) / rv) ** 2)
+    phi = p["phi0"] + 1.5 * p["phi0"] * g(0.1) + 0.75 * p["phi0"] * g(0.23)
+    return np.zeros_like(phi), phi, np.full_like(phi, 0.5 * p["xs_max"])
