@@ -95,6 +95,10 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=20)
     ap.add_argument("--adjoint-ckpt", default="5,1", help="checkpoint spacings to measure (comma list)")
     ap.add_argument("--adjoint-fd", type=int, default=0, help="finite-difference directions to check")
+    ap.add_argument("--reactive", action="store_true",
+                    help="measure the reactive porosity-wave solver (Art. 3) instead: T_eff with A_eff = 7 N p")
+    ap.add_argument("--rx-n", type=int, default=255, help="reactive grid n x n x 4n")
+    ap.add_argument("--rx-iters", type=int, default=100, help="PT iterations per physical step (reactive)")
     ap.add_argument("--batched-converge", action="store_true",
                     help="run one step of the batched ensemble to convergence and report p50/p99 "
                          "time-to-converge (minutes of GPU time) instead of the throughput bench")
@@ -433,6 +437,56 @@ def measure_adjoint(args, dev) -> dict:
     return out
 
 
+def measure_reactive(args, dev) -> dict:
+    """Reactive porosity-wave solver (thesis Art. 3; appendix A.6 parameters, Da = 100,
+    dt = 1e-6) on n x n x 4n cells: `--steps` physical steps of `--rx-iters` PT iterations after
+    `--warmup` steps, FP32 (the thesis's precision for this solver) and FP64; T_eff = 7 N p / t_it
+    (3 unknowns read and written, 1 known field read, Art. 3); the fused iteration kernel moves
+    10 arrays per cell (Pf, phi with neighbours, Xs, 3 old-step fields read; Pf, phi, Xs written)."""
+    import torch
+    from paper_2207_08716_gb300 import native as N
+    from paper_2207_08716_gb300.solver import RXSolver
+
+    n = args.rx_n
+    out = {}
+    for prec, pbytes in (("fp32", 4), ("fp64", 8)):
+        p = I.rx_params(n)
+        p["precision"] = N.PT_FP32 if prec == "fp32" else N.PT_FP64
+        Pf, phi, Xs = I.rx_initial(p)
+        s = RXSolver(p, Pf, phi, Xs, device=dev)
+        del Pf, phi, Xs
+        for _ in range(args.warmup):
+            s.iterate(args.rx_iters)
+        torch.cuda.synchronize(dev)
+        clocks = M.ClockSampler(dev.index or 0)
+        clocks.start()
+        l0 = s.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(args.steps):
+            s.iterate(args.rx_iters)
+        e1.record(s.stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        t = e0.elapsed_time(e1) / 1e3
+        ncell = p["nx"] * p["ny"] * p["nz"]
+        iters = args.steps * args.rx_iters
+        t_it = t / iters
+        hbm, hbm_kind = peaks()
+        kern_gbs = 10 * pbytes * ncell / t_it / 1e9
+        out[prec] = {"value": 7 * pbytes * ncell / t_it / 1e9, "unit": "GB/s", "t_it_ms": t_it * 1e3,
+                     "it_per_s": 1.0 / t_it, "cells": ncell, "grid": [p["nx"], p["ny"], p["nz"]],
+                     "gpu_launches": s.launch_count() - l0, "clocks": clk,
+                     "roofline": {"kernel": "k_rx_iter (whole step, begin/end and checks included)",
+                                  "bound": "hbm", "achieved": kern_gbs, "peak": hbm, "unit": "GB/s",
+                                  "frac": kern_gbs / hbm, "traffic": None,
+                                  "algorithmic_bytes_per_cell": 10 * pbytes}}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -443,6 +497,16 @@ def run_native(args):
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl", device_id=dev)
 
+    if args.reactive:
+        if rank == 0:
+            r = measure_reactive(args, dev)
+            print(json.dumps({"metric": "reactive porosity-wave solver T_eff (A_eff = 7 N p)",
+                              "value": r["fp32"]["value"], "unit": "GB/s", "dtype": "f32",
+                              "config": {"workload": f"reactive porosity waves (Art. 3, Da = 100), "
+                                                     f"{args.rx_n}x{args.rx_n}x{4 * args.rx_n} cells, "
+                                                     f"{args.rx_iters} PT iterations per step"},
+                              "forms": r}), flush=True)
+        return 0
     if args.adjoint:
         if rank == 0:
             r = measure_adjoint(args, dev)

@@ -1,0 +1,74 @@
+/* porowave_rx.h — C ABI of the GB300 reactive porosity-wave solver (thesis Art. 3, Eqs. 8-10;
+ * the pseudo-transient form of its appendix A.6 script). Fluid pressure Pf (effective pressure
+ * -Pf), porosity phi and the mass fraction Xs of volatiles bound to the solid are advanced by
+ * implicit physical steps of length dt, each iterated to its fixed point by one fused
+ * pseudo-transient kernel per iteration:
+ *   Xs_eq = clamp(beta_x Pf + Xs_max / 2, 0, Xs_max),  dXs/dt = (Xs_eq - Xs) / tau   (Eqs. 4, 10)
+ *   beta_P dPf/dt = -div qD - Pf / (eta (1 - phi)) + S_r (1 - phi)(1 + dX)/(1 - Xs) dXs/dt (Eq. 8)
+ *   dphi/dt = (1 - phi) (beta_phi dPf/dt + Pf / (eta (1 - phi)) - (1 + dX)/(1 - Xs) dXs/dt) (Eq. 9)
+ * qD = -k0 (phi/phi0)^3 (grad Pf - rho_f g e_z) with no flux through the walls,
+ * beta_P = phi beta_f + beta_d - (1 + phi) beta_s, beta_phi = beta_d - beta_s / (1 - phi),
+ * S_r = 1 - rho_s / (rho_f (1 + dX)); the Pf update takes the cell's own compaction and
+ * linearised reaction terms implicitly, Xs is updated local-implicitly; convergence when the
+ * one-iteration change max(|dphi|, |dPf| / pf_scale, |dXs|) of an nup-th iteration is < tol.
+ * All pointers are device pointers in the padded box layout of porowave_pt.h (pt_pitch_x,
+ * pt_field_elems; only the cell entries are used); every call is stream-ordered on the
+ * context's stream and returns after its work is done. Errors: PT_EINVAL, PT_ESPACE,
+ * PT_ECUDA; rx_step returns PT_ENOTCONV at the cap and PT_ENAN for a non-finite change. */
+#ifndef POROWAVE_RX_H
+#define POROWAVE_RX_H
+
+#include "porowave_pt.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rx_ctx rx_ctx;
+
+/* Physical parameters, nondimensional (compaction length, compaction pressure, viscous time). */
+typedef struct {
+  double phi0;      /* background porosity of k = k0 (phi / phi0)^3          */
+  double k0;        /* permeability over fluid viscosity                      */
+  double eta;       /* bulk viscosity                                         */
+  double rhof;      /* fluid density                                          */
+  double rhos;      /* solid density                                          */
+  double g;         /* gravity along -z                                       */
+  double beta_d, beta_s, beta_f;  /* drained, solid, fluid compressibility    */
+  double beta_x;    /* d Xs_eq / d Pf (its sign is the Clapeyron slope's)     */
+  double dX;        /* solid density change with Xs (Delta X)                 */
+  double xs_max;    /* largest mass fraction of volatiles in the solid        */
+  double tau;       /* reaction time (1 / Damkoehler number)                  */
+} rx_phys;
+
+typedef struct {
+  double dt;        /* physical time step (> 0)                                          */
+  double tol;       /* convergence on the one-iteration change                           */
+  double cfl_div;   /* pseudo step dtau = min(d)^2 / max(k / beta_P) / cfl_div (> 0)     */
+  double pf_scale;  /* Pf's divisor in the change norm (> 0)                             */
+  int32_t max_iter; /* iteration cap per physical step                                   */
+  int32_t nup;      /* check (change norm, pseudo-step refresh) every nup-th iteration   */
+  int32_t precision;/* PT_FP64 or PT_FP32 (iterations in single precision, as the thesis
+                       ran this solver; the caller's fields stay FP64)                    */
+} rx_num;
+
+/* Caller-owned device fields (box layout): unknowns and the rate dPf/dt of the last iterate. */
+typedef struct {
+  double *Pf, *phi, *Xs, *R;
+} rx_fields;
+
+size_t rx_workspace_size(const pt_grid *grid, const rx_num *num);
+int rx_init(rx_ctx **ctx, const pt_grid *grid, const rx_phys *phys, const rx_num *num,
+            const rx_fields *fields, void *workspace, size_t bytes, void *stream);
+/* One physical step to convergence (rep->iters, rep->res_v = last change norm). */
+int rx_step(rx_ctx *ctx, pt_report *rep);
+/* One physical step of exactly niter iterations (no convergence exit; rep as rx_step). */
+int rx_iterate(rx_ctx *ctx, int32_t niter, pt_report *rep);
+/* Launches of the library's kernels so far (benchmark accounting). */
+long long rx_launch_count(const rx_ctx *ctx);
+void rx_destroy(rx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

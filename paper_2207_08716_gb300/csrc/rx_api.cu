@@ -1,0 +1,245 @@
+// rx_api.cu — host side of the reactive porosity-wave C ABI (include/porowave_rx.h).
+//
+// A context keeps the iterate in the workspace in the iteration type (FP64 or FP32): the
+// caller's FP64 fields are read at the start of each physical step and written back at its
+// end. Per step: old-step copies, the first pseudo step from max k / beta_P, then fused
+// iterations (ping-pong of Pf, phi, Xs); every nup-th iteration reads the change norm and
+// max k / beta_P of the new porosity (pseudo step of the next iterations) back to the host.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "porowave_rx.h"
+#include "rx.cuh"
+
+using namespace pt;
+
+struct rx_ctx {
+  Box box;
+  rx_phys phys;
+  rx_num num;
+  cudaStream_t stream;
+  rx_fields f;                       // caller's FP64 fields
+  bool fp32;
+  RxCoef<double> cd;
+  RxCoef<float> cf;
+  void* Pf[2];                       // iteration-type arrays (double* or float*)
+  void* phi[2];
+  void* Xs[2];
+  void *Pf_o, *phi_o, *Xs_o, *R;
+  unsigned long long* red;
+  unsigned long long* h_red;
+  double hmin2;
+  long long launches;
+};
+
+namespace {
+
+constexpr size_t kRxAlign = 256;
+constexpr int kRxArrays = 10;        // Pf, phi, Xs (x2), Pf_o, phi_o, Xs_o, R
+
+size_t rx_align(size_t x) { return (x + kRxAlign - 1) / kRxAlign * kRxAlign; }
+
+bool rx_box(const pt_grid* g, Box* b) {
+  const size_t n = pt_field_elems(g);
+  if (n == 0) return false;
+  b->nx = g->nx;
+  b->ny = g->ny;
+  b->nz = g->nz;
+  b->px = pt_pitch_x(g);
+  b->pxy = (long long)b->px * (g->ny + 1);
+  b->n = (long long)n;
+  return true;
+}
+
+template <class T>
+void fill(RxCoef<T>& c, const pt_grid& g, const rx_phys& p, const rx_num& n) {
+  c.rdx = (T)(g.nx / g.lx);
+  c.rdy = (T)(g.ny / g.ly);
+  c.rdz = (T)(g.nz / g.lz);
+  c.rhofg = (T)(p.rhof * p.g);
+  c.rphi0 = (T)(1.0 / p.phi0);
+  c.k0 = (T)p.k0;
+  c.reta = (T)(1.0 / p.eta);
+  c.beta_d = (T)p.beta_d;
+  c.beta_s = (T)p.beta_s;
+  c.beta_f = (T)p.beta_f;
+  c.beta_x = (T)p.beta_x;
+  c.half_xs = (T)(0.5 * p.xs_max);
+  c.xs_max = (T)p.xs_max;
+  c.rtau = (T)(1.0 / p.tau);
+  c.dt = (T)n.dt;
+  c.rdt = (T)(1.0 / n.dt);
+  c.dt_tau = (T)(n.dt / p.tau);
+  c.r1dt_tau = (T)(1.0 / (1.0 + n.dt / p.tau));
+  const double sr = 1.0 - p.rhos / (p.rhof * (1.0 + p.dX));
+  c.sr_opdx = (T)(sr * (1.0 + p.dX));
+  c.opdx = (T)(1.0 + p.dX);
+  c.pf_iscale = (T)(1.0 / n.pf_scale);
+}
+
+bool num_ok(const rx_num* n) {
+  return n && n->dt > 0 && std::isfinite(n->dt) && n->tol >= 0 && n->cfl_div > 0 && n->pf_scale > 0 &&
+         n->max_iter >= 1 && n->nup >= 1 && (n->precision == PT_FP64 || n->precision == PT_FP32);
+}
+
+bool phys_ok(const rx_phys* p) {
+  return p && p->phi0 > 0 && p->k0 > 0 && p->eta > 0 && p->rhof > 0 && p->tau > 0 && p->xs_max > 0 &&
+         p->dX > -1.0;
+}
+
+int status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
+
+// max k / beta_P from the reduction block (after a synchronising read) -> pseudo step
+int read_red(rx_ctx* c, double* change, double* kb) {
+  cudaError_t e = cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  std::memcpy(change, &c->h_red[RED_V], sizeof(double));
+  std::memcpy(kb, &c->h_red[RED_MUMAX], sizeof(double));
+  return PT_OK;
+}
+
+double pseudo_step(const rx_ctx* c, double kb) { return c->hmin2 / kb / c->num.cfl_div; }
+
+template <class T>
+const RxCoef<T>& coef_of(const rx_ctx* c);
+template <>
+const RxCoef<double>& coef_of<double>(const rx_ctx* c) { return c->cd; }
+template <>
+const RxCoef<float>& coef_of<float>(const rx_ctx* c) { return c->cf; }
+
+template <class T>
+int run_step(rx_ctx* c, int32_t niter, bool converge, pt_report* rep) {
+  const Box& b = c->box;
+  const RxCoef<T>& k = coef_of<T>(c);
+  T* Pf[2] = {(T*)c->Pf[0], (T*)c->Pf[1]};
+  T* phi[2] = {(T*)c->phi[0], (T*)c->phi[1]};
+  T* Xs[2] = {(T*)c->Xs[0], (T*)c->Xs[1]};
+  rx_begin<T>(c->stream, b, c->f.Pf, c->f.phi, c->f.Xs, Pf[0], phi[0], Xs[0], (T*)c->Pf_o, (T*)c->phi_o,
+              (T*)c->Xs_o);
+  cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  rx_kbmax<T>(c->stream, b, k, phi[0], c->red);
+  c->launches += 2;
+  double change = 0.0, kb = 0.0;
+  int rc = read_red(c, &change, &kb);
+  if (rc != PT_OK) return rc;
+  if (!(kb > 0) || !std::isfinite(kb)) return PT_ENAN;
+  double dtau = pseudo_step(c, kb);
+  int cur = 0, it = 0;
+  bool converged = false;
+  change = 0.0;
+  while (it < niter) {
+    ++it;
+    const int check = (it % c->num.nup) == 0;
+    const bool last = it == niter;
+    if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+    const RxIn<T> in{Pf[cur], phi[cur], Xs[cur], (const T*)c->Pf_o, (const T*)c->phi_o, (const T*)c->Xs_o};
+    const RxOut<T> out{Pf[1 - cur], phi[1 - cur], Xs[1 - cur], (check || last) ? (T*)c->R : nullptr};
+    rx_iter<T>(c->stream, b, k, dtau, in, out, c->red, check);
+    ++c->launches;
+    cur = 1 - cur;
+    if (check) {
+      rc = read_red(c, &change, &kb);
+      if (rc != PT_OK) return rc;
+      if (!std::isfinite(change) || !std::isfinite(kb)) {
+        rc = PT_ENAN;
+        break;
+      }
+      dtau = pseudo_step(c, kb);
+      if (converge && change < c->num.tol) {   // this check iteration wrote the final rate
+        converged = true;
+        break;
+      }
+    }
+  }
+  if (rc == PT_OK) {
+    rx_end<T>(c->stream, b, Pf[cur], phi[cur], Xs[cur], (const T*)c->R, c->f.Pf, c->f.phi, c->f.Xs, c->f.R);
+    ++c->launches;
+    rc = status(cudaStreamSynchronize(c->stream));
+  }
+  if (rc == PT_OK && converge && !converged) rc = PT_ENOTCONV;
+  if (rep) {
+    std::memset(rep, 0, sizeof *rep);
+    rep->iters = it;
+    rep->status = rc;
+    rep->res_v = change;
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rx_workspace_size(const pt_grid* grid, const rx_num* num) {
+  Box b;
+  if (!rx_box(grid, &b) || !num_ok(num)) return 0;
+  const size_t elem = num->precision == PT_FP32 ? sizeof(float) : sizeof(double);
+  return kRxArrays * rx_align((size_t)b.n * elem) + rx_align(RED_N * sizeof(unsigned long long));
+}
+
+int rx_init(rx_ctx** out, const pt_grid* grid, const rx_phys* phys, const rx_num* num, const rx_fields* fields,
+            void* workspace, size_t bytes, void* stream) {
+  if (!out) return PT_EINVAL;
+  *out = nullptr;
+  Box b;
+  if (!rx_box(grid, &b) || !phys_ok(phys) || !num_ok(num) || !fields || !workspace) return PT_EINVAL;
+  if (!fields->Pf || !fields->phi || !fields->Xs || !fields->R) return PT_EINVAL;
+  if (((uintptr_t)workspace & (kRxAlign - 1)) != 0) return PT_EINVAL;
+  if (bytes < rx_workspace_size(grid, num)) return PT_ESPACE;
+  rx_ctx* c = new (std::nothrow) rx_ctx();
+  if (!c) return PT_ECUDA;
+  c->box = b;
+  c->phys = *phys;
+  c->num = *num;
+  c->stream = (cudaStream_t)stream;
+  c->f = *fields;
+  c->fp32 = num->precision == PT_FP32;
+  fill(c->cd, *grid, *phys, *num);
+  fill(c->cf, *grid, *phys, *num);
+  const double h = std::fmin(grid->lx / grid->nx, std::fmin(grid->ly / grid->ny, grid->lz / grid->nz));
+  c->hmin2 = h * h;
+  const size_t stride = rx_align((size_t)b.n * (c->fp32 ? sizeof(float) : sizeof(double)));
+  char* w = (char*)workspace;
+  void** slots[kRxArrays] = {&c->Pf[0], &c->Pf[1], &c->phi[0], &c->phi[1], &c->Xs[0], &c->Xs[1],
+                             &c->Pf_o, &c->phi_o, &c->Xs_o, &c->R};
+  for (int s = 0; s < kRxArrays; ++s) *slots[s] = w + s * stride;
+  c->red = (unsigned long long*)(w + kRxArrays * stride);
+  c->launches = 0;
+  if (cudaMallocHost(&c->h_red, RED_N * sizeof(unsigned long long)) != cudaSuccess) {
+    delete c;
+    return PT_ECUDA;
+  }
+  if (cudaMemsetAsync(workspace, 0, rx_workspace_size(grid, num), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaFreeHost(c->h_red);
+    delete c;
+    return PT_ECUDA;
+  }
+  *out = c;
+  return PT_OK;
+}
+
+int rx_step(rx_ctx* c, pt_report* rep) {
+  if (!c) return PT_EINVAL;
+  return c->fp32 ? run_step<float>(c, c->num.max_iter, true, rep) : run_step<double>(c, c->num.max_iter, true, rep);
+}
+
+int rx_iterate(rx_ctx* c, int32_t niter, pt_report* rep) {
+  if (!c || niter < 1) return PT_EINVAL;
+  return c->fp32 ? run_step<float>(c, niter, false, rep) : run_step<double>(c, niter, false, rep);
+}
+
+long long rx_launch_count(const rx_ctx* c) { return c ? c->launches : -1; }
+
+void rx_destroy(rx_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  cudaFreeHost(c->h_red);
+  delete c;
+}
+
+}  // extern "C"

@@ -17,8 +17,9 @@ _INC = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
 SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu",
-           "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu")
-HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh")
+           "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu",
+           "rx_api.cu", "rx_kernels.cu")
+HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -31,6 +32,7 @@ PT_FP64, PT_FP32, PT_FP64_STEPWISE = 0, 1, 2
 def _inputs():
     files = [os.path.join(_CSRC, s) for s in SOURCES + HEADERS]
     files.append(os.path.join(_INC, "porowave_pt.h"))
+    files.append(os.path.join(_INC, "porowave_rx.h"))
     return files
 
 
@@ -129,6 +131,20 @@ class OldFields(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("Pto", "Pfo", "txxo", "tyyo", "tzzo", "txyo", "txzo", "tyzo")]
 
 
+class RxPhys(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("phi0", "k0", "eta", "rhof", "rhos", "g", "beta_d", "beta_s", "beta_f",
+                                          "beta_x", "dX", "xs_max", "tau")]
+
+
+class RxNum(C.Structure):
+    _fields_ = [("dt", C.c_double), ("tol", C.c_double), ("cfl_div", C.c_double), ("pf_scale", C.c_double),
+                ("max_iter", C.c_int32), ("nup", C.c_int32), ("precision", C.c_int32)]
+
+
+class RxFields(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("Pf", "phi", "Xs", "R")]
+
+
 class AdjVec(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("Vx", "Vy", "Vz", "Pt", "Pf", "phi")]
 
@@ -158,6 +174,13 @@ SIGNATURES = {
     "pt_adjoint_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(Report)]),
     "pt_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Report)]),
     "pt_adjoint_apply": (C.c_int, [C.c_void_p, C.POINTER(AdjVec), C.POINTER(AdjVec), C.c_void_p, C.c_size_t]),
+    "rx_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.POINTER(RxNum)]),
+    "rx_init": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Grid), C.POINTER(RxPhys), C.POINTER(RxNum),
+                          C.POINTER(RxFields), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "rx_step": (C.c_int, [C.c_void_p, C.POINTER(Report)]),
+    "rx_iterate": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Report)]),
+    "rx_launch_count": (C.c_longlong, [C.c_void_p]),
+    "rx_destroy": (None, [C.c_void_p]),
     "pt_dd_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.POINTER(Num), C.POINTER(C.c_int32)]),
     "pt_dd_init": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Grid), C.POINTER(Phys), C.POINTER(Num),
                              C.POINTER(Fields), C.POINTER(C.c_int32), C.c_void_p, C.c_size_t, C.c_void_p]),

@@ -372,3 +372,78 @@ class PTDomains:
             self.close()
         except Exception:
             pass
+
+
+class RXSolver:
+    """Reactive porosity-wave solver (rx_* of the C ABI; thesis Art. 3, Eqs. 8-10).
+
+    params: the keys of ``pt_inputs.rx_params`` plus optional ``precision`` (PT_FP64 default,
+    PT_FP32); Pf, phi, Xs: initial cell fields (nz, ny, nx)."""
+
+    _PHYS = ("phi0", "k0", "eta", "rhof", "rhos", "g", "beta_d", "beta_s", "beta_f", "beta_x", "dX",
+             "xs_max", "tau")
+
+    def __init__(self, params: dict, Pf, phi, Xs, device="cuda", stream=None):
+        self.lib = N.load()
+        p = dict(params)
+        self.params = p
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.nx, self.ny, self.nz = p["nx"], p["ny"], p["nz"]
+        self._grid = N.Grid(p["nx"], p["ny"], p["nz"], p["lx"], p["ly"], p["lz"])
+        self._phys = N.RxPhys(*[float(p[k]) for k in self._PHYS])
+        self._num = N.RxNum(p["dt"], p["tol"], p["cfl_div"], p["pf_scale"], int(p["max_iter"]), int(p["nup"]),
+                            int(p.get("precision", N.PT_FP64)))
+        px = self.lib.pt_pitch_x(C.byref(self._grid))
+        if px == 0:
+            raise PTError(N.PT_EINVAL, "grid")
+        self.box_shape = (self.nz + 1, self.ny + 1, px)
+        ws = self.lib.rx_workspace_size(C.byref(self._grid), C.byref(self._num))
+        if ws == 0:
+            raise PTError(N.PT_EINVAL, "rx_workspace_size")
+        with torch.cuda.device(self.device):
+            self.f = {k: torch.zeros(self.box_shape, dtype=torch.float64, device=self.device)
+                      for k in ("Pf", "phi", "Xs", "R")}
+            for k, v in (("Pf", Pf), ("phi", phi), ("Xs", Xs)):
+                self.f[k][: self.nz, : self.ny, : self.nx].copy_(torch.as_tensor(v, dtype=torch.float64))
+            self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        fs = N.RxFields(*[self.f[k].data_ptr() for k in ("Pf", "phi", "Xs", "R")])
+        torch.cuda.synchronize(self.device)
+        h = C.c_void_p()
+        rc = self.lib.rx_init(C.byref(h), C.byref(self._grid), C.byref(self._phys), C.byref(self._num),
+                              C.byref(fs), self.workspace.data_ptr(), ws, self.stream.cuda_stream)
+        if rc != N.PT_OK:
+            raise PTError(rc, "rx_init")
+        self.h = h
+
+    def step(self, raise_on_notconv: bool = False) -> dict:
+        rep = N.Report()
+        rc = self.lib.rx_step(self.h, C.byref(rep))
+        if rc not in ((N.PT_OK,) if raise_on_notconv else (N.PT_OK, N.PT_ENOTCONV)):
+            raise PTError(rc, "rx_step")
+        return rep.as_dict()
+
+    def iterate(self, niter: int) -> dict:
+        rep = N.Report()
+        rc = self.lib.rx_iterate(self.h, niter, C.byref(rep))
+        if rc != N.PT_OK:
+            raise PTError(rc, "rx_iterate")
+        return rep.as_dict()
+
+    def get(self, name: str) -> np.ndarray:
+        torch.cuda.synchronize(self.device)
+        return self.f[name][: self.nz, : self.ny, : self.nx].cpu().numpy().copy()
+
+    def launch_count(self) -> int:
+        return int(self.lib.rx_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
