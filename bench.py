@@ -36,10 +36,10 @@ HBM_FALLBACK_GBS = 6800.0
 KERNEL_BYTES_PER_CELL = {
     "k_perm": 3 * 8, "k_centres": 19 * 8, "k_edges": 10 * 8, "k_porosity": 11 * 8,
     "k_faces": 21 * 8, "k_picard": 13 * 8, "k_begin_step": 6 * 8,
-    # FP64-lean form: cells reads 25 arrays (V, Pt, Pf, phi, w, k, Pto, Pfo, phio, Eo, iEo, ieta,
-    # idtp, cm2, 3 toa_ii, 3 em2, 3 toa_e) and writes 11 (Pt, Pf, phi, w, k, 6 stresses);
-    # faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
-    "k_lean_cells": 36 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
+    # FP64-lean form: cells reads 28 arrays (V, Pt, Pf, phi, w, k, Pto, Pfo, phio, Eo, iEo, ieta,
+    # idtp, cm2, 3 toa_ii, 6 pre-multiplied edge moduli, 3 toa_e) and writes 11 (Pt, Pf, phi, w, k,
+    # 6 stresses); faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
+    "k_lean_cells": 39 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
     "k_lean_begin": 11 * 8,
     # mixed precision, FP32 correction iterations: cells reads 17 arrays (3 dV, dPt, dPf, cc, k,
     # idtp, iden_pt, idtf, iden_pf, r_pt, r_pf, cm2, 3 em2) and writes 8 (dPt, dPf, 6 stresses);
@@ -52,9 +52,9 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2}
 # FP64 thread instructions (DFMA + DADD + DMUL) and flops (DFMA x 2 + DADD + DMUL) per cell and
 # launch from one ncu capture of the kernel (profiles/k_lean_fp64_191.md, k_adj_cells_95.md,
 # k_centres_fp64_stepwise_191.md); a kernel missing here has no current count.
-KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 114.8, "k_lean_faces": 35.8, "k_adj_cells": 76.5,
+KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 106.8, "k_lean_faces": 35.8, "k_adj_cells": 76.5,
                              "k_centres": 152.0}
-KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 168.7, "k_lean_faces": 52.7, "k_adj_cells": 115.2,
+KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 156.8, "k_lean_faces": 52.7, "k_adj_cells": 115.2,
                               "k_centres": 237.0}
 # The FP64 pipe issues at most 304 thread-instructions per GPU clock (2 per SM; ncu's
 # sm__inst_executed_pipe_fp64 peak on this machine's GB300), i.e. 629 G/s at 2.07 GHz.
@@ -62,7 +62,7 @@ FP64_PIPE_INST_PER_CLK = 304.0
 # FP32 kernels are bound by HBM (their FP32 work is far below the FP32 pipe's rate).
 # DRAM bytes per cell and launch (dram__bytes_read.sum + dram__bytes_write.sum) from the same
 # captures; the 191^3 case's per-cell figure scales with the cells of a launch.
-KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 286.8, "k_lean_faces": 180.6, "k_centres": 150.6,
+KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 311.0, "k_lean_faces": 180.6, "k_centres": 150.6,
                            "k_adj_cells": 270.5}
 
 

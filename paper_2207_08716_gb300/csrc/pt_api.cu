@@ -31,7 +31,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kPitchMultiple = 16;
 constexpr int kRefArrays = 23;   // step-by-step path
-constexpr int kLeanArrays = 23;  // extra arrays of the FP64-lean path
+constexpr int kLeanArrays = 26;  // extra arrays of the FP64-lean path
 constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
 // Default relative drop at which the inner FP32 solves of the mixed-precision path stop. The
 // outer loop's convergence is bound by the log-space Picard relaxation of mu and eta (one
@@ -86,7 +86,7 @@ struct pt_ctx {
   bool lean;
   double *lperm[2], *lw[2], *phio, *Eo, *iEo;
   double *toa_xx, *toa_yy, *toa_zz, *toa_xy, *toa_xz, *toa_yz, *cm2, *idtp, *ieta;
-  double *em2_xy, *em2_xz, *em2_yz, *dtv_x, *dtv_y, *dtv_z, *K0;
+  double *em2_xy, *em2_xz, *em2_yz, *eb_xy, *eb_xz, *eb_yz, *dtv_x, *dtv_y, *dtv_z, *K0;
   LeanCoef<double> lcoef;
   // mixed-precision path (precision PT_FP32): FP32 correction problem
   bool mixed;
@@ -238,6 +238,7 @@ void fill_lean_coef(pt_ctx* c) {
   L.bd_rdt = k.beta_d * k.rdt;
   L.bda_B_rdt = k.beta_d * k.alpha / k.B * k.rdt;
   L.alpha = k.alpha;
+  L.bd_rdt_a = k.beta_d * k.alpha * k.rdt;
   L.alpha_B = k.alpha / k.B;
   L.beta_n = k.beta_n;
   L.beta_phi = k.beta_phi;
@@ -327,7 +328,8 @@ void launch_lean_coef(pt_ctx* c) {
   const Box& b = c->box;
   LeanCoefIn<double> ci{c->mu, c->eta, c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
   LeanCoefOut<double> co{c->cm2, c->toa_xx, c->toa_yy, c->toa_zz, c->idtp, c->ieta, c->em2_xy,
-                         c->em2_xz, c->em2_yz, c->toa_xy, c->toa_xz, c->toa_yz, c->dtv_x, c->dtv_y,
+                         c->em2_xz, c->em2_yz, c->eb_xy, c->eb_xz, c->eb_yz, c->toa_xy, c->toa_xz, c->toa_yz,
+                         c->dtv_x, c->dtv_y,
                          c->dtv_z};
   PT_LAUNCH(c, K_LEAN_COEF, lean_coef<double>(grid_dims(b), block_dims(), c->stream, b, c->lcoef, ci, co));
 }
@@ -341,7 +343,8 @@ void launch_iteration_lean(pt_ctx* c, int check) {
   if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
   LeanCellIn<double> ci{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->lw[a], c->lperm[a],
                         c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->ieta, c->idtp, c->cm2,
-                        c->toa_xx, c->toa_yy, c->toa_zz, c->em2_xy, c->em2_xz, c->em2_yz,
+                        c->toa_xx, c->toa_yy, c->toa_zz, c->em2_xy, c->em2_xz, c->em2_yz, c->eb_xy,
+                        c->eb_xz, c->eb_yz,
                         c->toa_xy, c->toa_xz, c->toa_yz, c->logk ? c->K0 : nullptr};
   LeanCellOut<double> co{c->Pt[n], c->Pf[n], c->phi[n], c->lw[n], c->lperm[n], c->s_txx, c->s_tyy,
                          c->s_tzz, c->s_txy, c->s_txz, c->s_tyz};
@@ -583,7 +586,8 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
       // FP64-lean extras
       &c->lperm[0], &c->lperm[1], &c->lw[0], &c->lw[1], &c->phio, &c->Eo, &c->iEo, &c->toa_xx,
       &c->toa_yy, &c->toa_zz, &c->toa_xy, &c->toa_xz, &c->toa_yz, &c->cm2, &c->idtp, &c->ieta,
-      &c->em2_xy, &c->em2_xz, &c->em2_yz, &c->dtv_x, &c->dtv_y, &c->dtv_z, &c->K0};
+      &c->em2_xy, &c->em2_xz, &c->em2_yz, &c->eb_xy, &c->eb_xz, &c->eb_yz, &c->dtv_x, &c->dtv_y, &c->dtv_z,
+      &c->K0};
   const int arrays = kRefArrays + (c->lean ? kLeanArrays : 0);
   for (int s = 0; s < arrays; ++s) *slots[s] = (double*)(w + s * stride);
   char* wend = w + arrays * stride;
@@ -873,7 +877,8 @@ void fill_batch_inst(pt_batch* B, int m, long long base) {
     I.cin[a] = LeanCellIn<double>{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->lw[a], c->lperm[a],
                                   c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->ieta, c->idtp, c->cm2,
                                   c->toa_xx, c->toa_yy, c->toa_zz, c->em2_xy, c->em2_xz, c->em2_yz,
-                                  c->toa_xy, c->toa_xz, c->toa_yz, c->logk ? c->K0 : nullptr};
+                                  c->eb_xy, c->eb_xz, c->eb_yz, c->toa_xy, c->toa_xz, c->toa_yz,
+                                  c->logk ? c->K0 : nullptr};
     I.cout[a] = LeanCellOut<double>{c->Pt[n], c->Pf[n], c->phi[n], c->lw[n], c->lperm[n], c->s_txx,
                                     c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz};
     I.fin[a] = LeanFaceIn<double>{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[n],
@@ -883,7 +888,8 @@ void fill_batch_inst(pt_batch* B, int m, long long base) {
   }
   I.kin = LeanCoefIn<double>{c->mu, c->eta, c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
   I.kout = LeanCoefOut<double>{c->cm2, c->toa_xx, c->toa_yy, c->toa_zz, c->idtp, c->ieta, c->em2_xy,
-                               c->em2_xz, c->em2_yz, c->toa_xy, c->toa_xz, c->toa_yz, c->dtv_x,
+                               c->em2_xz, c->em2_yz, c->eb_xy, c->eb_xz, c->eb_yz, c->toa_xy, c->toa_xz,
+                               c->toa_yz, c->dtv_x,
                                c->dtv_y, c->dtv_z};
   I.Vx = c->Vx; I.Vy = c->Vy; I.Vz = c->Vz;
   I.Rx = c->Rx; I.Ry = c->Ry; I.Rz = c->Rz;

@@ -15,6 +15,7 @@ struct LeanCoef {
   T buoy_dz;                    // (rho_f - rho_BG) g dz
   T bd_rdt, bda_B_rdt;          // beta_d / dt, beta_d alpha / (B dt)
   T alpha, alpha_B;             // alpha, alpha / B
+  T bd_rdt_a;                   // beta_d alpha / dt
   T beta_n, beta_phi, dt;
   T rphi0, k0, phi0, drho_g;    // 1 / phi0, k0, phi0, (rho_f - rho_s) g
   T ifac_pf;                    // 1 / (cfl_pf h^2 (1 + beta_d B / alpha)): 1/dtau_Pf = kmax * ifac_pf
@@ -31,8 +32,10 @@ template <class T>
 struct LeanCellIn {
   const T *Vx, *Vy, *Vz, *Pt, *Pf, *phi, *w, *perm;
   const T *Pto, *Pfo, *phio, *Eo, *iEo;
-  const T *ieta, *idtp, *cm2, *toa_xx, *toa_yy, *toa_zz;
-  const T *em2_xy, *em2_xz, *em2_yz, *toa_xy, *toa_xz, *toa_yz;
+  const T *ieta, *idtp, *cm2, *toa_xx, *toa_yy, *toa_zz;   // idtp holds 1/dtau_Pt + beta_d/dt
+  // edge moduli 2 mu/(1+xi) pre-multiplied by the two half inverse spacings of each edge's strain
+  // rate: em2_xy = m hrdy, eb_xy = m hrdx; em2_xz = m hrdz, eb_xz = m hrdx; em2_yz = m hrdz, eb_yz = m hrdy
+  const T *em2_xy, *em2_xz, *em2_yz, *eb_xy, *eb_xz, *eb_yz, *toa_xy, *toa_xz, *toa_yz;
   const T *K0;  // k0 e^logk per cell, or null (scalar k0)
 };
 template <class T>
@@ -55,7 +58,7 @@ struct LeanCoefIn {
 template <class T>
 struct LeanCoefOut {
   T *cm2, *toa_xx, *toa_yy, *toa_zz, *idtp, *ieta;
-  T *em2_xy, *em2_xz, *em2_yz, *toa_xy, *toa_xz, *toa_yz;
+  T *em2_xy, *em2_xz, *em2_yz, *eb_xy, *eb_xz, *eb_yz, *toa_xy, *toa_xz, *toa_yz;
   T *dtv_x, *dtv_y, *dtv_z;
 };
 template <class T>

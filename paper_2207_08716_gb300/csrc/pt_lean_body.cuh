@@ -82,20 +82,15 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     // ---- edges owned by this index: xy (i, j, k), xz (i, j, k), yz (i, j, k); stored at the end
     // with the cell's outputs, after every load (the arrays are not declared non-aliasing)
     T t_xy = T(0), t_xz = T(0), t_yz = T(0);
-    if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
-      const T e = (in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx;
-      t_xy = in.toa_xy[q] + in.em2_xy[q] * e;   // toa_xy holds the background part too
+    if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {   // toa_xy holds the background part too
+      t_xy = fma(in.eb_xy[q], in.Vy[q] - in.Vy[q - 1], fma(in.em2_xy[q], in.Vx[q] - in.Vx[q - px], in.toa_xy[q]));
     } else if (k < b.nz && c.bg_on) {   // wall xy-edge under background shear (Eqs. 32-33)
       t_xy = in.toa_xy[q];
     }
-    if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
-      const T e = (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx;
-      t_xz = in.toa_xz[q] + in.em2_xz[q] * e;
-    }
-    if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
-      const T e = (in.Vy[q] - in.Vy[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - px]) * c.hrdy;
-      t_yz = in.toa_yz[q] + in.em2_yz[q] * e;
-    }
+    if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz)
+      t_xz = fma(in.eb_xz[q], in.Vz[q] - in.Vz[q - 1], fma(in.em2_xz[q], in.Vx[q] - in.Vx[q - pxy], in.toa_xz[q]));
+    if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz)
+      t_yz = fma(in.eb_yz[q], in.Vz[q] - in.Vz[q - px], fma(in.em2_yz[q], in.Vy[q] - in.Vy[q - pxy], in.toa_yz[q]));
     if (cell) {
       const T Pt = in.Pt[q], Pf = in.Pf[q], Pto = in.Pto[q], Pfo = in.Pfo[q];
       const T ph = in.phi[q], w = in.w[q], ieta = in.ieta[q];
@@ -104,8 +99,9 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       const T gx = (vxr - vxl) * c.rdx, gy = (vyr - vyl) * c.rdy, gz = (vzr - vzl) * c.rdz;
       const T divV = gx + gy + gz;
       const T cc = c.compaction_on ? ieta * w : T(0);
-      const T dPt = Pt - Pto, dPf = Pf - Pfo;
-      const T divVn = divV + c.bd_rdt * (dPt - c.alpha * dPf) + (Pt - Pf) * cc;
+      const T dPt = Pt - Pto, dPf = Pf - Pfo, dpp = Pt - Pf;
+      // explicit fused multiply-adds: the same rounding in every kernel that inlines this body
+      const T divVn = fma(dpp, cc, fma(-c.bd_rdt_a, dPf, fma(c.bd_rdt, dPt, divV)));
       // Darcy flux through the six faces (zero on the boundary) and the largest neighbour k
       const T kc = in.perm[q];
       T kmax = kc, sx = T(0), sy = T(0), sz = T(0);
@@ -143,16 +139,15 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       const T divqD = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
       // local-implicit pressure updates, Eqs. 17-18: P1 = P - res / (1/dtau + d res/dP), the
       // residuals being divVn (row Pt) and resF (row Pf)
-      const T resF = divqD + c.bda_B_rdt * dPf - c.bd_rdt * c.alpha * dPt + (Pf - Pt) * cc;
-      const T Pt1 = Pt - rcp_pseudo(in.idtp[q] + c.bd_rdt + cc) * divVn;
+      const T resF = fma(-dpp, cc, fma(-c.bd_rdt_a, dPt, fma(c.bda_B_rdt, dPf, divqD)));
+      const T Pt1 = Pt - rcp_pseudo(in.idtp[q] + cc) * divVn;   // idtp holds 1/dtau_Pt + beta_d/dt
       const T Pf1 = Pf - rcp_pseudo(kmax * c.ifac_pf + c.bda_B_rdt + cc) * resF;
       // normal deviatoric stresses (Eq. 21): tau = tau_o xi/(1+xi) + 2 mu/(1+xi) (edot + beta_n divVn)
-      const T third = divV * T(1.0 / 3.0);
-      const T bn = c.beta_n * divVn;
+      const T s3 = fma(c.beta_n, divVn, -(divV * T(1.0 / 3.0)));
       const T cm2 = in.cm2[q];
-      const T sxx = in.toa_xx[q] + cm2 * (gx - third + bn);
-      const T syy = in.toa_yy[q] + cm2 * (gy - third + bn);
-      const T szz = in.toa_zz[q] + cm2 * (gz - third + bn);
+      const T sxx = fma(cm2, gx + s3, in.toa_xx[q]);
+      const T syy = fma(cm2, gy + s3, in.toa_yy[q]);
+      const T szz = fma(cm2, gz + s3, in.toa_zz[q]);
       // porosity in log space (Eq. 22): L = Lo + delta,
       // delta = -[beta_phi ((Pf1 - Pfo) - (Pt1 - Pto)) + dt (Pf1 - Pt1) / eta + dt V.grad(1-phi)/(1-phi)]
       T ax = T(0), ay = T(0), az = T(0);
@@ -286,31 +281,33 @@ __device__ __forceinline__ void lean_coef_point(const Box& b, const LeanCoef<T>&
     out.toa_xx[q] = (T)(in.txxo[q] * a);
     out.toa_yy[q] = (T)(in.tyyo[q] * a);
     out.toa_zz[q] = (T)(in.tzzo[q] * a);
-    out.idtp[q] = (T)(1.0 / (c.dtaupt_fac * m));
+    out.idtp[q] = (T)(1.0 / (c.dtaupt_fac * m) + (double)c.bd_rdt);   // 1/dtau_Pt + beta_d/dt
     out.ieta[q] = (T)(1.0 / (double)in.eta[q]);
   }
   if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
     const double m = 0.25 * ((double)in.mu[q - 1 - px] + in.mu[q - px] + in.mu[q - 1] + in.mu[q]);
     const double s = 1.0 / (1.0 + m * rG);
-    out.em2_xy[q] = (T)(2.0 * m * s);
+    out.em2_xy[q] = (T)(2.0 * m * s * (double)c.hrdy);
+    out.eb_xy[q] = (T)(2.0 * m * s * (double)c.hrdx);
     // the background shear's stress 2 mu/(1+xi) tau_bg/(2 mu0) (Eqs. 32-33) joins the old-stress part
     out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
   } else if (k < b.nz && c.bg_on) {   // wall xy-edges carry the background stress
     const double m = edge_mean_mu_xy(b, in.mu, q, i, j);
     const double s = 1.0 / (1.0 + m * rG);
-    out.em2_xy[q] = (T)(2.0 * m * s);
     out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
   }
   if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
     const double m = 0.25 * ((double)in.mu[q - 1 - pxy] + in.mu[q - pxy] + in.mu[q - 1] + in.mu[q]);
     const double s = 1.0 / (1.0 + m * rG);
-    out.em2_xz[q] = (T)(2.0 * m * s);
+    out.em2_xz[q] = (T)(2.0 * m * s * (double)c.hrdz);
+    out.eb_xz[q] = (T)(2.0 * m * s * (double)c.hrdx);
     out.toa_xz[q] = (T)(in.txzo[q] * (1.0 - s));
   }
   if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
     const double m = 0.25 * ((double)in.mu[q - px - pxy] + in.mu[q - pxy] + in.mu[q - px] + in.mu[q]);
     const double s = 1.0 / (1.0 + m * rG);
-    out.em2_yz[q] = (T)(2.0 * m * s);
+    out.em2_yz[q] = (T)(2.0 * m * s * (double)c.hrdz);
+    out.eb_yz[q] = (T)(2.0 * m * s * (double)c.hrdy);
     out.toa_yz[q] = (T)(in.tyzo[q] * (1.0 - s));
   }
   // pseudo-time steps of the velocities, mean of the two centres' dtau_V = fac / mu
