@@ -8,14 +8,14 @@ namespace pt {
 namespace lean_detail {
 
 // exp(d) - 1 and exp(-d) - 1 from the Taylor series of exp split into its odd part
-// O = d + d^3/3! + ... and even part E = d^2/2! + d^4/4! + ... (truncated after d^5 / d^4 for
+// O = d + d^3/3! + ... and even part E = d^2/2! + d^4/4! + ... (truncated after d^3 / d^2 for
 // |d| <= 2^-20 and after d^9 / d^8 for |d| <= 2^-6: in both cases the first dropped term is
 // below 2^-60 |d|). expm1(d) = E + O, expm1(-d) = E - O.
 __device__ inline void expm1_pair(double d, double& em_pos, double& em_neg) {
   if (fabs(d) <= 0x1p-20) {
     const double d2 = d * d;
-    const double E = d2 * fma(d2, 1.0 / 24.0, 0.5);
-    const double O = d * fma(d2, fma(d2, 1.0 / 120.0, 1.0 / 6.0), 1.0);
+    const double E = 0.5 * d2;
+    const double O = d * fma(d2, 1.0 / 6.0, 1.0);
     em_pos = E + O;
     em_neg = E - O;
   } else if (fabs(d) <= 0.015625) {
@@ -150,15 +150,17 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       const T szz = fma(cm2, gz + s3, in.toa_zz[q]);
       // porosity in log space (Eq. 22): L = Lo + delta,
       // delta = -[beta_phi ((Pf1 - Pfo) - (Pt1 - Pto)) + dt (Pf1 - Pt1) / eta + dt V.grad(1-phi)/(1-phi)]
+      // V.grad(1-phi)/(1-phi) = -(w/2) sum_d rd [v_r (phi_r - phi) + v_l (phi - phi_l)]
+      //                      = -w [sum_d hrd (v_r phi_r - v_l phi_l) - phi divV / 2]
+      // (the velocities of wall faces are zero, so the divergence term is div V exactly)
       T ax = T(0), ay = T(0), az = T(0);
-      if (i > 0) ax += vxl * (ph - in.phi[q - 1]);
-      if (i < b.nx - 1) ax += vxr * (in.phi[q + 1] - ph);
-      if (j > 0) ay += vyl * (ph - in.phi[q - px]);
-      if (j < b.ny - 1) ay += vyr * (in.phi[q + px] - ph);
-      if (k > 0) az += vzl * (ph - in.phi[q - pxy]);
-      if (k < b.nz - 1) az += vzr * (in.phi[q + pxy] - ph);
-      // V.grad(1-phi)/(1-phi) = -(1/2) w sum_d rd (...)
-      const T adv = -(ax * c.hrdx + ay * c.hrdy + az * c.hrdz) * w;
+      if (i > 0) ax = -vxl * in.phi[q - 1];
+      if (i < b.nx - 1) ax = fma(vxr, in.phi[q + 1], ax);
+      if (j > 0) ay = -vyl * in.phi[q - px];
+      if (j < b.ny - 1) ay = fma(vyr, in.phi[q + px], ay);
+      if (k > 0) az = -vzl * in.phi[q - pxy];
+      if (k < b.nz - 1) az = fma(vzr, in.phi[q + pxy], az);
+      const T adv = -w * fma(T(-0.5) * ph, divV, fma(ax, c.hrdx, fma(ay, c.hrdy, az * c.hrdz)));
       const T comp = c.compaction_on ? (Pf1 - Pt1) * ieta : T(0);
       const T delta = -(c.beta_phi * ((Pf1 - Pfo) - (Pt1 - Pto)) + c.dt * (comp + adv));
       T em_p, em_n;
