@@ -25,17 +25,20 @@ def lib_path() -> str:
 
 _RX_SRC = os.path.join(_HERE, "rx_oracle.c")
 _RX_HDR = os.path.join(_HERE, "rx_oracle.h")
+_MG_SRC = os.path.join(_HERE, "rx_mg_oracle.c")
+_MG_HDR = os.path.join(_HERE, "rx_mg_oracle.h")
 
 
 def build(force: bool = False) -> str:
-    """Compile pt_oracle.c and rx_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    """Compile pt_oracle.c, rx_oracle.c and rx_mg_oracle.c into oracle/_build/liboracle.so (gcc,
+    -O2, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(f) for f in (_SRC, _HDR, _RX_SRC, _RX_HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _HDR, _RX_SRC, _RX_HDR, _MG_SRC, _MG_HDR))
     stale = not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
-               "-o", tmp, _SRC, _RX_SRC, "-lm"]
+               "-o", tmp, _SRC, _RX_SRC, _MG_SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB

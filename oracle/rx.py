@@ -32,6 +32,18 @@ class RxParams(C.Structure):
 _FIELDS = ("Pf", "phi", "Xs", "R", "Pf_o", "phi_o", "Xs_o")
 
 
+class RxMgParams(C.Structure):
+    _fields_ = [(k, C.c_int) for k in ("levels", "nu_pre", "nu_post", "nu_coarse", "max_cycles")] + \
+               [("omega", C.c_double)]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "RxMgParams":
+        m = cls()
+        for name, _ in cls._fields_:
+            setattr(m, name, float(d[name]) if name == "omega" else int(d[name]))
+        return m
+
+
 class RxStateC(C.Structure):
     _fields_ = [(k, C.POINTER(C.c_double)) for k in _FIELDS] + [("dtau", C.c_double)]
 
@@ -54,7 +66,13 @@ def _L():
         lib.rx_pseudo_step.restype = C.c_double
         lib.rx_xseq.argtypes = [P, C.c_double]
         lib.rx_xseq.restype = C.c_double
-        for f in ("rx_begin_step", "rx_iteration", "rx_step", "rx_iterate_n"):
+        M = C.POINTER(RxMgParams)
+        lib.rx_mg_step.argtypes = [P, M, S, C.POINTER(C.c_int), D]
+        lib.rx_mg_cycles_n.argtypes = [P, M, S, C.c_int, D]
+        lib.rx_mg_restrict.argtypes = [C.c_int, C.c_int, C.c_int, D, D]
+        lib.rx_mg_prolong_add.argtypes = [C.c_int, C.c_int, C.c_int, D, D]
+        lib.rx_mg_equations.argtypes = [P] + [D] * 9 + [C.c_double] + [D] * 5
+        for f in ("rx_begin_step", "rx_iteration", "rx_step", "rx_iterate_n", "rx_mg_step", "rx_mg_cycles_n"):
             getattr(lib, f).restype = C.c_int
         _lib = lib
     return _lib
@@ -115,3 +133,49 @@ def pseudo_step(p: dict, phi) -> float:
 
 def xseq(p: dict, Pf: float) -> float:
     return _L().rx_xseq(C.byref(RxParams.from_dict(p)), float(Pf))
+
+
+def mg_step(st: RxState, mg: dict):
+    """One physical step by FAS V-cycles to the change tolerance: (rc, cycles, change)."""
+    it, ch = C.c_int(0), C.c_double(0.0)
+    rc = _L().rx_mg_step(C.byref(st.cp), C.byref(RxMgParams.from_dict(mg)), C.byref(st.c), C.byref(it),
+                         C.byref(ch))
+    return rc, it.value, ch.value
+
+
+def mg_cycles(st: RxState, mg: dict, ncycles: int):
+    """Begin a step and run exactly ncycles V-cycles: (rc, change of the last)."""
+    ch = C.c_double(0.0)
+    rc = _L().rx_mg_cycles_n(C.byref(st.cp), C.byref(RxMgParams.from_dict(mg)), C.byref(st.c), ncycles,
+                             C.byref(ch))
+    return rc, ch.value
+
+
+def mg_restrict(fine) -> np.ndarray:
+    fine = np.ascontiguousarray(fine, dtype=float)
+    nz, ny, nx = fine.shape
+    out = np.zeros((nz // 2, ny // 2, nx // 2))
+    _L().rx_mg_restrict(nx, ny, nz, _ptr(fine), _ptr(out))
+    return out
+
+
+def mg_prolong_add(coarse_e, fine) -> np.ndarray:
+    """fine + the trilinear interpolation of the coarse correction (a new array)."""
+    e = np.ascontiguousarray(coarse_e, dtype=float)
+    out = np.array(fine, dtype=float, copy=True, order="C")
+    nz, ny, nx = out.shape
+    assert e.shape == (nz // 2, ny // 2, nx // 2)
+    _L().rx_mg_prolong_add(nx, ny, nz, _ptr(e), _ptr(out))
+    return out
+
+
+def mg_equations(p: dict, u, old, f=None, omega: float = 6.0 / 7.0):
+    """(gP, gphi, gX, den, R) of the step equations at the state u = (Pf, phi, Xs) with old-step
+    fields old and FAS sources f (None: zero)."""
+    cp = RxParams.from_dict(p)
+    arr = [np.ascontiguousarray(a, dtype=float) for a in (*u, *old)]
+    fs = [None] * 3 if f is None else [np.ascontiguousarray(a, dtype=float) for a in f]
+    outs = [np.zeros_like(arr[0]) for _ in range(5)]
+    fp = [None if a is None else _ptr(a) for a in fs]
+    _L().rx_mg_equations(C.byref(cp), *[_ptr(a) for a in arr], *fp, float(omega), *[_ptr(a) for a in outs])
+    return tuple(outs)

@@ -103,7 +103,8 @@ int rx_iteration(const rx_params *p, rx_state *s, int it, double *change) {
   rx_div_qd(p, s->Pf, s->phi, divq);
   const double Sr = 1.0 - p->rhos / (p->rhof * (1.0 + p->dX));
   double err = 0.0;
-#pragma omp parallel for reduction(max : err)
+  int bad = 0;
+#pragma omp parallel for reduction(max : err) reduction(| : bad)
   for (long c = 0; c < n; ++c) {
     const double Pf = s->Pf[c], phi = s->phi[c], Xs = s->Xs[c];
     const double Pe = -Pf;
@@ -124,7 +125,9 @@ int rx_iteration(const rx_params *p, rx_state *s, int it, double *change) {
     R1[c] = R;
     const double e = fmax(fabs(phi1[c] - phi), fmax(fabs(Pf1[c] - Pf) / p->pf_scale, fabs(Xs1[c] - Xs)));
     err = fmax(err, e);
+    bad |= !(isfinite(Pf1[c]) && isfinite(phi1[c]) && isfinite(Xs1[c]));   /* fmax drops NaN */
   }
+  if (bad) err = NAN;
   memcpy(s->Pf, Pf1, n * sizeof(double));
   memcpy(s->phi, phi1, n * sizeof(double));
   memcpy(s->Xs, Xs1, n * sizeof(double));

@@ -5,7 +5,9 @@
 * linear limit: compaction and reaction off and beta_s = beta_d (1 - phi0) (porosity frozen),
   no gravity: the fluid pressure obeys backward-Euler diffusion with no-flux walls, whose exact
   discrete solution comes from the DCT-II eigenbasis of the Neumann Laplacian;
-* equilibrium limit: with a reaction time far below dt the converged Xs equals Xs_eq(Pf);
+* fast reaction: with dt / tau = 10 the converged Xs keeps tau / (tau + dt) of the old
+  disequilibrium from Xs_eq(Pf) (backward Euler of Eq. 10); a reaction time far below dt makes
+  the iteration diverge, which the step reports (ENAN) instead of converging on NaN;
 * the Darcy divergence telescopes to zero over the box (no-flux walls) and vanishes for the
   hydrostatic fluid pressure Pf = rho_f g z;
 * two anomalies centred in x and y keep the x and y mirror symmetries.
@@ -75,14 +77,30 @@ def test_linear_limit_is_backward_euler_diffusion():
     np.testing.assert_allclose(st["phi"], p["phi0"], rtol=1e-14)
 
 
-def test_equilibrium_limit_binds_xs_to_the_fluid_pressure():
-    p = _p(tau=1e-12, tol=1e-14, max_iter=400000)
+def test_fast_reaction_relaxes_xs_towards_equilibrium():
+    # backward Euler of dXs/dt = (Xs_eq - Xs) / tau leaves tau / (tau + dt) of the old
+    # disequilibrium (Eq. 10); dt / tau = 10, from a state in equilibrium before the step
+    p = _p(tau=1e-7, tol=1e-14, max_iter=400000)
+    Pf, phi, _ = I.rx_initial(p)
+    Pf = Pf + 0.05
+    xs0 = np.clip(p["beta_x"] * Pf + 0.5 * p["xs_max"], 0.0, p["xs_max"])
+    st = R.RxState(p, Pf, phi, xs0)
+    rc, iters, ch = R.step(st)
+    assert rc == 0, (iters, ch)
+    xseq = np.clip(p["beta_x"] * st["Pf"] + 0.5 * p["xs_max"], 0.0, p["xs_max"])
+    gap_old = np.abs(xs0 - xseq)
+    assert gap_old.max() > 1e-8                                    # the fluid pressure did move
+    shrink = p["tau"] / (p["tau"] + p["dt"])
+    assert np.all(np.abs(st["Xs"] - xseq) <= gap_old * shrink * (1.0 + 1e-6) + 1e-15)
+
+
+def test_diverging_step_reports_nan():
+    # a reaction time far below dt makes the first Jacobi iterate's porosity rate explode
+    p = _p(tau=1e-12, tol=1e-14, max_iter=1000)
     Pf, phi, Xs = I.rx_initial(p)
     st = R.RxState(p, Pf + 0.05, phi, Xs)
     rc, iters, ch = R.step(st)
-    assert rc == 0
-    xseq = np.clip(p["beta_x"] * st["Pf"] + 0.5 * p["xs_max"], 0.0, p["xs_max"])
-    np.testing.assert_allclose(st["Xs"], xseq, rtol=0, atol=1e-9)
+    assert rc == -3 and not np.isfinite(ch), (rc, iters, ch)
 
 
 def test_darcy_divergence_telescopes_and_hydrostatic_flux_vanishes():
