@@ -99,6 +99,13 @@ def parse():
                     help="measure the reactive porosity-wave solver (Art. 3) instead: T_eff with A_eff = 7 N p")
     ap.add_argument("--rx-n", type=int, default=255, help="reactive grid n x n x 4n")
     ap.add_argument("--rx-iters", type=int, default=100, help="PT iterations per physical step (reactive)")
+    ap.add_argument("--reactive-mg", action="store_true",
+                    help="measure the multigrid-accelerated reactive step instead: time to a converged "
+                         "physical step, FAS V-cycles against the plain PT iteration, n x n x 4n cells")
+    ap.add_argument("--mg-n", type=int, default=256, help="multigrid reactive grid n x n x 4n (n divisible by 2^(levels-1))")
+    ap.add_argument("--mg-levels", type=int, default=7)
+    ap.add_argument("--mg-plain-steps", type=int, default=2,
+                    help="timed converged steps of the plain PT solver (after one warm-up step)")
     ap.add_argument("--batched-converge", action="store_true",
                     help="run one step of the batched ensemble to convergence and report p50/p99 "
                          "time-to-converge (minutes of GPU time) instead of the throughput bench")
@@ -487,6 +494,80 @@ def measure_reactive(args, dev) -> dict:
     return out
 
 
+MG_DEFAULT = dict(nu_pre=2, nu_post=2, nu_coarse=30, max_cycles=100, omega=6.0 / 7.0)
+
+
+def measure_reactive_mg(args, dev) -> dict:
+    """Multigrid-accelerated reactive step (FAS V-cycles smoothed by the PT iteration with local
+    pseudo steps) against the plain PT iteration, on the reactive workload of Art. 3 (Da = 100,
+    dt = 1e-6, tol 2e-8) on n x n x 4n cells: both solvers advance the same physical steps from
+    the same state; time to a converged step with CUDA events (host reads of the change norm
+    included: they decide when to stop). FP32 (the thesis's precision for this solver) for both;
+    FP64 for the multigrid form. The fine-grid sweep (k_mg_smooth, the dominant kernel) is timed
+    alone for its roofline: 6 arrays read (Pf, phi with neighbours, Xs, 3 old-step fields) and
+    3 written per cell."""
+    import torch
+    from paper_2207_08716_gb300 import native as N
+    from paper_2207_08716_gb300.solver import RXSolver
+
+    n = args.mg_n
+    mg = dict(MG_DEFAULT, levels=args.mg_levels)
+    hbm, hbm_kind = peaks()
+    out = {"mg": mg}
+
+    def timed(s, fn, nsteps):
+        torch.cuda.synchronize(dev)
+        l0 = s.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = []
+        e0.record(s.stream)
+        for _ in range(nsteps):
+            reps.append(fn())
+        e1.record(s.stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / nsteps, reps, s.launch_count() - l0
+
+    for prec, pbytes in (("fp32", 4), ("fp64", 8)):
+        p = I.rx_params(n)
+        p["precision"] = N.PT_FP32 if prec == "fp32" else N.PT_FP64
+        Pf, phi, Xs = I.rx_initial(p)
+        ncell = p["nx"] * p["ny"] * p["nz"]
+        r = {"grid": [p["nx"], p["ny"], p["nz"]], "cells": ncell}
+        s = RXSolver(p, Pf, phi, Xs, device=dev, mg=mg)
+        for _ in range(args.warmup):
+            s.mg_step(raise_on_notconv=True)
+        clocks = M.ClockSampler(dev.index or 0)
+        clocks.start()
+        ms, reps, launches = timed(s, lambda: s.mg_step(raise_on_notconv=True), args.steps)
+        r["multigrid"] = {"ms_per_step": ms, "cycles": [q["iters"] for q in reps],
+                          "change": [q["r_v"] for q in reps], "gpu_launches": launches}
+        r["clocks"] = clocks.stop()
+        s.close()
+        # the fine-grid sweep alone: a one-level hierarchy of nu_coarse sweeps per cycle
+        one = RXSolver(p, Pf, phi, Xs, device=dev, mg=dict(mg, levels=1, nu_coarse=50))
+        one.mg_cycles(1)
+        t_cyc, _, _ = timed(one, lambda: one.mg_cycles(1), 3)
+        one.close()
+        t_sweep = t_cyc / 50 / 1e3
+        gbs = 9 * pbytes * ncell / t_sweep / 1e9
+        r["roofline"] = {"kernel": "k_mg_smooth (finest grid)", "bound": "hbm", "achieved": gbs, "peak": hbm,
+                         "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "algorithmic_bytes_per_cell": 9 * pbytes,
+                         "peak_kind": hbm_kind, "sweep_ms": t_sweep * 1e3}
+        if prec == "fp32" and args.mg_plain_steps > 0:
+            b = RXSolver(dict(p, max_iter=200000), Pf, phi, Xs, device=dev)
+            for _ in range(args.warmup):
+                b.step(raise_on_notconv=True)
+            ms_b, reps_b, launches_b = timed(b, lambda: b.step(raise_on_notconv=True), args.mg_plain_steps)
+            r["plain"] = {"ms_per_step": ms_b, "iters": [q["iters"] for q in reps_b], "gpu_launches": launches_b,
+                          "steps": args.mg_plain_steps}
+            r["speedup"] = ms_b / ms
+            b.close()
+        out[prec] = r
+        del Pf, phi, Xs
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -505,6 +586,21 @@ def run_native(args):
                               "config": {"workload": f"reactive porosity waves (Art. 3, Da = 100), "
                                                      f"{args.rx_n}x{args.rx_n}x{4 * args.rx_n} cells, "
                                                      f"{args.rx_iters} PT iterations per step"},
+                              "forms": r}), flush=True)
+        return 0
+    if args.reactive_mg:
+        if rank == 0:
+            r = measure_reactive_mg(args, dev)
+            f32 = r["fp32"]
+            print(json.dumps({"metric": "reactive step time-to-solution (multigrid-accelerated PT)",
+                              "value": f32["multigrid"]["ms_per_step"], "unit": "ms per converged step",
+                              "higher_is_better": False, "dtype": "f32", "steps": args.steps,
+                              "warmup": args.warmup,
+                              "config": {"workload": f"reactive porosity waves (Art. 3, Da = 100, dt = 1e-6, "
+                                                     f"tol 2e-8), {args.mg_n}x{args.mg_n}x{4 * args.mg_n} cells, "
+                                                     f"FAS V({MG_DEFAULT['nu_pre']},{MG_DEFAULT['nu_post']}) "
+                                                     f"cycles on {args.mg_levels} levels"},
+                              "gpu_launches": f32["multigrid"]["gpu_launches"], "roofline": f32["roofline"],
                               "forms": r}), flush=True)
         return 0
     if args.adjoint:

@@ -64,6 +64,38 @@ int rx_init(rx_ctx **ctx, const pt_grid *grid, const rx_phys *phys, const rx_num
 int rx_step(rx_ctx *ctx, pt_report *rep);
 /* One physical step of exactly niter iterations (no convergence exit; rep as rx_step). */
 int rx_iterate(rx_ctx *ctx, int32_t niter, pt_report *rep);
+/* ---- Geometric multigrid acceleration (the thesis's future-work section: PT iterations with
+ * local pseudo steps are weighted Jacobi iterations, which geometric multigrid accelerates; the
+ * nonlinearity by the full approximation scheme, FAS). The smoother is the iteration above with
+ * the local pseudo step dtau = omega beta_P / Dk (Dk = Jacobi diagonal of the Darcy operator,
+ * the cell's own terms implicit); coarse grids are 2 x 2 x 2 agglomerations (nx, ny, nz
+ * divisible by 2^(levels-1)), restriction = mean of the 8 children (iterate and residual),
+ * prolongation = trilinear interpolation of the coarse correction (neighbour held at the wall).
+ * A V-cycle on level l: nu_pre sweeps, restriction, FAS source f_c = mean(r) - g_c(u0_c), the
+ * cycle on l + 1 (nu_coarse sweeps on the coarsest), correction, nu_post sweeps. The change of a
+ * cycle is max(|dphi|, |dPf| / pf_scale, |dXs|) of its last sweep on the finest grid; R is that
+ * sweep's rate. The converged step is the fixed point of the plain iteration. */
+typedef struct {
+  int32_t levels;     /* grids in the hierarchy, 1..16 (1 = the smoother alone)              */
+  int32_t nu_pre;     /* sweeps before the coarse-grid correction (>= 0)                     */
+  int32_t nu_post;    /* sweeps after it (>= 1 when levels > 1)                              */
+  int32_t nu_coarse;  /* sweeps on the coarsest grid (>= 1)                                  */
+  int32_t max_cycles; /* V-cycle cap of rx_mg_step (>= 1)                                    */
+  double omega;       /* Jacobi weight of the Darcy part, 0 < omega <= 1 (6/7: 3-D optimum)  */
+} rx_mg;
+
+/* Workspace of a multigrid context: rx_workspace_size plus 15 arrays per coarse level; 0 for an
+ * invalid grid, numerics or hierarchy (a dimension not divisible by 2^(levels-1)). */
+size_t rx_mg_workspace_size(const pt_grid *grid, const rx_num *num, const rx_mg *mg);
+/* As rx_init, with the hierarchy; the context also runs rx_step / rx_iterate (plain PT). */
+int rx_mg_init(rx_ctx **ctx, const pt_grid *grid, const rx_phys *phys, const rx_num *num,
+               const rx_mg *mg, const rx_fields *fields, void *workspace, size_t bytes, void *stream);
+/* One physical step by V-cycles until the change is < num.tol (rep->iters = cycles; PT_ENOTCONV
+ * at max_cycles, PT_ENAN for a non-finite change, PT_EINVAL on a plain context). */
+int rx_mg_step(rx_ctx *ctx, pt_report *rep);
+/* One physical step of exactly ncycles V-cycles (rep as rx_mg_step). */
+int rx_mg_cycles(rx_ctx *ctx, int32_t ncycles, pt_report *rep);
+
 /* Launches of the library's kernels so far (benchmark accounting). */
 long long rx_launch_count(const rx_ctx *ctx);
 void rx_destroy(rx_ctx *ctx);

@@ -16,7 +16,29 @@ struct RxCoef {
   T dt, rdt, dt_tau, r1dt_tau;           // dt, 1/dt, dt/tau, 1/(1 + dt/tau)
   T sr_opdx, opdx;                       // S_r (1 + dX), 1 + dX
   T pf_iscale;                           // 1 / pf_scale
+  T rdx2, rdy2, rdz2;                    // 1/d^2 (Jacobi diagonal of the Darcy operator)
 };
+
+template <class T>
+__device__ inline T rx_clamp(T v, T lo, T hi) { return v < lo ? lo : (v > hi ? hi : v); }
+template <class T>
+__device__ inline T rx_abs(T x) { return x < T(0) ? -x : x; }
+// k = k0 (phi / phi0)^3
+template <class T>
+__device__ inline T rx_perm(const RxCoef<T>& c, T ph) {
+  const T r = ph * c.rphi0;
+  return c.k0 * r * r * r;
+}
+// beta_P = phi beta_f + beta_d - (1 + phi) beta_s
+template <class T>
+__device__ inline T rx_bp(const RxCoef<T>& c, T ph) {
+  return ph * c.beta_f + c.beta_d - (T(1) + ph) * c.beta_s;
+}
+// max of the three one-iteration changes; NaN if any is (fmax alone would drop it)
+__device__ inline double rx_change(double d_phi, double d_pf, double d_xs) {
+  const double s = d_phi + d_pf + d_xs;
+  return s != s ? s : fmax(d_phi, fmax(d_pf, d_xs));
+}
 
 template <class T>
 struct RxIn {
@@ -43,5 +65,45 @@ void rx_begin(cudaStream_t s, Box b, const double* Pf, const double* phi, const 
 template <class T>
 void rx_end(cudaStream_t s, Box b, const T* Pf, const T* phi, const T* Xs, const T* R, double* Pf1, double* phi1,
             double* Xs1, double* R1);
+
+// ---- geometric multigrid (FAS V-cycle) of the implicit step: rx_mg_kernels.cu ----
+
+// FAS sources of a coarse level (unused on the finest)
+template <class T>
+struct MgSrc {
+  const T *fP, *fphi, *fX;
+};
+// What the restriction writes on the coarse level: the restricted iterate (twice: the
+// iterate the coarse sweeps start from and the copy u0 the correction is measured against)
+// and the restricted residual in the FAS source slots.
+template <class T>
+struct MgCoarse {
+  T *Pf, *phi, *Xs, *Pf0, *phi0, *Xs0, *fP, *fphi, *fX;
+};
+// Coarse iterate and its restricted start u0 (the correction is their difference)
+template <class T>
+struct MgCorr {
+  const T *Pf, *phi, *Xs, *Pf0, *phi0, *Xs0;
+};
+
+// One weighted-Jacobi sweep (the PT iteration with local pseudo steps); fas: add the FAS
+// sources; check: change norm into red[RED_V]; out.R written when non-null.
+template <class T>
+void mg_smooth(cudaStream_t s, Box b, const RxCoef<T>& c, double omega, const RxIn<T>& in, const MgSrc<T>* fas,
+               const RxOut<T>& out, unsigned long long* red, int check);
+// fine residual and iterate -> coarse iterate, u0 and (restricted residual) sources
+template <class T>
+void mg_restrict(cudaStream_t s, Box fine, Box coarse, const RxCoef<T>& c, const RxIn<T>& in, const MgSrc<T>* fas,
+                 const MgCoarse<T>& out);
+// coarse sources f -= g(u0) (the FAS right-hand side)
+template <class T>
+void mg_coarse_rhs(cudaStream_t s, Box coarse, const RxCoef<T>& c, const RxIn<T>& u0, const MgCoarse<T>& out);
+// fine iterate += trilinear interpolation of (coarse iterate - u0); phi kept in [1e-4, 1]
+template <class T>
+void mg_prolong(cudaStream_t s, Box fine, Box coarse, const MgCorr<T>& e, T* Pf, T* phi, T* Xs);
+// old-step fields: 8-child means
+template <class T>
+void mg_restrict_old(cudaStream_t s, Box fine, Box coarse, const T* Pf_o, const T* phi_o, const T* Xs_o, T* cPf_o,
+                     T* cphi_o, T* cXs_o);
 
 }  // namespace pt

@@ -2,9 +2,11 @@
 //
 // A context keeps the iterate in the workspace in the iteration type (FP64 or FP32): the
 // caller's FP64 fields are read at the start of each physical step and written back at its
-// end. Per step: old-step copies, the first pseudo step from max k / beta_P, then fused
+// end. Plain PT step: old-step copies, the first pseudo step from max k / beta_P, then fused
 // iterations (ping-pong of Pf, phi, Xs); every nup-th iteration reads the change norm and
 // max k / beta_P of the new porosity (pseudo step of the next iterations) back to the host.
+// Multigrid step (contexts made by rx_mg_init): the old-step fields are restricted down the
+// hierarchy once, then FAS V-cycles run with one host read of the change norm per cycle.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -14,6 +16,23 @@
 #include "rx.cuh"
 
 using namespace pt;
+
+namespace {
+constexpr int kMgMaxLevels = 16;
+// One grid of the multigrid hierarchy (level 0 aliases the context's own arrays).
+struct MgLevel {
+  Box b;
+  RxCoef<double> cd;
+  RxCoef<float> cf;
+  void* Pf[2];
+  void* phi[2];
+  void* Xs[2];
+  void *Pf_o, *phi_o, *Xs_o;
+  void *fP, *fphi, *fX;              // FAS sources (coarse levels)
+  void *Pf0, *phi0, *Xs0;            // restricted iterate before the coarse solve
+  int cur;                           // which of the ping-pong pair holds the iterate
+};
+}  // namespace
 
 struct rx_ctx {
   Box box;
@@ -32,12 +51,15 @@ struct rx_ctx {
   unsigned long long* h_red;
   double hmin2;
   long long launches;
+  rx_mg mg;                          // multigrid settings (mg.levels = 0: plain context)
+  MgLevel lv[kMgMaxLevels];
 };
 
 namespace {
 
 constexpr size_t kRxAlign = 256;
 constexpr int kRxArrays = 10;        // Pf, phi, Xs (x2), Pf_o, phi_o, Xs_o, R
+constexpr int kMgArrays = 15;        // per coarse level: Pf, phi, Xs (x2), old (3), f (3), u0 (3)
 
 size_t rx_align(size_t x) { return (x + kRxAlign - 1) / kRxAlign * kRxAlign; }
 
@@ -77,6 +99,9 @@ void fill(RxCoef<T>& c, const pt_grid& g, const rx_phys& p, const rx_num& n) {
   c.sr_opdx = (T)(sr * (1.0 + p.dX));
   c.opdx = (T)(1.0 + p.dX);
   c.pf_iscale = (T)(1.0 / n.pf_scale);
+  c.rdx2 = (T)((g.nx / g.lx) * (g.nx / g.lx));
+  c.rdy2 = (T)((g.ny / g.ly) * (g.ny / g.ly));
+  c.rdz2 = (T)((g.nz / g.lz) * (g.nz / g.lz));
 }
 
 bool num_ok(const rx_num* n) {
@@ -170,6 +195,137 @@ int run_step(rx_ctx* c, int32_t niter, bool converge, pt_report* rep) {
   return rc;
 }
 
+// ---- multigrid ----
+
+bool mg_ok(const pt_grid* g, const rx_mg* m) {
+  if (!g || !m || m->levels < 1 || m->levels > kMgMaxLevels || m->nu_pre < 0 || m->nu_coarse < 1 ||
+      m->max_cycles < 1 || !(m->omega > 0.0 && m->omega <= 1.0))
+    return false;
+  if (m->levels > 1 && m->nu_post < 1) return false;
+  const int32_t s = 1 << (m->levels - 1);
+  return g->nx % s == 0 && g->ny % s == 0 && g->nz % s == 0;
+}
+
+pt_grid level_grid(const pt_grid& g, int l) {
+  pt_grid c = g;
+  c.nx = g.nx >> l;
+  c.ny = g.ny >> l;
+  c.nz = g.nz >> l;
+  return c;
+}
+
+size_t mg_extra_bytes(const pt_grid& g, int levels, size_t elem) {
+  size_t s = 0;
+  for (int l = 1; l < levels; ++l) {
+    const pt_grid c = level_grid(g, l);
+    s += kMgArrays * rx_align(pt_field_elems(&c) * elem);
+  }
+  return s;
+}
+
+template <class T>
+const RxCoef<T>& lcoef(const MgLevel& L);
+template <>
+const RxCoef<double>& lcoef<double>(const MgLevel& L) { return L.cd; }
+template <>
+const RxCoef<float>& lcoef<float>(const MgLevel& L) { return L.cf; }
+
+template <class T>
+RxIn<T> level_in(const MgLevel& L) {
+  return RxIn<T>{(const T*)L.Pf[L.cur], (const T*)L.phi[L.cur], (const T*)L.Xs[L.cur],
+                 (const T*)L.Pf_o,      (const T*)L.phi_o,      (const T*)L.Xs_o};
+}
+
+// one weighted-Jacobi sweep on level l; the last sweep of a cycle on the finest level writes
+// the rate and the change norm
+template <class T>
+void mg_sweep(rx_ctx* c, int l, bool last) {
+  MgLevel& L = c->lv[l];
+  const bool fine = l == 0;
+  const MgSrc<T> src{(const T*)L.fP, (const T*)L.fphi, (const T*)L.fX};
+  const int cur = L.cur;
+  const RxOut<T> out{(T*)L.Pf[1 - cur], (T*)L.phi[1 - cur], (T*)L.Xs[1 - cur], (fine && last) ? (T*)c->R : nullptr};
+  mg_smooth<T>(c->stream, L.b, lcoef<T>(L), c->mg.omega, level_in<T>(L), fine ? nullptr : &src, out, c->red,
+               fine && last);
+  L.cur = 1 - cur;
+  ++c->launches;
+}
+
+template <class T>
+void vcycle(rx_ctx* c, int l) {
+  const rx_mg& m = c->mg;
+  MgLevel& L = c->lv[l];
+  if (l == m.levels - 1) {
+    for (int s = 0; s < m.nu_coarse; ++s) mg_sweep<T>(c, l, s == m.nu_coarse - 1);
+    return;
+  }
+  for (int s = 0; s < m.nu_pre; ++s) mg_sweep<T>(c, l, false);
+  MgLevel& C = c->lv[l + 1];
+  C.cur = 0;
+  const MgCoarse<T> co{(T*)C.Pf[0], (T*)C.phi[0], (T*)C.Xs[0], (T*)C.Pf0, (T*)C.phi0,
+                       (T*)C.Xs0,   (T*)C.fP,     (T*)C.fphi,  (T*)C.fX};
+  const MgSrc<T> src{(const T*)L.fP, (const T*)L.fphi, (const T*)L.fX};
+  mg_restrict<T>(c->stream, L.b, C.b, lcoef<T>(L), level_in<T>(L), l == 0 ? nullptr : &src, co);
+  const RxIn<T> u0{(const T*)C.Pf0, (const T*)C.phi0, (const T*)C.Xs0,
+                   (const T*)C.Pf_o, (const T*)C.phi_o, (const T*)C.Xs_o};
+  mg_coarse_rhs<T>(c->stream, C.b, lcoef<T>(C), u0, co);
+  c->launches += 2;
+  vcycle<T>(c, l + 1);
+  const MgCorr<T> e{(const T*)C.Pf[C.cur], (const T*)C.phi[C.cur], (const T*)C.Xs[C.cur],
+                    (const T*)C.Pf0,       (const T*)C.phi0,       (const T*)C.Xs0};
+  mg_prolong<T>(c->stream, L.b, C.b, e, (T*)L.Pf[L.cur], (T*)L.phi[L.cur], (T*)L.Xs[L.cur]);
+  ++c->launches;
+  for (int s = 0; s < m.nu_post; ++s) mg_sweep<T>(c, l, s == m.nu_post - 1);
+}
+
+template <class T>
+int run_mg(rx_ctx* c, int32_t ncycles, bool converge, pt_report* rep) {
+  MgLevel& F = c->lv[0];
+  F.cur = 0;
+  rx_begin<T>(c->stream, c->box, c->f.Pf, c->f.phi, c->f.Xs, (T*)F.Pf[0], (T*)F.phi[0], (T*)F.Xs[0], (T*)F.Pf_o,
+              (T*)F.phi_o, (T*)F.Xs_o);
+  ++c->launches;
+  for (int l = 1; l < c->mg.levels; ++l) {
+    const MgLevel& A = c->lv[l - 1];
+    MgLevel& B = c->lv[l];
+    mg_restrict_old<T>(c->stream, A.b, B.b, (const T*)A.Pf_o, (const T*)A.phi_o, (const T*)A.Xs_o, (T*)B.Pf_o,
+                       (T*)B.phi_o, (T*)B.Xs_o);
+    ++c->launches;
+  }
+  int rc = PT_OK, it = 0;
+  bool converged = false;
+  double change = 0.0, kb = 0.0;
+  while (it < ncycles) {
+    ++it;
+    cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+    vcycle<T>(c, 0);
+    rc = read_red(c, &change, &kb);
+    if (rc != PT_OK) break;
+    if (!std::isfinite(change)) {
+      rc = PT_ENAN;
+      break;
+    }
+    if (converge && change < c->num.tol) {
+      converged = true;
+      break;
+    }
+  }
+  if (rc == PT_OK) {
+    rx_end<T>(c->stream, c->box, (const T*)F.Pf[F.cur], (const T*)F.phi[F.cur], (const T*)F.Xs[F.cur],
+              (const T*)c->R, c->f.Pf, c->f.phi, c->f.Xs, c->f.R);
+    ++c->launches;
+    rc = status(cudaStreamSynchronize(c->stream));
+  }
+  if (rc == PT_OK && converge && !converged) rc = PT_ENOTCONV;
+  if (rep) {
+    std::memset(rep, 0, sizeof *rep);
+    rep->iters = it;
+    rep->status = rc;
+    rep->res_v = change;
+  }
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -234,6 +390,72 @@ int rx_iterate(rx_ctx* c, int32_t niter, pt_report* rep) {
 }
 
 long long rx_launch_count(const rx_ctx* c) { return c ? c->launches : -1; }
+
+size_t rx_mg_workspace_size(const pt_grid* grid, const rx_num* num, const rx_mg* mg) {
+  const size_t base = rx_workspace_size(grid, num);
+  if (base == 0 || !mg_ok(grid, mg)) return 0;
+  const size_t elem = num->precision == PT_FP32 ? sizeof(float) : sizeof(double);
+  return base + mg_extra_bytes(*grid, mg->levels, elem);
+}
+
+int rx_mg_init(rx_ctx** out, const pt_grid* grid, const rx_phys* phys, const rx_num* num, const rx_mg* mg,
+               const rx_fields* fields, void* workspace, size_t bytes, void* stream) {
+  if (!out) return PT_EINVAL;
+  *out = nullptr;
+  const size_t need = rx_mg_workspace_size(grid, num, mg);
+  if (need == 0) return PT_EINVAL;
+  if (bytes < need) return PT_ESPACE;
+  const size_t base = rx_workspace_size(grid, num);
+  rx_ctx* c = nullptr;
+  int rc = rx_init(&c, grid, phys, num, fields, workspace, base, stream);
+  if (rc != PT_OK) return rc;
+  c->mg = *mg;
+  MgLevel& F = c->lv[0];
+  F.b = c->box;
+  F.cd = c->cd;
+  F.cf = c->cf;
+  for (int s = 0; s < 2; ++s) {
+    F.Pf[s] = c->Pf[s];
+    F.phi[s] = c->phi[s];
+    F.Xs[s] = c->Xs[s];
+  }
+  F.Pf_o = c->Pf_o;
+  F.phi_o = c->phi_o;
+  F.Xs_o = c->Xs_o;
+  F.fP = F.fphi = F.fX = F.Pf0 = F.phi0 = F.Xs0 = nullptr;
+  const size_t elem = c->fp32 ? sizeof(float) : sizeof(double);
+  char* w = (char*)workspace + base;
+  for (int l = 1; l < mg->levels; ++l) {
+    MgLevel& L = c->lv[l];
+    const pt_grid g = level_grid(*grid, l);
+    rx_box(&g, &L.b);
+    fill(L.cd, g, *phys, *num);
+    fill(L.cf, g, *phys, *num);
+    const size_t stride = rx_align((size_t)L.b.n * elem);
+    void** slots[kMgArrays] = {&L.Pf[0], &L.Pf[1], &L.phi[0], &L.phi[1], &L.Xs[0], &L.Xs[1], &L.Pf_o, &L.phi_o,
+                               &L.Xs_o,   &L.fP,     &L.fphi,   &L.fX,     &L.Pf0,   &L.phi0,  &L.Xs0};
+    for (int s = 0; s < kMgArrays; ++s) *slots[s] = w + s * stride;
+    w += kMgArrays * stride;
+    L.cur = 0;
+  }
+  if (cudaMemsetAsync((char*)workspace + base, 0, need - base, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    rx_destroy(c);
+    return PT_ECUDA;
+  }
+  *out = c;
+  return PT_OK;
+}
+
+int rx_mg_step(rx_ctx* c, pt_report* rep) {
+  if (!c || c->mg.levels < 1) return PT_EINVAL;
+  return c->fp32 ? run_mg<float>(c, c->mg.max_cycles, true, rep) : run_mg<double>(c, c->mg.max_cycles, true, rep);
+}
+
+int rx_mg_cycles(rx_ctx* c, int32_t ncycles, pt_report* rep) {
+  if (!c || c->mg.levels < 1 || ncycles < 1) return PT_EINVAL;
+  return c->fp32 ? run_mg<float>(c, ncycles, false, rep) : run_mg<double>(c, ncycles, false, rep);
+}
 
 void rx_destroy(rx_ctx* c) {
   if (!c) return;

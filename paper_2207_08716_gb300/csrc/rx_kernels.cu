@@ -7,22 +7,6 @@
 
 namespace pt {
 
-namespace {
-template <class T>
-__device__ inline T tclamp(T v, T lo, T hi) { return v < lo ? lo : (v > hi ? hi : v); }
-template <class T>
-__device__ inline T kperm(const RxCoef<T>& c, T ph) {
-  const T r = ph * c.rphi0;
-  return c.k0 * r * r * r;
-}
-template <class T>
-__device__ inline T beta_p(const RxCoef<T>& c, T ph) {
-  return ph * c.beta_f + c.beta_d - (T(1) + ph) * c.beta_s;
-}
-template <class T>
-__device__ inline T tabs(T x) { return x < T(0) ? -x : x; }
-}  // namespace
-
 template <class T>
 __global__ void __launch_bounds__(256) k_rx_iter(Box b, RxCoef<T> c, T dtau, RxIn<T> in, RxOut<T> out,
                                                  unsigned long long* red, int check) {
@@ -34,23 +18,23 @@ __global__ void __launch_bounds__(256) k_rx_iter(Box b, RxCoef<T> c, T dtau, RxI
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
     const T Pf = in.Pf[q], ph = in.phi[q], Xs = in.Xs[q];
-    const T kc = kperm(c, ph);
+    const T kc = rx_perm(c, ph);
     // Darcy flux through the six faces, zero through the walls; z faces carry rho_f g
     T sx = T(0), sy = T(0), sz = T(0);
-    if (i > 0) sx -= (kperm(c, in.phi[q - 1]) + kc) * (Pf - in.Pf[q - 1]) * c.rdx;
-    if (i < b.nx - 1) sx += (kc + kperm(c, in.phi[q + 1])) * (in.Pf[q + 1] - Pf) * c.rdx;
-    if (j > 0) sy -= (kperm(c, in.phi[q - px]) + kc) * (Pf - in.Pf[q - px]) * c.rdy;
-    if (j < b.ny - 1) sy += (kc + kperm(c, in.phi[q + px])) * (in.Pf[q + px] - Pf) * c.rdy;
-    if (k > 0) sz -= (kperm(c, in.phi[q - pxy]) + kc) * ((Pf - in.Pf[q - pxy]) * c.rdz - c.rhofg);
-    if (k < b.nz - 1) sz += (kc + kperm(c, in.phi[q + pxy])) * ((in.Pf[q + pxy] - Pf) * c.rdz - c.rhofg);
+    if (i > 0) sx -= (rx_perm(c, in.phi[q - 1]) + kc) * (Pf - in.Pf[q - 1]) * c.rdx;
+    if (i < b.nx - 1) sx += (kc + rx_perm(c, in.phi[q + 1])) * (in.Pf[q + 1] - Pf) * c.rdx;
+    if (j > 0) sy -= (rx_perm(c, in.phi[q - px]) + kc) * (Pf - in.Pf[q - px]) * c.rdy;
+    if (j < b.ny - 1) sy += (kc + rx_perm(c, in.phi[q + px])) * (in.Pf[q + px] - Pf) * c.rdy;
+    if (k > 0) sz -= (rx_perm(c, in.phi[q - pxy]) + kc) * ((Pf - in.Pf[q - pxy]) * c.rdz - c.rhofg);
+    if (k < b.nz - 1) sz += (kc + rx_perm(c, in.phi[q + pxy])) * ((in.Pf[q + pxy] - Pf) * c.rdz - c.rhofg);
     // div qD = -(1/2) sum_d [(k + k_r)(dPf_r) - (k_l + k)(dPf_l)] / d
     const T divq = -(sx * c.rdx + sy * c.rdy + sz * c.rdz) * T(0.5);
     const T Pf_o = in.Pf_o[q], phi_o = in.phi_o[q], Xs_o = in.Xs_o[q];
     const T w = T(1) / (T(1) - ph), ixs = T(1) / (T(1) - Xs);
     const T xr = c.beta_x * Pf + c.half_xs;
-    const T xseq = tclamp(xr, T(0), c.xs_max);
+    const T xseq = rx_clamp(xr, T(0), c.xs_max);
     const T dXs = (xseq - Xs) * c.rtau;
-    const T bp = beta_p(c, ph);
+    const T bp = rx_bp(c, ph);
     const T rbp = T(1) / bp;
     const T src = c.sr_opdx * (T(1) - ph) * ixs;
     const T comp = Pf * w * c.reta;                       // -Pe / (eta (1 - phi)), Pe = -Pf
@@ -61,14 +45,15 @@ __global__ void __launch_bounds__(256) k_rx_iter(Box b, RxCoef<T> c, T dtau, RxI
     const T Pf1 = Pf + dtau * (R - (Pf - Pf_o) * c.rdt) / (T(1) + dtau * (c.rdt + a));
     const T bphi = c.beta_d - c.beta_s * w;
     const T dphi = (T(1) - ph) * (bphi * R + comp - c.opdx * ixs * dXs);
-    const T phi1 = tclamp(phi_o + c.dt * dphi, T(1e-4), T(1));
+    const T phi1 = rx_clamp(phi_o + c.dt * dphi, T(1e-4), T(1));
     out.Pf[q] = Pf1;
     out.phi[q] = phi1;
     out.Xs[q] = Xs1;
     if (out.R) out.R[q] = R;
     if (check) {
-      chg = fmax((double)tabs(phi1 - ph), fmax((double)tabs(Pf1 - Pf) * (double)c.pf_iscale, (double)tabs(Xs1 - Xs)));
-      kb = (double)(kperm(c, phi1) / beta_p(c, phi1));
+      chg = rx_change((double)rx_abs(phi1 - ph), (double)rx_abs(Pf1 - Pf) * (double)c.pf_iscale,
+                      (double)rx_abs(Xs1 - Xs));
+      kb = (double)(rx_perm(c, phi1) / rx_bp(c, phi1));
     }
   }
   if (check) {
@@ -86,7 +71,7 @@ __global__ void __launch_bounds__(256) k_rx_kbmax(Box b, RxCoef<T> c, const T* _
   double kb = 0.0;
   if (i < b.nx && j < b.ny && k < b.nz) {
     const T ph = phi[cidx(b, i, j, k)];
-    kb = (double)(kperm(c, ph) / beta_p(c, ph));
+    kb = (double)(rx_perm(c, ph) / rx_bp(c, ph));
   }
   block_max_atomic(kb, red + RED_MUMAX);
 }

@@ -1,0 +1,274 @@
+// rx_mg_kernels.cu — geometric multigrid (FAS V-cycle) of the reactive porosity-wave step (thesis
+// Art. 3, Eqs. 8-10; the thesis's future-work section on multigrid-accelerated PT iterations).
+//
+// The smoother is the reactive PT iteration with a local pseudo step: per cell
+//   gP   = R - (Pf - Pf_o) / dt + fP
+//   Pf'  = Pf + gP / (Dk / (omega BP) + 1/dt + a)        (Dk: Jacobi diagonal of the Darcy operator)
+//   phi' = clamp(phi_o + dt dphi, 1e-4, 1) + fphi,   Xs' = (Xs_o + (dt/tau) Xs_eq) / (1 + dt/tau) + fX
+// with every right-hand side at the sweep's input and f = 0 on the finest grid. Coarse grids are
+// 2 x 2 x 2 agglomerations; the restriction takes 8-child means of the iterate and of the
+// residual (g = target - current), the FAS source is f_c = mean(r) - g_c(u0_c), and the
+// correction u_c - u0_c comes back by trilinear interpolation (3/4, 1/4 per direction, the
+// neighbour held at the wall). Every kernel runs one thread per cell of the grid it writes.
+#include "rx.cuh"
+
+namespace pt {
+
+namespace {
+
+// Step equations at cell (i, j, k) of a grid: the rate R, gP, the Jacobi denominator (DEN) and
+// the porosity and Xs targets (with the FAS sources when FAS).
+template <class T>
+struct MgEq {
+  T R, gP, den, phi1, Xs1;
+};
+
+template <class T, bool FAS, bool DEN>
+__device__ __forceinline__ MgEq<T> mg_eq(const Box& b, const RxCoef<T>& c, T romega, const RxIn<T>& in,
+                                         const MgSrc<T>& f, long long q, int i, int j, int k) {
+  const long long px = b.px, pxy = b.pxy;
+  const T Pf = in.Pf[q], ph = in.phi[q], Xs = in.Xs[q];
+  const T kc = rx_perm(c, ph);
+  // Darcy flux through the six faces (zero through the walls) and the face permeability sums
+  T sx = T(0), sy = T(0), sz = T(0), kx = T(0), ky = T(0), kz = T(0);
+  if (i > 0) {
+    const T kf = rx_perm(c, in.phi[q - 1]) + kc;
+    sx -= kf * (Pf - in.Pf[q - 1]) * c.rdx;
+    kx += kf;
+  }
+  if (i < b.nx - 1) {
+    const T kf = kc + rx_perm(c, in.phi[q + 1]);
+    sx += kf * (in.Pf[q + 1] - Pf) * c.rdx;
+    kx += kf;
+  }
+  if (j > 0) {
+    const T kf = rx_perm(c, in.phi[q - px]) + kc;
+    sy -= kf * (Pf - in.Pf[q - px]) * c.rdy;
+    ky += kf;
+  }
+  if (j < b.ny - 1) {
+    const T kf = kc + rx_perm(c, in.phi[q + px]);
+    sy += kf * (in.Pf[q + px] - Pf) * c.rdy;
+    ky += kf;
+  }
+  if (k > 0) {
+    const T kf = rx_perm(c, in.phi[q - pxy]) + kc;
+    sz -= kf * ((Pf - in.Pf[q - pxy]) * c.rdz - c.rhofg);
+    kz += kf;
+  }
+  if (k < b.nz - 1) {
+    const T kf = kc + rx_perm(c, in.phi[q + pxy]);
+    sz += kf * ((in.Pf[q + pxy] - Pf) * c.rdz - c.rhofg);
+    kz += kf;
+  }
+  const T divq = -(sx * c.rdx + sy * c.rdy + sz * c.rdz) * T(0.5);
+  const T Pf_o = in.Pf_o[q], phi_o = in.phi_o[q], Xs_o = in.Xs_o[q];
+  const T w = T(1) / (T(1) - ph), ixs = T(1) / (T(1) - Xs);
+  const T xr = c.beta_x * Pf + c.half_xs;
+  const T xseq = rx_clamp(xr, T(0), c.xs_max);
+  const T dXs = (xseq - Xs) * c.rtau;
+  const T bp = rx_bp(c, ph);
+  const T rbp = T(1) / bp;
+  const T src = c.sr_opdx * (T(1) - ph) * ixs;
+  const T comp = Pf * w * c.reta;                        // -Pe / (eta (1 - phi)), Pe = -Pf
+  MgEq<T> e;
+  e.R = (-divq - comp + src * dXs) * rbp;
+  e.gP = e.R - (Pf - Pf_o) * c.rdt;
+  if (FAS) e.gP += f.fP[q];
+  if (DEN) {
+    const T dxs_dpf = (xr > T(0) && xr < c.xs_max) ? c.beta_x : T(0);
+    const T a = (w * c.reta - src * dxs_dpf * c.rtau) * rbp;
+    const T Dk = (kx * c.rdx2 + ky * c.rdy2 + kz * c.rdz2) * T(0.5);
+    e.den = Dk * rbp * romega + c.rdt + a;
+  } else {
+    e.den = T(1);
+  }
+  const T bphi = c.beta_d - c.beta_s * w;
+  const T dphi = (T(1) - ph) * (bphi * e.R + comp - c.opdx * ixs * dXs);
+  e.phi1 = rx_clamp(phi_o + c.dt * dphi, T(1e-4), T(1));
+  e.Xs1 = (Xs_o + c.dt_tau * xseq) * c.r1dt_tau;
+  if (FAS) {
+    e.phi1 += f.fphi[q];
+    e.Xs1 += f.fX[q];
+  }
+  return e;
+}
+
+// the coarse neighbour on the side of fine index i, held inside [0, m)
+__device__ __forceinline__ int side_nb(int i, int m) {
+  const int n = (i & 1) ? (i >> 1) + 1 : (i >> 1) - 1;
+  return n < 0 ? 0 : (n > m - 1 ? m - 1 : n);
+}
+
+dim3 grid_of(const Box& b) { return dim3((unsigned)((b.nx + 31) / 32), (unsigned)((b.ny + 7) / 8), (unsigned)b.nz); }
+
+}  // namespace
+
+template <class T, bool FAS>
+__global__ void __launch_bounds__(256) k_mg_smooth(Box b, RxCoef<T> c, T romega, RxIn<T> in, MgSrc<T> f,
+                                                   RxOut<T> out, unsigned long long* red, int check) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double chg = 0.0;
+  if (i < b.nx && j < b.ny && k < b.nz) {
+    const long long q = cidx(b, i, j, k);
+    const MgEq<T> e = mg_eq<T, FAS, true>(b, c, romega, in, f, q, i, j, k);
+    const T Pf = in.Pf[q], ph = in.phi[q], Xs = in.Xs[q];
+    const T Pf1 = Pf + e.gP / e.den;
+    out.Pf[q] = Pf1;
+    out.phi[q] = e.phi1;
+    out.Xs[q] = e.Xs1;
+    if (out.R) out.R[q] = e.R;
+    if (check)
+      chg = rx_change((double)rx_abs(e.phi1 - ph), (double)rx_abs(Pf1 - Pf) * (double)c.pf_iscale,
+                      (double)rx_abs(e.Xs1 - Xs));
+  }
+  if (check) block_max_atomic(chg, red + RED_V);
+}
+
+template <class T, bool FAS>
+__global__ void __launch_bounds__(256) k_mg_restrict(Box fb, Box cb, RxCoef<T> c, RxIn<T> in, MgSrc<T> f,
+                                                     MgCoarse<T> out) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= cb.nx || J >= cb.ny || K >= cb.nz) return;
+  T sPf = T(0), sphi = T(0), sXs = T(0), gP = T(0), gphi = T(0), gX = T(0);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int i = 2 * I + (n & 1), j = 2 * J + ((n >> 1) & 1), k = 2 * K + (n >> 2);
+    const long long q = cidx(fb, i, j, k);
+    const MgEq<T> e = mg_eq<T, FAS, false>(fb, c, T(1), in, f, q, i, j, k);
+    const T ph = in.phi[q], Xs = in.Xs[q];
+    sPf += in.Pf[q];
+    sphi += ph;
+    sXs += Xs;
+    gP += e.gP;
+    gphi += e.phi1 - ph;
+    gX += e.Xs1 - Xs;
+  }
+  const long long Q = cidx(cb, I, J, K);
+  const T m = T(0.125);
+  out.Pf[Q] = sPf * m;
+  out.phi[Q] = sphi * m;
+  out.Xs[Q] = sXs * m;
+  out.Pf0[Q] = sPf * m;
+  out.phi0[Q] = sphi * m;
+  out.Xs0[Q] = sXs * m;
+  out.fP[Q] = gP * m;
+  out.fphi[Q] = gphi * m;
+  out.fX[Q] = gX * m;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_coarse_rhs(Box b, RxCoef<T> c, RxIn<T> u0, MgCoarse<T> out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= b.nx || j >= b.ny || k >= b.nz) return;
+  const long long q = cidx(b, i, j, k);
+  const MgEq<T> e = mg_eq<T, false, false>(b, c, T(1), u0, MgSrc<T>{nullptr, nullptr, nullptr}, q, i, j, k);
+  out.fP[q] -= e.gP;
+  out.fphi[q] -= e.phi1 - u0.phi[q];
+  out.fX[q] -= e.Xs1 - u0.Xs[q];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_prolong(Box fb, Box cb, MgCorr<T> e, T* Pf, T* phi, T* Xs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= fb.nx || j >= fb.ny || k >= fb.nz) return;
+  const int Ix[2] = {i >> 1, side_nb(i, cb.nx)};
+  const int Jy[2] = {j >> 1, side_nb(j, cb.ny)};
+  const int Kz[2] = {k >> 1, side_nb(k, cb.nz)};
+  const T wt[2] = {T(0.75), T(0.25)};
+  T ePf = T(0), ephi = T(0), eXs = T(0);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int a = n & 1, bb = (n >> 1) & 1, cc = n >> 2;
+    const T w = wt[a] * wt[bb] * wt[cc];
+    const long long Q = cidx(cb, Ix[a], Jy[bb], Kz[cc]);
+    ePf += w * (e.Pf[Q] - e.Pf0[Q]);
+    ephi += w * (e.phi[Q] - e.phi0[Q]);
+    eXs += w * (e.Xs[Q] - e.Xs0[Q]);
+  }
+  const long long q = cidx(fb, i, j, k);
+  Pf[q] += ePf;
+  phi[q] = rx_clamp(phi[q] + ephi, T(1e-4), T(1));
+  Xs[q] += eXs;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_restrict_old(Box fb, Box cb, const T* __restrict__ a,
+                                                         const T* __restrict__ b, const T* __restrict__ d, T* A, T* B,
+                                                         T* D) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= cb.nx || J >= cb.ny || K >= cb.nz) return;
+  T sa = T(0), sb = T(0), sd = T(0);
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const long long q = cidx(fb, 2 * I + (n & 1), 2 * J + ((n >> 1) & 1), 2 * K + (n >> 2));
+    sa += a[q];
+    sb += b[q];
+    sd += d[q];
+  }
+  const long long Q = cidx(cb, I, J, K);
+  A[Q] = sa * T(0.125);
+  B[Q] = sb * T(0.125);
+  D[Q] = sd * T(0.125);
+}
+
+template <class T>
+void mg_smooth(cudaStream_t s, Box b, const RxCoef<T>& c, double omega, const RxIn<T>& in, const MgSrc<T>* fas,
+               const RxOut<T>& out, unsigned long long* red, int check) {
+  const T romega = (T)(1.0 / omega);
+  if (fas)
+    k_mg_smooth<T, true><<<grid_of(b), dim3(32, 8, 1), 0, s>>>(b, c, romega, in, *fas, out, red, check);
+  else
+    k_mg_smooth<T, false><<<grid_of(b), dim3(32, 8, 1), 0, s>>>(b, c, romega, in,
+                                                               MgSrc<T>{nullptr, nullptr, nullptr}, out, red, check);
+}
+
+template <class T>
+void mg_restrict(cudaStream_t s, Box fine, Box coarse, const RxCoef<T>& c, const RxIn<T>& in, const MgSrc<T>* fas,
+                 const MgCoarse<T>& out) {
+  if (fas)
+    k_mg_restrict<T, true><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(fine, coarse, c, in, *fas, out);
+  else
+    k_mg_restrict<T, false><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(fine, coarse, c, in,
+                                                                      MgSrc<T>{nullptr, nullptr, nullptr}, out);
+}
+
+template <class T>
+void mg_coarse_rhs(cudaStream_t s, Box coarse, const RxCoef<T>& c, const RxIn<T>& u0, const MgCoarse<T>& out) {
+  k_mg_coarse_rhs<T><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(coarse, c, u0, out);
+}
+
+template <class T>
+void mg_prolong(cudaStream_t s, Box fine, Box coarse, const MgCorr<T>& e, T* Pf, T* phi, T* Xs) {
+  k_mg_prolong<T><<<grid_of(fine), dim3(32, 8, 1), 0, s>>>(fine, coarse, e, Pf, phi, Xs);
+}
+
+template <class T>
+void mg_restrict_old(cudaStream_t s, Box fine, Box coarse, const T* Pf_o, const T* phi_o, const T* Xs_o, T* cPf_o,
+                     T* cphi_o, T* cXs_o) {
+  k_mg_restrict_old<T><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(fine, coarse, Pf_o, phi_o, Xs_o, cPf_o, cphi_o,
+                                                                  cXs_o);
+}
+
+#define MG_INSTANTIATE(T)                                                                                          \
+  template void mg_smooth<T>(cudaStream_t, Box, const RxCoef<T>&, double, const RxIn<T>&, const MgSrc<T>*,        \
+                             const RxOut<T>&, unsigned long long*, int);                                          \
+  template void mg_restrict<T>(cudaStream_t, Box, Box, const RxCoef<T>&, const RxIn<T>&, const MgSrc<T>*,         \
+                               const MgCoarse<T>&);                                                               \
+  template void mg_coarse_rhs<T>(cudaStream_t, Box, const RxCoef<T>&, const RxIn<T>&, const MgCoarse<T>&);        \
+  template void mg_prolong<T>(cudaStream_t, Box, Box, const MgCorr<T>&, T*, T*, T*);                             \
+  template void mg_restrict_old<T>(cudaStream_t, Box, Box, const T*, const T*, const T*, T*, T*, T*);
+MG_INSTANTIATE(double)
+MG_INSTANTIATE(float)
+
+}  // namespace pt

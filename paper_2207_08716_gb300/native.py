@@ -18,7 +18,7 @@ _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
 SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu",
            "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu",
-           "rx_api.cu", "rx_kernels.cu")
+           "rx_api.cu", "rx_kernels.cu", "rx_mg_kernels.cu")
 HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -141,6 +141,11 @@ class RxNum(C.Structure):
                 ("max_iter", C.c_int32), ("nup", C.c_int32), ("precision", C.c_int32)]
 
 
+class RxMg(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("levels", "nu_pre", "nu_post", "nu_coarse", "max_cycles")] + \
+               [("omega", C.c_double)]
+
+
 class RxFields(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("Pf", "phi", "Xs", "R")]
 
@@ -179,6 +184,11 @@ SIGNATURES = {
                           C.POINTER(RxFields), C.c_void_p, C.c_size_t, C.c_void_p]),
     "rx_step": (C.c_int, [C.c_void_p, C.POINTER(Report)]),
     "rx_iterate": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Report)]),
+    "rx_mg_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.POINTER(RxNum), C.POINTER(RxMg)]),
+    "rx_mg_init": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Grid), C.POINTER(RxPhys), C.POINTER(RxNum),
+                             C.POINTER(RxMg), C.POINTER(RxFields), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "rx_mg_step": (C.c_int, [C.c_void_p, C.POINTER(Report)]),
+    "rx_mg_cycles": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Report)]),
     "rx_launch_count": (C.c_longlong, [C.c_void_p]),
     "rx_destroy": (None, [C.c_void_p]),
     "pt_dd_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.POINTER(Num), C.POINTER(C.c_int32)]),

@@ -378,12 +378,16 @@ class RXSolver:
     """Reactive porosity-wave solver (rx_* of the C ABI; thesis Art. 3, Eqs. 8-10).
 
     params: the keys of ``pt_inputs.rx_params`` plus optional ``precision`` (PT_FP64 default,
-    PT_FP32); Pf, phi, Xs: initial cell fields (nz, ny, nx)."""
+    PT_FP32); Pf, phi, Xs: initial cell fields (nz, ny, nx); mg: multigrid settings (keys of
+    rx_mg: levels, nu_pre, nu_post, nu_coarse, max_cycles, omega) to enable ``mg_step`` and
+    ``mg_cycles`` (FAS V-cycles) besides the plain PT ``step`` and ``iterate``."""
 
     _PHYS = ("phi0", "k0", "eta", "rhof", "rhos", "g", "beta_d", "beta_s", "beta_f", "beta_x", "dX",
              "xs_max", "tau")
 
-    def __init__(self, params: dict, Pf, phi, Xs, device="cuda", stream=None):
+    _MG = ("levels", "nu_pre", "nu_post", "nu_coarse", "max_cycles", "omega")
+
+    def __init__(self, params: dict, Pf, phi, Xs, device="cuda", stream=None, mg: dict | None = None):
         self.lib = N.load()
         p = dict(params)
         self.params = p
@@ -398,7 +402,12 @@ class RXSolver:
         if px == 0:
             raise PTError(N.PT_EINVAL, "grid")
         self.box_shape = (self.nz + 1, self.ny + 1, px)
-        ws = self.lib.rx_workspace_size(C.byref(self._grid), C.byref(self._num))
+        self._mg = None
+        if mg is not None:
+            self._mg = N.RxMg(*[int(mg[k]) for k in self._MG[:-1]], float(mg["omega"]))
+            ws = self.lib.rx_mg_workspace_size(C.byref(self._grid), C.byref(self._num), C.byref(self._mg))
+        else:
+            ws = self.lib.rx_workspace_size(C.byref(self._grid), C.byref(self._num))
         if ws == 0:
             raise PTError(N.PT_EINVAL, "rx_workspace_size")
         with torch.cuda.device(self.device):
@@ -410,8 +419,13 @@ class RXSolver:
         fs = N.RxFields(*[self.f[k].data_ptr() for k in ("Pf", "phi", "Xs", "R")])
         torch.cuda.synchronize(self.device)
         h = C.c_void_p()
-        rc = self.lib.rx_init(C.byref(h), C.byref(self._grid), C.byref(self._phys), C.byref(self._num),
-                              C.byref(fs), self.workspace.data_ptr(), ws, self.stream.cuda_stream)
+        if self._mg is not None:
+            rc = self.lib.rx_mg_init(C.byref(h), C.byref(self._grid), C.byref(self._phys), C.byref(self._num),
+                                     C.byref(self._mg), C.byref(fs), self.workspace.data_ptr(), ws,
+                                     self.stream.cuda_stream)
+        else:
+            rc = self.lib.rx_init(C.byref(h), C.byref(self._grid), C.byref(self._phys), C.byref(self._num),
+                                  C.byref(fs), self.workspace.data_ptr(), ws, self.stream.cuda_stream)
         if rc != N.PT_OK:
             raise PTError(rc, "rx_init")
         self.h = h
@@ -428,6 +442,21 @@ class RXSolver:
         rc = self.lib.rx_iterate(self.h, niter, C.byref(rep))
         if rc != N.PT_OK:
             raise PTError(rc, "rx_iterate")
+        return rep.as_dict()
+
+    def mg_step(self, raise_on_notconv: bool = False) -> dict:
+        """One physical step by FAS V-cycles to the tolerance (report iters = cycles)."""
+        rep = N.Report()
+        rc = self.lib.rx_mg_step(self.h, C.byref(rep))
+        if rc not in ((N.PT_OK,) if raise_on_notconv else (N.PT_OK, N.PT_ENOTCONV)):
+            raise PTError(rc, "rx_mg_step")
+        return rep.as_dict()
+
+    def mg_cycles(self, ncycles: int) -> dict:
+        rep = N.Report()
+        rc = self.lib.rx_mg_cycles(self.h, ncycles, C.byref(rep))
+        if rc != N.PT_OK:
+            raise PTError(rc, "rx_mg_cycles")
         return rep.as_dict()
 
     def get(self, name: str) -> np.ndarray:

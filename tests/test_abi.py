@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports every symbol include/porowave_pt.h declares;
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares;
 host-only logic (sizes, layout, argument validation) is checked without a GPU."""
 import ctypes as C
 import os
@@ -16,7 +16,7 @@ def _declared_functions():
             continue
         txt = open(os.path.join(ROOT, "include", h)).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(pt_\w+)\s*\(", txt, flags=re.M)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b((?:pt|rx)_\w+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
 
 
@@ -108,3 +108,36 @@ def test_decomposition_sizes_are_validated_on_the_host(lib):
     assert lib.pt_dd_init(C.byref(h), C.byref(g), C.byref(ph), C.byref(num), C.byref(fs), parts(2, 2, 2),
                           aligned, 16, None) == N.PT_ESPACE
     assert not h.value
+
+
+def test_multigrid_hierarchy_is_validated_on_the_host(lib):
+    """rx_mg_workspace_size / rx_mg_init reject hierarchies whose grids do not halve evenly, bad
+    sweep counts and weights before any CUDA call (runs without a GPU)."""
+    import pt_inputs as I
+    from paper_2207_08716_gb300 import native as N
+    p = I.rx_params(16, 16, 40)                          # 40 = 8 * 5: at most 4 levels
+    g = N.Grid(p["nx"], p["ny"], p["nz"], p["lx"], p["ly"], p["lz"])
+    num = N.RxNum(p["dt"], p["tol"], p["cfl_div"], p["pf_scale"], p["max_iter"], p["nup"], N.PT_FP64)
+    mg = lambda **kw: N.RxMg(*[kw.get(k, d) for k, d in (("levels", 4), ("nu_pre", 2), ("nu_post", 2),
+                                                        ("nu_coarse", 20), ("max_cycles", 50))],
+                             kw.get("omega", 6.0 / 7.0))
+    base = lib.rx_workspace_size(C.byref(g), C.byref(num))
+    four = lib.rx_mg_workspace_size(C.byref(g), C.byref(num), C.byref(mg()))
+    assert base > 0 and four > base
+    assert lib.rx_mg_workspace_size(C.byref(g), C.byref(num), C.byref(mg(levels=1))) == base
+    for bad in (dict(levels=5), dict(levels=0), dict(levels=17), dict(nu_post=0), dict(nu_coarse=0),
+                dict(nu_pre=-1), dict(max_cycles=0), dict(omega=0.0), dict(omega=1.2)):
+        assert lib.rx_mg_workspace_size(C.byref(g), C.byref(num), C.byref(mg(**bad))) == 0, bad
+    assert lib.rx_mg_workspace_size(C.byref(g), C.byref(num), C.byref(mg(levels=1, nu_post=0))) == base
+    ph = N.RxPhys(*[float(p[k]) for k in ("phi0", "k0", "eta", "rhof", "rhos", "g", "beta_d", "beta_s",
+                                          "beta_f", "beta_x", "dX", "xs_max", "tau")])
+    aligned = 1 << 20
+    fs = N.RxFields(aligned, aligned, aligned, aligned)
+    h = C.c_void_p()
+    assert lib.rx_mg_init(C.byref(h), C.byref(g), C.byref(ph), C.byref(num), C.byref(mg(levels=5)), C.byref(fs),
+                          aligned, four, None) == N.PT_EINVAL
+    assert lib.rx_mg_init(C.byref(h), C.byref(g), C.byref(ph), C.byref(num), C.byref(mg()), C.byref(fs),
+                          aligned, four - 1, None) == N.PT_ESPACE
+    assert not h.value
+    assert lib.rx_mg_step(None, None) == N.PT_EINVAL
+    assert lib.rx_mg_cycles(None, 1, None) == N.PT_EINVAL
