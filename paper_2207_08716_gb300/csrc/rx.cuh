@@ -17,6 +17,8 @@ struct RxCoef {
   T sr_opdx, opdx;                       // S_r (1 + dX), 1 + dX
   T pf_iscale;                           // 1 / pf_scale
   T rdx2, rdy2, rdz2;                    // 1/d^2 (Jacobi diagonal of the Darcy operator)
+  T kc3;                                 // k0 / phi0^3: k = kc3 phi^3
+  T rhofg_dz;                            // rho_f g dz (buoyancy as a pressure difference over a z face)
 };
 
 template <class T>
@@ -26,14 +28,24 @@ __device__ inline T rx_abs(T x) { return x < T(0) ? -x : x; }
 // k = k0 (phi / phi0)^3
 template <class T>
 __device__ inline T rx_perm(const RxCoef<T>& c, T ph) {
-  const T r = ph * c.rphi0;
-  return c.k0 * r * r * r;
+  return c.kc3 * (ph * ph) * ph;
 }
 // beta_P = phi beta_f + beta_d - (1 + phi) beta_s
 template <class T>
 __device__ inline T rx_bp(const RxCoef<T>& c, T ph) {
   return ph * c.beta_f + c.beta_d - (T(1) + ph) * c.beta_s;
 }
+// 1 / x from the hardware's approximate reciprocal refined by Newton steps r' = r + r (1 - x r),
+// each of which squares the relative error (FP64: ~2^-23 seed, rounding-limited after two). x is
+// 1 - phi, 1 - Xs, beta_P or a Jacobi denominator here: positive and far inside the normal range.
+// FP32 takes the fast reciprocal-multiply intrinsic (2 ulp).
+__device__ inline double rx_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ inline float rx_rcp(float x) { return __fdividef(1.0f, x); }
 // max of the three one-iteration changes; NaN if any is (fmax alone would drop it)
 __device__ inline double rx_change(double d_phi, double d_pf, double d_xs) {
   const double s = d_phi + d_pf + d_xs;
@@ -80,17 +92,22 @@ template <class T>
 struct MgCoarse {
   T *Pf, *phi, *Xs, *Pf0, *phi0, *Xs0, *fP, *fphi, *fX;
 };
-// Coarse iterate and its restricted start u0 (the correction is their difference)
+// The coarse correction e = u - u0, written by the coarse level's last sweep over u0
+template <class T>
+struct MgE {
+  T *Pf, *phi, *Xs;
+};
 template <class T>
 struct MgCorr {
-  const T *Pf, *phi, *Xs, *Pf0, *phi0, *Xs0;
+  const T *Pf, *phi, *Xs;
 };
 
 // One weighted-Jacobi sweep (the PT iteration with local pseudo steps); fas: add the FAS
-// sources; check: change norm into red[RED_V]; out.R written when non-null.
+// sources; laste (coarse levels, with fas): write e = u' - u0 over u0 instead of u' to out;
+// check: change norm into red[RED_V]; out.R written when non-null.
 template <class T>
 void mg_smooth(cudaStream_t s, Box b, const RxCoef<T>& c, double omega, const RxIn<T>& in, const MgSrc<T>* fas,
-               const RxOut<T>& out, unsigned long long* red, int check);
+               const RxOut<T>& out, const MgE<T>* laste, unsigned long long* red, int check);
 // fine residual and iterate -> coarse iterate, u0 and (restricted residual) sources
 template <class T>
 void mg_restrict(cudaStream_t s, Box fine, Box coarse, const RxCoef<T>& c, const RxIn<T>& in, const MgSrc<T>* fas,
@@ -98,7 +115,7 @@ void mg_restrict(cudaStream_t s, Box fine, Box coarse, const RxCoef<T>& c, const
 // coarse sources f -= g(u0) (the FAS right-hand side)
 template <class T>
 void mg_coarse_rhs(cudaStream_t s, Box coarse, const RxCoef<T>& c, const RxIn<T>& u0, const MgCoarse<T>& out);
-// fine iterate += trilinear interpolation of (coarse iterate - u0); phi kept in [1e-4, 1]
+// fine iterate += trilinear interpolation of the coarse correction e; phi kept in [1e-4, 1]
 template <class T>
 void mg_prolong(cudaStream_t s, Box fine, Box coarse, const MgCorr<T>& e, T* Pf, T* phi, T* Xs);
 // old-step fields: 8-child means

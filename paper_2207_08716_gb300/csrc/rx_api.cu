@@ -102,6 +102,8 @@ void fill(RxCoef<T>& c, const pt_grid& g, const rx_phys& p, const rx_num& n) {
   c.rdx2 = (T)((g.nx / g.lx) * (g.nx / g.lx));
   c.rdy2 = (T)((g.ny / g.ly) * (g.ny / g.ly));
   c.rdz2 = (T)((g.nz / g.lz) * (g.nz / g.lz));
+  c.kc3 = (T)(p.k0 / (p.phi0 * p.phi0 * p.phi0));
+  c.rhofg_dz = (T)(p.rhof * p.g * g.lz / g.nz);
 }
 
 bool num_ok(const rx_num* n) {
@@ -237,17 +239,19 @@ RxIn<T> level_in(const MgLevel& L) {
 }
 
 // one weighted-Jacobi sweep on level l; the last sweep of a cycle on the finest level writes
-// the rate and the change norm
+// the rate and the change norm, the last sweep of a coarse level's visit writes the correction
+// e = u' - u0 over u0 (the iterate itself is not needed after it)
 template <class T>
 void mg_sweep(rx_ctx* c, int l, bool last) {
   MgLevel& L = c->lv[l];
   const bool fine = l == 0;
   const MgSrc<T> src{(const T*)L.fP, (const T*)L.fphi, (const T*)L.fX};
+  const MgE<T> e{(T*)L.Pf0, (T*)L.phi0, (T*)L.Xs0};
   const int cur = L.cur;
   const RxOut<T> out{(T*)L.Pf[1 - cur], (T*)L.phi[1 - cur], (T*)L.Xs[1 - cur], (fine && last) ? (T*)c->R : nullptr};
-  mg_smooth<T>(c->stream, L.b, lcoef<T>(L), c->mg.omega, level_in<T>(L), fine ? nullptr : &src, out, c->red,
-               fine && last);
-  L.cur = 1 - cur;
+  mg_smooth<T>(c->stream, L.b, lcoef<T>(L), c->mg.omega, level_in<T>(L), fine ? nullptr : &src, out,
+               (!fine && last) ? &e : nullptr, c->red, fine && last);
+  if (fine || !last) L.cur = 1 - cur;
   ++c->launches;
 }
 
@@ -271,8 +275,7 @@ void vcycle(rx_ctx* c, int l) {
   mg_coarse_rhs<T>(c->stream, C.b, lcoef<T>(C), u0, co);
   c->launches += 2;
   vcycle<T>(c, l + 1);
-  const MgCorr<T> e{(const T*)C.Pf[C.cur], (const T*)C.phi[C.cur], (const T*)C.Xs[C.cur],
-                    (const T*)C.Pf0,       (const T*)C.phi0,       (const T*)C.Xs0};
+  const MgCorr<T> e{(const T*)C.Pf0, (const T*)C.phi0, (const T*)C.Xs0};   // the correction, see mg_sweep
   mg_prolong<T>(c->stream, L.b, C.b, e, (T*)L.Pf[L.cur], (T*)L.phi[L.cur], (T*)L.Xs[L.cur]);
   ++c->launches;
   for (int s = 0; s < m.nu_post; ++s) mg_sweep<T>(c, l, s == m.nu_post - 1);

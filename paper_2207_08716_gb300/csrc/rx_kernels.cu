@@ -2,7 +2,7 @@
 // one fused pseudo-transient iteration per launch. Per cell it reads Pf and phi with their six
 // neighbours (Darcy flux, k = k0 (phi/phi0)^3 averaged to the faces) and Xs plus the old step,
 // and writes the next Pf, phi, Xs: 7 arrays read, 3 written (the rate dPf/dt only on check and
-// final iterations). HBM-bound in FP32; in FP64 its divisions bound it on the FP64 pipe.
+// final iterations). Divisions are Newton-refined hardware reciprocals (rx_rcp).
 #include "rx.cuh"
 
 namespace pt {
@@ -30,19 +30,19 @@ __global__ void __launch_bounds__(256) k_rx_iter(Box b, RxCoef<T> c, T dtau, RxI
     // div qD = -(1/2) sum_d [(k + k_r)(dPf_r) - (k_l + k)(dPf_l)] / d
     const T divq = -(sx * c.rdx + sy * c.rdy + sz * c.rdz) * T(0.5);
     const T Pf_o = in.Pf_o[q], phi_o = in.phi_o[q], Xs_o = in.Xs_o[q];
-    const T w = T(1) / (T(1) - ph), ixs = T(1) / (T(1) - Xs);
+    const T w = rx_rcp(T(1) - ph), ixs = rx_rcp(T(1) - Xs);
     const T xr = c.beta_x * Pf + c.half_xs;
     const T xseq = rx_clamp(xr, T(0), c.xs_max);
     const T dXs = (xseq - Xs) * c.rtau;
     const T bp = rx_bp(c, ph);
-    const T rbp = T(1) / bp;
+    const T rbp = rx_rcp(bp);
     const T src = c.sr_opdx * (T(1) - ph) * ixs;
     const T comp = Pf * w * c.reta;                       // -Pe / (eta (1 - phi)), Pe = -Pf
     const T R = (-divq - comp + src * dXs) * rbp;
     const T dxs_dpf = (xr > T(0) && xr < c.xs_max) ? c.beta_x : T(0);
     const T a = (w * c.reta - src * dxs_dpf * c.rtau) * rbp;   // -dR/dPf of the cell's own terms
     const T Xs1 = (Xs_o + c.dt_tau * xseq) * c.r1dt_tau;
-    const T Pf1 = Pf + dtau * (R - (Pf - Pf_o) * c.rdt) / (T(1) + dtau * (c.rdt + a));
+    const T Pf1 = Pf + dtau * (R - (Pf - Pf_o) * c.rdt) * rx_rcp(T(1) + dtau * (c.rdt + a));
     const T bphi = c.beta_d - c.beta_s * w;
     const T dphi = (T(1) - ph) * (bphi * R + comp - c.opdx * ixs * dXs);
     const T phi1 = rx_clamp(phi_o + c.dt * dphi, T(1e-4), T(1));
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_rx_iter(Box b, RxCoef<T> c, T dtau, RxI
     if (check) {
       chg = rx_change((double)rx_abs(phi1 - ph), (double)rx_abs(Pf1 - Pf) * (double)c.pf_iscale,
                       (double)rx_abs(Xs1 - Xs));
-      kb = (double)(rx_perm(c, phi1) / rx_bp(c, phi1));
+      kb = (double)(rx_perm(c, phi1) * rx_rcp(rx_bp(c, phi1)));
     }
   }
   if (check) {

@@ -8,8 +8,9 @@
 // with every right-hand side at the sweep's input and f = 0 on the finest grid. Coarse grids are
 // 2 x 2 x 2 agglomerations; the restriction takes 8-child means of the iterate and of the
 // residual (g = target - current), the FAS source is f_c = mean(r) - g_c(u0_c), and the
-// correction u_c - u0_c comes back by trilinear interpolation (3/4, 1/4 per direction, the
-// neighbour held at the wall). Every kernel runs one thread per cell of the grid it writes.
+// correction u_c - u0_c (written by the coarse level's last sweep) comes back by trilinear
+// interpolation (3/4, 1/4 per direction, the neighbour held at the wall). The sweeps and the
+// right-hand side run one thread per cell; the transfers one thread per coarse cell.
 #include "rx.cuh"
 
 namespace pt {
@@ -29,46 +30,49 @@ __device__ __forceinline__ MgEq<T> mg_eq(const Box& b, const RxCoef<T>& c, T rom
   const long long px = b.px, pxy = b.pxy;
   const T Pf = in.Pf[q], ph = in.phi[q], Xs = in.Xs[q];
   const T kc = rx_perm(c, ph);
-  // Darcy flux through the six faces (zero through the walls) and the face permeability sums
+  // Darcy flux through the six faces (zero through the walls): s_d = sum over the d-faces of the
+  // face permeability (k + k_nb, twice the mean) times the pressure difference (z: minus the
+  // buoyancy rho_f g dz across the face); k_d = the sum of those face permeabilities
   T sx = T(0), sy = T(0), sz = T(0), kx = T(0), ky = T(0), kz = T(0);
   if (i > 0) {
     const T kf = rx_perm(c, in.phi[q - 1]) + kc;
-    sx -= kf * (Pf - in.Pf[q - 1]) * c.rdx;
+    sx = fma(kf, in.Pf[q - 1] - Pf, sx);
     kx += kf;
   }
   if (i < b.nx - 1) {
     const T kf = kc + rx_perm(c, in.phi[q + 1]);
-    sx += kf * (in.Pf[q + 1] - Pf) * c.rdx;
+    sx = fma(kf, in.Pf[q + 1] - Pf, sx);
     kx += kf;
   }
   if (j > 0) {
     const T kf = rx_perm(c, in.phi[q - px]) + kc;
-    sy -= kf * (Pf - in.Pf[q - px]) * c.rdy;
+    sy = fma(kf, in.Pf[q - px] - Pf, sy);
     ky += kf;
   }
   if (j < b.ny - 1) {
     const T kf = kc + rx_perm(c, in.phi[q + px]);
-    sy += kf * (in.Pf[q + px] - Pf) * c.rdy;
+    sy = fma(kf, in.Pf[q + px] - Pf, sy);
     ky += kf;
   }
   if (k > 0) {
     const T kf = rx_perm(c, in.phi[q - pxy]) + kc;
-    sz -= kf * ((Pf - in.Pf[q - pxy]) * c.rdz - c.rhofg);
+    sz = fma(kf, (in.Pf[q - pxy] - Pf) + c.rhofg_dz, sz);
     kz += kf;
   }
   if (k < b.nz - 1) {
     const T kf = kc + rx_perm(c, in.phi[q + pxy]);
-    sz += kf * ((in.Pf[q + pxy] - Pf) * c.rdz - c.rhofg);
+    sz = fma(kf, (in.Pf[q + pxy] - Pf) - c.rhofg_dz, sz);
     kz += kf;
   }
-  const T divq = -(sx * c.rdx + sy * c.rdy + sz * c.rdz) * T(0.5);
+  // div qD = -(1/2) sum_d s_d / d^2
+  const T divq = T(-0.5) * fma(sx, c.rdx2, fma(sy, c.rdy2, sz * c.rdz2));
   const T Pf_o = in.Pf_o[q], phi_o = in.phi_o[q], Xs_o = in.Xs_o[q];
-  const T w = T(1) / (T(1) - ph), ixs = T(1) / (T(1) - Xs);
+  const T w = rx_rcp(T(1) - ph), ixs = rx_rcp(T(1) - Xs);
   const T xr = c.beta_x * Pf + c.half_xs;
   const T xseq = rx_clamp(xr, T(0), c.xs_max);
   const T dXs = (xseq - Xs) * c.rtau;
   const T bp = rx_bp(c, ph);
-  const T rbp = T(1) / bp;
+  const T rbp = rx_rcp(bp);
   const T src = c.sr_opdx * (T(1) - ph) * ixs;
   const T comp = Pf * w * c.reta;                        // -Pe / (eta (1 - phi)), Pe = -Pf
   MgEq<T> e;
@@ -78,7 +82,7 @@ __device__ __forceinline__ MgEq<T> mg_eq(const Box& b, const RxCoef<T>& c, T rom
   if (DEN) {
     const T dxs_dpf = (xr > T(0) && xr < c.xs_max) ? c.beta_x : T(0);
     const T a = (w * c.reta - src * dxs_dpf * c.rtau) * rbp;
-    const T Dk = (kx * c.rdx2 + ky * c.rdy2 + kz * c.rdz2) * T(0.5);
+    const T Dk = T(0.5) * fma(kx, c.rdx2, fma(ky, c.rdy2, kz * c.rdz2));
     e.den = Dk * rbp * romega + c.rdt + a;
   } else {
     e.den = T(1);
@@ -104,9 +108,11 @@ dim3 grid_of(const Box& b) { return dim3((unsigned)((b.nx + 31) / 32), (unsigned
 
 }  // namespace
 
-template <class T, bool FAS>
-__global__ void __launch_bounds__(256) k_mg_smooth(Box b, RxCoef<T> c, T romega, RxIn<T> in, MgSrc<T> f,
-                                                   RxOut<T> out, unsigned long long* red, int check) {
+// LASTE: the last sweep of a coarse level's visit writes the correction e = u' - u0 into the u0
+// slots (read and written by the same thread) instead of u', which nothing reads afterwards.
+template <class T, bool FAS, bool LASTE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 5) k_mg_smooth(Box b, RxCoef<T> c, T romega, RxIn<T> in, MgSrc<T> f,
+                                                   RxOut<T> out, MgE<T> e0, unsigned long long* red, int check) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -115,11 +121,17 @@ __global__ void __launch_bounds__(256) k_mg_smooth(Box b, RxCoef<T> c, T romega,
     const long long q = cidx(b, i, j, k);
     const MgEq<T> e = mg_eq<T, FAS, true>(b, c, romega, in, f, q, i, j, k);
     const T Pf = in.Pf[q], ph = in.phi[q], Xs = in.Xs[q];
-    const T Pf1 = Pf + e.gP / e.den;
-    out.Pf[q] = Pf1;
-    out.phi[q] = e.phi1;
-    out.Xs[q] = e.Xs1;
-    if (out.R) out.R[q] = e.R;
+    const T Pf1 = Pf + e.gP * rx_rcp(e.den);
+    if (LASTE) {
+      e0.Pf[q] = Pf1 - e0.Pf[q];
+      e0.phi[q] = e.phi1 - e0.phi[q];
+      e0.Xs[q] = e.Xs1 - e0.Xs[q];
+    } else {
+      out.Pf[q] = Pf1;
+      out.phi[q] = e.phi1;
+      out.Xs[q] = e.Xs1;
+      if (out.R) out.R[q] = e.R;
+    }
     if (check)
       chg = rx_change((double)rx_abs(e.phi1 - ph), (double)rx_abs(Pf1 - Pf) * (double)c.pf_iscale,
                       (double)rx_abs(e.Xs1 - Xs));
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(256) k_mg_smooth(Box b, RxCoef<T> c, T romega,
 }
 
 template <class T, bool FAS>
-__global__ void __launch_bounds__(256) k_mg_restrict(Box fb, Box cb, RxCoef<T> c, RxIn<T> in, MgSrc<T> f,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mg_restrict(Box fb, Box cb, RxCoef<T> c, RxIn<T> in, MgSrc<T> f,
                                                      MgCoarse<T> out) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -174,30 +186,56 @@ __global__ void __launch_bounds__(256) k_mg_coarse_rhs(Box b, RxCoef<T> c, RxIn<
   out.fX[q] -= e.Xs1 - u0.Xs[q];
 }
 
+// One thread per coarse cell (I, J, K): the correction on its 3 x 3 x 3 neighbourhood (indices
+// held inside the grid), interpolated separably to its 8 children: a child on the low side of
+// its parent in x takes 3/4 of the parent's column and 1/4 of the column at I - 1, on the high
+// side 1/4 of the column at I + 1; then y, then z.
+template <class T>
+__device__ __forceinline__ void prolong_field(const Box& fb, const Box& cb, const T* __restrict__ e, T* u, int I,
+                                              int J, int K, bool clamp) {
+  long long xo[3], yo[3], zo[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    xo[d] = min(max(I + d - 1, 0), cb.nx - 1);
+    yo[d] = (long long)cb.px * min(max(J + d - 1, 0), cb.ny - 1);
+    zo[d] = cb.pxy * min(max(K + d - 1, 0), cb.nz - 1);
+  }
+  // x: rows (y, z) of the neighbourhood -> the two x-children
+  T rx[2][3][3];
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      const T* row = e + yo[dy] + zo[dz];
+      const T m = row[xo[1]];
+      rx[0][dy][dz] = fma(T(0.75), m, T(0.25) * row[xo[0]]);
+      rx[1][dy][dz] = fma(T(0.75), m, T(0.25) * row[xo[2]]);
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      T ry[3];
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz) ry[dz] = fma(T(0.75), rx[a][1][dz], T(0.25) * rx[a][b ? 2 : 0][dz]);
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        const T v = fma(T(0.75), ry[1], T(0.25) * ry[cc ? 2 : 0]);
+        const long long q = cidx(fb, 2 * I + a, 2 * J + b, 2 * K + cc);
+        u[q] = clamp ? rx_clamp(u[q] + v, T(1e-4), T(1)) : u[q] + v;
+      }
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_prolong(Box fb, Box cb, MgCorr<T> e, T* Pf, T* phi, T* Xs) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= fb.nx || j >= fb.ny || k >= fb.nz) return;
-  const int Ix[2] = {i >> 1, side_nb(i, cb.nx)};
-  const int Jy[2] = {j >> 1, side_nb(j, cb.ny)};
-  const int Kz[2] = {k >> 1, side_nb(k, cb.nz)};
-  const T wt[2] = {T(0.75), T(0.25)};
-  T ePf = T(0), ephi = T(0), eXs = T(0);
-#pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    const int a = n & 1, bb = (n >> 1) & 1, cc = n >> 2;
-    const T w = wt[a] * wt[bb] * wt[cc];
-    const long long Q = cidx(cb, Ix[a], Jy[bb], Kz[cc]);
-    ePf += w * (e.Pf[Q] - e.Pf0[Q]);
-    ephi += w * (e.phi[Q] - e.phi0[Q]);
-    eXs += w * (e.Xs[Q] - e.Xs0[Q]);
-  }
-  const long long q = cidx(fb, i, j, k);
-  Pf[q] += ePf;
-  phi[q] = rx_clamp(phi[q] + ephi, T(1e-4), T(1));
-  Xs[q] += eXs;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= cb.nx || J >= cb.ny || K >= cb.nz) return;
+  prolong_field(fb, cb, e.Pf, Pf, I, J, K, false);
+  prolong_field(fb, cb, e.phi, phi, I, J, K, true);
+  prolong_field(fb, cb, e.Xs, Xs, I, J, K, false);
 }
 
 template <class T>
@@ -224,13 +262,17 @@ __global__ void __launch_bounds__(256) k_mg_restrict_old(Box fb, Box cb, const T
 
 template <class T>
 void mg_smooth(cudaStream_t s, Box b, const RxCoef<T>& c, double omega, const RxIn<T>& in, const MgSrc<T>* fas,
-               const RxOut<T>& out, unsigned long long* red, int check) {
+               const RxOut<T>& out, const MgE<T>* laste, unsigned long long* red, int check) {
   const T romega = (T)(1.0 / omega);
-  if (fas)
-    k_mg_smooth<T, true><<<grid_of(b), dim3(32, 8, 1), 0, s>>>(b, c, romega, in, *fas, out, red, check);
+  const MgSrc<T> none{nullptr, nullptr, nullptr};
+  const MgE<T> noe{nullptr, nullptr, nullptr};
+  const dim3 g = grid_of(b), blk(32, 8, 1);
+  if (!fas)
+    k_mg_smooth<T, false, false><<<g, blk, 0, s>>>(b, c, romega, in, none, out, noe, red, check);
+  else if (!laste)
+    k_mg_smooth<T, true, false><<<g, blk, 0, s>>>(b, c, romega, in, *fas, out, noe, red, check);
   else
-    k_mg_smooth<T, false><<<grid_of(b), dim3(32, 8, 1), 0, s>>>(b, c, romega, in,
-                                                               MgSrc<T>{nullptr, nullptr, nullptr}, out, red, check);
+    k_mg_smooth<T, true, true><<<g, blk, 0, s>>>(b, c, romega, in, *fas, out, *laste, red, check);
 }
 
 template <class T>
@@ -250,7 +292,7 @@ void mg_coarse_rhs(cudaStream_t s, Box coarse, const RxCoef<T>& c, const RxIn<T>
 
 template <class T>
 void mg_prolong(cudaStream_t s, Box fine, Box coarse, const MgCorr<T>& e, T* Pf, T* phi, T* Xs) {
-  k_mg_prolong<T><<<grid_of(fine), dim3(32, 8, 1), 0, s>>>(fine, coarse, e, Pf, phi, Xs);
+  k_mg_prolong<T><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(fine, coarse, e, Pf, phi, Xs);
 }
 
 template <class T>
@@ -262,7 +304,7 @@ void mg_restrict_old(cudaStream_t s, Box fine, Box coarse, const T* Pf_o, const 
 
 #define MG_INSTANTIATE(T)                                                                                          \
   template void mg_smooth<T>(cudaStream_t, Box, const RxCoef<T>&, double, const RxIn<T>&, const MgSrc<T>*,        \
-                             const RxOut<T>&, unsigned long long*, int);                                          \
+                             const RxOut<T>&, const MgE<T>*, unsigned long long*, int);                           \
   template void mg_restrict<T>(cudaStream_t, Box, Box, const RxCoef<T>&, const RxIn<T>&, const MgSrc<T>*,         \
                                const MgCoarse<T>&);                                                               \
   template void mg_coarse_rhs<T>(cudaStream_t, Box, const RxCoef<T>&, const RxIn<T>&, const MgCoarse<T>&);        \

@@ -12,6 +12,7 @@ import shutil
 import signal
 import subprocess
 import tempfile
+import time
 
 UNKNOWN_DOFS = 12
 KNOWN_DOFS = 1
@@ -28,7 +29,9 @@ def t_eff_gbs(n_cells: int, p_bytes: int, t_it_s: float, **kw) -> float:
 
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms while active."""
+    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms while active. start() returns
+    once the first sample is written (or after 1 s), so the tool's start-up (driver queries) falls
+    before the timed region that follows it."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -47,6 +50,9 @@ class ClockSampler:
         self.proc = subprocess.Popen(
             ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
              "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        deadline = time.monotonic() + 1.0          # the tool may buffer its output: wait at most 1 s
+        while time.monotonic() < deadline and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
     def stop(self) -> dict | None:
         if self.proc is None:
