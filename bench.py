@@ -63,7 +63,7 @@ FP64_PIPE_INST_PER_CLK = 304.0
 # DRAM bytes per cell and launch (dram__bytes_read.sum + dram__bytes_write.sum) from the same
 # captures; the 191^3 case's per-cell figure scales with the cells of a launch.
 KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 311.0, "k_lean_faces": 180.6, "k_centres": 150.6,
-                           "k_adj_cells": 270.5}
+                           "k_adj_cells": 270.5, "k_mg_smooth_fp32": 36.4}
 
 
 def parse():
@@ -556,9 +556,11 @@ def measure_reactive_mg(args, dev) -> dict:
         one.close()
         t_sweep = t_cyc / 50 / 1e3
         gbs = 9 * pbytes * ncell / t_sweep / 1e9
+        traffic_cell = KERNEL_TRAFFIC_PER_CELL.get(f"k_mg_smooth_{prec}")
         r["roofline"] = {"kernel": "k_mg_smooth (finest grid)", "bound": "hbm", "achieved": gbs, "peak": hbm,
-                         "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "algorithmic_bytes_per_cell": 9 * pbytes,
-                         "peak_kind": hbm_kind, "sweep_ms": t_sweep * 1e3}
+                         "unit": "GB/s", "frac": gbs / hbm,
+                         "traffic": traffic_cell * ncell if traffic_cell else None,
+                         "algorithmic_bytes_per_cell": 9 * pbytes, "peak_kind": hbm_kind, "sweep_ms": t_sweep * 1e3}
         if prec == "fp32" and args.mg_plain_steps > 0:
             b = RXSolver(dict(p, max_iter=200000), Pf, phi, Xs, device=dev)
             for _ in range(args.warmup):

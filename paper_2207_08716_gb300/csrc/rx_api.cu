@@ -6,7 +6,8 @@
 // iterations (ping-pong of Pf, phi, Xs); every nup-th iteration reads the change norm and
 // max k / beta_P of the new porosity (pseudo step of the next iterations) back to the host.
 // Multigrid step (contexts made by rx_mg_init): the old-step fields are restricted down the
-// hierarchy once, then FAS V-cycles run with one host read of the change norm per cycle.
+// hierarchy once, then FAS V-cycles run, each replayed from a CUDA graph with one host read of
+// the change norm.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -53,6 +54,13 @@ struct rx_ctx {
   long long launches;
   rx_mg mg;                          // multigrid settings (mg.levels = 0: plain context)
   MgLevel lv[kMgMaxLevels];
+  // One V-cycle (reduction reset, kernels, read-back of the change norm) as a CUDA graph per
+  // parity of the finest level's ping-pong index at its start; captured on a stream of the
+  // context's own (the legacy default stream cannot be captured), replayed on `stream`.
+  cudaStream_t cap;
+  cudaGraphExec_t cyc[2];
+  long long cyc_launches[2];
+  int cyc_end[2];
 };
 
 namespace {
@@ -282,6 +290,33 @@ void vcycle(rx_ctx* c, int l) {
 }
 
 template <class T>
+int build_cycle_graph(rx_ctx* c, int parity) {
+  MgLevel& F = c->lv[0];
+  F.cur = parity;
+  const long long l0 = c->launches;
+  const cudaStream_t s = c->stream;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PT_ECUDA;
+  c->stream = c->cap;
+  cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->cap);
+  vcycle<T>(c, 0);
+  cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->cap);
+  c->stream = s;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cyc[parity], g, 0);
+  if (g) cudaGraphDestroy(g);
+  c->cyc_launches[parity] = c->launches - l0;
+  c->launches = l0;
+  c->cyc_end[parity] = F.cur;
+  F.cur = parity;                     // the captured cycle has not run yet
+  if (e != cudaSuccess) {
+    c->cyc[parity] = nullptr;
+    return PT_ECUDA;
+  }
+  return PT_OK;
+}
+
+template <class T>
 int run_mg(rx_ctx* c, int32_t ncycles, bool converge, pt_report* rep) {
   MgLevel& F = c->lv[0];
   F.cur = 0;
@@ -297,13 +332,22 @@ int run_mg(rx_ctx* c, int32_t ncycles, bool converge, pt_report* rep) {
   }
   int rc = PT_OK, it = 0;
   bool converged = false;
-  double change = 0.0, kb = 0.0;
+  double change = 0.0;
   while (it < ncycles) {
     ++it;
-    cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-    vcycle<T>(c, 0);
-    rc = read_red(c, &change, &kb);
-    if (rc != PT_OK) break;
+    const int parity = F.cur;
+    if (!c->cyc[parity]) {
+      rc = build_cycle_graph<T>(c, parity);
+      if (rc != PT_OK) break;
+    }
+    if (cudaGraphLaunch(c->cyc[parity], c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      rc = PT_ECUDA;
+      break;
+    }
+    c->launches += c->cyc_launches[parity];
+    F.cur = c->cyc_end[parity];
+    std::memcpy(&change, &c->h_red[RED_V], sizeof(double));
     if (!std::isfinite(change)) {
       rc = PT_ENAN;
       break;
@@ -413,6 +457,11 @@ int rx_mg_init(rx_ctx** out, const pt_grid* grid, const rx_phys* phys, const rx_
   int rc = rx_init(&c, grid, phys, num, fields, workspace, base, stream);
   if (rc != PT_OK) return rc;
   c->mg = *mg;
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap = nullptr;
+    rx_destroy(c);
+    return PT_ECUDA;
+  }
   MgLevel& F = c->lv[0];
   F.b = c->box;
   F.cd = c->cd;
@@ -463,6 +512,9 @@ int rx_mg_cycles(rx_ctx* c, int32_t ncycles, pt_report* rep) {
 void rx_destroy(rx_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (int p = 0; p < 2; ++p)
+    if (c->cyc[p]) cudaGraphExecDestroy(c->cyc[p]);
+  if (c->cap) cudaStreamDestroy(c->cap);
   cudaFreeHost(c->h_red);
   delete c;
 }

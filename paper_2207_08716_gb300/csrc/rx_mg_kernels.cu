@@ -9,8 +9,9 @@
 // 2 x 2 x 2 agglomerations; the restriction takes 8-child means of the iterate and of the
 // residual (g = target - current), the FAS source is f_c = mean(r) - g_c(u0_c), and the
 // correction u_c - u0_c (written by the coarse level's last sweep) comes back by trilinear
-// interpolation (3/4, 1/4 per direction, the neighbour held at the wall). The sweeps and the
-// right-hand side run one thread per cell; the transfers one thread per coarse cell.
+// interpolation (3/4, 1/4 per direction, the neighbour held at the wall). The sweeps, the
+// restriction and the right-hand side run one thread per cell, the prolongation one per fine
+// x-pair.
 #include "rx.cuh"
 
 namespace pt {
@@ -139,38 +140,55 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 5) k_mg_smooth(Box b
   if (check) block_max_atomic(chg, red + RED_V);
 }
 
+// One fine cell per thread: its residual (the step equations, without the Jacobi denominator) and
+// iterate; the 8 children of a coarse cell sit in one block of 32 x 4 x 2 threads (x pairs
+// summed by a warp shuffle, y and z pairs through shared memory), whose 16 x 2 x 1 coarse cells
+// receive the 8-child means.
+constexpr int kRbx = 32, kRby = 4, kRbz = 2;
+
 template <class T, bool FAS>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_mg_restrict(Box fb, Box cb, RxCoef<T> c, RxIn<T> in, MgSrc<T> f,
-                                                     MgCoarse<T> out) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  const int K = blockIdx.z;
-  if (I >= cb.nx || J >= cb.ny || K >= cb.nz) return;
-  T sPf = T(0), sphi = T(0), sXs = T(0), gP = T(0), gphi = T(0), gX = T(0);
-#pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    const int i = 2 * I + (n & 1), j = 2 * J + ((n >> 1) & 1), k = 2 * K + (n >> 2);
+__global__ void __launch_bounds__(kRbx * kRby * kRbz) k_mg_restrict(Box fb, Box cb, RxCoef<T> c, RxIn<T> in,
+                                                                    MgSrc<T> f, MgCoarse<T> out) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int i = blockIdx.x * kRbx + tx, j = blockIdx.y * kRby + ty, k = blockIdx.z * kRbz + tz;
+  T v[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};        // Pf, phi, Xs, gP, gphi, gX
+  if (i < fb.nx && j < fb.ny && k < fb.nz) {
     const long long q = cidx(fb, i, j, k);
     const MgEq<T> e = mg_eq<T, FAS, false>(fb, c, T(1), in, f, q, i, j, k);
     const T ph = in.phi[q], Xs = in.Xs[q];
-    sPf += in.Pf[q];
-    sphi += ph;
-    sXs += Xs;
-    gP += e.gP;
-    gphi += e.phi1 - ph;
-    gX += e.Xs1 - Xs;
+    v[0] = in.Pf[q];
+    v[1] = ph;
+    v[2] = Xs;
+    v[3] = e.gP;
+    v[4] = e.phi1 - ph;
+    v[5] = e.Xs1 - Xs;
   }
-  const long long Q = cidx(cb, I, J, K);
-  const T m = T(0.125);
-  out.Pf[Q] = sPf * m;
-  out.phi[Q] = sphi * m;
-  out.Xs[Q] = sXs * m;
-  out.Pf0[Q] = sPf * m;
-  out.phi0[Q] = sphi * m;
-  out.Xs0[Q] = sXs * m;
-  out.fP[Q] = gP * m;
-  out.fphi[Q] = gphi * m;
-  out.fX[Q] = gX * m;
+  __shared__ T part[kRbz][kRby][kRbx / 2][6];
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    const T o = __shfl_down_sync(0xffffffffu, v[n], 1);
+    if ((tx & 1) == 0) part[tz][ty][tx >> 1][n] = v[n] + o;
+  }
+  __syncthreads();
+  if (tz == 0 && (ty & 1) == 0 && tx < kRbx / 2) {
+    const int I = blockIdx.x * (kRbx / 2) + tx, J = blockIdx.y * (kRby / 2) + (ty >> 1), K = blockIdx.z;
+    if (I < cb.nx && J < cb.ny && K < cb.nz) {
+      T s[6];
+#pragma unroll
+      for (int n = 0; n < 6; ++n)
+        s[n] = T(0.125) * ((part[0][ty][tx][n] + part[0][ty + 1][tx][n]) + (part[1][ty][tx][n] + part[1][ty + 1][tx][n]));
+      const long long Q = cidx(cb, I, J, K);
+      out.Pf[Q] = s[0];
+      out.phi[Q] = s[1];
+      out.Xs[Q] = s[2];
+      out.Pf0[Q] = s[0];
+      out.phi0[Q] = s[1];
+      out.Xs0[Q] = s[2];
+      out.fP[Q] = s[3];
+      out.fphi[Q] = s[4];
+      out.fX[Q] = s[5];
+    }
+  }
 }
 
 template <class T>
@@ -186,56 +204,47 @@ __global__ void __launch_bounds__(256) k_mg_coarse_rhs(Box b, RxCoef<T> c, RxIn<
   out.fX[q] -= e.Xs1 - u0.Xs[q];
 }
 
-// One thread per coarse cell (I, J, K): the correction on its 3 x 3 x 3 neighbourhood (indices
-// held inside the grid), interpolated separably to its 8 children: a child on the low side of
-// its parent in x takes 3/4 of the parent's column and 1/4 of the column at I - 1, on the high
-// side 1/4 of the column at I + 1; then y, then z.
+// One thread per fine x-pair (the two x-children of coarse column I at fine row (j, k)): the
+// correction's coarse columns I - 1, I, I + 1 (held inside the grid) are first weighted over the
+// parent's row and the row on the child's side in y and z (3/4 x 3/4, 3/4 x 1/4, 1/4 x 1/4),
+// then the low child takes 3/4 of column I and 1/4 of I - 1, the high child 1/4 of I + 1.
 template <class T>
-__device__ __forceinline__ void prolong_field(const Box& fb, const Box& cb, const T* __restrict__ e, T* u, int I,
-                                              int J, int K, bool clamp) {
-  long long xo[3], yo[3], zo[3];
+struct __align__(2 * sizeof(T)) MgPair {
+  T lo, hi;
+};
+
+template <class T>
+__device__ __forceinline__ void prolong_pair(const T* __restrict__ e, T* u, long long q0, const long long (&xo)[3],
+                                             const long long (&ro)[4], bool clamp) {
+  T col[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    xo[d] = min(max(I + d - 1, 0), cb.nx - 1);
-    yo[d] = (long long)cb.px * min(max(J + d - 1, 0), cb.ny - 1);
-    zo[d] = cb.pxy * min(max(K + d - 1, 0), cb.nz - 1);
+  for (int d = 0; d < 3; ++d)
+    col[d] = fma(T(0.5625), e[ro[0] + xo[d]],
+                 fma(T(0.1875), e[ro[1] + xo[d]] + e[ro[2] + xo[d]], T(0.0625) * e[ro[3] + xo[d]]));
+  MgPair<T> p = *reinterpret_cast<const MgPair<T>*>(u + q0);
+  p.lo += fma(T(0.75), col[1], T(0.25) * col[0]);
+  p.hi += fma(T(0.75), col[1], T(0.25) * col[2]);
+  if (clamp) {
+    p.lo = rx_clamp(p.lo, T(1e-4), T(1));
+    p.hi = rx_clamp(p.hi, T(1e-4), T(1));
   }
-  // x: rows (y, z) of the neighbourhood -> the two x-children
-  T rx[2][3][3];
-#pragma unroll
-  for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-      const T* row = e + yo[dy] + zo[dz];
-      const T m = row[xo[1]];
-      rx[0][dy][dz] = fma(T(0.75), m, T(0.25) * row[xo[0]]);
-      rx[1][dy][dz] = fma(T(0.75), m, T(0.25) * row[xo[2]]);
-    }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      T ry[3];
-#pragma unroll
-      for (int dz = 0; dz < 3; ++dz) ry[dz] = fma(T(0.75), rx[a][1][dz], T(0.25) * rx[a][b ? 2 : 0][dz]);
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const T v = fma(T(0.75), ry[1], T(0.25) * ry[cc ? 2 : 0]);
-        const long long q = cidx(fb, 2 * I + a, 2 * J + b, 2 * K + cc);
-        u[q] = clamp ? rx_clamp(u[q] + v, T(1e-4), T(1)) : u[q] + v;
-      }
-    }
+  *reinterpret_cast<MgPair<T>*>(u + q0) = p;
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_prolong(Box fb, Box cb, MgCorr<T> e, T* Pf, T* phi, T* Xs) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  const int K = blockIdx.z;
-  if (I >= cb.nx || J >= cb.ny || K >= cb.nz) return;
-  prolong_field(fb, cb, e.Pf, Pf, I, J, K, false);
-  prolong_field(fb, cb, e.phi, phi, I, J, K, true);
-  prolong_field(fb, cb, e.Xs, Xs, I, J, K, false);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (I >= cb.nx || j >= fb.ny || k >= fb.nz) return;
+  const long long xo[3] = {max(I - 1, 0), I, min(I + 1, cb.nx - 1)};
+  const long long yJ = (long long)cb.px * (j >> 1), yN = (long long)cb.px * side_nb(j, cb.ny);
+  const long long zK = cb.pxy * (k >> 1), zN = cb.pxy * side_nb(k, cb.nz);
+  const long long ro[4] = {yJ + zK, yN + zK, yJ + zN, yN + zN};   // weights 9/16, 3/16, 3/16, 1/16
+  const long long q0 = cidx(fb, 2 * I, j, k);
+  prolong_pair(e.Pf, Pf, q0, xo, ro, false);
+  prolong_pair(e.phi, phi, q0, xo, ro, true);
+  prolong_pair(e.Xs, Xs, q0, xo, ro, false);
 }
 
 template <class T>
@@ -278,11 +287,13 @@ void mg_smooth(cudaStream_t s, Box b, const RxCoef<T>& c, double omega, const Rx
 template <class T>
 void mg_restrict(cudaStream_t s, Box fine, Box coarse, const RxCoef<T>& c, const RxIn<T>& in, const MgSrc<T>* fas,
                  const MgCoarse<T>& out) {
+  const dim3 g((unsigned)((fine.nx + kRbx - 1) / kRbx), (unsigned)((fine.ny + kRby - 1) / kRby),
+               (unsigned)((fine.nz + kRbz - 1) / kRbz));
+  const dim3 blk(kRbx, kRby, kRbz);
   if (fas)
-    k_mg_restrict<T, true><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(fine, coarse, c, in, *fas, out);
+    k_mg_restrict<T, true><<<g, blk, 0, s>>>(fine, coarse, c, in, *fas, out);
   else
-    k_mg_restrict<T, false><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(fine, coarse, c, in,
-                                                                      MgSrc<T>{nullptr, nullptr, nullptr}, out);
+    k_mg_restrict<T, false><<<g, blk, 0, s>>>(fine, coarse, c, in, MgSrc<T>{nullptr, nullptr, nullptr}, out);
 }
 
 template <class T>
@@ -292,7 +303,8 @@ void mg_coarse_rhs(cudaStream_t s, Box coarse, const RxCoef<T>& c, const RxIn<T>
 
 template <class T>
 void mg_prolong(cudaStream_t s, Box fine, Box coarse, const MgCorr<T>& e, T* Pf, T* phi, T* Xs) {
-  k_mg_prolong<T><<<grid_of(coarse), dim3(32, 8, 1), 0, s>>>(fine, coarse, e, Pf, phi, Xs);
+  const dim3 g((unsigned)((coarse.nx + 31) / 32), (unsigned)((fine.ny + 7) / 8), (unsigned)fine.nz);
+  k_mg_prolong<T><<<g, dim3(32, 8, 1), 0, s>>>(fine, coarse, e, Pf, phi, Xs);
 }
 
 template <class T>
