@@ -253,6 +253,7 @@ void fill_lean_coef(pt_ctx* c) {
   L.compaction_on = k.compaction_on;
   L.powerlaw_on = k.powerlaw_on;
   L.mu0 = k.mu0; L.eta0 = k.eta0; L.tau0 = k.tau0; L.n_pow = k.n_pow;
+  L.rtau0_2 = 1.0 / (k.tau0 * k.tau0);
   L.rel_mu = k.rel_mu; L.rel_eta = k.rel_eta; L.R_weak = k.R_weak;
   L.rGdtS = k.rGdtS;
   L.dtaupt_fac = k.dtaupt_fac;

@@ -25,6 +25,7 @@ struct LeanCoef {
   int bg_on;                    // tau_bg != 0: wall xy-edges carry the background stress
   // Picard and coefficient refresh run in FP64
   double mu0, eta0, tau0, n_pow, rel_mu, rel_eta, R_weak;
+  double rtau0_2;               // 1 / tau0^2
   double rGdtS, dtaupt_fac, dtauv_fac;
 };
 

@@ -66,6 +66,15 @@ __device__ inline double rcp_pseudo(double x) {
 }
 __device__ inline float rcp_pseudo(float x) { return __frcp_rn(x); }
 
+// 1 / x to rounding accuracy for the coefficients that set the fixed point (x > 0, normal):
+// two Newton steps r' = r + r (1 - x r) on the hardware's approximate reciprocal.
+__device__ inline double rcp_full(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
 
 }  // namespace lean_detail
 
@@ -248,22 +257,27 @@ __device__ __forceinline__ void lean_picard_point(const Box& b, const LeanCoef<T
     const double axz = 0.25 * ((double)in.txz[q] + in.txz[q + 1] + in.txz[q + pxy] + in.txz[q + 1 + pxy]);
     const double ayz = 0.25 * ((double)in.tyz[q] + in.tyz[q + px] + in.tyz[q + pxy] + in.tyz[q + px + pxy]);
     const double sxx = in.txx[q], syy = in.tyy[q], szz = in.tzz[q];
-    const double tII = sqrt(0.5 * (sxx * sxx + syy * syy + szz * szz) + axy * axy + axz * axz + ayz * ayz);
-    double mus = c.mu0;
+    // tau_II^2 = (sxx^2 + syy^2 + szz^2) / 2 + axy^2 + axz^2 + ayz^2 (explicit FMAs: every form
+    // that inlines this body rounds it alike)
+    const double tII2 = fma(0.5, fma(sxx, sxx, fma(syy, syy, szz * szz)), fma(axy, axy, fma(axz, axz, ayz * ayz)));
+    // Eq. 24: mu* = mu0 / (1 + (tau_II / tau0)^(n-1)); the log-space relaxation
+    // exp(rel log mu* + (1 - rel) log mu) is written mu (mu* / mu)^rel, and log(mu* / mu) is the
+    // Picard change itself
+    double den = 1.0;
     if (c.powerlaw_on) {
-      const double x = tII / c.tau0;
+      const double x2 = tII2 * c.rtau0_2;                        // (tau_II / tau0)^2
       const double p = c.n_pow - 1.0;
-      mus = c.mu0 / (1.0 + (p == 2.0 ? x * x : pow(x, p)));
+      den = p == 2.0 ? 1.0 + x2 : 1.0 + exp(0.5 * p * log(x2));
     }
     const double mu_old = mu[q], eta_old = eta[q];
-    const double lmus = log(mus), lmu = log(mu_old);
-    const double mu_new = exp(c.rel_mu * lmus + (1.0 - c.rel_mu) * lmu);
+    const double d_mu = log(c.mu0 / (den * mu_old));             // log mu* - log mu
+    const double mu_new = mu_old * exp(c.rel_mu * d_mu);
     const double R = (in.Pf1[q] > in.Pt1[q]) ? c.R_weak : 1.0;
-    const double etas = c.eta0 * mu_new / (double)in.phi1[q] * R;
-    const double letas = log(etas), leta = log(eta_old);
-    r = fmax(fabs(lmus - lmu), fabs(letas - leta));
+    // Eq. 26: eta* = eta0 mu / phi R (with the relaxed mu), relaxed the same way
+    const double d_eta = log(c.eta0 * mu_new * R / ((double)in.phi1[q] * eta_old));
+    r = fmax(fabs(d_mu), fabs(d_eta));
     mu[q] = (T)mu_new;
-    eta[q] = (T)exp(c.rel_eta * letas + (1.0 - c.rel_eta) * leta);
+    eta[q] = (T)(eta_old * exp(c.rel_eta * d_eta));
   }
 }
 
@@ -271,54 +285,56 @@ __device__ __forceinline__ void lean_picard_point(const Box& b, const LeanCoef<T
 template <class T>
 __device__ __forceinline__ void lean_coef_point(const Box& b, const LeanCoef<T>& c, const LeanCoefIn<T>& in,
                                                 const LeanCoefOut<T>& out, int i, int j, int k) {
+  using namespace lean_detail;
   if (i > b.nx || j > b.ny || k > b.nz) return;
   const long long q = cidx(b, i, j, k);
   const long long px = b.px, pxy = b.pxy;
   const double rG = c.rGdtS;
   if (i < b.nx && j < b.ny && k < b.nz) {
     const double m = in.mu[q];
-    const double s = 1.0 / (1.0 + m * rG);
+    const double s = rcp_full(fma(m, rG, 1.0));
     const double a = 1.0 - s;                         // xi / (1 + xi)
     out.cm2[q] = (T)(2.0 * m * s);
     out.toa_xx[q] = (T)(in.txxo[q] * a);
     out.toa_yy[q] = (T)(in.tyyo[q] * a);
     out.toa_zz[q] = (T)(in.tzzo[q] * a);
-    out.idtp[q] = (T)(1.0 / (c.dtaupt_fac * m) + (double)c.bd_rdt);   // 1/dtau_Pt + beta_d/dt
-    out.ieta[q] = (T)(1.0 / (double)in.eta[q]);
+    out.idtp[q] = (T)(rcp_full(c.dtaupt_fac * m) + (double)c.bd_rdt);   // 1/dtau_Pt + beta_d/dt
+    out.ieta[q] = (T)rcp_full((double)in.eta[q]);
   }
   if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
     const double m = 0.25 * ((double)in.mu[q - 1 - px] + in.mu[q - px] + in.mu[q - 1] + in.mu[q]);
-    const double s = 1.0 / (1.0 + m * rG);
+    const double s = rcp_full(fma(m, rG, 1.0));
     out.em2_xy[q] = (T)(2.0 * m * s * (double)c.hrdy);
     out.eb_xy[q] = (T)(2.0 * m * s * (double)c.hrdx);
     // the background shear's stress 2 mu/(1+xi) tau_bg/(2 mu0) (Eqs. 32-33) joins the old-stress part
     out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
   } else if (k < b.nz && c.bg_on) {   // wall xy-edges carry the background stress
     const double m = edge_mean_mu_xy(b, in.mu, q, i, j);
-    const double s = 1.0 / (1.0 + m * rG);
+    const double s = rcp_full(fma(m, rG, 1.0));
     out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
   }
   if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
     const double m = 0.25 * ((double)in.mu[q - 1 - pxy] + in.mu[q - pxy] + in.mu[q - 1] + in.mu[q]);
-    const double s = 1.0 / (1.0 + m * rG);
+    const double s = rcp_full(fma(m, rG, 1.0));
     out.em2_xz[q] = (T)(2.0 * m * s * (double)c.hrdz);
     out.eb_xz[q] = (T)(2.0 * m * s * (double)c.hrdx);
     out.toa_xz[q] = (T)(in.txzo[q] * (1.0 - s));
   }
   if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
     const double m = 0.25 * ((double)in.mu[q - px - pxy] + in.mu[q - pxy] + in.mu[q - px] + in.mu[q]);
-    const double s = 1.0 / (1.0 + m * rG);
+    const double s = rcp_full(fma(m, rG, 1.0));
     out.em2_yz[q] = (T)(2.0 * m * s * (double)c.hrdz);
     out.eb_yz[q] = (T)(2.0 * m * s * (double)c.hrdy);
     out.toa_yz[q] = (T)(in.tyzo[q] * (1.0 - s));
   }
   // pseudo-time steps of the velocities, mean of the two centres' dtau_V = fac / mu
+  const double imu = (i < b.nx && j < b.ny && k < b.nz) ? rcp_full((double)in.mu[q]) : 0.0;
   if (i > 0 && i < b.nx && j < b.ny && k < b.nz)
-    out.dtv_x[q] = (T)(0.5 * c.dtauv_fac * (1.0 / (double)in.mu[q - 1] + 1.0 / (double)in.mu[q]));
+    out.dtv_x[q] = (T)(0.5 * c.dtauv_fac * (rcp_full((double)in.mu[q - 1]) + imu));
   if (j > 0 && j < b.ny && i < b.nx && k < b.nz)
-    out.dtv_y[q] = (T)(0.5 * c.dtauv_fac * (1.0 / (double)in.mu[q - px] + 1.0 / (double)in.mu[q]));
+    out.dtv_y[q] = (T)(0.5 * c.dtauv_fac * (rcp_full((double)in.mu[q - px]) + imu));
   if (k > 0 && k < b.nz && i < b.nx && j < b.ny)
-    out.dtv_z[q] = (T)(0.5 * c.dtauv_fac * (1.0 / (double)in.mu[q - pxy] + 1.0 / (double)in.mu[q]));
+    out.dtv_z[q] = (T)(0.5 * c.dtauv_fac * (rcp_full((double)in.mu[q - pxy]) + imu));
 }
 
 }  // namespace pt
