@@ -249,6 +249,9 @@ void fill_lean_coef(pt_ctx* c) {
   L.drho_g = p.rhof_g - p.rhos_g;
   L.ifac_pf = 1.0 / k.dtaupf_fac;
   L.rrho_i = k.rrho_i;
+  L.rho_i = 1.0 / k.rrho_i;
+  L.rdx_r = k.rdx * k.rrho_i; L.rdy_r = k.rdy * k.rrho_i; L.rdz_r = k.rdz * k.rrho_i;
+  L.drho_g_r = (p.rhof_g - p.rhos_g) * k.rrho_i;
   L.damp_x = k.damp_x; L.damp_y = k.damp_y; L.damp_z = k.damp_z;
   L.compaction_on = k.compaction_on;
   L.powerlaw_on = k.powerlaw_on;

@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(BX * BY) k_batch_phase(const BatchInst* __rest
       lean_face_point(I.b, I.c, I.fin[a], I.Vx, I.Vy, I.Vz, I.Rx, I.Ry, I.Rz, i, j, k, check, r_v, mask);
       if (check) block_max_atomic(r_v, I.red + RED_V);
     } else if (PHASE == BATCH_PICARD) {
-      double rp = 0.0;
+      double rp = 1.0;
       lean_picard_point(I.b, I.c, I.pin[a], I.mu, I.eta, i, j, k, rp);
-      block_max_atomic(own ? rp : 0.0, I.red + RED_PIC);
+      block_max_log_atomic(own ? rp : 1.0, I.red + RED_PIC);
     } else {
       lean_coef_point(I.b, I.c, I.kin, I.kout, i, j, k);
     }

@@ -59,7 +59,8 @@ enum { RED_V = 0, RED_PT = 1, RED_PF = 2, RED_PIC = 3, RED_MUMAX = 4, RED_GMAX =
 // Max-reduction of non-negative doubles through their bit patterns (monotone for x >= 0; a
 // NaN from fabs has the largest pattern and therefore surfaces in the norm). Every thread of
 // the block must call it (it synchronises the block).
-__device__ inline void block_max_atomic(double v, unsigned long long* slot) {
+template <bool LOG>
+__device__ inline void block_max_atomic_impl(double v, unsigned long long* slot) {
   unsigned long long u = (unsigned long long)__double_as_longlong(v);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -79,9 +80,23 @@ __device__ inline void block_max_atomic(double v, unsigned long long* slot) {
       unsigned long long w = __shfl_xor_sync(0xffffffffu, u, o);
       u = w > u ? w : u;
     }
-    if (lane == 0 && u != 0ull) atomicMax(slot, u);
+    if (LOG) {
+      if (lane == 0) {
+        const double l = log(__longlong_as_double((long long)u));
+        if (!(l <= 0.0)) atomicMax(slot, (unsigned long long)__double_as_longlong(l));   // > 0 or NaN
+      }
+    } else if (lane == 0 && u != 0ull) {
+      atomicMax(slot, u);
+    }
   }
   __syncthreads();  // warp_max may be reused by the next call in the same kernel
 }
+
+__device__ inline void block_max_atomic(double v, unsigned long long* slot) { block_max_atomic_impl<false>(v, slot); }
+
+// The same for values >= 1 whose log goes into the slot: log is monotone, so the block takes the
+// max of the values and one thread the log (a NaN still has the largest pattern). Every thread of
+// the block calls it; a thread with nothing to contribute passes 1.
+__device__ inline void block_max_log_atomic(double v, unsigned long long* slot) { block_max_atomic_impl<true>(v, slot); }
 
 }  // namespace pt

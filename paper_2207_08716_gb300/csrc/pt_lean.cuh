@@ -20,6 +20,8 @@ struct LeanCoef {
   T rphi0, k0, phi0, drho_g;    // 1 / phi0, k0, phi0, (rho_f - rho_s) g
   T ifac_pf;                    // 1 / (cfl_pf h^2 (1 + beta_d B / alpha)): 1/dtau_Pf = kmax * ifac_pf
   T rrho_i, damp_x, damp_y, damp_z;
+  T rdx_r, rdy_r, rdz_r, drho_g_r;  // 1/(d rho_i), (rho_f - rho_s) g / rho_i: the momentum residual over rho_i
+  T rho_i;
   int compaction_on, powerlaw_on;
   T ebg;                        // background xy strain rate tau_bg / (2 mu0) (Eqs. 32-33)
   int bg_on;                    // tau_bg != 0: wall xy-edges carry the background stress

@@ -214,42 +214,46 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
     const bool fz = k > 0 && k < b.nz && i < b.nx && j < b.ny;
     // all loads before the first store (the arrays are not declared non-aliasing)
     T Fx = T(0), Fy = T(0), Fz = T(0), Rx1 = T(0), Ry1 = T(0), Rz1 = T(0), Vx1 = T(0), Vy1 = T(0), Vz1 = T(0);
+    // F / rho_i directly (the spacings carry 1/rho_i); the norm takes |F| = rho_i |F / rho_i|
     if (fx) {
-      Fx = (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
-           (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - 1]) * c.rdx;
-      Rx1 = Fx * c.rrho_i + c.damp_x * Rx[q];
-      Vx1 = Vx[q] + in.dtv_x[q] * Rx1;
+      Fx = (in.txx[q] - in.txx[q - 1]) * c.rdx_r + (in.txy[q + px] - in.txy[q]) * c.rdy_r +
+           (in.txz[q + pxy] - in.txz[q]) * c.rdz_r - (in.Pt1[q] - in.Pt1[q - 1]) * c.rdx_r;
+      Rx1 = fma(c.damp_x, Rx[q], Fx);
+      Vx1 = fma(in.dtv_x[q], Rx1, Vx[q]);
     }
     if (fy) {
-      Fy = (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
-           (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - px]) * c.rdy;
-      Ry1 = Fy * c.rrho_i + c.damp_y * Ry[q];
-      Vy1 = Vy[q] + in.dtv_y[q] * Ry1;
+      Fy = (in.txy[q + 1] - in.txy[q]) * c.rdx_r + (in.tyy[q] - in.tyy[q - px]) * c.rdy_r +
+           (in.tyz[q + pxy] - in.tyz[q]) * c.rdz_r - (in.Pt1[q] - in.Pt1[q - px]) * c.rdy_r;
+      Ry1 = fma(c.damp_y, Ry[q], Fy);
+      Vy1 = fma(in.dtv_y[q], Ry1, Vy[q]);
     }
     if (fz) {
       // buoyancy -(rho g - rho_BG g) averaged to the face, rho g - rho_BG g = (phi - phi0) drho_g
-      const T rog = (T(0.5) * (in.phi[q - pxy] + in.phi[q]) - c.phi0) * c.drho_g;
-      Fz = (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
-           (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.Pt1[q] - in.Pt1[q - pxy]) * c.rdz - rog;
-      Rz1 = Fz * c.rrho_i + c.damp_z * Rz[q];
-      Vz1 = Vz[q] + in.dtv_z[q] * Rz1;
+      const T rog = (T(0.5) * (in.phi[q - pxy] + in.phi[q]) - c.phi0) * c.drho_g_r;
+      Fz = (in.txz[q + 1] - in.txz[q]) * c.rdx_r + (in.tyz[q + px] - in.tyz[q]) * c.rdy_r +
+           (in.tzz[q] - in.tzz[q - pxy]) * c.rdz_r - (in.Pt1[q] - in.Pt1[q - pxy]) * c.rdz_r - rog;
+      Rz1 = fma(c.damp_z, Rz[q], Fz);
+      Vz1 = fma(in.dtv_z[q], Rz1, Vz[q]);
     }
     if (fx) { Rx[q] = Rx1; Vx[q] = Vx1; }
     if (fy) { Ry[q] = Ry1; Vy[q] = Vy1; }
     if (fz) { Rz[q] = Rz1; Vz[q] = Vz1; }
     if (check) {
-      if (fx && (mask & 1)) r_v = fmax(r_v, (double)tabs(Fx));
-      if (fy && (mask & 2)) r_v = fmax(r_v, (double)tabs(Fy));
-      if (fz && (mask & 4)) r_v = fmax(r_v, (double)tabs(Fz));
+      if (fx && (mask & 1)) r_v = fmax(r_v, (double)tabs(Fx) * (double)c.rho_i);
+      if (fy && (mask & 2)) r_v = fmax(r_v, (double)tabs(Fy) * (double)c.rho_i);
+      if (fz && (mask & 4)) r_v = fmax(r_v, (double)tabs(Fz) * (double)c.rho_i);
     }
   }
 }
 
-// Picard targets and relaxation at cell (i, j, k).
+// Picard targets and relaxation at cell (i, j, k). m = max(x, 1/x) over the ratios x = mu*/mu
+// and eta*/eta (>= 1): its log is the Picard change max(|log mu* - log mu|, |log eta* - log eta|),
+// taken once per block by the caller (log is monotone).
 template <class T>
 __device__ __forceinline__ void lean_picard_point(const Box& b, const LeanCoef<T>& c, const LeanPicardIn<T>& in,
                                                   T* __restrict__ mu, T* __restrict__ eta, int i, int j, int k,
-                                                  double& r) {
+                                                  double& m) {
+  using namespace lean_detail;
   if (i < b.nx && j < b.ny && k < b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
@@ -261,8 +265,7 @@ __device__ __forceinline__ void lean_picard_point(const Box& b, const LeanCoef<T
     // that inlines this body rounds it alike)
     const double tII2 = fma(0.5, fma(sxx, sxx, fma(syy, syy, szz * szz)), fma(axy, axy, fma(axz, axz, ayz * ayz)));
     // Eq. 24: mu* = mu0 / (1 + (tau_II / tau0)^(n-1)); the log-space relaxation
-    // exp(rel log mu* + (1 - rel) log mu) is written mu (mu* / mu)^rel, and log(mu* / mu) is the
-    // Picard change itself
+    // exp(rel log mu* + (1 - rel) log mu) is written mu (mu* / mu)^rel (a square root for rel = 1/2)
     double den = 1.0;
     if (c.powerlaw_on) {
       const double x2 = tII2 * c.rtau0_2;                        // (tau_II / tau0)^2
@@ -270,14 +273,15 @@ __device__ __forceinline__ void lean_picard_point(const Box& b, const LeanCoef<T
       den = p == 2.0 ? 1.0 + x2 : 1.0 + exp(0.5 * p * log(x2));
     }
     const double mu_old = mu[q], eta_old = eta[q];
-    const double d_mu = log(c.mu0 / (den * mu_old));             // log mu* - log mu
-    const double mu_new = mu_old * exp(c.rel_mu * d_mu);
+    const double x_mu = c.mu0 / (den * mu_old);                  // mu* / mu
+    const double mu_new = mu_old * (c.rel_mu == 0.5 ? sqrt(x_mu) : exp(c.rel_mu * log(x_mu)));
     const double R = (in.Pf1[q] > in.Pt1[q]) ? c.R_weak : 1.0;
     // Eq. 26: eta* = eta0 mu / phi R (with the relaxed mu), relaxed the same way
-    const double d_eta = log(c.eta0 * mu_new * R / ((double)in.phi1[q] * eta_old));
-    r = fmax(fabs(d_mu), fabs(d_eta));
+    const double x_eta = c.eta0 * mu_new * R / ((double)in.phi1[q] * eta_old);
+    m = fmax(fmax(x_mu, rcp_full(x_mu)), fmax(x_eta, rcp_full(x_eta)));
+    if (!(x_mu == x_mu && x_eta == x_eta)) m = x_mu + x_eta;     // NaN stays NaN (fmax drops it)
     mu[q] = (T)mu_new;
-    eta[q] = (T)(eta_old * exp(c.rel_eta * d_eta));
+    eta[q] = (T)(eta_old * (c.rel_eta == 0.5 ? sqrt(x_eta) : exp(c.rel_eta * log(x_eta))));
   }
 }
 

@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(256) k_lean_picard(Box b, LeanCoef<T> c, LeanP
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  double r = 0.0;
-  lean_picard_point(b, c, in, mu, eta, i, j, k, r);
-  block_max_atomic(r, red + RED_PIC);
+  double m = 1.0;
+  lean_picard_point(b, c, in, mu, eta, i, j, k, m);
+  block_max_log_atomic(m, red + RED_PIC);
 }
 
 // --------------------------------------------------------------------- coefficient refresh
