@@ -52,9 +52,9 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2}
 # FP64 thread instructions (DFMA + DADD + DMUL) and flops (DFMA x 2 + DADD + DMUL) per cell and
 # launch from one ncu capture of the kernel (profiles/k_lean_fp64_191.md, k_adj_cells_95.md,
 # k_centres_fp64_stepwise_191.md); a kernel missing here has no current count.
-KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 99.9, "k_lean_faces": 35.8, "k_adj_cells": 76.5,
-                             "k_centres": 152.0}
-KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 147.9, "k_lean_faces": 52.7, "k_adj_cells": 115.2,
+KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 99.9, "k_lean_faces": 32.8, "k_lean_picard": 105.2,
+                             "k_lean_coef": 91.5, "k_adj_cells": 76.5, "k_centres": 152.0}
+KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 147.9, "k_lean_faces": 49.7, "k_adj_cells": 115.2,
                               "k_centres": 237.0}
 # The FP64 pipe issues at most 304 thread-instructions per GPU clock (2 per SM; ncu's
 # sm__inst_executed_pipe_fp64 peak on this machine's GB300), i.e. 629 G/s at 2.07 GHz.
