@@ -111,6 +111,9 @@ def parse():
     ap.add_argument("--mg-sweeps", default="", help="nu_pre,nu_post,nu_coarse of the V-cycle (default 2,2,30)")
     ap.add_argument("--mg-plain-steps", type=int, default=2,
                     help="timed converged steps of the plain PT solver (after one warm-up step)")
+    ap.add_argument("--batch-precision", choices=("fp64", "fp32"), default="fp64",
+                    help="precision of the batched ensemble (fp32: defect-correction solvers stepped "
+                         "concurrently, each on its own stream)")
     ap.add_argument("--batched-converge", action="store_true",
                     help="run one step of the batched ensemble to convergence and report p50/p99 "
                          "time-to-converge (minutes of GPU time) instead of the throughput bench")
@@ -318,13 +321,17 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
     import torch
     from paper_2207_08716_gb300.solver import PTBatch
 
-    mem = I.ensemble(seed=M.replica_seed(rank), n_inst=args.batch_n, max_iter=40000)
+    fp32 = getattr(args, "batch_precision", "fp64") == "fp32"
+    # the FP32 form counts its inner FP32 iterations, 2-4x the FP64 form's iterations (at least
+    # nup of them per outer Picard update)
+    mem = I.ensemble(seed=M.replica_seed(rank), n_inst=args.batch_n, max_iter=160000 if fp32 else 40000)
     if not converge:
         for p, _ in mem:
             p["tol"] = 0.0
             p["max_iter"] = args.batch_iters
     cells = [p["nx"] * p["ny"] * p["nz"] for p, _ in mem]
-    b = PTBatch(mem, device=dev)
+    from paper_2207_08716_gb300 import native as N
+    b = PTBatch(mem, device=dev, precision=N.PT_FP32 if fp32 else N.PT_FP64)
     del mem
     for _ in range(warmup):
         b.step()
@@ -348,7 +355,9 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
            "cell_updates_per_s": upd / t, "instances": len(cells), "total_cells": sum(cells),
            "iters_per_step": None if converge else args.batch_iters, "seconds": t,
            "tile": [bx, by], "iters_per_graph": ipg, "clocks": clk,
-           "value_definition": "T_eff-equivalent: 25 x 8 B x aggregate cell updates per second"}
+           "precision": "fp32" if fp32 else "fp64",
+           "value_definition": "T_eff-equivalent: 25 x 8 B x aggregate cell updates per second"
+                               + (" (FP32: inner FP32 PT iterations)" if fp32 else "")}
     if converge:
         st = sorted(ttc_all)
         out.update(statuses=[r["status"] for r in reps], iters=[r["iters"] for r in reps],

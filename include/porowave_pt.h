@@ -245,8 +245,12 @@ typedef struct {
 int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *workspace, size_t bytes);
 
 /* ---- Batched ensemble --------------------------------------------------------
- * ninst independent instances (each its own grid, parameters, fields and numerics; FP64 lean
- * form, precision PT_FP64) advanced together: one launch per PT phase covers all instances
+ * ninst independent instances (each its own grid, parameters, fields and numerics), all
+ * PT_FP64 or all PT_FP32 (mixing returns PT_EINVAL). FP32 ensembles: every instance runs the
+ * FP32 + FP64 defect-correction pt_step, whose outer and inner iterations are decided per
+ * instance, on a stream of its own, the instances stepped concurrently by one host thread each;
+ * time_to_converge_ms is host time from the common start to the instance's return, and
+ * pt_batch_config reports zeros. FP64 ensembles (the FP64-lean form) are advanced together: one launch per PT phase covers all instances
  * through a flat work list of (instance, tile) items walked by a persistent grid-stride grid, and
  * 2 nup (or 4 nup) iterations are captured in one CUDA graph per replay. Each instance stops at
  * its own first check with norms < tol (or at its max_iter / a non-finite norm), exactly where

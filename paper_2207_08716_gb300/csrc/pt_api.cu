@@ -13,6 +13,8 @@
 #include <cstring>
 #include <new>
 #include <array>
+#include <chrono>
+#include <thread>
 #include <vector>
 
 #include "../../include/porowave_pt.h"
@@ -90,6 +92,8 @@ struct pt_ctx {
   LeanCoef<double> lcoef;
   // mixed-precision path (precision PT_FP32): FP32 correction problem
   bool mixed;
+  double mix_omega;         // PT_FP32: weight of the outer update u <- u + omega delta
+  double mix_prev;          // PT_FP32: the previous outer residual max (0 at a step's start)
   float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_iden_pt, *m_idtf, *m_iden_pf;
   float *m_cm2, *m_em2_xy, *m_em2_xz, *m_em2_yz;
   float *m_dVx, *m_dVy, *m_dVz, *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
@@ -425,6 +429,17 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
     *converged = true;
     return PT_OK;
   }
+  // globalisation of the outer loop: when the last update more than doubled the FP64 residual,
+  // halve the weight of the next ones (down to 1/16); while it falls, let the weight grow back
+  // to 1 (the fixed point does not depend on the weight)
+  {
+    const double r = report_max(outer);
+    if (c->mix_prev > 0.0) {
+      if (r > 2.0 * c->mix_prev) c->mix_omega = std::max(c->mix_omega * 0.5, 0.0625);
+      else if (r < c->mix_prev) c->mix_omega = std::min(c->mix_omega * 1.25, 1.0);
+    }
+    c->mix_prev = r;
+  }
   const double target = (c->num.inner_rtol > 0 ? c->num.inner_rtol : kInnerRtol) * report_max(outer);
   // (iii) FP32 PT on the correction, from delta = 0, R = 0
   MixCoefOut mco{c->m_cm2, c->m_em2_xy, c->m_em2_xz, c->m_em2_yz, c->m_dtv_x, c->m_dtv_y, c->m_dtv_z};
@@ -457,7 +472,8 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
     }
   }
   // (iv) u <- u + delta in FP64, then the FP64 porosity time integration (Eq. 22, log space)
-  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d]};
+  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d],
+               c->mix_omega};
   PT_LAUNCH(c, K_MIX_UPDATE, mix_update(gr, bl, c->stream, b, mu));
   PT_LAUNCH(c, K_POROSITY,
             k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[a], c->Pf[a],
@@ -596,6 +612,8 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   for (int s = 0; s < arrays; ++s) *slots[s] = (double*)(w + s * stride);
   char* wend = w + arrays * stride;
   c->mixed = num->precision == PT_FP32;
+  c->mix_omega = 1.0;
+  c->mix_prev = 0.0;
   if (c->mixed) {
     const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
     float** fslots[kMixArrays] = {
@@ -644,6 +662,10 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
 }
 
 int pt_step_begin(pt_ctx* c) {
+  if (c) {
+    c->mix_omega = 1.0;
+    c->mix_prev = 0.0;
+  }
   if (!c) return PT_EINVAL;
   int rc = step_begin_launch(c);
   double mu_max = 0.0;
@@ -862,6 +884,11 @@ struct pt_batch {
   int nslabs, slab_elems;
   DDTables tables;
   std::vector<std::array<int, 6>> own;   // per instance: own_lo[3], own_hi[3]
+  // FP32 ensembles (every instance PT_FP32): the defect-correction loop's outer and inner
+  // iterations are decided per instance on the host, so the instances run as independent
+  // solvers, each on a stream of its own, stepped concurrently by one host thread per instance
+  bool concurrent;
+  std::vector<cudaStream_t> streams;
 };
 
 namespace {
@@ -1000,8 +1027,9 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   *out = nullptr;
   if (ninst < 1 || !grids || !phys || !nums || !fields || !workspace) return PT_EINVAL;
   if (((uintptr_t)workspace & (kAlign - 1)) != 0) return PT_EINVAL;
+  const bool fp32 = nums[0].precision == PT_FP32;
   for (int m = 0; m < ninst; ++m)
-    if (nums[m].precision != PT_FP64 || nums[m].nup != nums[0].nup) return PT_EINVAL;
+    if (nums[m].precision != (fp32 ? PT_FP32 : PT_FP64) || nums[m].nup != nums[0].nup) return PT_EINVAL;
   const size_t need = pt_batch_workspace_size(ninst, grids, nums);
   if (need == 0) return PT_EINVAL;
   if (workspace_bytes < need) return PT_ESPACE;
@@ -1031,11 +1059,18 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   B->slab_elems = 0;
   B->ctx.assign(ninst, nullptr);
   B->h_inst.resize(ninst);
+  B->concurrent = fp32;
   char* w = (char*)workspace;
   int rc = PT_OK;
+  if (fp32) {
+    B->streams.assign(ninst, nullptr);
+    for (int m = 0; m < ninst && rc == PT_OK; ++m)
+      if (cudaStreamCreateWithFlags(&B->streams[m], cudaStreamNonBlocking) != cudaSuccess) rc = PT_ECUDA;
+  }
   for (int m = 0; m < ninst && rc == PT_OK; ++m) {
     const size_t s = pt_workspace_size(&grids[m], &nums[m]);
-    rc = pt_init(&B->ctx[m], &grids[m], &phys[m], &nums[m], &fields[m], w, s, (void*)B->stream, 0);
+    rc = pt_init(&B->ctx[m], &grids[m], &phys[m], &nums[m], &fields[m], w, s,
+                 (void*)(fp32 ? B->streams[m] : B->stream), 0);
     w += align_up(s, kAlign);
   }
   if (rc == PT_OK) {
@@ -1045,6 +1080,8 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   }
   if (rc != PT_OK) {
     for (pt_ctx* c : B->ctx) pt_destroy(c);
+    for (cudaStream_t s : B->streams)
+      if (s) cudaStreamDestroy(s);
     cudaStreamDestroy(B->stream);
     delete B;
     return rc;
@@ -1053,10 +1090,36 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   return PT_OK;
 }
 
+namespace {
+// FP32 ensemble step: every instance's pt_step (defect-correction loop, host-driven) on its own
+// stream and host thread; time to converge = host time from the common start to its return.
+int batch_step_concurrent(pt_batch* B, pt_report* reps, double* ttc_ms) {
+  std::vector<int> rcs(B->ninst, PT_OK);
+  std::vector<std::thread> pool;
+  pool.reserve(B->ninst);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int m = 0; m < B->ninst; ++m)
+    pool.emplace_back([B, m, reps, ttc_ms, t0, &rcs] {
+      rcs[m] = pt_step(B->ctx[m], &reps[m]);
+      const auto t1 = std::chrono::steady_clock::now();
+      if (ttc_ms) ttc_ms[m] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    });
+  for (std::thread& t : pool) t.join();
+  int any_nc = 0, any_nan = 0;
+  for (int m = 0; m < B->ninst; ++m) {
+    if (rcs[m] != PT_OK && rcs[m] != PT_ENOTCONV && rcs[m] != PT_ENAN) return rcs[m];
+    any_nc |= rcs[m] == PT_ENOTCONV;
+    any_nan |= rcs[m] == PT_ENAN;
+  }
+  return any_nan ? PT_ENAN : (any_nc ? PT_ENOTCONV : PT_OK);
+}
+}  // namespace
+
 int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
   if (!B || !reps) return PT_EINVAL;
   // order after the caller's prior work on its stream
   if (cudaStreamSynchronize(B->caller) != cudaSuccess) return PT_ECUDA;
+  if (B->concurrent) return batch_step_concurrent(B, reps, ttc_ms);
   int rc = PT_OK;
   int cap = 0;
   if (B->coupled) {
@@ -1152,9 +1215,9 @@ int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
 
 int pt_batch_config(const pt_batch* B, int32_t* tile_x, int32_t* tile_y, int32_t* ipg) {
   if (!B) return PT_EINVAL;
-  if (tile_x) *tile_x = B->bx;
-  if (tile_y) *tile_y = B->by;
-  if (ipg) *ipg = B->ipg;
+  if (tile_x) *tile_x = B->concurrent ? 0 : B->bx;
+  if (tile_y) *tile_y = B->concurrent ? 0 : B->by;
+  if (ipg) *ipg = B->concurrent ? 0 : B->ipg;
   return PT_OK;
 }
 
@@ -1163,6 +1226,8 @@ void pt_batch_destroy(pt_batch* B) {
   cudaStreamSynchronize(B->stream);
   if (B->exec) cudaGraphExecDestroy(B->exec);
   for (pt_ctx* c : B->ctx) pt_destroy(c);
+  for (cudaStream_t s : B->streams)
+    if (s) cudaStreamDestroy(s);
   cudaFreeHost(B->h_st);
   cudaStreamDestroy(B->stream);
   delete B;

@@ -23,6 +23,7 @@ struct MixCoefOut {
 struct MixUpdate {
   double *Vx, *Vy, *Vz, *Pt, *Pf;
   const float *dVx, *dVy, *dVz, *dPt, *dPf;
+  double omega;             // u <- u + omega delta
 };
 
 template <class T>

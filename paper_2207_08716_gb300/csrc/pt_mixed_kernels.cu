@@ -295,12 +295,13 @@ __global__ void __launch_bounds__(256) k_mix_update(Box b, MixUpdate u) {
   const int k = blockIdx.z;
   if (i > b.nx || j > b.ny || k > b.nz) return;
   const long long q = cidx(b, i, j, k);
-  if (i > 0 && i < b.nx && j < b.ny && k < b.nz) u.Vx[q] += (double)u.dVx[q];
-  if (j > 0 && j < b.ny && i < b.nx && k < b.nz) u.Vy[q] += (double)u.dVy[q];
-  if (k > 0 && k < b.nz && i < b.nx && j < b.ny) u.Vz[q] += (double)u.dVz[q];
+  const double w = u.omega;
+  if (i > 0 && i < b.nx && j < b.ny && k < b.nz) u.Vx[q] = fma(w, (double)u.dVx[q], u.Vx[q]);
+  if (j > 0 && j < b.ny && i < b.nx && k < b.nz) u.Vy[q] = fma(w, (double)u.dVy[q], u.Vy[q]);
+  if (k > 0 && k < b.nz && i < b.nx && j < b.ny) u.Vz[q] = fma(w, (double)u.dVz[q], u.Vz[q]);
   if (i < b.nx && j < b.ny && k < b.nz) {
-    u.Pt[q] += (double)u.dPt[q];
-    u.Pf[q] += (double)u.dPf[q];
+    u.Pt[q] = fma(w, (double)u.dPt[q], u.Pt[q]);
+    u.Pf[q] = fma(w, (double)u.dPf[q], u.Pf[q]);
   }
 }
 

@@ -225,11 +225,12 @@ class PTSolver:
 class PTBatch:
     """An ensemble of independent instances advanced together (pt_batch_* of the C ABI).
 
-    members: list of (params, phi) or (params, phi, logk); every instance uses the FP64-lean
-    form and the same nup.
+    members: list of (params, phi) or (params, phi, logk); every instance uses the same nup and
+    the same precision: PT_FP64 (the FP64-lean form in the persistent batched engine) or PT_FP32
+    (defect-correction solvers stepped concurrently, each on a stream of its own).
     """
 
-    def __init__(self, members, device="cuda", stream=None):
+    def __init__(self, members, device="cuda", stream=None, precision: int = N.PT_FP64):
         self.lib = N.load()
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -240,7 +241,7 @@ class PTBatch:
         with torch.cuda.device(self.device):
             for m, mem in enumerate(members):
                 p = dict(mem[0])
-                p["precision"] = N.PT_FP64
+                p["precision"] = precision
                 G[m], P[m], U[m] = N.grid_from(p), N.phys_from(p), N.num_from(p)
                 px = self.lib.pt_pitch_x(C.byref(G[m]))
                 box = (p["nz"] + 1, p["ny"] + 1, px)

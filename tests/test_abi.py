@@ -141,3 +141,19 @@ def test_multigrid_hierarchy_is_validated_on_the_host(lib):
     assert not h.value
     assert lib.rx_mg_step(None, None) == N.PT_EINVAL
     assert lib.rx_mg_cycles(None, 1, None) == N.PT_EINVAL
+
+
+def test_batch_rejects_mixed_precisions_on_the_host(lib):
+    """An ensemble is all PT_FP64 or all PT_FP32; a mix is rejected before any CUDA call."""
+    import pt_inputs as I
+    from paper_2207_08716_gb300 import native as N
+    ps = [I.c1_params(8), dict(I.c1_params(10), precision=N.PT_FP32)]
+    G = (N.Grid * 2)(*[N.grid_from(p) for p in ps])
+    P = (N.Phys * 2)(*[N.phys_from(p) for p in ps])
+    U = (N.Num * 2)(*[N.num_from(p) for p in ps])
+    F = (N.Fields * 2)(*[N.Fields(*([None] * 15)) for _ in ps])
+    ws = lib.pt_batch_workspace_size(2, G, U)
+    assert ws > 0
+    h = C.c_void_p()
+    assert lib.pt_batch_init(C.byref(h), 2, G, P, U, F, 1 << 20, ws, None) == N.PT_EINVAL
+    assert not h.value

@@ -2,7 +2,9 @@
 same iteration count and status at its own convergence check, fields equal to 1e-12 relative
 (the per-point code is shared; the compiler may fuse multiply-adds differently in the two
 kernels, so the last bits can differ) — whatever tile shape and iterations per graph the tuner
-picks; and it agrees with the FP64 oracle within the 1e-10 parity bar."""
+picks; and it agrees with the FP64 oracle within the 1e-10 parity bar. The FP32 ensemble
+(defect-correction solvers on their own streams, stepped concurrently) reproduces each
+instance's single-solver FP32 run exactly: concurrency does not enter the arithmetic."""
 import numpy as np
 import pytest
 
@@ -71,4 +73,27 @@ def test_batched_instance_matches_oracle():
         for name in ("Vx", "Vz", "Pt", "Pf", "phi", "mu", "eta"):
             g, o = b.get(m, name), st[name]
             assert np.abs(g - o).max() <= 1e-10 * max(np.abs(o).max(), 1e-300), (m, name)
+    b.close()
+
+
+def test_fp32_ensemble_instances_equal_single_fp32_runs():
+    PTBatch, PTSolver = _mods()
+    from paper_2207_08716_gb300 import native as N
+    mem = I.ensemble(seed=5, n_inst=5, sizes=(9, 12, 16), max_iter=6000)
+    mem[1][0]["max_iter"] = 60             # one instance hits its cap
+    b = PTBatch(mem, precision=N.PT_FP32)
+    assert b.config() == (0, 0, 0)
+    reps, ttc = b.step()
+    reps2, _ = b.step()
+    for m, (p, phi) in enumerate(mem):
+        s = PTSolver(dict(p, precision=N.PT_FP32), phi)
+        r1 = s.step()
+        r2 = s.step()
+        assert (reps[m]["iters"], reps[m]["status"]) == (r1["iters"], r1["status"]), (m, reps[m], r1)
+        assert (reps2[m]["iters"], reps2[m]["status"]) == (r2["iters"], r2["status"]), (m, reps2[m], r2)
+        for name in FIELDS:
+            np.testing.assert_array_equal(b.get(m, name), s.get(name), err_msg=f"{m} {name}")
+        s.close()
+    assert reps[1]["status"] == -2
+    assert all(t > 0 for t in ttc)
     b.close()
