@@ -114,6 +114,8 @@ def parse():
     ap.add_argument("--batch-precision", choices=("fp64", "fp32"), default="fp64",
                     help="precision of the batched ensemble (fp32: defect-correction solvers stepped "
                          "concurrently, each on its own stream)")
+    ap.add_argument("--batch-inner-rtol", type=float, default=0.0,
+                    help="FP32 ensembles: relative residual drop of each FP32 correction solve (0: library default)")
     ap.add_argument("--batched-converge", action="store_true",
                     help="run one step of the batched ensemble to convergence and report p50/p99 "
                          "time-to-converge (minutes of GPU time) instead of the throughput bench")
@@ -325,6 +327,9 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
     # the FP32 form counts its inner FP32 iterations, 2-4x the FP64 form's iterations (at least
     # nup of them per outer Picard update)
     mem = I.ensemble(seed=M.replica_seed(rank), n_inst=args.batch_n, max_iter=160000 if fp32 else 40000)
+    if fp32 and getattr(args, "batch_inner_rtol", 0.0) > 0:
+        for p, _ in mem:
+            p["inner_rtol"] = args.batch_inner_rtol
     if not converge:
         for p, _ in mem:
             p["tol"] = 0.0

@@ -112,7 +112,7 @@ typedef struct {
   int32_t precision;      /* PT_FP64, PT_FP64_STEPWISE or PT_FP32 (see the enum above)     */
   int32_t iters_per_graph;/* PT iterations per CUDA-graph replay; 0 = nup                  */
   double inner_rtol;      /* PT_FP32: each FP32 correction solve stops at this relative drop
-                           * of its residual (0 = 0.3)                                     */
+                           * of its residual (0 = 0.1)                                     */
 } pt_num;
 
 /* Caller-owned device fields, padded box layout above. logk may be NULL (logk = 0). */

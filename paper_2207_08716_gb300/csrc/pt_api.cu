@@ -40,7 +40,7 @@ constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
 // update per outer iteration), not by the inner accuracy: a drop of 0.3 per inner solve needs
 // about as many FP32 iterations in total as the FP64 path needs FP64 iterations (measured on
 // 32^3-96^3), while 1e-4 needs 3-4 times more.
-constexpr double kInnerRtol = 0.3;
+constexpr double kInnerRtol = 0.1;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
