@@ -1096,14 +1096,20 @@ namespace {
 int batch_step_concurrent(pt_batch* B, pt_report* reps, double* ttc_ms) {
   std::vector<int> rcs(B->ninst, PT_OK);
   std::vector<std::thread> pool;
-  pool.reserve(B->ninst);
   const auto t0 = std::chrono::steady_clock::now();
-  for (int m = 0; m < B->ninst; ++m)
-    pool.emplace_back([B, m, reps, ttc_ms, t0, &rcs] {
-      rcs[m] = pt_step(B->ctx[m], &reps[m]);
-      const auto t1 = std::chrono::steady_clock::now();
-      if (ttc_ms) ttc_ms[m] = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    });
+  auto run = [B, reps, ttc_ms, t0, &rcs](int m) {
+    rcs[m] = pt_step(B->ctx[m], &reps[m]);
+    const auto t1 = std::chrono::steady_clock::now();
+    if (ttc_ms) ttc_ms[m] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  };
+  int started = 0;
+  try {
+    pool.reserve(B->ninst);
+    for (; started < B->ninst; ++started) pool.emplace_back(run, started);
+  } catch (...) {
+    // no more threads to be had: the instances not yet started run on this thread
+  }
+  for (int m = started; m < B->ninst; ++m) run(m);
   for (std::thread& t : pool) t.join();
   int any_nc = 0, any_nan = 0;
   for (int m = 0; m < B->ninst; ++m) {
