@@ -114,6 +114,12 @@ def parse():
     ap.add_argument("--batch-precision", choices=("fp64", "fp32"), default="fp64",
                     help="precision of the batched ensemble (fp32: defect-correction solvers stepped "
                          "concurrently, each on its own stream)")
+    ap.add_argument("--precision-check", action="store_true",
+                    help="porosity of the FP32 form against the FP64 form (and the oracle at 32^3) after "
+                         "--pc-steps converged physical steps of the c1 workload at each --pc-n")
+    ap.add_argument("--pc-n", default="32,64", help="grid sizes of the precision check")
+    ap.add_argument("--pc-steps", type=int, default=50)
+    ap.add_argument("--pc-oracle", type=int, default=1, help="also run the oracle at 32^3 (1) or not (0)")
     ap.add_argument("--batch-inner-rtol", type=float, default=0.0,
                     help="FP32 ensembles: relative residual drop of each FP32 correction solve (0: library default)")
     ap.add_argument("--batched-converge", action="store_true",
@@ -517,6 +523,59 @@ def measure_reactive(args, dev) -> dict:
     return out
 
 
+def measure_precision(args, dev) -> dict:
+    """The FP32 + FP64 defect-correction form against the FP64-lean form after --pc-steps
+    converged physical steps of the c1 workload (one centred anomaly), n^3 cells per --pc-n, both
+    on the GPU from the same state; at 32^3 also against the FP64 oracle's converged steps.
+    Porosity error = max |phi - phi_ref| / max |phi_ref| and, more telling, relative to the
+    porosity change over the run, max |phi - phi_ref| / max |phi_ref - phi_initial|."""
+    import torch
+    from paper_2207_08716_gb300 import native as N
+    from paper_2207_08716_gb300.solver import PTSolver
+
+    def run(p, phi0, nsteps):
+        s = PTSolver(p, phi0, device=dev)
+        iters, t0 = [], time.perf_counter()
+        for _ in range(nsteps):
+            r = s.step(raise_on_notconv=True)
+            iters.append(r["iters"])
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        phi = s.get("phi")
+        s.close()
+        return phi, iters, t
+
+    def errs(a, ref, phi0):
+        d = float(np.abs(a - ref).max())
+        return {"max_rel": d / float(np.abs(ref).max()), "rel_to_change": d / float(np.abs(ref - phi0).max())}
+
+    out = {}
+    for n in [int(v) for v in args.pc_n.split(",") if v.strip()]:
+        p = I.c1_params(n)
+        p["max_iter"] = 400000
+        phi0 = I.gaussian_porosity(p)
+        phi64, it64, t64 = run(dict(p, precision=N.PT_FP64), phi0, args.pc_steps)
+        phi32, it32, t32 = run(dict(p, precision=N.PT_FP32), phi0, args.pc_steps)
+        r = {"steps": args.pc_steps, "fp64_iters": sum(it64), "fp32_iters": sum(it32), "fp64_s": t64,
+             "fp32_s": t32, "fp32_vs_fp64": errs(phi32, phi64, phi0),
+             "porosity_change_max": float(np.abs(phi64 - phi0).max())}
+        if n == 32 and args.pc_oracle:
+            import oracle as O
+            st = O.make_state(p, phi0)
+            t0 = time.perf_counter()
+            for _ in range(args.pc_steps):
+                rc, _, _ = O.step(st)
+                if rc != 0:
+                    raise RuntimeError(f"oracle rc {rc}")
+            r["oracle_s"] = time.perf_counter() - t0
+            phio = st["phi"]
+            r["fp64_vs_oracle"] = errs(phi64, phio, phi0)
+            r["fp32_vs_oracle"] = errs(phi32, phio, phi0)
+        out[str(n)] = r
+        torch.cuda.empty_cache()
+    return out
+
+
 MG_DEFAULT = dict(nu_pre=2, nu_post=2, nu_coarse=30, max_cycles=100, omega=6.0 / 7.0)
 
 
@@ -616,6 +675,13 @@ def run_native(args):
                                                      f"{args.rx_n}x{args.rx_n}x{4 * args.rx_n} cells, "
                                                      f"{args.rx_iters} PT iterations per step"},
                               "forms": r}), flush=True)
+        return 0
+    if args.precision_check:
+        if rank == 0:
+            r = measure_precision(args, dev)
+            print(json.dumps({"metric": "porosity error of the FP32 form after converged steps", "unit": "max rel",
+                              "config": {"workload": f"c1 workload (one centred anomaly), {args.pc_steps} "
+                                                     f"converged physical steps per grid"}, "grids": r}), flush=True)
         return 0
     if args.reactive_mg:
         if rank == 0:
