@@ -209,7 +209,7 @@ int pt_residual_static(const pt_grid *grid, const pt_phys *phys, const pt_num *n
                        const pt_fields *fields, const pt_old_fields *old, double dtS,
                        void *stream, pt_report *rep);
 
-/* ---- Adjoint -----------------------------------------------------------------
+/* ---- Adjoint (no thesis counterpart) -------------------------------------------------------
  * Gradient of an objective J(phi^N) of the porosity after N physical steps with respect to the
  * log-permeability field logk (k = k0 e^logk (phi/phi0)^3), by the discrete adjoint of the
  * converged implicit steps: for n = N..1, J_F(u^n)^T lambda^n = g^n is solved with the same
@@ -244,7 +244,7 @@ typedef struct {
 } pt_adj_vec;
 int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *workspace, size_t bytes);
 
-/* ---- Batched ensemble --------------------------------------------------------
+/* ---- Batched ensemble --------------------------------------------------------------------
  * ninst independent instances (each its own grid, parameters, fields and numerics), all
  * PT_FP64 or all PT_FP32 (mixing returns PT_EINVAL). FP32 ensembles: every instance runs the
  * FP32 + FP64 defect-correction pt_step, whose outer and inner iterations are decided per
@@ -275,7 +275,7 @@ int pt_batch_config(const pt_batch *batch, int32_t *tile_x, int32_t *tile_y,
                     int32_t *iters_per_graph);
 void pt_batch_destroy(pt_batch *batch);
 
-/* ---- Sub-domain (halo-exchange) form ---------------------------------------
+/* ---- Sub-domain (halo-exchange) form (Art. 1 Section 2.2) ----------------------------------
  * The distributed-memory decomposition of the thesis (Art. 1 Section 2.2; Art. 2: one
  * sub-domain per GPU, halos exchanged every iteration), run on one GPU: the grid is split into
  * parts[0] x parts[1] x parts[2] parts of near-equal size (at least 2 cells per part and

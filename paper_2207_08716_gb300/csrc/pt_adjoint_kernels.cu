@@ -1,4 +1,5 @@
-// pt_adjoint_kernels.cu — discrete adjoint of the converged implicit step.
+// pt_adjoint_kernels.cu — discrete adjoint of the converged implicit step (Art. 1, Eqs. 17-26;
+// the thesis has no adjoint: the gradient of a final-porosity misfit w.r.t. the log-k field).
 //
 // Each physical step solves F(u; u_o, theta) = 0 for u = (V, Pt, Pf, phi) (Eqs. 17-22 with the
 // power law off, no weakening switch, beta_n = 0 and fixed old stresses, so eta = eta0 mu0 / phi).

@@ -1,4 +1,4 @@
-// pt_batch_kernels.cu — batched ensemble kernels.
+// pt_batch_kernels.cu — batched ensemble kernels (many independent instances of the Art. 1 solver).
 //
 // All instances of an ensemble are advanced by one launch per PT phase (cells, faces, Picard,
 // coefficients). The work list is the concatenation of every instance's tiles (bx x by cells of

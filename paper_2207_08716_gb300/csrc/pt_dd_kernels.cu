@@ -1,5 +1,5 @@
-// pt_dd_kernels.cu — halo exchange, scatter and gather of the sub-domain form (SURVEY NEXT 1:
-// the thesis's distributed-memory decomposition, Art. 1 Section 2.2 and Art. 2, run on one GPU).
+// pt_dd_kernels.cu — halo exchange, scatter and gather of the sub-domain form (the thesis's
+// distributed-memory decomposition, Art. 1 Section 2.2 and Art. 2, run on one GPU).
 //
 // Part p owns global cells [a_p, b_p) per direction; its box covers [a_p - h_lo, b_p + h_hi)
 // with h = 1 on every side that has a neighbour. Halo values are what a neighbouring GPU would
