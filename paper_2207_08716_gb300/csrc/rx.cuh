@@ -55,10 +55,12 @@ __device__ inline double rx_change(double d_phi, double d_pf, double d_xs) {
 template <class T>
 struct RxIn {
   const T *Pf, *phi, *Xs, *Pf_o, *phi_o, *Xs_o;
+  const T* k;                            // k(phi) of the iterate (plain FP64 iteration; else null)
 };
 template <class T>
 struct RxOut {
   T *Pf, *phi, *Xs, *R;                  // R written when non-null
+  T* k;                                  // k(phi') for the next iteration (plain FP64 iteration)
 };
 
 // One PT iteration over the cells with pseudo step dtau; check: change norm into red[RED_V]
@@ -69,10 +71,11 @@ void rx_iter(cudaStream_t s, Box b, const RxCoef<T>& c, double dtau, const RxIn<
 // max k / beta_P over the cells into red[RED_MUMAX]
 template <class T>
 void rx_kbmax(cudaStream_t s, Box b, const RxCoef<T>& c, const T* phi, unsigned long long* red);
-// caller FP64 fields -> iterate and old-step arrays in T (start of a step)
+// caller FP64 fields -> iterate and old-step arrays in T (start of a step); k1 (may be null):
+// k(phi) of the iterate
 template <class T>
-void rx_begin(cudaStream_t s, Box b, const double* Pf, const double* phi, const double* Xs, T* Pf1, T* phi1, T* Xs1,
-              T* Pf_o, T* phi_o, T* Xs_o);
+void rx_begin(cudaStream_t s, Box b, const RxCoef<T>& c, const double* Pf, const double* phi, const double* Xs,
+              T* Pf1, T* phi1, T* Xs1, T* Pf_o, T* phi_o, T* Xs_o, T* k1);
 // iterate (and rate) in T -> caller FP64 fields (end of a step)
 template <class T>
 void rx_end(cudaStream_t s, Box b, const T* Pf, const T* phi, const T* Xs, const T* R, double* Pf1, double* phi1,

@@ -48,6 +48,7 @@ struct rx_ctx {
   void* phi[2];
   void* Xs[2];
   void *Pf_o, *phi_o, *Xs_o, *R;
+  void* k[2];                        // k(phi) of the ping-pong iterates (plain iteration)
   unsigned long long* red;
   unsigned long long* h_red;
   double hmin2;
@@ -66,7 +67,7 @@ struct rx_ctx {
 namespace {
 
 constexpr size_t kRxAlign = 256;
-constexpr int kRxArrays = 10;        // Pf, phi, Xs (x2), Pf_o, phi_o, Xs_o, R
+constexpr int kRxArrays = 12;        // Pf, phi, Xs, k (x2), Pf_o, phi_o, Xs_o, R
 constexpr int kMgArrays = 15;        // per coarse level: Pf, phi, Xs (x2), old (3), f (3), u0 (3)
 
 size_t rx_align(size_t x) { return (x + kRxAlign - 1) / kRxAlign * kRxAlign; }
@@ -153,8 +154,10 @@ int run_step(rx_ctx* c, int32_t niter, bool converge, pt_report* rep) {
   T* Pf[2] = {(T*)c->Pf[0], (T*)c->Pf[1]};
   T* phi[2] = {(T*)c->phi[0], (T*)c->phi[1]};
   T* Xs[2] = {(T*)c->Xs[0], (T*)c->Xs[1]};
-  rx_begin<T>(c->stream, b, c->f.Pf, c->f.phi, c->f.Xs, Pf[0], phi[0], Xs[0], (T*)c->Pf_o, (T*)c->phi_o,
-              (T*)c->Xs_o);
+  // k travels with phi in FP64 only (see k_rx_iter)
+  T* kk[2] = {sizeof(T) == 8 ? (T*)c->k[0] : nullptr, sizeof(T) == 8 ? (T*)c->k[1] : nullptr};
+  rx_begin<T>(c->stream, b, k, c->f.Pf, c->f.phi, c->f.Xs, Pf[0], phi[0], Xs[0], (T*)c->Pf_o, (T*)c->phi_o,
+              (T*)c->Xs_o, kk[0]);
   cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
   rx_kbmax<T>(c->stream, b, k, phi[0], c->red);
   c->launches += 2;
@@ -171,8 +174,8 @@ int run_step(rx_ctx* c, int32_t niter, bool converge, pt_report* rep) {
     const int check = (it % c->num.nup) == 0;
     const bool last = it == niter;
     if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-    const RxIn<T> in{Pf[cur], phi[cur], Xs[cur], (const T*)c->Pf_o, (const T*)c->phi_o, (const T*)c->Xs_o};
-    const RxOut<T> out{Pf[1 - cur], phi[1 - cur], Xs[1 - cur], (check || last) ? (T*)c->R : nullptr};
+    const RxIn<T> in{Pf[cur], phi[cur], Xs[cur], (const T*)c->Pf_o, (const T*)c->phi_o, (const T*)c->Xs_o, kk[cur]};
+    const RxOut<T> out{Pf[1 - cur], phi[1 - cur], Xs[1 - cur], (check || last) ? (T*)c->R : nullptr, kk[1 - cur]};
     rx_iter<T>(c->stream, b, k, dtau, in, out, c->red, check);
     ++c->launches;
     cur = 1 - cur;
@@ -320,8 +323,8 @@ template <class T>
 int run_mg(rx_ctx* c, int32_t ncycles, bool converge, pt_report* rep) {
   MgLevel& F = c->lv[0];
   F.cur = 0;
-  rx_begin<T>(c->stream, c->box, c->f.Pf, c->f.phi, c->f.Xs, (T*)F.Pf[0], (T*)F.phi[0], (T*)F.Xs[0], (T*)F.Pf_o,
-              (T*)F.phi_o, (T*)F.Xs_o);
+  rx_begin<T>(c->stream, c->box, lcoef<T>(F), c->f.Pf, c->f.phi, c->f.Xs, (T*)F.Pf[0], (T*)F.phi[0], (T*)F.Xs[0],
+              (T*)F.Pf_o, (T*)F.phi_o, (T*)F.Xs_o, nullptr);
   ++c->launches;
   for (int l = 1; l < c->mg.levels; ++l) {
     const MgLevel& A = c->lv[l - 1];
@@ -408,7 +411,7 @@ int rx_init(rx_ctx** out, const pt_grid* grid, const rx_phys* phys, const rx_num
   const size_t stride = rx_align((size_t)b.n * (c->fp32 ? sizeof(float) : sizeof(double)));
   char* w = (char*)workspace;
   void** slots[kRxArrays] = {&c->Pf[0], &c->Pf[1], &c->phi[0], &c->phi[1], &c->Xs[0], &c->Xs[1],
-                             &c->Pf_o, &c->phi_o, &c->Xs_o, &c->R};
+                             &c->Pf_o, &c->phi_o, &c->Xs_o, &c->R,      &c->k[0],  &c->k[1]};
   for (int s = 0; s < kRxArrays; ++s) *slots[s] = w + s * stride;
   c->red = (unsigned long long*)(w + kRxArrays * stride);
   c->launches = 0;
