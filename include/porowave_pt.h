@@ -54,7 +54,9 @@ enum {
   PT_EINVAL = -1,     /* bad argument: null pointer, size < 1, dt <= 0, misaligned, ...      */
   PT_ENOTCONV = -2,   /* max_iter reached before the residual fell below tol                  */
   PT_ENAN = -3,       /* a residual norm was not finite                                       */
-  PT_ETIMEOUT = -4,   /* a bounded device-side wait expired                                   */
+  PT_ETIMEOUT = -4,   /* a bounded device-side wait expired (reserved: no kernel of this
+                         library waits on another; every convergence decision is a host read
+                         of a reduction or a non-spinning retire kernel)                       */
   PT_ECUDA = -5,      /* a CUDA call or kernel launch failed                                  */
   PT_ESPACE = -6      /* workspace smaller than pt_workspace_size()                            */
 };
