@@ -8,6 +8,7 @@ import pytest
 from paper_2207_08716_gb300 import measure as M
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "teff_eq39.json")
+GOLDEN_41_43 = os.path.join(os.path.dirname(__file__), "golden", "teff_eqs41_43.json")
 
 
 def test_t_eff_reproduces_eq39():
@@ -22,6 +23,14 @@ def test_t_eff_reproduces_eq39():
     assert abs(M.t_eff_gbs(n, g["p_bytes"], g["t_it_s"], **kw) - g["T_eff_gbs"]) < 0.2
     # A_eff = 25 N p (Eq. 37) for the default DOF counts
     assert M.a_eff_bytes(n, 8) == 25 * n * 8
+
+
+def test_t_eff_reproduces_eqs41_43():
+    # the thesis's estimates for three other solvers (Eq. 40 with 12 unknown + 1 known DOF):
+    # each printed value is the formula's value rounded to the printed decimals
+    for c in json.load(open(GOLDEN_41_43))["cases"]:
+        v = M.t_eff_gbs(int(c["N"]), c["p_bytes"], c["t_it_s"])
+        assert round(v, c["printed_decimals"]) == c["T_eff_gbs"], (c["eq"], v)
 
 
 def _worker(rank, world, port, q):
