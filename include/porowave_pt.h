@@ -196,9 +196,12 @@ int64_t pt_launch_count(const pt_ctx *ctx);
  * PT_RESIDUAL_STATIC_SCRATCH_BYTES large, which every GPU that loads the library holds until
  * the process exits. Grids whose padded box needs more than 10 arrays of that array (boxes of
  * about 838,000 elements, e.g. 90^3 cells) are rejected with PT_ESPACE before any device work.
- * Layout, alignment and argument rules are those of pt_init; the current device must be the
+ * Layout, alignment and argument rules are those of pt_init (the same validation and the same
+ * coefficient builder; the background shear tau_bg included); the current device must be the
  * one holding the fields. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture. Every
+ * (cudaGetSymbolAddress) and caches it. Under CUDA's lazy module loading (the default) that
+ * first call is also when the device reserves the array's memory, so make it early: before a
+ * pool allocator claims the device's free memory, and before any stream capture. Every
  * call shares the array and clears its reduction block first; calls whose device work
  * overlaps (other streams or host threads) race on it. Calls no cudaMalloc / cudaFree and no
  * allocating library routine; synchronises `stream` to read the norms into `rep`. */

@@ -25,13 +25,13 @@
 #include "pt_batch.cuh"
 #include "pt_adjoint.cuh"
 #include "pt_dd.cuh"
+#include "pt_host.h"
 
 using namespace pt;
 
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kPitchMultiple = 16;
 constexpr int kRefArrays = 23;   // step-by-step path
 constexpr int kLeanArrays = 26;  // extra arrays of the FP64-lean path
 constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
@@ -44,24 +44,6 @@ constexpr double kInnerRtol = 0.1;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-bool grid_ok(const pt_grid* g) {
-  return g && g->nx >= 1 && g->ny >= 1 && g->nz >= 1 && g->nx < (1 << 20) && g->ny < (1 << 20) &&
-         g->nz < 65535 && g->lx > 0 && g->ly > 0 && g->lz > 0 && std::isfinite(g->lx) &&
-         std::isfinite(g->ly) && std::isfinite(g->lz);
-}
-
-Box make_box(const pt_grid* g) {
-  Box b;
-  b.nx = g->nx;
-  b.ny = g->ny;
-  b.nz = g->nz;
-  b.px = (g->nx + 1 + kPitchMultiple - 1) / kPitchMultiple * kPitchMultiple;
-  b.pxy = (long long)b.px * (g->ny + 1);
-  b.n = b.pxy * (g->nz + 1);
-  return b;
-}
-
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
@@ -179,50 +161,7 @@ void fill_lean_coef(pt_ctx* c);
 void fill_corr_coef(pt_ctx* c);
 
 void fill_coef(pt_ctx* c) {
-  const pt_grid& g = c->metric;
-  const pt_phys& p = c->phys;
-  const pt_num& n = c->num;
-  Coef& k = c->coef;
-  const double dx = g.lx / g.nx, dy = g.ly / g.ny, dz = g.lz / g.nz;
-  const double h = std::fmin(dx, std::fmin(dy, dz));
-  k.rdx = 1.0 / dx;
-  k.rdy = 1.0 / dy;
-  k.rdz = 1.0 / dz;
-  k.h2 = h * h;
-  k.phi0 = p.phi0;
-  k.rphi0 = 1.0 / p.phi0;
-  k.k0 = p.k0;
-  k.mu0 = p.mu0;
-  k.eta0 = p.eta0;
-  k.R_weak = p.R_weak;
-  k.n_pow = p.n_pow;
-  k.tau0 = p.tau0;
-  k.alpha = p.alpha;
-  k.B = p.B;
-  k.beta_d = p.beta_d;
-  k.beta_phi = p.beta_phi;
-  k.G = p.G;
-  k.rhof_g = p.rhof_g;
-  k.rhos_g = p.rhos_g;
-  k.rho_bg_g = p.phi0 * p.rhof_g + (1.0 - p.phi0) * p.rhos_g;
-  k.powerlaw_on = p.powerlaw_on;
-  k.compaction_on = p.compaction_on;
-  k.dt = n.dt;
-  k.rdt = 1.0 / n.dt;
-  k.damp_x = n.damp[0];
-  k.damp_y = n.damp[1];
-  k.damp_z = n.damp[2];
-  k.rho_i = n.rho_i;
-  k.rrho_i = 1.0 / n.rho_i;
-  k.beta_n = n.beta_n;
-  k.rel_mu = n.rel_mu;
-  k.rel_eta = n.rel_eta;
-  k.dtauv_fac = n.cfl_v * k.h2 * n.rho_i / (1.0 + n.beta_n);
-  k.dtaupt_fac = n.dtpt_scale * (1.0 + n.beta_n) / g.nz;
-  k.dtaupf_fac = n.cfl_pf * k.h2 * (1.0 + p.beta_d * p.B / p.alpha);
-  k.rGdtS = c->dtS > 0 ? 1.0 / (p.G * c->dtS) : 0.0;
-  k.ebg = 0.5 * p.tau_bg / p.mu0;
-  k.bg_on = p.tau_bg != 0.0;
+  c->coef = make_coef(c->metric, c->phys, c->num, c->dtS);
   fill_lean_coef(c);
   fill_corr_coef(c);
 }
@@ -572,9 +511,7 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
     return PT_EINVAL;
   if (num->precision != PT_FP64 && num->precision != PT_FP64_STEPWISE && num->precision != PT_FP32)
     return PT_EINVAL;
-  if (!(phys->phi0 > 0 && phys->phi0 < 1) || !(phys->k0 > 0) || !(phys->mu0 > 0) || !(phys->eta0 > 0) ||
-      !(phys->G > 0) || !(phys->alpha > 0) || !(phys->B > 0) || !(phys->tau0 > 0) || !(phys->R_weak > 0))
-    return PT_EINVAL;
+  if (!phys_ok(phys)) return PT_EINVAL;
   double* const ptrs[] = {f->Vx, f->Vy, f->Vz, f->Pt, f->Pf, f->phi, f->txx, f->tyy,
                           f->tzz, f->txy, f->txz, f->tyz, f->mu, f->eta};
   for (double* p : ptrs)

@@ -23,6 +23,7 @@
 #include "../../include/porowave_pt.h"
 #include "pt_common.cuh"
 #include "pt_kernels.cuh"
+#include "pt_host.h"
 
 using namespace pt;
 
@@ -57,68 +58,21 @@ int scratch_on_current_device(unsigned char** out) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The argument rules of pt_init (grid_ok, phys_ok, the numerics' positive pseudo-step factors,
+// 16-byte aligned non-null fields), plus a positive finite stress sub-step.
 bool args_ok(const pt_grid* g, const pt_phys* p, const pt_num* n, const pt_fields* f,
              const pt_old_fields* o, double dtS) {
-  if (!g || !p || !n || !f || !o) return false;
-  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nz >= 65535 || !(g->lx > 0) || !(g->ly > 0) ||
-      !(g->lz > 0))
-    return false;
-  if (!(n->dt > 0) || !(n->rho_i > 0) || !(n->cfl_v > 0) || !(n->cfl_pf > 0) || !(n->dtpt_scale > 0))
-    return false;
-  if (!(p->phi0 > 0 && p->phi0 < 1) || !(p->k0 > 0) || !(p->mu0 > 0) || !(p->eta0 > 0) ||
-      !(p->G > 0) || !(p->alpha > 0) || !(p->B > 0) || !(p->tau0 > 0) || !(p->R_weak > 0))
+  if (!grid_ok(g) || !phys_ok(p) || !n || !f || !o) return false;
+  if (!(n->dt > 0) || !std::isfinite(n->dt) || !(n->rho_i > 0) || !(n->cfl_v > 0) || !(n->cfl_pf > 0) ||
+      !(n->dtpt_scale > 0))
     return false;
   if (!(dtS > 0) || !std::isfinite(dtS)) return false;
   const void* ptrs[] = {f->Vx, f->Vy, f->Vz, f->Pt, f->Pf, f->phi, f->mu, f->eta, o->Pto,
                         o->Pfo, o->txxo, o->tyyo, o->tzzo, o->txyo, o->txzo, o->tyzo};
   for (const void* q : ptrs)
-    if (!q || ((uintptr_t)q & 15u)) return false;
-  if (f->logk && ((uintptr_t)f->logk & 15u)) return false;
+    if (!q || !aligned16(q)) return false;
+  if (f->logk && !aligned16(f->logk)) return false;
   return true;
-}
-
-Coef coef_for(const pt_grid& g, const pt_phys& p, const pt_num& n, double dtS) {
-  Coef k;
-  std::memset(&k, 0, sizeof k);
-  const double dx = g.lx / g.nx, dy = g.ly / g.ny, dz = g.lz / g.nz;
-  const double h = std::fmin(dx, std::fmin(dy, dz));
-  k.rdx = 1.0 / dx;
-  k.rdy = 1.0 / dy;
-  k.rdz = 1.0 / dz;
-  k.h2 = h * h;
-  k.phi0 = p.phi0;
-  k.rphi0 = 1.0 / p.phi0;
-  k.k0 = p.k0;
-  k.mu0 = p.mu0;
-  k.eta0 = p.eta0;
-  k.R_weak = p.R_weak;
-  k.n_pow = p.n_pow;
-  k.tau0 = p.tau0;
-  k.alpha = p.alpha;
-  k.B = p.B;
-  k.beta_d = p.beta_d;
-  k.beta_phi = p.beta_phi;
-  k.G = p.G;
-  k.rhof_g = p.rhof_g;
-  k.rhos_g = p.rhos_g;
-  k.rho_bg_g = p.phi0 * p.rhof_g + (1.0 - p.phi0) * p.rhos_g;
-  k.powerlaw_on = p.powerlaw_on;
-  k.compaction_on = p.compaction_on;
-  k.dt = n.dt;
-  k.rdt = 1.0 / n.dt;
-  k.damp_x = n.damp[0];
-  k.damp_y = n.damp[1];
-  k.damp_z = n.damp[2];
-  k.rho_i = n.rho_i;
-  k.rrho_i = 1.0 / n.rho_i;
-  k.beta_n = n.beta_n;
-  k.rel_mu = n.rel_mu;
-  k.rel_eta = n.rel_eta;
-  k.dtauv_fac = n.cfl_v * k.h2 * n.rho_i / (1.0 + n.beta_n);
-  k.dtaupt_fac = n.dtpt_scale * (1.0 + n.beta_n) / g.nz;
-  k.dtaupf_fac = n.cfl_pf * k.h2 * (1.0 + p.beta_d * p.B / p.alpha);
-  k.rGdtS = 1.0 / (p.G * dtS);
-  return k;
 }
 
 }  // namespace
@@ -129,13 +83,7 @@ extern "C" int pt_residual_static(const pt_grid* grid, const pt_phys* phys, cons
   if (!rep) return PT_EINVAL;
   std::memset(rep, 0, sizeof *rep);
   if (!args_ok(grid, phys, num, f, old, dtS)) return rep->status = PT_EINVAL;
-  Box b;
-  b.nx = grid->nx;
-  b.ny = grid->ny;
-  b.nz = grid->nz;
-  b.px = (grid->nx + 1 + 15) / 16 * 16;
-  b.pxy = (long long)b.px * (grid->ny + 1);
-  b.n = b.pxy * (grid->nz + 1);
+  const Box b = make_box(grid);
   const size_t stride = align_up((size_t)b.n * sizeof(double), kAlign);
   if (kScratchArrays * stride + kAlign > (size_t)PT_RESIDUAL_STATIC_SCRATCH_BYTES)
     return rep->status = PT_ESPACE;
@@ -148,7 +96,7 @@ extern "C" int pt_residual_static(const pt_grid* grid, const pt_phys* phys, cons
   unsigned long long* red = (unsigned long long*)(base + kScratchArrays * stride);
 
   cudaStream_t st = (cudaStream_t)stream_handle;
-  const Coef k = coef_for(*grid, *phys, *num, dtS);
+  const Coef k = make_coef(*grid, *phys, *num, dtS);   // the same builder as pt_init's
   const dim3 bl(32, 8, 1);
   const dim3 gr((unsigned)((b.nx + 1 + 31) / 32), (unsigned)((b.ny + 1 + 7) / 8), (unsigned)(b.nz + 1));
   double *perm = s[0], *rog = s[1], *Pt1 = s[2], *Pf1 = s[3];

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
 SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu",
            "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu",
            "rx_api.cu", "rx_kernels.cu", "rx_mg_kernels.cu")
-HEADERS = ("pt_common.cuh", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
+HEADERS = ("pt_common.cuh", "pt_host.h", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()

@@ -62,3 +62,28 @@ def test_decomposed_converged_step_matches_single_solver():
         err = np.abs(got[k] - ref).max() / max(np.abs(ref).max(), 1e-300)
         assert err <= 1e-12, (k, err)
     s.close()
+
+
+@pytest.mark.parametrize("parts", [(2, 2, 2), (3, 1, 2)])
+def test_decomposed_matches_oracle_after_fixed_iterations(parts):
+    """Against the FP64 oracle itself (not the undivided GPU run): two physical steps capped at
+    a fixed iteration count (not converged, so both sides take exactly the cap), with a
+    log-permeability field; all 14 fields within the FP64 parity bar 1e-10."""
+    _torch()
+    import oracle as O
+    dims = (26, 20, 18)
+    p = I.c1_params(*dims)
+    p["max_iter"] = 240
+    phi = I.gaussian_porosity(p, centres=((0.42, 0.55, 0.47),), width=0.15)
+    logk = I.gaussian_random_field(phi.shape, seed=9, corr_len=0.15, std=0.4)
+    reps, got = _run(p, phi, parts, logk, 2)
+    st = O.make_state(p, phi, logk=logk)
+    for s in range(2):
+        rc, iters, res = O.step(st)
+        assert rc == -2 and iters == p["max_iter"], (rc, iters)       # capped, like the GPU run
+        assert reps[s]["status"] == -2 and reps[s]["iters"] == iters, reps[s]
+        for k in ("r_v", "r_pt", "r_pf", "r_pic"):
+            assert abs(reps[s][k] - res[k]) <= 1e-8 * abs(res[k]) + 1e-14, (s, k, reps[s][k], res[k])
+    for k in FIELDS:
+        err = np.abs(got[k] - st[k]).max() / max(np.abs(st[k]).max(), 1e-300)
+        assert err <= 1e-10, (parts, k, err)
