@@ -47,8 +47,14 @@ KERNEL_BYTES_PER_CELL = {
     "k_corr_cells": 25 * 4, "k_corr_faces": 25 * 4,
     # adjoint PT iteration: cells reads 26 arrays and writes 10, faces reads 17 and writes 6
     "k_adj_cells": 36 * 8, "k_adj_faces": 23 * 8,
+    # double-float form (8 B per value): cells reads 21 arrays (V, Pt, Pf, phi, Pto, Pfo, phio, ieta,
+    # idtp, cm2, 3 toa_ii, 3 edge moduli, 3 toa_e) and writes 9 (Pt, Pf, phi, 6 stresses); faces
+    # reads 15 (6 stresses, Pt, phi, centre dtau_V, 3 R, 3 V) and writes 6; Picard reads 11 and
+    # writes 2; coefficients read 8 (mu, eta, 6 old stresses) and write 13; step start 4 + 3
+    "k_lean_cells_df64": 30 * 8, "k_lean_faces_df64": 21 * 8, "k_lean_picard_df64": 13 * 8,
+    "k_lean_coef_df64": 21 * 8, "k_lean_begin_df64": 7 * 8,
 }
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2, "df64": 3}
 # FP64 thread instructions (DFMA + DADD + DMUL) and flops (DFMA x 2 + DADD + DMUL) per cell and
 # launch from one ncu capture of the kernel (profiles/k_lean_fp64_191.md, k_adj_cells_95.md,
 # k_centres_fp64_stepwise_191.md); a kernel missing here has no current count.

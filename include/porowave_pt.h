@@ -65,8 +65,13 @@ enum {
  * fused kernels per iteration, coefficients refreshed at Picard updates). PT_FP64_STEPWISE:
  * FP64, one kernel per data-flow step (the straightforward form, kept for comparison).
  * PT_FP32: FP32 PT iterations with FP64 residuals, defect correction and porosity time
- * integration. Fields at the boundary are FP64 in every mode. */
-enum { PT_FP64 = 0, PT_FP32 = 1, PT_FP64_STEPWISE = 2 };
+ * integration. PT_DF64: the FP64-lean form's iteration in double-float arithmetic (each value
+ * the unevaluated sum of two FP32 numbers, a 48-bit significand in FP32's exponent range,
+ * computed on the FP32 pipe): the iterate lives in the workspace from pt_step_begin on and is
+ * written to the caller's FP64 fields when each call returns; residual norms and reports are
+ * FP64. Fields at the boundary are FP64 in every mode. PT_DF64 serves pt_init / pt_step /
+ * pt_iterate / pt_residual; the batched, sub-domain and adjoint entry points take PT_FP64. */
+enum { PT_FP64 = 0, PT_FP32 = 1, PT_FP64_STEPWISE = 2, PT_DF64 = 3 };
 
 /* Cell-centred grid on [0, lx] x [0, ly] x [0, lz]; dx = lx / nx. */
 typedef struct {
@@ -111,7 +116,7 @@ typedef struct {
   double cfl_pf;          /* dtau_Pf = cfl_pf h^2 (1 + beta_d B / alpha) / max local k      */
   double dtpt_scale;      /* dtau_Pt = dtpt_scale mu (1 + beta_n) / nz                      */
   double xsi_w;           /* stress sub-step dtS = max(mu) / (G xsi_w)                      */
-  int32_t precision;      /* PT_FP64, PT_FP64_STEPWISE or PT_FP32 (see the enum above)     */
+  int32_t precision;      /* PT_FP64, PT_FP64_STEPWISE, PT_FP32 or PT_DF64 (enum above)     */
   int32_t iters_per_graph;/* PT iterations per CUDA-graph replay; 0 = nup                  */
   double inner_rtol;      /* PT_FP32: each FP32 correction solve stops at this relative drop
                            * of its residual (0 = 0.1)                                     */
@@ -184,6 +189,26 @@ int pt_profile_begin(pt_ctx *ctx);
 int pt_profile_end(pt_ctx *ctx, pt_kernel_time *out, int32_t max_out, int32_t *n_out);
 /* Kernel launches issued by this context since pt_init. */
 int64_t pt_launch_count(const pt_ctx *ctx);
+
+/* ---- Check of the hand-written device arithmetic (test aid; no thesis counterpart) ----------
+ * Applies one device routine of the PT kernels element-wise: out[e] = f(a[e] (, b[e])), n
+ * elements, device pointers, synchronises `stream`. It exists so that each replacement of a
+ * library operation can be compared with CUDA's own function and with its stated error bound:
+ *   PT_MATH_RCP_PSEUDO   1/x, approximate FP64 reciprocal + one Newton-Raphson step (~2^-46)
+ *   PT_MATH_RCP_FULL     1/x, approximate FP64 reciprocal + two Newton-Raphson steps (rounding)
+ *   PT_MATH_EXPM1_POS/NEG  expm1(x), expm1(-x) from the split Taylor series of exp (tiers
+ *                          |x| <= 2^-20, <= 2^-6; beyond, CUDA's expm1)
+ *   PT_MATH_DF_ADD/SUB/MUL   double-float a + b, a - b, a * b (inputs rounded to double-float)
+ *   PT_MATH_DF_FMA       double-float a * b + a
+ *   PT_MATH_DF_RCP/SQRT  double-float 1/a, sqrt(a) (FP32 seed + one Newton step)
+ *   PT_MATH_DF_ROOT      double-float a^(1/m), m = (int)b[e] (Newton's m-th root)
+ *   PT_MATH_DF_EXPM1_POS/NEG  the split Taylor series in double-float
+ * Returns PT_EINVAL for an unknown code or a missing operand. */
+enum { PT_MATH_RCP_PSEUDO = 0, PT_MATH_RCP_FULL = 1, PT_MATH_EXPM1_POS = 2, PT_MATH_EXPM1_NEG = 3,
+       PT_MATH_DF_ADD = 4, PT_MATH_DF_SUB = 5, PT_MATH_DF_MUL = 6, PT_MATH_DF_FMA = 7,
+       PT_MATH_DF_RCP = 8, PT_MATH_DF_SQRT = 9, PT_MATH_DF_ROOT = 10, PT_MATH_DF_EXPM1_POS = 11,
+       PT_MATH_DF_EXPM1_NEG = 12 };
+int pt_math_check(int32_t fn, const double *a, const double *b, double *out, int64_t n, void *stream);
 
 /* ---- Residual norms with no allocation at all -------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot

@@ -35,6 +35,7 @@ constexpr size_t kAlign = 256;
 constexpr int kRefArrays = 23;   // step-by-step path
 constexpr int kLeanArrays = 26;  // extra arrays of the FP64-lean path
 constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
+constexpr int kDfArrays = 28;    // double-float iterate, stresses, residuals, old fields (PT_DF64)
 // Default relative drop at which the inner FP32 solves of the mixed-precision path stop. The
 // outer loop's convergence is bound by the log-space Picard relaxation of mu and eta (one
 // update per outer iteration), not by the inner accuracy: a drop of 0.3 per inner solve needs
@@ -72,6 +73,15 @@ struct pt_ctx {
   double *toa_xx, *toa_yy, *toa_zz, *toa_xy, *toa_xz, *toa_yz, *cm2, *idtp, *ieta;
   double *em2_xy, *em2_xz, *em2_yz, *eb_xy, *eb_xz, *eb_yz, *dtv_x, *dtv_y, *dtv_z, *K0;
   LeanCoef<double> lcoef;
+  // double-float path (precision PT_DF64): the lean arrays above hold df64 values; the iterate
+  // lives in these df64 arrays between pt_step_begin and the return of each call, the caller's
+  // FP64 fields receive it (export) when a call returns
+  bool dfm, df_dirty;
+  int fcur;
+  df64 *fVx, *fVy, *fVz, *fPt[2], *fPf[2], *fphi[2], *fmu, *feta, *fRx, *fRy, *fRz;
+  df64 *fs_txx, *fs_tyy, *fs_tzz, *fs_txy, *fs_txz, *fs_tyz;
+  df64 *ftxxo, *ftyyo, *ftzzo, *ftxyo, *ftxzo, *ftyzo, *fPto, *fPfo;
+  LeanCoef<df64> fcoef;
   // mixed-precision path (precision PT_FP32): FP32 correction problem
   bool mixed;
   double mix_omega;         // PT_FP32: weight of the outer update u <- u + omega delta
@@ -106,14 +116,18 @@ namespace {
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
                 K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_CELLS, K_CORR_FACES,
-                K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_COUNT };
+                K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_DF_CELLS, K_DF_FACES,
+                K_DF_PICARD, K_DF_COEF, K_DF_BEGIN, K_DF_K0, K_DF_CONVERT, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
                                            "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0",
                                            "k_mix_prepare", "k_mix_res_faces", "k_mix_coef",
                                            "k_corr_cells", "k_corr_faces", "k_mix_update",
-                                           "k_adj_prep", "k_adj_cells", "k_adj_faces", "k_adj_carry"};
+                                           "k_adj_prep", "k_adj_cells", "k_adj_faces", "k_adj_carry",
+                                           "k_lean_cells_df64", "k_lean_faces_df64", "k_lean_picard_df64",
+                                           "k_lean_coef_df64", "k_lean_begin_df64", "k_lean_k0_df64",
+                                           "k_df64_convert"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -160,6 +174,39 @@ dim3 grid_dims(const Box& b) {
 void fill_lean_coef(pt_ctx* c);
 void fill_corr_coef(pt_ctx* c);
 
+// m when the Picard relaxation weight is 1/m (2 <= m <= 64, to rounding), else 0: the
+// double-float path takes x^(1/m) by Newton's m-th root instead of exp(rel log x).
+int relax_root(double rel) {
+  if (!(rel > 0.0) || !std::isfinite(rel)) return 0;
+  const double m = std::nearbyint(1.0 / rel);
+  if (m >= 2.0 && m <= 64.0 && std::fabs(m * rel - 1.0) <= 4.0 * 2.220446049250313e-16) return (int)m;
+  return 0;
+}
+
+// The per-step scalars of the lean form rounded to double-float (each to ~2^-48 relative).
+LeanCoef<df64> lean_coef_df64(const LeanCoef<double>& L) {
+  LeanCoef<df64> F;
+#define PT_DF(x) F.x = df64(L.x)
+  PT_DF(rdx); PT_DF(rdy); PT_DF(rdz); PT_DF(hrdx); PT_DF(hrdy); PT_DF(hrdz);
+  PT_DF(hrdx2); PT_DF(hrdy2); PT_DF(hrdz2); PT_DF(buoy_dz); PT_DF(bd_rdt); PT_DF(bda_B_rdt);
+  PT_DF(alpha); PT_DF(alpha_B); PT_DF(bd_rdt_a); PT_DF(beta_n); PT_DF(beta_phi); PT_DF(dt);
+  PT_DF(rphi0); PT_DF(k0); PT_DF(phi0); PT_DF(drho_g); PT_DF(ifac_pf); PT_DF(rrho_i);
+  PT_DF(damp_x); PT_DF(damp_y); PT_DF(damp_z); PT_DF(rdx_r); PT_DF(rdy_r); PT_DF(rdz_r);
+  PT_DF(drho_g_r); PT_DF(rho_i); PT_DF(ebg); PT_DF(mu0); PT_DF(eta0); PT_DF(R_weak);
+  PT_DF(rtau0_2); PT_DF(rGdtS); PT_DF(dtaupt_fac); PT_DF(dtauv_fac);
+#undef PT_DF
+  F.compaction_on = L.compaction_on;
+  F.powerlaw_on = L.powerlaw_on;
+  F.bg_on = L.bg_on;
+  F.tau0 = L.tau0;
+  F.n_pow = L.n_pow;
+  F.rel_mu = L.rel_mu;
+  F.rel_eta = L.rel_eta;
+  F.root_mu = L.root_mu;
+  F.root_eta = L.root_eta;
+  return F;
+}
+
 void fill_coef(pt_ctx* c) {
   c->coef = make_coef(c->metric, c->phys, c->num, c->dtS);
   fill_lean_coef(c);
@@ -204,6 +251,9 @@ void fill_lean_coef(pt_ctx* c) {
   L.rGdtS = k.rGdtS;
   L.dtaupt_fac = k.dtaupt_fac;
   L.dtauv_fac = k.dtauv_fac;
+  L.root_mu = relax_root(k.rel_mu);
+  L.root_eta = relax_root(k.rel_eta);
+  c->fcoef = lean_coef_df64(L);
 }
 
 void fill_corr_coef(pt_ctx* c) {
@@ -223,7 +273,13 @@ void fill_corr_coef(pt_ctx* c) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
 
+void df_export(pt_ctx* c);
+
 int sync_current_to_caller(pt_ctx* c) {
+  if (c->dfm) {
+    df_export(c);
+    return cuda_status(cudaGetLastError());
+  }
   if (c->cur == 0) return PT_OK;
   const size_t bytes = (size_t)c->box.n * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(c->Pt[0], c->Pt[1], bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -239,8 +295,13 @@ int sync_current_to_caller(pt_ctx* c) {
 
 // One PT iteration number `it` (1-based); check = Picard update + norms.
 void launch_iteration_lean(pt_ctx* c, int check);
+void launch_iteration_df(pt_ctx* c, int check);
 
 void launch_iteration(pt_ctx* c, int check) {
+  if (c->dfm) {
+    launch_iteration_df(c, check);
+    return;
+  }
   if (c->lean) {
     launch_iteration_lean(c, check);
     return;
@@ -307,6 +368,97 @@ void launch_iteration_lean(pt_ctx* c, int check) {
     launch_lean_coef(c);
   }
   c->cur = n;
+}
+
+// ------------------------------------------------------ double-float path (PT_DF64)
+// The lean-form kernels instantiated for df64: the same per-point code on double-float values,
+// the lean arrays of the workspace reinterpreted (8 bytes per element either way).
+df64* D(double* p) { return reinterpret_cast<df64*>(p); }
+
+void df_convert(pt_ctx* c, double* const* d, df64* const* f, int n, bool to_df) {
+  DfCopy cp;
+  std::memset(&cp, 0, sizeof cp);
+  for (int i = 0; i < n; ++i) {
+    cp.d[i] = d[i];
+    cp.f[i] = f[i];
+  }
+  PT_LAUNCH(c, K_DF_CONVERT, df64_convert(c->stream, cp, n, c->box.n, to_df));
+}
+
+// The caller's FP64 fields -> the double-float iterate (buffer 0).
+void df_import(pt_ctx* c) {
+  double* const d[8] = {c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->eta};
+  df64* const f[8] = {c->fVx, c->fVy, c->fVz, c->fPt[0], c->fPf[0], c->fphi[0], c->fmu, c->feta};
+  df_convert(c, d, f, 8, true);
+  c->fcur = 0;
+  c->df_dirty = false;
+}
+
+// The double-float iterate -> the caller's FP64 fields (when iterations ran since the last one).
+void df_export(pt_ctx* c) {
+  if (!c->df_dirty) return;
+  const int a = c->fcur;
+  double* const d[8] = {c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->eta};
+  df64* const f[8] = {c->fVx, c->fVy, c->fVz, c->fPt[a], c->fPf[a], c->fphi[a], c->fmu, c->feta};
+  df_convert(c, d, f, 8, false);
+  c->df_dirty = false;
+}
+
+void launch_df_coef(pt_ctx* c) {
+  const Box& b = c->box;
+  LeanCoefIn<df64> ci{c->fmu, c->feta, c->ftxxo, c->ftyyo, c->ftzzo, c->ftxyo, c->ftxzo, c->ftyzo};
+  LeanCoefOut<df64> co{D(c->cm2), D(c->toa_xx), D(c->toa_yy), D(c->toa_zz), D(c->idtp), D(c->ieta),
+                       D(c->em2_xy), D(c->em2_xz), D(c->em2_yz), D(c->eb_xy), D(c->eb_xz), D(c->eb_yz),
+                       D(c->toa_xy), D(c->toa_xz), D(c->toa_yz), D(c->dtv_x), D(c->dtv_x), D(c->dtv_x)};
+  // (double-float form: em2_* hold the raw edge moduli, dtv_x the per-centre velocity pseudo-step)
+  PT_LAUNCH(c, K_DF_COEF, lean_coef<df64>(grid_dims(b), block_dims(), c->stream, b, c->fcoef, ci, co));
+}
+
+// The cells kernel's inputs at double-float iterate a, outputs into buffer n.
+void df_cells(pt_ctx* c, int a, int n, int check) {
+  const Box& b = c->box;
+  LeanCellIn<df64> ci{c->fVx, c->fVy, c->fVz, c->fPt[a], c->fPf[a], c->fphi[a], D(c->lw[a]), D(c->lperm[a]),
+                      c->fPto, c->fPfo, D(c->phio), D(c->Eo), D(c->iEo), D(c->ieta), D(c->idtp), D(c->cm2),
+                      D(c->toa_xx), D(c->toa_yy), D(c->toa_zz), D(c->em2_xy), D(c->em2_xz), D(c->em2_yz),
+                      D(c->eb_xy), D(c->eb_xz), D(c->eb_yz), D(c->toa_xy), D(c->toa_xz), D(c->toa_yz),
+                      c->logk ? D(c->K0) : nullptr};
+  LeanCellOut<df64> co{c->fPt[n], c->fPf[n], c->fphi[n], D(c->lw[n]), D(c->lperm[n]), c->fs_txx, c->fs_tyy,
+                       c->fs_tzz, c->fs_txy, c->fs_txz, c->fs_tyz};
+  PT_LAUNCH(c, K_DF_CELLS, lean_cells<df64>(grid_dims(b), block_dims(), c->stream, b, c->fcoef, ci, co, c->red, check));
+}
+
+// One PT iteration in double-float: the lean form's kernels on the df64 iterate.
+void launch_iteration_df(pt_ctx* c, int check) {
+  const Box& b = c->box;
+  const dim3 bl = block_dims(), gr = grid_dims(b);
+  const int a = c->fcur, n = 1 - a;
+  if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+  df_cells(c, a, n, check);
+  LeanFaceIn<df64> fi{c->fs_txx, c->fs_tyy, c->fs_tzz, c->fs_txy, c->fs_txz, c->fs_tyz, c->fPt[n],
+                      c->fphi[a], D(c->dtv_x), D(c->dtv_x), D(c->dtv_x)};
+  PT_LAUNCH(c, K_DF_FACES, lean_faces<df64>(gr, bl, c->stream, b, c->fcoef, fi, c->fVx, c->fVy, c->fVz, c->fRx,
+                                            c->fRy, c->fRz, c->red, check));
+  if (check) {
+    LeanPicardIn<df64> pi{c->fs_txx, c->fs_tyy, c->fs_tzz, c->fs_txy, c->fs_txz, c->fs_tyz, c->fphi[n],
+                          c->fPt[n], c->fPf[n]};
+    PT_LAUNCH(c, K_DF_PICARD, lean_picard<df64>(gr, bl, c->stream, b, c->fcoef, pi, c->fmu, c->feta, c->red));
+    launch_df_coef(c);
+  }
+  c->fcur = n;
+  c->df_dirty = true;
+}
+
+// End of a double-float step: the stresses of the final state (one cells evaluation at the
+// current iterate; its pressure and porosity outputs land in the idle buffers and are dropped),
+// written to the caller's stress fields together with the iterate.
+int df_step_end(pt_ctx* c) {
+  const int a = c->fcur;
+  df_cells(c, a, 1 - a, 0);
+  double* const d[6] = {c->txx, c->tyy, c->tzz, c->txy, c->txz, c->tyz};
+  df64* const f[6] = {c->fs_txx, c->fs_tyy, c->fs_tzz, c->fs_txy, c->fs_txz, c->fs_tyz};
+  df_convert(c, d, f, 6, false);
+  df_export(c);
+  return cuda_status(cudaGetLastError());
 }
 
 int read_report(pt_ctx* c, pt_report* rep) {
@@ -432,7 +584,17 @@ int step_begin_launch(pt_ctx* c) {
   if (rc != PT_OK) return rc;
   const Box& b = c->box;
   cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-  if (c->lean) {
+  if (c->dfm) {
+    // the caller's fields become the double-float iterate; the FP64 old pressures are kept too
+    // (pt_residual evaluates the FP64 residual of the caller's fields)
+    df_import(c);
+    const size_t bytes = (size_t)b.n * sizeof(double);
+    cudaMemcpyAsync(c->Pto, c->Pt[0], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->Pfo, c->Pf[0], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    LeanBeginIn<df64> bi{c->fPt[0], c->fPf[0], c->fphi[0], c->fmu, c->logk ? D(c->K0) : nullptr};
+    LeanBeginOut<df64> bo{c->fPto, c->fPfo, D(c->phio), D(c->Eo), D(c->iEo), D(c->lw[0]), D(c->lperm[0])};
+    PT_LAUNCH(c, K_DF_BEGIN, lean_begin<df64>(grid_dims(b), block_dims(), c->stream, b, c->fcoef, bi, bo, c->red));
+  } else if (c->lean) {
     LeanBeginIn<double> bi{c->Pt[0], c->Pf[0], c->phi[0], c->mu, c->logk ? c->K0 : nullptr};
     LeanBeginOut<double> bo{c->Pto, c->Pfo, c->phio, c->Eo, c->iEo, c->lw[0], c->lperm[0]};
     PT_LAUNCH(c, K_LEAN_BEGIN, lean_begin<double>(grid_dims(b), block_dims(), c->stream, b, c->lcoef, bi, bo, c->red));
@@ -465,12 +627,20 @@ int step_begin_finish(pt_ctx* c, double mu_max) {
     double* dst[6] = {c->txxo, c->tyyo, c->tzzo, c->txyo, c->txzo, c->tyzo};
     for (int s = 0; s < 6 && e == cudaSuccess; ++s)
       e = cudaMemcpyAsync(dst[s], src[s], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (c->dfm && e == cudaSuccess) {
+      df64* const f[6] = {c->ftxxo, c->ftyyo, c->ftzzo, c->ftxyo, c->ftxzo, c->ftyzo};
+      df_convert(c, dst, f, 6, true);
+    }
     c->dt_cum = 0.0;
   }
   c->nsteps += 1;
   fill_coef(c);
   if (c->lean && e == cudaSuccess) {
     launch_lean_coef(c);
+    e = cudaGetLastError();
+  }
+  if (c->dfm && e == cudaSuccess) {
+    launch_df_coef(c);
     e = cudaGetLastError();
   }
   return cuda_status(e);
@@ -493,7 +663,8 @@ int32_t pt_pitch_x(const pt_grid* grid) {
 size_t pt_workspace_size(const pt_grid* grid, const pt_num* num) {
   if (!grid_ok(grid) || !num) return 0;
   const Box b = make_box(grid);
-  const int arrays = kRefArrays + (num->precision == PT_FP64 ? kLeanArrays : 0);
+  const bool df = num->precision == PT_DF64;
+  const int arrays = kRefArrays + ((num->precision == PT_FP64 || df) ? kLeanArrays : 0) + (df ? kDfArrays : 0);
   const size_t mixed = num->precision == PT_FP32 ? kMixArrays * align_up((size_t)b.n * sizeof(float), kAlign) : 0;
   return arrays * align_up((size_t)b.n * sizeof(double), kAlign) + mixed + kAlign;
 }
@@ -509,7 +680,8 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   if (!(num->rho_i > 0) || !(num->cfl_v > 0) || !(num->cfl_pf > 0) || !(num->dtpt_scale > 0) ||
       !(num->xsi_w > 0))
     return PT_EINVAL;
-  if (num->precision != PT_FP64 && num->precision != PT_FP64_STEPWISE && num->precision != PT_FP32)
+  if (num->precision != PT_FP64 && num->precision != PT_FP64_STEPWISE && num->precision != PT_FP32 &&
+      num->precision != PT_DF64)
     return PT_EINVAL;
   if (!phys_ok(phys)) return PT_EINVAL;
   double* const ptrs[] = {f->Vx, f->Vy, f->Vz, f->Pt, f->Pf, f->phi, f->txx, f->tyy,
@@ -545,9 +717,21 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
       &c->toa_yy, &c->toa_zz, &c->toa_xy, &c->toa_xz, &c->toa_yz, &c->cm2, &c->idtp, &c->ieta,
       &c->em2_xy, &c->em2_xz, &c->em2_yz, &c->eb_xy, &c->eb_xz, &c->eb_yz, &c->dtv_x, &c->dtv_y, &c->dtv_z,
       &c->K0};
-  const int arrays = kRefArrays + (c->lean ? kLeanArrays : 0);
+  c->dfm = num->precision == PT_DF64;
+  c->df_dirty = false;
+  c->fcur = 0;
+  const int arrays = kRefArrays + ((c->lean || c->dfm) ? kLeanArrays : 0);
   for (int s = 0; s < arrays; ++s) *slots[s] = (double*)(w + s * stride);
   char* wend = w + arrays * stride;
+  if (c->dfm) {
+    df64** fslots[kDfArrays] = {&c->fVx, &c->fVy, &c->fVz, &c->fPt[0], &c->fPt[1], &c->fPf[0], &c->fPf[1],
+                                &c->fphi[0], &c->fphi[1], &c->fmu, &c->feta, &c->fRx, &c->fRy, &c->fRz,
+                                &c->fs_txx, &c->fs_tyy, &c->fs_tzz, &c->fs_txy, &c->fs_txz, &c->fs_tyz,
+                                &c->ftxxo, &c->ftyyo, &c->ftzzo, &c->ftxyo, &c->ftxzo, &c->ftyzo, &c->fPto,
+                                &c->fPfo};
+    for (int s = 0; s < kDfArrays; ++s) *fslots[s] = (df64*)(wend + s * stride);
+    wend += kDfArrays * stride;
+  }
   c->mixed = num->precision == PT_FP32;
   c->mix_omega = 1.0;
   c->mix_prev = 0.0;
@@ -578,6 +762,11 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   fill_coef(c);
   // zero the whole workspace (damped residuals, old stresses, scratch padding)
   cudaError_t e = cudaMemsetAsync(workspace, 0, pt_workspace_size(grid, num), c->stream);
+  if (e == cudaSuccess && c->dfm && c->logk) {
+    PT_LAUNCH(c, K_DF_K0, lean_k0<df64>(grid_dims(c->box), block_dims(), c->stream, c->box, c->phys.k0, c->logk,
+                                        D(c->K0)));
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && c->lean && c->logk) {
     PT_LAUNCH(c, K_LEAN_K0, lean_k0<double>(grid_dims(c->box), block_dims(), c->stream, c->box, c->phys.k0, c->logk,
                                             c->K0));
@@ -654,6 +843,11 @@ int pt_iterate(pt_ctx* c, int32_t it0, int32_t niter, pt_report* rep) {
 
 int pt_step_end(pt_ctx* c) {
   if (!c) return PT_EINVAL;
+  if (c->dfm) {
+    const int rc = df_step_end(c);
+    c->dt_cum += c->num.dt;
+    return rc;
+  }
   int rc = sync_current_to_caller(c);
   if (rc != PT_OK) return rc;
   const Box& b = c->box;
@@ -781,6 +975,17 @@ void pt_destroy(pt_ctx* c) {
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   cudaFreeHost(c->h_red);
   delete c;
+}
+
+int pt_math_check(int32_t fn, const double* a, const double* b, double* out, int64_t n, void* stream) {
+  if (fn < 0 || fn >= MATH_COUNT || !a || !out || n < 0) return PT_EINVAL;
+  if ((fn == MATH_DF_ADD || fn == MATH_DF_SUB || fn == MATH_DF_MUL || fn == MATH_DF_FMA || fn == MATH_DF_ROOT) && !b)
+    return PT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  math_check(st, fn, a, b, out, (long long)n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e);
 }
 
 const char* pt_strerror(int code) {
@@ -1226,7 +1431,7 @@ int ckpt_io(pt_ctx* c, int slot, bool save) {
 
 bool adjoint_scope_ok(const pt_ctx* c) {
   return c->phys.powerlaw_on == 0 && c->phys.compaction_on != 0 && c->phys.R_weak == 1.0 &&
-         c->num.beta_n == 0.0 && !c->mixed && (c->lean || !c->logk);
+         c->num.beta_n == 0.0 && !c->mixed && !c->dfm && (c->lean || !c->logk);
 }
 
 // The adjoint's working arrays (kAdjArrays consecutive workspace arrays from `base`).

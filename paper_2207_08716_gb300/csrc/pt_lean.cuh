@@ -1,7 +1,9 @@
 // pt_lean.cuh — argument structs and declarations of the FP64-lean PT kernels
-// (pt_lean_kernels.cu). T is the field type (double; float for the FP32 form).
+// (pt_lean_kernels.cu). T is the field and arithmetic type: double (PT_FP64) or the
+// double-float df64 (PT_DF64).
 #pragma once
 
+#include "df64.cuh"
 #include "pt_common.cuh"
 
 namespace pt {
@@ -25,10 +27,12 @@ struct LeanCoef {
   int compaction_on, powerlaw_on;
   T ebg;                        // background xy strain rate tau_bg / (2 mu0) (Eqs. 32-33)
   int bg_on;                    // tau_bg != 0: wall xy-edges carry the background stress
-  // Picard and coefficient refresh run in FP64
-  double mu0, eta0, tau0, n_pow, rel_mu, rel_eta, R_weak;
-  double rtau0_2;               // 1 / tau0^2
-  double rGdtS, dtaupt_fac, dtauv_fac;
+  // Picard update and coefficient refresh
+  T mu0, eta0, R_weak;
+  T rtau0_2;                    // 1 / tau0^2
+  T rGdtS, dtaupt_fac, dtauv_fac;
+  double tau0, n_pow, rel_mu, rel_eta;
+  int root_mu, root_eta;        // m when rel = 1/m (2 <= m <= 64), else 0 (double-float roots)
 };
 
 template <class T>
@@ -91,5 +95,18 @@ void lean_begin(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, 
                 const LeanBeginOut<T>& out, unsigned long long* red);
 template <class T>
 void lean_k0(dim3 gr, dim3 bl, cudaStream_t st, Box b, double k0, const double* logk, T* K0);
+
+// Up to 16 arrays converted in one launch between FP64 (d) and double-float (f), whole boxes.
+struct DfCopy {
+  double* d[16];
+  df64* f[16];
+};
+void df64_convert(cudaStream_t st, const DfCopy& cp, int narrays, long long n, bool to_df);
+
+// Element-wise application of one device math routine (pt_math_check; codes in porowave_pt.h).
+enum { MATH_RCP_PSEUDO = 0, MATH_RCP_FULL = 1, MATH_EXPM1_POS = 2, MATH_EXPM1_NEG = 3, MATH_DF_ADD = 4,
+       MATH_DF_SUB = 5, MATH_DF_MUL = 6, MATH_DF_FMA = 7, MATH_DF_RCP = 8, MATH_DF_SQRT = 9,
+       MATH_DF_ROOT = 10, MATH_DF_EXPM1_POS = 11, MATH_DF_EXPM1_NEG = 12, MATH_COUNT = 13 };
+void math_check(cudaStream_t st, int fn, const double* a, const double* b, double* out, long long n);
 
 }  // namespace pt

@@ -2,6 +2,7 @@
 // the method), shared by the single-instance kernels and the batched (ensemble) kernels.
 #pragma once
 
+#include "df64.cuh"
 #include "pt_lean.cuh"
 
 namespace pt {
@@ -57,8 +58,9 @@ __device__ inline T tabs(T x) { return x < T(0) ? -x : x; }
 
 // 1 / x for the local-implicit pseudo-step denominators (x > 0, far inside the normal range):
 // the hardware's approximate reciprocal refined by one Newton step, r' = r + r (1 - x r), whose
-// relative error is the square of the seed's (~2^-46 in FP64). It only scales the pseudo-time
-// step of the update P - res / x, so the fixed point of the iteration does not depend on it.
+// relative error is the square of the seed's (the approximate FP64 reciprocal is good to about
+// 2^-20, so ~2^-40 after the step; measured below 1e-12). It only scales the pseudo-time step of
+// the update P - res / x, so the fixed point of the iteration does not depend on it.
 __device__ inline double rcp_pseudo(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
@@ -75,8 +77,79 @@ __device__ inline double rcp_full(double x) {
   return fma(r, fma(-x, r, 1.0), r);
 }
 
+// ---- the same operations in double-float (PT_DF64): one Newton step from the FP32 seed
+// reaches the format's own rounding (~2^-46), so the pseudo-step and the fixed-point
+// reciprocals are the same function
+__device__ inline df64 rcp_pseudo(df64 x) { return df_rcp(x); }
+__device__ inline df64 rcp_full(df64 x) { return df_rcp(x); }
+
+__device__ inline df64 pos_max(df64 a, df64 b) { return a < b ? b : a; }
+
+// Same tiers as the FP64 pair (the truncation stays below 2^-60 |d|, far under the format's
+// 2^-48); outside them the library expm1 in FP64.
+__device__ inline void expm1_pair(df64 d, df64& em_pos, df64& em_neg) {
+  const float ad = fabsf(d.hi);
+  if (ad <= 0x1p-20f) {
+    const df64 d2 = d * d;
+    const df64 E = scale2(d2, 0.5f);
+    const df64 O = d * fma(d2, df64(1.0 / 6.0), df64(1.0));
+    em_pos = E + O;
+    em_neg = E - O;
+  } else if (ad <= 0.015625f) {
+    const df64 d2 = d * d;
+    const df64 E = d2 * fma(d2, fma(d2, fma(d2, df64(1.0 / 40320.0), df64(1.0 / 720.0)), df64(1.0 / 24.0)),
+                            df64(0.5));
+    const df64 O = d * fma(d2, fma(d2, fma(d2, fma(d2, df64(1.0 / 362880.0), df64(1.0 / 5040.0)),
+                                           df64(1.0 / 120.0)), df64(1.0 / 6.0)), df64(1.0));
+    em_pos = E + O;
+    em_neg = E - O;
+  } else {
+    const double x = (double)d;
+    em_pos = df64(expm1(x));
+    em_neg = df64(expm1(-x));
+  }
+}
+
+// conversions between the field type and FP64 (identity for FP64)
+__device__ inline double to_d(double x) { return x; }
+__device__ inline double to_d(df64 x) { return (double)x; }
+template <class T>
+__device__ inline T from_d(double x) { return T(x); }
+
+// a / b: the plain quotient in FP64, the refined reciprocal in double-float
+__device__ inline double tdiv(double a, double b) { return a / b; }
+__device__ inline df64 tdiv(df64 a, df64 b) { return a * df_rcp(b); }
+
+__device__ inline double tmax(double a, double b) { return fmax(a, b); }
+__device__ inline df64 tmax(df64 a, df64 b) { return a < b ? b : a; }
+
+// x^rel of the log-space Picard relaxation (x > 0). FP64: sqrt for rel = 1/2, else
+// exp(rel log x). Double-float: the square root for rel = 1/2, Newton's m-th root for
+// rel = 1/m (root = m, set on the host), else exp(rel log x) in FP64.
+__device__ inline double relax_pow(double x, double rel, int /*root*/) {
+  return rel == 0.5 ? sqrt(x) : exp(rel * log(x));
+}
+__device__ inline df64 relax_pow(df64 x, double rel, int root) {
+  if (root == 2) return df_sqrt(x);
+  if (root > 2) return df_root(x, root);
+  return df64(exp(rel * log((double)x)));
+}
+
 
 }  // namespace lean_detail
+
+// Which arrays a form stores. The FP64 form is bound by the FP64 pipe and stores everything that
+// changes less often than every iteration (1/(1-phi) and k travelling with phi, 1 - phi_o and its
+// reciprocal, edge moduli pre-multiplied by both spacings, three face pseudo-steps). Double-float
+// arithmetic is cheap and the double-float form is bound by HBM, so it recomputes 1/(1-phi),
+// k(phi) (from the porosity neighbours it loads anyway), 1 - phi_o and its reciprocal, keeps one
+// modulus per edge (em2_* hold 2 mu/(1+xi); eb_* unused) and one velocity pseudo-step per centre
+// (dtv_x = dtv_y = dtv_z hold fac / mu, averaged to each face): 72 fewer bytes per cell and
+// iteration.
+template <class T>
+struct LeanRecompute { static constexpr bool value = false; };
+template <>
+struct LeanRecompute<df64> { static constexpr bool value = true; };
 
 // Cells, stresses of the three lower edges, pressures, porosity at box index (i, j, k).
 template <class T>
@@ -90,19 +163,39 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     const bool cell = i < b.nx && j < b.ny && k < b.nz;
     // ---- edges owned by this index: xy (i, j, k), xz (i, j, k), yz (i, j, k); stored at the end
     // with the cell's outputs, after every load (the arrays are not declared non-aliasing)
+    constexpr bool RC = LeanRecompute<T>::value;
     T t_xy = T(0), t_xz = T(0), t_yz = T(0);
     if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {   // toa_xy holds the background part too
-      t_xy = fma(in.eb_xy[q], in.Vy[q] - in.Vy[q - 1], fma(in.em2_xy[q], in.Vx[q] - in.Vx[q - px], in.toa_xy[q]));
+      if constexpr (RC)
+        t_xy = fma(in.em2_xy[q], fma(in.Vy[q] - in.Vy[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - px]) * c.hrdy), in.toa_xy[q]);
+      else
+        t_xy = fma(in.eb_xy[q], in.Vy[q] - in.Vy[q - 1], fma(in.em2_xy[q], in.Vx[q] - in.Vx[q - px], in.toa_xy[q]));
     } else if (k < b.nz && c.bg_on) {   // wall xy-edge under background shear (Eqs. 32-33)
       t_xy = in.toa_xy[q];
     }
-    if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz)
-      t_xz = fma(in.eb_xz[q], in.Vz[q] - in.Vz[q - 1], fma(in.em2_xz[q], in.Vx[q] - in.Vx[q - pxy], in.toa_xz[q]));
-    if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz)
-      t_yz = fma(in.eb_yz[q], in.Vz[q] - in.Vz[q - px], fma(in.em2_yz[q], in.Vy[q] - in.Vy[q - pxy], in.toa_yz[q]));
+    if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
+      if constexpr (RC)
+        t_xz = fma(in.em2_xz[q], fma(in.Vz[q] - in.Vz[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz), in.toa_xz[q]);
+      else
+        t_xz = fma(in.eb_xz[q], in.Vz[q] - in.Vz[q - 1], fma(in.em2_xz[q], in.Vx[q] - in.Vx[q - pxy], in.toa_xz[q]));
+    }
+    if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
+      if constexpr (RC)
+        t_yz = fma(in.em2_yz[q], fma(in.Vz[q] - in.Vz[q - px], c.hrdy, (in.Vy[q] - in.Vy[q - pxy]) * c.hrdz), in.toa_yz[q]);
+      else
+        t_yz = fma(in.eb_yz[q], in.Vz[q] - in.Vz[q - px], fma(in.em2_yz[q], in.Vy[q] - in.Vy[q - pxy], in.toa_yz[q]));
+    }
     if (cell) {
       const T Pt = in.Pt[q], Pf = in.Pf[q], Pto = in.Pto[q], Pfo = in.Pfo[q];
-      const T ph = in.phi[q], w = in.w[q], ieta = in.ieta[q];
+      const T ph = in.phi[q], ieta = in.ieta[q];
+      // k = K0 (phi / phi0)^3 (Eq. 23) at box index e with porosity p (recomputing forms)
+      auto kperm = [&](T p, long long e) {
+        const T r = p * c.rphi0;
+        return (in.K0 ? in.K0[e] : c.k0) * r * r * r;
+      };
+      T w;
+      if constexpr (RC) w = rcp_full(T(1.0) - ph);
+      else w = in.w[q];
       const T vxl = in.Vx[q], vxr = in.Vx[q + 1], vyl = in.Vy[q], vyr = in.Vy[q + px];
       const T vzl = in.Vz[q], vzr = in.Vz[q + pxy];
       const T gx = (vxr - vxl) * c.rdx, gy = (vyr - vyl) * c.rdy, gz = (vzr - vzl) * c.rdz;
@@ -112,35 +205,49 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       // explicit fused multiply-adds: the same rounding in every kernel that inlines this body
       const T divVn = fma(dpp, cc, fma(-c.bd_rdt_a, dPf, fma(c.bd_rdt, dPt, divV)));
       // Darcy flux through the six faces (zero on the boundary) and the largest neighbour k
-      const T kc = in.perm[q];
+      T kc;
+      if constexpr (RC) kc = kperm(ph, q);
+      else kc = in.perm[q];
       T kmax = kc, sx = T(0), sy = T(0), sz = T(0);
       if (i > 0) {
-        const T kn = in.perm[q - 1];
+        T kn;
+        if constexpr (RC) kn = kperm(in.phi[q - 1], q - 1);
+        else kn = in.perm[q - 1];
         kmax = pos_max(kmax, kn);
         sx -= (kn + kc) * (Pf - in.Pf[q - 1]);
       }
       if (i < b.nx - 1) {
-        const T kn = in.perm[q + 1];
+        T kn;
+        if constexpr (RC) kn = kperm(in.phi[q + 1], q + 1);
+        else kn = in.perm[q + 1];
         kmax = pos_max(kmax, kn);
         sx += (kc + kn) * (in.Pf[q + 1] - Pf);
       }
       if (j > 0) {
-        const T kn = in.perm[q - px];
+        T kn;
+        if constexpr (RC) kn = kperm(in.phi[q - px], q - px);
+        else kn = in.perm[q - px];
         kmax = pos_max(kmax, kn);
         sy -= (kn + kc) * (Pf - in.Pf[q - px]);
       }
       if (j < b.ny - 1) {
-        const T kn = in.perm[q + px];
+        T kn;
+        if constexpr (RC) kn = kperm(in.phi[q + px], q + px);
+        else kn = in.perm[q + px];
         kmax = pos_max(kmax, kn);
         sy += (kc + kn) * (in.Pf[q + px] - Pf);
       }
       if (k > 0) {
-        const T kn = in.perm[q - pxy];
+        T kn;
+        if constexpr (RC) kn = kperm(in.phi[q - pxy], q - pxy);
+        else kn = in.perm[q - pxy];
         kmax = pos_max(kmax, kn);
         sz -= (kn + kc) * ((Pf - in.Pf[q - pxy]) + c.buoy_dz);
       }
       if (k < b.nz - 1) {
-        const T kn = in.perm[q + pxy];
+        T kn;
+        if constexpr (RC) kn = kperm(in.phi[q + pxy], q + pxy);
+        else kn = in.perm[q + pxy];
         kmax = pos_max(kmax, kn);
         sz += (kc + kn) * ((in.Pf[q + pxy] - Pf) + c.buoy_dz);
       }
@@ -174,7 +281,15 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       const T delta = -(c.beta_phi * ((Pf1 - Pfo) - (Pt1 - Pto)) + c.dt * (comp + adv));
       T em_p, em_n;
       expm1_pair(delta, em_p, em_n);
-      const T phio = in.phio[q], Eo = in.Eo[q], iEo = in.iEo[q];
+      const T phio = in.phio[q];
+      T Eo, iEo;
+      if constexpr (RC) {
+        Eo = T(1.0) - phio;
+        iEo = T(0.0);   // not needed: 1/(1-phi) is recomputed from phi
+      } else {
+        Eo = in.Eo[q];
+        iEo = in.iEo[q];
+      }
       const T K0 = in.K0 ? in.K0[q] : c.k0;
       const T ph1 = phio - Eo * em_p;
       const T r = ph1 * c.rphi0;
@@ -185,11 +300,13 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       out.tyy[q] = syy;
       out.tzz[q] = szz;
       out.phi[q] = ph1;
-      out.w[q] = iEo + iEo * em_n;
-      out.perm[q] = K0 * r * r * r;
+      if constexpr (!RC) {
+        out.w[q] = iEo + iEo * em_n;
+        out.perm[q] = K0 * r * r * r;
+      }
       if (check) {
-        r_pt = (double)tabs(divVn);
-        r_pf = (double)tabs(resF);
+        r_pt = to_d(tabs(divVn));
+        r_pf = to_d(tabs(resF));
       }
     }
     if (k < b.nz) out.txy[q] = t_xy;
@@ -206,6 +323,7 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
                                                 T* __restrict__ Rx, T* __restrict__ Ry, T* __restrict__ Rz,
                                                 int i, int j, int k, int check, double& r_v, int mask = 7) {
   using namespace lean_detail;
+  constexpr bool RC = LeanRecompute<T>::value;
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
@@ -219,13 +337,19 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
       Fx = (in.txx[q] - in.txx[q - 1]) * c.rdx_r + (in.txy[q + px] - in.txy[q]) * c.rdy_r +
            (in.txz[q + pxy] - in.txz[q]) * c.rdz_r - (in.Pt1[q] - in.Pt1[q - 1]) * c.rdx_r;
       Rx1 = fma(c.damp_x, Rx[q], Fx);
-      Vx1 = fma(in.dtv_x[q], Rx1, Vx[q]);
+      T dtv;
+      if constexpr (RC) dtv = T(0.5) * (in.dtv_x[q - 1] + in.dtv_x[q]);
+      else dtv = in.dtv_x[q];
+      Vx1 = fma(dtv, Rx1, Vx[q]);
     }
     if (fy) {
       Fy = (in.txy[q + 1] - in.txy[q]) * c.rdx_r + (in.tyy[q] - in.tyy[q - px]) * c.rdy_r +
            (in.tyz[q + pxy] - in.tyz[q]) * c.rdz_r - (in.Pt1[q] - in.Pt1[q - px]) * c.rdy_r;
       Ry1 = fma(c.damp_y, Ry[q], Fy);
-      Vy1 = fma(in.dtv_y[q], Ry1, Vy[q]);
+      T dtv;
+      if constexpr (RC) dtv = T(0.5) * (in.dtv_y[q - px] + in.dtv_y[q]);
+      else dtv = in.dtv_y[q];
+      Vy1 = fma(dtv, Ry1, Vy[q]);
     }
     if (fz) {
       // buoyancy -(rho g - rho_BG g) averaged to the face, rho g - rho_BG g = (phi - phi0) drho_g
@@ -233,15 +357,18 @@ __device__ __forceinline__ void lean_face_point(const Box& b, const LeanCoef<T>&
       Fz = (in.txz[q + 1] - in.txz[q]) * c.rdx_r + (in.tyz[q + px] - in.tyz[q]) * c.rdy_r +
            (in.tzz[q] - in.tzz[q - pxy]) * c.rdz_r - (in.Pt1[q] - in.Pt1[q - pxy]) * c.rdz_r - rog;
       Rz1 = fma(c.damp_z, Rz[q], Fz);
-      Vz1 = fma(in.dtv_z[q], Rz1, Vz[q]);
+      T dtv;
+      if constexpr (RC) dtv = T(0.5) * (in.dtv_z[q - pxy] + in.dtv_z[q]);
+      else dtv = in.dtv_z[q];
+      Vz1 = fma(dtv, Rz1, Vz[q]);
     }
     if (fx) { Rx[q] = Rx1; Vx[q] = Vx1; }
     if (fy) { Ry[q] = Ry1; Vy[q] = Vy1; }
     if (fz) { Rz[q] = Rz1; Vz[q] = Vz1; }
     if (check) {
-      if (fx && (mask & 1)) r_v = fmax(r_v, (double)tabs(Fx) * (double)c.rho_i);
-      if (fy && (mask & 2)) r_v = fmax(r_v, (double)tabs(Fy) * (double)c.rho_i);
-      if (fz && (mask & 4)) r_v = fmax(r_v, (double)tabs(Fz) * (double)c.rho_i);
+      if (fx && (mask & 1)) r_v = fmax(r_v, to_d(tabs(Fx)) * to_d(c.rho_i));
+      if (fy && (mask & 2)) r_v = fmax(r_v, to_d(tabs(Fy)) * to_d(c.rho_i));
+      if (fz && (mask & 4)) r_v = fmax(r_v, to_d(tabs(Fz)) * to_d(c.rho_i));
     }
   }
 }
@@ -257,32 +384,45 @@ __device__ __forceinline__ void lean_picard_point(const Box& b, const LeanCoef<T
   if (i < b.nx && j < b.ny && k < b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
-    const double axy = 0.25 * ((double)in.txy[q] + in.txy[q + 1] + in.txy[q + px] + in.txy[q + 1 + px]);
-    const double axz = 0.25 * ((double)in.txz[q] + in.txz[q + 1] + in.txz[q + pxy] + in.txz[q + 1 + pxy]);
-    const double ayz = 0.25 * ((double)in.tyz[q] + in.tyz[q + px] + in.tyz[q + pxy] + in.tyz[q + px + pxy]);
-    const double sxx = in.txx[q], syy = in.tyy[q], szz = in.tzz[q];
+    const T axy = T(0.25) * (in.txy[q] + in.txy[q + 1] + in.txy[q + px] + in.txy[q + 1 + px]);
+    const T axz = T(0.25) * (in.txz[q] + in.txz[q + 1] + in.txz[q + pxy] + in.txz[q + 1 + pxy]);
+    const T ayz = T(0.25) * (in.tyz[q] + in.tyz[q + px] + in.tyz[q + pxy] + in.tyz[q + px + pxy]);
+    const T sxx = in.txx[q], syy = in.tyy[q], szz = in.tzz[q];
     // tau_II^2 = (sxx^2 + syy^2 + szz^2) / 2 + axy^2 + axz^2 + ayz^2 (explicit FMAs: every form
     // that inlines this body rounds it alike)
-    const double tII2 = fma(0.5, fma(sxx, sxx, fma(syy, syy, szz * szz)), fma(axy, axy, fma(axz, axz, ayz * ayz)));
+    const T tII2 = fma(T(0.5), fma(sxx, sxx, fma(syy, syy, szz * szz)), fma(axy, axy, fma(axz, axz, ayz * ayz)));
     // Eq. 24: mu* = mu0 / (1 + (tau_II / tau0)^(n-1)); the log-space relaxation
     // exp(rel log mu* + (1 - rel) log mu) is written mu (mu* / mu)^rel (a square root for rel = 1/2)
-    double den = 1.0;
+    T den = T(1.0);
     if (c.powerlaw_on) {
-      const double x2 = tII2 * c.rtau0_2;                        // (tau_II / tau0)^2
+      const T x2 = tII2 * c.rtau0_2;                               // (tau_II / tau0)^2
       const double p = c.n_pow - 1.0;
-      den = p == 2.0 ? 1.0 + x2 : 1.0 + exp(0.5 * p * log(x2));
+      den = p == 2.0 ? T(1.0) + x2 : from_d<T>(1.0 + exp(0.5 * p * log(to_d(x2))));
     }
-    const double mu_old = mu[q], eta_old = eta[q];
-    const double x_mu = c.mu0 / (den * mu_old);                  // mu* / mu
-    const double mu_new = mu_old * (c.rel_mu == 0.5 ? sqrt(x_mu) : exp(c.rel_mu * log(x_mu)));
-    const double R = (in.Pf1[q] > in.Pt1[q]) ? c.R_weak : 1.0;
+    const T mu_old = mu[q], eta_old = eta[q];
+    const T x_mu = tdiv(c.mu0, den * mu_old);                        // mu* / mu
+    const T mu_new = mu_old * relax_pow(x_mu, c.rel_mu, c.root_mu);
+    const T R = (in.Pf1[q] > in.Pt1[q]) ? c.R_weak : T(1.0);
     // Eq. 26: eta* = eta0 mu / phi R (with the relaxed mu), relaxed the same way
-    const double x_eta = c.eta0 * mu_new * R / ((double)in.phi1[q] * eta_old);
-    m = fmax(fmax(x_mu, rcp_full(x_mu)), fmax(x_eta, rcp_full(x_eta)));
-    if (!(x_mu == x_mu && x_eta == x_eta)) m = x_mu + x_eta;     // NaN stays NaN (fmax drops it)
-    mu[q] = (T)mu_new;
-    eta[q] = (T)(eta_old * (c.rel_eta == 0.5 ? sqrt(x_eta) : exp(c.rel_eta * log(x_eta))));
+    const T x_eta = tdiv(c.eta0 * mu_new * R, in.phi1[q] * eta_old);
+    m = to_d(tmax(tmax(x_mu, rcp_full(x_mu)), tmax(x_eta, rcp_full(x_eta))));
+    if (!(x_mu == x_mu && x_eta == x_eta)) m = to_d(x_mu) + to_d(x_eta);   // NaN stays NaN (fmax drops it)
+    mu[q] = mu_new;
+    eta[q] = eta_old * relax_pow(x_eta, c.rel_eta, c.root_eta);
   }
+}
+
+// Mean shear viscosity over the centres next to the xy-edge q = (i, j, .) that lie inside the
+// grid (four inside, two on a wall, one in a corner), in a fixed order (1/n exact: n = 1, 2, 4).
+template <class T>
+__device__ inline T lean_edge_mean_mu_xy(const Box& b, const T* mu, long long q, int i, int j) {
+  T s = T(0.0);
+  int n = 0;
+  if (i > 0 && j > 0) { s += mu[q - 1 - b.px]; ++n; }
+  if (i < b.nx && j > 0) { s += mu[q - b.px]; ++n; }
+  if (i > 0 && j < b.ny) { s += mu[q - 1]; ++n; }
+  if (i < b.nx && j < b.ny) { s += mu[q]; ++n; }
+  return s * T(n == 4 ? 0.25 : (n == 2 ? 0.5 : 1.0));
 }
 
 // Coefficient refresh at box index (i, j, k).
@@ -293,52 +433,71 @@ __device__ __forceinline__ void lean_coef_point(const Box& b, const LeanCoef<T>&
   if (i > b.nx || j > b.ny || k > b.nz) return;
   const long long q = cidx(b, i, j, k);
   const long long px = b.px, pxy = b.pxy;
-  const double rG = c.rGdtS;
+  constexpr bool RC = LeanRecompute<T>::value;
+  const T rG = c.rGdtS;
+  const T one = T(1.0), two = T(2.0);
   if (i < b.nx && j < b.ny && k < b.nz) {
-    const double m = in.mu[q];
-    const double s = rcp_full(fma(m, rG, 1.0));
-    const double a = 1.0 - s;                         // xi / (1 + xi)
-    out.cm2[q] = (T)(2.0 * m * s);
-    out.toa_xx[q] = (T)(in.txxo[q] * a);
-    out.toa_yy[q] = (T)(in.tyyo[q] * a);
-    out.toa_zz[q] = (T)(in.tzzo[q] * a);
-    out.idtp[q] = (T)(rcp_full(c.dtaupt_fac * m) + (double)c.bd_rdt);   // 1/dtau_Pt + beta_d/dt
-    out.ieta[q] = (T)rcp_full((double)in.eta[q]);
+    const T m = in.mu[q];
+    const T s = rcp_full(fma(m, rG, one));
+    const T a = one - s;                              // xi / (1 + xi)
+    out.cm2[q] = two * m * s;
+    out.toa_xx[q] = in.txxo[q] * a;
+    out.toa_yy[q] = in.tyyo[q] * a;
+    out.toa_zz[q] = in.tzzo[q] * a;
+    out.idtp[q] = rcp_full(c.dtaupt_fac * m) + c.bd_rdt;   // 1/dtau_Pt + beta_d/dt
+    out.ieta[q] = rcp_full(in.eta[q]);
   }
   if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
-    const double m = 0.25 * ((double)in.mu[q - 1 - px] + in.mu[q - px] + in.mu[q - 1] + in.mu[q]);
-    const double s = rcp_full(fma(m, rG, 1.0));
-    out.em2_xy[q] = (T)(2.0 * m * s * (double)c.hrdy);
-    out.eb_xy[q] = (T)(2.0 * m * s * (double)c.hrdx);
+    const T m = T(0.25) * (in.mu[q - 1 - px] + in.mu[q - px] + in.mu[q - 1] + in.mu[q]);
+    const T s = rcp_full(fma(m, rG, one));
+    if constexpr (RC) {
+      out.em2_xy[q] = two * m * s;
+    } else {
+      out.em2_xy[q] = two * m * s * c.hrdy;
+      out.eb_xy[q] = two * m * s * c.hrdx;
+    }
     // the background shear's stress 2 mu/(1+xi) tau_bg/(2 mu0) (Eqs. 32-33) joins the old-stress part
-    out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
+    out.toa_xy[q] = in.txyo[q] * (one - s) + two * m * s * c.ebg;
   } else if (k < b.nz && c.bg_on) {   // wall xy-edges carry the background stress
-    const double m = edge_mean_mu_xy(b, in.mu, q, i, j);
-    const double s = rcp_full(fma(m, rG, 1.0));
-    out.toa_xy[q] = (T)(in.txyo[q] * (1.0 - s) + 2.0 * m * s * (double)c.ebg);
+    const T m = lean_edge_mean_mu_xy(b, in.mu, q, i, j);
+    const T s = rcp_full(fma(m, rG, one));
+    out.toa_xy[q] = in.txyo[q] * (one - s) + two * m * s * c.ebg;
   }
   if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
-    const double m = 0.25 * ((double)in.mu[q - 1 - pxy] + in.mu[q - pxy] + in.mu[q - 1] + in.mu[q]);
-    const double s = rcp_full(fma(m, rG, 1.0));
-    out.em2_xz[q] = (T)(2.0 * m * s * (double)c.hrdz);
-    out.eb_xz[q] = (T)(2.0 * m * s * (double)c.hrdx);
-    out.toa_xz[q] = (T)(in.txzo[q] * (1.0 - s));
+    const T m = T(0.25) * (in.mu[q - 1 - pxy] + in.mu[q - pxy] + in.mu[q - 1] + in.mu[q]);
+    const T s = rcp_full(fma(m, rG, one));
+    if constexpr (RC) {
+      out.em2_xz[q] = two * m * s;
+    } else {
+      out.em2_xz[q] = two * m * s * c.hrdz;
+      out.eb_xz[q] = two * m * s * c.hrdx;
+    }
+    out.toa_xz[q] = in.txzo[q] * (one - s);
   }
   if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
-    const double m = 0.25 * ((double)in.mu[q - px - pxy] + in.mu[q - pxy] + in.mu[q - px] + in.mu[q]);
-    const double s = rcp_full(fma(m, rG, 1.0));
-    out.em2_yz[q] = (T)(2.0 * m * s * (double)c.hrdz);
-    out.eb_yz[q] = (T)(2.0 * m * s * (double)c.hrdy);
-    out.toa_yz[q] = (T)(in.tyzo[q] * (1.0 - s));
+    const T m = T(0.25) * (in.mu[q - px - pxy] + in.mu[q - pxy] + in.mu[q - px] + in.mu[q]);
+    const T s = rcp_full(fma(m, rG, one));
+    if constexpr (RC) {
+      out.em2_yz[q] = two * m * s;
+    } else {
+      out.em2_yz[q] = two * m * s * c.hrdz;
+      out.eb_yz[q] = two * m * s * c.hrdy;
+    }
+    out.toa_yz[q] = in.tyzo[q] * (one - s);
   }
-  // pseudo-time steps of the velocities, mean of the two centres' dtau_V = fac / mu
-  const double imu = (i < b.nx && j < b.ny && k < b.nz) ? rcp_full((double)in.mu[q]) : 0.0;
+  // pseudo-time steps of the velocities, mean of the two centres' dtau_V = fac / mu (the
+  // recomputing forms store the centre values and average them in the faces kernel)
+  if constexpr (RC) {
+    if (i < b.nx && j < b.ny && k < b.nz) out.dtv_x[q] = c.dtauv_fac * rcp_full(in.mu[q]);
+    return;
+  }
+  const T imu = (i < b.nx && j < b.ny && k < b.nz) ? rcp_full(in.mu[q]) : T(0.0);
   if (i > 0 && i < b.nx && j < b.ny && k < b.nz)
-    out.dtv_x[q] = (T)(0.5 * c.dtauv_fac * (rcp_full((double)in.mu[q - 1]) + imu));
+    out.dtv_x[q] = T(0.5) * c.dtauv_fac * (rcp_full(in.mu[q - 1]) + imu);
   if (j > 0 && j < b.ny && i < b.nx && k < b.nz)
-    out.dtv_y[q] = (T)(0.5 * c.dtauv_fac * (rcp_full((double)in.mu[q - px]) + imu));
+    out.dtv_y[q] = T(0.5) * c.dtauv_fac * (rcp_full(in.mu[q - px]) + imu);
   if (k > 0 && k < b.nz && i < b.nx && j < b.ny)
-    out.dtv_z[q] = (T)(0.5 * c.dtauv_fac * (rcp_full((double)in.mu[q - pxy]) + imu));
+    out.dtv_z[q] = T(0.5) * c.dtauv_fac * (rcp_full(in.mu[q - pxy]) + imu);
 }
 
 }  // namespace pt

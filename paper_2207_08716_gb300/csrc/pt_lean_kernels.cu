@@ -24,11 +24,13 @@
 // damped R, V^{k+1}. k_lean_picard: Picard targets (Eqs. 24-26) with log-space relaxation.
 #include "pt_lean_body.cuh"
 
+#include <algorithm>
+
 namespace pt {
 
 // ------------------------------------------------------------------------------ cells
 template <class T>
-__global__ void __launch_bounds__(256) k_lean_cells(Box b, LeanCoef<T> c, LeanCellIn<T> in,
+__global__ void __launch_bounds__(256, 3) k_lean_cells(Box b, LeanCoef<T> c, LeanCellIn<T> in,
                                                     LeanCellOut<T> out, unsigned long long* red,
                                                     int check) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,24 +88,27 @@ __global__ void __launch_bounds__(256) k_lean_coef(Box b, LeanCoef<T> c, LeanCoe
 template <class T>
 __global__ void __launch_bounds__(256) k_lean_begin(Box b, LeanCoef<T> c, LeanBeginIn<T> in,
                                                     LeanBeginOut<T> out, unsigned long long* red) {
+  using namespace lean_detail;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   double m = 0.0;
   if (i < b.nx && j < b.ny && k < b.nz) {
     const long long q = cidx(b, i, j, k);
-    const double ph = in.phi[q];
-    const double Eo = 1.0 - ph;
-    const double iEo = 1.0 / Eo;
+    const T ph = in.phi[q];
     out.Pto[q] = in.Pt[q];
     out.Pfo[q] = in.Pf[q];
-    out.phio[q] = (T)ph;
-    out.Eo[q] = (T)Eo;
-    out.iEo[q] = (T)iEo;
-    out.w[q] = (T)iEo;
-    const double r = ph * (double)c.rphi0;
-    out.perm[q] = (T)((in.K0 ? (double)in.K0[q] : (double)c.k0) * r * r * r);
-    m = in.mu[q];
+    out.phio[q] = ph;
+    if constexpr (!LeanRecompute<T>::value) {   // the recomputing forms derive these from phi
+      const T Eo = T(1.0) - ph;
+      const T iEo = tdiv(T(1.0), Eo);
+      out.Eo[q] = Eo;
+      out.iEo[q] = iEo;
+      out.w[q] = iEo;
+      const T r = ph * c.rphi0;
+      out.perm[q] = (in.K0 ? in.K0[q] : c.k0) * r * r * r;
+    }
+    m = to_d(in.mu[q]);
   }
   block_max_atomic(m, red + RED_MUMAX);
 }
@@ -116,8 +121,71 @@ __global__ void k_lean_k0(Box b, double k0, const double* __restrict__ logk, T* 
   const int k = blockIdx.z;
   if (i < b.nx && j < b.ny && k < b.nz) {
     const long long q = cidx(b, i, j, k);
-    K0[q] = (T)(k0 * exp(logk[q]));
+    K0[q] = lean_detail::from_d<T>(k0 * exp(logk[q]));
   }
+}
+
+// ----------------------------------------------------------- FP64 <-> double-float copies
+// Element-wise over whole padded boxes (padding included), one array per blockIdx.y.
+__global__ void k_to_df64(DfCopy cp, long long n) {
+  const double* __restrict__ src = cp.d[blockIdx.y];
+  df64* __restrict__ dst = cp.f[blockIdx.y];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = df64(src[e]);
+}
+__global__ void k_from_df64(DfCopy cp, long long n) {
+  double* __restrict__ dst = cp.d[blockIdx.y];
+  const df64* __restrict__ src = cp.f[blockIdx.y];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+
+void df64_convert(cudaStream_t st, const DfCopy& cp, int narrays, long long n, bool to_df) {
+  if (narrays <= 0) return;
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = (n + 255) / 256;
+  const unsigned gx = (unsigned)std::max(1LL, std::min<long long>(want, 8LL * sms));
+  const dim3 gr(gx, (unsigned)narrays, 1);
+  if (to_df) k_to_df64<<<gr, 256, 0, st>>>(cp, n);
+  else k_from_df64<<<gr, 256, 0, st>>>(cp, n);
+}
+
+// ---------------------------------------------------------------- math check (test aid)
+// One of the hand-written device routines applied element-wise, so that each can be compared
+// with CUDA's own functions and with its stated error bound (the kernels inline the same code).
+__global__ void k_math_check(int fn, const double* __restrict__ a, const double* __restrict__ b,
+                             double* __restrict__ out, long long n) {
+  using namespace lean_detail;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double x = a[e], y = b ? b[e] : 0.0;
+    double r = 0.0, p = 0.0, m = 0.0;
+    df64 dp, dm;
+    switch (fn) {
+      case MATH_RCP_PSEUDO: r = rcp_pseudo(x); break;
+      case MATH_RCP_FULL: r = rcp_full(x); break;
+      case MATH_EXPM1_POS: expm1_pair(x, p, m); r = p; break;
+      case MATH_EXPM1_NEG: expm1_pair(x, p, m); r = m; break;
+      case MATH_DF_ADD: r = (double)(df64(x) + df64(y)); break;
+      case MATH_DF_SUB: r = (double)(df64(x) - df64(y)); break;
+      case MATH_DF_MUL: r = (double)(df64(x) * df64(y)); break;
+      case MATH_DF_FMA: r = (double)fma(df64(x), df64(y), df64(x)); break;
+      case MATH_DF_RCP: r = (double)df_rcp(df64(x)); break;
+      case MATH_DF_SQRT: r = (double)df_sqrt(df64(x)); break;
+      case MATH_DF_ROOT: r = (double)df_root(df64(x), (int)y); break;
+      case MATH_DF_EXPM1_POS: expm1_pair(df64(x), dp, dm); r = (double)dp; break;
+      case MATH_DF_EXPM1_NEG: expm1_pair(df64(x), dp, dm); r = (double)dm; break;
+      default: r = nan(""); break;
+    }
+    out[e] = r;
+  }
+}
+
+void math_check(cudaStream_t st, int fn, const double* a, const double* b, double* out, long long n) {
+  if (n <= 0) return;
+  const unsigned g = (unsigned)std::min<long long>((n + 255) / 256, 4096);
+  k_math_check<<<g, 256, 0, st>>>(fn, a, b, out, n);
 }
 
 template <class T>
@@ -161,5 +229,17 @@ template void lean_coef<double>(dim3, dim3, cudaStream_t, Box, const LeanCoef<do
 template void lean_begin<double>(dim3, dim3, cudaStream_t, Box, const LeanCoef<double>&, const LeanBeginIn<double>&,
                                  const LeanBeginOut<double>&, unsigned long long*);
 template void lean_k0<double>(dim3, dim3, cudaStream_t, Box, double, const double*, double*);
+
+template void lean_cells<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanCellIn<df64>&,
+                                 const LeanCellOut<df64>&, unsigned long long*, int);
+template void lean_faces<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanFaceIn<df64>&,
+                                 df64*, df64*, df64*, df64*, df64*, df64*, unsigned long long*, int);
+template void lean_picard<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanPicardIn<df64>&,
+                                  df64*, df64*, unsigned long long*);
+template void lean_coef<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanCoefIn<df64>&,
+                                const LeanCoefOut<df64>&);
+template void lean_begin<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanBeginIn<df64>&,
+                                 const LeanBeginOut<df64>&, unsigned long long*);
+template void lean_k0<df64>(dim3, dim3, cudaStream_t, Box, double, const double*, df64*);
 
 }  // namespace pt

@@ -19,14 +19,14 @@ LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
 SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu",
            "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu",
            "rx_api.cu", "rx_kernels.cu", "rx_mg_kernels.cu")
-HEADERS = ("pt_common.cuh", "pt_host.h", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
+HEADERS = ("pt_common.cuh", "pt_host.h", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "df64.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
 _lib = None
 
 PT_OK, PT_EINVAL, PT_ENOTCONV, PT_ENAN, PT_ETIMEOUT, PT_ECUDA, PT_ESPACE = 0, -1, -2, -3, -4, -5, -6
-PT_FP64, PT_FP32, PT_FP64_STEPWISE = 0, 1, 2
+PT_FP64, PT_FP32, PT_FP64_STEPWISE, PT_DF64 = 0, 1, 2, 3
 
 
 def _inputs():
@@ -173,6 +173,7 @@ SIGNATURES = {
     "pt_profile_begin": (C.c_int, [C.c_void_p]),
     "pt_profile_end": (C.c_int, [C.c_void_p, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
     "pt_launch_count": (C.c_int64, [C.c_void_p]),
+    "pt_math_check": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "pt_residual_static": (C.c_int, [C.POINTER(Grid), C.POINTER(Phys), C.POINTER(Num), C.POINTER(Fields),
                                      C.POINTER(OldFields), C.c_double, C.c_void_p, C.POINTER(Report)]),
     "pt_adjoint_workspace_size": (C.c_size_t, [C.POINTER(Grid), C.c_int32, C.c_int32]),

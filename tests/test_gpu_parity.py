@@ -35,7 +35,7 @@ def assert_fields(s, st, names=FIELDS, tol=TOL):
     return errs
 
 
-FP64_MODES = (0, 2)   # PT_FP64 (lean form), PT_FP64_STEPWISE
+FP64_MODES = (0, 2, 3)   # PT_FP64 (lean form), PT_FP64_STEPWISE, PT_DF64 (lean form in double-float)
 
 
 @pytest.mark.parametrize("mode", FP64_MODES)
@@ -104,11 +104,13 @@ def test_two_steps_stress_substepping(mode):
     s.close()
 
 
-def test_full_step_converges_like_oracle():
+@pytest.mark.parametrize("mode", (0, 3))
+def test_full_step_converges_like_oracle(mode):
     """pt_step on the 32^3 workload: converges (PT_OK) within one check interval of the
     oracle's iteration count; fields agree to the convergence tolerance."""
     PTSolver = _solver()
     p = I.c1_params(32)
+    p["precision"] = mode
     phi = I.gaussian_porosity(p)
     s = PTSolver(p, phi)
     rep = s.step()
@@ -169,7 +171,8 @@ def test_iteration_cap_returns_not_converged():
     s.close()
 
 
-def test_full_size_sampled_parity_511():
+@pytest.mark.parametrize("mode", (0, 3))
+def test_full_size_sampled_parity_511(mode):
     """511^3 benchmark workload, the launch configuration the benchmark times: 15 PT
     iterations (one Picard/check) on the GPU; the oracle recomputes sampled sub-blocks. One
     iteration depends on neighbours within 3 cells, so a sub-block with a 48-cell margin
@@ -178,11 +181,12 @@ def test_full_size_sampled_parity_511():
     import torch
     n, K, margin = 511, 15, 48
     p = I.large_params(n)
+    p["precision"] = mode
     centre = I.perturbed_centre(0)
     phi = I.gaussian_porosity(p, centres=(centre,))
     free = torch.cuda.mem_get_info()[0]
-    if free < 48e9:
-        pytest.skip("needs ~45 GB of free device memory")
+    if free < (48e9 if mode == 0 else 100e9):
+        pytest.skip("needs ~45 GB (FP64) or ~97 GB (double-float) of free device memory")
     s = PTSolver(p, phi)
     s.step_begin()
     s.iterate(0, K)
