@@ -47,34 +47,63 @@ KERNEL_BYTES_PER_CELL = {
     "k_corr_cells": 25 * 4, "k_corr_faces": 25 * 4,
     # adjoint PT iteration: cells reads 26 arrays and writes 10, faces reads 17 and writes 6
     "k_adj_cells": 36 * 8, "k_adj_faces": 23 * 8,
-    # double-float form (8 B per value): cells reads 21 arrays (V, Pt, Pf, phi, Pto, Pfo, phio, ieta,
-    # idtp, cm2, 3 toa_ii, 3 edge moduli, 3 toa_e) and writes 9 (Pt, Pf, phi, 6 stresses); faces
+    # double-float form (8 B per value): cells reads 22 arrays (V, Pt, Pf, phi, k, Pto, Pfo, phio,
+    # ieta, idtp, cm2, 3 toa_ii, 3 edge moduli, 3 toa_e) and writes 10 (Pt, Pf, phi, k, 6 stresses); faces
     # reads 15 (6 stresses, Pt, phi, centre dtau_V, 3 R, 3 V) and writes 6; Picard reads 11 and
     # writes 2; coefficients read 8 (mu, eta, 6 old stresses) and write 13; step start 4 + 3
-    "k_lean_cells_df64": 30 * 8, "k_lean_faces_df64": 21 * 8, "k_lean_picard_df64": 13 * 8,
-    "k_lean_coef_df64": 21 * 8, "k_lean_begin_df64": 7 * 8,
+    "k_lean_cells_df64": 32 * 8, "k_lean_faces_df64": 21 * 8, "k_lean_picard_df64": 13 * 8,
+    "k_lean_coef_df64": 21 * 8, "k_lean_begin_df64": 8 * 8,
 }
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp64-stepwise": 2, "df64": 3}
-# FP64 thread instructions (DFMA + DADD + DMUL) and flops (DFMA x 2 + DADD + DMUL) per cell and
-# launch from one ncu capture of the kernel (profiles/k_lean_fp64_191.md, k_adj_cells_95.md,
-# k_centres_fp64_stepwise_191.md); a kernel missing here has no current count.
-KERNEL_FP64_INST_PER_CELL = {"k_lean_cells": 99.9, "k_lean_faces": 32.8, "k_lean_picard": 105.2,
-                             "k_lean_coef": 91.5, "k_adj_cells": 76.5, "k_centres": 152.0}
-KERNEL_FP64_FLOPS_PER_CELL = {"k_lean_cells": 147.9, "k_lean_faces": 49.7, "k_adj_cells": 115.2,
-                              "k_centres": 237.0}
-# The FP64 pipe issues at most 304 thread-instructions per GPU clock (2 per SM; ncu's
-# sm__inst_executed_pipe_fp64 peak on this machine's GB300), i.e. 629 G/s at 2.07 GHz.
+# arithmetic each form computes in: df64 = double-float (an FP32 pair, 48-bit significand), the
+# form whose fields match the FP64 oracle within 1e-10 after the same iterations (tests)
+DTYPES = {"fp64": "f64", "fp32": "f32", "fp64-stepwise": "f64", "df64": "df64"}
+# Per-kernel figures from one ncu capture each (profiles/*.md): FP64 thread-instructions
+# (DADD + DFMA + DMUL) and flops (DFMA x 2 + DADD + DMUL) per cell, DRAM bytes per cell
+# (dram__bytes_read.sum + dram__bytes_write.sum; the capture's per-cell figure scales with the
+# cells of a launch). Each entry records the sha256 (16 hex digits) of the kernel's source files
+# at the capture; when the sources have changed since, the figures are stale and the bench
+# reports them as null (`python bench.py --source-hashes` prints the current hashes).
+KERNEL_SOURCES = {
+    **{k: ("pt_lean_kernels.cu", "pt_lean_body.cuh", "pt_lean.cuh", "df64.cuh", "pt_common.cuh")
+       for k in ("k_lean_cells", "k_lean_faces", "k_lean_picard", "k_lean_coef", "k_lean_cells_df64",
+                 "k_lean_faces_df64", "k_lean_picard_df64", "k_lean_coef_df64")},
+    "k_centres": ("pt_ref_kernels.cu", "pt_kernels.cuh", "pt_common.cuh"),
+    "k_adj_cells": ("pt_adjoint_kernels.cu", "pt_adjoint.cuh", "pt_common.cuh"),
+    "k_corr_cells": ("pt_mixed_kernels.cu", "pt_mixed.cuh", "pt_common.cuh"),
+    "k_mg_smooth_fp32": ("rx_mg_kernels.cu", "rx.cuh"),
+}
+PROFILED: dict = {}
+# The FP64 pipe's nominal issue capacity: 304 thread-instructions per GPU clock (2 per SM; ncu's
+# sm__inst_executed_pipe_fp64 peak on this machine's GB300), 629 G/s at 2.07 GHz.
 FP64_PIPE_INST_PER_CLK = 304.0
-# FP32 kernels are bound by HBM (their FP32 work is far below the FP32 pipe's rate).
-# DRAM bytes per cell and launch (dram__bytes_read.sum + dram__bytes_write.sum) from the same
-# captures; the 191^3 case's per-cell figure scales with the cells of a launch.
-KERNEL_TRAFFIC_PER_CELL = {"k_lean_cells": 311.0, "k_lean_faces": 180.6, "k_centres": 150.6,
-                           "k_adj_cells": 270.5, "k_mg_smooth_fp32": 36.4}
+CSRC = os.path.join(ROOT, "paper_2207_08716_gb300", "csrc")
 
+
+def source_hash(kernel: str) -> str | None:
+    import hashlib
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in sorted(files):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled(kernel: str) -> dict:
+    """The kernel's ncu figures if they were captured from its current sources, else {}."""
+    e = PROFILED.get(kernel)
+    if not e or e.get("src") != source_hash(kernel):
+        return {}
+    return e
 
 def parse():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--source-hashes", action="store_true",
+                    help="print the current source hash of every kernel with ncu figures and exit")
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
@@ -87,10 +116,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=191, help="sub-block edge of the CPU sample")
     ap.add_argument("--cpu-iters", type=int, default=6)
-    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="fp64",
-                    help="fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
-    ap.add_argument("--forms", default="fp32,batched", help="extra forms measured after the headline one "
-                    "(comma list of fp32, fp64-stepwise, batched; '' for none)")
+    ap.add_argument("--precision", choices=tuple(PRECISIONS), default="df64",
+                    help="df64: the FP64-lean iteration in double-float arithmetic (FP64 oracle parity 1e-10); "
+                         "fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
+    ap.add_argument("--forms", default="fp64,fp32,batched", help="extra forms measured after the headline one "
+                    "(comma list of fp64, df64, fp32, fp64-stepwise, batched; '' for none)")
+    ap.add_argument("--no-own-peaks", action="store_true",
+                    help="skip the library's own copy / FP64 / FP32 peak measurements")
     ap.add_argument("--fp32-iters", type=int, default=300, help="FP32 iterations per step of the fp32 form")
     ap.add_argument("--batch-n", type=int, default=64, help="instances of the batched form")
     ap.add_argument("--batch-iters", type=int, default=60, help="PT iterations per step of the batched form")
@@ -216,30 +248,43 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def roofline(kernels: dict, ncell: int, sm_mhz: float | None = None) -> dict:
+def roofline(kernels: dict, ncell: int, sm_mhz: float | None = None, own: dict | None = None) -> dict:
     """Roofline of the dominant kernel (largest device time) from the live per-kernel events.
-    FP64 kernels issue-bound on the FP64 pipe report FP64 thread-instructions per second
-    against the pipe's capacity (304 per clock at the SM clock measured during the run)."""
+    HBM: algorithmic bytes per launch over the launch time against the measured copy peak
+    (MEASURED_PEAKS.json; the library's own 16-byte copy kernel in `own_copy_gbs` beside it).
+    FP64 kernels issue-bound on the FP64 pipe (when their ncu counts are current) report FP64
+    thread-instructions per second against the library's own FP64 issue-rate measurement
+    (DFMA/DADD/DMUL mix) when given, else the pipe's nominal 304 per clock at the sampled clock."""
     hbm, hbm_kind = peaks()
     name, (nl, ms) = max(kernels.items(), key=lambda kv: kv[1][1])
     per_launch_s = ms / 1e3 / nl
     bytes_launch = KERNEL_BYTES_PER_CELL.get(name, 0) * ncell
-    inst_cell = KERNEL_FP64_INST_PER_CELL.get(name)
-    flops_cell = KERNEL_FP64_FLOPS_PER_CELL.get(name)
-    traffic_cell = KERNEL_TRAFFIC_PER_CELL.get(name)
+    prof = profiled(name)
+    inst_cell = prof.get("fp64_inst")
+    flops_cell = prof.get("fp64_flops")
+    traffic_cell = prof.get("traffic")
     gbs = bytes_launch / per_launch_s / 1e9
     roof = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
             "frac": gbs / hbm, "peak_source": f"{hbm_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": traffic_cell * ncell if traffic_cell else None,
-            "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": per_launch_s * 1e3}
+            "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": per_launch_s * 1e3,
+            "ncu_figures": "current" if prof else ("stale (sources changed since the capture)"
+                                                     if name in PROFILED else "none")}
+    if own and own.get("copy_gbs"):
+        roof["own_copy_gbs"] = own["copy_gbs"]
+        roof["frac_of_own_copy"] = gbs / own["copy_gbs"]
     if inst_cell:
         clk = (sm_mhz or 2070.0) * 1e6
-        peak = FP64_PIPE_INST_PER_CLK * clk / 1e9
+        nominal = FP64_PIPE_INST_PER_CLK * clk / 1e9
+        peak, src = nominal, (f"FP64 pipe nominal capacity, {FP64_PIPE_INST_PER_CLK:.0f} thread-instructions "
+                              f"per clock at the measured {clk / 1e6:.0f} MHz (ncu pipe peak)")
+        if own and own.get("fp64_ginst"):
+            peak, src = own["fp64_ginst"], ("measured FP64 issue rate, DFMA/DADD/DMUL mix "
+                                            "(pt_peak_arith, this run)")
         ginst = inst_cell * ncell / per_launch_s / 1e9
         if ginst / peak > roof["frac"]:
             roof.update(bound="alu", achieved=ginst, peak=peak, unit="G FP64 inst/s", frac=ginst / peak,
-                        peak_source=f"FP64 pipe capacity, {FP64_PIPE_INST_PER_CLK:.0f} thread-instructions "
-                                    f"per clock at the measured {clk / 1e6:.0f} MHz (ncu pipe peak)")
+                        peak_source=src, frac_of_nominal_pipe=ginst / nominal)
         roof["fp64_inst_per_cell"] = inst_cell
         if flops_cell:
             roof["fp64_tflops"] = flops_cell * ncell / per_launch_s / 1e12
@@ -247,8 +292,42 @@ def roofline(kernels: dict, ncell: int, sm_mhz: float | None = None) -> dict:
     return roof
 
 
+def measure_own_peaks(dev, copy_gib: float = 4.0) -> dict:
+    """The library's own peak measurements on this GPU: 16-byte vector copy over copy_gib GiB
+    (read + write bytes, best of 10), FP64 DFMA/DADD/DMUL mix and FP32 FMA issue rates."""
+    import ctypes as C
+    import torch
+    from paper_2207_08716_gb300 import native as N
+    lib = N.load()
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    nbytes = int(copy_gib * (1 << 30))
+    src = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dst = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    src.fill_(1)
+    ms, g = C.c_double(), C.c_double()
+    torch.cuda.synchronize(dev)
+    if lib.pt_peak_copy(src.data_ptr(), dst.data_ptr(), nbytes, 10, stream.cuda_stream, C.byref(ms), C.byref(g)) == 0:
+        out["copy_gbs"] = g.value
+        out["copy_bytes"] = nbytes
+    del src, dst
+    sink = torch.zeros(1 << 16, dtype=torch.float64, device=dev)
+    if lib.pt_peak_arith(0, sink.data_ptr(), 2000, 5, stream.cuda_stream, C.byref(ms), C.byref(g)) == 0:
+        out["fp64_ginst"] = g.value
+        out["fp64_tflops_mix"] = g.value * 4.0 / 3.0 / 1e3     # DFMA counts 2 flops, DADD and DMUL 1
+    if lib.pt_peak_arith(1, sink.data_ptr(), 100000, 5, stream.cuda_stream, C.byref(ms), C.byref(g)) == 0:
+        out["fp32_ginst"] = g.value
+        out["fp32_tflops"] = 2.0 * g.value / 1e3
+    out["how"] = ("pt_peak_copy (16-byte vector copy, best of 10), pt_peak_arith (8 independent chains per "
+                  "thread, 2048 threads per SM, best of 5)")
+    del sink
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_steps: int,
-                 dev, world: int, rank: int, local_rank: int, seed: int | None = None) -> dict:
+                 dev, world: int, rank: int, local_rank: int, seed: int | None = None,
+                 own: dict | None = None) -> dict:
     """Time `steps` physical steps (after `warmup`) of one form of the solver on this rank
     (anomaly seed = rank unless given)."""
     import torch
@@ -299,7 +378,7 @@ def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_
     out = {"precision": precision, "value": value, "unit": "GB/s", "p_bytes": pbytes,
            "ms_per_step": t / steps * 1e3, "iters_per_step": iters, "it_per_s": world * total_iters / t,
            "t_it_ms": t / total_iters * 1e3, "teff_frac_of_hbm": value / world / peaks()[0],
-           "roofline": roofline(kernels, ncell, clk.get("sm_mhz") if clk else None),
+           "roofline": roofline(kernels, ncell, clk.get("sm_mhz") if clk else None, own),
            "gpu_launches": launches, "clocks": clk,
            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kernels.items()}}
     if e2e_steps > 0:
@@ -646,7 +725,7 @@ def measure_reactive_mg(args, dev) -> dict:
         one.close()
         t_sweep = t_cyc / 50 / 1e3
         gbs = 9 * pbytes * ncell / t_sweep / 1e9
-        traffic_cell = KERNEL_TRAFFIC_PER_CELL.get(f"k_mg_smooth_{prec}")
+        traffic_cell = profiled(f"k_mg_smooth_{prec}").get("traffic")
         r["roofline"] = {"kernel": "k_mg_smooth (finest grid)", "bound": "hbm", "achieved": gbs, "peak": hbm,
                          "unit": "GB/s", "frac": gbs / hbm,
                          "traffic": traffic_cell * ncell if traffic_cell else None,
@@ -721,11 +800,12 @@ def run_native(args):
             print(json.dumps({"metric": "batched ensemble time-to-converge", **r}), flush=True)
         return 0
     head_iters = args.fp32_iters if args.precision == "fp32" else args.iters
+    own = None if args.no_own_peaks else measure_own_peaks(dev)
     seeds = [int(v) for v in args.seeds.split(",") if v.strip()] if world == 1 else [None]
     runs = []
     for m, sd in enumerate(seeds or [None]):
         r = measure_form(args, args.precision, head_iters, args.steps, args.warmup,
-                         args.e2e_steps if m == 0 else 0, dev, world, rank, local_rank, seed=sd)
+                         args.e2e_steps if m == 0 else 0, dev, world, rank, local_rank, seed=sd, own=own)
         r["seed"] = sd if sd is not None else M.replica_seed(rank)
         runs.append(r)
     head = sorted(runs, key=lambda r: r["value"])[len(runs) // 2]      # the median seed's run
@@ -737,7 +817,8 @@ def run_native(args):
             forms[f] = measure_batched(args, max(2, args.steps // 2), 1, dev, world, rank)
         elif f in PRECISIONS:
             it = args.fp32_iters if f == "fp32" else args.iters
-            forms[f] = measure_form(args, f, it, max(2, args.steps // 2), 2, 0, dev, world, rank, local_rank)
+            forms[f] = measure_form(args, f, it, max(2, args.steps // 2), 2, 0, dev, world, rank, local_rank,
+                                    own=own)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -748,7 +829,7 @@ def run_native(args):
             "metric": METRIC, "value": head["value"], "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": workload_name(args.n, head["iters_per_step"], args.precision, args.workload),
                        "n": args.n, "iters_per_step": head["iters_per_step"], "precision": args.precision,
                        "parallelism": "replicas" if world > 1 else "single",
@@ -758,7 +839,7 @@ def run_native(args):
             "seeds": {str(r["seed"]): r["value"] for r in runs}, "median_seed": head["seed"],
             "teff_frac_of_hbm": head["teff_frac_of_hbm"], "roofline": head["roofline"],
             "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
-            "clocks": head["clocks"], "kernels": head["kernels"],
+            "clocks": head["clocks"], "kernels": head["kernels"], "own_peaks": own,
             "forms": {k: ({kk: v[kk] for kk in ("value", "unit", "p_bytes", "it_per_s", "t_it_ms",
                                                   "teff_frac_of_hbm", "iters_per_step", "roofline",
                                                   "gpu_launches", "clocks")} if k != "batched" else v)
@@ -772,6 +853,9 @@ def run_native(args):
 
 def main():
     args = parse()
+    if args.source_hashes:
+        print(json.dumps({k: source_hash(k) for k in KERNEL_SOURCES}, indent=1))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

@@ -190,6 +190,20 @@ int pt_profile_end(pt_ctx *ctx, pt_kernel_time *out, int32_t max_out, int32_t *n
 /* Kernel launches issued by this context since pt_init. */
 int64_t pt_launch_count(const pt_ctx *ctx);
 
+/* ---- Measured peaks (benchmarking aids; thesis Art. 1 Eqs. 28-29 compare T_eff with a measured
+ * copy throughput) ---------------------------------------------------------------------------
+ * pt_peak_copy: dst = src over `bytes` (16-byte aligned device buffers, bytes rounded down to a
+ * multiple of 16) with 16-byte vector loads and stores, grid-stride over 8 CTAs of 256 threads per
+ * SM; best of `reps` timed launches after one warm-up; *gbs = read + write bytes / best time.
+ * pt_peak_arith: kind 0 = FP64 (DFMA, DADD, DMUL, one each per step of 8 independent chains per
+ * thread), kind 1 = FP32 FMA (8 chains); 2048 threads per SM, `steps` steps; *ginst = thread-
+ * instructions per second / 1e9 (FP32 flops = 2 x that). `sink` is device memory of at least
+ * 8 x (SM count) doubles (never written for these inputs). Both synchronise `stream`. */
+int pt_peak_copy(const void *src, void *dst, size_t bytes, int32_t reps, void *stream, double *best_ms,
+                 double *gbs);
+int pt_peak_arith(int32_t kind, void *sink, int32_t steps, int32_t reps, void *stream, double *best_ms,
+                  double *ginst);
+
 /* ---- Check of the hand-written device arithmetic (test aid; no thesis counterpart) ----------
  * Applies one device routine of the PT kernels element-wise: out[e] = f(a[e] (, b[e])), n
  * elements, device pointers, synchronises `stream`. It exists so that each replacement of a

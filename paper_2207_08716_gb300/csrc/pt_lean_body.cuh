@@ -141,21 +141,33 @@ __device__ inline df64 relax_pow(df64 x, double rel, int root) {
 // Which arrays a form stores. The FP64 form is bound by the FP64 pipe and stores everything that
 // changes less often than every iteration (1/(1-phi) and k travelling with phi, 1 - phi_o and its
 // reciprocal, edge moduli pre-multiplied by both spacings, three face pseudo-steps). Double-float
-// arithmetic is cheap and the double-float form is bound by HBM, so it recomputes 1/(1-phi),
-// k(phi) (from the porosity neighbours it loads anyway), 1 - phi_o and its reciprocal, keeps one
-// modulus per edge (em2_* hold 2 mu/(1+xi); eb_* unused) and one velocity pseudo-step per centre
-// (dtv_x = dtv_y = dtv_z hold fac / mu, averaged to each face): 72 fewer bytes per cell and
-// iteration.
+// arithmetic is cheap and the double-float form is bound by HBM and instruction issue, so it
+// recomputes 1/(1-phi), 1 - phi_o and its reciprocal, keeps one modulus per edge (em2_* hold
+// 2 mu/(1+xi); eb_* unused) and one velocity pseudo-step per centre (dtv_x = dtv_y = dtv_z hold
+// fac / mu, averaged to each face): 56 fewer bytes per cell and iteration.
 template <class T>
 struct LeanRecompute { static constexpr bool value = false; };
 template <>
 struct LeanRecompute<df64> { static constexpr bool value = true; };
+// k(phi) travels with phi (written by the cells kernel for the next iteration) in both forms:
+// recomputing it for the cell and its six neighbours costs more issue slots than its 16 bytes
+template <class T>
+struct LeanStoreK { static constexpr bool value = true; };
+
+// Where the cells body reads the arrays it needs only at its own index q ("pointwise"): straight
+// from global memory, or from a shared-memory stage that cp.async filled ahead (slot order below).
+enum { S_PTO, S_PFO, S_PHIO, S_IETA, S_IDTP, S_CM2, S_TXX, S_TYY, S_TZZ, S_EXY, S_EXZ, S_EYZ, S_TXY, S_TXZ,
+       S_TYZ, kStageSlots };
+struct DirectPoint {
+  template <class T>
+  __device__ __forceinline__ T operator()(const T* a, long long q, int) const { return a[q]; }
+};
 
 // Cells, stresses of the three lower edges, pressures, porosity at box index (i, j, k).
-template <class T>
+template <class T, class PP = DirectPoint>
 __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>& c, const LeanCellIn<T>& in,
                                                 const LeanCellOut<T>& out, int i, int j, int k, int check,
-                                                double& r_pt, double& r_pf) {
+                                                double& r_pt, double& r_pf, const PP& pp = PP()) {
   using namespace lean_detail;
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
@@ -164,30 +176,37 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     // ---- edges owned by this index: xy (i, j, k), xz (i, j, k), yz (i, j, k); stored at the end
     // with the cell's outputs, after every load (the arrays are not declared non-aliasing)
     constexpr bool RC = LeanRecompute<T>::value;
+    constexpr bool KS = LeanStoreK<T>::value;
     T t_xy = T(0), t_xz = T(0), t_yz = T(0);
     if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {   // toa_xy holds the background part too
       if constexpr (RC)
-        t_xy = fma(in.em2_xy[q], fma(in.Vy[q] - in.Vy[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - px]) * c.hrdy), in.toa_xy[q]);
+        t_xy = fma(pp(in.em2_xy, q, S_EXY), fma(in.Vy[q] - in.Vy[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - px]) * c.hrdy),
+                   pp(in.toa_xy, q, S_TXY));
       else
-        t_xy = fma(in.eb_xy[q], in.Vy[q] - in.Vy[q - 1], fma(in.em2_xy[q], in.Vx[q] - in.Vx[q - px], in.toa_xy[q]));
+        t_xy = fma(in.eb_xy[q], in.Vy[q] - in.Vy[q - 1], fma(pp(in.em2_xy, q, S_EXY), in.Vx[q] - in.Vx[q - px],
+                                                             pp(in.toa_xy, q, S_TXY)));
     } else if (k < b.nz && c.bg_on) {   // wall xy-edge under background shear (Eqs. 32-33)
-      t_xy = in.toa_xy[q];
+      t_xy = pp(in.toa_xy, q, S_TXY);
     }
     if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
       if constexpr (RC)
-        t_xz = fma(in.em2_xz[q], fma(in.Vz[q] - in.Vz[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz), in.toa_xz[q]);
+        t_xz = fma(pp(in.em2_xz, q, S_EXZ), fma(in.Vz[q] - in.Vz[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz),
+                   pp(in.toa_xz, q, S_TXZ));
       else
-        t_xz = fma(in.eb_xz[q], in.Vz[q] - in.Vz[q - 1], fma(in.em2_xz[q], in.Vx[q] - in.Vx[q - pxy], in.toa_xz[q]));
+        t_xz = fma(in.eb_xz[q], in.Vz[q] - in.Vz[q - 1], fma(pp(in.em2_xz, q, S_EXZ), in.Vx[q] - in.Vx[q - pxy],
+                                                             pp(in.toa_xz, q, S_TXZ)));
     }
     if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
       if constexpr (RC)
-        t_yz = fma(in.em2_yz[q], fma(in.Vz[q] - in.Vz[q - px], c.hrdy, (in.Vy[q] - in.Vy[q - pxy]) * c.hrdz), in.toa_yz[q]);
+        t_yz = fma(pp(in.em2_yz, q, S_EYZ), fma(in.Vz[q] - in.Vz[q - px], c.hrdy, (in.Vy[q] - in.Vy[q - pxy]) * c.hrdz),
+                   pp(in.toa_yz, q, S_TYZ));
       else
-        t_yz = fma(in.eb_yz[q], in.Vz[q] - in.Vz[q - px], fma(in.em2_yz[q], in.Vy[q] - in.Vy[q - pxy], in.toa_yz[q]));
+        t_yz = fma(in.eb_yz[q], in.Vz[q] - in.Vz[q - px], fma(pp(in.em2_yz, q, S_EYZ), in.Vy[q] - in.Vy[q - pxy],
+                                                              pp(in.toa_yz, q, S_TYZ)));
     }
     if (cell) {
-      const T Pt = in.Pt[q], Pf = in.Pf[q], Pto = in.Pto[q], Pfo = in.Pfo[q];
-      const T ph = in.phi[q], ieta = in.ieta[q];
+      const T Pt = in.Pt[q], Pf = in.Pf[q], Pto = pp(in.Pto, q, S_PTO), Pfo = pp(in.Pfo, q, S_PFO);
+      const T ph = in.phi[q], ieta = pp(in.ieta, q, S_IETA);
       // k = K0 (phi / phi0)^3 (Eq. 23) at box index e with porosity p (recomputing forms)
       auto kperm = [&](T p, long long e) {
         const T r = p * c.rphi0;
@@ -206,47 +225,47 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       const T divVn = fma(dpp, cc, fma(-c.bd_rdt_a, dPf, fma(c.bd_rdt, dPt, divV)));
       // Darcy flux through the six faces (zero on the boundary) and the largest neighbour k
       T kc;
-      if constexpr (RC) kc = kperm(ph, q);
+      if constexpr (!KS) kc = kperm(ph, q);
       else kc = in.perm[q];
       T kmax = kc, sx = T(0), sy = T(0), sz = T(0);
       if (i > 0) {
         T kn;
-        if constexpr (RC) kn = kperm(in.phi[q - 1], q - 1);
+        if constexpr (!KS) kn = kperm(in.phi[q - 1], q - 1);
         else kn = in.perm[q - 1];
         kmax = pos_max(kmax, kn);
         sx -= (kn + kc) * (Pf - in.Pf[q - 1]);
       }
       if (i < b.nx - 1) {
         T kn;
-        if constexpr (RC) kn = kperm(in.phi[q + 1], q + 1);
+        if constexpr (!KS) kn = kperm(in.phi[q + 1], q + 1);
         else kn = in.perm[q + 1];
         kmax = pos_max(kmax, kn);
         sx += (kc + kn) * (in.Pf[q + 1] - Pf);
       }
       if (j > 0) {
         T kn;
-        if constexpr (RC) kn = kperm(in.phi[q - px], q - px);
+        if constexpr (!KS) kn = kperm(in.phi[q - px], q - px);
         else kn = in.perm[q - px];
         kmax = pos_max(kmax, kn);
         sy -= (kn + kc) * (Pf - in.Pf[q - px]);
       }
       if (j < b.ny - 1) {
         T kn;
-        if constexpr (RC) kn = kperm(in.phi[q + px], q + px);
+        if constexpr (!KS) kn = kperm(in.phi[q + px], q + px);
         else kn = in.perm[q + px];
         kmax = pos_max(kmax, kn);
         sy += (kc + kn) * (in.Pf[q + px] - Pf);
       }
       if (k > 0) {
         T kn;
-        if constexpr (RC) kn = kperm(in.phi[q - pxy], q - pxy);
+        if constexpr (!KS) kn = kperm(in.phi[q - pxy], q - pxy);
         else kn = in.perm[q - pxy];
         kmax = pos_max(kmax, kn);
         sz -= (kn + kc) * ((Pf - in.Pf[q - pxy]) + c.buoy_dz);
       }
       if (k < b.nz - 1) {
         T kn;
-        if constexpr (RC) kn = kperm(in.phi[q + pxy], q + pxy);
+        if constexpr (!KS) kn = kperm(in.phi[q + pxy], q + pxy);
         else kn = in.perm[q + pxy];
         kmax = pos_max(kmax, kn);
         sz += (kc + kn) * ((in.Pf[q + pxy] - Pf) + c.buoy_dz);
@@ -256,14 +275,14 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       // local-implicit pressure updates, Eqs. 17-18: P1 = P - res / (1/dtau + d res/dP), the
       // residuals being divVn (row Pt) and resF (row Pf)
       const T resF = fma(-dpp, cc, fma(-c.bd_rdt_a, dPt, fma(c.bda_B_rdt, dPf, divqD)));
-      const T Pt1 = Pt - rcp_pseudo(in.idtp[q] + cc) * divVn;   // idtp holds 1/dtau_Pt + beta_d/dt
+      const T Pt1 = Pt - rcp_pseudo(pp(in.idtp, q, S_IDTP) + cc) * divVn;   // idtp holds 1/dtau_Pt + beta_d/dt
       const T Pf1 = Pf - rcp_pseudo(kmax * c.ifac_pf + c.bda_B_rdt + cc) * resF;
       // normal deviatoric stresses (Eq. 21): tau = tau_o xi/(1+xi) + 2 mu/(1+xi) (edot + beta_n divVn)
       const T s3 = fma(c.beta_n, divVn, -(divV * T(1.0 / 3.0)));
-      const T cm2 = in.cm2[q];
-      const T sxx = fma(cm2, gx + s3, in.toa_xx[q]);
-      const T syy = fma(cm2, gy + s3, in.toa_yy[q]);
-      const T szz = fma(cm2, gz + s3, in.toa_zz[q]);
+      const T cm2 = pp(in.cm2, q, S_CM2);
+      const T sxx = fma(cm2, gx + s3, pp(in.toa_xx, q, S_TXX));
+      const T syy = fma(cm2, gy + s3, pp(in.toa_yy, q, S_TYY));
+      const T szz = fma(cm2, gz + s3, pp(in.toa_zz, q, S_TZZ));
       // porosity in log space (Eq. 22): L = Lo + delta,
       // delta = -[beta_phi ((Pf1 - Pfo) - (Pt1 - Pto)) + dt (Pf1 - Pt1) / eta + dt V.grad(1-phi)/(1-phi)]
       // V.grad(1-phi)/(1-phi) = -(w/2) sum_d rd [v_r (phi_r - phi) + v_l (phi - phi_l)]
@@ -281,7 +300,7 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       const T delta = -(c.beta_phi * ((Pf1 - Pfo) - (Pt1 - Pto)) + c.dt * (comp + adv));
       T em_p, em_n;
       expm1_pair(delta, em_p, em_n);
-      const T phio = in.phio[q];
+      const T phio = pp(in.phio, q, S_PHIO);
       T Eo, iEo;
       if constexpr (RC) {
         Eo = T(1.0) - phio;
@@ -300,10 +319,8 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       out.tyy[q] = syy;
       out.tzz[q] = szz;
       out.phi[q] = ph1;
-      if constexpr (!RC) {
-        out.w[q] = iEo + iEo * em_n;
-        out.perm[q] = K0 * r * r * r;
-      }
+      if constexpr (!RC) out.w[q] = iEo + iEo * em_n;
+      if constexpr (KS) out.perm[q] = K0 * r * r * r;
       if (check) {
         r_pt = to_d(tabs(divVn));
         r_pf = to_d(tabs(resF));

@@ -44,6 +44,85 @@ __global__ void __launch_bounds__(256, 3) k_lean_cells(Box b, LeanCoef<T> c, Lea
   }
 }
 
+// ------------------------------------------------- cells, z-marching with staged inputs
+// The double-float cells kernel is limited by memory latency: with 80 registers a thread cannot
+// hold all of its ~30 loads in flight, so memory time and issue time add up. Here each 32 x 8
+// block marches through kLeanZChunk z-levels of its column; the 15 arrays read only at the
+// thread's own index (kStageSlots, pointwise) of level k+1 are copied into a shared-memory stage
+// by cp.async while level k computes (two stages, 61,440 B per block), so those loads take no
+// registers and overlap the arithmetic. The neighbour arrays (V, Pt, Pf, phi, k) are loaded
+// directly (z-neighbours of consecutive levels hit L1 / L2).
+constexpr int kLeanZChunk = 16;
+constexpr int kStageThreads = 256;
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <class T>
+struct StagedPoint {
+  const T* s;   // this level's stage: kStageSlots x kStageThreads values
+  int tid;
+  __device__ __forceinline__ T operator()(const T*, long long, int slot) const { return s[slot * kStageThreads + tid]; }
+};
+
+template <class T>
+__device__ __forceinline__ void stage_level(T* dst, const LeanCellIn<T>& in, long long q) {
+  cp_async8(dst + S_PTO * kStageThreads, in.Pto + q);
+  cp_async8(dst + S_PFO * kStageThreads, in.Pfo + q);
+  cp_async8(dst + S_PHIO * kStageThreads, in.phio + q);
+  cp_async8(dst + S_IETA * kStageThreads, in.ieta + q);
+  cp_async8(dst + S_IDTP * kStageThreads, in.idtp + q);
+  cp_async8(dst + S_CM2 * kStageThreads, in.cm2 + q);
+  cp_async8(dst + S_TXX * kStageThreads, in.toa_xx + q);
+  cp_async8(dst + S_TYY * kStageThreads, in.toa_yy + q);
+  cp_async8(dst + S_TZZ * kStageThreads, in.toa_zz + q);
+  cp_async8(dst + S_EXY * kStageThreads, in.em2_xy + q);
+  cp_async8(dst + S_EXZ * kStageThreads, in.em2_xz + q);
+  cp_async8(dst + S_EYZ * kStageThreads, in.em2_yz + q);
+  cp_async8(dst + S_TXY * kStageThreads, in.toa_xy + q);
+  cp_async8(dst + S_TXZ * kStageThreads, in.toa_xz + q);
+  cp_async8(dst + S_TYZ * kStageThreads, in.toa_yz + q);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kStageThreads, 3) k_lean_cells_zmarch(Box b, LeanCoef<T> c, LeanCellIn<T> in,
+                                                                       LeanCellOut<T> out,
+                                                                       unsigned long long* red, int check) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* stage = reinterpret_cast<T*>(smem_raw);   // [2][kStageSlots][kStageThreads]
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * kLeanZChunk;
+  const int k1 = min(k0 + kLeanZChunk, b.nz + 1);   // levels [k0, k1), all inside the box
+  const bool active = i <= b.nx && j <= b.ny;      // the body's own index range
+  constexpr int stage_elems = kStageSlots * kStageThreads;
+  if (active) stage_level(stage + tid, in, cidx(b, i, j, k0));
+  cp_async_commit();
+  unsigned long long m_pt = 0ull, m_pf = 0ull;     // norms as bit patterns: a NaN stays the largest
+  for (int k = k0; k < k1; ++k) {
+    const int buf = (k - k0) & 1;
+    if (active && k + 1 < k1) stage_level(stage + (buf ^ 1) * stage_elems + tid, in, cidx(b, i, j, k + 1));
+    cp_async_commit();
+    cp_async_wait_1();                              // this level's copies have landed
+    double r_pt = 0.0, r_pf = 0.0;
+    lean_cell_point(b, c, in, out, i, j, k, check, r_pt, r_pf, StagedPoint<T>{stage + buf * stage_elems, tid});
+    const unsigned long long a = (unsigned long long)__double_as_longlong(r_pt);
+    const unsigned long long d = (unsigned long long)__double_as_longlong(r_pf);
+    m_pt = a > m_pt ? a : m_pt;
+    m_pf = d > m_pf ? d : m_pf;
+    __syncthreads();                                // every read of this stage precedes its refill
+  }
+  if (check) {
+    block_max_atomic(__longlong_as_double((long long)m_pt), red + RED_PT);
+    block_max_atomic(__longlong_as_double((long long)m_pf), red + RED_PF);
+  }
+}
+
 // ------------------------------------------------------------------------------ faces
 template <class T>
 __global__ void __launch_bounds__(256) k_lean_faces(Box b, LeanCoef<T> c, LeanFaceIn<T> in,
@@ -105,6 +184,8 @@ __global__ void __launch_bounds__(256) k_lean_begin(Box b, LeanCoef<T> c, LeanBe
       out.Eo[q] = Eo;
       out.iEo[q] = iEo;
       out.w[q] = iEo;
+    }
+    if constexpr (LeanStoreK<T>::value) {
       const T r = ph * c.rphi0;
       out.perm[q] = (in.K0 ? in.K0[q] : c.k0) * r * r * r;
     }
@@ -193,6 +274,15 @@ void lean_cells(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, 
                 const LeanCellOut<T>& out, unsigned long long* red, int check) {
   k_lean_cells<T><<<gr, bl, 0, st>>>(b, c, in, out, red, check);
 }
+// The double-float form's cells launch: the z-marching staged kernel (the block shape stays 32 x 8).
+template <>
+void lean_cells<df64>(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<df64>& c, const LeanCellIn<df64>& in,
+                      const LeanCellOut<df64>& out, unsigned long long* red, int check) {
+  const int smem = 2 * kStageSlots * kStageThreads * (int)sizeof(df64);
+  cudaFuncSetAttribute(k_lean_cells_zmarch<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const dim3 g(gr.x, gr.y, (unsigned)((b.nz + 1 + kLeanZChunk - 1) / kLeanZChunk));
+  k_lean_cells_zmarch<df64><<<g, dim3(32, 8, 1), smem, st>>>(b, c, in, out, red, check);
+}
 template <class T>
 void lean_faces(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, const LeanFaceIn<T>& in,
                 T* Vx, T* Vy, T* Vz, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check) {
@@ -230,8 +320,6 @@ template void lean_begin<double>(dim3, dim3, cudaStream_t, Box, const LeanCoef<d
                                  const LeanBeginOut<double>&, unsigned long long*);
 template void lean_k0<double>(dim3, dim3, cudaStream_t, Box, double, const double*, double*);
 
-template void lean_cells<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanCellIn<df64>&,
-                                 const LeanCellOut<df64>&, unsigned long long*, int);
 template void lean_faces<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanFaceIn<df64>&,
                                  df64*, df64*, df64*, df64*, df64*, df64*, unsigned long long*, int);
 template void lean_picard<df64>(dim3, dim3, cudaStream_t, Box, const LeanCoef<df64>&, const LeanPicardIn<df64>&,

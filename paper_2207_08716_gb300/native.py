@@ -17,7 +17,7 @@ _INC = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
 SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu",
-           "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu",
+           "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu", "pt_peaks.cu",
            "rx_api.cu", "rx_kernels.cu", "rx_mg_kernels.cu")
 HEADERS = ("pt_common.cuh", "pt_host.h", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "df64.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -173,6 +173,10 @@ SIGNATURES = {
     "pt_profile_begin": (C.c_int, [C.c_void_p]),
     "pt_profile_end": (C.c_int, [C.c_void_p, C.POINTER(KernelTime), C.c_int32, C.POINTER(C.c_int32)]),
     "pt_launch_count": (C.c_int64, [C.c_void_p]),
+    "pt_peak_copy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32, C.c_void_p,
+                               C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pt_peak_arith": (C.c_int, [C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pt_math_check": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "pt_residual_static": (C.c_int, [C.POINTER(Grid), C.POINTER(Phys), C.POINTER(Num), C.POINTER(Fields),
                                      C.POINTER(OldFields), C.c_double, C.c_void_p, C.POINTER(Report)]),
