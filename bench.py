@@ -73,7 +73,13 @@ KERNEL_SOURCES = {
     "k_corr_cells": ("pt_mixed_kernels.cu", "pt_mixed.cuh", "pt_common.cuh"),
     "k_mg_smooth_fp32": ("rx_mg_kernels.cu", "rx.cuh"),
 }
-PROFILED: dict = {}
+PROFILED = {
+    # profiles/kernels_191_ncu_metrics.md (191^3, every launch of one step of each form)
+    "k_lean_cells": {"src": "847b74c5871329ee", "fp64_inst": 100.2, "fp64_flops": 148.4, "traffic": 310.9},
+    "k_lean_faces": {"src": "847b74c5871329ee", "fp64_inst": 33.1, "fp64_flops": 50.0, "traffic": 180.3},
+    "k_lean_cells_df64": {"src": "847b74c5871329ee", "traffic": 260.0, "thread_inst": 1929.0},
+    "k_lean_faces_df64": {"src": "847b74c5871329ee", "traffic": 164.3, "thread_inst": 724.9},
+}
 # The FP64 pipe's nominal issue capacity: 304 thread-instructions per GPU clock (2 per SM; ncu's
 # sm__inst_executed_pipe_fp64 peak on this machine's GB300), 629 G/s at 2.07 GHz.
 FP64_PIPE_INST_PER_CLK = 304.0

@@ -157,7 +157,9 @@ struct LeanStoreK { static constexpr bool value = true; };
 // Where the cells body reads the arrays it needs only at its own index q ("pointwise"): straight
 // from global memory, or from a shared-memory stage that cp.async filled ahead (slot order below).
 enum { S_PTO, S_PFO, S_PHIO, S_IETA, S_IDTP, S_CM2, S_TXX, S_TYY, S_TZZ, S_EXY, S_EXZ, S_EYZ, S_TXY, S_TXZ,
-       S_TYZ, kStageSlots };
+       S_TYZ, kStageSlots,
+       // own-index values of the neighbour arrays (staged too when the whole level is staged)
+       S_VX = kStageSlots, S_VY, S_VZ, S_PT, S_PF, S_PHI, S_K, kStageSlotsAll };
 struct DirectPoint {
   template <class T>
   __device__ __forceinline__ T operator()(const T* a, long long q, int) const { return a[q]; }
@@ -180,7 +182,8 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     T t_xy = T(0), t_xz = T(0), t_yz = T(0);
     if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {   // toa_xy holds the background part too
       if constexpr (RC)
-        t_xy = fma(pp(in.em2_xy, q, S_EXY), fma(in.Vy[q] - in.Vy[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - px]) * c.hrdy),
+        t_xy = fma(pp(in.em2_xy, q, S_EXY), fma(pp(in.Vy, q, S_VY) - in.Vy[q - 1], c.hrdx,
+                                                (pp(in.Vx, q, S_VX) - in.Vx[q - px]) * c.hrdy),
                    pp(in.toa_xy, q, S_TXY));
       else
         t_xy = fma(in.eb_xy[q], in.Vy[q] - in.Vy[q - 1], fma(pp(in.em2_xy, q, S_EXY), in.Vx[q] - in.Vx[q - px],
@@ -190,7 +193,8 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     }
     if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
       if constexpr (RC)
-        t_xz = fma(pp(in.em2_xz, q, S_EXZ), fma(in.Vz[q] - in.Vz[q - 1], c.hrdx, (in.Vx[q] - in.Vx[q - pxy]) * c.hrdz),
+        t_xz = fma(pp(in.em2_xz, q, S_EXZ), fma(pp(in.Vz, q, S_VZ) - in.Vz[q - 1], c.hrdx,
+                                                (pp(in.Vx, q, S_VX) - in.Vx[q - pxy]) * c.hrdz),
                    pp(in.toa_xz, q, S_TXZ));
       else
         t_xz = fma(in.eb_xz[q], in.Vz[q] - in.Vz[q - 1], fma(pp(in.em2_xz, q, S_EXZ), in.Vx[q] - in.Vx[q - pxy],
@@ -198,15 +202,16 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
     }
     if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
       if constexpr (RC)
-        t_yz = fma(pp(in.em2_yz, q, S_EYZ), fma(in.Vz[q] - in.Vz[q - px], c.hrdy, (in.Vy[q] - in.Vy[q - pxy]) * c.hrdz),
+        t_yz = fma(pp(in.em2_yz, q, S_EYZ), fma(pp(in.Vz, q, S_VZ) - in.Vz[q - px], c.hrdy,
+                                                (pp(in.Vy, q, S_VY) - in.Vy[q - pxy]) * c.hrdz),
                    pp(in.toa_yz, q, S_TYZ));
       else
         t_yz = fma(in.eb_yz[q], in.Vz[q] - in.Vz[q - px], fma(pp(in.em2_yz, q, S_EYZ), in.Vy[q] - in.Vy[q - pxy],
                                                               pp(in.toa_yz, q, S_TYZ)));
     }
     if (cell) {
-      const T Pt = in.Pt[q], Pf = in.Pf[q], Pto = pp(in.Pto, q, S_PTO), Pfo = pp(in.Pfo, q, S_PFO);
-      const T ph = in.phi[q], ieta = pp(in.ieta, q, S_IETA);
+      const T Pt = pp(in.Pt, q, S_PT), Pf = pp(in.Pf, q, S_PF), Pto = pp(in.Pto, q, S_PTO), Pfo = pp(in.Pfo, q, S_PFO);
+      const T ph = pp(in.phi, q, S_PHI), ieta = pp(in.ieta, q, S_IETA);
       // k = K0 (phi / phi0)^3 (Eq. 23) at box index e with porosity p (recomputing forms)
       auto kperm = [&](T p, long long e) {
         const T r = p * c.rphi0;
@@ -215,8 +220,8 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       T w;
       if constexpr (RC) w = rcp_full(T(1.0) - ph);
       else w = in.w[q];
-      const T vxl = in.Vx[q], vxr = in.Vx[q + 1], vyl = in.Vy[q], vyr = in.Vy[q + px];
-      const T vzl = in.Vz[q], vzr = in.Vz[q + pxy];
+      const T vxl = pp(in.Vx, q, S_VX), vxr = in.Vx[q + 1], vyl = pp(in.Vy, q, S_VY), vyr = in.Vy[q + px];
+      const T vzl = pp(in.Vz, q, S_VZ), vzr = in.Vz[q + pxy];
       const T gx = (vxr - vxl) * c.rdx, gy = (vyr - vyl) * c.rdy, gz = (vzr - vzl) * c.rdz;
       const T divV = gx + gy + gz;
       const T cc = c.compaction_on ? ieta * w : T(0);
@@ -226,7 +231,7 @@ __device__ __forceinline__ void lean_cell_point(const Box& b, const LeanCoef<T>&
       // Darcy flux through the six faces (zero on the boundary) and the largest neighbour k
       T kc;
       if constexpr (!KS) kc = kperm(ph, q);
-      else kc = in.perm[q];
+      else kc = pp(in.perm, q, S_K);
       T kmax = kc, sx = T(0), sy = T(0), sz = T(0);
       if (i > 0) {
         T kn;

@@ -54,6 +54,12 @@ __global__ void __launch_bounds__(256, 3) k_lean_cells(Box b, LeanCoef<T> c, Lea
 // directly (z-neighbours of consecutive levels hit L1 / L2).
 constexpr int kLeanZChunk = 16;
 constexpr int kStageThreads = 256;
+// stage the own-index values of the neighbour arrays too (22 slots, 102 registers, 2 blocks per
+// SM: 10.4 ms per 511^3 launch) or only the pointwise arrays (15 slots, 80 registers, 3 blocks
+// per SM: 9.9 ms)
+constexpr bool kStageAll = false;
+constexpr int kSlots = kStageAll ? (int)kStageSlotsAll : (int)kStageSlots;
+constexpr int kZmarchBlocks = kStageAll ? 2 : 3;
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
@@ -62,11 +68,15 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Reads a staged slot from this level's stage (kSlots x kStageThreads values); slots outside the
+// staged set are read from global memory (the stage holds nothing for them).
 template <class T>
 struct StagedPoint {
-  const T* s;   // this level's stage: kStageSlots x kStageThreads values
+  const T* s;
   int tid;
-  __device__ __forceinline__ T operator()(const T*, long long, int slot) const { return s[slot * kStageThreads + tid]; }
+  __device__ __forceinline__ T operator()(const T* a, long long q, int slot) const {
+    return slot < kSlots ? s[slot * kStageThreads + tid] : a[q];
+  }
 };
 
 template <class T>
@@ -86,21 +96,30 @@ __device__ __forceinline__ void stage_level(T* dst, const LeanCellIn<T>& in, lon
   cp_async8(dst + S_TXY * kStageThreads, in.toa_xy + q);
   cp_async8(dst + S_TXZ * kStageThreads, in.toa_xz + q);
   cp_async8(dst + S_TYZ * kStageThreads, in.toa_yz + q);
+  if constexpr (kStageAll) {
+    cp_async8(dst + S_VX * kStageThreads, in.Vx + q);
+    cp_async8(dst + S_VY * kStageThreads, in.Vy + q);
+    cp_async8(dst + S_VZ * kStageThreads, in.Vz + q);
+    cp_async8(dst + S_PT * kStageThreads, in.Pt + q);
+    cp_async8(dst + S_PF * kStageThreads, in.Pf + q);
+    cp_async8(dst + S_PHI * kStageThreads, in.phi + q);
+    cp_async8(dst + S_K * kStageThreads, in.perm + q);
+  }
 }
 
 template <class T>
-__global__ void __launch_bounds__(kStageThreads, 3) k_lean_cells_zmarch(Box b, LeanCoef<T> c, LeanCellIn<T> in,
+__global__ void __launch_bounds__(kStageThreads, kZmarchBlocks) k_lean_cells_zmarch(Box b, LeanCoef<T> c, LeanCellIn<T> in,
                                                                        LeanCellOut<T> out,
                                                                        unsigned long long* red, int check) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* stage = reinterpret_cast<T*>(smem_raw);   // [2][kStageSlots][kStageThreads]
+  T* stage = reinterpret_cast<T*>(smem_raw);   // [2][kSlots][kStageThreads]
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k0 = blockIdx.z * kLeanZChunk;
   const int k1 = min(k0 + kLeanZChunk, b.nz + 1);   // levels [k0, k1), all inside the box
   const bool active = i <= b.nx && j <= b.ny;      // the body's own index range
-  constexpr int stage_elems = kStageSlots * kStageThreads;
+  constexpr int stage_elems = kSlots * kStageThreads;
   if (active) stage_level(stage + tid, in, cidx(b, i, j, k0));
   cp_async_commit();
   unsigned long long m_pt = 0ull, m_pf = 0ull;     // norms as bit patterns: a NaN stays the largest
@@ -278,7 +297,7 @@ void lean_cells(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<T>& c, 
 template <>
 void lean_cells<df64>(dim3 gr, dim3 bl, cudaStream_t st, Box b, const LeanCoef<df64>& c, const LeanCellIn<df64>& in,
                       const LeanCellOut<df64>& out, unsigned long long* red, int check) {
-  const int smem = 2 * kStageSlots * kStageThreads * (int)sizeof(df64);
+  const int smem = 2 * kSlots * kStageThreads * (int)sizeof(df64);
   cudaFuncSetAttribute(k_lean_cells_zmarch<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const dim3 g(gr.x, gr.y, (unsigned)((b.nz + 1 + kLeanZChunk - 1) / kLeanZChunk));
   k_lean_cells_zmarch<df64><<<g, dim3(32, 8, 1), smem, st>>>(b, c, in, out, red, check);
