@@ -122,6 +122,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=191, help="sub-block edge of the CPU sample")
     ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--cpu-timings", action="store_true",
+                    help="time the oracle at 127^3 and 511^3 (PT iterations) and one full c1 step, on all host "
+                         "cores and on one core, each in its own process, and exit")
+    ap.add_argument("--cpu-timing-iters", type=int, default=20)
     ap.add_argument("--precision", choices=tuple(PRECISIONS), default="df64",
                     help="df64: the FP64-lean iteration in double-float arithmetic (FP64 oracle parity 1e-10); "
                          "fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
@@ -226,6 +230,53 @@ def cpu_sample(n_sub: int, iters: int) -> dict:
             "sample": (f"{n_sub}^3-cell block of the 511^3 workload (same spacing, parameters and "
                        f"anomaly width), {iters} PT iterations of the first step, FP64 C oracle "
                        f"with OpenMP; T_eff with A_eff = 25 N 8 B over the block")}
+
+
+def _cpu_job(kind: str, n: int, iters: int, warm: int) -> dict:
+    """One oracle timing in this process (its OpenMP thread count set by the caller's
+    OMP_NUM_THREADS): `iters` PT iterations after `warm` warm-up ones of the first step of the n^3
+    benchmark workload (kind "iter"), or one full step of the 32^3 c1 workload to its tolerance
+    (kind "c1")."""
+    import oracle as O
+    if kind == "c1":
+        p = I.c1_params(32)
+        st = O.make_state(p, I.gaussian_porosity(p))
+        t0 = time.perf_counter()
+        rc, it, _ = O.step(st)
+        dt = time.perf_counter() - t0
+        return {"kind": "c1 step to tol 1e-8", "n": 32, "rc": rc, "iters": it, "seconds": dt,
+                "t_it_s": dt / max(it, 1), "cores": O.max_threads()}
+    p = workload_params(n, iters)
+    st = O.make_state(p, I.gaussian_porosity(p, centres=(I.perturbed_centre(0),)))
+    O.begin_step(st)
+    O.iterate_n(st, 0, warm)
+    t0 = time.perf_counter()
+    rc, _ = O.iterate_n(st, warm, iters)
+    dt = time.perf_counter() - t0
+    return {"kind": "PT iterations", "n": n, "rc": rc, "iters": iters, "seconds": dt, "t_it_s": dt / iters,
+            "t_eff_gbs": M.t_eff_gbs(n ** 3, 8, dt / iters), "cores": O.max_threads()}
+
+
+def cpu_timings(args) -> dict:
+    """The oracle timed as the measurement plan asks, each case in a fresh process with its
+    thread count: t_it over 20 PT iterations (after 2 warm-up) at 127^3 and 511^3, with all
+    host cores and with one; one full c1 step (32^3 to tol) likewise. A baseline, not a target."""
+    import subprocess
+    out = []
+    ncores = os.cpu_count() or 1
+    cases = [("iter", 127), ("iter", 511), ("c1", 32)]
+    for kind, n in cases:
+        for threads in (ncores, 1):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            code = (f"import json, bench; print('CPUJOB ' + json.dumps(bench._cpu_job({kind!r}, {n}, "
+                    f"{args.cpu_timing_iters}, 2)))")
+            r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+            line = [l for l in r.stdout.splitlines() if l.startswith("CPUJOB ")]
+            rec = json.loads(line[-1][7:]) if line else {"error": (r.stderr or "")[-300:]}
+            rec["threads_requested"] = threads
+            out.append(rec)
+            print(json.dumps(rec), flush=True)
+    return {"host_cores": ncores, "cases": out}
 
 
 def run_reference(args):
@@ -861,6 +912,10 @@ def main():
     args = parse()
     if args.source_hashes:
         print(json.dumps({k: source_hash(k) for k in KERNEL_SOURCES}, indent=1))
+        return 0
+    if args.cpu_timings:
+        print(json.dumps({"metric": "oracle t_it and T_eff on the host cores (baseline)", **cpu_timings(args)}),
+              flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args)
