@@ -41,10 +41,9 @@ KERNEL_BYTES_PER_CELL = {
     # 6 stresses); faces reads 17 (6 stresses, Pt, phi, 3 dtv, 3 R, 3 V) and writes 6 (3 R, 3 V)
     "k_lean_cells": 39 * 8, "k_lean_faces": 23 * 8, "k_lean_picard": 11 * 8, "k_lean_coef": 23 * 8,
     "k_lean_begin": 11 * 8,
-    # mixed precision, FP32 correction iterations: cells reads 17 arrays (3 dV, dPt, dPf, cc, k,
-    # idtp, iden_pt, idtf, iden_pf, r_pt, r_pf, cm2, 3 em2) and writes 8 (dPt, dPf, 6 stresses);
-    # faces reads 19 (6 stresses, dPt, 3 dtv, 3 r_F, 3 R, 3 dV) and writes 6 (3 R, 3 dV)
-    "k_corr_cells": 25 * 4, "k_corr_faces": 25 * 4,
+    # mixed precision, one fused FP32 correction iteration: reads 18 arrays (3 dV, dPt, dPf, cc, k,
+    # 1/dtau_Pt, r_Pt, r_Pf, mu, centre dtau_V, 3 r_F, 3 R) and writes 8 (3 dV', dPt', dPf', 3 R)
+    "k_corr_iteration": 26 * 4,
     # adjoint PT iteration: cells reads 26 arrays and writes 10, faces reads 17 and writes 6
     "k_adj_cells": 36 * 8, "k_adj_faces": 23 * 8,
     # double-float form (8 B per value): cells reads 22 arrays (V, Pt, Pf, phi, k, Pto, Pfo, phio,
@@ -70,7 +69,7 @@ KERNEL_SOURCES = {
                  "k_lean_faces_df64", "k_lean_picard_df64", "k_lean_coef_df64")},
     "k_centres": ("pt_ref_kernels.cu", "pt_kernels.cuh", "pt_common.cuh"),
     "k_adj_cells": ("pt_adjoint_kernels.cu", "pt_adjoint.cuh", "pt_common.cuh"),
-    "k_corr_cells": ("pt_mixed_kernels.cu", "pt_mixed.cuh", "pt_common.cuh"),
+    "k_corr_iteration": ("pt_mixed_kernels.cu", "pt_mixed.cuh", "pt_common.cuh"),
     "k_mg_smooth_fp32": ("rx_mg_kernels.cu", "rx.cuh"),
 }
 PROFILED = {

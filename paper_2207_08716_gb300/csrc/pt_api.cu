@@ -34,7 +34,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kRefArrays = 23;   // step-by-step path
 constexpr int kLeanArrays = 26;  // extra arrays of the FP64-lean path
-constexpr int kMixArrays = 34;   // FP32 arrays of the mixed-precision path
+constexpr int kMixArrays = 23;   // FP32 arrays of the mixed-precision path
 constexpr int kDfArrays = 28;    // double-float iterate, stresses, residuals, old fields (PT_DF64)
 // Default relative drop at which the inner FP32 solves of the mixed-precision path stop. The
 // outer loop's convergence is bound by the log-space Picard relaxation of mu and eta (one
@@ -86,10 +86,8 @@ struct pt_ctx {
   bool mixed;
   double mix_omega;         // PT_FP32: weight of the outer update u <- u + omega delta
   double mix_prev;          // PT_FP32: the previous outer residual max (0 at a step's start)
-  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_iden_pt, *m_idtf, *m_iden_pf;
-  float *m_cm2, *m_em2_xy, *m_em2_xz, *m_em2_yz;
-  float *m_dVx, *m_dVy, *m_dVz, *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
-  float *m_txx, *m_tyy, *m_tzz, *m_txy, *m_txz, *m_tyz, *m_dtv_x, *m_dtv_y, *m_dtv_z;
+  float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_mu, *m_dtvc;
+  float *m_dVx[2], *m_dVy[2], *m_dVz[2], *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
   CorrCoef<float> ccoef;
   // adjoint recording (pt_adjoint_forward / pt_adjoint)
   char* adj_ws;
@@ -115,7 +113,7 @@ namespace {
 
 enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEGIN, K_INIT_VISC,
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
-                K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_CELLS, K_CORR_FACES,
+                K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_ITER,
                 K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_DF_CELLS, K_DF_FACES,
                 K_DF_PICARD, K_DF_COEF, K_DF_BEGIN, K_DF_K0, K_DF_CONVERT, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
@@ -123,7 +121,7 @@ const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
                                            "k_lean_picard", "k_lean_coef", "k_lean_begin", "k_lean_k0",
                                            "k_mix_prepare", "k_mix_res_faces", "k_mix_coef",
-                                           "k_corr_cells", "k_corr_faces", "k_mix_update",
+                                           "k_corr_iteration", "k_mix_update",
                                            "k_adj_prep", "k_adj_cells", "k_adj_faces", "k_adj_carry",
                                            "k_lean_cells_df64", "k_lean_faces_df64", "k_lean_picard_df64",
                                            "k_lean_coef_df64", "k_lean_begin_df64", "k_lean_k0_df64",
@@ -269,6 +267,8 @@ void fill_corr_coef(pt_ctx* c) {
   f.beta_n = (float)k.beta_n;
   f.rrho_i = (float)k.rrho_i;
   f.damp_x = (float)k.damp_x; f.damp_y = (float)k.damp_y; f.damp_z = (float)k.damp_z;
+  f.rG = (float)k.rGdtS;
+  f.ifac_pf = (float)(1.0 / k.dtaupf_fac);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
@@ -501,8 +501,7 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   PT_LAUNCH(c, K_PERM, k_perm<<<gr, bl, 0, c->stream>>>(b, k, c->phi[a], c->logk, c->perm, c->rog));
   MixPrepIn pin{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->mu, c->eta, c->perm, c->Pto,
                 c->Pfo, c->txxo, c->tyyo, c->tzzo};
-  MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_idtp,
-                  c->m_iden_pt, c->m_idtf, c->m_iden_pf};
+  MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_idtp};
   PT_LAUNCH(c, K_MIX_PREP, mix_prepare(gr, bl, c->stream, b, k, pin, pout, c->red));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
@@ -533,26 +532,23 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   }
   const double target = (c->num.inner_rtol > 0 ? c->num.inner_rtol : kInnerRtol) * report_max(outer);
   // (iii) FP32 PT on the correction, from delta = 0, R = 0
-  MixCoefOut mco{c->m_cm2, c->m_em2_xy, c->m_em2_xz, c->m_em2_yz, c->m_dtv_x, c->m_dtv_y, c->m_dtv_z};
+  MixCoefOut mco{c->m_mu, c->m_dtvc};
   PT_LAUNCH(c, K_MIX_COEF, mix_coef(gr, bl, c->stream, b, k, c->mu, mco));
   const size_t fb = (size_t)b.n * sizeof(float);
-  float* zero[] = {c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[0], c->m_dPf[0], c->m_Rx, c->m_Ry, c->m_Rz};
+  // both correction-velocity buffers: the wall faces, never written by the iteration, stay zero
+  float* zero[] = {c->m_dVx[0], c->m_dVy[0], c->m_dVz[0], c->m_dVx[1], c->m_dVy[1], c->m_dVz[1],
+                   c->m_dPt[0], c->m_dPf[0], c->m_Rx, c->m_Ry, c->m_Rz};
   for (float* z : zero) cudaMemsetAsync(z, 0, fb, c->stream);
   int d = 0;
   const int nup = c->num.nup;
   for (int it = 1; it <= n_in; ++it) {
     const int check = early_exit && (it % nup) == 0;
     if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
-    const CorrIn<float> ci{c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d], c->m_cc, c->m_perm,
-                           c->m_idtp, c->m_iden_pt, c->m_idtf, c->m_iden_pf, c->m_rpt, c->m_rpf, c->m_cm2,
-                           c->m_em2_xy, c->m_em2_xz, c->m_em2_yz};
-    const CorrCellOut<float> co{c->m_dPt[1 - d], c->m_dPf[1 - d], c->m_txx, c->m_tyy, c->m_tzz,
-                                c->m_txy, c->m_txz, c->m_tyz};
-    PT_LAUNCH(c, K_CORR_CELLS, corr_cells<float>(gr, bl, c->stream, b, c->ccoef, ci, co, c->red, check));
-    const CorrFaceIn<float> fi{c->m_txx, c->m_tyy, c->m_tzz, c->m_txy, c->m_txz, c->m_tyz, c->m_dPt[1 - d],
-                               c->m_dtv_x, c->m_dtv_y, c->m_dtv_z, c->m_rfx, c->m_rfy, c->m_rfz};
-    PT_LAUNCH(c, K_CORR_FACES, corr_faces<float>(gr, bl, c->stream, b, c->ccoef, fi, c->m_dVx, c->m_dVy,
-                                                 c->m_dVz, c->m_Rx, c->m_Ry, c->m_Rz, c->red, check));
+    const CorrIn<float> ci{c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d], c->m_dPf[d], c->m_cc, c->m_perm,
+                           c->m_idtp, c->m_rpt, c->m_rpf, c->m_mu, c->m_dtvc, c->m_rfx, c->m_rfy, c->m_rfz};
+    const CorrOut<float> co{c->m_dVx[1 - d], c->m_dVy[1 - d], c->m_dVz[1 - d], c->m_dPt[1 - d], c->m_dPf[1 - d],
+                            c->m_Rx, c->m_Ry, c->m_Rz};
+    PT_LAUNCH(c, K_CORR_ITER, corr_iteration(c->stream, b, c->ccoef, ci, co, c->red, check));
     d = 1 - d;
     *inner_done = it;
     if (check) {
@@ -563,7 +559,7 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
     }
   }
   // (iv) u <- u + delta in FP64, then the FP64 porosity time integration (Eq. 22, log space)
-  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx, c->m_dVy, c->m_dVz, c->m_dPt[d], c->m_dPf[d],
+  MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d], c->m_dPf[d],
                c->mix_omega};
   PT_LAUNCH(c, K_MIX_UPDATE, mix_update(gr, bl, c->stream, b, mu));
   PT_LAUNCH(c, K_POROSITY,
@@ -684,6 +680,8 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
       num->precision != PT_DF64)
     return PT_EINVAL;
   if (!phys_ok(phys)) return PT_EINVAL;
+  // the fused FP32 correction iteration indexes the box with 32-bit integers
+  if (num->precision == PT_FP32 && make_box(grid).n >= (1LL << 31)) return PT_EINVAL;
   double* const ptrs[] = {f->Vx, f->Vy, f->Vz, f->Pt, f->Pf, f->phi, f->txx, f->tyy,
                           f->tzz, f->txy, f->txz, f->tyz, f->mu, f->eta};
   for (double* p : ptrs)
@@ -738,10 +736,9 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   if (c->mixed) {
     const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
     float** fslots[kMixArrays] = {
-        &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_idtp,
-        &c->m_iden_pt, &c->m_idtf, &c->m_iden_pf, &c->m_cm2, &c->m_em2_xy, &c->m_em2_xz, &c->m_em2_yz, &c->m_dVx, &c->m_dVy, &c->m_dVz, &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0],
-        &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz, &c->m_txx, &c->m_tyy, &c->m_tzz, &c->m_txy, &c->m_txz,
-        &c->m_tyz, &c->m_dtv_x, &c->m_dtv_y, &c->m_dtv_z};
+        &c->m_rpt, &c->m_rpf, &c->m_rfx, &c->m_rfy, &c->m_rfz, &c->m_cc, &c->m_perm, &c->m_idtp, &c->m_mu,
+        &c->m_dtvc, &c->m_dVx[0], &c->m_dVx[1], &c->m_dVy[0], &c->m_dVy[1], &c->m_dVz[0], &c->m_dVz[1],
+        &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0], &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz};
     for (int s = 0; s < kMixArrays; ++s) *fslots[s] = (float*)(wend + s * fstride);
     wend += kMixArrays * fstride;
   }

@@ -11,14 +11,14 @@ struct MixPrepIn {
 };
 struct MixPrepOut {
   double *txx, *tyy, *tzz;                                  // FP64 stresses at u
-  float *r_pt, *r_pf, *cc, *perm, *idtp, *iden_pt, *idtf, *iden_pf;
+  float *r_pt, *r_pf, *cc, *perm, *idtp;
 };
 struct MixFaceIn {
   const double *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt, *phi;
 };
 struct MixCoefOut {
-  float *cm2, *em2_xy, *em2_xz, *em2_yz;                    // 2 mu / (1 + xi) at centres and edges
-  float *dtv_x, *dtv_y, *dtv_z;                             // velocity pseudo-steps at faces
+  float *mu;                                                // mu at centres (FP32)
+  float *dtvc;                                              // velocity pseudo-step fac / mu at centres
 };
 struct MixUpdate {
   double *Vx, *Vy, *Vz, *Pt, *Pf;
@@ -30,20 +30,20 @@ template <class T>
 struct CorrCoef {
   T rdx, rdy, rdz, hrdx, hrdy, hrdz, hrdx2, hrdy2, hrdz2;
   T bd_rdt, bd_rdt_a, bda_B_rdt, beta_n, rrho_i, damp_x, damp_y, damp_z;
+  T rG;         // 1 / (G dtS): xi = mu rG
+  T ifac_pf;    // 1 / dtau_Pf = kmax ifac_pf
 };
-// FP32 PT iteration on the correction: current correction and frozen coefficients.
+// One FP32 PT iteration on the correction, in one pass: the current correction (dV, dPt, dPf),
+// the frozen coefficients and right-hand sides, and where the next correction goes.
 template <class T>
 struct CorrIn {
   const T *Vx, *Vy, *Vz, *Pt, *Pf;                 // current correction dV, dPt, dPf
-  const T *cc, *perm, *idtp, *iden_pt, *idtf, *iden_pf, *r_pt, *r_pf, *cm2, *em2_xy, *em2_xz, *em2_yz;
+  const T *cc, *perm, *idtp, *r_pt, *r_pf, *mu, *dtvc, *rfx, *rfy, *rfz;
 };
 template <class T>
-struct CorrCellOut {
-  T *Pt, *Pf, *txx, *tyy, *tzz, *txy, *txz, *tyz;  // next dPt, dPf; stresses of the correction
-};
-template <class T>
-struct CorrFaceIn {
-  const T *txx, *tyy, *tzz, *txy, *txz, *tyz, *Pt1, *dtv_x, *dtv_y, *dtv_z, *rfx, *rfy, *rfz;
+struct CorrOut {
+  T *Vx, *Vy, *Vz, *Pt, *Pf;                       // next dV, dPt, dPf (other buffers)
+  T *Rx, *Ry, *Rz;                                 // damped residuals (in place)
 };
 
 void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPrepIn& in,
@@ -52,11 +52,8 @@ void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const 
                    float* rfy, float* rfz, unsigned long long* red);
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out);
 void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u);
-template <class T>
-void corr_cells(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrIn<T>& in,
-                const CorrCellOut<T>& out, unsigned long long* red, int check);
-template <class T>
-void corr_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrFaceIn<T>& in, T* Vx,
-                T* Vy, T* Vz, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check);
+// One fused FP32 correction iteration over the whole grid (z-marching tiles, see the kernel).
+void corr_iteration(cudaStream_t s, Box b, const CorrCoef<float>& c, const CorrIn<float>& in,
+                    const CorrOut<float>& out, unsigned long long* red, int check);
 
 }  // namespace pt

@@ -9,7 +9,7 @@
 //   (iii) FP32 PT on the correction delta = (dV, dPt, dPf) of the system linearised at u with
 //         frozen coefficients (k, 1/(eta(1-phi)), mu, pseudo-time steps): the same damped,
 //         local-implicit scheme as the FP64 iteration, iterating on the small correction so
-//         that FP32 keeps its relative precision on it (k_corr_cells, k_corr_faces);
+//         that FP32 keeps its relative precision on it (k_corr_iteration, one pass per iteration);
 //   (iv)  u <- u + delta in FP64 (k_mix_update), then the porosity time integration of
 //         Eq. 22 in FP64 (log space) from the corrected pressures and velocities.
 // Converged when the FP64 residual max-norms and the Picard change are below tol.
@@ -85,17 +85,14 @@ __global__ void __launch_bounds__(256) k_mix_prepare(Box b, Coef c, MixPrepIn in
     out.txx[q] = (in.txxo[q] * xi + 2.0 * mu * ((in.Vx[q + 1] - in.Vx[q]) * c.rdx - divV / 3.0 + bn)) * s;
     out.tyy[q] = (in.tyyo[q] * xi + 2.0 * mu * ((in.Vy[q + px] - in.Vy[q]) * c.rdy - divV / 3.0 + bn)) * s;
     out.tzz[q] = (in.tzzo[q] * xi + 2.0 * mu * ((in.Vz[q + pxy] - in.Vz[q]) * c.rdz - divV / 3.0 + bn)) * s;
-    // right-hand side and frozen coefficients of the correction problem
-    const double idtp = 1.0 / (c.dtaupt_fac * mu);
-    const double idtf = kmax / c.dtaupf_fac;
+    // right-hand side and frozen coefficients of the correction problem (the iteration derives
+    // 1/dtau_Pf from the largest neighbour k and the local-implicit denominators itself)
+    (void)kmax;
     out.r_pt[q] = (float)divVn;
     out.r_pf[q] = (float)rpf;
     out.cc[q] = (float)cc;
     out.perm[q] = (float)kc;
-    out.idtp[q] = (float)idtp;
-    out.iden_pt[q] = (float)(1.0 / (idtp + c.beta_d * c.rdt + cc));
-    out.idtf[q] = (float)idtf;
-    out.iden_pf[q] = (float)(1.0 / (idtf + c.beta_d * c.alpha / c.B * c.rdt + cc));
+    out.idtp[q] = (float)(1.0 / (c.dtaupt_fac * mu));
     r_pt = fabs(divVn);
     r_pf = fabs(rpf);
   }
@@ -137,155 +134,263 @@ __global__ void __launch_bounds__(256) k_mix_res_faces(Box b, Coef c, MixFaceIn 
   block_max_atomic(r_v, red + RED_V);
 }
 
-// Frozen mu-dependent coefficients of the correction problem: 2 mu/(1+xi) at centres and
-// edges, dtau_V on faces (FP32).
+// Frozen mu-dependent coefficients of the correction problem: mu and the velocity pseudo-step
+// dtau_V = fac / mu at centres, in FP32 (the iteration forms 2 mu/(1+xi) at centres and edges and
+// the face pseudo-steps from them).
 __global__ void __launch_bounds__(256) k_mix_coef(Box b, Coef c, const double* __restrict__ mu, MixCoefOut out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
-  if (i > b.nx || j > b.ny || k > b.nz) return;
-  const long long q = cidx(b, i, j, k);
-  const long long px = b.px, pxy = b.pxy;
-  const double rG = c.rGdtS;
-  // viscoelastic moduli 2 mu / (1 + xi) at centres and edges (mean of the four cells' mu)
   if (i < b.nx && j < b.ny && k < b.nz) {
-    const double m = mu[q];
-    out.cm2[q] = (float)(2.0 * m / (1.0 + m * rG));
+    const long long q = cidx(b, i, j, k);
+    out.mu[q] = (float)mu[q];
+    out.dtvc[q] = (float)(c.dtauv_fac / mu[q]);
   }
-  if (k < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
-    const double m = 0.25 * (mu[q - 1 - px] + mu[q - px] + mu[q - 1] + mu[q]);
-    out.em2_xy[q] = (float)(2.0 * m / (1.0 + m * rG));
-  }
-  if (j < b.ny && i > 0 && i < b.nx && k > 0 && k < b.nz) {
-    const double m = 0.25 * (mu[q - 1 - pxy] + mu[q - pxy] + mu[q - 1] + mu[q]);
-    out.em2_xz[q] = (float)(2.0 * m / (1.0 + m * rG));
-  }
-  if (i < b.nx && j > 0 && j < b.ny && k > 0 && k < b.nz) {
-    const double m = 0.25 * (mu[q - px - pxy] + mu[q - pxy] + mu[q - px] + mu[q]);
-    out.em2_yz[q] = (float)(2.0 * m / (1.0 + m * rG));
-  }
-  // pseudo-time steps of the velocity correction, mean of the two centres' dtau_V = fac / mu
-  if (i > 0 && i < b.nx && j < b.ny && k < b.nz)
-    out.dtv_x[q] = (float)(0.5 * c.dtauv_fac * (1.0 / mu[q - 1] + 1.0 / mu[q]));
-  if (j > 0 && j < b.ny && i < b.nx && k < b.nz)
-    out.dtv_y[q] = (float)(0.5 * c.dtauv_fac * (1.0 / mu[q - px] + 1.0 / mu[q]));
-  if (k > 0 && k < b.nz && i < b.nx && j < b.ny)
-    out.dtv_z[q] = (float)(0.5 * c.dtauv_fac * (1.0 / mu[q - pxy] + 1.0 / mu[q]));
 }
 
-// (iii) one FP32 PT iteration on the correction, cells: edge and centre stresses of dV (no
-// old-stress term, it is in r_F), local-implicit dPt and dPf updates of the linearised Eqs.
-// 17-18 with right-hand sides r_Pt, r_Pf and frozen coefficients.
-template <class T>
-__global__ void __launch_bounds__(256) k_corr_cells(Box b, CorrCoef<T> c, CorrIn<T> in,
-                                                    CorrCellOut<T> out, unsigned long long* red, int check) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  double r_pt = 0.0, r_pf = 0.0;
-  if (i <= b.nx && j <= b.ny && k <= b.nz) {
-    const long long q = cidx(b, i, j, k);
-    const long long px = b.px, pxy = b.pxy;
-    if (k < b.nz) {
-      T t = T(0);
-      if (i > 0 && i < b.nx && j > 0 && j < b.ny)
-        t = in.em2_xy[q] * ((in.Vx[q] - in.Vx[q - px]) * c.hrdy + (in.Vy[q] - in.Vy[q - 1]) * c.hrdx);
-      out.txy[q] = t;
+// (iii) one FP32 PT iteration on the correction in a single pass.
+//
+// The iteration's two halves depend on each other across neighbours: the faces (momentum,
+// damped R, dV) of level k read the cells' stresses and new dPt at k and k-1 (own cell, x- and
+// y-neighbours below) and the edge stresses at k and k+1 (own edge, x- and y-neighbours above).
+// A 32 x 8 block owns a tile of 30 x 6 faces and cells and marches up a column of kCorrZChunk
+// levels: at level L every thread computes the cell and the three lower edges at its index for
+// the tile plus a one-cell halo on each side (the halo is recomputed by the neighbouring tiles'
+// blocks from the same inputs, bit for bit), into a three-level ring in shared memory; after a
+// barrier the tile's threads compute the faces of level L-1 from the ring. Stresses and the new
+// dPt never go to global memory: per cell the pass reads dV, dPt, dPf, R, the right-hand sides
+// and the frozen cc, k, 1/dtau_Pt, mu, dtau_V (18 arrays) and writes dV', dPt', dPf', R (8 arrays):
+// 104 B per cell against 200 B for a cells kernel plus a faces kernel. dV is read from one buffer
+// and written to another (other blocks' halos still read the old dV). The pseudo-step of dPf
+// (largest neighbour k), the local-implicit denominators, 2 mu/(1+xi) at centres and edges (mean
+// of the four centres' mu) and the face pseudo-steps (mean of the two centres') are formed here.
+constexpr int kCorrTX = 30, kCorrTY = 6, kCorrZChunk = 64;
+// The 11 arrays the cell phase reads at its own index are copied into a shared-memory stage by
+// cp.async ahead of their level; the cell phase reads its own values and its x- and y-neighbours
+// inside the block's region from the stage.
+enum { C_VX, C_VY, C_VZ, C_PT, C_PF, C_CC, C_K, C_IDTP, C_RPT, C_RPF, C_MU, kCorrStage };
+// Stage depth: 2 = the next level's copies in flight while this level computes; 3 = two levels
+// ahead, and the z+1 values read from the stage too. Blocks per SM asked of the register allocator.
+constexpr int kCorrStages = 2, kCorrMinBlocks = 4;
+// rings of three levels for cells (4 values) and edges (3), kCorrStages for the staged inputs
+constexpr int kCorrSmemBytes = (3 * (4 + 3) + kCorrStages * kCorrStage) * 8 * 32 * (int)sizeof(float);
+
+__device__ __forceinline__ void corr_cp4(float* smem, const float* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ float corr_modulus(const CorrCoef<float>& c, float m) {
+  return __fdividef(2.0f * m, 1.0f + m * c.rG);
+}
+
+__global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, CorrCoef<float> c, CorrIn<float> in,
+                                                        CorrOut<float> out, unsigned long long* red, int check) {
+  using T = float;
+  // ring of three levels: cells (txx, tyy, tzz, dPt') and edges (txy, txz, tyz) of the region
+  extern __shared__ __align__(16) float corr_smem[];   // kCorrSmemBytes, dynamic (above 48 KB)
+  T(*s_cell)[4][8][32] = reinterpret_cast<T(*)[4][8][32]>(corr_smem);
+  T(*s_edge)[3][8][32] = reinterpret_cast<T(*)[3][8][32]>(corr_smem + 3 * 4 * 8 * 32);
+  T(*s_in)[kCorrStage][8][32] = reinterpret_cast<T(*)[kCorrStage][8][32]>(corr_smem + 3 * 7 * 8 * 32);
+  (void)kCorrSmemBytes;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * kCorrTX - 1 + tx;
+  const int j = blockIdx.y * kCorrTY - 1 + ty;
+  const int k0 = blockIdx.z * kCorrZChunk;
+  const int k1 = min(k0 + kCorrZChunk, b.nz + 1);       // face levels [k0, k1) of this block
+  const bool own = tx >= 1 && tx <= kCorrTX && ty >= 1 && ty <= kCorrTY;
+  const int ipx = b.px, ipxy = (int)b.pxy;   // the host keeps the box below 2^31 elements
+  // residual norms as bit patterns of non-negative doubles: a NaN (largest pattern) stays in them
+  unsigned long long r_pt = 0ull, r_pf = 0ull, r_v = 0ull;
+  auto keep_max = [](unsigned long long& m, float x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong((double)fabsf(x));
+    m = u > m ? u : m;
+  };
+  const bool in_box = i >= 0 && j >= 0 && i <= b.nx && j <= b.ny;
+  auto stage = [&](int L) {   // own-index values of level L (inside the box) into stage L mod 3
+    if (in_box && L >= 0 && L <= b.nz) {
+      const int q = i + ipx * j + ipxy * L;
+      float(*st)[8][32] = s_in[(L + kCorrStages) % kCorrStages];
+      corr_cp4(&st[C_VX][ty][tx], in.Vx + q);
+      corr_cp4(&st[C_VY][ty][tx], in.Vy + q);
+      corr_cp4(&st[C_VZ][ty][tx], in.Vz + q);
+      corr_cp4(&st[C_PT][ty][tx], in.Pt + q);
+      corr_cp4(&st[C_PF][ty][tx], in.Pf + q);
+      corr_cp4(&st[C_CC][ty][tx], in.cc + q);
+      corr_cp4(&st[C_K][ty][tx], in.perm + q);
+      corr_cp4(&st[C_IDTP][ty][tx], in.idtp + q);
+      corr_cp4(&st[C_RPT][ty][tx], in.r_pt + q);
+      corr_cp4(&st[C_RPF][ty][tx], in.r_pf + q);
+      corr_cp4(&st[C_MU][ty][tx], in.mu + q);
     }
-    if (j < b.ny) {
-      T t = T(0);
-      if (i > 0 && i < b.nx && k > 0 && k < b.nz)
-        t = in.em2_xz[q] * ((in.Vx[q] - in.Vx[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - 1]) * c.hrdx);
-      out.txz[q] = t;
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  for (int d = 0; d < kCorrStages - 1; ++d) stage(k0 - 1 + d);
+  for (int L = k0 - 1; L <= k1; ++L) {
+    const int sl = (L + 3) % 3;
+    stage(L + kCorrStages - 1);                        // the level kCorrStages - 1 ahead goes out now
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this thread's copies up to level L landed
+    // every thread's staged copies are visible (the cell phase reads neighbours' staged values),
+    // and the previous level's faces are done with the ring slot this level overwrites
+    __syncthreads();
+    const float(*S)[8][32] = s_in[(L + kCorrStages) % kCorrStages];
+    const float(*Su)[8][32] = s_in[(L + 1 + kCorrStages) % kCorrStages];   // level L + 1 (3 stages)
+    // the faces of level L - 1 read these after the cell phase: their loads go out first
+    const int F = L - 1;
+    const bool face_here = own && F >= k0 && F < k1 && in_box && F <= b.nz;
+    T rfx = T(0), rfy = T(0), rfz = T(0), Rx0 = T(0), Ry0 = T(0), Rz0 = T(0), Vx0 = T(0), Vy0 = T(0), Vz0 = T(0);
+    T dtx = T(0), dty = T(0), dtz = T(0);
+    const bool fx = face_here && i > 0 && i < b.nx && j < b.ny && F < b.nz;
+    const bool fy = face_here && j > 0 && j < b.ny && i < b.nx && F < b.nz;
+    const bool fz = face_here && F > 0 && F < b.nz && i < b.nx && j < b.ny;
+    if (face_here) {
+      const int q = i + ipx * j + ipxy * F;
+      if (fx) { rfx = in.rfx[q]; Rx0 = out.Rx[q]; Vx0 = in.Vx[q]; dtx = T(0.5) * (in.dtvc[q - 1] + in.dtvc[q]); }
+      if (fy) { rfy = in.rfy[q]; Ry0 = out.Ry[q]; Vy0 = in.Vy[q]; dty = T(0.5) * (in.dtvc[q - ipx] + in.dtvc[q]); }
+      if (fz) { rfz = in.rfz[q]; Rz0 = out.Rz[q]; Vz0 = in.Vz[q]; dtz = T(0.5) * (in.dtvc[q - ipxy] + in.dtvc[q]); }
     }
-    if (i < b.nx) {
-      T t = T(0);
-      if (j > 0 && j < b.ny && k > 0 && k < b.nz)
-        t = in.em2_yz[q] * ((in.Vy[q] - in.Vy[q - pxy]) * c.hrdz + (in.Vz[q] - in.Vz[q - px]) * c.hrdy);
-      out.tyz[q] = t;
+    // ---------------- cell and lower edges at (i, j, L). Cells are needed for the tile and its
+    // left / lower halo (tx <= 30, ty <= 6), edges for the tile and its right / upper halo
+    // (tx >= 1, ty >= 1). Indices are 32-bit (the host keeps the box below 2^31 elements);
+    // x- and y-neighbours inside the block's region come from this level's stage.
+    T txx = T(0), tyy = T(0), tzz = T(0), P1 = T(0), exy = T(0), exz = T(0), eyz = T(0);
+    if (in_box && L >= 0 && L <= b.nz) {
+      const int q = i + ipx * j + ipxy * L;
+      auto nb = [&](int slot, int dx, int dy, const float* g, int off) -> float {
+        const int x = tx + dx, y = ty + dy;
+        return (x >= 0 && x < 32 && y >= 0 && y < 8) ? S[slot][y][x] : g[q + off];
+      };
+      const T mu_c = S[C_MU][ty][tx], vx_c = S[C_VX][ty][tx], vy_c = S[C_VY][ty][tx], vz_c = S[C_VZ][ty][tx];
+      if (tx >= 1 && ty >= 1) {
+        if (L < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
+          const T m = T(0.25) * (nb(C_MU, -1, -1, in.mu, -1 - ipx) + nb(C_MU, 0, -1, in.mu, -ipx) +
+                                 nb(C_MU, -1, 0, in.mu, -1) + mu_c);
+          exy = corr_modulus(c, m) * ((vx_c - nb(C_VX, 0, -1, in.Vx, -ipx)) * c.hrdy +
+                                      (vy_c - nb(C_VY, -1, 0, in.Vy, -1)) * c.hrdx);
+        }
+        if (j < b.ny && i > 0 && i < b.nx && L > 0 && L < b.nz) {
+          const T m = T(0.25) * (in.mu[q - 1 - ipxy] + in.mu[q - ipxy] + nb(C_MU, -1, 0, in.mu, -1) + mu_c);
+          exz = corr_modulus(c, m) * ((vx_c - in.Vx[q - ipxy]) * c.hrdz + (vz_c - nb(C_VZ, -1, 0, in.Vz, -1)) * c.hrdx);
+        }
+        if (i < b.nx && j > 0 && j < b.ny && L > 0 && L < b.nz) {
+          const T m = T(0.25) * (in.mu[q - ipx - ipxy] + in.mu[q - ipxy] + nb(C_MU, 0, -1, in.mu, -ipx) + mu_c);
+          eyz = corr_modulus(c, m) * ((vy_c - in.Vy[q - ipxy]) * c.hrdz + (vz_c - nb(C_VZ, 0, -1, in.Vz, -ipx)) * c.hrdy);
+        }
+      }
+      if (tx <= kCorrTX && ty <= kCorrTY && i < b.nx && j < b.ny && L < b.nz) {
+        const T dPt = S[C_PT][ty][tx], dPf = S[C_PF][ty][tx], cc = S[C_CC][ty][tx];
+        const T rpt = S[C_RPT][ty][tx], rpf = S[C_RPF][ty][tx];
+        const T gx = (nb(C_VX, 1, 0, in.Vx, 1) - vx_c) * c.rdx, gy = (nb(C_VY, 0, 1, in.Vy, ipx) - vy_c) * c.rdy;
+        const T gz = (((kCorrStages > 2) ? Su[C_VZ][ty][tx] : in.Vz[q + ipxy]) - vz_c) * c.rdz;
+        const T divV = gx + gy + gz;
+        const T cpl = c.bd_rdt_a + cc;                 // beta_d alpha / dt + cc
+        const T rho_pt = rpt + divV + (c.bd_rdt + cc) * dPt - cpl * dPf;
+        const T kc = S[C_K][ty][tx];
+        T kmax = kc, sx = T(0), sy = T(0), sz = T(0);
+        if (i > 0) {
+          const T kn = nb(C_K, -1, 0, in.perm, -1);
+          kmax = fmaxf(kmax, kn);
+          sx -= (kn + kc) * (dPf - nb(C_PF, -1, 0, in.Pf, -1));
+        }
+        if (i < b.nx - 1) {
+          const T kn = nb(C_K, 1, 0, in.perm, 1);
+          kmax = fmaxf(kmax, kn);
+          sx += (kc + kn) * (nb(C_PF, 1, 0, in.Pf, 1) - dPf);
+        }
+        if (j > 0) {
+          const T kn = nb(C_K, 0, -1, in.perm, -ipx);
+          kmax = fmaxf(kmax, kn);
+          sy -= (kn + kc) * (dPf - nb(C_PF, 0, -1, in.Pf, -ipx));
+        }
+        if (j < b.ny - 1) {
+          const T kn = nb(C_K, 0, 1, in.perm, ipx);
+          kmax = fmaxf(kmax, kn);
+          sy += (kc + kn) * (nb(C_PF, 0, 1, in.Pf, ipx) - dPf);
+        }
+        if (L > 0) {
+          const T kn = in.perm[q - ipxy];
+          kmax = fmaxf(kmax, kn);
+          sz -= (kn + kc) * (dPf - in.Pf[q - ipxy]);
+        }
+        if (L < b.nz - 1) {
+          const T kn = (kCorrStages > 2) ? Su[C_K][ty][tx] : in.perm[q + ipxy];
+          kmax = fmaxf(kmax, kn);
+          sz += (kc + kn) * (((kCorrStages > 2) ? Su[C_PF][ty][tx] : in.Pf[q + ipxy]) - dPf);
+        }
+        const T divq = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
+        const T rho_pf = rpf + divq + (c.bda_B_rdt + cc) * dPf - cpl * dPt;
+        // dP' = dP - dtau rho(dP', ...) solved for dP' (local terms implicit; the quotients only
+        // scale the pseudo-step, so the fast reciprocal does)
+        const T idtp = S[C_IDTP][ty][tx], idtf = kmax * c.ifac_pf;
+        const T dPt1 = __fdividef(dPt * idtp - (rpt + divV - cpl * dPf), idtp + c.bd_rdt + cc);
+        const T dPf1 = __fdividef(dPf * idtf - (rpf + divq - cpl * dPt), idtf + c.bda_B_rdt + cc);
+        const T third = divV * T(1.0 / 3.0);
+        const T bn = c.beta_n * (rho_pt - rpt);
+        const T cm2 = corr_modulus(c, mu_c);
+        txx = cm2 * (gx - third + bn);
+        tyy = cm2 * (gy - third + bn);
+        tzz = cm2 * (gz - third + bn);
+        P1 = dPt1;
+        if (own && L >= k0 && L < k1) {
+          out.Pt[q] = dPt1;
+          out.Pf[q] = dPf1;
+          if (check) {
+            keep_max(r_pt, rho_pt);
+            keep_max(r_pf, rho_pf);
+          }
+        }
+      }
     }
-    if (i < b.nx && j < b.ny && k < b.nz) {
-      const T dPt = in.Pt[q], dPf = in.Pf[q], cc = in.cc[q];
-      const T gx = (in.Vx[q + 1] - in.Vx[q]) * c.rdx, gy = (in.Vy[q + px] - in.Vy[q]) * c.rdy;
-      const T gz = (in.Vz[q + pxy] - in.Vz[q]) * c.rdz;
-      const T divV = gx + gy + gz;
-      const T cpl = c.bd_rdt_a + cc;                 // beta_d alpha / dt + cc
-      const T rho_pt = in.r_pt[q] + divV + (c.bd_rdt + cc) * dPt - cpl * dPf;
-      const T kc = in.perm[q];
-      T sx = T(0), sy = T(0), sz = T(0);
-      if (i > 0) sx -= (in.perm[q - 1] + kc) * (dPf - in.Pf[q - 1]);
-      if (i < b.nx - 1) sx += (kc + in.perm[q + 1]) * (in.Pf[q + 1] - dPf);
-      if (j > 0) sy -= (in.perm[q - px] + kc) * (dPf - in.Pf[q - px]);
-      if (j < b.ny - 1) sy += (kc + in.perm[q + px]) * (in.Pf[q + px] - dPf);
-      if (k > 0) sz -= (in.perm[q - pxy] + kc) * (dPf - in.Pf[q - pxy]);
-      if (k < b.nz - 1) sz += (kc + in.perm[q + pxy]) * (in.Pf[q + pxy] - dPf);
-      const T divq = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
-      const T rho_pf = in.r_pf[q] + divq + (c.bda_B_rdt + cc) * dPf - cpl * dPt;
-      // dP' = dP - dtau rho(dP', ...) solved for dP' (local terms implicit)
-      const T dPt1 = (dPt * in.idtp[q] - (in.r_pt[q] + divV - cpl * dPf)) * in.iden_pt[q];
-      const T dPf1 = (dPf * in.idtf[q] - (in.r_pf[q] + divq - cpl * dPt)) * in.iden_pf[q];
-      out.Pt[q] = dPt1;
-      out.Pf[q] = dPf1;
-      const T third = divV * T(1.0 / 3.0);
-      const T bn = c.beta_n * (rho_pt - in.r_pt[q]);
-      const T cm2 = in.cm2[q];
-      out.txx[q] = cm2 * (gx - third + bn);
-      out.tyy[q] = cm2 * (gy - third + bn);
-      out.tzz[q] = cm2 * (gz - third + bn);
+    s_cell[sl][0][ty][tx] = txx;
+    s_cell[sl][1][ty][tx] = tyy;
+    s_cell[sl][2][ty][tx] = tzz;
+    s_cell[sl][3][ty][tx] = P1;
+    s_edge[sl][0][ty][tx] = exy;
+    s_edge[sl][1][ty][tx] = exz;
+    s_edge[sl][2][ty][tx] = eyz;
+    __syncthreads();
+    // ---------------- faces of level F = L - 1 (cells at F and F-1, edges at F and L = F+1)
+    if (face_here) {
+      const int sf = (F + 3) % 3, sb = (F + 2) % 3, su = sl;
+      const int q = i + ipx * j + ipxy * F;
+      const T Pc = s_cell[sf][3][ty][tx];
+      T Fx = T(0), Fy = T(0), Fz = T(0);
+      if (fx) {
+        Fx = rfx + (s_cell[sf][0][ty][tx] - s_cell[sf][0][ty][tx - 1]) * c.rdx +
+             (s_edge[sf][0][ty + 1][tx] - s_edge[sf][0][ty][tx]) * c.rdy +
+             (s_edge[su][1][ty][tx] - s_edge[sf][1][ty][tx]) * c.rdz - (Pc - s_cell[sf][3][ty][tx - 1]) * c.rdx;
+        const T R1 = Fx * c.rrho_i + c.damp_x * Rx0;
+        out.Rx[q] = R1;
+        out.Vx[q] = Vx0 + dtx * R1;
+      }
+      if (fy) {
+        Fy = rfy + (s_edge[sf][0][ty][tx + 1] - s_edge[sf][0][ty][tx]) * c.rdx +
+             (s_cell[sf][1][ty][tx] - s_cell[sf][1][ty - 1][tx]) * c.rdy +
+             (s_edge[su][2][ty][tx] - s_edge[sf][2][ty][tx]) * c.rdz - (Pc - s_cell[sf][3][ty - 1][tx]) * c.rdy;
+        const T R1 = Fy * c.rrho_i + c.damp_y * Ry0;
+        out.Ry[q] = R1;
+        out.Vy[q] = Vy0 + dty * R1;
+      }
+      if (fz) {
+        Fz = rfz + (s_edge[sf][1][ty][tx + 1] - s_edge[sf][1][ty][tx]) * c.rdx +
+             (s_edge[sf][2][ty + 1][tx] - s_edge[sf][2][ty][tx]) * c.rdy +
+             (s_cell[sf][2][ty][tx] - s_cell[sb][2][ty][tx]) * c.rdz - (Pc - s_cell[sb][3][ty][tx]) * c.rdz;
+        const T R1 = Fz * c.rrho_i + c.damp_z * Rz0;
+        out.Rz[q] = R1;
+        out.Vz[q] = Vz0 + dtz * R1;
+      }
       if (check) {
-        r_pt = (double)tabs(rho_pt);
-        r_pf = (double)tabs(rho_pf);
+        keep_max(r_v, Fx);
+        keep_max(r_v, Fy);
+        keep_max(r_v, Fz);
       }
     }
   }
   if (check) {
-    block_max_atomic(r_pt, red + RED_PT);
-    block_max_atomic(r_pf, red + RED_PF);
+    block_max_atomic(__longlong_as_double((long long)r_pt), red + RED_PT);
+    block_max_atomic(__longlong_as_double((long long)r_pf), red + RED_PF);
+    block_max_atomic(__longlong_as_double((long long)r_v), red + RED_V);
   }
-}
-
-// (iii) faces: linearised momentum residual r_F + div tau(dV) - grad dPt', damped R, dV update.
-// Reads 19 FP32 arrays and writes 6, all loads before the first store.
-template <class T>
-__global__ void __launch_bounds__(256) k_corr_faces(Box b, CorrCoef<T> c, CorrFaceIn<T> in,
-                                                    T* __restrict__ Vx, T* __restrict__ Vy, T* __restrict__ Vz,
-                                                    T* __restrict__ Rx, T* __restrict__ Ry, T* __restrict__ Rz,
-                                                    unsigned long long* red, int check) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  double r_v = 0.0;
-  if (i <= b.nx && j <= b.ny && k <= b.nz) {
-    const long long q = cidx(b, i, j, k);
-    const long long px = b.px, pxy = b.pxy;
-    const bool fx = i > 0 && i < b.nx && j < b.ny && k < b.nz;
-    const bool fy = j > 0 && j < b.ny && i < b.nx && k < b.nz;
-    const bool fz = k > 0 && k < b.nz && i < b.nx && j < b.ny;
-    T Fx = T(0), Fy = T(0), Fz = T(0), Rx1 = T(0), Ry1 = T(0), Rz1 = T(0), Vx1 = T(0), Vy1 = T(0), Vz1 = T(0);
-    if (fx) {
-      Fx = in.rfx[q] + (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
-           (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - 1]) * c.rdx;
-      Rx1 = Fx * c.rrho_i + c.damp_x * Rx[q];
-      Vx1 = Vx[q] + in.dtv_x[q] * Rx1;
-    }
-    if (fy) {
-      Fy = in.rfy[q] + (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
-           (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.Pt1[q] - in.Pt1[q - px]) * c.rdy;
-      Ry1 = Fy * c.rrho_i + c.damp_y * Ry[q];
-      Vy1 = Vy[q] + in.dtv_y[q] * Ry1;
-    }
-    if (fz) {
-      Fz = in.rfz[q] + (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
-           (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.Pt1[q] - in.Pt1[q - pxy]) * c.rdz;
-      Rz1 = Fz * c.rrho_i + c.damp_z * Rz[q];
-      Vz1 = Vz[q] + in.dtv_z[q] * Rz1;
-    }
-    if (fx) { Rx[q] = Rx1; Vx[q] = Vx1; }
-    if (fy) { Ry[q] = Ry1; Vy[q] = Vy1; }
-    if (fz) { Rz[q] = Rz1; Vz[q] = Vz1; }
-    if (check) r_v = fmax((double)tabs(Fx), fmax((double)tabs(Fy), (double)tabs(Fz)));
-  }
-  if (check) block_max_atomic(r_v, red + RED_V);
 }
 
 // (iv) u <- u + delta (FP64 += FP32 correction).
@@ -319,19 +424,12 @@ void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const doubl
 void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u) {
   k_mix_update<<<g, bl, 0, s>>>(b, u);
 }
-template <class T>
-void corr_cells(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrIn<T>& in,
-                const CorrCellOut<T>& out, unsigned long long* red, int check) {
-  k_corr_cells<T><<<g, bl, 0, s>>>(b, c, in, out, red, check);
+void corr_iteration(cudaStream_t s, Box b, const CorrCoef<float>& c, const CorrIn<float>& in,
+                    const CorrOut<float>& out, unsigned long long* red, int check) {
+  const dim3 g((unsigned)((b.nx + 1 + kCorrTX - 1) / kCorrTX), (unsigned)((b.ny + 1 + kCorrTY - 1) / kCorrTY),
+               (unsigned)((b.nz + 1 + kCorrZChunk - 1) / kCorrZChunk));
+  cudaFuncSetAttribute(k_corr_iteration, cudaFuncAttributeMaxDynamicSharedMemorySize, kCorrSmemBytes);
+  k_corr_iteration<<<g, dim3(32, 8, 1), kCorrSmemBytes, s>>>(b, c, in, out, red, check);
 }
-template <class T>
-void corr_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const CorrCoef<T>& c, const CorrFaceIn<T>& in, T* Vx,
-                T* Vy, T* Vz, T* Rx, T* Ry, T* Rz, unsigned long long* red, int check) {
-  k_corr_faces<T><<<g, bl, 0, s>>>(b, c, in, Vx, Vy, Vz, Rx, Ry, Rz, red, check);
-}
-template void corr_cells<float>(dim3, dim3, cudaStream_t, Box, const CorrCoef<float>&, const CorrIn<float>&,
-                                const CorrCellOut<float>&, unsigned long long*, int);
-template void corr_faces<float>(dim3, dim3, cudaStream_t, Box, const CorrCoef<float>&, const CorrFaceIn<float>&,
-                                float*, float*, float*, float*, float*, float*, unsigned long long*, int);
 
 }  // namespace pt

@@ -50,24 +50,24 @@ def test_source_hash_tracks_the_kernel_files(tmp_path, monkeypatch):
     assert bench.source_hash("k_lean_cells") == h          # same translation unit and headers
     assert bench.source_hash("no_such_kernel") is None
     # identical copies give the same hash; one changed byte changes it
-    before = bench.source_hash("k_corr_cells")
-    for f in bench.KERNEL_SOURCES["k_corr_cells"]:
+    before = bench.source_hash("k_corr_iteration")
+    for f in bench.KERNEL_SOURCES["k_corr_iteration"]:
         with open(bench.os.path.join(bench.CSRC, f), "rb") as fh:
             (tmp_path / f).write_bytes(fh.read())
     monkeypatch.setattr(bench, "CSRC", str(tmp_path))
-    assert bench.source_hash("k_corr_cells") == before
-    f0 = bench.KERNEL_SOURCES["k_corr_cells"][0]
+    assert bench.source_hash("k_corr_iteration") == before
+    f0 = bench.KERNEL_SOURCES["k_corr_iteration"][0]
     (tmp_path / f0).write_bytes((tmp_path / f0).read_bytes() + b" ")
-    assert bench.source_hash("k_corr_cells") != before
+    assert bench.source_hash("k_corr_iteration") != before
 
 
 def test_fp32_correction_reports_hbm():
     n = 511 ** 3
-    k = {"k_corr_cells": (300, 300 * 4.0), "k_corr_faces": (300, 300 * 3.9), "k_mix_prepare": (2, 2 * 20.0)}
+    k = {"k_corr_iteration": (300, 300 * 4.0), "k_mix_prepare": (2, 2 * 20.0)}
     r = bench.roofline(k, n)
     hbm, _ = bench.peaks()
-    assert r["kernel"] == "k_corr_cells" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    gbs = bench.KERNEL_BYTES_PER_CELL["k_corr_cells"] * n / 4.0e-3 / 1e9
+    assert r["kernel"] == "k_corr_iteration" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    gbs = bench.KERNEL_BYTES_PER_CELL["k_corr_iteration"] * n / 4.0e-3 / 1e9
     assert abs(r["achieved"] - gbs) < 1e-6 * gbs
     assert abs(r["peak"] - hbm) < 1e-9 and abs(r["frac"] - gbs / hbm) < 1e-12
 
