@@ -119,8 +119,8 @@ def parse():
                     help="anomaly-position seeds of the headline form at N = 1 (value = median over them); "
                          "under torchrun each rank uses seed = rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-n", type=int, default=191, help="sub-block edge of the CPU sample")
-    ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--cpu-n", type=int, default=255, help="sub-block edge of the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=60)
     ap.add_argument("--cpu-timings", action="store_true",
                     help="time the oracle at 127^3 and 511^3 (PT iterations) and one full c1 step, on all host "
                          "cores and on one core, each in its own process, and exit")
@@ -264,6 +264,18 @@ def cpu_timings(args) -> dict:
     out = []
     ncores = os.cpu_count() or 1
     cases = [("iter", 127), ("iter", 511), ("c1", 32)]
+    # the 511^3 oracle state and scratch take ~60 GB of host memory: run it only with room to spare
+    avail_gb = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail_gb = int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    if avail_gb is None or avail_gb < 120:
+        cases = [c for c in cases if c[1] != 511]
+        out.append({"skipped": "511^3", "reason": f"host memory available {avail_gb} GB < 120 GB"})
     for kind, n in cases:
         for threads in (ncores, 1):
             env = dict(os.environ, OMP_NUM_THREADS=str(threads))
@@ -275,7 +287,7 @@ def cpu_timings(args) -> dict:
             rec["threads_requested"] = threads
             out.append(rec)
             print(json.dumps(rec), flush=True)
-    return {"host_cores": ncores, "cases": out}
+    return {"host_cores": ncores, "host_mem_available_gb": avail_gb, "cases": out}
 
 
 def run_reference(args):

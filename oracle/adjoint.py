@@ -6,9 +6,14 @@ u = (V, Pt, Pf, phi); for J = sum (phi^N - phi_target)^2 the adjoint recursion i
     J_F(u^{n+1})^T lambda^{n+1} = g^{n+1},
     g^N = dJ/du^N,   g^n = -(dF^{n+1}/du^n)^T lambda^{n+1}  (n < N),
     dJ/dtheta = -sum_n (dF^{n}/dtheta)^T lambda^{n}.
-Scope: power law off (mu = mu0), no weakening switch (R = 1), beta_n = 0 and old-step
-stresses fixed over the window (no stress sub-step refresh), so the converged Picard state is
-eta = eta0 mu0 / phi exactly and u = (V on interior faces, Pt, Pf, phi) is the whole unknown.
+Scope: no weakening switch (R = 1; Eq. 25 is a step function), beta_n = 0, zero old-step
+stresses over the window (no stress sub-step refresh). With the power law off the converged
+Picard state is mu = mu0, eta = eta0 mu0 / phi and u = (V on interior faces, Pt, Pf, phi) is
+the whole unknown. With the power law on (Eq. 24) mu joins the unknowns with the Picard
+fixed-point row F_mu = log mu - log mu*(tau_II) (the Maxwell stresses of Eq. 21 with moduli
+2 mu / (1 + xi), xi = mu / (G dtS), edge values from the mean of the four centres' mu),
+eta = eta0 mu / phi (Eq. 26 at its fixed point), and the step's stress sub-step
+dtS = max(mu_prev) / (G xsi_w) makes each step depend on the previous step's mu as well.
 
 The residual is written with plain PyTorch CPU ops in FP64 (one expression per term of the
 oracle's discretisation), so autograd gives exact Jacobian products; on tiny grids the adjoint
@@ -41,8 +46,14 @@ def residual(p: dict, u: dict, old: dict, theta: torch.Tensor) -> dict:
     Pto, Pfo, Lo = old["Pto"], old["Pfo"], old["Lo"]
     bd, al, B_, bphi, dt = p["beta_d"], p["alpha"], p["B"], p["beta_phi"], p["dt"]
     mu0, eta0, G = p["mu0"], p["eta0"], p["G"]
+    pl = bool(p.get("powerlaw_on", 0))
     rho_bg = p["phi0"] * p["rhof_g"] + (1 - p["phi0"]) * p["rhos_g"]
-    eta = eta0 * mu0 / phi                                          # Eq. 26, R = 1
+    if pl:
+        mu = u["mu"]
+        Gdt = torch.max(old["mu_o"]) / p["xsi_w"]                   # G dtS, dtS = max mu_prev / (G xsi_w)
+        eta = eta0 * mu / phi                                       # Eq. 26, R = 1
+    else:
+        eta = eta0 * mu0 / phi                                      # Eq. 26, R = 1
     cc = 1.0 / (eta * (1.0 - phi))                                  # compaction coefficient
     # div V and the total-pressure residual (Eq. 17)
     gx = (Vx[:, :, 1:] - Vx[:, :, :-1]) / dx
@@ -61,19 +72,26 @@ def residual(p: dict, u: dict, old: dict, theta: torch.Tensor) -> dict:
     qz = torch.cat([z(qz, 0), qz, z(qz, 0)], 0)
     divq = (qx[:, :, 1:] - qx[:, :, :-1]) / dx + (qy[:, 1:, :] - qy[:, :-1, :]) / dy + (qz[1:] - qz[:-1]) / dz
     Fpf = divq + bd * al * ((Pf - Pfo) / B_ - (Pt - Pto)) / dt + (Pf - Pt) * cc
-    # Maxwell stresses with tau_o = 0, xi = mu0 / (G dtS), dtS = mu0 / (G xsi_w) (Eq. 21)
-    xi = p["xsi_w"]
-    m2 = 2.0 * mu0 / (1.0 + xi)
-    txx = m2 * (gx - divV / 3.0)
-    tyy = m2 * (gy - divV / 3.0)
-    tzz = m2 * (gz - divV / 3.0)
+    # Maxwell stresses with tau_o = 0 (Eq. 21): 2 mu / (1 + xi) times the deviatoric strain rate,
+    # xi = mu / (G dtS); the power law off: mu = mu0 and dtS = mu0 / (G xsi_w), so xi = xsi_w
     exy = 0.5 * ((Vx[:, 1:, 1:-1] - Vx[:, :-1, 1:-1]) / dy + (Vy[:, 1:-1, 1:] - Vy[:, 1:-1, :-1]) / dx)
     exz = 0.5 * ((Vx[1:, :, 1:-1] - Vx[:-1, :, 1:-1]) / dz + (Vz[1:-1, :, 1:] - Vz[1:-1, :, :-1]) / dx)
     eyz = 0.5 * ((Vy[1:, 1:-1, :] - Vy[:-1, 1:-1, :]) / dz + (Vz[1:-1, 1:, :] - Vz[1:-1, :-1, :]) / dy)
     pad = lambda t, dims: torch.nn.functional.pad(t, dims)
-    txy = pad(m2 * exy, (1, 1, 1, 1))            # zero on boundary edges (free slip)
-    txz = pad(m2 * exz, (1, 1, 0, 0, 1, 1))
-    tyz = pad(m2 * eyz, (0, 0, 1, 1, 1, 1))
+    if pl:
+        mod = lambda m: 2.0 * m / (1.0 + m / Gdt)
+        mc = mod(mu)
+        m_xy = mod(0.25 * (mu[:, 1:, 1:] + mu[:, :-1, 1:] + mu[:, 1:, :-1] + mu[:, :-1, :-1]))
+        m_xz = mod(0.25 * (mu[1:, :, 1:] + mu[:-1, :, 1:] + mu[1:, :, :-1] + mu[:-1, :, :-1]))
+        m_yz = mod(0.25 * (mu[1:, 1:, :] + mu[:-1, 1:, :] + mu[1:, :-1, :] + mu[:-1, :-1, :]))
+    else:
+        mc = m_xy = m_xz = m_yz = 2.0 * mu0 / (1.0 + p["xsi_w"])
+    txx = mc * (gx - divV / 3.0)
+    tyy = mc * (gy - divV / 3.0)
+    tzz = mc * (gz - divV / 3.0)
+    txy = pad(m_xy * exy, (1, 1, 1, 1))          # zero on boundary edges (free slip)
+    txz = pad(m_xz * exz, (1, 1, 0, 0, 1, 1))
+    tyz = pad(m_yz * eyz, (0, 0, 1, 1, 1, 1))
     rog = (phi - p["phi0"]) * (p["rhof_g"] - p["rhos_g"])
     Fx = ((txx[:, :, 1:] - txx[:, :, :-1]) / dx + (txy[:, 1:, 1:-1] - txy[:, :-1, 1:-1]) / dy +
           (txz[1:, :, 1:-1] - txz[:-1, :, 1:-1]) / dz - (Pt[:, :, 1:] - Pt[:, :, :-1]) / dx)
@@ -92,13 +110,26 @@ def residual(p: dict, u: dict, old: dict, theta: torch.Tensor) -> dict:
         torch.nn.functional.pad(Vz[1:-1] * (om[1:] - om[:-1]) / dz, (0, 0, 0, 0, 0, 1))
     adv = 0.5 * (ax + ay + az) / om
     FL = torch.log(1.0 - phi) - (Lo - dt * (bphi * ((Pf - Pfo) - (Pt - Pto)) / dt + (Pf - Pt) / eta + adv))
-    return dict(Fx=Fx, Fy=Fy, Fz=Fz, Fpt=Fpt, Fpf=Fpf, FL=FL)
+    out = dict(Fx=Fx, Fy=Fy, Fz=Fz, Fpt=Fpt, Fpf=Fpf, FL=FL)
+    if pl:
+        # Picard fixed point of Eq. 24: log mu - log(mu0 / (1 + (tau_II / tau0)^(n-1))), tau_II from
+        # the centre stresses and the four edges' shear stresses averaged to the centre
+        axy = 0.25 * (txy[:, :-1, :-1] + txy[:, :-1, 1:] + txy[:, 1:, :-1] + txy[:, 1:, 1:])
+        axz = 0.25 * (txz[:-1, :, :-1] + txz[:-1, :, 1:] + txz[1:, :, :-1] + txz[1:, :, 1:])
+        ayz = 0.25 * (tyz[:-1, :-1, :] + tyz[:-1, 1:, :] + tyz[1:, :-1, :] + tyz[1:, 1:, :])
+        t2 = 0.5 * (txx * txx + tyy * tyy + tzz * tzz) + axy * axy + axz * axz + ayz * ayz
+        x = (t2 / p["tau0"] ** 2) ** (0.5 * (p["n_pow"] - 1.0))
+        out["Fmu"] = torch.log(mu) - np.log(mu0) + torch.log(1.0 + x)
+    return out
 
 
 # ---------------------------------------------------------------- packing of the unknowns
 def _interior(u):
-    return dict(Vx=u["Vx"][:, :, 1:-1], Vy=u["Vy"][:, 1:-1, :], Vz=u["Vz"][1:-1], Pt=u["Pt"], Pf=u["Pf"],
-                phi=u["phi"])
+    d = dict(Vx=u["Vx"][:, :, 1:-1], Vy=u["Vy"][:, 1:-1, :], Vz=u["Vz"][1:-1], Pt=u["Pt"], Pf=u["Pf"],
+             phi=u["phi"])
+    if "mu" in u:
+        d["mu"] = u["mu"]
+    return d
 
 
 def _pack(d, keys):
@@ -107,14 +138,20 @@ def _pack(d, keys):
 
 U_KEYS = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi")
 F_KEYS = ("Fx", "Fy", "Fz", "Fpt", "Fpf", "FL")
+U_KEYS_PL = U_KEYS + ("mu",)
+F_KEYS_PL = F_KEYS + ("Fmu",)
+
+
+def _keys(p):
+    return (U_KEYS_PL, F_KEYS_PL) if p.get("powerlaw_on", 0) else (U_KEYS, F_KEYS)
 
 
 def _unpack_u(x, p):
     nx, ny, nz = p["nx"], p["ny"], p["nz"]
     shapes = dict(Vx=(nz, ny, nx - 1), Vy=(nz, ny - 1, nx), Vz=(nz - 1, ny, nx), Pt=(nz, ny, nx),
-                  Pf=(nz, ny, nx), phi=(nz, ny, nx))
+                  Pf=(nz, ny, nx), phi=(nz, ny, nx), mu=(nz, ny, nx))
     out, o = {}, 0
-    for k in U_KEYS:
+    for k in _keys(p)[0]:
         n = int(np.prod(shapes[k]))
         out[k] = x[o:o + n].reshape(shapes[k])
         o += n
@@ -129,24 +166,24 @@ def _t(a):
 
 
 def state_u(st) -> dict:
-    return {k: _t(st[k]) for k in U_KEYS}
+    return {k: _t(st[k]) for k in U_KEYS_PL}
 
 
 def old_from(st) -> dict:
-    """Old-step fields a step starting from oracle state `st` uses."""
-    return dict(Pto=_t(st["Pt"]), Pfo=_t(st["Pf"]), Lo=torch.log(1.0 - _t(st["phi"])))
+    """Old-step fields a step starting from oracle state `st` uses (mu_o sets its dtS)."""
+    return dict(Pto=_t(st["Pt"]), Pfo=_t(st["Pf"]), Lo=torch.log(1.0 - _t(st["phi"])), mu_o=_t(st["mu"]))
 
 
-def adjoint_params(p: dict) -> dict:
-    """The scope of the adjoint: power law off, no weakening, beta_n = 0."""
+def adjoint_params(p: dict, powerlaw: bool = False) -> dict:
+    """The scope of the adjoint: no weakening, beta_n = 0; the power law off unless asked for."""
     q = dict(p)
-    q.update(powerlaw_on=0, R_weak=1.0, beta_n=0.0, tau_bg=0.0)
+    q.update(powerlaw_on=int(bool(powerlaw)), R_weak=1.0, beta_n=0.0, tau_bg=0.0)
     return q
 
 
 def forward(p: dict, phi0: np.ndarray, theta: np.ndarray, nsteps: int, tol: float = 1e-12):
     """Converged oracle steps; returns the list of states [u^0, ..., u^N] (oracle states)."""
-    q = dict(adjoint_params(p), tol=tol, max_iter=max(p["max_iter"], 400000))
+    q = dict(adjoint_params(p, p.get("powerlaw_on", 0)), tol=tol, max_iter=max(p["max_iter"], 400000))
     st = B.make_state(q, phi0, logk=theta)
     states = [st.copy()]
     for _ in range(nsteps):
@@ -163,32 +200,38 @@ def misfit(phi: np.ndarray, target: np.ndarray) -> float:
 
 def gradient(p: dict, states: list, theta: np.ndarray, target: np.ndarray) -> np.ndarray:
     """dJ/dtheta by the discrete adjoint (dense LU per step; tiny grids only)."""
-    q = adjoint_params(p)
+    q = adjoint_params(p, p.get("powerlaw_on", 0))
+    UK, FK = _keys(q)
     th = _t(theta)
     N = len(states) - 1
-    u = [_interior(state_u(s)) for s in states]
+    u = [{k: v for k, v in _interior(state_u(s)).items() if k in UK} for s in states]
     g = {k: torch.zeros_like(v) for k, v in u[N].items()}
     g["phi"] = 2.0 * (_t(states[N]["phi"]) - _t(target))
     grad = torch.zeros_like(th)
     for n in range(N, 0, -1):
         old = old_from(states[n - 1])
-        x0 = _pack(u[n], U_KEYS)
+        x0 = _pack(u[n], UK)
 
         def Fu(x):
-            return _pack(residual(q, _unpack_u(x, q), old, th), F_KEYS)
+            return _pack(residual(q, _unpack_u(x, q), old, th), FK)
 
         Jm = torch.autograd.functional.jacobian(Fu, x0)
-        lam = torch.linalg.solve(Jm.T, _pack(g, U_KEYS))
+        lam = torch.linalg.solve(Jm.T, _pack(g, UK))
         # dJ/dtheta -= (dF/dtheta)^T lambda
         thv = th.clone().requires_grad_(True)
-        Fth = _pack(residual(q, _unpack_u(x0, q), old, thv), F_KEYS)
+        Fth = _pack(residual(q, _unpack_u(x0, q), old, thv), FK)
         (gth,) = torch.autograd.grad(Fth, thv, grad_outputs=lam)
         grad -= gth
-        # carry into the previous step: g^{n-1} = -(dF^n/du^{n-1})^T lambda (through Pto, Pfo, Lo)
+        # carry into the previous step: g^{n-1} = -(dF^n/du^{n-1})^T lambda (through Pto, Pfo,
+        # Lo and, with the power law, the previous mu's maximum in dtS)
         prev = {k: v.clone().requires_grad_(True) for k, v in u[n - 1].items()}
-        oldv = dict(Pto=prev["Pt"], Pfo=prev["Pf"], Lo=torch.log(1.0 - prev["phi"]))
-        Fo = _pack(residual(q, _unpack_u(x0, q), oldv, th), F_KEYS)
-        gs = torch.autograd.grad(Fo, [prev[k] for k in ("Pt", "Pf", "phi")], grad_outputs=lam)
+        oldv = dict(Pto=prev["Pt"], Pfo=prev["Pf"], Lo=torch.log(1.0 - prev["phi"]),
+                    mu_o=prev["mu"] if "mu" in prev else old["mu_o"])
+        Fo = _pack(residual(q, _unpack_u(x0, q), oldv, th), FK)
+        keys = [k for k in ("Pt", "Pf", "phi", "mu") if k in prev]
+        gs = torch.autograd.grad(Fo, [prev[k] for k in keys], grad_outputs=lam, allow_unused=True)
         g = {k: torch.zeros_like(v) for k, v in u[n - 1].items()}
-        g["Pt"], g["Pf"], g["phi"] = -gs[0], -gs[1], -gs[2]
+        for k, gk in zip(keys, gs):
+            if gk is not None:
+                g[k] = -gk
     return grad.numpy()
