@@ -600,9 +600,11 @@ def measure_adjoint(args, dev) -> dict:
         # algorithmic bytes of one adjoint PT iteration: cells reads 26 arrays (3 lambda_V, 4 centre
         # multipliers, 3 right-hand sides, phi, 1/(1-phi), 6 Darcy face factors, 5 row factors, V (3))
         # and writes 10 (6 adjoint stresses, 4 multipliers); faces reads 17 (6 stresses, lambda_P,
-        # lambda_L/(1-phi), 3 advection factors, 3 lambda_V, 3 R) and writes 6 (3 R, 3 lambda_V)
+        # lambda_L/(1-phi), 3 advection factors, 3 lambda_V, 3 R) and writes 6 (3 R, 3 lambda_V).
+        # With the power law: edges 10 read + 6 written, cells 49 + 8, faces 20 + 6 (99 arrays).
+        arrays = 99 if p.get("powerlaw_on") else 36 + 23
         if adj_ms > 0:
-            r["adjoint_gbs"] = (36 + 23) * 8 * ncell * rep["iters"] / (adj_ms / 1e3) / 1e9
+            r["adjoint_gbs"] = arrays * 8 * ncell * rep["iters"] / (adj_ms / 1e3) / 1e9
         if grad is not None:
             r["max_rel_diff_vs_first"] = float(np.abs(g - grad).max() / np.abs(grad).max())
         grad = g if grad is None else grad
@@ -613,7 +615,9 @@ def measure_adjoint(args, dev) -> dict:
         adj = {k: (v["launches"], v["ms"]) for k, v in r["kernels"].items() if k in ("k_adj_cells", "k_adj_faces")}
         if adj:
             r["roofline"] = roofline(adj, ncell, clk.get("sm_mhz") if clk else None)
-    out = {"n": n, "steps": N, "target_forward_s": t_target, "runs": runs, "clocks": clk}
+    out = {"n": n, "steps": N, "target_forward_s": t_target, "runs": runs, "clocks": clk,
+           "model": {"powerlaw_on": int(p.get("powerlaw_on", 0)), "R_weak": p["R_weak"], "beta_n": p["beta_n"],
+                     "tau0": p["tau0"], "n_pow": p["n_pow"]}}
     if args.adjoint_fd > 0:
         eps = 1e-6 * float(np.abs(theta).max())
         checks = []

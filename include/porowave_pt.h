@@ -259,9 +259,13 @@ int pt_residual_static(const pt_grid *grid, const pt_phys *phys, const pt_num *n
  * converged implicit steps: for n = N..1, J_F(u^n)^T lambda^n = g^n is solved with the same
  * pseudo-transient scheme as the forward steps on the transposed staggered stencils, the
  * gradient accumulates -(dF/dlogk)^T lambda^n and g^{n-1} = -(dF^n/du^{n-1})^T lambda^n.
- * Scope: power law off (powerlaw_on = 0), no weakening (R_weak = 1), beta_n = 0, and no
- * old-stress refresh inside the window (the window starts at the context's first step and the
- * accumulated time stays below the stress sub-step dtS); other settings return PT_EINVAL.
+ * Scope: no weakening (R_weak = 1: Eq. 25 is a step function), beta_n = 0, no background shear,
+ * and no old-stress refresh inside the window (the window starts at the context's first step
+ * with zero stresses and the accumulated time stays below the stress sub-step dtS); other
+ * settings return PT_EINVAL. With the power law on (Eq. 24) mu is an unknown of each step with
+ * the Picard fixed-point row log mu - log mu*(tau_II), eta = eta0 mu / phi, the Maxwell moduli
+ * 2 mu / (1 + xi) vary per centre and edge, and the step's dtS = max(mu of the previous step) /
+ * (G xsi_w) is differentiated too (into the cell holding that maximum).
  * pt_adjoint_forward runs the N forward steps from the context's current state, keeping a
  * checkpoint of the full state every ckpt_every steps in the adjoint workspace
  * (pt_adjoint_workspace_size bytes, 256-byte aligned, device memory; ckpt_every = 1 stores every
@@ -275,16 +279,18 @@ int pt_adjoint_forward(pt_ctx *ctx, int32_t nsteps, int32_t ckpt_every, void *ad
 int pt_adjoint(pt_ctx *ctx, const double *dJ_dphi, double *dJ_dlogk, pt_report *rep);
 
 /* One application of the transposed operator: out = J_F(u)^T lam, J_F the Jacobian of the
- * residual F = (F_V, F_Pt, F_Pf, F_L) of the implicit step (Eqs. 17-22, same scope as
- * pt_adjoint) at the context's current fields u (k0 e^logk from pt_init). Components are in
- * box layout on the device: lam/out Vx, Vy, Vz on faces (the wall-normal faces of lam must hold
- * zero; those of out are set to zero), Pt, Pf, phi at centres (lam->Pt pairs with F_Pt, ... ,
- * lam->phi with F_L; out->phi is dF/dphi^T lam). Requires a step begun (pt_step or
+ * residual F = (F_V, F_Pt, F_Pf, F_L[, F_mu]) of the implicit step (Eqs. 17-22 and, with the
+ * power law, 24; same scope as pt_adjoint) at the context's current fields u (k0 e^logk from
+ * pt_init; the context's current dtS). Components are in box layout on the device: lam/out Vx,
+ * Vy, Vz on faces (the wall-normal faces of lam must hold zero; those of out are set to zero),
+ * Pt, Pf, phi and mu at centres (lam->Pt pairs with F_Pt, ... , lam->phi with F_L, lam->mu with
+ * F_mu; out->phi is dF/dphi^T lam, out->mu dF/dmu^T lam). Requires a step begun (pt_step or
  * pt_step_begin); workspace: pt_adjoint_workspace_size(grid, 0, 1) bytes of device memory,
  * 256-byte aligned, used as scratch. Synchronises the stream. The thesis has no counterpart:
  * this exists so that the transposed stencils can be checked against an independent Jacobian. */
 typedef struct {
   double *Vx, *Vy, *Vz, *Pt, *Pf, *phi;
+  double *mu;   /* the Picard row / unknown mu (power law on; may be NULL when it is off) */
 } pt_adj_vec;
 int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *workspace, size_t bytes);
 

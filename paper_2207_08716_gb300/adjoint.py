@@ -1,8 +1,8 @@
 """Porosity evolution as a differentiable PyTorch function of the log-permeability field.
 
 ``evolve(logk, params, phi0, nsteps)`` runs `nsteps` implicit steps of the two-phase solver
-(thesis Art. 1, Eqs. 17-27, in the adjoint's scope: power law off, no weakening, beta_n = 0) on
-the GPU and returns the porosity after the last step; its backward is the discrete adjoint of
+(thesis Art. 1, Eqs. 17-27, in the adjoint's scope: no weakening, beta_n = 0; the power law of
+Eq. 24 as the parameters set it) on the GPU and returns the porosity after the last step; its backward is the discrete adjoint of
 the converged steps (pt_adjoint of the C ABI), so ``torch.autograd`` gives dJ/dlogk for any
 objective J of the final porosity. Forward and backward both run in the CUDA library.
 """
@@ -14,9 +14,10 @@ from .solver import PTSolver
 
 
 def adjoint_scope(params: dict) -> dict:
-    """Parameters restricted to the adjoint's scope (power law off, R = 1, beta_n = 0)."""
+    """Parameters restricted to the adjoint's scope: no weakening (R = 1; Eq. 25 is a step
+    function), beta_n = 0, no background shear; the power law (Eq. 24) stays as given."""
     q = dict(params)
-    q.update(powerlaw_on=0, R_weak=1.0, beta_n=0.0, compaction_on=1)
+    q.update(R_weak=1.0, beta_n=0.0, compaction_on=1, tau_bg=0.0)
     return q
 
 

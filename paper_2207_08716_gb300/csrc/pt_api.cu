@@ -1384,8 +1384,10 @@ void pt_batch_destroy(pt_batch* B) {
 namespace {
 
 constexpr int kCkptArrays = 23;   // 14 caller fields, R (3), old stresses (6)
-constexpr int kSegArrays = 6;     // converged Vx, Vy, Vz, Pt, Pf, phi per step of a segment
-constexpr int kAdjArrays = 40;    // multipliers, residual memory, stresses, right-hand sides, coefficients
+constexpr int kSegArrays = 7;     // converged Vx, Vy, Vz, Pt, Pf, phi, mu per step of a segment
+// multipliers, residual memory, stresses, right-hand sides, coefficients (40), and for the power
+// law lambda_mu (2), g_mu, Z (3), the power-law coefficients (26) and an accumulator
+constexpr int kAdjArrays = 73;
 
 int n_ckpts(int nsteps, int every) { return (nsteps + every - 1) / every + 1; }  // + final state
 
@@ -1427,7 +1429,7 @@ int ckpt_io(pt_ctx* c, int slot, bool save) {
 }
 
 bool adjoint_scope_ok(const pt_ctx* c) {
-  return c->phys.powerlaw_on == 0 && c->phys.compaction_on != 0 && c->phys.R_weak == 1.0 &&
+  return c->phys.compaction_on != 0 && c->phys.R_weak == 1.0 && c->phys.tau_bg == 0.0 &&
          c->num.beta_n == 0.0 && !c->mixed && !c->dfm && (c->lean || !c->logk);
 }
 
@@ -1435,7 +1437,9 @@ bool adjoint_scope_ok(const pt_ctx* c) {
 struct AdjArrays {
   double *Lx, *Ly, *Lz, *LRx, *LRy, *LRz, *lP[2], *lF[2], *lL[2], *mL[2];
   double *txx, *tyy, *tzz, *txy, *txz, *tyz, *gP, *gF, *gphi, *gth;
+  double *lM[2], *gM, *Zxy, *Zxz, *Zyz, *acc;
   AdjPrep prep;
+  AdjPrepPL pl;
   double* all[kAdjArrays];
   AdjArrays(char* base, const Box& b) {
     for (int i = 0; i < kAdjArrays; ++i) all[i] = ws_array(base, b, i);
@@ -1447,6 +1451,14 @@ struct AdjArrays {
     gP = A[20]; gF = A[21]; gphi = A[22]; gth = A[23];
     prep = AdjPrep{A[24], A[25], A[26], A[27], A[28], A[29], A[30], A[31], A[32], A[33],
                    A[34], A[35], A[36], A[37], A[38], A[39], nullptr, nullptr};
+    lM[0] = A[40]; lM[1] = A[41]; gM = A[42]; Zxy = A[43]; Zxz = A[44]; Zyz = A[45];
+    double** P = A + 46;
+    pl = AdjPrepPL{P[0], P[1], P[2], P[3], P[4], P[5], P[6], P[7], P[8], P[9], P[10], P[11], P[12],
+                   P[13], P[14], P[15], P[16], P[17], P[18], P[19], P[20], P[21], P[22], P[23], P[24], P[25]};
+    acc = A[72];
+  }
+  AdjEdgeIn edge_in(int cur) const {
+    return AdjEdgeIn{Lx, Ly, Lz, lM[cur], pl.Axy, pl.Axz, pl.Ayz, pl.me_xy, pl.me_xz, pl.me_yz};
   }
   AdjPrep prep_for(int cur) const {
     AdjPrep p = prep;
@@ -1486,6 +1498,13 @@ AdjCoef adjoint_coef(const pt_ctx* c) {
   ac.rrho_i = k.rrho_i;
   ac.damp_x = k.damp_x; ac.damp_y = k.damp_y; ac.damp_z = k.damp_z;
   ac.dtauv = k.dtauv_fac / c->phys.mu0;
+  ac.powerlaw = c->phys.powerlaw_on != 0;
+  ac.Gdt = c->phys.G * c->dtS;           // set per step from that step's dtS
+  ac.rtau0_2 = 1.0 / (c->phys.tau0 * c->phys.tau0);
+  ac.pw = 0.5 * (c->phys.n_pow - 1.0);
+  ac.r_eta0 = 1.0 / c->phys.eta0;
+  ac.dtauv_fac = k.dtauv_fac;
+  ac.dtaupt_fac = k.dtaupt_fac;
   return ac;
 }
 
@@ -1549,8 +1568,10 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
   if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, bytes, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(A.gphi, dJ_dphi, bytes, cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return PT_ECUDA;
-  const AdjCoef ac = adjoint_coef(c);
+  AdjCoef ac = adjoint_coef(c);
+  const bool pl = ac.powerlaw;
   const double* K0 = (c->lean && c->logk) ? c->K0 : nullptr;
+  std::vector<double> seg_dtS((size_t)every + 1, 0.0);   // each kept step's stress sub-step dtS
   long long total_iters = 0;
   pt_report last;
   std::memset(&last, 0, sizeof last);
@@ -1560,11 +1581,12 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
     const int n0 = s * every, n1 = std::min(N, n0 + every);
     // re-run the segment from its checkpoint, keeping every converged state; its last state is
     // the next checkpoint (no recompute at all when every step is checkpointed)
-    double* src[kSegArrays] = {c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0]};
+    double* src[kSegArrays] = {c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu};
     auto keep = [&](int m) {
       for (int f = 0; f < kSegArrays && rc == PT_OK; ++f)
         if (cudaMemcpyAsync(seg(m, f), src[f], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
           rc = PT_ECUDA;
+      seg_dtS[(size_t)m] = c->dtS;
     };
     rc = ckpt_io(c, s, false);
     if (rc == PT_OK) keep(0);
@@ -1579,11 +1601,19 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
     // adjoint steps n1 .. n0+1, warm-started from the previous step's multipliers
     for (int n = n1; n > n0 && rc == PT_OK; --n) {
       const int m = n - n0;
-      const AdjState u{seg(m, 0), seg(m, 1), seg(m, 2), seg(m, 3), seg(m, 4), seg(m, 5)};
-      PT_LAUNCH(c, K_ADJ_PREP, adj_prep(gr, bl, c->stream, b, ac, u, K0, A.prep_for(cur)));
+      const AdjState u{seg(m, 0), seg(m, 1), seg(m, 2), seg(m, 3), seg(m, 4), seg(m, 5), seg(m, 6)};
+      ac.Gdt = c->phys.G * seg_dtS[(size_t)m];
+      if (pl) {
+        // the state's edge stresses go to the Z arrays as scratch (the iteration overwrites them)
+        PT_LAUNCH(c, K_ADJ_PREP, adj_prep_pl(gr, bl, c->stream, b, ac, u, K0, A.prep_for(cur), A.pl, A.Zxy, A.Zxz,
+                                             A.Zyz));
+      } else {
+        PT_LAUNCH(c, K_ADJ_PREP, adj_prep(gr, bl, c->stream, b, ac, u, K0, A.prep_for(cur)));
+      }
       // convergence: residual max-norms below tol times the largest right-hand side |g|
       cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
       PT_LAUNCH(c, K_ADJ_CARRY, adj_gmax(gr, bl, c->stream, b, A.gP, A.gF, A.gphi, c->red));
+      if (pl) PT_LAUNCH(c, K_ADJ_CARRY, adj_gmax(gr, bl, c->stream, b, A.gM, A.gM, A.gM, c->red));
       double gscale = 0.0;
       if (cudaMemcpyAsync(c->h_red, c->red, RED_N * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                           c->stream) != cudaSuccess ||
@@ -1594,15 +1624,27 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
       std::memcpy(&gscale, &c->h_red[RED_GMAX], sizeof gscale);
       int it = 0;
       const int nup = c->num.nup, cap = c->num.max_iter;
+      const AdjFaceIn fi0{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, nullptr, nullptr, A.prep.bfx, A.prep.bfy,
+                          A.prep.bfz, nullptr, nullptr, nullptr, 1, pl ? A.pl.dtvx : nullptr,
+                          pl ? A.pl.dtvy : nullptr, pl ? A.pl.dtvz : nullptr};
       while (gscale > 0.0 && it < cap && rc == PT_OK) {
         ++it;
         const int check = (it % nup) == 0 || it == cap;
         if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
         const AdjCellOut co{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[1 - cur], A.lF[1 - cur],
                             A.lL[1 - cur], A.mL[1 - cur], check ? A.gth : nullptr, nullptr, nullptr, nullptr};
-        PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(cur, K0), co, c->red, check));
-        const AdjFaceIn fi{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[1 - cur], A.mL[1 - cur],
-                           A.prep.bfx, A.prep.bfy, A.prep.bfz, nullptr, nullptr, nullptr, 1};
+        if (pl) {
+          PT_LAUNCH(c, K_ADJ_CELLS, adj_edges_pl(gr, bl, c->stream, b, ac, A.edge_in(cur),
+                                                 AdjEdgeOut{A.txy, A.txz, A.tyz, A.Zxy, A.Zxz, A.Zyz}));
+          const AdjMuIn mi{A.lM[cur], A.gM, A.Zxy, A.Zxz, A.Zyz, A.lM[1 - cur], nullptr};
+          PT_LAUNCH(c, K_ADJ_CELLS, adj_cells_pl(gr, bl, c->stream, b, ac, u, A.cell_in(cur, K0), co, A.pl, mi,
+                                                 c->red, check));
+        } else {
+          PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(cur, K0), co, c->red, check));
+        }
+        AdjFaceIn fi = fi0;
+        fi.lP1 = A.lP[1 - cur];
+        fi.mL = A.mL[1 - cur];
         PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz,
                                             c->red, check));
         cur = 1 - cur;
@@ -1618,6 +1660,20 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
       // gradient and carry into step n-1 (phi_o = phi^{n-1})
       const AdjCarry ca{A.lP[cur], A.lF[cur], A.lL[cur], A.gth, seg(m - 1, 5), grad, A.gP, A.gF, A.gphi};
       PT_LAUNCH(c, K_ADJ_CARRY, adj_carry(gr, bl, c->stream, b, ac, ca));
+      if (pl) {
+        // the power law: this step's dtS = max(mu^{n-1}) / (G xsi_w) carries
+        // -(d(lambda . F)/d(G dtS)) / xsi_w into row mu of step n-1 at the cell holding that maximum
+        cudaMemsetAsync(A.gM, 0, bytes, c->stream);
+        cudaMemsetAsync(A.acc, 0, sizeof(double), c->stream);
+        PT_LAUNCH(c, K_ADJ_CARRY, adj_edges_pl(gr, bl, c->stream, b, ac, A.edge_in(cur),
+                                               AdjEdgeOut{A.txy, A.txz, A.tyz, A.Zxy, A.Zxz, A.Zyz}));
+        PT_LAUNCH(c, K_ADJ_CARRY, adj_dgdt_pl(gr, bl, c->stream, b, ac, u, A.pl, A.Lx, A.Ly, A.Lz, A.lM[cur],
+                                              A.Zxy, A.Zxz, A.Zyz, A.acc));
+        cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+        cudaMemsetAsync(c->red + RED_ARG, 0xff, sizeof(unsigned long long), c->stream);
+        PT_LAUNCH(c, K_ADJ_CARRY, adj_argmax(gr, bl, c->stream, b, seg(m - 1, 6), c->red));
+        PT_LAUNCH(c, K_ADJ_CARRY, adj_add_at(c->stream, b, A.gM, c->red, A.acc, -1.0 / c->num.xsi_w));
+      }
       if (cudaGetLastError() != cudaSuccess) rc = PT_ECUDA;
     }
   }
@@ -1636,6 +1692,8 @@ int pt_adjoint_apply(pt_ctx* c, const pt_adj_vec* lam, pt_adj_vec* out, void* ws
   if (!lam->Vx || !lam->Vy || !lam->Vz || !lam->Pt || !lam->Pf || !lam->phi) return PT_EINVAL;
   if (!out->Vx || !out->Vy || !out->Vz || !out->Pt || !out->Pf || !out->phi) return PT_EINVAL;
   if (!adjoint_scope_ok(c) || c->nsteps < 1) return PT_EINVAL;
+  const bool pl = c->phys.powerlaw_on != 0;
+  if (pl && (!lam->mu || !out->mu)) return PT_EINVAL;
   if (((uintptr_t)ws & (kAlign - 1)) != 0) return PT_EINVAL;
   if (wbytes < pt_adjoint_workspace_size(&c->grid, 0, 1)) return PT_ESPACE;
   int rc = sync_current_to_caller(c);
@@ -1646,23 +1704,33 @@ int pt_adjoint_apply(pt_ctx* c, const pt_adj_vec* lam, pt_adj_vec* out, void* ws
   AdjArrays A((char*)ws, b);
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < kAdjArrays && e == cudaSuccess; ++i) e = cudaMemsetAsync(A.all[i], 0, bytes, c->stream);
-  const double* src[6] = {lam->Vx, lam->Vy, lam->Vz, lam->Pt, lam->Pf, lam->phi};
-  double* dst[6] = {A.Lx, A.Ly, A.Lz, A.lP[0], A.lF[0], A.lL[0]};
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+  const double* src[7] = {lam->Vx, lam->Vy, lam->Vz, lam->Pt, lam->Pf, lam->phi, lam->mu};
+  double* dst[7] = {A.Lx, A.Ly, A.Lz, A.lP[0], A.lF[0], A.lL[0], A.lM[0]};
+  const int nv = pl ? 7 : 6;
+  for (int i = 0; i < nv && e == cudaSuccess; ++i)
     e = cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToDevice, c->stream);
-  double* outs[6] = {out->Vx, out->Vy, out->Vz, out->Pt, out->Pf, out->phi};
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMemsetAsync(outs[i], 0, bytes, c->stream);
+  double* outs[7] = {out->Vx, out->Vy, out->Vz, out->Pt, out->Pf, out->phi, out->mu};
+  for (int i = 0; i < nv && e == cudaSuccess; ++i) e = cudaMemsetAsync(outs[i], 0, bytes, c->stream);
   if (e != cudaSuccess) return PT_ECUDA;
   const AdjCoef ac = adjoint_coef(c);
   const double* K0 = (c->lean && c->logk) ? c->K0 : nullptr;
-  const AdjState u{c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0]};
-  PT_LAUNCH(c, K_ADJ_PREP, adj_prep(gr, bl, c->stream, b, ac, u, K0, A.prep_for(0)));
+  const AdjState u{c->Vx, c->Vy, c->Vz, c->Pt[0], c->Pf[0], c->phi[0], c->mu};
   // with g = 0 the residual rows of the iteration kernels are J^T lambda itself
   const AdjCellOut co{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[1], A.lF[1], A.lL[1], A.mL[1],
                       nullptr, out->Pt, out->Pf, out->phi};
-  PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(0, K0), co, c->red, 0));
+  if (pl) {
+    PT_LAUNCH(c, K_ADJ_PREP, adj_prep_pl(gr, bl, c->stream, b, ac, u, K0, A.prep_for(0), A.pl, A.Zxy, A.Zxz,
+                                         A.Zyz));
+    PT_LAUNCH(c, K_ADJ_CELLS, adj_edges_pl(gr, bl, c->stream, b, ac, A.edge_in(0),
+                                           AdjEdgeOut{A.txy, A.txz, A.tyz, A.Zxy, A.Zxz, A.Zyz}));
+    const AdjMuIn mi{A.lM[0], A.gM, A.Zxy, A.Zxz, A.Zyz, A.lM[1], out->mu};
+    PT_LAUNCH(c, K_ADJ_CELLS, adj_cells_pl(gr, bl, c->stream, b, ac, u, A.cell_in(0, K0), co, A.pl, mi, c->red, 0));
+  } else {
+    PT_LAUNCH(c, K_ADJ_PREP, adj_prep(gr, bl, c->stream, b, ac, u, K0, A.prep_for(0)));
+    PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(0, K0), co, c->red, 0));
+  }
   const AdjFaceIn fi{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[0], A.mL[0],
-                     A.prep.bfx, A.prep.bfy, A.prep.bfz, out->Vx, out->Vy, out->Vz, 0};
+                     A.prep.bfx, A.prep.bfy, A.prep.bfz, out->Vx, out->Vy, out->Vz, 0, nullptr, nullptr, nullptr};
   PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz,
                                       c->red, 0));
   e = cudaGetLastError();

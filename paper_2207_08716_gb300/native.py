@@ -151,7 +151,7 @@ class RxFields(C.Structure):
 
 
 class AdjVec(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("Vx", "Vy", "Vz", "Pt", "Pf", "phi")]
+    _fields_ = [(n, C.c_void_p) for n in ("Vx", "Vy", "Vz", "Pt", "Pf", "phi", "mu")]
 
 
 class KernelTime(C.Structure):

@@ -153,8 +153,9 @@ class PTSolver:
 
     def adjoint_apply(self, lam: dict) -> dict:
         """J_F(u)^T lam at the current fields (pt_adjoint_apply): lam and the result map
-        Vx, Vy, Vz, Pt, Pf, phi (natural shapes; wall-normal faces of lam must be zero)."""
-        keys = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi")
+        Vx, Vy, Vz, Pt, Pf, phi and, with the power law on, mu (natural shapes; wall-normal
+        faces of lam must be zero)."""
+        keys = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi") + (("mu",) if self.params.get("powerlaw_on") else ())
         need = self.lib.pt_adjoint_workspace_size(C.byref(self._grid), 0, 1)
         with torch.cuda.device(self.device):
             ws = torch.empty(need, dtype=torch.uint8, device=self.device)
@@ -163,8 +164,8 @@ class PTSolver:
         for k in keys:
             self._put(lb[k], k, lam[k])
         torch.cuda.current_stream(self.device).synchronize()
-        lv = N.AdjVec(*[lb[k].data_ptr() for k in keys])
-        ov = N.AdjVec(*[ob[k].data_ptr() for k in keys])
+        lv = N.AdjVec(*[lb[k].data_ptr() for k in keys] + [None] * (7 - len(keys)))
+        ov = N.AdjVec(*[ob[k].data_ptr() for k in keys] + [None] * (7 - len(keys)))
         self._check(self.lib.pt_adjoint_apply(self.ctx, C.byref(lv), C.byref(ov), ws.data_ptr(), need),
                     "pt_adjoint_apply")
         out = {}
