@@ -46,6 +46,11 @@ KERNEL_BYTES_PER_CELL = {
     "k_corr_iteration": 26 * 4,
     # adjoint PT iteration: cells reads 26 arrays and writes 10, faces reads 17 and writes 6
     "k_adj_cells": 36 * 8, "k_adj_faces": 23 * 8,
+    # with the power law (Eq. 24): edges read 10 arrays and write 6; cells read 50 (23
+    # multiplier, right-hand-side and row-factor arrays, V, phi, mu, 17 power-law coefficients,
+    # lambda_mu, g_mu, 3 edge Z) and write 8; faces read 20
+    # (the per-face pseudo-steps added) and write 6
+    "k_adj_edges_pl": 16 * 8, "k_adj_cells_pl": 58 * 8, "k_adj_faces_pl": 26 * 8,
     # double-float form (8 B per value): cells reads 22 arrays (V, Pt, Pf, phi, k, Pto, Pfo, phio,
     # ieta, idtp, cm2, 3 toa_ii, 3 edge moduli, 3 toa_e) and writes 10 (Pt, Pf, phi, k, 6 stresses); faces
     # reads 15 (6 stresses, Pt, phi, centre dtau_V, 3 R, 3 V) and writes 6; Picard reads 11 and
@@ -68,7 +73,8 @@ KERNEL_SOURCES = {
        for k in ("k_lean_cells", "k_lean_faces", "k_lean_picard", "k_lean_coef", "k_lean_cells_df64",
                  "k_lean_faces_df64", "k_lean_picard_df64", "k_lean_coef_df64")},
     "k_centres": ("pt_ref_kernels.cu", "pt_kernels.cuh", "pt_common.cuh"),
-    "k_adj_cells": ("pt_adjoint_kernels.cu", "pt_adjoint.cuh", "pt_common.cuh"),
+    **{k: ("pt_adjoint_kernels.cu", "pt_adjoint.cuh", "pt_common.cuh")
+       for k in ("k_adj_cells", "k_adj_faces", "k_adj_edges_pl", "k_adj_cells_pl", "k_adj_faces_pl")},
     "k_corr_iteration": ("pt_mixed_kernels.cu", "pt_mixed.cuh", "pt_common.cuh"),
     "k_mg_smooth_fp32": ("rx_mg_kernels.cu", "rx.cuh"),
 }
@@ -128,8 +134,9 @@ def parse():
     ap.add_argument("--precision", choices=tuple(PRECISIONS), default="df64",
                     help="df64: the FP64-lean iteration in double-float arithmetic (FP64 oracle parity 1e-10); "
                          "fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
-    ap.add_argument("--forms", default="fp64,fp32,batched", help="extra forms measured after the headline one "
-                    "(comma list of fp64, df64, fp32, fp64-stepwise, batched; '' for none)")
+    ap.add_argument("--forms", default="fp64,fp32,batched,batched32", help="extra forms measured after the headline one "
+                    "(comma list of fp64, df64, fp32, fp64-stepwise, batched (FP64 ensemble), batched32 (FP32 "
+                    "ensemble); '' for none)")
     ap.add_argument("--no-own-peaks", action="store_true",
                     help="skip the library's own copy / FP64 / FP32 peak measurements")
     ap.add_argument("--fp32-iters", type=int, default=300, help="FP32 iterations per step of the fp32 form")
@@ -162,11 +169,14 @@ def parse():
                     help="precision of the batched ensemble (fp32: defect-correction solvers stepped "
                          "concurrently, each on its own stream)")
     ap.add_argument("--precision-check", action="store_true",
-                    help="porosity of the FP32 form against the FP64 form (and the oracle at 32^3) after "
-                         "--pc-steps converged physical steps of the c1 workload at each --pc-n")
-    ap.add_argument("--pc-n", default="32,64", help="grid sizes of the precision check")
-    ap.add_argument("--pc-steps", type=int, default=50)
-    ap.add_argument("--pc-oracle", type=int, default=1, help="also run the oracle at 32^3 (1) or not (0)")
+                    help="porosity of the FP32 form against an FP64-class form (and the oracle at the "
+                         "--pc-oracle-n sizes) after converged physical steps of the c1 workload at each --pc-n")
+    ap.add_argument("--pc-n", default="32,64", help="grid sizes of the precision check, n[:steps] each")
+    ap.add_argument("--pc-steps", type=int, default=50, help="converged steps where --pc-n gives none")
+    ap.add_argument("--pc-ref", choices=("fp64", "df64"), default="fp64",
+                    help="the FP64-class form the FP32 form is compared with")
+    ap.add_argument("--pc-oracle", type=int, default=1, help="also run the oracle (1) or not (0)")
+    ap.add_argument("--pc-oracle-n", default="32", help="grid sizes at which the oracle runs too")
     ap.add_argument("--batch-inner-rtol", type=float, default=0.0,
                     help="FP32 ensembles: relative residual drop of each FP32 correction solve (0: library default)")
     ap.add_argument("--batched-converge", action="store_true",
@@ -479,14 +489,16 @@ def measure_form(args, precision: str, iters: int, steps: int, warmup: int, e2e_
     return out
 
 
-def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, converge: bool = False) -> dict:
+def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, converge: bool = False,
+                    fp32: bool | None = None) -> dict:
     """The batched ensemble (64 instances, sizes {32,48,64,96,127}^3, seeded parameters and
     anomalies; seed = rank): aggregate cell updates per second over `steps` physical steps of
     `--batch-iters` PT iterations each, or one step to convergence with time-to-converge."""
     import torch
     from paper_2207_08716_gb300.solver import PTBatch
 
-    fp32 = getattr(args, "batch_precision", "fp64") == "fp32"
+    if fp32 is None:
+        fp32 = getattr(args, "batch_precision", "fp64") == "fp32"
     # the FP32 form counts its inner FP32 iterations, 2-4x the FP64 form's iterations (at least
     # nup of them per outer Picard update)
     mem = I.ensemble(seed=M.replica_seed(rank), n_inst=args.batch_n, max_iter=160000 if fp32 else 40000)
@@ -519,13 +531,16 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
     clk = clocks.stop()
     upd = M.sum_over_ranks(float(sum(c * it for c, it in zip(cells, iters))), dev)
     bx, by, ipg = b.config()
-    out = {"value": M.a_eff_bytes(1, 8) * upd / t / 1e9, "unit": "GB/s",
+    pbytes = 4 if fp32 else 8
+    out = {"value": M.a_eff_bytes(1, pbytes) * upd / t / 1e9, "unit": "GB/s",
            "cell_updates_per_s": upd / t, "instances": len(cells), "total_cells": sum(cells),
            "iters_per_step": None if converge else args.batch_iters, "seconds": t,
            "tile": [bx, by], "iters_per_graph": ipg, "clocks": clk,
            "precision": "fp32" if fp32 else "fp64",
-           "value_definition": "T_eff-equivalent: 25 x 8 B x aggregate cell updates per second"
+           "value_definition": f"T_eff-equivalent: 25 x {pbytes} B x aggregate cell updates per second"
                                + (" (FP32: inner FP32 PT iterations)" if fp32 else "")}
+    if fp32:
+        out["corr_tile_z"], out["corr_blocks_per_sm"] = b.config_fp32()
     if converge:
         st = sorted(ttc_all)
         out.update(statuses=[r["status"] for r in reps], iters=[r["iters"] for r in reps],
@@ -536,6 +551,10 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
     del b
     torch.cuda.empty_cache()
     return out
+
+
+# the kernels of one adjoint PT iteration (without and with the power law)
+ADJ_ITER_KERNELS = ("k_adj_cells", "k_adj_faces", "k_adj_edges_pl", "k_adj_cells_pl", "k_adj_faces_pl")
 
 
 def measure_adjoint(args, dev) -> dict:
@@ -589,7 +608,7 @@ def measure_adjoint(args, dev) -> dict:
         kernels = s.profile_end()
         launches = s.launch_count() - launches0
         g = g.cpu().numpy()
-        adj_ms = sum(kernels.get(k, (0, 0.0))[1] for k in ("k_adj_cells", "k_adj_faces"))
+        adj_ms = sum(kernels.get(k, (0, 0.0))[1] for k in ADJ_ITER_KERNELS)
         r = {"ckpt_every": every, "forward_s": t_fwd, "backward_s": t_bwd, "cost_multiple": t_bwd / t_fwd,
              "forward_pt_iters": sum(x["iters"] for x in reps), "adjoint_pt_iters": rep["iters"],
              "adjoint_ms_per_iter": adj_ms / max(rep["iters"], 1),
@@ -601,8 +620,8 @@ def measure_adjoint(args, dev) -> dict:
         # multipliers, 3 right-hand sides, phi, 1/(1-phi), 6 Darcy face factors, 5 row factors, V (3))
         # and writes 10 (6 adjoint stresses, 4 multipliers); faces reads 17 (6 stresses, lambda_P,
         # lambda_L/(1-phi), 3 advection factors, 3 lambda_V, 3 R) and writes 6 (3 R, 3 lambda_V).
-        # With the power law: edges 10 read + 6 written, cells 49 + 8, faces 20 + 6 (99 arrays).
-        arrays = 99 if p.get("powerlaw_on") else 36 + 23
+        # With the power law: edges 10 read + 6 written, cells 50 + 8, faces 20 + 6 (100 arrays).
+        arrays = 100 if p.get("powerlaw_on") else 36 + 23
         if adj_ms > 0:
             r["adjoint_gbs"] = arrays * 8 * ncell * rep["iters"] / (adj_ms / 1e3) / 1e9
         if grad is not None:
@@ -610,9 +629,11 @@ def measure_adjoint(args, dev) -> dict:
         grad = g if grad is None else grad
         runs.append(r)
         s.close()
+        print(json.dumps({"adjoint_run": {k: v for k, v in r.items() if k != "kernels"}}), file=sys.stderr,
+              flush=True)
     clk = clocks.stop()
     for r in runs:
-        adj = {k: (v["launches"], v["ms"]) for k, v in r["kernels"].items() if k in ("k_adj_cells", "k_adj_faces")}
+        adj = {k: (v["launches"], v["ms"]) for k, v in r["kernels"].items() if k in ADJ_ITER_KERNELS}
         if adj:
             r["roofline"] = roofline(adj, ncell, clk.get("sm_mhz") if clk else None)
     out = {"n": n, "steps": N, "target_forward_s": t_target, "runs": runs, "clocks": clk,
@@ -628,6 +649,7 @@ def measure_adjoint(args, dev) -> dict:
             fd = (Jp - Jm) / (2 * eps)
             ad = float(np.sum(grad * v))
             checks.append({"seed": 10 + d, "adjoint": ad, "fd": fd, "rel": abs(ad - fd) / abs(fd)})
+            print(json.dumps({"fd_check": checks[-1]}), file=sys.stderr, flush=True)
         out["fd_checks"] = checks
         out["fd_eps"] = eps
     torch.cuda.empty_cache()
@@ -684,15 +706,62 @@ def measure_reactive(args, dev) -> dict:
     return out
 
 
+def _oracle_steps_job(n: int, nsteps: int, out_path: str) -> dict:
+    """The oracle's `nsteps` converged physical steps of the c1 workload at n^3 (run in a child
+    process by the precision check); the final porosity goes to `out_path` (.npy)."""
+    import oracle as O
+    p = I.c1_params(n)
+    p["max_iter"] = 400000
+    st = O.make_state(p, I.gaussian_porosity(p))
+    iters, t0 = [], time.perf_counter()
+    for _ in range(nsteps):
+        rc, it, _ = O.step(st)
+        if rc != 0:
+            raise RuntimeError(f"oracle rc {rc}")
+        iters.append(it)
+    dt = time.perf_counter() - t0
+    np.save(out_path, st["phi"])
+    return {"n": n, "steps": nsteps, "iters": iters, "seconds": dt, "cores": O.max_threads()}
+
+
+def _parse_sizes(spec: str, default_steps: int) -> list:
+    """'127:3,511:1,32' -> [(127, 3), (511, 1), (32, default_steps)]."""
+    out = []
+    for tok in spec.split(","):
+        tok = tok.strip()
+        if tok:
+            n, _, k = tok.partition(":")
+            out.append((int(n), int(k) if k else default_steps))
+    return out
+
+
 def measure_precision(args, dev) -> dict:
-    """The FP32 + FP64 defect-correction form against the FP64-lean form after --pc-steps
-    converged physical steps of the c1 workload (one centred anomaly), n^3 cells per --pc-n, both
-    on the GPU from the same state; at 32^3 also against the FP64 oracle's converged steps.
+    """The FP32 + FP64 defect-correction form against an FP64-class form (--pc-ref: the FP64-lean
+    or the double-float form, which matches the FP64 oracle to 1e-10) after converged physical
+    steps of the c1 workload (one centred anomaly), both on the GPU from the same state; at the
+    sizes of --pc-oracle-n also against the FP64 oracle's converged steps, which run on the host
+    cores in a child process started before the first GPU call. --pc-n lists n[:steps] entries.
     Porosity error = max |phi - phi_ref| / max |phi_ref| and, more telling, relative to the
     porosity change over the run, max |phi - phi_ref| / max |phi_ref - phi_initial|."""
+    import subprocess
+    import tempfile
     import torch
     from paper_2207_08716_gb300 import native as N
     from paper_2207_08716_gb300.solver import PTSolver
+
+    sizes = _parse_sizes(args.pc_n, args.pc_steps)
+    oracle_n = {int(v) for v in str(args.pc_oracle_n).split(",") if v.strip()} if args.pc_oracle else set()
+    ref_prec = {"fp64": N.PT_FP64, "df64": N.PT_DF64}[args.pc_ref]
+    tmp = tempfile.mkdtemp(prefix="pc_oracle_")
+    children = {}
+    ncores = os.cpu_count() or 1
+    for n, k in sizes:
+        if n in oracle_n:
+            path = os.path.join(tmp, f"phi_{n}.npy")
+            code = f"import json, bench; print('ORACLE ' + json.dumps(bench._oracle_steps_job({n}, {k}, {path!r})))"
+            env = dict(os.environ, OMP_NUM_THREADS=str(max(1, ncores - 1)))
+            children[n] = (subprocess.Popen([sys.executable, "-c", code], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                                            stderr=subprocess.PIPE, text=True), path)
 
     def run(p, phi0, nsteps):
         s = PTSolver(p, phi0, device=dev)
@@ -710,30 +779,35 @@ def measure_precision(args, dev) -> dict:
         d = float(np.abs(a - ref).max())
         return {"max_rel": d / float(np.abs(ref).max()), "rel_to_change": d / float(np.abs(ref - phi0).max())}
 
-    out = {}
-    for n in [int(v) for v in args.pc_n.split(",") if v.strip()]:
+    out = {"reference_form": args.pc_ref}
+    for n, k in sizes:
         p = I.c1_params(n)
         p["max_iter"] = 400000
         phi0 = I.gaussian_porosity(p)
-        phi64, it64, t64 = run(dict(p, precision=N.PT_FP64), phi0, args.pc_steps)
-        phi32, it32, t32 = run(dict(p, precision=N.PT_FP32), phi0, args.pc_steps)
-        r = {"steps": args.pc_steps, "fp64_iters": sum(it64), "fp32_iters": sum(it32), "fp64_s": t64,
-             "fp32_s": t32, "fp32_vs_fp64": errs(phi32, phi64, phi0),
-             "porosity_change_max": float(np.abs(phi64 - phi0).max())}
-        if n == 32 and args.pc_oracle:
-            import oracle as O
-            st = O.make_state(p, phi0)
-            t0 = time.perf_counter()
-            for _ in range(args.pc_steps):
-                rc, _, _ = O.step(st)
-                if rc != 0:
-                    raise RuntimeError(f"oracle rc {rc}")
-            r["oracle_s"] = time.perf_counter() - t0
-            phio = st["phi"]
-            r["fp64_vs_oracle"] = errs(phi64, phio, phi0)
-            r["fp32_vs_oracle"] = errs(phi32, phio, phi0)
+        phi64, it64, t64 = run(dict(p, precision=ref_prec), phi0, k)
+        phi32, it32, t32 = run(dict(p, precision=N.PT_FP32), phi0, k)
+        r = {"steps": k, "ref_iters": sum(it64), "fp32_iters": sum(it32), "ref_s": t64, "fp32_s": t32,
+             "fp32_vs_ref": errs(phi32, phi64, phi0), "porosity_change_max": float(np.abs(phi64 - phi0).max())}
+        print(json.dumps({"precision_check": {str(n): r}}), file=sys.stderr, flush=True)
+        if n in children:
+            proc, path = children.pop(n)
+            so, se = proc.communicate()
+            line = [l for l in so.splitlines() if l.startswith("ORACLE ")]
+            if proc.returncode != 0 or not line:
+                r["oracle_error"] = (se or "")[-300:]
+            else:
+                rec = json.loads(line[-1][7:])
+                phio = np.load(path)
+                r["oracle_s"], r["oracle_iters"], r["oracle_cores"] = rec["seconds"], sum(rec["iters"]), rec["cores"]
+                r["ref_vs_oracle"] = errs(phi64, phio, phi0)
+                r["fp32_vs_oracle"] = errs(phi32, phio, phi0)
+                os.remove(path)
         out[str(n)] = r
         torch.cuda.empty_cache()
+    for proc, _ in children.values():
+        proc.kill()
+    if not os.listdir(tmp):
+        os.rmdir(tmp)
     return out
 
 
@@ -841,8 +915,9 @@ def run_native(args):
         if rank == 0:
             r = measure_precision(args, dev)
             print(json.dumps({"metric": "porosity error of the FP32 form after converged steps", "unit": "max rel",
-                              "config": {"workload": f"c1 workload (one centred anomaly), {args.pc_steps} "
-                                                     f"converged physical steps per grid"}, "grids": r}), flush=True)
+                              "config": {"workload": "c1 workload (one centred anomaly), converged physical "
+                                                     f"steps per grid (n:steps) {args.pc_n}",
+                                         "reference_form": args.pc_ref}, "grids": r}), flush=True)
         return 0
     if args.reactive_mg:
         if rank == 0:
@@ -885,8 +960,8 @@ def run_native(args):
         head["e2e"] = runs[0]["e2e"]
     forms = {}
     for f in [x for x in args.forms.split(",") if x and x != args.precision]:
-        if f == "batched":
-            forms[f] = measure_batched(args, max(2, args.steps // 2), 1, dev, world, rank)
+        if f in ("batched", "batched32"):
+            forms[f] = measure_batched(args, max(2, args.steps // 2), 1, dev, world, rank, fp32=f == "batched32")
         elif f in PRECISIONS:
             it = args.fp32_iters if f == "fp32" else args.iters
             forms[f] = measure_form(args, f, it, max(2, args.steps // 2), 2, 0, dev, world, rank, local_rank,
@@ -914,7 +989,7 @@ def run_native(args):
             "clocks": head["clocks"], "kernels": head["kernels"], "own_peaks": own,
             "forms": {k: ({kk: v[kk] for kk in ("value", "unit", "p_bytes", "it_per_s", "t_it_ms",
                                                   "teff_frac_of_hbm", "iters_per_step", "roofline",
-                                                  "gpu_launches", "clocks")} if k != "batched" else v)
+                                                  "gpu_launches", "clocks")} if not k.startswith("batched") else v)
                       for k, v in forms.items()},
         }
         print(json.dumps(line), flush=True)

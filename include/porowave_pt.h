@@ -120,6 +120,13 @@ typedef struct {
   int32_t iters_per_graph;/* PT iterations per CUDA-graph replay; 0 = nup                  */
   double inner_rtol;      /* PT_FP32: each FP32 correction solve stops at this relative drop
                            * of its residual (0 = 0.1)                                     */
+  int32_t mg_levels;      /* PT_FP32: 0 or 1 = each correction problem is solved by FP32 PT
+                           * iterations; L >= 2 = by geometric-multigrid V-cycles over L grids
+                           * (each 2x coarser per direction; nx, ny, nz divisible by 2^(L-1),
+                           * the coarsest at least 2 cells per direction), smoothed by the PT
+                           * sweep (see pt_mixed_kernels.cu); PT_EINVAL otherwise, and for
+                           * batched ensembles                                               */
+  int32_t mg_reserved;    /* 0                                                              */
 } pt_num;
 
 /* Caller-owned device fields, padded box layout above. logk may be NULL (logk = 0). */
@@ -296,20 +303,26 @@ int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *
 
 /* ---- Batched ensemble --------------------------------------------------------------------
  * ninst independent instances (each its own grid, parameters, fields and numerics), all
- * PT_FP64 or all PT_FP32 (mixing returns PT_EINVAL). FP32 ensembles: every instance runs the
- * FP32 + FP64 defect-correction pt_step, whose outer and inner iterations are decided per
- * instance, on a stream of its own, the instances stepped concurrently by one host thread each;
- * time_to_converge_ms is host time from the common start to the instance's return, and
- * pt_batch_config reports zeros. FP64 ensembles (the FP64-lean form) are advanced together: one launch per PT phase covers all instances
- * through a flat work list of (instance, tile) items walked by a persistent grid-stride grid, and
- * 2 nup (or 4 nup) iterations are captured in one CUDA graph per replay. Each instance stops at
- * its own first check with norms < tol (or at its max_iter / a non-finite norm), exactly where
- * its single-instance pt_step would, and reproduces that run bit for bit. The first
- * pt_batch_step tunes the tile shape (32x4, 32x8, 64x4) and the iterations per graph by timing
- * graph replays (tuning replays are real iterations: the arithmetic does not depend on them).
- * grids/phys/nums/fields are arrays of ninst; the workspace holds every instance's workspace
- * (pt_workspace_size) plus the descriptor table. The batch works on a stream of its own
- * (graphs cannot be captured on the legacy default stream): pt_batch_init and pt_batch_step
+ * PT_FP64 or all PT_FP32 (mixing returns PT_EINVAL), advanced together by one persistent engine:
+ * one launch per phase covers all instances through a flat work list of (instance, tile) items
+ * walked by a persistent grid-stride grid (SMs x resident CTAs), the launch sequence captured
+ * in one CUDA graph per replay, and every decision (convergence, iteration cap, non-finite
+ * norms) taken on the device per instance; the host reads a status table once per replay.
+ * FP64 ensembles (the FP64-lean form): 2 nup (or 4 nup) PT iterations per replay; each instance
+ * stops at its own first check with norms < tol (or at its max_iter / a non-finite norm). The
+ * first pt_batch_step tunes the tile shape (32x4, 32x8, 64x4) and the iterations per replay.
+ * FP32 ensembles (the FP32 + FP64 defect-correction form): a replay runs `rounds` rounds of
+ * [FP64 residuals, stresses and Picard update of the instances starting an outer iteration;
+ * their outer decision (converged, outer weight, inner target); nup FP32 correction iterations
+ * of the instances in a correction solve; their inner decision (relative drop reached or budget
+ * spent); the FP64 update and porosity integration of the instances ending one]. The first
+ * pt_batch_step tunes the correction tile depth (32, 64, 128 levels), the CTAs per SM of the
+ * correction kernel (3, 4) and the rounds per replay (1, 2).
+ * Either way each instance reproduces its single-instance pt_step bit for bit (same per-point
+ * code, same decisions in the same order), whatever the configuration (tuning replays are real
+ * iterations). grids/phys/nums/fields are arrays of ninst; the workspace holds every instance's
+ * workspace (pt_workspace_size) plus the descriptor tables. The batch works on a stream of its
+ * own (graphs cannot be captured on the legacy default stream): pt_batch_init and pt_batch_step
  * first synchronise the caller's `stream`, and pt_batch_step returns after its work is done. */
 typedef struct pt_batch pt_batch;
 size_t pt_batch_workspace_size(int32_t ninst, const pt_grid *grids, const pt_num *nums);
@@ -320,9 +333,13 @@ int pt_batch_init(pt_batch **batch, int32_t ninst, const pt_grid *grids, const p
  * time_to_converge_ms[ninst] (may be NULL) its device time from the step's first iteration to
  * its stop. Returns PT_OK when every instance converged, PT_ENOTCONV if any hit its cap. */
 int pt_batch_step(pt_batch *batch, pt_report *reps, double *time_to_converge_ms);
-/* The tuned configuration (valid after the first pt_batch_step). */
+/* The tuned configuration (valid after the first pt_batch_step): the tile's x and y extents
+ * (FP32 ensembles: the correction tile, 30 x 6 faces) and the (correction) iterations per replay. */
 int pt_batch_config(const pt_batch *batch, int32_t *tile_x, int32_t *tile_y,
                     int32_t *iters_per_graph);
+/* FP32 ensembles: the tuned correction tile depth (z levels) and CTAs per SM of the correction
+ * kernel; PT_EINVAL for an FP64 ensemble. */
+int pt_batch_config_fp32(const pt_batch *batch, int32_t *tile_z, int32_t *blocks_per_sm);
 void pt_batch_destroy(pt_batch *batch);
 
 /* ---- Sub-domain (halo-exchange) form (Art. 1 Section 2.2) ----------------------------------

@@ -14,7 +14,6 @@
 #include <new>
 #include <array>
 #include <chrono>
-#include <thread>
 #include <vector>
 
 #include "../../include/porowave_pt.h"
@@ -115,7 +114,8 @@ enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEG
                 K_RESIDUAL_FACES, K_LEAN_CELLS, K_LEAN_FACES, K_LEAN_PICARD, K_LEAN_COEF, K_LEAN_BEGIN,
                 K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_ITER,
                 K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_DF_CELLS, K_DF_FACES,
-                K_DF_PICARD, K_DF_COEF, K_DF_BEGIN, K_DF_K0, K_DF_CONVERT, K_COUNT };
+                K_DF_PICARD, K_DF_COEF, K_DF_BEGIN, K_DF_K0, K_DF_CONVERT, K_ADJ_EDGES_PL, K_ADJ_CELLS_PL,
+                K_ADJ_FACES_PL, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
@@ -125,7 +125,8 @@ const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_
                                            "k_adj_prep", "k_adj_cells", "k_adj_faces", "k_adj_carry",
                                            "k_lean_cells_df64", "k_lean_faces_df64", "k_lean_picard_df64",
                                            "k_lean_coef_df64", "k_lean_begin_df64", "k_lean_k0_df64",
-                                           "k_df64_convert"};
+                                           "k_df64_convert", "k_adj_edges_pl", "k_adj_cells_pl",
+                                           "k_adj_faces_pl"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -1023,17 +1024,29 @@ struct pt_batch {
   int nslabs, slab_elems;
   DDTables tables;
   std::vector<std::array<int, 6>> own;   // per instance: own_lo[3], own_hi[3]
-  // FP32 ensembles (every instance PT_FP32): the defect-correction loop's outer and inner
-  // iterations are decided per instance on the host, so the instances run as independent
-  // solvers, each on a stream of its own, stepped concurrently by one host thread per instance
-  bool concurrent;
-  std::vector<cudaStream_t> streams;
+  // FP32 ensembles (every instance PT_FP32): the defect-correction engine of pt_mixed.cuh, its
+  // decisions taken on the device per member; one graph replay = `mult` rounds of nup
+  // correction iterations with the outer phases between them
+  bool mixed;
+  std::vector<MixBatchInst> h_minst;
+  MixBatchInst* d_minst;
+  MixBatchStatus* d_mst;
+  MixBatchStatus* h_mst;
+  unsigned long long* d_ired;
+  int zchunk, minb, mult;   // correction tile depth, CTAs per SM of the correction kernel, rounds per replay
+  long long nptiles, nctiles;
+  int pgrid, cgrid;
+  int exec_zchunk, exec_minb, exec_mult;
 };
 
 namespace {
 
+// Descriptor tables: the FP64 engine's (instances, statuses), then the FP32 engine's (members,
+// statuses, inner reduction slots).
 size_t batch_table_bytes(int ninst) {
-  return align_up(sizeof(BatchInst) * ninst, kAlign) + align_up(sizeof(BatchStatus) * ninst, kAlign);
+  return align_up(sizeof(BatchInst) * ninst, kAlign) + align_up(sizeof(BatchStatus) * ninst, kAlign) +
+         align_up(sizeof(MixBatchInst) * ninst, kAlign) + align_up(sizeof(MixBatchStatus) * ninst, kAlign) +
+         align_up(sizeof(unsigned long long) * RED_N * ninst, kAlign);
 }
 
 // Descriptor of instance m for the batch's tile shape (pointers of both ping-pong parities).
@@ -1145,6 +1158,205 @@ int batch_active(pt_batch* B, int* nactive) {
   return PT_OK;
 }
 
+// ---- FP32 ensembles: descriptors, graph and decisions of the device-side engine
+void fill_mix_inst(pt_batch* B, int m, long long base, long long cbase) {
+  pt_ctx* c = B->ctx[m];
+  MixBatchInst& I = B->h_minst[m];
+  I.b = c->box;
+  I.k = c->coef;
+  I.lc = c->lcoef;
+  I.cc = c->ccoef;
+  I.Vx = c->Vx; I.Vy = c->Vy; I.Vz = c->Vz;
+  for (int a = 0; a < 2; ++a) {
+    I.Pt[a] = c->Pt[a]; I.Pf[a] = c->Pf[a]; I.phi[a] = c->phi[a];
+    I.dVx[a] = c->m_dVx[a]; I.dVy[a] = c->m_dVy[a]; I.dVz[a] = c->m_dVz[a];
+    I.dPt[a] = c->m_dPt[a]; I.dPf[a] = c->m_dPf[a];
+  }
+  I.mu = c->mu; I.eta = c->eta; I.perm = c->perm; I.rog = c->rog; I.Pto = c->Pto; I.Pfo = c->Pfo; I.Lo = c->Lo;
+  I.logk = c->logk;
+  I.txxo = c->txxo; I.tyyo = c->tyyo; I.tzzo = c->tzzo; I.txyo = c->txyo; I.txzo = c->txzo; I.tyzo = c->tyzo;
+  I.s_txx = c->s_txx; I.s_tyy = c->s_tyy; I.s_tzz = c->s_tzz; I.s_txy = c->s_txy; I.s_txz = c->s_txz;
+  I.s_tyz = c->s_tyz;
+  I.rpt = c->m_rpt; I.rpf = c->m_rpf; I.rfx = c->m_rfx; I.rfy = c->m_rfy; I.rfz = c->m_rfz;
+  I.ccf = c->m_cc; I.kf = c->m_perm; I.idtp = c->m_idtp; I.muf = c->m_mu; I.dtvc = c->m_dtvc;
+  I.Rx = c->m_Rx; I.Ry = c->m_Ry; I.Rz = c->m_Rz;
+  for (int d = 0; d < 2; ++d) {
+    I.cin[d] = CorrIn<float>{I.dVx[d], I.dVy[d], I.dVz[d], I.dPt[d], I.dPf[d], I.ccf, I.kf, I.idtp, I.rpt,
+                             I.rpf, I.muf, I.dtvc, I.rfx, I.rfy, I.rfz};
+    I.cout[d] = CorrOut<float>{I.dVx[1 - d], I.dVy[1 - d], I.dVz[1 - d], I.dPt[1 - d], I.dPf[1 - d], I.Rx, I.Ry,
+                               I.Rz};
+  }
+  I.red = c->red;
+  I.ired = B->d_ired + (size_t)RED_N * m;
+  I.tol = c->num.tol;
+  I.rtol = c->num.inner_rtol > 0 ? c->num.inner_rtol : kInnerRtol;
+  I.max_iter = c->num.max_iter;
+  I.gx = (c->box.nx + 1 + 31) / 32;
+  I.gy = (c->box.ny + 1 + 7) / 8;
+  I.cgx = (c->box.nx + 1 + corr_tile_x() - 1) / corr_tile_x();
+  I.cgy = (c->box.ny + 1 + corr_tile_y() - 1) / corr_tile_y();
+  I.cgz = (c->box.nz + 1 + B->zchunk - 1) / B->zchunk;
+  I.tile_base = base;
+  I.ctile_base = cbase;
+}
+
+cudaError_t upload_mix(pt_batch* B) {
+  long long base = 0, cbase = 0;
+  for (int m = 0; m < B->ninst; ++m) {
+    fill_mix_inst(B, m, base, cbase);
+    const MixBatchInst& I = B->h_minst[m];
+    base += (long long)I.gx * I.gy * (I.b.nz + 1);
+    cbase += (long long)I.cgx * I.cgy * I.cgz;
+  }
+  B->nptiles = base;
+  B->nctiles = cbase;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  B->pgrid = std::max(1, sms * mb_points_blocks_per_sm());
+  B->cgrid = std::max(1, sms * mb_corr_blocks_per_sm(B->minb));
+  return cudaMemcpyAsync(B->d_minst, B->h_minst.data(), sizeof(MixBatchInst) * B->ninst, cudaMemcpyHostToDevice,
+                         B->stream);
+}
+
+// One replay: `mult` rounds of the engine (outer phases, nup correction iterations, update).
+void record_mix_rounds(pt_batch* B) {
+  const int n = B->ninst;
+  for (int r = 0; r < B->mult; ++r) {
+    mb_points(B->pgrid, B->stream, MB_PH_PERM, B->d_minst, B->d_mst, n, B->nptiles);
+    mb_points(B->pgrid, B->stream, MB_PH_PREP, B->d_minst, B->d_mst, n, B->nptiles);
+    mb_points(B->pgrid, B->stream, MB_PH_FACES, B->d_minst, B->d_mst, n, B->nptiles);
+    mb_decide_outer(B->stream, B->d_minst, B->d_mst, n);
+    mb_points(B->pgrid, B->stream, MB_PH_INIT, B->d_minst, B->d_mst, n, B->nptiles);
+    for (int s = 1; s <= B->nup; ++s)
+      mb_corr(B->cgrid, B->minb, B->stream, B->d_minst, B->d_mst, n, B->nctiles, s, B->nup, B->zchunk);
+    mb_decide_inner(B->stream, B->d_minst, B->d_mst, n, B->nup);
+    mb_points(B->pgrid, B->stream, MB_PH_UPDATE, B->d_minst, B->d_mst, n, B->nptiles);
+    mb_points(B->pgrid, B->stream, MB_PH_POROSITY, B->d_minst, B->d_mst, n, B->nptiles);
+    mb_finish(B->stream, B->d_minst, B->d_mst, n);
+  }
+}
+
+int build_mix_graph(pt_batch* B) {
+  if (B->exec && B->exec_zchunk == B->zchunk && B->exec_minb == B->minb && B->exec_mult == B->mult) return PT_OK;
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PT_ECUDA;
+  record_mix_rounds(B);
+  cudaError_t e = cudaStreamEndCapture(B->stream, &g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    B->exec = nullptr;
+    return PT_ECUDA;
+  }
+  B->exec_zchunk = B->zchunk;
+  B->exec_minb = B->minb;
+  B->exec_mult = B->mult;
+  return PT_OK;
+}
+
+int mix_active(pt_batch* B, int* nactive) {
+  cudaError_t e = cudaMemcpyAsync(B->h_mst, B->d_mst, sizeof(MixBatchStatus) * B->ninst, cudaMemcpyDeviceToHost,
+                                  B->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) return PT_ECUDA;
+  int n = 0;
+  for (int m = 0; m < B->ninst; ++m) n += B->h_mst[m].phase != MB_DONE;
+  *nactive = n;
+  return PT_OK;
+}
+
+// FP32 ensemble step: every member's step begin (host, as pt_step), then graph replays until
+// every member is done; the first step times one replay of each candidate configuration
+// (correction tile depth, CTAs per SM, rounds per replay) and keeps the fastest per round.
+int batch_step_mixed(pt_batch* B, pt_report* reps, double* ttc_ms) {
+  int rc = PT_OK;
+  int cap = 0;
+  for (int m = 0; m < B->ninst && rc == PT_OK; ++m) {
+    rc = pt_step_begin(B->ctx[m]);
+    cap = std::max(cap, B->ctx[m]->num.max_iter);
+  }
+  if (rc != PT_OK) return rc;
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return PT_ECUDA;
+  if (upload_mix(B) != cudaSuccess) return PT_ECUDA;
+  mb_start(B->stream, B->d_minst, B->d_mst, B->ninst);
+  // every round advances each member that is not done: an outer iteration takes at least one
+  // round and at least min(nup, budget) correction iterations, so this many rounds end every member
+  const long long max_rounds = 2LL * ((long long)cap / B->nup + 2) + 4;
+  struct Cfg { int zchunk, minb, mult; };
+  const Cfg cands[] = {{64, 4, 1}, {64, 3, 1}, {32, 4, 1}, {128, 4, 1}, {64, 4, 2}};
+  const int ncand = B->tuned ? 0 : (int)(sizeof cands / sizeof cands[0]);
+  float best_ms = 1e30f;
+  Cfg best = {B->zchunk, B->minb, B->mult};
+  long long rounds = 0;
+  int nactive = B->ninst;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ncand && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) return PT_ECUDA;
+  for (int t = 0; t < ncand && nactive > 0 && rounds < max_rounds; ++t) {
+    B->zchunk = cands[t].zchunk;
+    B->minb = cands[t].minb;
+    B->mult = cands[t].mult;
+    if (upload_mix(B) != cudaSuccess) return PT_ECUDA;
+    rc = build_mix_graph(B);
+    if (rc != PT_OK) return rc;
+    cudaEventRecord(e0, B->stream);
+    if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return PT_ECUDA;
+    cudaEventRecord(e1, B->stream);
+    rounds += B->mult;
+    rc = mix_active(B, &nactive);
+    if (rc != PT_OK) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / B->mult < best_ms) {
+      best_ms = ms / B->mult;
+      best = cands[t];
+    }
+  }
+  if (ncand) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->zchunk = best.zchunk;
+    B->minb = best.minb;
+    B->mult = best.mult;
+    B->tuned = true;
+    if (upload_mix(B) != cudaSuccess) return PT_ECUDA;
+  }
+  rc = build_mix_graph(B);
+  if (rc != PT_OK) return rc;
+  while (nactive > 0 && rounds < max_rounds) {
+    if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return PT_ECUDA;
+    rounds += B->mult;
+    rc = mix_active(B, &nactive);
+    if (rc != PT_OK) return rc;
+  }
+  if (nactive > 0) return PT_ECUDA;   // cannot happen: see max_rounds
+  int any_nc = 0, any_nan = 0;
+  for (int m = 0; m < B->ninst; ++m) {
+    const MixBatchStatus& S = B->h_mst[m];
+    pt_ctx* c = B->ctx[m];
+    c->cur = S.cur;
+    c->mix_omega = S.omega;
+    c->mix_prev = S.prev;
+    const int rc_end = pt_step_end(c);
+    reps[m].iters = S.iters;
+    reps[m].status = S.status;
+    reps[m].res_v = S.res[0];
+    reps[m].res_pt = S.res[1];
+    reps[m].res_pf = S.res[2];
+    reps[m].res_pic = S.res[3];
+    if (ttc_ms) ttc_ms[m] = S.t_stop > S.t_start ? (double)(S.t_stop - S.t_start) * 1e-6 : -1.0;
+    if (rc_end != PT_OK) return rc_end;
+    any_nc |= S.status == PT_ENOTCONV;
+    any_nan |= S.status == PT_ENAN;
+  }
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return PT_ECUDA;
+  return any_nan ? PT_ENAN : (any_nc ? PT_ENOTCONV : PT_OK);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1198,29 +1410,39 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   B->slab_elems = 0;
   B->ctx.assign(ninst, nullptr);
   B->h_inst.resize(ninst);
-  B->concurrent = fp32;
+  B->mixed = fp32;
+  B->zchunk = 64;
+  B->minb = 4;
+  B->mult = 1;
+  B->exec_zchunk = B->exec_minb = B->exec_mult = 0;
+  B->h_st = nullptr;
+  B->h_mst = nullptr;
+  if (fp32) B->h_minst.resize(ninst);
   char* w = (char*)workspace;
   int rc = PT_OK;
-  if (fp32) {
-    B->streams.assign(ninst, nullptr);
-    for (int m = 0; m < ninst && rc == PT_OK; ++m)
-      if (cudaStreamCreateWithFlags(&B->streams[m], cudaStreamNonBlocking) != cudaSuccess) rc = PT_ECUDA;
-  }
   for (int m = 0; m < ninst && rc == PT_OK; ++m) {
     const size_t s = pt_workspace_size(&grids[m], &nums[m]);
-    rc = pt_init(&B->ctx[m], &grids[m], &phys[m], &nums[m], &fields[m], w, s,
-                 (void*)(fp32 ? B->streams[m] : B->stream), 0);
+    rc = pt_init(&B->ctx[m], &grids[m], &phys[m], &nums[m], &fields[m], w, s, (void*)B->stream, 0);
     w += align_up(s, kAlign);
   }
   if (rc == PT_OK) {
-    B->d_inst = (BatchInst*)w;
-    B->d_st = (BatchStatus*)(w + align_up(sizeof(BatchInst) * ninst, kAlign));
+    char* t = w;
+    B->d_inst = (BatchInst*)t;
+    t += align_up(sizeof(BatchInst) * ninst, kAlign);
+    B->d_st = (BatchStatus*)t;
+    t += align_up(sizeof(BatchStatus) * ninst, kAlign);
+    B->d_minst = (MixBatchInst*)t;
+    t += align_up(sizeof(MixBatchInst) * ninst, kAlign);
+    B->d_mst = (MixBatchStatus*)t;
+    t += align_up(sizeof(MixBatchStatus) * ninst, kAlign);
+    B->d_ired = (unsigned long long*)t;
     if (cudaMallocHost(&B->h_st, sizeof(BatchStatus) * ninst) != cudaSuccess) rc = PT_ECUDA;
+    if (rc == PT_OK && cudaMallocHost(&B->h_mst, sizeof(MixBatchStatus) * ninst) != cudaSuccess) rc = PT_ECUDA;
   }
   if (rc != PT_OK) {
     for (pt_ctx* c : B->ctx) pt_destroy(c);
-    for (cudaStream_t s : B->streams)
-      if (s) cudaStreamDestroy(s);
+    if (B->h_st) cudaFreeHost(B->h_st);
+    if (B->h_mst) cudaFreeHost(B->h_mst);
     cudaStreamDestroy(B->stream);
     delete B;
     return rc;
@@ -1229,42 +1451,11 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   return PT_OK;
 }
 
-namespace {
-// FP32 ensemble step: every instance's pt_step (defect-correction loop, host-driven) on its own
-// stream and host thread; time to converge = host time from the common start to its return.
-int batch_step_concurrent(pt_batch* B, pt_report* reps, double* ttc_ms) {
-  std::vector<int> rcs(B->ninst, PT_OK);
-  std::vector<std::thread> pool;
-  const auto t0 = std::chrono::steady_clock::now();
-  auto run = [B, reps, ttc_ms, t0, &rcs](int m) {
-    rcs[m] = pt_step(B->ctx[m], &reps[m]);
-    const auto t1 = std::chrono::steady_clock::now();
-    if (ttc_ms) ttc_ms[m] = std::chrono::duration<double, std::milli>(t1 - t0).count();
-  };
-  int started = 0;
-  try {
-    pool.reserve(B->ninst);
-    for (; started < B->ninst; ++started) pool.emplace_back(run, started);
-  } catch (...) {
-    // no more threads to be had: the instances not yet started run on this thread
-  }
-  for (int m = started; m < B->ninst; ++m) run(m);
-  for (std::thread& t : pool) t.join();
-  int any_nc = 0, any_nan = 0;
-  for (int m = 0; m < B->ninst; ++m) {
-    if (rcs[m] != PT_OK && rcs[m] != PT_ENOTCONV && rcs[m] != PT_ENAN) return rcs[m];
-    any_nc |= rcs[m] == PT_ENOTCONV;
-    any_nan |= rcs[m] == PT_ENAN;
-  }
-  return any_nan ? PT_ENAN : (any_nc ? PT_ENOTCONV : PT_OK);
-}
-}  // namespace
-
 int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
   if (!B || !reps) return PT_EINVAL;
   // order after the caller's prior work on its stream
   if (cudaStreamSynchronize(B->caller) != cudaSuccess) return PT_ECUDA;
-  if (B->concurrent) return batch_step_concurrent(B, reps, ttc_ms);
+  if (B->mixed) return batch_step_mixed(B, reps, ttc_ms);
   int rc = PT_OK;
   int cap = 0;
   if (B->coupled) {
@@ -1360,9 +1551,16 @@ int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
 
 int pt_batch_config(const pt_batch* B, int32_t* tile_x, int32_t* tile_y, int32_t* ipg) {
   if (!B) return PT_EINVAL;
-  if (tile_x) *tile_x = B->concurrent ? 0 : B->bx;
-  if (tile_y) *tile_y = B->concurrent ? 0 : B->by;
-  if (ipg) *ipg = B->concurrent ? 0 : B->ipg;
+  if (tile_x) *tile_x = B->mixed ? corr_tile_x() : B->bx;
+  if (tile_y) *tile_y = B->mixed ? corr_tile_y() : B->by;
+  if (ipg) *ipg = B->mixed ? B->mult * B->nup : B->ipg;
+  return PT_OK;
+}
+
+int pt_batch_config_fp32(const pt_batch* B, int32_t* tile_z, int32_t* blocks_per_sm) {
+  if (!B || !B->mixed) return PT_EINVAL;
+  if (tile_z) *tile_z = B->zchunk;
+  if (blocks_per_sm) *blocks_per_sm = B->minb;
   return PT_OK;
 }
 
@@ -1371,9 +1569,8 @@ void pt_batch_destroy(pt_batch* B) {
   cudaStreamSynchronize(B->stream);
   if (B->exec) cudaGraphExecDestroy(B->exec);
   for (pt_ctx* c : B->ctx) pt_destroy(c);
-  for (cudaStream_t s : B->streams)
-    if (s) cudaStreamDestroy(s);
   cudaFreeHost(B->h_st);
+  cudaFreeHost(B->h_mst);
   cudaStreamDestroy(B->stream);
   delete B;
 }
@@ -1634,10 +1831,10 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
         const AdjCellOut co{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[1 - cur], A.lF[1 - cur],
                             A.lL[1 - cur], A.mL[1 - cur], check ? A.gth : nullptr, nullptr, nullptr, nullptr};
         if (pl) {
-          PT_LAUNCH(c, K_ADJ_CELLS, adj_edges_pl(gr, bl, c->stream, b, ac, A.edge_in(cur),
-                                                 AdjEdgeOut{A.txy, A.txz, A.tyz, A.Zxy, A.Zxz, A.Zyz}));
+          PT_LAUNCH(c, K_ADJ_EDGES_PL, adj_edges_pl(gr, bl, c->stream, b, ac, A.edge_in(cur),
+                                                    AdjEdgeOut{A.txy, A.txz, A.tyz, A.Zxy, A.Zxz, A.Zyz}));
           const AdjMuIn mi{A.lM[cur], A.gM, A.Zxy, A.Zxz, A.Zyz, A.lM[1 - cur], nullptr};
-          PT_LAUNCH(c, K_ADJ_CELLS, adj_cells_pl(gr, bl, c->stream, b, ac, u, A.cell_in(cur, K0), co, A.pl, mi,
+          PT_LAUNCH(c, K_ADJ_CELLS_PL, adj_cells_pl(gr, bl, c->stream, b, ac, u, A.cell_in(cur, K0), co, A.pl, mi,
                                                  c->red, check));
         } else {
           PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(cur, K0), co, c->red, check));
@@ -1645,8 +1842,8 @@ int pt_adjoint(pt_ctx* c, const double* dJ_dphi, double* grad, pt_report* rep) {
         AdjFaceIn fi = fi0;
         fi.lP1 = A.lP[1 - cur];
         fi.mL = A.mL[1 - cur];
-        PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz,
-                                            c->red, check));
+        PT_LAUNCH(c, pl ? K_ADJ_FACES_PL : K_ADJ_FACES,
+                  adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz, c->red, check));
         cur = 1 - cur;
         if (check) {
           rc = read_report(c, &last);
@@ -1721,18 +1918,18 @@ int pt_adjoint_apply(pt_ctx* c, const pt_adj_vec* lam, pt_adj_vec* out, void* ws
   if (pl) {
     PT_LAUNCH(c, K_ADJ_PREP, adj_prep_pl(gr, bl, c->stream, b, ac, u, K0, A.prep_for(0), A.pl, A.Zxy, A.Zxz,
                                          A.Zyz));
-    PT_LAUNCH(c, K_ADJ_CELLS, adj_edges_pl(gr, bl, c->stream, b, ac, A.edge_in(0),
-                                           AdjEdgeOut{A.txy, A.txz, A.tyz, A.Zxy, A.Zxz, A.Zyz}));
+    PT_LAUNCH(c, K_ADJ_EDGES_PL, adj_edges_pl(gr, bl, c->stream, b, ac, A.edge_in(0),
+                                              AdjEdgeOut{A.txy, A.txz, A.tyz, A.Zxy, A.Zxz, A.Zyz}));
     const AdjMuIn mi{A.lM[0], A.gM, A.Zxy, A.Zxz, A.Zyz, A.lM[1], out->mu};
-    PT_LAUNCH(c, K_ADJ_CELLS, adj_cells_pl(gr, bl, c->stream, b, ac, u, A.cell_in(0, K0), co, A.pl, mi, c->red, 0));
+    PT_LAUNCH(c, K_ADJ_CELLS_PL, adj_cells_pl(gr, bl, c->stream, b, ac, u, A.cell_in(0, K0), co, A.pl, mi, c->red, 0));
   } else {
     PT_LAUNCH(c, K_ADJ_PREP, adj_prep(gr, bl, c->stream, b, ac, u, K0, A.prep_for(0)));
     PT_LAUNCH(c, K_ADJ_CELLS, adj_cells(gr, bl, c->stream, b, ac, u, A.cell_in(0, K0), co, c->red, 0));
   }
   const AdjFaceIn fi{A.txx, A.tyy, A.tzz, A.txy, A.txz, A.tyz, A.lP[0], A.mL[0],
                      A.prep.bfx, A.prep.bfy, A.prep.bfz, out->Vx, out->Vy, out->Vz, 0, nullptr, nullptr, nullptr};
-  PT_LAUNCH(c, K_ADJ_FACES, adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz,
-                                      c->red, 0));
+  PT_LAUNCH(c, pl ? K_ADJ_FACES_PL : K_ADJ_FACES,
+            adj_faces(gr, bl, c->stream, b, ac, fi, A.Lx, A.Ly, A.Lz, A.LRx, A.LRy, A.LRz, c->red, 0));
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_status(e);

@@ -14,6 +14,9 @@
 //         Eq. 22 in FP64 (log space) from the corrected pressures and velocities.
 // Converged when the FP64 residual max-norms and the Picard change are below tol.
 #include "pt_mixed.cuh"
+#include "pt_ref_points.cuh"
+#include "pt_lean_body.cuh"
+#include "../../include/porowave_pt.h"
 
 namespace pt {
 
@@ -28,12 +31,9 @@ __device__ inline double pos_max64(double a, double b) {
 
 // (i) FP64 residuals at cell centres, normal stresses at u, and the frozen coefficients of the
 // correction problem (in FP32).
-__global__ void __launch_bounds__(256) k_mix_prepare(Box b, Coef c, MixPrepIn in, MixPrepOut out,
-                                                     unsigned long long* red) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  double r_pt = 0.0, r_pf = 0.0;
+__device__ __forceinline__ void mix_prepare_point(const Box& b, const Coef& c, const MixPrepIn& in,
+                                                  const MixPrepOut& out, int i, int j, int k, double& r_pt,
+                                                  double& r_pf) {
   if (i < b.nx && j < b.ny && k < b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
@@ -96,18 +96,23 @@ __global__ void __launch_bounds__(256) k_mix_prepare(Box b, Coef c, MixPrepIn in
     r_pt = fabs(divVn);
     r_pf = fabs(rpf);
   }
+}
+
+__global__ void __launch_bounds__(256) k_mix_prepare(Box b, Coef c, MixPrepIn in, MixPrepOut out,
+                                                     unsigned long long* red) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double r_pt = 0.0, r_pf = 0.0;
+  mix_prepare_point(b, c, in, out, i, j, k, r_pt, r_pf);
   block_max_atomic(r_pt, red + RED_PT);
   block_max_atomic(r_pf, red + RED_PF);
 }
 
 // (i) FP64 momentum residual at u (Eq. 19), stored in FP32; its max-norm.
-__global__ void __launch_bounds__(256) k_mix_res_faces(Box b, Coef c, MixFaceIn in, float* __restrict__ rfx,
-                                                       float* __restrict__ rfy, float* __restrict__ rfz,
-                                                       unsigned long long* red) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  double r_v = 0.0;
+__device__ __forceinline__ void mix_res_faces_point(const Box& b, const Coef& c, const MixFaceIn& in,
+                                                    float* __restrict__ rfx, float* __restrict__ rfy,
+                                                    float* __restrict__ rfz, int i, int j, int k, double& r_v) {
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
@@ -131,16 +136,24 @@ __global__ void __launch_bounds__(256) k_mix_res_faces(Box b, Coef c, MixFaceIn 
       r_v = fmax(r_v, fabs(F));
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_mix_res_faces(Box b, Coef c, MixFaceIn in, float* __restrict__ rfx,
+                                                       float* __restrict__ rfy, float* __restrict__ rfz,
+                                                       unsigned long long* red) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double r_v = 0.0;
+  mix_res_faces_point(b, c, in, rfx, rfy, rfz, i, j, k, r_v);
   block_max_atomic(r_v, red + RED_V);
 }
 
 // Frozen mu-dependent coefficients of the correction problem: mu and the velocity pseudo-step
 // dtau_V = fac / mu at centres, in FP32 (the iteration forms 2 mu/(1+xi) at centres and edges and
 // the face pseudo-steps from them).
-__global__ void __launch_bounds__(256) k_mix_coef(Box b, Coef c, const double* __restrict__ mu, MixCoefOut out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+__device__ __forceinline__ void mix_coef_point(const Box& b, const Coef& c, const double* __restrict__ mu,
+                                               const MixCoefOut& out, int i, int j, int k) {
   if (i < b.nx && j < b.ny && k < b.nz) {
     const long long q = cidx(b, i, j, k);
     out.mu[q] = (float)mu[q];
@@ -148,32 +161,41 @@ __global__ void __launch_bounds__(256) k_mix_coef(Box b, Coef c, const double* _
   }
 }
 
+__global__ void __launch_bounds__(256) k_mix_coef(Box b, Coef c, const double* __restrict__ mu, MixCoefOut out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  mix_coef_point(b, c, mu, out, i, j, (int)blockIdx.z);
+}
+
 // (iii) one FP32 PT iteration on the correction in a single pass.
 //
 // The iteration's two halves depend on each other across neighbours: the faces (momentum,
 // damped R, dV) of level k read the cells' stresses and new dPt at k and k-1 (own cell, x- and
 // y-neighbours below) and the edge stresses at k and k+1 (own edge, x- and y-neighbours above).
-// A 32 x 8 block owns a tile of 30 x 6 faces and cells and marches up a column of kCorrZChunk
-// levels: at level L every thread computes the cell and the three lower edges at its index for
-// the tile plus a one-cell halo on each side (the halo is recomputed by the neighbouring tiles'
-// blocks from the same inputs, bit for bit), into a three-level ring in shared memory; after a
-// barrier the tile's threads compute the faces of level L-1 from the ring. Stresses and the new
-// dPt never go to global memory: per cell the pass reads dV, dPt, dPf, R, the right-hand sides
-// and the frozen cc, k, 1/dtau_Pt, mu, dtau_V (18 arrays) and writes dV', dPt', dPf', R (8 arrays):
-// 104 B per cell against 200 B for a cells kernel plus a faces kernel. dV is read from one buffer
-// and written to another (other blocks' halos still read the old dV). The pseudo-step of dPf
-// (largest neighbour k), the local-implicit denominators, 2 mu/(1+xi) at centres and edges (mean
-// of the four centres' mu) and the face pseudo-steps (mean of the two centres') are formed here.
+// A 32 x 8 block owns a tile of 30 x 6 faces and cells and marches up a column of face levels:
+// at level L every thread computes the cell and the three lower edges at its index for the tile
+// plus a one-cell halo on each side (the halo is recomputed by the neighbouring tiles' blocks from
+// the same inputs, bit for bit), into rings in shared memory; after a barrier the tile's threads
+// compute the faces of level L-1 from the rings. Stresses and the new dPt never go to global
+// memory: per cell the pass reads dV, dPt, dPf, R, the right-hand sides and the frozen cc, k,
+// 1/dtau_Pt, mu, dtau_V (18 arrays) and writes dV', dPt', dPf', R (8 arrays): 104 B per cell
+// against 200 B for a cells kernel plus a faces kernel. dV is read from one buffer and written to
+// another (other blocks' halos still read the old dV). The pseudo-step of dPf (largest neighbour
+// k), the local-implicit denominators, 2 mu/(1+xi) at centres and edges (mean of the four
+// centres' mu) and the face pseudo-steps (mean of the two centres') are formed here.
+//
+// Staging: the 12 arrays read at a point's own index go into a three-slot shared-memory ring by
+// cp.async, one level ahead (levels L-1 and L resident while L+1 is in flight), so every x-, y-
+// and z-1 neighbour a point reads comes from shared memory; only the three z+1 values of a cell
+// (Vz; k and dPf for the Darcy flux) and the faces' own right-hand side and R are plain loads.
+// The Darcy part (dPf', its residual) is formed for the tile's own cells only: the halo cells
+// feed the faces through their stresses and dPt' alone.
 constexpr int kCorrTX = 30, kCorrTY = 6, kCorrZChunk = 64;
-// The 11 arrays the cell phase reads at its own index are copied into a shared-memory stage by
-// cp.async ahead of their level; the cell phase reads its own values and its x- and y-neighbours
-// inside the block's region from the stage.
-enum { C_VX, C_VY, C_VZ, C_PT, C_PF, C_CC, C_K, C_IDTP, C_RPT, C_RPF, C_MU, kCorrStage };
-// Stage depth: 2 = the next level's copies in flight while this level computes; 3 = two levels
-// ahead, and the z+1 values read from the stage too. Blocks per SM asked of the register allocator.
-constexpr int kCorrStages = 2, kCorrMinBlocks = 4;
-// rings of three levels for cells (4 values) and edges (3), kCorrStages for the staged inputs
-constexpr int kCorrSmemBytes = (3 * (4 + 3) + kCorrStages * kCorrStage) * 8 * 32 * (int)sizeof(float);
+enum { C_VX, C_VY, C_VZ, C_PT, C_PF, C_CC, C_K, C_IDTP, C_RPT, C_RPF, C_MU, C_DTV, kCorrStage };
+// Blocks per SM asked of the register allocator.
+constexpr int kCorrMinBlocks = 4;
+// rings: cells (4 values) over three levels, edges (3) over two, staged inputs over three
+constexpr int kCorrSmemBytes = (3 * 4 + 2 * 3 + 3 * kCorrStage) * 8 * 32 * (int)sizeof(float);
 
 __device__ __forceinline__ void corr_cp4(float* smem, const float* gmem) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
@@ -184,20 +206,19 @@ __device__ __forceinline__ float corr_modulus(const CorrCoef<float>& c, float m)
   return __fdividef(2.0f * m, 1.0f + m * c.rG);
 }
 
-__global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, CorrCoef<float> c, CorrIn<float> in,
-                                                        CorrOut<float> out, unsigned long long* red, int check) {
+// One tile of the iteration: faces and cells of columns [tbx kCorrTX, +kCorrTX) x [tby kCorrTY,
+// +kCorrTY) and face levels [k0, k1), by a 32 x 8 block whose dynamic shared memory (kCorrSmemBytes)
+// starts at corr_smem. Leaves no copy in flight: the block may start another tile after a barrier.
+__device__ __forceinline__ void corr_tile(const Box& b, const CorrCoef<float>& c, const CorrIn<float>& in,
+                                          const CorrOut<float>& out, int tbx, int tby, int k0, int k1,
+                                          unsigned long long* red, int check, float* corr_smem) {
   using T = float;
-  // ring of three levels: cells (txx, tyy, tzz, dPt') and edges (txy, txz, tyz) of the region
-  extern __shared__ __align__(16) float corr_smem[];   // kCorrSmemBytes, dynamic (above 48 KB)
-  T(*s_cell)[4][8][32] = reinterpret_cast<T(*)[4][8][32]>(corr_smem);
-  T(*s_edge)[3][8][32] = reinterpret_cast<T(*)[3][8][32]>(corr_smem + 3 * 4 * 8 * 32);
-  T(*s_in)[kCorrStage][8][32] = reinterpret_cast<T(*)[kCorrStage][8][32]>(corr_smem + 3 * 7 * 8 * 32);
-  (void)kCorrSmemBytes;
+  T(*s_cell)[4][8][32] = reinterpret_cast<T(*)[4][8][32]>(corr_smem);                 // txx, tyy, tzz, dPt'
+  T(*s_edge)[3][8][32] = reinterpret_cast<T(*)[3][8][32]>(corr_smem + 3 * 4 * 8 * 32);  // txy, txz, tyz
+  T(*s_in)[kCorrStage][8][32] = reinterpret_cast<T(*)[kCorrStage][8][32]>(corr_smem + (3 * 4 + 2 * 3) * 8 * 32);
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * kCorrTX - 1 + tx;
-  const int j = blockIdx.y * kCorrTY - 1 + ty;
-  const int k0 = blockIdx.z * kCorrZChunk;
-  const int k1 = min(k0 + kCorrZChunk, b.nz + 1);       // face levels [k0, k1) of this block
+  const int i = tbx * kCorrTX - 1 + tx;
+  const int j = tby * kCorrTY - 1 + ty;
   const bool own = tx >= 1 && tx <= kCorrTX && ty >= 1 && ty <= kCorrTY;
   const int ipx = b.px, ipxy = (int)b.pxy;   // the host keeps the box below 2^31 elements
   // residual norms as bit patterns of non-negative doubles: a NaN (largest pattern) stays in them
@@ -206,11 +227,12 @@ __global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, C
     const unsigned long long u = (unsigned long long)__double_as_longlong((double)fabsf(x));
     m = u > m ? u : m;
   };
+  auto slot = [](int L) { return (L + 6) % 3; };     // L >= -2
   const bool in_box = i >= 0 && j >= 0 && i <= b.nx && j <= b.ny;
-  auto stage = [&](int L) {   // own-index values of level L (inside the box) into stage L mod 3
+  auto stage = [&](int L) {   // own-index values of level L (inside the box) into its ring slot
     if (in_box && L >= 0 && L <= b.nz) {
       const int q = i + ipx * j + ipxy * L;
-      float(*st)[8][32] = s_in[(L + kCorrStages) % kCorrStages];
+      float(*st)[8][32] = s_in[slot(L)];
       corr_cp4(&st[C_VX][ty][tx], in.Vx + q);
       corr_cp4(&st[C_VY][ty][tx], in.Vy + q);
       corr_cp4(&st[C_VZ][ty][tx], in.Vz + q);
@@ -222,118 +244,121 @@ __global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, C
       corr_cp4(&st[C_RPT][ty][tx], in.r_pt + q);
       corr_cp4(&st[C_RPF][ty][tx], in.r_pf + q);
       corr_cp4(&st[C_MU][ty][tx], in.mu + q);
+      corr_cp4(&st[C_DTV][ty][tx], in.dtvc + q);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  for (int d = 0; d < kCorrStages - 1; ++d) stage(k0 - 1 + d);
+  T dtv_zm = T(0);   // dtau_V at (i, j, F - 1) for the z-face of level F (carried up the column)
+  stage(k0 - 2);
+  stage(k0 - 1);
   for (int L = k0 - 1; L <= k1; ++L) {
-    const int sl = (L + 3) % 3;
-    stage(L + kCorrStages - 1);                        // the level kCorrStages - 1 ahead goes out now
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this thread's copies up to level L landed
-    // every thread's staged copies are visible (the cell phase reads neighbours' staged values),
-    // and the previous level's faces are done with the ring slot this level overwrites
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this thread's copies of level L landed
+    // every thread's copies are visible (points read their neighbours' staged values), and every
+    // thread is done with the previous level: its faces' ring slots and the stage slot L - 2
     __syncthreads();
-    const float(*S)[8][32] = s_in[(L + kCorrStages) % kCorrStages];
-    const float(*Su)[8][32] = s_in[(L + 1 + kCorrStages) % kCorrStages];   // level L + 1 (3 stages)
+    stage(L + 1);                                             // in flight while this level computes
+    const float(*S)[8][32] = s_in[slot(L)];
+    const float(*Sm)[8][32] = s_in[slot(L - 1)];
+    const int sl = slot(L), se = L & 1;
     // the faces of level L - 1 read these after the cell phase: their loads go out first
     const int F = L - 1;
     const bool face_here = own && F >= k0 && F < k1 && in_box && F <= b.nz;
-    T rfx = T(0), rfy = T(0), rfz = T(0), Rx0 = T(0), Ry0 = T(0), Rz0 = T(0), Vx0 = T(0), Vy0 = T(0), Vz0 = T(0);
-    T dtx = T(0), dty = T(0), dtz = T(0);
+    T rfx = T(0), rfy = T(0), rfz = T(0), Rx0 = T(0), Ry0 = T(0), Rz0 = T(0);
     const bool fx = face_here && i > 0 && i < b.nx && j < b.ny && F < b.nz;
     const bool fy = face_here && j > 0 && j < b.ny && i < b.nx && F < b.nz;
     const bool fz = face_here && F > 0 && F < b.nz && i < b.nx && j < b.ny;
     if (face_here) {
       const int q = i + ipx * j + ipxy * F;
-      if (fx) { rfx = in.rfx[q]; Rx0 = out.Rx[q]; Vx0 = in.Vx[q]; dtx = T(0.5) * (in.dtvc[q - 1] + in.dtvc[q]); }
-      if (fy) { rfy = in.rfy[q]; Ry0 = out.Ry[q]; Vy0 = in.Vy[q]; dty = T(0.5) * (in.dtvc[q - ipx] + in.dtvc[q]); }
-      if (fz) { rfz = in.rfz[q]; Rz0 = out.Rz[q]; Vz0 = in.Vz[q]; dtz = T(0.5) * (in.dtvc[q - ipxy] + in.dtvc[q]); }
+      if (fx) { rfx = in.rfx[q]; Rx0 = out.Rx[q]; }
+      if (fy) { rfy = in.rfy[q]; Ry0 = out.Ry[q]; }
+      if (fz) { rfz = in.rfz[q]; Rz0 = out.Rz[q]; }
     }
     // ---------------- cell and lower edges at (i, j, L). Cells are needed for the tile and its
     // left / lower halo (tx <= 30, ty <= 6), edges for the tile and its right / upper halo
-    // (tx >= 1, ty >= 1). Indices are 32-bit (the host keeps the box below 2^31 elements);
-    // x- and y-neighbours inside the block's region come from this level's stage.
+    // (tx >= 1, ty >= 1); x-, y- and z-1 neighbours come from the stage ring.
     T txx = T(0), tyy = T(0), tzz = T(0), P1 = T(0), exy = T(0), exz = T(0), eyz = T(0);
     if (in_box && L >= 0 && L <= b.nz) {
       const int q = i + ipx * j + ipxy * L;
-      auto nb = [&](int slot, int dx, int dy, const float* g, int off) -> float {
-        const int x = tx + dx, y = ty + dy;
-        return (x >= 0 && x < 32 && y >= 0 && y < 8) ? S[slot][y][x] : g[q + off];
-      };
       const T mu_c = S[C_MU][ty][tx], vx_c = S[C_VX][ty][tx], vy_c = S[C_VY][ty][tx], vz_c = S[C_VZ][ty][tx];
       if (tx >= 1 && ty >= 1) {
         if (L < b.nz && i > 0 && i < b.nx && j > 0 && j < b.ny) {
-          const T m = T(0.25) * (nb(C_MU, -1, -1, in.mu, -1 - ipx) + nb(C_MU, 0, -1, in.mu, -ipx) +
-                                 nb(C_MU, -1, 0, in.mu, -1) + mu_c);
-          exy = corr_modulus(c, m) * ((vx_c - nb(C_VX, 0, -1, in.Vx, -ipx)) * c.hrdy +
-                                      (vy_c - nb(C_VY, -1, 0, in.Vy, -1)) * c.hrdx);
+          const T m = T(0.25) * (S[C_MU][ty - 1][tx - 1] + S[C_MU][ty - 1][tx] + S[C_MU][ty][tx - 1] + mu_c);
+          exy = corr_modulus(c, m) * ((vx_c - S[C_VX][ty - 1][tx]) * c.hrdy + (vy_c - S[C_VY][ty][tx - 1]) * c.hrdx);
         }
         if (j < b.ny && i > 0 && i < b.nx && L > 0 && L < b.nz) {
-          const T m = T(0.25) * (in.mu[q - 1 - ipxy] + in.mu[q - ipxy] + nb(C_MU, -1, 0, in.mu, -1) + mu_c);
-          exz = corr_modulus(c, m) * ((vx_c - in.Vx[q - ipxy]) * c.hrdz + (vz_c - nb(C_VZ, -1, 0, in.Vz, -1)) * c.hrdx);
+          const T m = T(0.25) * (Sm[C_MU][ty][tx - 1] + Sm[C_MU][ty][tx] + S[C_MU][ty][tx - 1] + mu_c);
+          exz = corr_modulus(c, m) * ((vx_c - Sm[C_VX][ty][tx]) * c.hrdz + (vz_c - S[C_VZ][ty][tx - 1]) * c.hrdx);
         }
         if (i < b.nx && j > 0 && j < b.ny && L > 0 && L < b.nz) {
-          const T m = T(0.25) * (in.mu[q - ipx - ipxy] + in.mu[q - ipxy] + nb(C_MU, 0, -1, in.mu, -ipx) + mu_c);
-          eyz = corr_modulus(c, m) * ((vy_c - in.Vy[q - ipxy]) * c.hrdz + (vz_c - nb(C_VZ, 0, -1, in.Vz, -ipx)) * c.hrdy);
+          const T m = T(0.25) * (Sm[C_MU][ty - 1][tx] + Sm[C_MU][ty][tx] + S[C_MU][ty - 1][tx] + mu_c);
+          eyz = corr_modulus(c, m) * ((vy_c - Sm[C_VY][ty][tx]) * c.hrdz + (vz_c - S[C_VZ][ty - 1][tx]) * c.hrdy);
         }
       }
       if (tx <= kCorrTX && ty <= kCorrTY && i < b.nx && j < b.ny && L < b.nz) {
         const T dPt = S[C_PT][ty][tx], dPf = S[C_PF][ty][tx], cc = S[C_CC][ty][tx];
-        const T rpt = S[C_RPT][ty][tx], rpf = S[C_RPF][ty][tx];
-        const T gx = (nb(C_VX, 1, 0, in.Vx, 1) - vx_c) * c.rdx, gy = (nb(C_VY, 0, 1, in.Vy, ipx) - vy_c) * c.rdy;
-        const T gz = (((kCorrStages > 2) ? Su[C_VZ][ty][tx] : in.Vz[q + ipxy]) - vz_c) * c.rdz;
+        const T rpt = S[C_RPT][ty][tx];
+        const T gx = (S[C_VX][ty][tx + 1] - vx_c) * c.rdx, gy = (S[C_VY][ty + 1][tx] - vy_c) * c.rdy;
+        const T gz = (in.Vz[q + ipxy] - vz_c) * c.rdz;
         const T divV = gx + gy + gz;
         const T cpl = c.bd_rdt_a + cc;                 // beta_d alpha / dt + cc
         const T rho_pt = rpt + divV + (c.bd_rdt + cc) * dPt - cpl * dPf;
-        const T kc = S[C_K][ty][tx];
-        T kmax = kc, sx = T(0), sy = T(0), sz = T(0);
-        if (i > 0) {
-          const T kn = nb(C_K, -1, 0, in.perm, -1);
-          kmax = fmaxf(kmax, kn);
-          sx -= (kn + kc) * (dPf - nb(C_PF, -1, 0, in.Pf, -1));
-        }
-        if (i < b.nx - 1) {
-          const T kn = nb(C_K, 1, 0, in.perm, 1);
-          kmax = fmaxf(kmax, kn);
-          sx += (kc + kn) * (nb(C_PF, 1, 0, in.Pf, 1) - dPf);
-        }
-        if (j > 0) {
-          const T kn = nb(C_K, 0, -1, in.perm, -ipx);
-          kmax = fmaxf(kmax, kn);
-          sy -= (kn + kc) * (dPf - nb(C_PF, 0, -1, in.Pf, -ipx));
-        }
-        if (j < b.ny - 1) {
-          const T kn = nb(C_K, 0, 1, in.perm, ipx);
-          kmax = fmaxf(kmax, kn);
-          sy += (kc + kn) * (nb(C_PF, 0, 1, in.Pf, ipx) - dPf);
-        }
-        if (L > 0) {
-          const T kn = in.perm[q - ipxy];
-          kmax = fmaxf(kmax, kn);
-          sz -= (kn + kc) * (dPf - in.Pf[q - ipxy]);
-        }
-        if (L < b.nz - 1) {
-          const T kn = (kCorrStages > 2) ? Su[C_K][ty][tx] : in.perm[q + ipxy];
-          kmax = fmaxf(kmax, kn);
-          sz += (kc + kn) * (((kCorrStages > 2) ? Su[C_PF][ty][tx] : in.Pf[q + ipxy]) - dPf);
-        }
-        const T divq = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
-        const T rho_pf = rpf + divq + (c.bda_B_rdt + cc) * dPf - cpl * dPt;
-        // dP' = dP - dtau rho(dP', ...) solved for dP' (local terms implicit; the quotients only
-        // scale the pseudo-step, so the fast reciprocal does)
-        const T idtp = S[C_IDTP][ty][tx], idtf = kmax * c.ifac_pf;
+        // dP' = dP - dtau rho(dP', ...) solved for dP' (local terms implicit; the quotient only
+        // scales the pseudo-step, so the fast reciprocal does)
+        const T idtp = S[C_IDTP][ty][tx];
         const T dPt1 = __fdividef(dPt * idtp - (rpt + divV - cpl * dPf), idtp + c.bd_rdt + cc);
-        const T dPf1 = __fdividef(dPf * idtf - (rpf + divq - cpl * dPt), idtf + c.bda_B_rdt + cc);
         const T third = divV * T(1.0 / 3.0);
         const T bn = c.beta_n * (rho_pt - rpt);
         const T cm2 = corr_modulus(c, mu_c);
         txx = cm2 * (gx - third + bn);
         tyy = cm2 * (gy - third + bn);
         tzz = cm2 * (gz - third + bn);
-        P1 = dPt1;
+        P1 = out.eval ? dPt : dPt1;
         if (own && L >= k0 && L < k1) {
-          out.Pt[q] = dPt1;
-          out.Pf[q] = dPf1;
+          // Darcy flux divergence, the largest neighbour k and dPf' (the tile's own cells)
+          const T rpf = S[C_RPF][ty][tx], kc = S[C_K][ty][tx];
+          T kmax = kc, sx = T(0), sy = T(0), sz = T(0);
+          if (i > 0) {
+            const T kn = S[C_K][ty][tx - 1];
+            kmax = fmaxf(kmax, kn);
+            sx -= (kn + kc) * (dPf - S[C_PF][ty][tx - 1]);
+          }
+          if (i < b.nx - 1) {
+            const T kn = S[C_K][ty][tx + 1];
+            kmax = fmaxf(kmax, kn);
+            sx += (kc + kn) * (S[C_PF][ty][tx + 1] - dPf);
+          }
+          if (j > 0) {
+            const T kn = S[C_K][ty - 1][tx];
+            kmax = fmaxf(kmax, kn);
+            sy -= (kn + kc) * (dPf - S[C_PF][ty - 1][tx]);
+          }
+          if (j < b.ny - 1) {
+            const T kn = S[C_K][ty + 1][tx];
+            kmax = fmaxf(kmax, kn);
+            sy += (kc + kn) * (S[C_PF][ty + 1][tx] - dPf);
+          }
+          if (L > 0) {
+            const T kn = Sm[C_K][ty][tx];
+            kmax = fmaxf(kmax, kn);
+            sz -= (kn + kc) * (dPf - Sm[C_PF][ty][tx]);
+          }
+          if (L < b.nz - 1) {
+            const T kn = in.perm[q + ipxy];
+            kmax = fmaxf(kmax, kn);
+            sz += (kc + kn) * (in.Pf[q + ipxy] - dPf);
+          }
+          const T divq = -(sx * c.hrdx2 + sy * c.hrdy2 + sz * c.hrdz2);
+          const T rho_pf = rpf + divq + (c.bda_B_rdt + cc) * dPf - cpl * dPt;
+          const T idtf = kmax * c.ifac_pf;
+          const T dPf1 = __fdividef(dPf * idtf - (rpf + divq - cpl * dPt), idtf + c.bda_B_rdt + cc);
+          if (!out.eval) {
+            out.Pt[q] = dPt1;
+            out.Pf[q] = dPf1;
+          }
+          if (out.res_pt) {
+            out.res_pt[q] = rho_pt;
+            out.res_pf[q] = rho_pf;
+          }
           if (check) {
             keep_max(r_pt, rho_pt);
             keep_max(r_pf, rho_pf);
@@ -345,39 +370,41 @@ __global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, C
     s_cell[sl][1][ty][tx] = tyy;
     s_cell[sl][2][ty][tx] = tzz;
     s_cell[sl][3][ty][tx] = P1;
-    s_edge[sl][0][ty][tx] = exy;
-    s_edge[sl][1][ty][tx] = exz;
-    s_edge[sl][2][ty][tx] = eyz;
+    s_edge[se][0][ty][tx] = exy;
+    s_edge[se][1][ty][tx] = exz;
+    s_edge[se][2][ty][tx] = eyz;
     __syncthreads();
-    // ---------------- faces of level F = L - 1 (cells at F and F-1, edges at F and L = F+1)
+    // ---------------- faces of level F = L - 1 (cells at F and F-1, edges at F and L = F+1;
+    // V and dtau_V at F from the stage slot of F, dtau_V at F - 1 carried from the level below)
     if (face_here) {
-      const int sf = (F + 3) % 3, sb = (F + 2) % 3, su = sl;
+      const int sf = slot(F), sb = slot(F - 1), ef = F & 1, eu = se;
       const int q = i + ipx * j + ipxy * F;
       const T Pc = s_cell[sf][3][ty][tx];
+      const T dtv_c = Sm[C_DTV][ty][tx];
       T Fx = T(0), Fy = T(0), Fz = T(0);
       if (fx) {
         Fx = rfx + (s_cell[sf][0][ty][tx] - s_cell[sf][0][ty][tx - 1]) * c.rdx +
-             (s_edge[sf][0][ty + 1][tx] - s_edge[sf][0][ty][tx]) * c.rdy +
-             (s_edge[su][1][ty][tx] - s_edge[sf][1][ty][tx]) * c.rdz - (Pc - s_cell[sf][3][ty][tx - 1]) * c.rdx;
+             (s_edge[ef][0][ty + 1][tx] - s_edge[ef][0][ty][tx]) * c.rdy +
+             (s_edge[eu][1][ty][tx] - s_edge[ef][1][ty][tx]) * c.rdz - (Pc - s_cell[sf][3][ty][tx - 1]) * c.rdx;
         const T R1 = Fx * c.rrho_i + c.damp_x * Rx0;
         out.Rx[q] = R1;
-        out.Vx[q] = Vx0 + dtx * R1;
+        if (!out.eval) out.Vx[q] = Sm[C_VX][ty][tx] + T(0.5) * (Sm[C_DTV][ty][tx - 1] + dtv_c) * R1;
       }
       if (fy) {
-        Fy = rfy + (s_edge[sf][0][ty][tx + 1] - s_edge[sf][0][ty][tx]) * c.rdx +
+        Fy = rfy + (s_edge[ef][0][ty][tx + 1] - s_edge[ef][0][ty][tx]) * c.rdx +
              (s_cell[sf][1][ty][tx] - s_cell[sf][1][ty - 1][tx]) * c.rdy +
-             (s_edge[su][2][ty][tx] - s_edge[sf][2][ty][tx]) * c.rdz - (Pc - s_cell[sf][3][ty - 1][tx]) * c.rdy;
+             (s_edge[eu][2][ty][tx] - s_edge[ef][2][ty][tx]) * c.rdz - (Pc - s_cell[sf][3][ty - 1][tx]) * c.rdy;
         const T R1 = Fy * c.rrho_i + c.damp_y * Ry0;
         out.Ry[q] = R1;
-        out.Vy[q] = Vy0 + dty * R1;
+        if (!out.eval) out.Vy[q] = Sm[C_VY][ty][tx] + T(0.5) * (Sm[C_DTV][ty - 1][tx] + dtv_c) * R1;
       }
       if (fz) {
-        Fz = rfz + (s_edge[sf][1][ty][tx + 1] - s_edge[sf][1][ty][tx]) * c.rdx +
-             (s_edge[sf][2][ty + 1][tx] - s_edge[sf][2][ty][tx]) * c.rdy +
+        Fz = rfz + (s_edge[ef][1][ty][tx + 1] - s_edge[ef][1][ty][tx]) * c.rdx +
+             (s_edge[ef][2][ty + 1][tx] - s_edge[ef][2][ty][tx]) * c.rdy +
              (s_cell[sf][2][ty][tx] - s_cell[sb][2][ty][tx]) * c.rdz - (Pc - s_cell[sb][3][ty][tx]) * c.rdz;
         const T R1 = Fz * c.rrho_i + c.damp_z * Rz0;
         out.Rz[q] = R1;
-        out.Vz[q] = Vz0 + dtz * R1;
+        if (!out.eval) out.Vz[q] = Sm[C_VZ][ty][tx] + T(0.5) * (dtv_zm + dtv_c) * R1;
       }
       if (check) {
         keep_max(r_v, Fx);
@@ -385,7 +412,10 @@ __global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, C
         keep_max(r_v, Fz);
       }
     }
+    // dtau_V at (i, j, L - 1), the z-face of the next level's lower pseudo-step
+    dtv_zm = (in_box && L >= 1 && L - 1 <= b.nz) ? Sm[C_DTV][ty][tx] : T(0);
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // the last level's look-ahead copies
   if (check) {
     block_max_atomic(__longlong_as_double((long long)r_pt), red + RED_PT);
     block_max_atomic(__longlong_as_double((long long)r_pf), red + RED_PF);
@@ -393,11 +423,15 @@ __global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, C
   }
 }
 
+__global__ void __launch_bounds__(256, kCorrMinBlocks) k_corr_iteration(Box b, CorrCoef<float> c, CorrIn<float> in,
+                                                        CorrOut<float> out, unsigned long long* red, int check) {
+  extern __shared__ __align__(16) float corr_smem[];   // kCorrSmemBytes, dynamic (above 48 KB)
+  const int k0 = blockIdx.z * kCorrZChunk;
+  corr_tile(b, c, in, out, blockIdx.x, blockIdx.y, k0, min(k0 + kCorrZChunk, b.nz + 1), red, check, corr_smem);
+}
+
 // (iv) u <- u + delta (FP64 += FP32 correction).
-__global__ void __launch_bounds__(256) k_mix_update(Box b, MixUpdate u) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+__device__ __forceinline__ void mix_update_point(const Box& b, const MixUpdate& u, int i, int j, int k) {
   if (i > b.nx || j > b.ny || k > b.nz) return;
   const long long q = cidx(b, i, j, k);
   const double w = u.omega;
@@ -408,6 +442,12 @@ __global__ void __launch_bounds__(256) k_mix_update(Box b, MixUpdate u) {
     u.Pt[q] = fma(w, (double)u.dPt[q], u.Pt[q]);
     u.Pf[q] = fma(w, (double)u.dPf[q], u.Pf[q]);
   }
+}
+
+__global__ void __launch_bounds__(256) k_mix_update(Box b, MixUpdate u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  mix_update_point(b, u, i, j, (int)blockIdx.z);
 }
 
 void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPrepIn& in,
@@ -431,5 +471,479 @@ void corr_iteration(cudaStream_t s, Box b, const CorrCoef<float>& c, const CorrI
   cudaFuncSetAttribute(k_corr_iteration, cudaFuncAttributeMaxDynamicSharedMemorySize, kCorrSmemBytes);
   k_corr_iteration<<<g, dim3(32, 8, 1), kCorrSmemBytes, s>>>(b, c, in, out, red, check);
 }
+
+
+// ============================================================ multigrid transfers (FP32)
+// Level f (fine, nx x ny x nz cells) and level c (coarse, nx/2 x ny/2 x nz/2): coarse cell I
+// covers fine cells 2I and 2I+1 per direction; coarse face I coincides with fine face 2I.
+namespace {
+
+__device__ __forceinline__ long long mg_q(const Box& b, int i, int j, int k) { return cidx(b, i, j, k); }
+
+// cell-centred linear interpolation weights along one direction: fine index i of a grid with nc
+// coarse cells -> coarse cells (a, b) with weights (3/4, 1/4); the outer neighbour is held at the
+// wall (zero gradient)
+__device__ __forceinline__ void mg_cc_lin(int i, int nc, int& a, int& b) {
+  a = i >> 1;
+  b = (i & 1) ? min(a + 1, nc - 1) : max(a - 1, 0);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_mg_coef(MgLevel f, MgLevel c, float dtaupt_fac, float dtauv_fac) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= c.b.nx || J >= c.b.ny || K >= c.b.nz) return;
+  float m = 0.f, k = 0.f, cc = 0.f;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const long long q = mg_q(f.b, 2 * I + dx, 2 * J + dy, 2 * K + dz);
+        m += f.mu[q];
+        k += f.perm[q];
+        cc += f.cc[q];
+      }
+  const long long qc = mg_q(c.b, I, J, K);
+  m *= 0.125f;
+  c.mu[qc] = m;
+  c.perm[qc] = 0.125f * k;
+  c.cc[qc] = 0.125f * cc;
+  c.idtp[qc] = 1.0f / (dtaupt_fac * m);
+  c.dtvc[qc] = dtauv_fac / m;
+}
+
+__global__ void __launch_bounds__(256) k_mg_restrict(MgLevel f, MgLevel c, float rho_i) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  const Box& B = c.b;
+  if (I > B.nx || J > B.ny || K > B.nz) return;
+  const long long qc = mg_q(B, I, J, K);
+  // a zero correction and damped residual on the coarse grid (walls included)
+  c.dVx[0][qc] = 0.f; c.dVx[1][qc] = 0.f; c.dVy[0][qc] = 0.f; c.dVy[1][qc] = 0.f;
+  c.dVz[0][qc] = 0.f; c.dVz[1][qc] = 0.f; c.dPt[0][qc] = 0.f; c.dPf[0][qc] = 0.f;
+  c.Rx[qc] = 0.f; c.Ry[qc] = 0.f; c.Rz[qc] = 0.f;
+  if (I < B.nx && J < B.ny && K < B.nz) {
+    float a = 0.f, b = 0.f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const long long q = mg_q(f.b, 2 * I + dx, 2 * J + dy, 2 * K + dz);
+          a += f.res_pt[q];
+          b += f.res_pf[q];
+        }
+    c.rpt[qc] = 0.125f * a;
+    c.rpf[qc] = 0.125f * b;
+  }
+  const long long fx = 1, fy = f.b.px, fz = f.b.pxy;
+  // x-face I (interior): fine faces 2I - 1, 2I, 2I + 1 of the children rows (2J + dy, 2K + dz)
+  if (I > 0 && I < B.nx && J < B.ny && K < B.nz) {
+    float s = 0.f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy) {
+        const long long q = mg_q(f.b, 2 * I, 2 * J + dy, 2 * K + dz);
+        s += 0.5f * f.Rx[q] + 0.25f * (f.Rx[q - fx] + f.Rx[q + fx]);
+      }
+    c.rfx[qc] = 0.25f * rho_i * s;
+  }
+  if (J > 0 && J < B.ny && I < B.nx && K < B.nz) {
+    float s = 0.f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dx = 0; dx < 2; ++dx) {
+        const long long q = mg_q(f.b, 2 * I + dx, 2 * J, 2 * K + dz);
+        s += 0.5f * f.Ry[q] + 0.25f * (f.Ry[q - fy] + f.Ry[q + fy]);
+      }
+    c.rfy[qc] = 0.25f * rho_i * s;
+  }
+  if (K > 0 && K < B.nz && I < B.nx && J < B.ny) {
+    float s = 0.f;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const long long q = mg_q(f.b, 2 * I + dx, 2 * J + dy, 2 * K);
+        s += 0.5f * f.Rz[q] + 0.25f * (f.Rz[q - fz] + f.Rz[q + fz]);
+      }
+    c.rfz[qc] = 0.25f * rho_i * s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mg_prolong(MgLevel c, int dc, MgLevel f, int df) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const Box& B = f.b;
+  if (i > B.nx || j > B.ny || k > B.nz) return;
+  const long long q = mg_q(B, i, j, k);
+  const int ncx = c.b.nx, ncy = c.b.ny, ncz = c.b.nz;
+  int ia, ib, ja, jb, ka, kb;
+  if (i < B.nx && j < B.ny && k < B.nz) {   // cells: trilinear
+    mg_cc_lin(i, ncx, ia, ib);
+    mg_cc_lin(j, ncy, ja, jb);
+    mg_cc_lin(k, ncz, ka, kb);
+    const int xs[2] = {ia, ib}, ys[2] = {ja, jb}, zs[2] = {ka, kb};
+    const float w[2] = {0.75f, 0.25f};
+    float pt = 0.f, pf = 0.f;
+    for (int a = 0; a < 2; ++a)
+      for (int bb = 0; bb < 2; ++bb)
+        for (int cc = 0; cc < 2; ++cc) {
+          const float ww = w[a] * w[bb] * w[cc];
+          const long long qc = mg_q(c.b, xs[cc], ys[bb], zs[a]);
+          pt += ww * c.dPt[dc][qc];
+          pf += ww * c.dPf[dc][qc];
+        }
+    f.dPt[df][q] += pt;
+    f.dPf[df][q] += pf;
+  }
+  const float w[2] = {0.75f, 0.25f};
+  if (i > 0 && i < B.nx && j < B.ny && k < B.nz) {   // x-faces
+    const int n0 = i >> 1, n1 = (i + 1) >> 1;         // coincident (i even: n0 = n1) or the two around
+    mg_cc_lin(j, ncy, ja, jb);
+    mg_cc_lin(k, ncz, ka, kb);
+    const int ys[2] = {ja, jb}, zs[2] = {ka, kb};
+    float v = 0.f;
+    for (int a = 0; a < 2; ++a)
+      for (int bb = 0; bb < 2; ++bb) {
+        const float ww = w[a] * w[bb];
+        v += ww * 0.5f * (c.dVx[dc][mg_q(c.b, n0, ys[bb], zs[a])] + c.dVx[dc][mg_q(c.b, n1, ys[bb], zs[a])]);
+      }
+    f.dVx[df][q] += v;
+  }
+  if (j > 0 && j < B.ny && i < B.nx && k < B.nz) {   // y-faces
+    const int n0 = j >> 1, n1 = (j + 1) >> 1;
+    mg_cc_lin(i, ncx, ia, ib);
+    mg_cc_lin(k, ncz, ka, kb);
+    const int xs[2] = {ia, ib}, zs[2] = {ka, kb};
+    float v = 0.f;
+    for (int a = 0; a < 2; ++a)
+      for (int cc = 0; cc < 2; ++cc) {
+        const float ww = w[a] * w[cc];
+        v += ww * 0.5f * (c.dVy[dc][mg_q(c.b, xs[cc], n0, zs[a])] + c.dVy[dc][mg_q(c.b, xs[cc], n1, zs[a])]);
+      }
+    f.dVy[df][q] += v;
+  }
+  if (k > 0 && k < B.nz && i < B.nx && j < B.ny) {   // z-faces
+    const int n0 = k >> 1, n1 = (k + 1) >> 1;
+    mg_cc_lin(i, ncx, ia, ib);
+    mg_cc_lin(j, ncy, ja, jb);
+    const int xs[2] = {ia, ib}, ys[2] = {ja, jb};
+    float v = 0.f;
+    for (int bb = 0; bb < 2; ++bb)
+      for (int cc = 0; cc < 2; ++cc) {
+        const float ww = w[bb] * w[cc];
+        v += ww * 0.5f * (c.dVz[dc][mg_q(c.b, xs[cc], ys[bb], n0)] + c.dVz[dc][mg_q(c.b, xs[cc], ys[bb], n1)]);
+      }
+    f.dVz[df][q] += v;
+  }
+}
+
+void mg_coef(cudaStream_t s, const MgLevel& f, const MgLevel& c, float dtaupt_fac, float dtauv_fac) {
+  const dim3 bl(32, 8, 1), g((c.b.nx + 31) / 32, (c.b.ny + 7) / 8, c.b.nz);
+  k_mg_coef<<<g, bl, 0, s>>>(f, c, dtaupt_fac, dtauv_fac);
+}
+void mg_restrict(cudaStream_t s, const MgLevel& f, const MgLevel& c, float rho_i) {
+  const dim3 bl(32, 8, 1), g((c.b.nx + 1 + 31) / 32, (c.b.ny + 1 + 7) / 8, c.b.nz + 1);
+  k_mg_restrict<<<g, bl, 0, s>>>(f, c, rho_i);
+}
+void mg_prolong(cudaStream_t s, const MgLevel& c, int dc, const MgLevel& f, int df) {
+  const dim3 bl(32, 8, 1), g((f.b.nx + 1 + 31) / 32, (f.b.ny + 1 + 7) / 8, f.b.nz + 1);
+  k_mg_prolong<<<g, bl, 0, s>>>(c, dc, f, df);
+}
+
+// ============================================================ batched FP32 ensembles (engine)
+namespace {
+
+__device__ inline unsigned long long mb_global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Last member whose first work item (tile_base or ctile_base) is <= t.
+template <long long MixBatchInst::*BASE>
+__device__ inline int mb_find(const MixBatchInst* inst, int ninst, long long t) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].*BASE <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ inline bool mb_runs(int phase, const MixBatchStatus& s) {
+  switch (phase) {
+    case MB_PH_PERM: case MB_PH_PREP: case MB_PH_FACES: return s.phase == MB_PREP;
+    case MB_PH_INIT: return s.phase == MB_INNER && s.fresh;
+    default: return s.phase == MB_UPDATE;
+  }
+}
+
+constexpr int kMbBX = 32, kMbBY = 8;   // point tiles: 32 x 8 cells of one z-level
+
+}  // namespace
+
+// The point phases over every member's tiles (grid-stride over the flat work list; a member not
+// in the phase skips its tiles, uniformly per CTA, so the block-wide reductions stay collective).
+template <int PHASE>
+__global__ void __launch_bounds__(kMbBX * kMbBY) k_mb_points(const MixBatchInst* __restrict__ inst,
+                                                            const MixBatchStatus* __restrict__ st, int ninst,
+                                                            long long ntiles) {
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int m = mb_find<&MixBatchInst::tile_base>(inst, ninst, t);
+    const MixBatchStatus& S = st[m];
+    if (!mb_runs(PHASE, S)) continue;
+    const MixBatchInst& I = inst[m];
+    const long long local = t - I.tile_base;
+    const long long per_z = (long long)I.gx * I.gy;
+    const int kz = (int)(local / per_z);
+    const int r = (int)(local - (long long)kz * per_z);
+    const int ty = r / I.gx, tx = r - ty * I.gx;
+    const int i = tx * kMbBX + threadIdx.x, j = ty * kMbBY + threadIdx.y;
+    const Box& b = I.b;
+    const int a = S.cur;
+    if (PHASE == MB_PH_PERM) {
+      perm_point(b, I.k, I.phi[a], I.logk, I.perm, I.rog, i, j, kz);
+    } else if (PHASE == MB_PH_PREP) {
+      const MixPrepIn pin{I.Vx, I.Vy, I.Vz, I.Pt[a], I.Pf[a], I.phi[a], I.mu, I.eta, I.perm, I.Pto, I.Pfo,
+                          I.txxo, I.tyyo, I.tzzo};
+      const MixPrepOut pout{I.s_txx, I.s_tyy, I.s_tzz, I.rpt, I.rpf, I.ccf, I.kf, I.idtp};
+      double r_pt = 0.0, r_pf = 0.0;
+      mix_prepare_point(b, I.k, pin, pout, i, j, kz, r_pt, r_pf);
+      edges_point(b, I.k, EdgeIn{I.Vx, I.Vy, I.Vz, I.mu, I.txyo, I.txzo, I.tyzo},
+                  EdgeOut{I.s_txy, I.s_txz, I.s_tyz}, i, j, kz);
+      block_max_atomic(r_pt, I.red + RED_PT);
+      block_max_atomic(r_pf, I.red + RED_PF);
+    } else if (PHASE == MB_PH_FACES) {
+      double r_v = 0.0, pic = 1.0;
+      mix_res_faces_point(b, I.k, MixFaceIn{I.s_txx, I.s_tyy, I.s_tzz, I.s_txy, I.s_txz, I.s_tyz, I.Pt[a], I.phi[a]},
+                          I.rfx, I.rfy, I.rfz, i, j, kz, r_v);
+      lean_picard_point(b, I.lc,
+                        LeanPicardIn<double>{I.s_txx, I.s_tyy, I.s_tzz, I.s_txy, I.s_txz, I.s_tyz, I.phi[a],
+                                             I.Pt[a], I.Pf[a]},
+                        I.mu, I.eta, i, j, kz, pic);
+      block_max_atomic(r_v, I.red + RED_V);
+      block_max_log_atomic(pic, I.red + RED_PIC);
+    } else if (PHASE == MB_PH_INIT) {
+      mix_coef_point(b, I.k, I.mu, MixCoefOut{I.muf, I.dtvc}, i, j, kz);
+      if (i <= b.nx && j <= b.ny && kz <= b.nz) {   // a zero correction and damped residual
+        const long long q = cidx(b, i, j, kz);
+        I.dVx[0][q] = 0.f; I.dVx[1][q] = 0.f; I.dVy[0][q] = 0.f; I.dVy[1][q] = 0.f;
+        I.dVz[0][q] = 0.f; I.dVz[1][q] = 0.f; I.dPt[0][q] = 0.f; I.dPf[0][q] = 0.f;
+        I.Rx[q] = 0.f; I.Ry[q] = 0.f; I.Rz[q] = 0.f;
+      }
+    } else if (PHASE == MB_PH_UPDATE) {
+      const int d = S.inner & 1;   // the last correction's buffer
+      mix_update_point(b, MixUpdate{I.Vx, I.Vy, I.Vz, I.Pt[a], I.Pf[a], I.dVx[d], I.dVy[d], I.dVz[d], I.dPt[d],
+                                    I.dPf[d], S.omega}, i, j, kz);
+    } else {   // MB_PH_POROSITY: phi moves to the other buffer, the pressures follow it
+      porosity_point(b, I.k, I.Vx, I.Vy, I.Vz, I.phi[a], I.Pt[a], I.Pf[a], I.Pto, I.Pfo, I.Lo, I.eta,
+                     I.phi[1 - a], i, j, kz);
+      if (i < b.nx && j < b.ny && kz < b.nz) {
+        const long long q = cidx(b, i, j, kz);
+        I.Pt[1 - a][q] = I.Pt[a][q];
+        I.Pf[1 - a][q] = I.Pf[a][q];
+      }
+    }
+  }
+}
+
+// Correction iteration number inner + step of the members in MB_INNER (within their budget),
+// one corr_tile per work item; the block's shared memory is reused from tile to tile.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_mb_corr(const MixBatchInst* __restrict__ inst,
+                                                       const MixBatchStatus* __restrict__ st, int ninst,
+                                                       long long nctiles, int step, int nup, int zchunk) {
+  extern __shared__ __align__(16) float corr_smem[];
+  for (long long t = blockIdx.x; t < nctiles; t += gridDim.x) {
+    const int m = mb_find<&MixBatchInst::ctile_base>(inst, ninst, t);
+    const MixBatchStatus& S = st[m];
+    const MixBatchInst& I = inst[m];
+    const int it = S.inner + step;
+    if (S.phase != MB_INNER || it > I.max_iter - S.iters) continue;
+    const int d = (it - 1) & 1;
+    const long long local = t - I.ctile_base;
+    const long long per_z = (long long)I.cgx * I.cgy;
+    const int bz = (int)(local / per_z);
+    const int r = (int)(local - (long long)bz * per_z);
+    const int tby = r / I.cgx, tbx = r - tby * I.cgx;
+    const int k0 = bz * zchunk;
+    corr_tile(I.b, I.cc, I.cin[d], I.cout[d], tbx, tby, k0, min(k0 + zchunk, I.b.nz + 1), I.ired, step == nup,
+              corr_smem);
+    __syncthreads();   // the next tile's stage and rings overwrite this one's
+  }
+}
+
+// Outer decision of the members in MB_PREP (the host loop's, in the same order): non-finite
+// norms stop the member (PT_ENAN), norms below tol end its step (PT_OK); otherwise the outer
+// weight adapts (halved down to 1/16 when the residual more than doubled, grown by 1.25 up to 1
+// while it falls), the inner target is rtol times the residual, and a correction solve starts.
+__global__ void k_mb_decide_outer(const MixBatchInst* __restrict__ inst, MixBatchStatus* __restrict__ st,
+                                  int ninst) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ninst || st[m].phase != MB_PREP) return;
+  MixBatchStatus& S = st[m];
+  unsigned long long* red = inst[m].red;
+  const int slot[4] = {RED_V, RED_PT, RED_PF, RED_PIC};
+  bool finite = true;
+  double r = 0.0;
+  for (int s = 0; s < 4; ++s) {
+    const double v = __longlong_as_double((long long)red[slot[s]]);
+    S.res[s] = v;
+    finite = finite && isfinite(v);
+    r = fmax(r, v);
+    red[slot[s]] = 0ull;
+  }
+  if (!finite) {
+    S.phase = MB_DONE;
+    S.status = PT_ENAN;
+    S.t_stop = mb_global_ns();
+    return;
+  }
+  if (r < inst[m].tol) {
+    S.phase = MB_DONE;
+    S.status = PT_OK;
+    S.t_stop = mb_global_ns();
+    return;
+  }
+  if (S.prev > 0.0) {
+    if (r > 2.0 * S.prev) S.omega = fmax(S.omega * 0.5, 0.0625);
+    else if (r < S.prev) S.omega = fmin(S.omega * 1.25, 1.0);
+  }
+  S.prev = r;
+  S.target = inst[m].rtol * r;
+  S.phase = MB_INNER;
+  S.fresh = 1;
+  S.inner = 0;
+}
+
+// Inner decision after `nup` correction launches: the iterations that ran are counted; after a
+// check iteration a non-finite norm stops the member (PT_ENAN) and a drop below the target ends
+// the solve; so does a spent budget (max_iter - iters).
+__global__ void k_mb_decide_inner(const MixBatchInst* __restrict__ inst, MixBatchStatus* __restrict__ st,
+                                  int ninst, int nup) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ninst || st[m].phase != MB_INNER) return;
+  MixBatchStatus& S = st[m];
+  S.fresh = 0;
+  const int budget = inst[m].max_iter - S.iters;
+  const int ran = min(nup, budget - S.inner);
+  S.inner += ran;
+  bool stop = S.inner >= budget;
+  if (ran == nup) {   // the last launch was a check iteration
+    unsigned long long* red = inst[m].ired;
+    const double v = __longlong_as_double((long long)red[RED_V]);
+    const double pt = __longlong_as_double((long long)red[RED_PT]);
+    const double pf = __longlong_as_double((long long)red[RED_PF]);
+    red[RED_V] = 0ull;
+    red[RED_PT] = 0ull;
+    red[RED_PF] = 0ull;
+    if (!(isfinite(v) && isfinite(pt) && isfinite(pf))) {
+      S.iters += S.inner;
+      S.phase = MB_DONE;
+      S.status = PT_ENAN;
+      S.t_stop = mb_global_ns();
+      return;
+    }
+    if (fmax(fmax(v, pt), pf) < S.target) stop = true;
+  }
+  if (stop) S.phase = MB_UPDATE;
+}
+
+// End of an outer iteration: the iterate moved to the other buffers; the solve's iterations are
+// counted; a member whose budget is spent stops unconverged (PT_ENOTCONV), the others go on.
+__global__ void k_mb_finish(const MixBatchInst* __restrict__ inst, MixBatchStatus* __restrict__ st, int ninst) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ninst || st[m].phase != MB_UPDATE) return;
+  MixBatchStatus& S = st[m];
+  S.cur = 1 - S.cur;
+  S.iters += S.inner;
+  S.inner = 0;
+  S.outer += 1;
+  if (S.iters >= inst[m].max_iter) {
+    S.phase = MB_DONE;
+    S.status = PT_ENOTCONV;
+    S.t_stop = mb_global_ns();
+  } else {
+    S.phase = MB_PREP;
+  }
+}
+
+__global__ void k_mb_start(const MixBatchInst* __restrict__ inst, MixBatchStatus* __restrict__ st, int ninst) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ninst) return;
+  MixBatchStatus& S = st[m];
+  S.phase = MB_PREP;
+  S.cur = 0;
+  S.inner = 0;
+  S.iters = 0;
+  S.outer = 0;
+  S.status = PT_ENOTCONV;
+  S.fresh = 0;
+  S.omega = 1.0;
+  S.prev = 0.0;
+  S.target = 0.0;
+  for (int s = 0; s < 4; ++s) S.res[s] = 0.0;
+  for (int s = 0; s < RED_N; ++s) {
+    inst[m].red[s] = 0ull;
+    inst[m].ired[s] = 0ull;
+  }
+  S.t_start = mb_global_ns();
+  S.t_stop = 0ull;
+}
+
+void mb_points(int grid, cudaStream_t s, int phase, const MixBatchInst* inst, const MixBatchStatus* st, int ninst,
+               long long ntiles) {
+  const dim3 bl(kMbBX, kMbBY, 1);
+  switch (phase) {
+    case MB_PH_PERM: k_mb_points<MB_PH_PERM><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
+    case MB_PH_PREP: k_mb_points<MB_PH_PREP><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
+    case MB_PH_FACES: k_mb_points<MB_PH_FACES><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
+    case MB_PH_INIT: k_mb_points<MB_PH_INIT><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
+    case MB_PH_UPDATE: k_mb_points<MB_PH_UPDATE><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
+    default: k_mb_points<MB_PH_POROSITY><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
+  }
+}
+
+void mb_corr(int grid, int minb, cudaStream_t s, const MixBatchInst* inst, const MixBatchStatus* st, int ninst,
+             long long nctiles, int step, int nup, int zchunk) {
+  if (minb == 3) {
+    k_mb_corr<3><<<grid, dim3(32, 8, 1), kCorrSmemBytes, s>>>(inst, st, ninst, nctiles, step, nup, zchunk);
+  } else {
+    k_mb_corr<4><<<grid, dim3(32, 8, 1), kCorrSmemBytes, s>>>(inst, st, ninst, nctiles, step, nup, zchunk);
+  }
+}
+
+void mb_decide_outer(cudaStream_t s, const MixBatchInst* inst, MixBatchStatus* st, int ninst) {
+  k_mb_decide_outer<<<(ninst + 127) / 128, 128, 0, s>>>(inst, st, ninst);
+}
+void mb_decide_inner(cudaStream_t s, const MixBatchInst* inst, MixBatchStatus* st, int ninst, int nup) {
+  k_mb_decide_inner<<<(ninst + 127) / 128, 128, 0, s>>>(inst, st, ninst, nup);
+}
+void mb_finish(cudaStream_t s, const MixBatchInst* inst, MixBatchStatus* st, int ninst) {
+  k_mb_finish<<<(ninst + 127) / 128, 128, 0, s>>>(inst, st, ninst);
+}
+void mb_start(cudaStream_t s, const MixBatchInst* inst, MixBatchStatus* st, int ninst) {
+  k_mb_start<<<(ninst + 127) / 128, 128, 0, s>>>(inst, st, ninst);
+}
+
+int mb_points_blocks_per_sm() {
+  int n = 0;
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mb_points<MB_PH_PREP>, kMbBX * kMbBY, 0);
+  return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+int mb_corr_blocks_per_sm(int minb) {
+  int n = 0;
+  cudaError_t e;
+  if (minb == 3) {
+    cudaFuncSetAttribute(k_mb_corr<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCorrSmemBytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mb_corr<3>, 256, kCorrSmemBytes);
+  } else {
+    cudaFuncSetAttribute(k_mb_corr<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCorrSmemBytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mb_corr<4>, 256, kCorrSmemBytes);
+  }
+  return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+int corr_tile_x() { return kCorrTX; }
+int corr_tile_y() { return kCorrTY; }
 
 }  // namespace pt

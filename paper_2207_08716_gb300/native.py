@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_BUILD, "libpt_gb300.so")
 SOURCES = ("pt_api.cu", "pt_ref_kernels.cu", "pt_lean_kernels.cu", "pt_mixed_kernels.cu",
            "pt_batch_kernels.cu", "pt_adjoint_kernels.cu", "pt_dd_kernels.cu", "pt_static.cu", "pt_peaks.cu",
            "rx_api.cu", "rx_kernels.cu", "rx_mg_kernels.cu")
-HEADERS = ("pt_common.cuh", "pt_host.h", "pt_kernels.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "df64.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
+HEADERS = ("pt_common.cuh", "pt_host.h", "pt_kernels.cuh", "pt_ref_points.cuh", "pt_lean.cuh", "pt_lean_body.cuh", "df64.cuh", "pt_mixed.cuh", "pt_batch.cuh", "pt_adjoint.cuh", "pt_dd.cuh", "rx.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 _lock = threading.Lock()
@@ -80,7 +80,7 @@ class Num(C.Structure):
                 ("beta_n", C.c_double), ("rel_mu", C.c_double), ("rel_eta", C.c_double),
                 ("cfl_v", C.c_double), ("cfl_pf", C.c_double), ("dtpt_scale", C.c_double),
                 ("xsi_w", C.c_double), ("precision", C.c_int32), ("iters_per_graph", C.c_int32),
-                ("inner_rtol", C.c_double)]
+                ("inner_rtol", C.c_double), ("mg_levels", C.c_int32), ("mg_reserved", C.c_int32)]
 
 
 FIELD_NAMES = ("Vx", "Vy", "Vz", "Pt", "Pf", "phi", "txx", "tyy", "tzz", "txy", "txz", "tyz",
@@ -122,6 +122,10 @@ def num_from(p: dict, precision: int = PT_FP64, iters_per_graph: int = 0) -> Num
             nm.iters_per_graph = p.get("iters_per_graph", iters_per_graph)
         elif n == "inner_rtol":
             nm.inner_rtol = p.get("inner_rtol", 0.0)
+        elif n == "mg_levels":
+            nm.mg_levels = p.get("mg_levels", 0)
+        elif n == "mg_reserved":
+            nm.mg_reserved = 0
         else:
             setattr(nm, n, p[n])
     return nm
@@ -209,6 +213,7 @@ SIGNATURES = {
                                 C.POINTER(Num), C.POINTER(Fields), C.c_void_p, C.c_size_t, C.c_void_p]),
     "pt_batch_step": (C.c_int, [C.c_void_p, C.POINTER(Report), C.POINTER(C.c_double)]),
     "pt_batch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pt_batch_config_fp32": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pt_batch_destroy": (None, [C.c_void_p]),
     "pt_destroy": (None, [C.c_void_p]),
     "pt_strerror": (C.c_char_p, [C.c_int]),

@@ -227,8 +227,8 @@ class PTBatch:
     """An ensemble of independent instances advanced together (pt_batch_* of the C ABI).
 
     members: list of (params, phi) or (params, phi, logk); every instance uses the same nup and
-    the same precision: PT_FP64 (the FP64-lean form in the persistent batched engine) or PT_FP32
-    (defect-correction solvers stepped concurrently, each on a stream of its own).
+    the same precision: PT_FP64 (the FP64-lean form) or PT_FP32 (the FP32 + FP64
+    defect-correction form), either way in the library's persistent batched engine.
     """
 
     def __init__(self, members, device="cuda", stream=None, precision: int = N.PT_FP64):
@@ -283,6 +283,14 @@ class PTBatch:
         bx, by, ipg = C.c_int32(), C.c_int32(), C.c_int32()
         self.lib.pt_batch_config(self.h, C.byref(bx), C.byref(by), C.byref(ipg))
         return bx.value, by.value, ipg.value
+
+    def config_fp32(self) -> tuple:
+        """FP32 ensembles: (correction tile depth, CTAs per SM of the correction kernel)."""
+        tz, mb = C.c_int32(), C.c_int32()
+        rc = self.lib.pt_batch_config_fp32(self.h, C.byref(tz), C.byref(mb))
+        if rc != N.PT_OK:
+            raise PTError(rc, "pt_batch_config_fp32")
+        return tz.value, mb.value
 
     def get(self, m: int, name: str) -> np.ndarray:
         torch.cuda.synchronize(self.device)

@@ -3,8 +3,10 @@ same iteration count and status at its own convergence check, fields equal to 1e
 (the per-point code is shared; the compiler may fuse multiply-adds differently in the two
 kernels, so the last bits can differ) — whatever tile shape and iterations per graph the tuner
 picks; and it agrees with the FP64 oracle within the 1e-10 parity bar. The FP32 ensemble
-(defect-correction solvers on their own streams, stepped concurrently) reproduces each
-instance's single-solver FP32 run exactly: concurrency does not enter the arithmetic."""
+(the defect-correction form in the same persistent engine, its outer and inner decisions taken
+on the device per member) reproduces each member's single-solver FP32 run bit for bit, iteration
+counts included, whatever correction tile depth, CTAs per SM and rounds per replay the tuner
+tries or keeps, with members stopping at their cap at the end of a round and inside one."""
 import numpy as np
 import pytest
 
@@ -80,20 +82,43 @@ def test_fp32_ensemble_instances_equal_single_fp32_runs():
     PTBatch, PTSolver = _mods()
     from paper_2207_08716_gb300 import native as N
     mem = I.ensemble(seed=5, n_inst=5, sizes=(9, 12, 16), max_iter=6000)
-    mem[1][0]["max_iter"] = 60             # one instance hits its cap
+    mem[1][0]["max_iter"] = 60             # cap at the end of a round (nup = 15)
+    mem[3][0]["max_iter"] = 97             # cap inside a round
     b = PTBatch(mem, precision=N.PT_FP32)
-    assert b.config() == (0, 0, 0)
     reps, ttc = b.step()
     reps2, _ = b.step()
+    tx, ty, ipg = b.config()
+    assert (tx, ty) == (30, 6) and ipg in (15, 30), (tx, ty, ipg)
+    assert b.config_fp32()[0] in (32, 64, 128) and b.config_fp32()[1] in (3, 4)
     for m, (p, phi) in enumerate(mem):
         s = PTSolver(dict(p, precision=N.PT_FP32), phi)
         r1 = s.step()
         r2 = s.step()
         assert (reps[m]["iters"], reps[m]["status"]) == (r1["iters"], r1["status"]), (m, reps[m], r1)
         assert (reps2[m]["iters"], reps2[m]["status"]) == (r2["iters"], r2["status"]), (m, reps2[m], r2)
+        for k in ("r_v", "r_pt", "r_pf", "r_pic"):
+            assert reps2[m][k] == r2[k], (m, k, reps2[m][k], r2[k])
         for name in FIELDS:
             np.testing.assert_array_equal(b.get(m, name), s.get(name), err_msg=f"{m} {name}")
         s.close()
-    assert reps[1]["status"] == -2
+    assert reps[1]["status"] == -2 and reps[1]["iters"] == 60
+    assert reps[3]["status"] == -2 and reps[3]["iters"] == 97
     assert all(t > 0 for t in ttc)
+    b.close()
+
+
+def test_fp32_ensemble_of_uneven_members_converges_like_single_runs():
+    """Members of several sizes and parameter sets converging after different numbers of outer
+    iterations: each stops at its own outer check, with the single run's iteration count."""
+    PTBatch, PTSolver = _mods()
+    from paper_2207_08716_gb300 import native as N
+    mem = I.ensemble(seed=8, n_inst=4, sizes=(12, 20, 24), max_iter=20000)
+    b = PTBatch(mem, precision=N.PT_FP32)
+    reps, _ = b.step()
+    for m, (p, phi) in enumerate(mem):
+        s = PTSolver(dict(p, precision=N.PT_FP32), phi)
+        r = s.step()
+        assert reps[m]["status"] == r["status"] == 0 and reps[m]["iters"] == r["iters"], (m, reps[m], r)
+        np.testing.assert_array_equal(b.get(m, "phi"), s.get("phi"))
+        s.close()
     b.close()
