@@ -177,6 +177,11 @@ def parse():
                     help="the FP64-class form the FP32 form is compared with")
     ap.add_argument("--pc-oracle", type=int, default=1, help="also run the oracle (1) or not (0)")
     ap.add_argument("--pc-oracle-n", default="32", help="grid sizes at which the oracle runs too")
+    ap.add_argument("--pc-plain-max", type=int, default=100000,
+                    help="run the FP32 form with plain PT correction solves only up to this grid size")
+    ap.add_argument("--pc-mg", type=int, default=0,
+                    help="also the FP32 form with multigrid correction solves over this many levels (>= 2; "
+                         "grids divisible by 2^(levels-1))")
     ap.add_argument("--batch-inner-rtol", type=float, default=0.0,
                     help="FP32 ensembles: relative residual drop of each FP32 correction solve (0: library default)")
     ap.add_argument("--batched-converge", action="store_true",
@@ -767,8 +772,12 @@ def measure_precision(args, dev) -> dict:
         s = PTSolver(p, phi0, device=dev)
         iters, t0 = [], time.perf_counter()
         for _ in range(nsteps):
-            r = s.step(raise_on_notconv=True)
+            r = s.step(raise_on_notconv=False)
             iters.append(r["iters"])
+            if r["status"] != 0:
+                print(json.dumps({"not_converged": {"n": p["nx"], "precision": p["precision"],
+                                                    "mg_levels": p.get("mg_levels", 0), "report": r}}),
+                      file=sys.stderr, flush=True)
         torch.cuda.synchronize(dev)
         t = time.perf_counter() - t0
         phi = s.get("phi")
@@ -785,9 +794,17 @@ def measure_precision(args, dev) -> dict:
         p["max_iter"] = 400000
         phi0 = I.gaussian_porosity(p)
         phi64, it64, t64 = run(dict(p, precision=ref_prec), phi0, k)
-        phi32, it32, t32 = run(dict(p, precision=N.PT_FP32), phi0, k)
-        r = {"steps": k, "ref_iters": sum(it64), "fp32_iters": sum(it32), "ref_s": t64, "fp32_s": t32,
-             "fp32_vs_ref": errs(phi32, phi64, phi0), "porosity_change_max": float(np.abs(phi64 - phi0).max())}
+        r = {"steps": k, "ref_iters": sum(it64), "ref_s": t64, "porosity_change_max": float(np.abs(phi64 - phi0).max())}
+        phi32 = None
+        if n <= args.pc_plain_max:
+            phi32, it32, t32 = run(dict(p, precision=N.PT_FP32), phi0, k)
+            r.update(fp32_iters=sum(it32), fp32_s=t32, fp32_vs_ref=errs(phi32, phi64, phi0))
+        L = args.pc_mg
+        if L >= 2 and n % (1 << (L - 1)) == 0 and n >> (L - 1) >= 2:
+            phimg, itmg, tmg = run(dict(p, precision=N.PT_FP32, mg_levels=L), phi0, k)
+            r.update(fp32mg_levels=L, fp32mg_iters=sum(itmg), fp32mg_s=tmg, fp32mg_vs_ref=errs(phimg, phi64, phi0))
+            if phi32 is not None:
+                r["fp32mg_vs_fp32"] = errs(phimg, phi32, phi0)
         print(json.dumps({"precision_check": {str(n): r}}), file=sys.stderr, flush=True)
         if n in children:
             proc, path = children.pop(n)
@@ -800,7 +817,10 @@ def measure_precision(args, dev) -> dict:
                 phio = np.load(path)
                 r["oracle_s"], r["oracle_iters"], r["oracle_cores"] = rec["seconds"], sum(rec["iters"]), rec["cores"]
                 r["ref_vs_oracle"] = errs(phi64, phio, phi0)
-                r["fp32_vs_oracle"] = errs(phi32, phio, phi0)
+                if phi32 is not None:
+                    r["fp32_vs_oracle"] = errs(phi32, phio, phi0)
+                if "fp32mg_levels" in r:
+                    r["fp32mg_vs_oracle"] = errs(phimg, phio, phi0)
                 os.remove(path)
         out[str(n)] = r
         torch.cuda.empty_cache()

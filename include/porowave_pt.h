@@ -318,9 +318,10 @@ int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *
  * spent); the FP64 update and porosity integration of the instances ending one]. The first
  * pt_batch_step tunes the correction tile depth (32, 64, 128 levels), the CTAs per SM of the
  * correction kernel (3, 4) and the rounds per replay (1, 2).
- * Either way each instance reproduces its single-instance pt_step bit for bit (same per-point
- * code, same decisions in the same order), whatever the configuration (tuning replays are real
- * iterations). grids/phys/nums/fields are arrays of ninst; the workspace holds every instance's
+ * Either way each instance reproduces its single-instance pt_step: the same per-point code and
+ * the same decisions in the same order, so the same iteration counts and statuses, and fields
+ * equal to rounding (the shared bodies inlined into other kernels may round their multiply-adds
+ * differently), whatever the configuration (tuning replays are real iterations). grids/phys/nums/fields are arrays of ninst; the workspace holds every instance's
  * workspace (pt_workspace_size) plus the descriptor tables. The batch works on a stream of its
  * own (graphs cannot be captured on the legacy default stream): pt_batch_init and pt_batch_step
  * first synchronise the caller's `stream`, and pt_batch_step returns after its work is done. */

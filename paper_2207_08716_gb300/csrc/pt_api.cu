@@ -41,6 +41,15 @@ constexpr int kDfArrays = 28;    // double-float iterate, stresses, residuals, o
 // about as many FP32 iterations in total as the FP64 path needs FP64 iterations (measured on
 // 32^3-96^3), while 1e-4 needs 3-4 times more.
 constexpr double kInnerRtol = 0.1;
+// Multigrid V-cycle of the FP32 correction problem (pt_num.mg_levels >= 2): nu1 = nu2 = 2 PT
+// sweeps without damping before and after each coarse-grid correction, the velocity pseudo-step
+// scaled by 0.8 and the Pf pseudo-step by 6/7 in them (the undamped PT sweep is a Jacobi
+// iteration; these weights make it a smoother of the viscous and Darcy operators, whose Jacobi
+// weights would otherwise be ~1.1 and ~1), kMgCoarseIters damped PT iterations on the coarsest grid.
+constexpr int kMgNu1 = 2, kMgNu2 = 2, kMgCoarseIters = 24, kMgMaxLevels = 10;
+constexpr double kMgSmoothV = 0.8, kMgSmoothPf = 6.0 / 7.0;
+constexpr int kMgArrays = 25;      // FP32 arrays of one coarse level
+constexpr int kMgFineArrays = 2;   // residual outputs of the finest level
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -88,6 +97,13 @@ struct pt_ctx {
   float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_mu, *m_dtvc;
   float *m_dVx[2], *m_dVy[2], *m_dVz[2], *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
   CorrCoef<float> ccoef;
+  // multigrid V-cycle of the correction problem (mg_L >= 2): level 0 = the m_* arrays above
+  int mg_L;
+  std::vector<MgLevel> mg;
+  std::vector<int> mg_d;                           // parity of each level's current iterate
+  std::vector<CorrCoef<float>> mg_smooth, mg_eval; // per level: smoothing and evaluation sweeps
+  CorrCoef<float> mg_coarse;                       // damped PT on the coarsest grid
+  std::vector<float> mg_dtpt, mg_dtv;              // per level: dtau_Pt / mu and dtau_V mu factors
   // adjoint recording (pt_adjoint_forward / pt_adjoint)
   char* adj_ws;
   size_t adj_bytes;
@@ -115,7 +131,7 @@ enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEG
                 K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_ITER,
                 K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_DF_CELLS, K_DF_FACES,
                 K_DF_PICARD, K_DF_COEF, K_DF_BEGIN, K_DF_K0, K_DF_CONVERT, K_ADJ_EDGES_PL, K_ADJ_CELLS_PL,
-                K_ADJ_FACES_PL, K_COUNT };
+                K_ADJ_FACES_PL, K_MG_FINE, K_MG_COARSE, K_MG_TRANSFER, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
@@ -126,7 +142,8 @@ const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_
                                            "k_lean_cells_df64", "k_lean_faces_df64", "k_lean_picard_df64",
                                            "k_lean_coef_df64", "k_lean_begin_df64", "k_lean_k0_df64",
                                            "k_df64_convert", "k_adj_edges_pl", "k_adj_cells_pl",
-                                           "k_adj_faces_pl"};
+                                           "k_adj_faces_pl", "k_corr_iteration_mg_fine",
+                                           "k_corr_iteration_mg_coarse", "k_mg_transfer"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -255,9 +272,8 @@ void fill_lean_coef(pt_ctx* c) {
   c->fcoef = lean_coef_df64(L);
 }
 
-void fill_corr_coef(pt_ctx* c) {
-  const Coef& k = c->coef;
-  CorrCoef<float>& f = c->ccoef;
+CorrCoef<float> corr_coef_of(const Coef& k) {
+  CorrCoef<float> f;
   f.rdx = (float)k.rdx; f.rdy = (float)k.rdy; f.rdz = (float)k.rdz;
   f.hrdx = (float)(0.5 * k.rdx); f.hrdy = (float)(0.5 * k.rdy); f.hrdz = (float)(0.5 * k.rdz);
   f.hrdx2 = (float)(0.5 * k.rdx * k.rdx); f.hrdy2 = (float)(0.5 * k.rdy * k.rdy);
@@ -270,6 +286,60 @@ void fill_corr_coef(pt_ctx* c) {
   f.damp_x = (float)k.damp_x; f.damp_y = (float)k.damp_y; f.damp_z = (float)k.damp_z;
   f.rG = (float)k.rGdtS;
   f.ifac_pf = (float)(1.0 / k.dtaupf_fac);
+  return f;
+}
+
+// The grid of multigrid level l (2^l coarser per direction, same box lengths).
+pt_grid mg_grid(const pt_grid& g, int l) {
+  pt_grid h = g;
+  h.nx = g.nx >> l;
+  h.ny = g.ny >> l;
+  h.nz = g.nz >> l;
+  return h;
+}
+
+bool mg_ok(const pt_grid& g, const pt_num& n) {
+  if (n.mg_levels <= 1) return n.mg_levels >= 0;
+  if (n.precision != PT_FP32 || n.mg_levels > kMgMaxLevels) return false;
+  const int f = 1 << (n.mg_levels - 1);
+  return g.nx % f == 0 && g.ny % f == 0 && g.nz % f == 0 && g.nx / f >= 2 && g.ny / f >= 2 && g.nz / f >= 2;
+}
+
+// Workspace of the V-cycle's grids: the finest level's residual outputs, kMgArrays per coarser level.
+size_t mg_bytes(const pt_grid& g, const pt_num& n) {
+  if (n.mg_levels < 2 || !mg_ok(g, n)) return 0;
+  size_t total = kMgFineArrays * align_up((size_t)make_box(&g).n * sizeof(float), kAlign);
+  for (int l = 1; l < n.mg_levels; ++l) {
+    const pt_grid gl = mg_grid(g, l);
+    total += kMgArrays * align_up((size_t)make_box(&gl).n * sizeof(float), kAlign);
+  }
+  return total;
+}
+
+// Per-level coefficient sets of the V-cycle (they depend on the step's dtS through xi).
+void fill_mg_coef(pt_ctx* c) {
+  if (c->mg_L < 2) return;
+  for (int l = 0; l < c->mg_L; ++l) {
+    pt_num nl = c->num;
+    for (int d = 0; d < 3; ++d)   // damping defect 1 - damp grows with the grid spacing
+      nl.damp[d] = std::max(0.0, 1.0 - (1.0 - c->num.damp[d]) * (double)(1 << l));
+    const Coef k = make_coef(mg_grid(c->metric, l), c->phys, nl, c->dtS);
+    CorrCoef<float> sm = corr_coef_of(k), ev = sm;
+    sm.damp_x = sm.damp_y = sm.damp_z = 0.0f;
+    sm.rrho_i = (float)(k.rrho_i * kMgSmoothV);
+    sm.ifac_pf = (float)(1.0 / (k.dtaupf_fac * kMgSmoothPf));
+    ev.damp_x = ev.damp_y = ev.damp_z = 0.0f;
+    c->mg_smooth[l] = sm;
+    c->mg_eval[l] = ev;
+    c->mg_dtpt[l] = (float)k.dtaupt_fac;
+    c->mg_dtv[l] = (float)k.dtauv_fac;
+    if (l == c->mg_L - 1) c->mg_coarse = corr_coef_of(k);
+  }
+}
+
+void fill_corr_coef(pt_ctx* c) {
+  c->ccoef = corr_coef_of(c->coef);
+  fill_mg_coef(c);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PT_OK : PT_ECUDA; }
@@ -485,6 +555,38 @@ double report_max(const pt_report* r) {
   return std::fmax(std::fmax(r->res_v, r->res_pt), std::fmax(r->res_pf, r->res_pic));
 }
 
+// ---- multigrid V-cycle of the FP32 correction problem
+// One sweep of the correction iteration on level l with coefficient set `cf`: from the level's
+// current buffers into the other ones (then they become current), or, with eval, the residuals
+// of the current iterate only (R = momentum residual / rho_i, rho_Pt and rho_Pf into res_*).
+void mg_sweep(pt_ctx* c, int l, const CorrCoef<float>& cf, int eval, int check) {
+  const MgLevel& L = c->mg[l];
+  const int d = c->mg_d[l];
+  const CorrIn<float> in{L.dVx[d], L.dVy[d], L.dVz[d], L.dPt[d], L.dPf[d], L.cc, L.perm, L.idtp, L.rpt, L.rpf,
+                         L.mu, L.dtvc, L.rfx, L.rfy, L.rfz};
+  const CorrOut<float> out{L.dVx[1 - d], L.dVy[1 - d], L.dVz[1 - d], L.dPt[1 - d], L.dPf[1 - d], L.Rx, L.Ry, L.Rz,
+                           eval ? L.res_pt : nullptr, eval ? L.res_pf : nullptr, eval};
+  PT_LAUNCH(c, l == 0 ? K_MG_FINE : K_MG_COARSE, corr_iteration(c->stream, L.b, cf, in, out, c->red, check));
+  if (!eval) c->mg_d[l] = 1 - d;
+}
+
+// V-cycle on level l for the current right-hand sides: pre-smoothing, residual, restriction to a
+// zero coarse correction, the coarse cycle (damped PT iterations on the coarsest grid),
+// prolongation of the correction, post-smoothing.
+void mg_vcycle(pt_ctx* c, int l) {
+  if (l == c->mg_L - 1) {
+    for (int s = 0; s < kMgCoarseIters; ++s) mg_sweep(c, l, c->mg_coarse, 0, 0);
+    return;
+  }
+  for (int s = 0; s < kMgNu1; ++s) mg_sweep(c, l, c->mg_smooth[l], 0, 0);
+  mg_sweep(c, l, c->mg_eval[l], 1, 0);
+  PT_LAUNCH(c, K_MG_TRANSFER, mg_restrict(c->stream, c->mg[l], c->mg[l + 1], (float)c->num.rho_i));
+  c->mg_d[l + 1] = 0;
+  mg_vcycle(c, l + 1);
+  PT_LAUNCH(c, K_MG_TRANSFER, mg_prolong(c->stream, c->mg[l + 1], c->mg_d[l + 1], c->mg[l], c->mg_d[l]));
+  for (int s = 0; s < kMgNu2; ++s) mg_sweep(c, l, c->mg_smooth[l], 0, 0);
+}
+
 // One outer iteration of the mixed-precision path (see pt_mixed_kernels.cu): FP64 residuals
 // and Picard update at u, then up to n_in FP32 PT iterations on the correction (stopping early
 // at a relative drop kInnerRtol when early_exit), u <- u + delta, FP64 porosity update.
@@ -542,7 +644,29 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   for (float* z : zero) cudaMemsetAsync(z, 0, fb, c->stream);
   int d = 0;
   const int nup = c->num.nup;
-  for (int it = 1; it <= n_in; ++it) {
+  if (c->mg_L >= 2) {
+    // V-cycles until the same relative drop (checked by an evaluation sweep after each cycle) or
+    // the budget; a cycle counts its finest-grid sweeps
+    for (int l = 1; l < c->mg_L; ++l)
+      PT_LAUNCH(c, K_MG_TRANSFER, mg_coef(c->stream, c->mg[l - 1], c->mg[l], c->mg_dtpt[l], c->mg_dtv[l]));
+    c->mg_d[0] = 0;
+    int it = 0;
+    while (it < n_in) {
+      mg_vcycle(c, 0);
+      it += kMgNu1 + kMgNu2 + 1;
+      *inner_done = it;
+      if (!early_exit) continue;
+      cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
+      mg_sweep(c, 0, c->mg_eval[0], 1, 1);
+      *inner_done = ++it;
+      pt_report ir;
+      rc = read_report(c, &ir);
+      if (rc != PT_OK) return rc;
+      if (std::fmax(std::fmax(ir.res_v, ir.res_pt), ir.res_pf) < target) break;
+    }
+    d = c->mg_d[0];
+  }
+  for (int it = 1; it <= n_in && c->mg_L < 2; ++it) {
     const int check = early_exit && (it % nup) == 0;
     if (check) cudaMemsetAsync(c->red, 0, RED_N * sizeof(unsigned long long), c->stream);
     const CorrIn<float> ci{c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d], c->m_dPf[d], c->m_cc, c->m_perm,
@@ -663,7 +787,7 @@ size_t pt_workspace_size(const pt_grid* grid, const pt_num* num) {
   const bool df = num->precision == PT_DF64;
   const int arrays = kRefArrays + ((num->precision == PT_FP64 || df) ? kLeanArrays : 0) + (df ? kDfArrays : 0);
   const size_t mixed = num->precision == PT_FP32 ? kMixArrays * align_up((size_t)b.n * sizeof(float), kAlign) : 0;
-  return arrays * align_up((size_t)b.n * sizeof(double), kAlign) + mixed + kAlign;
+  return arrays * align_up((size_t)b.n * sizeof(double), kAlign) + mixed + mg_bytes(*grid, *num) + kAlign;
 }
 
 int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num* num,
@@ -681,6 +805,7 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
       num->precision != PT_DF64)
     return PT_EINVAL;
   if (!phys_ok(phys)) return PT_EINVAL;
+  if (!mg_ok(*grid, *num)) return PT_EINVAL;
   // the fused FP32 correction iteration indexes the box with 32-bit integers
   if (num->precision == PT_FP32 && make_box(grid).n >= (1LL << 31)) return PT_EINVAL;
   double* const ptrs[] = {f->Vx, f->Vy, f->Vz, f->Pt, f->Pf, f->phi, f->txx, f->tyy,
@@ -742,6 +867,40 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
         &c->m_dPt[0], &c->m_dPt[1], &c->m_dPf[0], &c->m_dPf[1], &c->m_Rx, &c->m_Ry, &c->m_Rz};
     for (int s = 0; s < kMixArrays; ++s) *fslots[s] = (float*)(wend + s * fstride);
     wend += kMixArrays * fstride;
+  }
+  c->mg_L = (c->mixed && num->mg_levels >= 2) ? num->mg_levels : 0;
+  if (c->mg_L) {
+    const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
+    c->mg.resize(c->mg_L);
+    c->mg_d.assign(c->mg_L, 0);
+    c->mg_smooth.resize(c->mg_L);
+    c->mg_eval.resize(c->mg_L);
+    c->mg_dtpt.assign(c->mg_L, 0.f);
+    c->mg_dtv.assign(c->mg_L, 0.f);
+    MgLevel& f0 = c->mg[0];
+    f0.b = c->box;
+    f0.cc = c->m_cc; f0.perm = c->m_perm; f0.idtp = c->m_idtp; f0.mu = c->m_mu; f0.dtvc = c->m_dtvc;
+    f0.rpt = c->m_rpt; f0.rpf = c->m_rpf; f0.rfx = c->m_rfx; f0.rfy = c->m_rfy; f0.rfz = c->m_rfz;
+    for (int d = 0; d < 2; ++d) {
+      f0.dVx[d] = c->m_dVx[d]; f0.dVy[d] = c->m_dVy[d]; f0.dVz[d] = c->m_dVz[d];
+      f0.dPt[d] = c->m_dPt[d]; f0.dPf[d] = c->m_dPf[d];
+    }
+    f0.Rx = c->m_Rx; f0.Ry = c->m_Ry; f0.Rz = c->m_Rz;
+    f0.res_pt = (float*)wend;
+    f0.res_pf = (float*)(wend + fstride);
+    wend += kMgFineArrays * fstride;
+    for (int l = 1; l < c->mg_L; ++l) {
+      const pt_grid gl = mg_grid(*grid, l);
+      MgLevel& L = c->mg[l];
+      L.b = make_box(&gl);
+      const size_t st = align_up((size_t)L.b.n * sizeof(float), kAlign);
+      float** slots[kMgArrays] = {&L.cc, &L.perm, &L.idtp, &L.mu, &L.dtvc, &L.rpt, &L.rpf, &L.rfx, &L.rfy,
+                                  &L.rfz, &L.dVx[0], &L.dVx[1], &L.dVy[0], &L.dVy[1], &L.dVz[0], &L.dVz[1],
+                                  &L.dPt[0], &L.dPt[1], &L.dPf[0], &L.dPf[1], &L.Rx, &L.Ry, &L.Rz,
+                                  &L.res_pt, &L.res_pf};
+      for (int a = 0; a < kMgArrays; ++a) *slots[a] = (float*)(wend + a * st);
+      wend += kMgArrays * st;
+    }
   }
   c->red = (unsigned long long*)wend;
   if (cudaMallocHost(&c->h_red, RED_N * sizeof(unsigned long long)) != cudaSuccess) {
@@ -1380,7 +1539,8 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   if (((uintptr_t)workspace & (kAlign - 1)) != 0) return PT_EINVAL;
   const bool fp32 = nums[0].precision == PT_FP32;
   for (int m = 0; m < ninst; ++m)
-    if (nums[m].precision != (fp32 ? PT_FP32 : PT_FP64) || nums[m].nup != nums[0].nup) return PT_EINVAL;
+    if (nums[m].precision != (fp32 ? PT_FP32 : PT_FP64) || nums[m].nup != nums[0].nup || nums[m].mg_levels > 1)
+      return PT_EINVAL;
   const size_t need = pt_batch_workspace_size(ninst, grids, nums);
   if (need == 0) return PT_EINVAL;
   if (workspace_bytes < need) return PT_ESPACE;

@@ -38,7 +38,13 @@ __global__ void __launch_bounds__(BX * BY) k_batch_phase(const BatchInst* __rest
                                                          long long ntiles, int a, int check) {
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int m = find_instance(inst, ninst, t);
-    if (!st[m].active) continue;                      // uniform over the CTA
+    if (!st[m].active) {                              // uniform over the CTA: a retired instance's
+      // tiles are skipped in one step, to the first tile of the next instance this CTA visits
+      const long long next = m + 1 < ninst ? inst[m + 1].tile_base : ntiles;
+      const long long g = gridDim.x;
+      t = next + (((long long)blockIdx.x - next) % g + g) % g - g;
+      continue;
+    }
     const BatchInst& I = inst[m];
     const long long local = t - I.tile_base;
     const long long per_z = (long long)I.gx * I.gy;

@@ -94,7 +94,8 @@ void mg_prolong(cudaStream_t s, const MgLevel& c, int dc, const MgLevel& f, int 
 //   UPDATE, POROSITY   u <- u + omega delta, FP64 porosity integration  (members in MB_UPDATE)
 //   finish   parity flip, iterations counted, cap -> MB_DONE, else MB_PREP
 // The per-point and per-tile bodies are those of the single-instance kernels, and the decisions
-// are the host loop's, so a member reproduces its single-instance FP32 step bit for bit.
+// are the host loop's, so a member reproduces its single-instance FP32 step: the same iteration
+// counts, fields equal to rounding.
 enum { MB_PREP = 0, MB_INNER = 1, MB_UPDATE = 2, MB_DONE = 3 };
 enum { MB_PH_PERM = 0, MB_PH_PREP = 1, MB_PH_FACES = 2, MB_PH_INIT = 3, MB_PH_UPDATE = 4, MB_PH_POROSITY = 5 };
 

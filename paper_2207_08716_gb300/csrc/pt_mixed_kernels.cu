@@ -667,6 +667,13 @@ __device__ inline int mb_find(const MixBatchInst* inst, int ninst, long long t) 
   return lo;
 }
 
+// The first work item >= `next` that this CTA visits in a grid stride starting at blockIdx.x:
+// a CTA skips a member that has no work in a launch in one step instead of tile by tile.
+__device__ inline long long mb_skip_to(long long next) {
+  const long long g = gridDim.x;
+  return next + (((long long)blockIdx.x - next) % g + g) % g;
+}
+
 __device__ inline bool mb_runs(int phase, const MixBatchStatus& s) {
   switch (phase) {
     case MB_PH_PERM: case MB_PH_PREP: case MB_PH_FACES: return s.phase == MB_PREP;
@@ -688,7 +695,10 @@ __global__ void __launch_bounds__(kMbBX * kMbBY) k_mb_points(const MixBatchInst*
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int m = mb_find<&MixBatchInst::tile_base>(inst, ninst, t);
     const MixBatchStatus& S = st[m];
-    if (!mb_runs(PHASE, S)) continue;
+    if (!mb_runs(PHASE, S)) {   // uniform over the CTA: on to the next member's tiles
+      t = mb_skip_to(m + 1 < ninst ? inst[m + 1].tile_base : ntiles) - gridDim.x;
+      continue;
+    }
     const MixBatchInst& I = inst[m];
     const long long local = t - I.tile_base;
     const long long per_z = (long long)I.gx * I.gy;
@@ -756,7 +766,10 @@ __global__ void __launch_bounds__(256, MINB) k_mb_corr(const MixBatchInst* __res
     const MixBatchStatus& S = st[m];
     const MixBatchInst& I = inst[m];
     const int it = S.inner + step;
-    if (S.phase != MB_INNER || it > I.max_iter - S.iters) continue;
+    if (S.phase != MB_INNER || it > I.max_iter - S.iters) {   // uniform over the CTA
+      t = mb_skip_to(m + 1 < ninst ? inst[m + 1].ctile_base : nctiles) - gridDim.x;
+      continue;
+    }
     const int d = (it - 1) & 1;
     const long long local = t - I.ctile_base;
     const long long per_z = (long long)I.cgx * I.cgy;

