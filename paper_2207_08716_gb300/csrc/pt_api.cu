@@ -1339,6 +1339,8 @@ void fill_mix_inst(pt_batch* B, int m, long long base, long long cbase) {
   I.rpt = c->m_rpt; I.rpf = c->m_rpf; I.rfx = c->m_rfx; I.rfy = c->m_rfy; I.rfz = c->m_rfz;
   I.ccf = c->m_cc; I.kf = c->m_perm; I.idtp = c->m_idtp; I.muf = c->m_mu; I.dtvc = c->m_dtvc;
   I.Rx = c->m_Rx; I.Ry = c->m_Ry; I.Rz = c->m_Rz;
+  I.fbase = c->m_rpt;
+  I.fstride = (long long)(c->m_rpf - c->m_rpt);
   for (int d = 0; d < 2; ++d) {
     I.cin[d] = CorrIn<float>{I.dVx[d], I.dVy[d], I.dVz[d], I.dPt[d], I.dPf[d], I.ccf, I.kf, I.idtp, I.rpt,
                              I.rpf, I.muf, I.dtvc, I.rfx, I.rfy, I.rfz};

@@ -110,6 +110,8 @@ struct MixBatchInst {
   double *s_txx, *s_tyy, *s_tzz, *s_txy, *s_txz, *s_tyz;
   float *rpt, *rpf, *rfx, *rfy, *rfz, *ccf, *kf, *idtp, *muf, *dtvc;
   float *dVx[2], *dVy[2], *dVz[2], *dPt[2], *dPf[2], *Rx, *Ry, *Rz;
+  const float* fbase;                       // the FP32 arrays above, kMixArrays consecutive arrays
+  long long fstride;                        // fbase + slot * fstride (floats), in the order of pt_init
   CorrIn<float> cin[2];                     // correction iteration reading buffer d (0/1) ...
   CorrOut<float> cout[2];                   // ... and writing buffer 1 - d
   unsigned long long* red;                  // outer norms (RED_N slots)

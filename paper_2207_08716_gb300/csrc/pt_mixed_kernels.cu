@@ -761,6 +761,7 @@ __global__ void __launch_bounds__(256, MINB) k_mb_corr(const MixBatchInst* __res
                                                        const MixBatchStatus* __restrict__ st, int ninst,
                                                        long long nctiles, int step, int nup, int zchunk) {
   extern __shared__ __align__(16) float corr_smem[];
+  __shared__ CorrCoef<float> s_cc;   // the member's coefficients, read from shared memory by the tile
   for (long long t = blockIdx.x; t < nctiles; t += gridDim.x) {
     const int m = mb_find<&MixBatchInst::ctile_base>(inst, ninst, t);
     const MixBatchStatus& S = st[m];
@@ -771,14 +772,26 @@ __global__ void __launch_bounds__(256, MINB) k_mb_corr(const MixBatchInst* __res
       continue;
     }
     const int d = (it - 1) & 1;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_cc = I.cc;
+    // the argument pointers as offsets of one base (cheap to recompute, unlike pointers loaded
+    // from the descriptor): slots rpt, rpf, rfx, rfy, rfz, cc, k, idtp, mu, dtvc, dVx[2], dVy[2],
+    // dVz[2], dPt[2], dPf[2], Rx, Ry, Rz
+    float* const B = const_cast<float*>(I.fbase);
+    const long long fs = I.fstride;
+    auto P = [B, fs](int slot) { return B + slot * fs; };
+    const CorrIn<float> ci{P(10 + d), P(12 + d), P(14 + d), P(16 + d), P(18 + d), P(5), P(6), P(7), P(0), P(1),
+                           P(8), P(9), P(2), P(3), P(4)};
+    const CorrOut<float> co{P(11 - d), P(13 - d), P(15 - d), P(17 - d), P(19 - d), P(20), P(21), P(22)};
     const long long local = t - I.ctile_base;
     const long long per_z = (long long)I.cgx * I.cgy;
     const int bz = (int)(local / per_z);
     const int r = (int)(local - (long long)bz * per_z);
     const int tby = r / I.cgx, tbx = r - tby * I.cgx;
     const int k0 = bz * zchunk;
-    corr_tile(I.b, I.cc, I.cin[d], I.cout[d], tbx, tby, k0, min(k0 + zchunk, I.b.nz + 1), I.ired, step == nup,
-              corr_smem);
+    const Box b = I.b;
+    unsigned long long* const ired = I.ired;
+    __syncthreads();   // s_cc written
+    corr_tile(b, s_cc, ci, co, tbx, tby, k0, min(k0 + zchunk, b.nz + 1), ired, step == nup, corr_smem);
     __syncthreads();   // the next tile's stage and rings overwrite this one's
   }
 }
