@@ -545,7 +545,7 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
            "value_definition": f"T_eff-equivalent: 25 x {pbytes} B x aggregate cell updates per second"
                                + (" (FP32: inner FP32 PT iterations)" if fp32 else "")}
     if fp32:
-        out["corr_tile_z"], out["corr_blocks_per_sm"] = b.config_fp32()
+        out["corr_tile_z"], out["corr_blocks_per_sm"], out["member_groups"] = b.config_fp32()
     if converge:
         st = sorted(ttc_all)
         out.update(statuses=[r["status"] for r in reps], iters=[r["iters"] for r in reps],

@@ -315,9 +315,10 @@ int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *
  * [FP64 residuals, stresses and Picard update of the instances starting an outer iteration;
  * their outer decision (converged, outer weight, inner target); nup FP32 correction iterations
  * of the instances in a correction solve; their inner decision (relative drop reached or budget
- * spent); the FP64 update and porosity integration of the instances ending one]. The first
- * pt_batch_step tunes the correction tile depth (32, 64, 128 levels), the CTAs per SM of the
- * correction kernel (3, 4) and the rounds per replay (1, 2).
+ * spent); the FP64 update and porosity integration of the instances ending one], the instances
+ * split into contiguous groups whose rounds are parallel branches of the graph. The first
+ * pt_batch_step tunes the correction tile depth (32, 64 levels), the CTAs per SM of the
+ * correction kernel (3, 4), the rounds per replay (1, 2) and the groups (1, 4, 8).
  * Either way each instance reproduces its single-instance pt_step: the same per-point code and
  * the same decisions in the same order, so the same iteration counts and statuses, and fields
  * equal to rounding (the shared bodies inlined into other kernels may round their multiply-adds
@@ -338,9 +339,11 @@ int pt_batch_step(pt_batch *batch, pt_report *reps, double *time_to_converge_ms)
  * (FP32 ensembles: the correction tile, 30 x 6 faces) and the (correction) iterations per replay. */
 int pt_batch_config(const pt_batch *batch, int32_t *tile_x, int32_t *tile_y,
                     int32_t *iters_per_graph);
-/* FP32 ensembles: the tuned correction tile depth (z levels) and CTAs per SM of the correction
- * kernel; PT_EINVAL for an FP64 ensemble. */
-int pt_batch_config_fp32(const pt_batch *batch, int32_t *tile_z, int32_t *blocks_per_sm);
+/* FP32 ensembles: the tuned correction tile depth (z levels), CTAs per SM of the correction
+ * kernel and number of member groups (contiguous groups of near-equal cells whose rounds are
+ * parallel branches of the replayed graph); PT_EINVAL for an FP64 ensemble. */
+int pt_batch_config_fp32(const pt_batch *batch, int32_t *tile_z, int32_t *blocks_per_sm,
+                         int32_t *groups);
 void pt_batch_destroy(pt_batch *batch);
 
 /* ---- Sub-domain (halo-exchange) form (Art. 1 Section 2.2) ----------------------------------

@@ -1193,9 +1193,13 @@ struct pt_batch {
   MixBatchStatus* h_mst;
   unsigned long long* d_ired;
   int zchunk, minb, mult;   // correction tile depth, CTAs per SM of the correction kernel, rounds per replay
+  int groups;               // members split into this many contiguous groups, each a parallel graph branch
   long long nptiles, nctiles;
   int pgrid, cgrid;
-  int exec_zchunk, exec_minb, exec_mult;
+  int exec_zchunk, exec_minb, exec_mult, exec_groups;
+  std::vector<int> gm;                  // group g = members [gm[g], gm[g + 1])
+  std::vector<cudaStream_t> gstream;    // capture streams of the branches
+  std::vector<cudaEvent_t> gevent;      // fork (0) and one join per branch
 };
 
 namespace {
@@ -1380,26 +1384,66 @@ cudaError_t upload_mix(pt_batch* B) {
                          B->stream);
 }
 
-// One replay: `mult` rounds of the engine (outer phases, nup correction iterations, update).
-void record_mix_rounds(pt_batch* B) {
-  const int n = B->ninst;
+// Contiguous member groups of near-equal cells (the branches of a replay).
+void split_mix_groups(pt_batch* B) {
+  const int G = std::max(1, std::min(B->groups, B->ninst));
+  long long total = 0;
+  for (int m = 0; m < B->ninst; ++m) total += B->ctx[m]->box.n;
+  B->gm.assign(1, 0);
+  long long acc = 0;
+  for (int m = 0; m < B->ninst; ++m) {
+    acc += B->ctx[m]->box.n;
+    const int g = (int)B->gm.size();   // the group being filled
+    if (g < G && m + 1 < B->ninst && acc * G >= total * g && B->ninst - (m + 1) >= G - g) B->gm.push_back(m + 1);
+  }
+  B->gm.push_back(B->ninst);
+}
+
+// The rounds of one member group on stream `s`: outer phases, nup correction iterations, update.
+void record_mix_group(pt_batch* B, int g, cudaStream_t s) {
+  const int m0 = B->gm[g], m1 = B->gm[g + 1], n = m1 - m0;
+  const MixBatchInst* inst = B->d_minst + m0;
+  MixBatchStatus* st = B->d_mst + m0;
+  const MixBatchInst& first = B->h_minst[m0];
+  const long long p0 = first.tile_base, c0 = first.ctile_base;
+  const long long p1 = m1 < B->ninst ? B->h_minst[m1].tile_base : B->nptiles;
+  const long long c1 = m1 < B->ninst ? B->h_minst[m1].ctile_base : B->nctiles;
   for (int r = 0; r < B->mult; ++r) {
-    mb_points(B->pgrid, B->stream, MB_PH_PERM, B->d_minst, B->d_mst, n, B->nptiles);
-    mb_points(B->pgrid, B->stream, MB_PH_PREP, B->d_minst, B->d_mst, n, B->nptiles);
-    mb_points(B->pgrid, B->stream, MB_PH_FACES, B->d_minst, B->d_mst, n, B->nptiles);
-    mb_decide_outer(B->stream, B->d_minst, B->d_mst, n);
-    mb_points(B->pgrid, B->stream, MB_PH_INIT, B->d_minst, B->d_mst, n, B->nptiles);
-    for (int s = 1; s <= B->nup; ++s)
-      mb_corr(B->cgrid, B->minb, B->stream, B->d_minst, B->d_mst, n, B->nctiles, s, B->nup, B->zchunk);
-    mb_decide_inner(B->stream, B->d_minst, B->d_mst, n, B->nup);
-    mb_points(B->pgrid, B->stream, MB_PH_UPDATE, B->d_minst, B->d_mst, n, B->nptiles);
-    mb_points(B->pgrid, B->stream, MB_PH_POROSITY, B->d_minst, B->d_mst, n, B->nptiles);
-    mb_finish(B->stream, B->d_minst, B->d_mst, n);
+    mb_points(B->pgrid, s, MB_PH_PERM, inst, st, n, p0, p1);
+    mb_points(B->pgrid, s, MB_PH_PREP, inst, st, n, p0, p1);
+    mb_points(B->pgrid, s, MB_PH_FACES, inst, st, n, p0, p1);
+    mb_decide_outer(s, inst, st, n);
+    mb_points(B->pgrid, s, MB_PH_INIT, inst, st, n, p0, p1);
+    for (int k = 1; k <= B->nup; ++k) mb_corr(B->cgrid, B->minb, s, inst, st, n, c0, c1, k, B->nup, B->zchunk);
+    mb_decide_inner(s, inst, st, n, B->nup);
+    mb_points(B->pgrid, s, MB_PH_UPDATE, inst, st, n, p0, p1);
+    mb_points(B->pgrid, s, MB_PH_POROSITY, inst, st, n, p0, p1);
+    mb_finish(s, inst, st, n);
   }
 }
 
+// One replay: the member groups as parallel branches (they share no data), forked from and
+// joined into the batch's stream.
+void record_mix_rounds(pt_batch* B) {
+  split_mix_groups(B);
+  const int G = (int)B->gm.size() - 1;
+  if (G == 1) {
+    record_mix_group(B, 0, B->stream);
+    return;
+  }
+  cudaEventRecord(B->gevent[0], B->stream);
+  for (int g = 0; g < G; ++g) {
+    cudaStreamWaitEvent(B->gstream[g], B->gevent[0], 0);
+    record_mix_group(B, g, B->gstream[g]);
+    cudaEventRecord(B->gevent[1 + g], B->gstream[g]);
+  }
+  for (int g = 0; g < G; ++g) cudaStreamWaitEvent(B->stream, B->gevent[1 + g], 0);
+}
+
 int build_mix_graph(pt_batch* B) {
-  if (B->exec && B->exec_zchunk == B->zchunk && B->exec_minb == B->minb && B->exec_mult == B->mult) return PT_OK;
+  if (B->exec && B->exec_zchunk == B->zchunk && B->exec_minb == B->minb && B->exec_mult == B->mult &&
+      B->exec_groups == B->groups)
+    return PT_OK;
   if (B->exec) {
     cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
@@ -1417,6 +1461,7 @@ int build_mix_graph(pt_batch* B) {
   B->exec_zchunk = B->zchunk;
   B->exec_minb = B->minb;
   B->exec_mult = B->mult;
+  B->exec_groups = B->groups;
   return PT_OK;
 }
 
@@ -1448,11 +1493,11 @@ int batch_step_mixed(pt_batch* B, pt_report* reps, double* ttc_ms) {
   // every round advances each member that is not done: an outer iteration takes at least one
   // round and at least min(nup, budget) correction iterations, so this many rounds end every member
   const long long max_rounds = 2LL * ((long long)cap / B->nup + 2) + 4;
-  struct Cfg { int zchunk, minb, mult; };
-  const Cfg cands[] = {{64, 4, 1}, {64, 3, 1}, {32, 4, 1}, {128, 4, 1}, {64, 4, 2}};
+  struct Cfg { int zchunk, minb, mult, groups; };
+  const Cfg cands[] = {{64, 4, 1, 1}, {64, 4, 1, 4}, {64, 3, 1, 4}, {32, 4, 1, 4}, {64, 4, 2, 4}, {64, 4, 1, 8}};
   const int ncand = B->tuned ? 0 : (int)(sizeof cands / sizeof cands[0]);
   float best_ms = 1e30f;
-  Cfg best = {B->zchunk, B->minb, B->mult};
+  Cfg best = {B->zchunk, B->minb, B->mult, B->groups};
   long long rounds = 0;
   int nactive = B->ninst;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1461,6 +1506,7 @@ int batch_step_mixed(pt_batch* B, pt_report* reps, double* ttc_ms) {
     B->zchunk = cands[t].zchunk;
     B->minb = cands[t].minb;
     B->mult = cands[t].mult;
+    B->groups = cands[t].groups;
     if (upload_mix(B) != cudaSuccess) return PT_ECUDA;
     rc = build_mix_graph(B);
     if (rc != PT_OK) return rc;
@@ -1483,6 +1529,7 @@ int batch_step_mixed(pt_batch* B, pt_report* reps, double* ttc_ms) {
     B->zchunk = best.zchunk;
     B->minb = best.minb;
     B->mult = best.mult;
+    B->groups = best.groups;
     B->tuned = true;
     if (upload_mix(B) != cudaSuccess) return PT_ECUDA;
   }
@@ -1576,12 +1623,21 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   B->zchunk = 64;
   B->minb = 4;
   B->mult = 1;
-  B->exec_zchunk = B->exec_minb = B->exec_mult = 0;
+  B->groups = 1;
+  B->exec_zchunk = B->exec_minb = B->exec_mult = B->exec_groups = 0;
   B->h_st = nullptr;
   B->h_mst = nullptr;
   if (fp32) B->h_minst.resize(ninst);
   char* w = (char*)workspace;
   int rc = PT_OK;
+  if (fp32) {   // capture streams and events of the parallel member groups (up to 8)
+    B->gstream.assign(8, nullptr);
+    B->gevent.assign(9, nullptr);
+    for (cudaStream_t& q : B->gstream)
+      if (rc == PT_OK && cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) rc = PT_ECUDA;
+    for (cudaEvent_t& e : B->gevent)
+      if (rc == PT_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = PT_ECUDA;
+  }
   for (int m = 0; m < ninst && rc == PT_OK; ++m) {
     const size_t s = pt_workspace_size(&grids[m], &nums[m]);
     rc = pt_init(&B->ctx[m], &grids[m], &phys[m], &nums[m], &fields[m], w, s, (void*)B->stream, 0);
@@ -1605,6 +1661,10 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
     for (pt_ctx* c : B->ctx) pt_destroy(c);
     if (B->h_st) cudaFreeHost(B->h_st);
     if (B->h_mst) cudaFreeHost(B->h_mst);
+    for (cudaStream_t q : B->gstream)
+      if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : B->gevent)
+      if (e) cudaEventDestroy(e);
     cudaStreamDestroy(B->stream);
     delete B;
     return rc;
@@ -1719,10 +1779,11 @@ int pt_batch_config(const pt_batch* B, int32_t* tile_x, int32_t* tile_y, int32_t
   return PT_OK;
 }
 
-int pt_batch_config_fp32(const pt_batch* B, int32_t* tile_z, int32_t* blocks_per_sm) {
+int pt_batch_config_fp32(const pt_batch* B, int32_t* tile_z, int32_t* blocks_per_sm, int32_t* groups) {
   if (!B || !B->mixed) return PT_EINVAL;
   if (tile_z) *tile_z = B->zchunk;
   if (blocks_per_sm) *blocks_per_sm = B->minb;
+  if (groups) *groups = std::max(1, std::min(B->groups, B->ninst));
   return PT_OK;
 }
 
@@ -1733,6 +1794,10 @@ void pt_batch_destroy(pt_batch* B) {
   for (pt_ctx* c : B->ctx) pt_destroy(c);
   cudaFreeHost(B->h_st);
   cudaFreeHost(B->h_mst);
+  for (cudaStream_t q : B->gstream)
+    if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t e : B->gevent)
+    if (e) cudaEventDestroy(e);
   cudaStreamDestroy(B->stream);
   delete B;
 }

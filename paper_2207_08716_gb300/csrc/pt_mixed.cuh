@@ -140,13 +140,15 @@ struct MixBatchStatus {
   unsigned long long t_start, t_stop;       // device %globaltimer (ns)
 };
 
+// The kernels take a slice of the member table (inst, st: its first member; ninst members) and
+// the range [t0, t1) of work items its members own (tile_base / ctile_base are global offsets).
 void mb_points(int grid, cudaStream_t s, int phase, const MixBatchInst* inst, const MixBatchStatus* st, int ninst,
-               long long ntiles);
+               long long t0, long long t1);
 // Correction iteration number inner + step (1-based) of every member in MB_INNER within its budget;
 // minb (3 or 4): the CTAs per SM the kernel's registers are budgeted for. Sets the kernel's
 // shared-memory attribute first (mb_corr_blocks_per_sm, before any capture).
 void mb_corr(int grid, int minb, cudaStream_t s, const MixBatchInst* inst, const MixBatchStatus* st, int ninst,
-             long long nctiles, int step, int nup, int zchunk);
+             long long t0, long long t1, int step, int nup, int zchunk);
 void mb_decide_outer(cudaStream_t s, const MixBatchInst* inst, MixBatchStatus* st, int ninst);
 void mb_decide_inner(cudaStream_t s, const MixBatchInst* inst, MixBatchStatus* st, int ninst, int nup);
 void mb_finish(cudaStream_t s, const MixBatchInst* inst, MixBatchStatus* st, int ninst);

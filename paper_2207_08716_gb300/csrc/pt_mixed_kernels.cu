@@ -669,9 +669,9 @@ __device__ inline int mb_find(const MixBatchInst* inst, int ninst, long long t) 
 
 // The first work item >= `next` that this CTA visits in a grid stride starting at blockIdx.x:
 // a CTA skips a member that has no work in a launch in one step instead of tile by tile.
-__device__ inline long long mb_skip_to(long long next) {
+__device__ inline long long mb_skip_to(long long next, long long t0) {
   const long long g = gridDim.x;
-  return next + (((long long)blockIdx.x - next) % g + g) % g;
+  return next + ((t0 + (long long)blockIdx.x - next) % g + g) % g;
 }
 
 __device__ inline bool mb_runs(int phase, const MixBatchStatus& s) {
@@ -691,12 +691,12 @@ constexpr int kMbBX = 32, kMbBY = 8;   // point tiles: 32 x 8 cells of one z-lev
 template <int PHASE>
 __global__ void __launch_bounds__(kMbBX * kMbBY) k_mb_points(const MixBatchInst* __restrict__ inst,
                                                             const MixBatchStatus* __restrict__ st, int ninst,
-                                                            long long ntiles) {
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                                                            long long t0, long long t1) {
+  for (long long t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
     const int m = mb_find<&MixBatchInst::tile_base>(inst, ninst, t);
     const MixBatchStatus& S = st[m];
     if (!mb_runs(PHASE, S)) {   // uniform over the CTA: on to the next member's tiles
-      t = mb_skip_to(m + 1 < ninst ? inst[m + 1].tile_base : ntiles) - gridDim.x;
+      t = mb_skip_to(m + 1 < ninst ? inst[m + 1].tile_base : t1, t0) - gridDim.x;
       continue;
     }
     const MixBatchInst& I = inst[m];
@@ -759,16 +759,17 @@ __global__ void __launch_bounds__(kMbBX * kMbBY) k_mb_points(const MixBatchInst*
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_mb_corr(const MixBatchInst* __restrict__ inst,
                                                        const MixBatchStatus* __restrict__ st, int ninst,
-                                                       long long nctiles, int step, int nup, int zchunk) {
+                                                       long long t0, long long t1, int step, int nup,
+                                                       int zchunk) {
   extern __shared__ __align__(16) float corr_smem[];
   __shared__ CorrCoef<float> s_cc;   // the member's coefficients, read from shared memory by the tile
-  for (long long t = blockIdx.x; t < nctiles; t += gridDim.x) {
+  for (long long t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
     const int m = mb_find<&MixBatchInst::ctile_base>(inst, ninst, t);
     const MixBatchStatus& S = st[m];
     const MixBatchInst& I = inst[m];
     const int it = S.inner + step;
     if (S.phase != MB_INNER || it > I.max_iter - S.iters) {   // uniform over the CTA
-      t = mb_skip_to(m + 1 < ninst ? inst[m + 1].ctile_base : nctiles) - gridDim.x;
+      t = mb_skip_to(m + 1 < ninst ? inst[m + 1].ctile_base : t1, t0) - gridDim.x;
       continue;
     }
     const int d = (it - 1) & 1;
@@ -915,24 +916,24 @@ __global__ void k_mb_start(const MixBatchInst* __restrict__ inst, MixBatchStatus
 }
 
 void mb_points(int grid, cudaStream_t s, int phase, const MixBatchInst* inst, const MixBatchStatus* st, int ninst,
-               long long ntiles) {
+               long long t0, long long t1) {
   const dim3 bl(kMbBX, kMbBY, 1);
   switch (phase) {
-    case MB_PH_PERM: k_mb_points<MB_PH_PERM><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
-    case MB_PH_PREP: k_mb_points<MB_PH_PREP><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
-    case MB_PH_FACES: k_mb_points<MB_PH_FACES><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
-    case MB_PH_INIT: k_mb_points<MB_PH_INIT><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
-    case MB_PH_UPDATE: k_mb_points<MB_PH_UPDATE><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
-    default: k_mb_points<MB_PH_POROSITY><<<grid, bl, 0, s>>>(inst, st, ninst, ntiles); break;
+    case MB_PH_PERM: k_mb_points<MB_PH_PERM><<<grid, bl, 0, s>>>(inst, st, ninst, t0, t1); break;
+    case MB_PH_PREP: k_mb_points<MB_PH_PREP><<<grid, bl, 0, s>>>(inst, st, ninst, t0, t1); break;
+    case MB_PH_FACES: k_mb_points<MB_PH_FACES><<<grid, bl, 0, s>>>(inst, st, ninst, t0, t1); break;
+    case MB_PH_INIT: k_mb_points<MB_PH_INIT><<<grid, bl, 0, s>>>(inst, st, ninst, t0, t1); break;
+    case MB_PH_UPDATE: k_mb_points<MB_PH_UPDATE><<<grid, bl, 0, s>>>(inst, st, ninst, t0, t1); break;
+    default: k_mb_points<MB_PH_POROSITY><<<grid, bl, 0, s>>>(inst, st, ninst, t0, t1); break;
   }
 }
 
 void mb_corr(int grid, int minb, cudaStream_t s, const MixBatchInst* inst, const MixBatchStatus* st, int ninst,
-             long long nctiles, int step, int nup, int zchunk) {
+             long long t0, long long t1, int step, int nup, int zchunk) {
   if (minb == 3) {
-    k_mb_corr<3><<<grid, dim3(32, 8, 1), kCorrSmemBytes, s>>>(inst, st, ninst, nctiles, step, nup, zchunk);
+    k_mb_corr<3><<<grid, dim3(32, 8, 1), kCorrSmemBytes, s>>>(inst, st, ninst, t0, t1, step, nup, zchunk);
   } else {
-    k_mb_corr<4><<<grid, dim3(32, 8, 1), kCorrSmemBytes, s>>>(inst, st, ninst, nctiles, step, nup, zchunk);
+    k_mb_corr<4><<<grid, dim3(32, 8, 1), kCorrSmemBytes, s>>>(inst, st, ninst, t0, t1, step, nup, zchunk);
   }
 }
 

@@ -213,7 +213,8 @@ SIGNATURES = {
                                 C.POINTER(Num), C.POINTER(Fields), C.c_void_p, C.c_size_t, C.c_void_p]),
     "pt_batch_step": (C.c_int, [C.c_void_p, C.POINTER(Report), C.POINTER(C.c_double)]),
     "pt_batch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-    "pt_batch_config_fp32": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pt_batch_config_fp32": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32)]),
     "pt_batch_destroy": (None, [C.c_void_p]),
     "pt_destroy": (None, [C.c_void_p]),
     "pt_strerror": (C.c_char_p, [C.c_int]),

@@ -285,12 +285,12 @@ class PTBatch:
         return bx.value, by.value, ipg.value
 
     def config_fp32(self) -> tuple:
-        """FP32 ensembles: (correction tile depth, CTAs per SM of the correction kernel)."""
-        tz, mb = C.c_int32(), C.c_int32()
-        rc = self.lib.pt_batch_config_fp32(self.h, C.byref(tz), C.byref(mb))
+        """FP32 ensembles: (correction tile depth, CTAs per SM of the correction kernel, member groups)."""
+        tz, mb, gr = C.c_int32(), C.c_int32(), C.c_int32()
+        rc = self.lib.pt_batch_config_fp32(self.h, C.byref(tz), C.byref(mb), C.byref(gr))
         if rc != N.PT_OK:
             raise PTError(rc, "pt_batch_config_fp32")
-        return tz.value, mb.value
+        return tz.value, mb.value, gr.value
 
     def get(self, m: int, name: str) -> np.ndarray:
         torch.cuda.synchronize(self.device)

@@ -94,7 +94,8 @@ def test_fp32_ensemble_instances_equal_single_fp32_runs():
     reps2, _ = b.step()
     tx, ty, ipg = b.config()
     assert (tx, ty) == (30, 6) and ipg in (15, 30), (tx, ty, ipg)
-    assert b.config_fp32()[0] in (32, 64, 128) and b.config_fp32()[1] in (3, 4)
+    tz, mb, groups = b.config_fp32()
+    assert tz in (32, 64) and mb in (3, 4) and 1 <= groups <= 5, (tz, mb, groups)
     for m, (p, phi) in enumerate(mem):
         s = PTSolver(dict(p, precision=N.PT_FP32), phi)
         r1 = s.step()
