@@ -318,7 +318,7 @@ int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *
  * spent); the FP64 update and porosity integration of the instances ending one], the instances
  * split into contiguous groups whose rounds are parallel branches of the graph. The first
  * pt_batch_step tunes the correction tile depth (32, 64 levels), the CTAs per SM of the
- * correction kernel (3, 4), the rounds per replay (1, 2) and the groups (1, 4, 8).
+ * correction kernel (3, 4), the rounds per replay (1, 2) and the groups (1, 4, 8, 16).
  * Either way each instance reproduces its single-instance pt_step: the same per-point code and
  * the same decisions in the same order, so the same iteration counts and statuses, and fields
  * equal to rounding (the shared bodies inlined into other kernels may round their multiply-adds

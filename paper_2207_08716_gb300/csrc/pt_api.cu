@@ -1494,7 +1494,8 @@ int batch_step_mixed(pt_batch* B, pt_report* reps, double* ttc_ms) {
   // round and at least min(nup, budget) correction iterations, so this many rounds end every member
   const long long max_rounds = 2LL * ((long long)cap / B->nup + 2) + 4;
   struct Cfg { int zchunk, minb, mult, groups; };
-  const Cfg cands[] = {{64, 4, 1, 1}, {64, 4, 1, 4}, {64, 3, 1, 4}, {32, 4, 1, 4}, {64, 4, 2, 4}, {64, 4, 1, 8}};
+  const Cfg cands[] = {{64, 4, 1, 1}, {64, 3, 1, 4}, {64, 4, 1, 4}, {64, 3, 1, 8}, {64, 3, 1, 16}, {32, 3, 1, 8},
+                       {64, 3, 2, 8}};
   const int ncand = B->tuned ? 0 : (int)(sizeof cands / sizeof cands[0]);
   float best_ms = 1e30f;
   Cfg best = {B->zchunk, B->minb, B->mult, B->groups};
@@ -1630,9 +1631,9 @@ int pt_batch_init(pt_batch** out, int32_t ninst, const pt_grid* grids, const pt_
   if (fp32) B->h_minst.resize(ninst);
   char* w = (char*)workspace;
   int rc = PT_OK;
-  if (fp32) {   // capture streams and events of the parallel member groups (up to 8)
-    B->gstream.assign(8, nullptr);
-    B->gevent.assign(9, nullptr);
+  if (fp32) {   // capture streams and events of the parallel member groups (up to 16)
+    B->gstream.assign(16, nullptr);
+    B->gevent.assign(17, nullptr);
     for (cudaStream_t& q : B->gstream)
       if (rc == PT_OK && cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) rc = PT_ECUDA;
     for (cudaEvent_t& e : B->gevent)
