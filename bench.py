@@ -173,8 +173,9 @@ def parse():
                          "--pc-oracle-n sizes) after converged physical steps of the c1 workload at each --pc-n")
     ap.add_argument("--pc-n", default="32,64", help="grid sizes of the precision check, n[:steps] each")
     ap.add_argument("--pc-steps", type=int, default=50, help="converged steps where --pc-n gives none")
-    ap.add_argument("--pc-ref", choices=("fp64", "df64"), default="fp64",
-                    help="the FP64-class form the FP32 form is compared with")
+    ap.add_argument("--pc-ref", choices=("fp64", "df64", "none"), default="fp64",
+                    help="the FP64-class form the FP32 form is compared with (none: run the multigrid form "
+                         "alone, no comparison)")
     ap.add_argument("--pc-oracle", type=int, default=1, help="also run the oracle (1) or not (0)")
     ap.add_argument("--pc-oracle-n", default="32", help="grid sizes at which the oracle runs too")
     ap.add_argument("--pc-plain-max", type=int, default=100000,
@@ -756,7 +757,7 @@ def measure_precision(args, dev) -> dict:
 
     sizes = _parse_sizes(args.pc_n, args.pc_steps)
     oracle_n = {int(v) for v in str(args.pc_oracle_n).split(",") if v.strip()} if args.pc_oracle else set()
-    ref_prec = {"fp64": N.PT_FP64, "df64": N.PT_DF64}[args.pc_ref]
+    ref_prec = {"fp64": N.PT_FP64, "df64": N.PT_DF64, "none": None}[args.pc_ref]
     tmp = tempfile.mkdtemp(prefix="pc_oracle_")
     children = {}
     ncores = os.cpu_count() or 1
@@ -793,6 +794,10 @@ def measure_precision(args, dev) -> dict:
         p = I.c1_params(n)
         p["max_iter"] = 400000
         phi0 = I.gaussian_porosity(p)
+        if ref_prec is None:   # the multigrid form alone (launch lists)
+            phimg, itmg, tmg = run(dict(p, precision=N.PT_FP32, mg_levels=args.pc_mg), phi0, k)
+            out[str(n)] = {"steps": k, "fp32mg_levels": args.pc_mg, "fp32mg_iters": sum(itmg), "fp32mg_s": tmg}
+            continue
         phi64, it64, t64 = run(dict(p, precision=ref_prec), phi0, k)
         r = {"steps": k, "ref_iters": sum(it64), "ref_s": t64, "porosity_change_max": float(np.abs(phi64 - phi0).max())}
         phi32 = None
