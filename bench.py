@@ -84,6 +84,8 @@ PROFILED = {
     "k_lean_faces": {"src": "847b74c5871329ee", "fp64_inst": 33.1, "fp64_flops": 50.0, "traffic": 180.3},
     "k_lean_cells_df64": {"src": "847b74c5871329ee", "traffic": 260.0, "thread_inst": 1929.0},
     "k_lean_faces_df64": {"src": "847b74c5871329ee", "traffic": 164.3, "thread_inst": 724.9},
+    # profiles/k_corr_iteration_fp32_255.md (255^3, one launch)
+    "k_corr_iteration": {"src": "f86ac348e6a52cd1", "traffic": 106.6, "thread_inst": 720.8},
 }
 # The FP64 pipe's nominal issue capacity: 304 thread-instructions per GPU clock (2 per SM; ncu's
 # sm__inst_executed_pipe_fp64 peak on this machine's GB300), 629 G/s at 2.07 GHz.
