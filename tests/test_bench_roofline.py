@@ -80,3 +80,15 @@ def test_double_float_cells_report_hbm_with_their_own_bytes():
     assert r["kernel"] == "k_lean_cells_df64" and r["bound"] == "hbm"
     assert abs(r["achieved"] - gbs) < 1e-6 * gbs
     assert abs(r["frac_of_own_copy"] - gbs / 6900.0) < 1e-12
+
+
+def test_fp32_correction_reports_ncu_traffic_while_current():
+    n = 511 ** 3
+    r = bench.roofline({"k_corr_iteration": (300, 300 * 4.85)}, n)
+    assert r["ncu_figures"] == "current" and r["traffic"] is not None
+    assert abs(r["traffic"] - bench.PROFILED["k_corr_iteration"]["traffic"] * n) < 1e-6 * r["traffic"]
+
+
+def test_precision_check_size_list():
+    assert bench._parse_sizes("512:1, 128:2,64", 50) == [(512, 1), (128, 2), (64, 50)]
+    assert bench._parse_sizes("", 3) == []
