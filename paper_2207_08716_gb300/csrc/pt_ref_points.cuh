@@ -18,9 +18,9 @@ __device__ __forceinline__ void perm_point(const Box& b, const Coef& c, const do
   if (i >= b.nx || j >= b.ny || k >= b.nz) return;
   const long long q = cidx(b, i, j, k);
   const double ph = phi[q];
-  const double th = logk ? logk[q] : 0.0;
   const double r = ph * c.rphi0;
-  perm[q] = c.k0 * exp(th) * r * r * r;
+  // without a log k field the factor e^0 is 1 exactly: no exponential evaluated
+  perm[q] = c.k0 * (logk ? exp(logk[q]) : 1.0) * r * r * r;
   rog[q] = (ph * c.rhof_g + (1.0 - ph) * c.rhos_g) - c.rho_bg_g;
 }
 
