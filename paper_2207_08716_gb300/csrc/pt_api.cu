@@ -97,7 +97,6 @@ struct pt_ctx {
   float *m_rpt, *m_rpf, *m_rfx, *m_rfy, *m_rfz, *m_cc, *m_perm, *m_idtp, *m_mu, *m_dtvc;
   float *m_dVx[2], *m_dVy[2], *m_dVz[2], *m_dPt[2], *m_dPf[2], *m_Rx, *m_Ry, *m_Rz;
   CorrCoef<float> ccoef;
-  MixCoefDF mcoef;                                 // double-float scalars of the outer residual phases
   // multigrid V-cycle of the correction problem (mg_L >= 2): level 0 = the m_* arrays above
   int mg_L;
   std::vector<MgLevel> mg;
@@ -132,7 +131,7 @@ enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEG
                 K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_ITER,
                 K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_DF_CELLS, K_DF_FACES,
                 K_DF_PICARD, K_DF_COEF, K_DF_BEGIN, K_DF_K0, K_DF_CONVERT, K_ADJ_EDGES_PL, K_ADJ_CELLS_PL,
-                K_ADJ_FACES_PL, K_MG_FINE, K_MG_COARSE, K_MG_TRANSFER, K_MIX_EDGES, K_COUNT };
+                K_ADJ_FACES_PL, K_MG_FINE, K_MG_COARSE, K_MG_TRANSFER, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
@@ -144,7 +143,7 @@ const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_
                                            "k_lean_coef_df64", "k_lean_begin_df64", "k_lean_k0_df64",
                                            "k_df64_convert", "k_adj_edges_pl", "k_adj_cells_pl",
                                            "k_adj_faces_pl", "k_corr_iteration_mg_fine",
-                                           "k_corr_iteration_mg_coarse", "k_mg_transfer", "k_mix_edges"};
+                                           "k_corr_iteration_mg_coarse", "k_mg_transfer"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -340,7 +339,6 @@ void fill_mg_coef(pt_ctx* c) {
 
 void fill_corr_coef(pt_ctx* c) {
   c->ccoef = corr_coef_of(c->coef);
-  c->mcoef = mix_coef_df(c->coef);
   fill_mg_coef(c);
 }
 
@@ -607,13 +605,12 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   MixPrepIn pin{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->phi[a], c->mu, c->eta, c->perm, c->Pto,
                 c->Pfo, c->txxo, c->tyyo, c->tzzo};
   MixPrepOut pout{c->s_txx, c->s_tyy, c->s_tzz, c->m_rpt, c->m_rpf, c->m_cc, c->m_perm, c->m_idtp};
-  PT_LAUNCH(c, K_MIX_PREP, mix_prepare(gr, bl, c->stream, b, c->mcoef, pin, pout, c->red));
+  PT_LAUNCH(c, K_MIX_PREP, mix_prepare(gr, bl, c->stream, b, k, pin, pout, c->red));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
-  PT_LAUNCH(c, K_MIX_EDGES, mix_edges(gr, bl, c->stream, b, c->mcoef, ei, eo));
+  PT_LAUNCH(c, K_EDGES, k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo));
   MixFaceIn fin{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[a], c->phi[a]};
-  PT_LAUNCH(c, K_MIX_FACES,
-            mix_res_faces(gr, bl, c->stream, b, c->mcoef, fin, c->m_rfx, c->m_rfy, c->m_rfz, c->red));
+  PT_LAUNCH(c, K_MIX_FACES, mix_res_faces(gr, bl, c->stream, b, k, fin, c->m_rfx, c->m_rfy, c->m_rfz, c->red));
   // (ii) Picard update of mu, eta from the stresses at u
   LeanPicardIn<double> pi{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->phi[a],
                           c->Pt[a], c->Pf[a]};
@@ -1330,7 +1327,6 @@ void fill_mix_inst(pt_batch* B, int m, long long base, long long cbase) {
   MixBatchInst& I = B->h_minst[m];
   I.b = c->box;
   I.k = c->coef;
-  I.kd = c->mcoef;
   I.lc = c->lcoef;
   I.cc = c->ccoef;
   I.Vx = c->Vx; I.Vy = c->Vy; I.Vz = c->Vz;

@@ -3,7 +3,6 @@
 #pragma once
 
 #include "pt_lean.cuh"
-#include "pt_kernels.cuh"
 
 namespace pt {
 
@@ -25,17 +24,6 @@ struct MixUpdate {
   double *Vx, *Vy, *Vz, *Pt, *Pf;
   const float *dVx, *dVy, *dVz, *dPt, *dPf;
   double omega;             // u <- u + omega delta
-};
-
-// The outer phases' FP64 arithmetic (residuals at u, stresses) is done in double-float (a pair of
-// FP32 numbers, 48-bit significand) on the FP32 pipe: these constants are the phases' scalars
-// rounded to double-float on the host.
-struct MixCoefDF {
-  df64 rdx, rdy, rdz, hrdx, hrdy, hrdz;   // 1 / d and 1 / (2 d)
-  df64 bd_rdt, bda_rdt, alpha, rB;        // beta_d / dt, beta_d alpha / dt, alpha, 1 / B
-  df64 buoy, drho, phi0;                  // rho_f g - rho_BG g, rho_f g - rho_s g, phi0
-  df64 rGdtS, beta_n, dtaupt_fac, ebg;
-  int compaction_on, bg_on;
 };
 
 template <class T>
@@ -72,12 +60,10 @@ struct MgLevel {
   float *res_pt, *res_pf;                          // cell residuals of an evaluation sweep
 };
 
-void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixCoefDF& c, const MixPrepIn& in,
+void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPrepIn& in,
                  const MixPrepOut& out, unsigned long long* red);
-void mix_edges(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixCoefDF& c, const EdgeIn& in, const EdgeOut& out);
-void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixCoefDF& c, const MixFaceIn& in, float* rfx,
+void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixFaceIn& in, float* rfx,
                    float* rfy, float* rfz, unsigned long long* red);
-MixCoefDF mix_coef_df(const Coef& k);
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out);
 void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u);
 // One fused FP32 correction iteration over the whole grid (z-marching tiles, see the kernel).
@@ -115,8 +101,7 @@ enum { MB_PH_PERM = 0, MB_PH_PREP = 1, MB_PH_FACES = 2, MB_PH_INIT = 3, MB_PH_UP
 
 struct MixBatchInst {
   Box b;
-  Coef k;                                   // porosity update, Picard update
-  MixCoefDF kd;                             // double-float residuals and stresses at u
+  Coef k;                                   // FP64 residuals, porosity update
   LeanCoef<double> lc;                      // Picard update
   CorrCoef<float> cc;                       // FP32 correction iteration
   double *Vx, *Vy, *Vz, *Pt[2], *Pf[2], *phi[2], *mu, *eta, *perm, *rog, *Pto, *Pfo, *Lo;

@@ -21,110 +21,84 @@
 namespace pt {
 
 namespace {
+template <class T>
+__device__ inline T tabs(T x) { return x < T(0) ? -x : x; }
+__device__ inline double pos_max64(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double(ia > ib ? ia : ib);
+}
 }  // namespace
 
-// (i) Residuals at cell centres, normal stresses at u, and the frozen coefficients of the
-// correction problem (in FP32). The FP64 state is read as double and the arithmetic is done in
-// double-float (48-bit significand; the residuals' cancellations need ~1e-8 relative, the
-// format carries ~3.6e-15), so the FP64 pipe only converts the loaded values.
-namespace {
-using D = df64;
-__device__ __forceinline__ D ld(const double* a, long long q) { return D(a[q]); }
-__device__ __forceinline__ float to_f(D x) { return __fadd_rn(x.hi, x.lo); }   // nearest float
-__device__ __forceinline__ double abs_d(D x) { return fabs((double)x); }
-}  // namespace
-
-__device__ __forceinline__ void mix_prepare_point(const Box& b, const MixCoefDF& c, const MixPrepIn& in,
+// (i) FP64 residuals at cell centres, normal stresses at u, and the frozen coefficients of the
+// correction problem (in FP32).
+__device__ __forceinline__ void mix_prepare_point(const Box& b, const Coef& c, const MixPrepIn& in,
                                                   const MixPrepOut& out, int i, int j, int k, double& r_pt,
                                                   double& r_pf) {
   if (i < b.nx && j < b.ny && k < b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
-    const D Pt = ld(in.Pt, q), Pf = ld(in.Pf, q), ph = ld(in.phi, q), mu = ld(in.mu, q);
-    const D dPt = Pt - ld(in.Pto, q), dPf = Pf - ld(in.Pfo, q);
-    const D gx = (ld(in.Vx, q + 1) - ld(in.Vx, q)) * c.rdx;
-    const D gy = (ld(in.Vy, q + px) - ld(in.Vy, q)) * c.rdy;
-    const D gz = (ld(in.Vz, q + pxy) - ld(in.Vz, q)) * c.rdz;
-    const D divV = gx + gy + gz;
-    const D cc = c.compaction_on ? df_rcp(ld(in.eta, q) * (D(1.0) - ph)) : D(0.0);
-    const D divVn = divV + c.bd_rdt * (dPt - c.alpha * dPf) + (Pt - Pf) * cc;
-    // Darcy flux on the 6 faces, -(k_l + k_r) / 2 (dPf/dn + buoyancy along z), zero on the walls
-    const D kc = ld(in.perm, q);
-    D sx(0.0), sy(0.0), sz(0.0);   // outflow minus inflow per direction, before 1/d
-    if (i > 0) sx = sx + (ld(in.perm, q - 1) + kc) * (Pf - ld(in.Pf, q - 1)) * c.hrdx;
-    if (i < b.nx - 1) sx = sx - (kc + ld(in.perm, q + 1)) * (ld(in.Pf, q + 1) - Pf) * c.hrdx;
-    if (j > 0) sy = sy + (ld(in.perm, q - px) + kc) * (Pf - ld(in.Pf, q - px)) * c.hrdy;
-    if (j < b.ny - 1) sy = sy - (kc + ld(in.perm, q + px)) * (ld(in.Pf, q + px) - Pf) * c.hrdy;
-    if (k > 0) sz = sz + scale2((ld(in.perm, q - pxy) + kc) * ((Pf - ld(in.Pf, q - pxy)) * c.rdz + c.buoy), 0.5f);
-    if (k < b.nz - 1)
-      sz = sz - scale2((kc + ld(in.perm, q + pxy)) * ((ld(in.Pf, q + pxy) - Pf) * c.rdz + c.buoy), 0.5f);
-    const D divqD = sx * c.rdx + sy * c.rdy + sz * c.rdz;
-    const D rpf = divqD + c.bda_rdt * (dPf * c.rB - dPt) + (Pf - Pt) * cc;
+    const double Pt = in.Pt[q], Pf = in.Pf[q], Pto = in.Pto[q], Pfo = in.Pfo[q];
+    const double ph = in.phi[q], mu = in.mu[q];
+    const double divV = (in.Vx[q + 1] - in.Vx[q]) * c.rdx + (in.Vy[q + px] - in.Vy[q]) * c.rdy +
+                        (in.Vz[q + pxy] - in.Vz[q]) * c.rdz;
+    const double cc = c.compaction_on ? 1.0 / (in.eta[q] * (1.0 - ph)) : 0.0;
+    const double divVn = divV + c.beta_d * ((Pt - Pto) - c.alpha * (Pf - Pfo)) * c.rdt + (Pt - Pf) * cc;
+    const double kc = in.perm[q];
+    const double buoy = c.rhof_g - c.rho_bg_g;
+    double kmax = kc, qxl = 0.0, qxr = 0.0, qyl = 0.0, qyr = 0.0, qzl = 0.0, qzr = 0.0;
+    if (i > 0) {
+      const double kn = in.perm[q - 1];
+      kmax = pos_max64(kmax, kn);
+      qxl = -0.5 * (kn + kc) * (Pf - in.Pf[q - 1]) * c.rdx;
+    }
+    if (i < b.nx - 1) {
+      const double kn = in.perm[q + 1];
+      kmax = pos_max64(kmax, kn);
+      qxr = -0.5 * (kc + kn) * (in.Pf[q + 1] - Pf) * c.rdx;
+    }
+    if (j > 0) {
+      const double kn = in.perm[q - px];
+      kmax = pos_max64(kmax, kn);
+      qyl = -0.5 * (kn + kc) * (Pf - in.Pf[q - px]) * c.rdy;
+    }
+    if (j < b.ny - 1) {
+      const double kn = in.perm[q + px];
+      kmax = pos_max64(kmax, kn);
+      qyr = -0.5 * (kc + kn) * (in.Pf[q + px] - Pf) * c.rdy;
+    }
+    if (k > 0) {
+      const double kn = in.perm[q - pxy];
+      kmax = pos_max64(kmax, kn);
+      qzl = -0.5 * (kn + kc) * ((Pf - in.Pf[q - pxy]) * c.rdz + buoy);
+    }
+    if (k < b.nz - 1) {
+      const double kn = in.perm[q + pxy];
+      kmax = pos_max64(kmax, kn);
+      qzr = -0.5 * (kc + kn) * ((in.Pf[q + pxy] - Pf) * c.rdz + buoy);
+    }
+    const double divqD = (qxr - qxl) * c.rdx + (qyr - qyl) * c.rdy + (qzr - qzl) * c.rdz;
+    const double rpf = divqD + c.beta_d * c.alpha * ((Pf - Pfo) / c.B - (Pt - Pto)) * c.rdt + (Pf - Pt) * cc;
     // stresses at u (Eq. 21) for the momentum residual and the Picard update
-    const D xi = mu * c.rGdtS;
-    const D s = df_rcp(D(1.0) + xi);
-    const D bn = c.beta_n * divVn;
-    const D m2 = scale2(mu, 2.0f);
-    const D third = divV * D(1.0 / 3.0);
-    out.txx[q] = (double)((ld(in.txxo, q) * xi + m2 * (gx - third + bn)) * s);
-    out.tyy[q] = (double)((ld(in.tyyo, q) * xi + m2 * (gy - third + bn)) * s);
-    out.tzz[q] = (double)((ld(in.tzzo, q) * xi + m2 * (gz - third + bn)) * s);
+    const double xi = mu * c.rGdtS;
+    const double s = 1.0 / (1.0 + xi);
+    const double bn = c.beta_n * divVn;
+    out.txx[q] = (in.txxo[q] * xi + 2.0 * mu * ((in.Vx[q + 1] - in.Vx[q]) * c.rdx - divV / 3.0 + bn)) * s;
+    out.tyy[q] = (in.tyyo[q] * xi + 2.0 * mu * ((in.Vy[q + px] - in.Vy[q]) * c.rdy - divV / 3.0 + bn)) * s;
+    out.tzz[q] = (in.tzzo[q] * xi + 2.0 * mu * ((in.Vz[q + pxy] - in.Vz[q]) * c.rdz - divV / 3.0 + bn)) * s;
     // right-hand side and frozen coefficients of the correction problem (the iteration derives
     // 1/dtau_Pf from the largest neighbour k and the local-implicit denominators itself)
-    out.r_pt[q] = to_f(divVn);
-    out.r_pf[q] = to_f(rpf);
-    out.cc[q] = to_f(cc);
-    out.perm[q] = to_f(kc);
-    out.idtp[q] = to_f(df_rcp(c.dtaupt_fac * mu));
-    r_pt = abs_d(divVn);
-    r_pf = abs_d(rpf);
+    (void)kmax;
+    out.r_pt[q] = (float)divVn;
+    out.r_pf[q] = (float)rpf;
+    out.cc[q] = (float)cc;
+    out.perm[q] = (float)kc;
+    out.idtp[q] = (float)(1.0 / (c.dtaupt_fac * mu));
+    r_pt = fabs(divVn);
+    r_pf = fabs(rpf);
   }
 }
 
-// Edge shear stresses at u (Eq. 21; the background shear of Eqs. 32-33 on every xy-edge), in
-// double-float.
-__device__ __forceinline__ void mix_edges_point(const Box& b, const MixCoefDF& c, const EdgeIn& in,
-                                                const EdgeOut& out, int i, int j, int k) {
-  if (i > b.nx || j > b.ny || k > b.nz) return;
-  const long long q = cidx(b, i, j, k);
-  const long long px = b.px, pxy = b.pxy;
-  if (k < b.nz) {  // xy-edge (i, j, k)
-    D t(0.0);
-    if (i > 0 && i < b.nx && j > 0 && j < b.ny) {
-      const D m = scale2(ld(in.mu, q - 1 - px) + ld(in.mu, q - px) + ld(in.mu, q - 1) + ld(in.mu, q), 0.25f);
-      const D xi = m * c.rGdtS;
-      const D e = (ld(in.Vx, q) - ld(in.Vx, q - px)) * c.hrdy + (ld(in.Vy, q) - ld(in.Vy, q - 1)) * c.hrdx + c.ebg;
-      t = (ld(in.txyo, q) * xi + scale2(m, 2.0f) * e) * df_rcp(D(1.0) + xi);
-    } else if (c.bg_on) {   // wall edge: background part only
-      const D m(edge_mean_mu_xy(b, in.mu, q, i, j));
-      const D xi = m * c.rGdtS;
-      t = (ld(in.txyo, q) * xi + scale2(m, 2.0f) * c.ebg) * df_rcp(D(1.0) + xi);
-    }
-    out.txy[q] = (double)t;
-  }
-  if (j < b.ny) {  // xz-edge (i, j, k)
-    D t(0.0);
-    if (i > 0 && i < b.nx && k > 0 && k < b.nz) {
-      const D m = scale2(ld(in.mu, q - 1 - pxy) + ld(in.mu, q - pxy) + ld(in.mu, q - 1) + ld(in.mu, q), 0.25f);
-      const D xi = m * c.rGdtS;
-      const D e = (ld(in.Vx, q) - ld(in.Vx, q - pxy)) * c.hrdz + (ld(in.Vz, q) - ld(in.Vz, q - 1)) * c.hrdx;
-      t = (ld(in.txzo, q) * xi + scale2(m, 2.0f) * e) * df_rcp(D(1.0) + xi);
-    }
-    out.txz[q] = (double)t;
-  }
-  if (i < b.nx) {  // yz-edge (i, j, k)
-    D t(0.0);
-    if (j > 0 && j < b.ny && k > 0 && k < b.nz) {
-      const D m = scale2(ld(in.mu, q - px - pxy) + ld(in.mu, q - pxy) + ld(in.mu, q - px) + ld(in.mu, q), 0.25f);
-      const D xi = m * c.rGdtS;
-      const D e = (ld(in.Vy, q) - ld(in.Vy, q - pxy)) * c.hrdz + (ld(in.Vz, q) - ld(in.Vz, q - px)) * c.hrdy;
-      t = (ld(in.tyzo, q) * xi + scale2(m, 2.0f) * e) * df_rcp(D(1.0) + xi);
-    }
-    out.tyz[q] = (double)t;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_mix_prepare(Box b, MixCoefDF c, MixPrepIn in, MixPrepOut out,
+__global__ void __launch_bounds__(256) k_mix_prepare(Box b, Coef c, MixPrepIn in, MixPrepOut out,
                                                      unsigned long long* red) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -135,42 +109,36 @@ __global__ void __launch_bounds__(256) k_mix_prepare(Box b, MixCoefDF c, MixPrep
   block_max_atomic(r_pf, red + RED_PF);
 }
 
-__global__ void __launch_bounds__(256) k_mix_edges(Box b, MixCoefDF c, EdgeIn in, EdgeOut out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  mix_edges_point(b, c, in, out, i, j, (int)blockIdx.z);
-}
-
-// (i) Momentum residual at u (Eq. 19) in double-float, stored in FP32; its max-norm.
-__device__ __forceinline__ void mix_res_faces_point(const Box& b, const MixCoefDF& c, const MixFaceIn& in,
+// (i) FP64 momentum residual at u (Eq. 19), stored in FP32; its max-norm.
+__device__ __forceinline__ void mix_res_faces_point(const Box& b, const Coef& c, const MixFaceIn& in,
                                                     float* __restrict__ rfx, float* __restrict__ rfy,
                                                     float* __restrict__ rfz, int i, int j, int k, double& r_v) {
   if (i <= b.nx && j <= b.ny && k <= b.nz) {
     const long long q = cidx(b, i, j, k);
     const long long px = b.px, pxy = b.pxy;
     if (i > 0 && i < b.nx && j < b.ny && k < b.nz) {
-      const D F = (ld(in.txx, q) - ld(in.txx, q - 1)) * c.rdx + (ld(in.txy, q + px) - ld(in.txy, q)) * c.rdy +
-                  (ld(in.txz, q + pxy) - ld(in.txz, q)) * c.rdz - (ld(in.Pt, q) - ld(in.Pt, q - 1)) * c.rdx;
-      rfx[q] = to_f(F);
-      r_v = fmax(r_v, abs_d(F));
+      const double F = (in.txx[q] - in.txx[q - 1]) * c.rdx + (in.txy[q + px] - in.txy[q]) * c.rdy +
+                       (in.txz[q + pxy] - in.txz[q]) * c.rdz - (in.Pt[q] - in.Pt[q - 1]) * c.rdx;
+      rfx[q] = (float)F;
+      r_v = fmax(r_v, fabs(F));
     }
     if (j > 0 && j < b.ny && i < b.nx && k < b.nz) {
-      const D F = (ld(in.txy, q + 1) - ld(in.txy, q)) * c.rdx + (ld(in.tyy, q) - ld(in.tyy, q - px)) * c.rdy +
-                  (ld(in.tyz, q + pxy) - ld(in.tyz, q)) * c.rdz - (ld(in.Pt, q) - ld(in.Pt, q - px)) * c.rdy;
-      rfy[q] = to_f(F);
-      r_v = fmax(r_v, abs_d(F));
+      const double F = (in.txy[q + 1] - in.txy[q]) * c.rdx + (in.tyy[q] - in.tyy[q - px]) * c.rdy +
+                       (in.tyz[q + pxy] - in.tyz[q]) * c.rdz - (in.Pt[q] - in.Pt[q - px]) * c.rdy;
+      rfy[q] = (float)F;
+      r_v = fmax(r_v, fabs(F));
     }
     if (k > 0 && k < b.nz && i < b.nx && j < b.ny) {
-      const D rog = (scale2(ld(in.phi, q - pxy) + ld(in.phi, q), 0.5f) - c.phi0) * c.drho;
-      const D F = (ld(in.txz, q + 1) - ld(in.txz, q)) * c.rdx + (ld(in.tyz, q + px) - ld(in.tyz, q)) * c.rdy +
-                  (ld(in.tzz, q) - ld(in.tzz, q - pxy)) * c.rdz - (ld(in.Pt, q) - ld(in.Pt, q - pxy)) * c.rdz - rog;
-      rfz[q] = to_f(F);
-      r_v = fmax(r_v, abs_d(F));
+      const double rog = (0.5 * (in.phi[q - pxy] + in.phi[q]) - c.phi0) * (c.rhof_g - c.rhos_g);
+      const double F = (in.txz[q + 1] - in.txz[q]) * c.rdx + (in.tyz[q + px] - in.tyz[q]) * c.rdy +
+                       (in.tzz[q] - in.tzz[q - pxy]) * c.rdz - (in.Pt[q] - in.Pt[q - pxy]) * c.rdz - rog;
+      rfz[q] = (float)F;
+      r_v = fmax(r_v, fabs(F));
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_mix_res_faces(Box b, MixCoefDF c, MixFaceIn in, float* __restrict__ rfx,
+__global__ void __launch_bounds__(256) k_mix_res_faces(Box b, Coef c, MixFaceIn in, float* __restrict__ rfx,
                                                        float* __restrict__ rfy, float* __restrict__ rfz,
                                                        unsigned long long* red) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -482,36 +450,13 @@ __global__ void __launch_bounds__(256) k_mix_update(Box b, MixUpdate u) {
   mix_update_point(b, u, i, j, (int)blockIdx.z);
 }
 
-void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixCoefDF& c, const MixPrepIn& in,
+void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPrepIn& in,
                  const MixPrepOut& out, unsigned long long* red) {
   k_mix_prepare<<<g, bl, 0, s>>>(b, c, in, out, red);
 }
-void mix_edges(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixCoefDF& c, const EdgeIn& in, const EdgeOut& out) {
-  k_mix_edges<<<g, bl, 0, s>>>(b, c, in, out);
-}
-void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixCoefDF& c, const MixFaceIn& in, float* rfx,
+void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixFaceIn& in, float* rfx,
                    float* rfy, float* rfz, unsigned long long* red) {
   k_mix_res_faces<<<g, bl, 0, s>>>(b, c, in, rfx, rfy, rfz, red);
-}
-
-MixCoefDF mix_coef_df(const Coef& k) {
-  MixCoefDF d;
-  d.rdx = df64(k.rdx); d.rdy = df64(k.rdy); d.rdz = df64(k.rdz);
-  d.hrdx = df64(0.5 * k.rdx); d.hrdy = df64(0.5 * k.rdy); d.hrdz = df64(0.5 * k.rdz);
-  d.bd_rdt = df64(k.beta_d * k.rdt);
-  d.bda_rdt = df64(k.beta_d * k.alpha * k.rdt);
-  d.alpha = df64(k.alpha);
-  d.rB = df64(1.0 / k.B);
-  d.buoy = df64(k.rhof_g - k.rho_bg_g);
-  d.drho = df64(k.rhof_g - k.rhos_g);
-  d.phi0 = df64(k.phi0);
-  d.rGdtS = df64(k.rGdtS);
-  d.beta_n = df64(k.beta_n);
-  d.dtaupt_fac = df64(k.dtaupt_fac);
-  d.ebg = df64(k.ebg);
-  d.compaction_on = k.compaction_on;
-  d.bg_on = k.bg_on;
-  return d;
 }
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out) {
   k_mix_coef<<<g, bl, 0, s>>>(b, c, mu, out);
@@ -770,14 +715,14 @@ __global__ void __launch_bounds__(kMbBX * kMbBY) k_mb_points(const MixBatchInst*
                           I.txxo, I.tyyo, I.tzzo};
       const MixPrepOut pout{I.s_txx, I.s_tyy, I.s_tzz, I.rpt, I.rpf, I.ccf, I.kf, I.idtp};
       double r_pt = 0.0, r_pf = 0.0;
-      mix_prepare_point(b, I.kd, pin, pout, i, j, kz, r_pt, r_pf);
-      mix_edges_point(b, I.kd, EdgeIn{I.Vx, I.Vy, I.Vz, I.mu, I.txyo, I.txzo, I.tyzo},
-                      EdgeOut{I.s_txy, I.s_txz, I.s_tyz}, i, j, kz);
+      mix_prepare_point(b, I.k, pin, pout, i, j, kz, r_pt, r_pf);
+      edges_point(b, I.k, EdgeIn{I.Vx, I.Vy, I.Vz, I.mu, I.txyo, I.txzo, I.tyzo},
+                  EdgeOut{I.s_txy, I.s_txz, I.s_tyz}, i, j, kz);
       block_max_atomic(r_pt, I.red + RED_PT);
       block_max_atomic(r_pf, I.red + RED_PF);
     } else if (PHASE == MB_PH_FACES) {
       double r_v = 0.0, pic = 1.0;
-      mix_res_faces_point(b, I.kd, MixFaceIn{I.s_txx, I.s_tyy, I.s_tzz, I.s_txy, I.s_txz, I.s_tyz, I.Pt[a], I.phi[a]},
+      mix_res_faces_point(b, I.k, MixFaceIn{I.s_txx, I.s_tyy, I.s_tzz, I.s_txy, I.s_txz, I.s_tyz, I.Pt[a], I.phi[a]},
                           I.rfx, I.rfy, I.rfz, i, j, kz, r_v);
       lean_picard_point(b, I.lc,
                         LeanPicardIn<double>{I.s_txx, I.s_tyy, I.s_tzz, I.s_txy, I.s_txz, I.s_tyz, I.phi[a],
