@@ -184,7 +184,7 @@ def parse():
                     help="run the FP32 form with plain PT correction solves only up to this grid size")
     ap.add_argument("--pc-mg", type=int, default=0,
                     help="also the FP32 form with multigrid correction solves over this many levels (>= 2; "
-                         "grids divisible by 2^(levels-1))")
+                         "each level ceil(n / 2) cells per direction, the coarsest at least 2)")
     ap.add_argument("--batch-inner-rtol", type=float, default=0.0,
                     help="FP32 ensembles: relative residual drop of each FP32 correction solve (0: library default)")
     ap.add_argument("--batched-converge", action="store_true",
@@ -807,7 +807,10 @@ def measure_precision(args, dev) -> dict:
             phi32, it32, t32 = run(dict(p, precision=N.PT_FP32), phi0, k)
             r.update(fp32_iters=sum(it32), fp32_s=t32, fp32_vs_ref=errs(phi32, phi64, phi0))
         L = args.pc_mg
-        if L >= 2 and n % (1 << (L - 1)) == 0 and n >> (L - 1) >= 2:
+        nc = n
+        for _ in range(max(L - 1, 0)):
+            nc = (nc + 1) // 2                     # each level ceil(n / 2) cells per direction
+        if L >= 2 and nc >= 2:
             phimg, itmg, tmg = run(dict(p, precision=N.PT_FP32, mg_levels=L), phi0, k)
             r.update(fp32mg_levels=L, fp32mg_iters=sum(itmg), fp32mg_s=tmg, fp32mg_vs_ref=errs(phimg, phi64, phi0))
             if phi32 is not None:

@@ -122,10 +122,10 @@ typedef struct {
                            * of its residual (0 = 0.1)                                     */
   int32_t mg_levels;      /* PT_FP32: 0 or 1 = each correction problem is solved by FP32 PT
                            * iterations; L >= 2 = by geometric-multigrid V-cycles over L grids
-                           * (each 2x coarser per direction; nx, ny, nz divisible by 2^(L-1),
-                           * the coarsest at least 2 cells per direction), smoothed by the PT
-                           * sweep (see pt_mixed_kernels.cu); PT_EINVAL otherwise, and for
-                           * batched ensembles                                               */
+                           * (each with ceil(n / 2) cells per direction of the one above, over
+                           * the same box: nested for even n; the coarsest at least 2 cells per
+                           * direction), smoothed by the PT sweep (see pt_mixed_kernels.cu);
+                           * PT_EINVAL otherwise, and for batched ensembles                   */
   int32_t mg_reserved;    /* 0                                                              */
 } pt_num;
 

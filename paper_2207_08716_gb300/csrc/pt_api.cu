@@ -289,20 +289,23 @@ CorrCoef<float> corr_coef_of(const Coef& k) {
   return f;
 }
 
-// The grid of multigrid level l (2^l coarser per direction, same box lengths).
+// The grid of multigrid level l: each level has ceil(n / 2) cells per direction of the level
+// above over the same box lengths (nested for an even n).
 pt_grid mg_grid(const pt_grid& g, int l) {
   pt_grid h = g;
-  h.nx = g.nx >> l;
-  h.ny = g.ny >> l;
-  h.nz = g.nz >> l;
+  for (int k = 0; k < l; ++k) {
+    h.nx = (h.nx + 1) / 2;
+    h.ny = (h.ny + 1) / 2;
+    h.nz = (h.nz + 1) / 2;
+  }
   return h;
 }
 
 bool mg_ok(const pt_grid& g, const pt_num& n) {
   if (n.mg_levels <= 1) return n.mg_levels >= 0;
   if (n.precision != PT_FP32 || n.mg_levels > kMgMaxLevels) return false;
-  const int f = 1 << (n.mg_levels - 1);
-  return g.nx % f == 0 && g.ny % f == 0 && g.nz % f == 0 && g.nx / f >= 2 && g.ny / f >= 2 && g.nz / f >= 2;
+  const pt_grid c = mg_grid(g, n.mg_levels - 1);   // the coarsest grid
+  return c.nx >= 2 && c.ny >= 2 && c.nz >= 2;
 }
 
 // Workspace of the V-cycle's grids: the finest level's residual outputs, kMgArrays per coarser level.
@@ -888,11 +891,17 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
     f0.Rx = c->m_Rx; f0.Ry = c->m_Ry; f0.Rz = c->m_Rz;
     f0.res_pt = (float*)wend;
     f0.res_pf = (float*)(wend + fstride);
+    for (int d = 0; d < 3; ++d) f0.r[d] = f0.rinv[d] = 1.0;
     wend += kMgFineArrays * fstride;
     for (int l = 1; l < c->mg_L; ++l) {
-      const pt_grid gl = mg_grid(*grid, l);
+      const pt_grid gl = mg_grid(*grid, l), gf = mg_grid(*grid, l - 1);
       MgLevel& L = c->mg[l];
       L.b = make_box(&gl);
+      const int nf[3] = {gf.nx, gf.ny, gf.nz}, nc[3] = {gl.nx, gl.ny, gl.nz};
+      for (int d = 0; d < 3; ++d) {   // fine cells per coarse cell: 2, or just under 2 for an odd count
+        L.r[d] = (double)nf[d] / nc[d];
+        L.rinv[d] = (double)nc[d] / nf[d];
+      }
       const size_t st = align_up((size_t)L.b.n * sizeof(float), kAlign);
       float** slots[kMgArrays] = {&L.cc, &L.perm, &L.idtp, &L.mu, &L.dtvc, &L.rpt, &L.rpf, &L.rfx, &L.rfy,
                                   &L.rfz, &L.dVx[0], &L.dVx[1], &L.dVy[0], &L.dVy[1], &L.dVz[0], &L.dVz[1],

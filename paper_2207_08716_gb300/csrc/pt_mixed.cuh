@@ -53,6 +53,9 @@ struct CorrOut {
 // own arrays; coarser levels live in the workspace).
 struct MgLevel {
   Box b;
+  double r[3];                                     // fine cells per cell of this level (x, y, z), 1 < r <= 2;
+                                                   // 2 when the finer grid has an even count
+  double rinv[3];                                  // 1 / r (positions in FP64: weights exact to FP32)
   float *cc, *perm, *idtp, *mu, *dtvc;             // frozen coefficients
   float *rpt, *rpf, *rfx, *rfy, *rfz;              // right-hand sides
   float *dVx[2], *dVy[2], *dVz[2], *dPt[2], *dPf[2];
@@ -69,15 +72,20 @@ void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u);
 // One fused FP32 correction iteration over the whole grid (z-marching tiles, see the kernel).
 void corr_iteration(cudaStream_t s, Box b, const CorrCoef<float>& c, const CorrIn<float>& in,
                     const CorrOut<float>& out, unsigned long long* red, int check);
-// Multigrid transfers between level `f` and the 2x coarser level `c`:
-//   mg_coef      coarse mu, k, cc = means of the 8 fine cells; 1/dtau_Pt and dtau_V from the coarse mu
-//                with the coarse grid's pseudo-step factors
-//   mg_restrict  coarse right-hand sides from the fine residuals (cells: mean of 8; faces: mean over
-//                the 2 x 2 tangential children of the (1/4, 1/2, 1/4) normal weighting; the fine
-//                momentum residual is rho_i R of the evaluation sweep), zero coarse iterate and R
+// Multigrid transfers between level `f` (n cells per direction) and the coarser level `c`
+// (ceil(n / 2) cells over the same box, so r = n / ceil(n / 2) fine cells per coarse cell: 2 for an
+// even n, slightly less for an odd one, where the grids are not nested):
+//   mg_coef      coarse mu, k, cc = means over the fine cells a coarse cell covers (weights = the
+//                covered fractions, "box" weights); 1/dtau_Pt and dtau_V from the coarse mu with the
+//                coarse grid's pseudo-step factors
+//   mg_restrict  coarse right-hand sides from the fine residuals (cells: box weights; faces: the
+//                hat function of half-width r along the normal, normalised -- (1/4, 1/2, 1/4) for
+//                r = 2 -- times box weights across it; the fine momentum residual is rho_i R of the
+//                evaluation sweep), zero coarse iterate and R
 //   mg_prolong   fine iterate (buffers df) += coarse correction (buffers dc) interpolated: cells
-//                trilinearly (cell-centred, 3/4 and 1/4, zero gradient at the walls), faces linearly
-//                between coincident coarse faces along the normal and cell-centred across it
+//                trilinearly between coarse centres (3/4 and 1/4 for r = 2; zero gradient beyond the
+//                first and last centre), faces linearly between coarse faces along the normal and
+//                between centres across it
 void mg_coef(cudaStream_t s, const MgLevel& f, const MgLevel& c, float dtaupt_fac, float dtauv_fac);
 void mg_restrict(cudaStream_t s, const MgLevel& f, const MgLevel& c, float rho_i);
 void mg_prolong(cudaStream_t s, const MgLevel& c, int dc, const MgLevel& f, int df);

@@ -474,18 +474,53 @@ void corr_iteration(cudaStream_t s, Box b, const CorrCoef<float>& c, const CorrI
 
 
 // ============================================================ multigrid transfers (FP32)
-// Level f (fine, nx x ny x nz cells) and level c (coarse, nx/2 x ny/2 x nz/2): coarse cell I
-// covers fine cells 2I and 2I+1 per direction; coarse face I coincides with fine face 2I.
+// Level f (fine, n cells per direction) and level c (coarse, ceil(n / 2)): in fine-cell units a
+// coarse cell I spans [I r, (I + 1) r] and a coarse face J sits at J r (r = c.r[d]).
 namespace {
 
-__device__ __forceinline__ long long mg_q(const Box& b, int i, int j, int k) { return cidx(b, i, j, k); }
+// Box weights of coarse cell I along one direction: the fractions of fine cells i0, i0 + 1,
+// i0 + 2 it covers (at most three for r <= 2), over r; they sum to 1.
+__device__ __forceinline__ void mg_box(int I, double r, int nf, int& i0, float w[3]) {
+  const double a = I * r, b = (I + 1) * r;
+  i0 = (int)floor(a);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int i = i0 + t;
+    const double lo = fmax(a, (double)i), hi = fmin(b, (double)(i + 1));
+    w[t] = (i < nf && hi > lo) ? (float)((hi - lo) / r) : 0.f;
+  }
+}
 
-// cell-centred linear interpolation weights along one direction: fine index i of a grid with nc
-// coarse cells -> coarse cells (a, b) with weights (3/4, 1/4); the outer neighbour is held at the
-// wall (zero gradient)
-__device__ __forceinline__ void mg_cc_lin(int i, int nc, int& a, int& b) {
-  a = i >> 1;
-  b = (i & 1) ? min(a + 1, nc - 1) : max(a - 1, 0);
+// Linear interpolation between coarse centres for fine cell i: coarse cells (a, b) with weights
+// (wa, wb); beyond the first and last centre the nearest centre's value (zero gradient).
+__device__ __forceinline__ void mg_lin(int i, double rinv, int nc, int& a, int& b, float& wa, float& wb) {
+  const double s = (i + 0.5) * rinv - 0.5;
+  const double fl = floor(s);
+  int i0 = (int)fl;
+  float t = (float)(s - fl);
+  if (i0 < 0) { i0 = 0; t = 0.f; }
+  if (i0 >= nc - 1) { i0 = nc - 1; t = 0.f; }
+  a = i0;
+  b = min(i0 + 1, nc - 1);
+  wa = 1.f - t;
+  wb = t;
+}
+
+// Hat weights of coarse face J over the fine faces within r of it (at most four), normalised.
+__device__ __forceinline__ int mg_hat(int J, double r, int nf, int& i0, float w[4]) {
+  const double X = J * r;
+  i0 = max((int)floor(X - r) + 1, 0);
+  float sum = 0.f;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int i = i0 + t;
+    const double v = (i <= nf) ? 1.0 - fabs((double)i - X) / r : 0.0;
+    w[t] = v > 0.0 ? (float)v : 0.f;
+    sum += w[t];
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) w[t] /= sum;
+  return 4;
 }
 
 }  // namespace
@@ -494,20 +529,26 @@ __global__ void __launch_bounds__(256) k_mg_coef(MgLevel f, MgLevel c, float dta
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= c.b.nx || J >= c.b.ny || K >= c.b.nz) return;
+  int i0, j0, k0;
+  float wx[3], wy[3], wz[3];
+  mg_box(I, c.r[0], f.b.nx, i0, wx);
+  mg_box(J, c.r[1], f.b.ny, j0, wy);
+  mg_box(K, c.r[2], f.b.nz, k0, wz);
   float m = 0.f, k = 0.f, cc = 0.f;
-  for (int dz = 0; dz < 2; ++dz)
-    for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx) {
-        const long long q = mg_q(f.b, 2 * I + dx, 2 * J + dy, 2 * K + dz);
-        m += f.mu[q];
-        k += f.perm[q];
-        cc += f.cc[q];
+  for (int dz = 0; dz < 3; ++dz)
+    for (int dy = 0; dy < 3; ++dy)
+      for (int dx = 0; dx < 3; ++dx) {
+        const float w = wx[dx] * wy[dy] * wz[dz];
+        if (w == 0.f) continue;
+        const long long q = cidx(f.b, i0 + dx, j0 + dy, k0 + dz);
+        m += w * f.mu[q];
+        k += w * f.perm[q];
+        cc += w * f.cc[q];
       }
-  const long long qc = mg_q(c.b, I, J, K);
-  m *= 0.125f;
+  const long long qc = cidx(c.b, I, J, K);
   c.mu[qc] = m;
-  c.perm[qc] = 0.125f * k;
-  c.cc[qc] = 0.125f * cc;
+  c.perm[qc] = k;
+  c.cc[qc] = cc;
   c.idtp[qc] = 1.0f / (dtaupt_fac * m);
   c.dtvc[qc] = dtauv_fac / m;
 }
@@ -517,51 +558,73 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgLevel f, MgLevel c, float
   const int K = blockIdx.z;
   const Box& B = c.b;
   if (I > B.nx || J > B.ny || K > B.nz) return;
-  const long long qc = mg_q(B, I, J, K);
+  const long long qc = cidx(B, I, J, K);
   // a zero correction and damped residual on the coarse grid (walls included)
   c.dVx[0][qc] = 0.f; c.dVx[1][qc] = 0.f; c.dVy[0][qc] = 0.f; c.dVy[1][qc] = 0.f;
   c.dVz[0][qc] = 0.f; c.dVz[1][qc] = 0.f; c.dPt[0][qc] = 0.f; c.dPf[0][qc] = 0.f;
   c.Rx[qc] = 0.f; c.Ry[qc] = 0.f; c.Rz[qc] = 0.f;
+  const Box& F = f.b;
+  int i0, j0, k0;
+  float bx[3], by[3], bz[3], h[4];
   if (I < B.nx && J < B.ny && K < B.nz) {
+    mg_box(I, c.r[0], F.nx, i0, bx);
+    mg_box(J, c.r[1], F.ny, j0, by);
+    mg_box(K, c.r[2], F.nz, k0, bz);
     float a = 0.f, b = 0.f;
-    for (int dz = 0; dz < 2; ++dz)
-      for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx) {
-          const long long q = mg_q(f.b, 2 * I + dx, 2 * J + dy, 2 * K + dz);
-          a += f.res_pt[q];
-          b += f.res_pf[q];
+    for (int dz = 0; dz < 3; ++dz)
+      for (int dy = 0; dy < 3; ++dy)
+        for (int dx = 0; dx < 3; ++dx) {
+          const float w = bx[dx] * by[dy] * bz[dz];
+          if (w == 0.f) continue;
+          const long long q = cidx(F, i0 + dx, j0 + dy, k0 + dz);
+          a += w * f.res_pt[q];
+          b += w * f.res_pf[q];
         }
-    c.rpt[qc] = 0.125f * a;
-    c.rpf[qc] = 0.125f * b;
+    c.rpt[qc] = a;
+    c.rpf[qc] = b;
   }
-  const long long fx = 1, fy = f.b.px, fz = f.b.pxy;
-  // x-face I (interior): fine faces 2I - 1, 2I, 2I + 1 of the children rows (2J + dy, 2K + dz)
+  // faces: hat weights along the normal, box weights across it
   if (I > 0 && I < B.nx && J < B.ny && K < B.nz) {
+    mg_hat(I, c.r[0], F.nx, i0, h);
+    mg_box(J, c.r[1], F.ny, j0, by);
+    mg_box(K, c.r[2], F.nz, k0, bz);
     float s = 0.f;
-    for (int dz = 0; dz < 2; ++dz)
-      for (int dy = 0; dy < 2; ++dy) {
-        const long long q = mg_q(f.b, 2 * I, 2 * J + dy, 2 * K + dz);
-        s += 0.5f * f.Rx[q] + 0.25f * (f.Rx[q - fx] + f.Rx[q + fx]);
-      }
-    c.rfx[qc] = 0.25f * rho_i * s;
+    for (int dz = 0; dz < 3; ++dz)
+      for (int dy = 0; dy < 3; ++dy)
+        for (int dx = 0; dx < 4; ++dx) {
+          const float w = h[dx] * by[dy] * bz[dz];
+          if (w == 0.f) continue;
+          s += w * f.Rx[cidx(F, i0 + dx, j0 + dy, k0 + dz)];
+        }
+    c.rfx[qc] = rho_i * s;
   }
   if (J > 0 && J < B.ny && I < B.nx && K < B.nz) {
+    mg_box(I, c.r[0], F.nx, i0, bx);
+    mg_hat(J, c.r[1], F.ny, j0, h);
+    mg_box(K, c.r[2], F.nz, k0, bz);
     float s = 0.f;
-    for (int dz = 0; dz < 2; ++dz)
-      for (int dx = 0; dx < 2; ++dx) {
-        const long long q = mg_q(f.b, 2 * I + dx, 2 * J, 2 * K + dz);
-        s += 0.5f * f.Ry[q] + 0.25f * (f.Ry[q - fy] + f.Ry[q + fy]);
-      }
-    c.rfy[qc] = 0.25f * rho_i * s;
+    for (int dz = 0; dz < 3; ++dz)
+      for (int dy = 0; dy < 4; ++dy)
+        for (int dx = 0; dx < 3; ++dx) {
+          const float w = bx[dx] * h[dy] * bz[dz];
+          if (w == 0.f) continue;
+          s += w * f.Ry[cidx(F, i0 + dx, j0 + dy, k0 + dz)];
+        }
+    c.rfy[qc] = rho_i * s;
   }
   if (K > 0 && K < B.nz && I < B.nx && J < B.ny) {
+    mg_box(I, c.r[0], F.nx, i0, bx);
+    mg_box(J, c.r[1], F.ny, j0, by);
+    mg_hat(K, c.r[2], F.nz, k0, h);
     float s = 0.f;
-    for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx) {
-        const long long q = mg_q(f.b, 2 * I + dx, 2 * J + dy, 2 * K);
-        s += 0.5f * f.Rz[q] + 0.25f * (f.Rz[q - fz] + f.Rz[q + fz]);
-      }
-    c.rfz[qc] = 0.25f * rho_i * s;
+    for (int dz = 0; dz < 4; ++dz)
+      for (int dy = 0; dy < 3; ++dy)
+        for (int dx = 0; dx < 3; ++dx) {
+          const float w = bx[dx] * by[dy] * h[dz];
+          if (w == 0.f) continue;
+          s += w * f.Rz[cidx(F, i0 + dx, j0 + dy, k0 + dz)];
+        }
+    c.rfz[qc] = rho_i * s;
   }
 }
 
@@ -570,65 +633,73 @@ __global__ void __launch_bounds__(256) k_mg_prolong(MgLevel c, int dc, MgLevel f
   const int k = blockIdx.z;
   const Box& B = f.b;
   if (i > B.nx || j > B.ny || k > B.nz) return;
-  const long long q = mg_q(B, i, j, k);
+  const long long q = cidx(B, i, j, k);
   const int ncx = c.b.nx, ncy = c.b.ny, ncz = c.b.nz;
-  int ia, ib, ja, jb, ka, kb;
-  if (i < B.nx && j < B.ny && k < B.nz) {   // cells: trilinear
-    mg_cc_lin(i, ncx, ia, ib);
-    mg_cc_lin(j, ncy, ja, jb);
-    mg_cc_lin(k, ncz, ka, kb);
-    const int xs[2] = {ia, ib}, ys[2] = {ja, jb}, zs[2] = {ka, kb};
-    const float w[2] = {0.75f, 0.25f};
+  int xa, xb, ya, yb, za, zb;
+  float wxa, wxb, wya, wyb, wza, wzb;
+  if (i < B.nx && j < B.ny && k < B.nz) {   // cells: trilinear between coarse centres
+    mg_lin(i, c.rinv[0], ncx, xa, xb, wxa, wxb);
+    mg_lin(j, c.rinv[1], ncy, ya, yb, wya, wyb);
+    mg_lin(k, c.rinv[2], ncz, za, zb, wza, wzb);
+    const int xs[2] = {xa, xb}, ys[2] = {ya, yb}, zs[2] = {za, zb};
+    const float wx[2] = {wxa, wxb}, wy[2] = {wya, wyb}, wz[2] = {wza, wzb};
     float pt = 0.f, pf = 0.f;
     for (int a = 0; a < 2; ++a)
       for (int bb = 0; bb < 2; ++bb)
         for (int cc = 0; cc < 2; ++cc) {
-          const float ww = w[a] * w[bb] * w[cc];
-          const long long qc = mg_q(c.b, xs[cc], ys[bb], zs[a]);
-          pt += ww * c.dPt[dc][qc];
-          pf += ww * c.dPf[dc][qc];
+          const float w = wz[a] * wy[bb] * wx[cc];
+          const long long qc = cidx(c.b, xs[cc], ys[bb], zs[a]);
+          pt += w * c.dPt[dc][qc];
+          pf += w * c.dPf[dc][qc];
         }
     f.dPt[df][q] += pt;
     f.dPf[df][q] += pf;
   }
-  const float w[2] = {0.75f, 0.25f};
-  if (i > 0 && i < B.nx && j < B.ny && k < B.nz) {   // x-faces
-    const int n0 = i >> 1, n1 = (i + 1) >> 1;         // coincident (i even: n0 = n1) or the two around
-    mg_cc_lin(j, ncy, ja, jb);
-    mg_cc_lin(k, ncz, ka, kb);
-    const int ys[2] = {ja, jb}, zs[2] = {ka, kb};
+  // faces: linear between coarse faces along the normal (s = i / r; coarse wall faces are zero),
+  // between coarse centres across it
+  if (i > 0 && i < B.nx && j < B.ny && k < B.nz) {
+    const double s = i * c.rinv[0];
+    const int n0 = (int)floor(s);
+    const float t = (float)(s - n0);
+    mg_lin(j, c.rinv[1], ncy, ya, yb, wya, wyb);
+    mg_lin(k, c.rinv[2], ncz, za, zb, wza, wzb);
+    const int ys[2] = {ya, yb}, zs[2] = {za, zb};
+    const float wy[2] = {wya, wyb}, wz[2] = {wza, wzb};
     float v = 0.f;
     for (int a = 0; a < 2; ++a)
-      for (int bb = 0; bb < 2; ++bb) {
-        const float ww = w[a] * w[bb];
-        v += ww * 0.5f * (c.dVx[dc][mg_q(c.b, n0, ys[bb], zs[a])] + c.dVx[dc][mg_q(c.b, n1, ys[bb], zs[a])]);
-      }
+      for (int bb = 0; bb < 2; ++bb)
+        v += wz[a] * wy[bb] * ((1.f - t) * c.dVx[dc][cidx(c.b, n0, ys[bb], zs[a])] +
+                               t * c.dVx[dc][cidx(c.b, min(n0 + 1, ncx), ys[bb], zs[a])]);
     f.dVx[df][q] += v;
   }
-  if (j > 0 && j < B.ny && i < B.nx && k < B.nz) {   // y-faces
-    const int n0 = j >> 1, n1 = (j + 1) >> 1;
-    mg_cc_lin(i, ncx, ia, ib);
-    mg_cc_lin(k, ncz, ka, kb);
-    const int xs[2] = {ia, ib}, zs[2] = {ka, kb};
+  if (j > 0 && j < B.ny && i < B.nx && k < B.nz) {
+    const double s = j * c.rinv[1];
+    const int n0 = (int)floor(s);
+    const float t = (float)(s - n0);
+    mg_lin(i, c.rinv[0], ncx, xa, xb, wxa, wxb);
+    mg_lin(k, c.rinv[2], ncz, za, zb, wza, wzb);
+    const int xs[2] = {xa, xb}, zs[2] = {za, zb};
+    const float wx[2] = {wxa, wxb}, wz[2] = {wza, wzb};
     float v = 0.f;
     for (int a = 0; a < 2; ++a)
-      for (int cc = 0; cc < 2; ++cc) {
-        const float ww = w[a] * w[cc];
-        v += ww * 0.5f * (c.dVy[dc][mg_q(c.b, xs[cc], n0, zs[a])] + c.dVy[dc][mg_q(c.b, xs[cc], n1, zs[a])]);
-      }
+      for (int cc = 0; cc < 2; ++cc)
+        v += wz[a] * wx[cc] * ((1.f - t) * c.dVy[dc][cidx(c.b, xs[cc], n0, zs[a])] +
+                               t * c.dVy[dc][cidx(c.b, xs[cc], min(n0 + 1, ncy), zs[a])]);
     f.dVy[df][q] += v;
   }
-  if (k > 0 && k < B.nz && i < B.nx && j < B.ny) {   // z-faces
-    const int n0 = k >> 1, n1 = (k + 1) >> 1;
-    mg_cc_lin(i, ncx, ia, ib);
-    mg_cc_lin(j, ncy, ja, jb);
-    const int xs[2] = {ia, ib}, ys[2] = {ja, jb};
+  if (k > 0 && k < B.nz && i < B.nx && j < B.ny) {
+    const double s = k * c.rinv[2];
+    const int n0 = (int)floor(s);
+    const float t = (float)(s - n0);
+    mg_lin(i, c.rinv[0], ncx, xa, xb, wxa, wxb);
+    mg_lin(j, c.rinv[1], ncy, ya, yb, wya, wyb);
+    const int xs[2] = {xa, xb}, ys[2] = {ya, yb};
+    const float wx[2] = {wxa, wxb}, wy[2] = {wya, wyb};
     float v = 0.f;
     for (int bb = 0; bb < 2; ++bb)
-      for (int cc = 0; cc < 2; ++cc) {
-        const float ww = w[bb] * w[cc];
-        v += ww * 0.5f * (c.dVz[dc][mg_q(c.b, xs[cc], ys[bb], n0)] + c.dVz[dc][mg_q(c.b, xs[cc], ys[bb], n1)]);
-      }
+      for (int cc = 0; cc < 2; ++cc)
+        v += wy[bb] * wx[cc] * ((1.f - t) * c.dVz[dc][cidx(c.b, xs[cc], ys[bb], n0)] +
+                                t * c.dVz[dc][cidx(c.b, xs[cc], ys[bb], min(n0 + 1, ncz))]);
     f.dVz[df][q] += v;
   }
 }

@@ -78,14 +78,15 @@ def test_init_rejects_bad_arguments_before_touching_the_device(lib):
     assert call(w=aligned * 2 + 16) == N.PT_EINVAL                            # workspace alignment
     assert call(wb=ws - 1) == N.PT_ESPACE
     assert lib.pt_step(None, None) == N.PT_EINVAL
-    # multigrid of the correction problem: FP32 only, sizes divisible by 2^(levels - 1), the
-    # coarsest grid at least 2 cells per direction
+    # multigrid of the correction problem: FP32 only; each level ceil(n / 2) cells per direction,
+    # the coarsest at least 2
     assert call(num=N.num_from(dict(p, mg_levels=3))) == N.PT_EINVAL                 # FP64 form
-    assert call(num=N.num_from(dict(p, mg_levels=3, precision=N.PT_FP32)), wb=1) == N.PT_ESPACE  # valid: 8 -> 2
-    assert call(num=N.num_from(dict(p, mg_levels=4, precision=N.PT_FP32))) == N.PT_EINVAL  # 8 -> 1
-    p6 = I.c1_params(6)
-    g6 = N.grid_from(p6)
-    assert call(g=g6, num=N.num_from(dict(p6, mg_levels=3, precision=N.PT_FP32))) == N.PT_EINVAL  # 6 / 4
+    assert call(num=N.num_from(dict(p, mg_levels=3, precision=N.PT_FP32)), wb=1) == N.PT_ESPACE  # 8 -> 4 -> 2
+    assert call(num=N.num_from(dict(p, mg_levels=4, precision=N.PT_FP32))) == N.PT_EINVAL  # 8 -> ... -> 1
+    p7 = I.c1_params(7, 6, 5)
+    g7 = N.grid_from(p7)
+    assert call(g=g7, num=N.num_from(dict(p7, mg_levels=3, precision=N.PT_FP32)), wb=1) == N.PT_ESPACE  # 4, 3, 3 -> 2
+    assert call(g=g7, num=N.num_from(dict(p7, mg_levels=4, precision=N.PT_FP32))) == N.PT_EINVAL   # -> 1
 
 
 def test_multigrid_workspace_adds_the_coarse_grids(lib):
@@ -100,6 +101,12 @@ def test_multigrid_workspace_adds_the_coarse_grids(lib):
         px = -(-(n + 1) // 16) * 16
         return -(-(px * (n + 1) * (n + 1) * 4) // 256) * 256
     assert mg - plain == 2 * fbytes(32) + 25 * (fbytes(16) + fbytes(8))
+    # an odd grid: 33 -> 17 -> 9 cells per direction
+    p = dict(I.c1_params(33), precision=N.PT_FP32)
+    g = N.grid_from(p)
+    plain = lib.pt_workspace_size(C.byref(g), C.byref(N.num_from(p)))
+    mg = lib.pt_workspace_size(C.byref(g), C.byref(N.num_from(dict(p, mg_levels=3))))
+    assert mg - plain == 2 * fbytes(33) + 25 * (fbytes(17) + fbytes(9))
     assert lib.pt_iterate(None, 0, 1, None) == N.PT_EINVAL
     assert lib.pt_strerror(N.PT_ENOTCONV).decode().startswith("PT iteration cap")
 

@@ -1,4 +1,5 @@
-"""Multigrid-accelerated FP32 correction solves (pt_num.mg_levels >= 2): each correction problem
+"""Multigrid-accelerated FP32 correction solves (pt_num.mg_levels >= 2; each grid ceil(n / 2) cells
+per direction of the one above, nested for even n, not nested for odd n): each correction problem
 of the FP32 + FP64 defect-correction step is solved by geometric-multigrid V-cycles smoothed by
 the PT sweep instead of plain PT iterations. The outer FP64 loop, its residuals and its fixed
 point are unchanged, so a converged step must reach the FP64 oracle's converged step within the
@@ -27,7 +28,8 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("dims, levels", [((32, 32, 32), 3), ((32, 24, 40), 4), ((16, 16, 16), 2)])
+@pytest.mark.parametrize("dims, levels", [((32, 32, 32), 3), ((32, 24, 40), 4), ((16, 16, 16), 2),
+                                          ((33, 27, 41), 3), ((31, 31, 31), 4)])
 def test_multigrid_step_reaches_the_oracle_solution(dims, levels):
     PTSolver = _solver()
     p = I.c1_params(*dims)
