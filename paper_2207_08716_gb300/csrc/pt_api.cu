@@ -14,6 +14,7 @@
 #include <new>
 #include <array>
 #include <chrono>
+#include <utility>
 #include <vector>
 
 #include "../../include/porowave_pt.h"
@@ -308,13 +309,92 @@ bool mg_ok(const pt_grid& g, const pt_num& n) {
   return c.nx >= 2 && c.ny >= 2 && c.nz >= 2;
 }
 
-// Workspace of the V-cycle's grids: the finest level's residual outputs, kMgArrays per coarser level.
+// 4-byte words of the transfer tables of one direction (MgAxis) between nf fine and nc coarse cells.
+size_t mg_axis_words(int nf, int nc) { return (size_t)9 * nc + (size_t)6 * nf + 7; }
+
+// The transfer tables of one direction, built from the cell and face positions in FP64 (coarse
+// cell I spans [I r, (I + 1) r] fine cells, coarse face J sits at J r, r = nf / nc); laid out as
+// box_i0[nc], box_w[3 nc], hat_i0[nc + 1], hat_w[4 (nc + 1)], lin_ab[2 nf], lin_w[2 nf],
+// fl_n0[nf + 1], fl_t[nf + 1] (MgAxis).
+std::vector<uint32_t> mg_axis_tables(int nf, int nc) {
+  std::vector<uint32_t> t(mg_axis_words(nf, nc), 0u);
+  const double r = (double)nf / nc, rinv = (double)nc / nf;
+  int32_t* box_i0 = (int32_t*)t.data();
+  float* box_w = (float*)(box_i0 + nc);
+  int32_t* hat_i0 = (int32_t*)(box_w + 3 * nc);
+  float* hat_w = (float*)(hat_i0 + nc + 1);
+  int32_t* lin_ab = (int32_t*)(hat_w + 4 * (nc + 1));
+  float* lin_w = (float*)(lin_ab + 2 * nf);
+  int32_t* fl_n0 = (int32_t*)(lin_w + 2 * nf);
+  float* fl_t = (float*)(fl_n0 + nf + 1);
+  for (int I = 0; I < nc; ++I) {   // covered fractions of fine cells i0, i0 + 1, i0 + 2
+    const double a = I * r, b = (I + 1) * r;
+    const int i0 = (int)std::floor(a);
+    box_i0[I] = i0;
+    for (int k = 0; k < 3; ++k) {
+      const int i = i0 + k;
+      const double lo = std::max(a, (double)i), hi = std::min(b, (double)(i + 1));
+      box_w[3 * I + k] = (i < nf && hi > lo) ? (float)((hi - lo) / r) : 0.f;
+    }
+  }
+  for (int J = 0; J <= nc; ++J) {  // normalised hat of half-width r around face J
+    const double X = J * r;
+    const int i0 = std::max((int)std::floor(X - r) + 1, 0);
+    hat_i0[J] = i0;
+    double w[4], sum = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k;
+      const double v = i <= nf ? 1.0 - std::fabs(i - X) / r : 0.0;
+      w[k] = v > 0.0 ? v : 0.0;
+      sum += w[k];
+    }
+    for (int k = 0; k < 4; ++k) hat_w[4 * J + k] = sum > 0.0 ? (float)(w[k] / sum) : 0.f;
+  }
+  for (int i = 0; i < nf; ++i) {   // fine centre between two coarse centres (held beyond the ends)
+    const double s = (i + 0.5) * rinv - 0.5;
+    int i0 = (int)std::floor(s);
+    double u = s - i0;
+    if (i0 < 0) { i0 = 0; u = 0.0; }
+    if (i0 >= nc - 1) { i0 = nc - 1; u = 0.0; }
+    lin_ab[2 * i] = i0;
+    lin_ab[2 * i + 1] = std::min(i0 + 1, nc - 1);
+    lin_w[2 * i] = (float)(1.0 - u);
+    lin_w[2 * i + 1] = (float)u;
+  }
+  for (int i = 0; i <= nf; ++i) {  // fine face between two coarse faces
+    const double s = i * rinv;
+    int n0 = std::min((int)std::floor(s), nc - 1);
+    fl_n0[i] = n0;
+    fl_t[i] = (float)(s - n0);
+  }
+  return t;
+}
+
+MgAxis mg_axis_at(char* base, int nf, int nc) {
+  MgAxis a;
+  int32_t* box_i0 = (int32_t*)base;
+  float* box_w = (float*)(box_i0 + nc);
+  int32_t* hat_i0 = (int32_t*)(box_w + 3 * nc);
+  float* hat_w = (float*)(hat_i0 + nc + 1);
+  int32_t* lin_ab = (int32_t*)(hat_w + 4 * (nc + 1));
+  float* lin_w = (float*)(lin_ab + 2 * nf);
+  int32_t* fl_n0 = (int32_t*)(lin_w + 2 * nf);
+  float* fl_t = (float*)(fl_n0 + nf + 1);
+  a.box_i0 = box_i0; a.box_w = box_w; a.hat_i0 = hat_i0; a.hat_w = hat_w;
+  a.lin_ab = lin_ab; a.lin_w = lin_w; a.fl_n0 = fl_n0; a.fl_t = fl_t;
+  return a;
+}
+
+// Workspace of the V-cycle's grids: the finest level's residual outputs, kMgArrays per coarser
+// level and its transfer tables.
 size_t mg_bytes(const pt_grid& g, const pt_num& n) {
   if (n.mg_levels < 2 || !mg_ok(g, n)) return 0;
   size_t total = kMgFineArrays * align_up((size_t)make_box(&g).n * sizeof(float), kAlign);
   for (int l = 1; l < n.mg_levels; ++l) {
-    const pt_grid gl = mg_grid(g, l);
+    const pt_grid gl = mg_grid(g, l), gf = mg_grid(g, l - 1);
     total += kMgArrays * align_up((size_t)make_box(&gl).n * sizeof(float), kAlign);
+    total += align_up(mg_axis_words(gf.nx, gl.nx) * 4, kAlign) + align_up(mg_axis_words(gf.ny, gl.ny) * 4, kAlign) +
+             align_up(mg_axis_words(gf.nz, gl.nz) * 4, kAlign);
   }
   return total;
 }
@@ -872,6 +952,7 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
     wend += kMixArrays * fstride;
   }
   c->mg_L = (c->mixed && num->mg_levels >= 2) ? num->mg_levels : 0;
+  std::vector<std::pair<char*, std::vector<uint32_t>>> mg_tables;   // (device address, host copy)
   if (c->mg_L) {
     const size_t fstride = align_up((size_t)c->box.n * sizeof(float), kAlign);
     c->mg.resize(c->mg_L);
@@ -891,17 +972,12 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
     f0.Rx = c->m_Rx; f0.Ry = c->m_Ry; f0.Rz = c->m_Rz;
     f0.res_pt = (float*)wend;
     f0.res_pf = (float*)(wend + fstride);
-    for (int d = 0; d < 3; ++d) f0.r[d] = f0.rinv[d] = 1.0;
     wend += kMgFineArrays * fstride;
     for (int l = 1; l < c->mg_L; ++l) {
       const pt_grid gl = mg_grid(*grid, l), gf = mg_grid(*grid, l - 1);
       MgLevel& L = c->mg[l];
       L.b = make_box(&gl);
       const int nf[3] = {gf.nx, gf.ny, gf.nz}, nc[3] = {gl.nx, gl.ny, gl.nz};
-      for (int d = 0; d < 3; ++d) {   // fine cells per coarse cell: 2, or just under 2 for an odd count
-        L.r[d] = (double)nf[d] / nc[d];
-        L.rinv[d] = (double)nc[d] / nf[d];
-      }
       const size_t st = align_up((size_t)L.b.n * sizeof(float), kAlign);
       float** slots[kMgArrays] = {&L.cc, &L.perm, &L.idtp, &L.mu, &L.dtvc, &L.rpt, &L.rpf, &L.rfx, &L.rfy,
                                   &L.rfz, &L.dVx[0], &L.dVx[1], &L.dVy[0], &L.dVy[1], &L.dVz[0], &L.dVz[1],
@@ -909,6 +985,11 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
                                   &L.res_pt, &L.res_pf};
       for (int a = 0; a < kMgArrays; ++a) *slots[a] = (float*)(wend + a * st);
       wend += kMgArrays * st;
+      for (int d = 0; d < 3; ++d) {   // transfer tables from the finer level, copied in after the memset
+        L.ax[d] = mg_axis_at(wend, nf[d], nc[d]);
+        mg_tables.emplace_back(wend, mg_axis_tables(nf[d], nc[d]));
+        wend += align_up(mg_axis_words(nf[d], nc[d]) * 4, kAlign);
+      }
     }
   }
   c->red = (unsigned long long*)wend;
@@ -928,6 +1009,9 @@ int pt_init(pt_ctx** ctx, const pt_grid* grid, const pt_phys* phys, const pt_num
   fill_coef(c);
   // zero the whole workspace (damped residuals, old stresses, scratch padding)
   cudaError_t e = cudaMemsetAsync(workspace, 0, pt_workspace_size(grid, num), c->stream);
+  for (const auto& tb : mg_tables)   // the host copies live until the synchronisation below
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tb.first, tb.second.data(), tb.second.size() * 4, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && c->dfm && c->logk) {
     PT_LAUNCH(c, K_DF_K0, lean_k0<df64>(grid_dims(c->box), block_dims(), c->stream, c->box, c->phys.k0, c->logk,
                                         D(c->K0)));

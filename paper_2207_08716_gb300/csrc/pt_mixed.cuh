@@ -51,11 +51,27 @@ struct CorrOut {
 
 // One grid of the multigrid hierarchy of the FP32 correction problem (level 0 = the problem's
 // own arrays; coarser levels live in the workspace).
+// Transfer weights between a level and the finer one above it along one direction (n fine cells,
+// nc = ceil(n / 2) coarse cells; built on the host from the cell and face positions, in the
+// workspace): the coarse cell I covers fine cells box_i0[I] + 0..2 with weights box_w[3 I + t]
+// (the covered fractions); the coarse face J gathers fine faces hat_i0[J] + 0..3 with weights
+// hat_w[4 J + t] (a hat of half-width n / nc, normalised); fine cell i interpolates coarse cells
+// lin_ab[2 i], lin_ab[2 i + 1] with weights lin_w[2 i], lin_w[2 i + 1]; fine face i interpolates
+// coarse faces fl_n0[i], fl_n0[i] + 1 with weights 1 - fl_t[i], fl_t[i].
+struct MgAxis {
+  const int* box_i0;
+  const float* box_w;
+  const int* hat_i0;
+  const float* hat_w;
+  const int* lin_ab;
+  const float* lin_w;
+  const int* fl_n0;
+  const float* fl_t;
+};
+
 struct MgLevel {
   Box b;
-  double r[3];                                     // fine cells per cell of this level (x, y, z), 1 < r <= 2;
-                                                   // 2 when the finer grid has an even count
-  double rinv[3];                                  // 1 / r (positions in FP64: weights exact to FP32)
+  MgAxis ax[3];                                    // transfers from the finer level (x, y, z)
   float *cc, *perm, *idtp, *mu, *dtvc;             // frozen coefficients
   float *rpt, *rpf, *rfx, *rfy, *rfz;              // right-hand sides
   float *dVx[2], *dVy[2], *dVz[2], *dPt[2], *dPf[2];

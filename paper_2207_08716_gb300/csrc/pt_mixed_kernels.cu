@@ -474,66 +474,16 @@ void corr_iteration(cudaStream_t s, Box b, const CorrCoef<float>& c, const CorrI
 
 
 // ============================================================ multigrid transfers (FP32)
-// Level f (fine, n cells per direction) and level c (coarse, ceil(n / 2)): in fine-cell units a
-// coarse cell I spans [I r, (I + 1) r] and a coarse face J sits at J r (r = c.r[d]).
-namespace {
-
-// Box weights of coarse cell I along one direction: the fractions of fine cells i0, i0 + 1,
-// i0 + 2 it covers (at most three for r <= 2), over r; they sum to 1.
-__device__ __forceinline__ void mg_box(int I, double r, int nf, int& i0, float w[3]) {
-  const double a = I * r, b = (I + 1) * r;
-  i0 = (int)floor(a);
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    const int i = i0 + t;
-    const double lo = fmax(a, (double)i), hi = fmin(b, (double)(i + 1));
-    w[t] = (i < nf && hi > lo) ? (float)((hi - lo) / r) : 0.f;
-  }
-}
-
-// Linear interpolation between coarse centres for fine cell i: coarse cells (a, b) with weights
-// (wa, wb); beyond the first and last centre the nearest centre's value (zero gradient).
-__device__ __forceinline__ void mg_lin(int i, double rinv, int nc, int& a, int& b, float& wa, float& wb) {
-  const double s = (i + 0.5) * rinv - 0.5;
-  const double fl = floor(s);
-  int i0 = (int)fl;
-  float t = (float)(s - fl);
-  if (i0 < 0) { i0 = 0; t = 0.f; }
-  if (i0 >= nc - 1) { i0 = nc - 1; t = 0.f; }
-  a = i0;
-  b = min(i0 + 1, nc - 1);
-  wa = 1.f - t;
-  wb = t;
-}
-
-// Hat weights of coarse face J over the fine faces within r of it (at most four), normalised.
-__device__ __forceinline__ int mg_hat(int J, double r, int nf, int& i0, float w[4]) {
-  const double X = J * r;
-  i0 = max((int)floor(X - r) + 1, 0);
-  float sum = 0.f;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int i = i0 + t;
-    const double v = (i <= nf) ? 1.0 - fabs((double)i - X) / r : 0.0;
-    w[t] = v > 0.0 ? (float)v : 0.f;
-    sum += w[t];
-  }
-#pragma unroll
-  for (int t = 0; t < 4; ++t) w[t] /= sum;
-  return 4;
-}
-
-}  // namespace
-
+// Level f (fine, n cells per direction) and level c (coarse, ceil(n / 2)), through the weight
+// tables of c.ax (MgAxis).
 __global__ void __launch_bounds__(256) k_mg_coef(MgLevel f, MgLevel c, float dtaupt_fac, float dtauv_fac) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z;
   if (I >= c.b.nx || J >= c.b.ny || K >= c.b.nz) return;
-  int i0, j0, k0;
-  float wx[3], wy[3], wz[3];
-  mg_box(I, c.r[0], f.b.nx, i0, wx);
-  mg_box(J, c.r[1], f.b.ny, j0, wy);
-  mg_box(K, c.r[2], f.b.nz, k0, wz);
+  const int i0 = c.ax[0].box_i0[I], j0 = c.ax[1].box_i0[J], k0 = c.ax[2].box_i0[K];
+  const float* wx = c.ax[0].box_w + 3 * I;
+  const float* wy = c.ax[1].box_w + 3 * J;
+  const float* wz = c.ax[2].box_w + 3 * K;
   float m = 0.f, k = 0.f, cc = 0.f;
   for (int dz = 0; dz < 3; ++dz)
     for (int dy = 0; dy < 3; ++dy)
@@ -564,12 +514,10 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgLevel f, MgLevel c, float
   c.dVz[0][qc] = 0.f; c.dVz[1][qc] = 0.f; c.dPt[0][qc] = 0.f; c.dPf[0][qc] = 0.f;
   c.Rx[qc] = 0.f; c.Ry[qc] = 0.f; c.Rz[qc] = 0.f;
   const Box& F = f.b;
-  int i0, j0, k0;
-  float bx[3], by[3], bz[3], h[4];
+  const MgAxis &X = c.ax[0], &Y = c.ax[1], &Z = c.ax[2];
   if (I < B.nx && J < B.ny && K < B.nz) {
-    mg_box(I, c.r[0], F.nx, i0, bx);
-    mg_box(J, c.r[1], F.ny, j0, by);
-    mg_box(K, c.r[2], F.nz, k0, bz);
+    const int i0 = X.box_i0[I], j0 = Y.box_i0[J], k0 = Z.box_i0[K];
+    const float *bx = X.box_w + 3 * I, *by = Y.box_w + 3 * J, *bz = Z.box_w + 3 * K;
     float a = 0.f, b = 0.f;
     for (int dz = 0; dz < 3; ++dz)
       for (int dy = 0; dy < 3; ++dy)
@@ -585,9 +533,8 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgLevel f, MgLevel c, float
   }
   // faces: hat weights along the normal, box weights across it
   if (I > 0 && I < B.nx && J < B.ny && K < B.nz) {
-    mg_hat(I, c.r[0], F.nx, i0, h);
-    mg_box(J, c.r[1], F.ny, j0, by);
-    mg_box(K, c.r[2], F.nz, k0, bz);
+    const int i0 = X.hat_i0[I], j0 = Y.box_i0[J], k0 = Z.box_i0[K];
+    const float *h = X.hat_w + 4 * I, *by = Y.box_w + 3 * J, *bz = Z.box_w + 3 * K;
     float s = 0.f;
     for (int dz = 0; dz < 3; ++dz)
       for (int dy = 0; dy < 3; ++dy)
@@ -599,9 +546,8 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgLevel f, MgLevel c, float
     c.rfx[qc] = rho_i * s;
   }
   if (J > 0 && J < B.ny && I < B.nx && K < B.nz) {
-    mg_box(I, c.r[0], F.nx, i0, bx);
-    mg_hat(J, c.r[1], F.ny, j0, h);
-    mg_box(K, c.r[2], F.nz, k0, bz);
+    const int i0 = X.box_i0[I], j0 = Y.hat_i0[J], k0 = Z.box_i0[K];
+    const float *bx = X.box_w + 3 * I, *h = Y.hat_w + 4 * J, *bz = Z.box_w + 3 * K;
     float s = 0.f;
     for (int dz = 0; dz < 3; ++dz)
       for (int dy = 0; dy < 4; ++dy)
@@ -613,9 +559,8 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgLevel f, MgLevel c, float
     c.rfy[qc] = rho_i * s;
   }
   if (K > 0 && K < B.nz && I < B.nx && J < B.ny) {
-    mg_box(I, c.r[0], F.nx, i0, bx);
-    mg_box(J, c.r[1], F.ny, j0, by);
-    mg_hat(K, c.r[2], F.nz, k0, h);
+    const int i0 = X.box_i0[I], j0 = Y.box_i0[J], k0 = Z.hat_i0[K];
+    const float *bx = X.box_w + 3 * I, *by = Y.box_w + 3 * J, *h = Z.hat_w + 4 * K;
     float s = 0.f;
     for (int dz = 0; dz < 4; ++dz)
       for (int dy = 0; dy < 3; ++dy)
@@ -634,72 +579,56 @@ __global__ void __launch_bounds__(256) k_mg_prolong(MgLevel c, int dc, MgLevel f
   const Box& B = f.b;
   if (i > B.nx || j > B.ny || k > B.nz) return;
   const long long q = cidx(B, i, j, k);
-  const int ncx = c.b.nx, ncy = c.b.ny, ncz = c.b.nz;
-  int xa, xb, ya, yb, za, zb;
-  float wxa, wxb, wya, wyb, wza, wzb;
+  const MgAxis &X = c.ax[0], &Y = c.ax[1], &Z = c.ax[2];
   if (i < B.nx && j < B.ny && k < B.nz) {   // cells: trilinear between coarse centres
-    mg_lin(i, c.rinv[0], ncx, xa, xb, wxa, wxb);
-    mg_lin(j, c.rinv[1], ncy, ya, yb, wya, wyb);
-    mg_lin(k, c.rinv[2], ncz, za, zb, wza, wzb);
-    const int xs[2] = {xa, xb}, ys[2] = {ya, yb}, zs[2] = {za, zb};
-    const float wx[2] = {wxa, wxb}, wy[2] = {wya, wyb}, wz[2] = {wza, wzb};
     float pt = 0.f, pf = 0.f;
     for (int a = 0; a < 2; ++a)
       for (int bb = 0; bb < 2; ++bb)
         for (int cc = 0; cc < 2; ++cc) {
-          const float w = wz[a] * wy[bb] * wx[cc];
-          const long long qc = cidx(c.b, xs[cc], ys[bb], zs[a]);
+          const float w = Z.lin_w[2 * k + a] * Y.lin_w[2 * j + bb] * X.lin_w[2 * i + cc];
+          const long long qc = cidx(c.b, X.lin_ab[2 * i + cc], Y.lin_ab[2 * j + bb], Z.lin_ab[2 * k + a]);
           pt += w * c.dPt[dc][qc];
           pf += w * c.dPf[dc][qc];
         }
     f.dPt[df][q] += pt;
     f.dPf[df][q] += pf;
   }
-  // faces: linear between coarse faces along the normal (s = i / r; coarse wall faces are zero),
-  // between coarse centres across it
+  // faces: linear between coarse faces along the normal (coarse wall faces are zero), between
+  // coarse centres across it
   if (i > 0 && i < B.nx && j < B.ny && k < B.nz) {
-    const double s = i * c.rinv[0];
-    const int n0 = (int)floor(s);
-    const float t = (float)(s - n0);
-    mg_lin(j, c.rinv[1], ncy, ya, yb, wya, wyb);
-    mg_lin(k, c.rinv[2], ncz, za, zb, wza, wzb);
-    const int ys[2] = {ya, yb}, zs[2] = {za, zb};
-    const float wy[2] = {wya, wyb}, wz[2] = {wza, wzb};
+    const int n0 = X.fl_n0[i];
+    const float t = X.fl_t[i];
     float v = 0.f;
     for (int a = 0; a < 2; ++a)
-      for (int bb = 0; bb < 2; ++bb)
-        v += wz[a] * wy[bb] * ((1.f - t) * c.dVx[dc][cidx(c.b, n0, ys[bb], zs[a])] +
-                               t * c.dVx[dc][cidx(c.b, min(n0 + 1, ncx), ys[bb], zs[a])]);
+      for (int bb = 0; bb < 2; ++bb) {
+        const int y = Y.lin_ab[2 * j + bb], z = Z.lin_ab[2 * k + a];
+        v += Z.lin_w[2 * k + a] * Y.lin_w[2 * j + bb] *
+             ((1.f - t) * c.dVx[dc][cidx(c.b, n0, y, z)] + t * c.dVx[dc][cidx(c.b, n0 + 1, y, z)]);
+      }
     f.dVx[df][q] += v;
   }
   if (j > 0 && j < B.ny && i < B.nx && k < B.nz) {
-    const double s = j * c.rinv[1];
-    const int n0 = (int)floor(s);
-    const float t = (float)(s - n0);
-    mg_lin(i, c.rinv[0], ncx, xa, xb, wxa, wxb);
-    mg_lin(k, c.rinv[2], ncz, za, zb, wza, wzb);
-    const int xs[2] = {xa, xb}, zs[2] = {za, zb};
-    const float wx[2] = {wxa, wxb}, wz[2] = {wza, wzb};
+    const int n0 = Y.fl_n0[j];
+    const float t = Y.fl_t[j];
     float v = 0.f;
     for (int a = 0; a < 2; ++a)
-      for (int cc = 0; cc < 2; ++cc)
-        v += wz[a] * wx[cc] * ((1.f - t) * c.dVy[dc][cidx(c.b, xs[cc], n0, zs[a])] +
-                               t * c.dVy[dc][cidx(c.b, xs[cc], min(n0 + 1, ncy), zs[a])]);
+      for (int cc = 0; cc < 2; ++cc) {
+        const int x = X.lin_ab[2 * i + cc], z = Z.lin_ab[2 * k + a];
+        v += Z.lin_w[2 * k + a] * X.lin_w[2 * i + cc] *
+             ((1.f - t) * c.dVy[dc][cidx(c.b, x, n0, z)] + t * c.dVy[dc][cidx(c.b, x, n0 + 1, z)]);
+      }
     f.dVy[df][q] += v;
   }
   if (k > 0 && k < B.nz && i < B.nx && j < B.ny) {
-    const double s = k * c.rinv[2];
-    const int n0 = (int)floor(s);
-    const float t = (float)(s - n0);
-    mg_lin(i, c.rinv[0], ncx, xa, xb, wxa, wxb);
-    mg_lin(j, c.rinv[1], ncy, ya, yb, wya, wyb);
-    const int xs[2] = {xa, xb}, ys[2] = {ya, yb};
-    const float wx[2] = {wxa, wxb}, wy[2] = {wya, wyb};
+    const int n0 = Z.fl_n0[k];
+    const float t = Z.fl_t[k];
     float v = 0.f;
     for (int bb = 0; bb < 2; ++bb)
-      for (int cc = 0; cc < 2; ++cc)
-        v += wy[bb] * wx[cc] * ((1.f - t) * c.dVz[dc][cidx(c.b, xs[cc], ys[bb], n0)] +
-                                t * c.dVz[dc][cidx(c.b, xs[cc], ys[bb], min(n0 + 1, ncz))]);
+      for (int cc = 0; cc < 2; ++cc) {
+        const int x = X.lin_ab[2 * i + cc], y = Y.lin_ab[2 * j + bb];
+        v += Y.lin_w[2 * j + bb] * X.lin_w[2 * i + cc] *
+             ((1.f - t) * c.dVz[dc][cidx(c.b, x, y, n0)] + t * c.dVz[dc][cidx(c.b, x, y, n0 + 1)]);
+      }
     f.dVz[df][q] += v;
   }
 }

@@ -100,13 +100,16 @@ def test_multigrid_workspace_adds_the_coarse_grids(lib):
     def fbytes(n):   # one FP32 array of an n^3 grid's padded box, 256-byte aligned
         px = -(-(n + 1) // 16) * 16
         return -(-(px * (n + 1) * (n + 1) * 4) // 256) * 256
-    assert mg - plain == 2 * fbytes(32) + 25 * (fbytes(16) + fbytes(8))
+
+    def tables(nf, nc):   # the transfer tables of 3 directions (9 nc + 6 nf + 7 words each)
+        return 3 * (-(-((9 * nc + 6 * nf + 7) * 4) // 256) * 256)
+    assert mg - plain == 2 * fbytes(32) + 25 * (fbytes(16) + fbytes(8)) + tables(32, 16) + tables(16, 8)
     # an odd grid: 33 -> 17 -> 9 cells per direction
     p = dict(I.c1_params(33), precision=N.PT_FP32)
     g = N.grid_from(p)
     plain = lib.pt_workspace_size(C.byref(g), C.byref(N.num_from(p)))
     mg = lib.pt_workspace_size(C.byref(g), C.byref(N.num_from(dict(p, mg_levels=3))))
-    assert mg - plain == 2 * fbytes(33) + 25 * (fbytes(17) + fbytes(9))
+    assert mg - plain == 2 * fbytes(33) + 25 * (fbytes(17) + fbytes(9)) + tables(33, 17) + tables(17, 9)
     assert lib.pt_iterate(None, 0, 1, None) == N.PT_EINVAL
     assert lib.pt_strerror(N.PT_ENOTCONV).decode().startswith("PT iteration cap")
 
