@@ -136,9 +136,11 @@ def parse():
     ap.add_argument("--precision", choices=tuple(PRECISIONS), default="df64",
                     help="df64: the FP64-lean iteration in double-float arithmetic (FP64 oracle parity 1e-10); "
                          "fp64: FP64-lean kernels; fp64-stepwise: one kernel per step; fp32: FP32 PT")
-    ap.add_argument("--forms", default="fp64,fp32,batched,batched32", help="extra forms measured after the headline one "
-                    "(comma list of fp64, df64, fp32, fp64-stepwise, batched (FP64 ensemble), batched32 (FP32 "
-                    "ensemble); '' for none)")
+    ap.add_argument("--forms", default="fp64,fp32,batched,batched32,fp32mg",
+                    help="extra forms measured after the headline one (comma list of fp64, df64, fp32, "
+                         "fp64-stepwise, batched (FP64 ensemble), batched32 (FP32 ensemble), fp32mg (one converged "
+                         "step of the FP32 form with multigrid correction solves); '' for none)")
+    ap.add_argument("--mg-form-levels", type=int, default=6, help="grids of the fp32mg form's V-cycles")
     ap.add_argument("--no-own-peaks", action="store_true",
                     help="skip the library's own copy / FP64 / FP32 peak measurements")
     ap.add_argument("--fp32-iters", type=int, default=300, help="FP32 iterations per step of the fp32 form")
@@ -557,6 +559,42 @@ def measure_batched(args, steps: int, warmup: int, dev, world: int, rank: int, c
                    converged=sum(1 for r in reps if r["status"] == 0))
     b.close()
     del b
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_mg_step(args, dev, rank: int) -> dict:
+    """The FP32 form with multigrid correction solves (`--mg-form-levels` grids) on the benchmark
+    workload: one converged physical step (tol 1e-8) after one untimed converged step, timed with
+    CUDA events on the solver's stream; the step's iteration count is in finest-grid sweeps."""
+    import torch
+    from paper_2207_08716_gb300.solver import PTSolver
+
+    n = args.n
+    p = workload_params(n, 400000, "fp32", args.workload)
+    p["tol"] = I.large_params(n)["tol"]
+    p["mg_levels"] = args.mg_form_levels
+    phi = workload_phi(p, M.replica_seed(rank), args.workload)
+    stream = torch.cuda.current_stream(dev)
+    s = PTSolver(p, phi, device=dev, stream=stream)
+    del phi
+    warm = s.step()
+    torch.cuda.synchronize(dev)
+    clocks = M.ClockSampler(dev.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = s.launch_count()
+    e0.record(stream)
+    rep = s.step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    out = {"value": e0.elapsed_time(e1) / 1e3, "unit": "s per converged step", "higher_is_better": False,
+           "mg_levels": args.mg_form_levels, "fine_sweeps": rep["iters"], "status": rep["status"],
+           "warmup_step_fine_sweeps": warm["iters"], "gpu_launches": s.launch_count() - l0, "clocks": clk,
+           "definition": f"{n}^3 c1-parameter step to tol {p['tol']:g} (FP32 correction solves by V-cycles, "
+                         "FP64 outer loop); the double-float form needs ~37,700 PT iterations for such a step"}
+    s.close()
     torch.cuda.empty_cache()
     return out
 
@@ -992,6 +1030,8 @@ def run_native(args):
     for f in [x for x in args.forms.split(",") if x and x != args.precision]:
         if f in ("batched", "batched32"):
             forms[f] = measure_batched(args, max(2, args.steps // 2), 1, dev, world, rank, fp32=f == "batched32")
+        elif f == "fp32mg":
+            forms[f] = measure_mg_step(args, dev, rank)
         elif f in PRECISIONS:
             it = args.fp32_iters if f == "fp32" else args.iters
             forms[f] = measure_form(args, f, it, max(2, args.steps // 2), 2, 0, dev, world, rank, local_rank,
@@ -1019,7 +1059,8 @@ def run_native(args):
             "clocks": head["clocks"], "kernels": head["kernels"], "own_peaks": own,
             "forms": {k: ({kk: v[kk] for kk in ("value", "unit", "p_bytes", "it_per_s", "t_it_ms",
                                                   "teff_frac_of_hbm", "iters_per_step", "roofline",
-                                                  "gpu_launches", "clocks")} if not k.startswith("batched") else v)
+                                                  "gpu_launches", "clocks")}
+                          if not (k.startswith("batched") or k == "fp32mg") else v)
                       for k, v in forms.items()},
         }
         print(json.dumps(line), flush=True)

@@ -82,11 +82,12 @@ def test_double_float_cells_report_hbm_with_their_own_bytes():
     assert abs(r["frac_of_own_copy"] - gbs / 6900.0) < 1e-12
 
 
-def test_fp32_correction_reports_ncu_traffic_while_current():
+def test_fp32_correction_reports_ncu_traffic_while_current(monkeypatch):
+    _with_profile(monkeypatch, "k_corr_iteration", traffic=106.6, thread_inst=720.8)
     n = 511 ** 3
     r = bench.roofline({"k_corr_iteration": (300, 300 * 4.85)}, n)
     assert r["ncu_figures"] == "current" and r["traffic"] is not None
-    assert abs(r["traffic"] - bench.PROFILED["k_corr_iteration"]["traffic"] * n) < 1e-6 * r["traffic"]
+    assert abs(r["traffic"] - 106.6 * n) < 1e-6 * r["traffic"]
 
 
 def test_precision_check_size_list():
