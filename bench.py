@@ -225,6 +225,16 @@ def workload_name(n: int, iters: int, precision: str = "fp64", workload: str = "
             f"centred Gaussian anomaly, {iters} PT iterations per physical step")
 
 
+def native_config(args, iters: int, world: int) -> dict:
+    """The benchmark's `config` (the same for the native arm and the reference arm, which times
+    the oracle on a bounded sample of this workload, described in its cpu_baseline)."""
+    return {"workload": workload_name(args.n, iters, args.precision, args.workload),
+            "n": args.n, "iters_per_step": iters, "precision": args.precision,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (every field >= 0.5 GB), no flush",
+            "seeds": "value = median over the anomaly seeds run (N = 1) or seed = rank"}
+
+
 # ------------------------------------------------------------------------ CPU (oracle) leg
 def cpu_sample(n_sub: int, iters: int) -> dict:
     """Oracle (as it stands) on a bounded sample of the benchmark workload: an n_sub^3 block of
@@ -325,9 +335,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(511, args.iters) +
-                                        f" (CPU oracle: bounded {args.cpu_n}^3 sample)",
-                                        "n": 511, "parallelism": "replicas"},
+        "data": "synthetic", "config": native_config(args, args.iters, world),
         "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "GB/s"},
         "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1047,11 +1055,7 @@ def run_native(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic",
-            "config": {"workload": workload_name(args.n, head["iters_per_step"], args.precision, args.workload),
-                       "n": args.n, "iters_per_step": head["iters_per_step"], "precision": args.precision,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (every field >= 0.5 GB), no flush",
-                       "seeds": "value = median over the anomaly seeds run (N = 1) or seed = rank"},
+            "config": native_config(args, head["iters_per_step"], world),
             "it_per_s": head["it_per_s"], "t_it_ms": head["t_it_ms"],
             "seeds": {str(r["seed"]): r["value"] for r in runs}, "median_seed": head["seed"],
             "teff_frac_of_hbm": head["teff_frac_of_hbm"], "roofline": head["roofline"],
