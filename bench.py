@@ -170,8 +170,8 @@ def parse():
     ap.add_argument("--mg-plain-steps", type=int, default=2,
                     help="timed converged steps of the plain PT solver (after one warm-up step)")
     ap.add_argument("--batch-precision", choices=("fp64", "fp32"), default="fp64",
-                    help="precision of the batched ensemble (fp32: defect-correction solvers stepped "
-                         "concurrently, each on its own stream)")
+                    help="precision of the batched ensemble (fp32: the defect-correction form in the "
+                         "persistent FP32 engine)")
     ap.add_argument("--precision-check", action="store_true",
                     help="porosity of the FP32 form against an FP64-class form (and the oracle at the "
                          "--pc-oracle-n sizes) after converged physical steps of the c1 workload at each --pc-n")
