@@ -132,7 +132,7 @@ enum KernelId { K_PERM, K_CENTRES, K_EDGES, K_POROSITY, K_FACES, K_PICARD, K_BEG
                 K_LEAN_K0, K_MIX_PREP, K_MIX_FACES, K_MIX_COEF, K_CORR_ITER,
                 K_MIX_UPDATE, K_ADJ_PREP, K_ADJ_CELLS, K_ADJ_FACES, K_ADJ_CARRY, K_DF_CELLS, K_DF_FACES,
                 K_DF_PICARD, K_DF_COEF, K_DF_BEGIN, K_DF_K0, K_DF_CONVERT, K_ADJ_EDGES_PL, K_ADJ_CELLS_PL,
-                K_ADJ_FACES_PL, K_MG_FINE, K_MG_COARSE, K_MG_TRANSFER, K_COUNT };
+                K_ADJ_FACES_PL, K_MG_FINE, K_MG_COARSE, K_MG_TRANSFER, K_MIX_EDGES, K_MIX_POROSITY, K_COUNT };
 const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_porosity", "k_faces",
                                            "k_picard", "k_begin_step", "k_init_visc",
                                            "k_residual_faces", "k_lean_cells", "k_lean_faces",
@@ -144,7 +144,8 @@ const char* const kKernelNames[K_COUNT] = {"k_perm", "k_centres", "k_edges", "k_
                                            "k_lean_coef_df64", "k_lean_begin_df64", "k_lean_k0_df64",
                                            "k_df64_convert", "k_adj_edges_pl", "k_adj_cells_pl",
                                            "k_adj_faces_pl", "k_corr_iteration_mg_fine",
-                                           "k_corr_iteration_mg_coarse", "k_mg_transfer"};
+                                           "k_corr_iteration_mg_coarse", "k_mg_transfer", "k_mix_edges",
+                                           "k_mix_porosity"};
 
 cudaEvent_t pooled_event(pt_ctx* c) {
   if (c->pool_used == c->pool.size()) {
@@ -691,7 +692,7 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   PT_LAUNCH(c, K_MIX_PREP, mix_prepare(gr, bl, c->stream, b, k, pin, pout, c->red));
   EdgeIn ei{c->Vx, c->Vy, c->Vz, c->mu, c->txyo, c->txzo, c->tyzo};
   EdgeOut eo{c->s_txy, c->s_txz, c->s_tyz};
-  PT_LAUNCH(c, K_EDGES, k_edges<<<gr, bl, 0, c->stream>>>(b, k, ei, eo));
+  PT_LAUNCH(c, K_MIX_EDGES, mix_edges(gr, bl, c->stream, b, k, ei, eo));
   MixFaceIn fin{c->s_txx, c->s_tyy, c->s_tzz, c->s_txy, c->s_txz, c->s_tyz, c->Pt[a], c->phi[a]};
   PT_LAUNCH(c, K_MIX_FACES, mix_res_faces(gr, bl, c->stream, b, k, fin, c->m_rfx, c->m_rfy, c->m_rfz, c->red));
   // (ii) Picard update of mu, eta from the stresses at u
@@ -770,9 +771,10 @@ int mixed_outer(pt_ctx* c, int n_in, bool early_exit, pt_report* outer, bool* co
   MixUpdate mu{c->Vx, c->Vy, c->Vz, c->Pt[a], c->Pf[a], c->m_dVx[d], c->m_dVy[d], c->m_dVz[d], c->m_dPt[d], c->m_dPf[d],
                c->mix_omega};
   PT_LAUNCH(c, K_MIX_UPDATE, mix_update(gr, bl, c->stream, b, mu));
-  PT_LAUNCH(c, K_POROSITY,
-            k_porosity<<<gr, bl, 0, c->stream>>>(b, k, c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[a], c->Pf[a],
-                                                  c->Pto, c->Pfo, c->Lo, c->eta, c->phi[1 - a]));
+  PT_LAUNCH(c, K_MIX_POROSITY,
+            mix_porosity(gr, bl, c->stream, b, k,
+                         MixPorosity{c->Vx, c->Vy, c->Vz, c->phi[a], c->Pt[a], c->Pf[a], c->Pto, c->Pfo, c->Lo,
+                                     c->eta, c->phi[1 - a]}));
   // Pt, Pf stay in buffer a; phi moves to 1 - a: copy the pressures along so cur stays paired
   cudaMemcpyAsync(c->Pt[1 - a], c->Pt[a], (size_t)b.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->Pf[1 - a], c->Pf[a], (size_t)b.n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);

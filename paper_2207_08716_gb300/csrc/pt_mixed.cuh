@@ -3,6 +3,7 @@
 #pragma once
 
 #include "pt_lean.cuh"
+#include "pt_kernels.cuh"
 
 namespace pt {
 
@@ -19,6 +20,10 @@ struct MixFaceIn {
 struct MixCoefOut {
   float *mu;                                                // mu at centres (FP32)
   float *dtvc;                                              // velocity pseudo-step fac / mu at centres
+};
+struct MixPorosity {       // the porosity integration of Eq. 22 at the corrected state
+  const double *Vx, *Vy, *Vz, *phi, *Pt1, *Pf1, *Pto, *Pfo, *Lo, *eta;
+  double* phi1;
 };
 struct MixUpdate {
   double *Vx, *Vy, *Vz, *Pt, *Pf;
@@ -84,6 +89,8 @@ void mix_prepare(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const Mi
 void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixFaceIn& in, float* rfx,
                    float* rfy, float* rfz, unsigned long long* red);
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out);
+void mix_edges(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const EdgeIn& in, const EdgeOut& out);
+void mix_porosity(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPorosity& p);
 void mix_update(dim3 g, dim3 bl, cudaStream_t s, Box b, const MixUpdate& u);
 // One fused FP32 correction iteration over the whole grid (z-marching tiles, see the kernel).
 void corr_iteration(cudaStream_t s, Box b, const CorrCoef<float>& c, const CorrIn<float>& in,

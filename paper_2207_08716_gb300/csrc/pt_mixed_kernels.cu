@@ -41,7 +41,8 @@ __device__ __forceinline__ void mix_prepare_point(const Box& b, const Coef& c, c
     const double ph = in.phi[q], mu = in.mu[q];
     const double divV = (in.Vx[q + 1] - in.Vx[q]) * c.rdx + (in.Vy[q + px] - in.Vy[q]) * c.rdy +
                         (in.Vz[q + pxy] - in.Vz[q]) * c.rdz;
-    const double cc = c.compaction_on ? 1.0 / (in.eta[q] * (1.0 - ph)) : 0.0;
+    // reciprocals by the two-step Newton iteration (within an ulp; these phases run on the FP64 pipe)
+    const double cc = c.compaction_on ? lean_detail::rcp_full(in.eta[q] * (1.0 - ph)) : 0.0;
     const double divVn = divV + c.beta_d * ((Pt - Pto) - c.alpha * (Pf - Pfo)) * c.rdt + (Pt - Pf) * cc;
     const double kc = in.perm[q];
     const double buoy = c.rhof_g - c.rho_bg_g;
@@ -80,7 +81,7 @@ __device__ __forceinline__ void mix_prepare_point(const Box& b, const Coef& c, c
     const double rpf = divqD + c.beta_d * c.alpha * ((Pf - Pfo) / c.B - (Pt - Pto)) * c.rdt + (Pf - Pt) * cc;
     // stresses at u (Eq. 21) for the momentum residual and the Picard update
     const double xi = mu * c.rGdtS;
-    const double s = 1.0 / (1.0 + xi);
+    const double s = lean_detail::rcp_full(1.0 + xi);
     const double bn = c.beta_n * divVn;
     out.txx[q] = (in.txxo[q] * xi + 2.0 * mu * ((in.Vx[q + 1] - in.Vx[q]) * c.rdx - divV / 3.0 + bn)) * s;
     out.tyy[q] = (in.tyyo[q] * xi + 2.0 * mu * ((in.Vy[q + px] - in.Vy[q]) * c.rdy - divV / 3.0 + bn)) * s;
@@ -92,10 +93,24 @@ __device__ __forceinline__ void mix_prepare_point(const Box& b, const Coef& c, c
     out.r_pf[q] = (float)rpf;
     out.cc[q] = (float)cc;
     out.perm[q] = (float)kc;
-    out.idtp[q] = (float)(1.0 / (c.dtaupt_fac * mu));
+    out.idtp[q] = (float)lean_detail::rcp_full(c.dtaupt_fac * mu);
     r_pt = fabs(divVn);
     r_pf = fabs(rpf);
   }
+}
+
+// The edge stresses and the porosity integration of the FP32 form's outer phases (the shared
+// bodies with Newton reciprocals).
+__global__ void __launch_bounds__(256) k_mix_edges(Box b, Coef c, EdgeIn in, EdgeOut out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  edges_point<true>(b, c, in, out, i, j, (int)blockIdx.z);
+}
+__global__ void __launch_bounds__(256) k_mix_porosity(Box b, Coef c, MixPorosity p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  porosity_point<true>(b, c, p.Vx, p.Vy, p.Vz, p.phi, p.Pt1, p.Pf1, p.Pto, p.Pfo, p.Lo, p.eta, p.phi1, i, j,
+                       (int)blockIdx.z);
 }
 
 __global__ void __launch_bounds__(256) k_mix_prepare(Box b, Coef c, MixPrepIn in, MixPrepOut out,
@@ -458,6 +473,12 @@ void mix_res_faces(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const 
                    float* rfy, float* rfz, unsigned long long* red) {
   k_mix_res_faces<<<g, bl, 0, s>>>(b, c, in, rfx, rfy, rfz, red);
 }
+void mix_edges(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const EdgeIn& in, const EdgeOut& out) {
+  k_mix_edges<<<g, bl, 0, s>>>(b, c, in, out);
+}
+void mix_porosity(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const MixPorosity& p) {
+  k_mix_porosity<<<g, bl, 0, s>>>(b, c, p);
+}
 void mix_coef(dim3 g, dim3 bl, cudaStream_t s, Box b, const Coef& c, const double* mu, const MixCoefOut& out) {
   k_mix_coef<<<g, bl, 0, s>>>(b, c, mu, out);
 }
@@ -716,8 +737,8 @@ __global__ void __launch_bounds__(kMbBX * kMbBY) k_mb_points(const MixBatchInst*
       const MixPrepOut pout{I.s_txx, I.s_tyy, I.s_tzz, I.rpt, I.rpf, I.ccf, I.kf, I.idtp};
       double r_pt = 0.0, r_pf = 0.0;
       mix_prepare_point(b, I.k, pin, pout, i, j, kz, r_pt, r_pf);
-      edges_point(b, I.k, EdgeIn{I.Vx, I.Vy, I.Vz, I.mu, I.txyo, I.txzo, I.tyzo},
-                  EdgeOut{I.s_txy, I.s_txz, I.s_tyz}, i, j, kz);
+      edges_point<true>(b, I.k, EdgeIn{I.Vx, I.Vy, I.Vz, I.mu, I.txyo, I.txzo, I.tyzo},
+                        EdgeOut{I.s_txy, I.s_txz, I.s_tyz}, i, j, kz);
       block_max_atomic(r_pt, I.red + RED_PT);
       block_max_atomic(r_pf, I.red + RED_PF);
     } else if (PHASE == MB_PH_FACES) {
@@ -743,8 +764,8 @@ __global__ void __launch_bounds__(kMbBX * kMbBY) k_mb_points(const MixBatchInst*
       mix_update_point(b, MixUpdate{I.Vx, I.Vy, I.Vz, I.Pt[a], I.Pf[a], I.dVx[d], I.dVy[d], I.dVz[d], I.dPt[d],
                                     I.dPf[d], S.omega}, i, j, kz);
     } else {   // MB_PH_POROSITY: phi moves to the other buffer, the pressures follow it
-      porosity_point(b, I.k, I.Vx, I.Vy, I.Vz, I.phi[a], I.Pt[a], I.Pf[a], I.Pto, I.Pfo, I.Lo, I.eta,
-                     I.phi[1 - a], i, j, kz);
+      porosity_point<true>(b, I.k, I.Vx, I.Vy, I.Vz, I.phi[a], I.Pt[a], I.Pf[a], I.Pto, I.Pfo, I.Lo, I.eta,
+                           I.phi[1 - a], i, j, kz);
       if (i < b.nx && j < b.ny && kz < b.nz) {
         const long long q = cidx(b, i, j, kz);
         I.Pt[1 - a][q] = I.Pt[a][q];

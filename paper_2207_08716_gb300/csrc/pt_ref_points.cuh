@@ -9,8 +9,18 @@
 #pragma once
 
 #include "pt_kernels.cuh"
+#include "pt_lean_body.cuh"
 
 namespace pt {
+
+// a / b: the IEEE quotient (FAST = false, the step-by-step form), or a times the two-step Newton
+// reciprocal of the hardware's approximate one (within an ulp; the FP32 form's outer phases,
+// which need far less and run on the FP64 pipe)
+template <bool FAST>
+__device__ __forceinline__ double ref_div(double a, double b) {
+  if constexpr (FAST) return a * lean_detail::rcp_full(b);
+  else return a / b;
+}
 
 __device__ __forceinline__ void perm_point(const Box& b, const Coef& c, const double* __restrict__ phi,
                                            const double* __restrict__ logk, double* __restrict__ perm,
@@ -24,6 +34,7 @@ __device__ __forceinline__ void perm_point(const Box& b, const Coef& c, const do
   rog[q] = (ph * c.rhof_g + (1.0 - ph) * c.rhos_g) - c.rho_bg_g;
 }
 
+template <bool FAST = false>
 __device__ __forceinline__ void edges_point(const Box& b, const Coef& c, const EdgeIn& in, const EdgeOut& out,
                                             int i, int j, int k) {
   if (i > b.nx || j > b.ny || k > b.nz) return;
@@ -35,11 +46,11 @@ __device__ __forceinline__ void edges_point(const Box& b, const Coef& c, const E
       const double m = 0.25 * (in.mu[q - 1 - px] + in.mu[q - px] + in.mu[q - 1] + in.mu[q]);
       const double xi = m * c.rGdtS;
       const double e = 0.5 * ((in.Vx[q] - in.Vx[q - px]) * c.rdy + (in.Vy[q] - in.Vy[q - 1]) * c.rdx) + c.ebg;
-      t = (in.txyo[q] * xi + 2.0 * m * e) / (1.0 + xi);
+      t = ref_div<FAST>(in.txyo[q] * xi + 2.0 * m * e, 1.0 + xi);
     } else if (c.bg_on) {   // wall edge: background part only
       const double m = edge_mean_mu_xy(b, in.mu, q, i, j);
       const double xi = m * c.rGdtS;
-      t = (in.txyo[q] * xi + 2.0 * m * c.ebg) / (1.0 + xi);
+      t = ref_div<FAST>(in.txyo[q] * xi + 2.0 * m * c.ebg, 1.0 + xi);
     }
     out.txy[q] = t;
   }
@@ -49,7 +60,7 @@ __device__ __forceinline__ void edges_point(const Box& b, const Coef& c, const E
       const double m = 0.25 * (in.mu[q - 1 - pxy] + in.mu[q - pxy] + in.mu[q - 1] + in.mu[q]);
       const double xi = m * c.rGdtS;
       const double e = 0.5 * ((in.Vx[q] - in.Vx[q - pxy]) * c.rdz + (in.Vz[q] - in.Vz[q - 1]) * c.rdx);
-      t = (in.txzo[q] * xi + 2.0 * m * e) / (1.0 + xi);
+      t = ref_div<FAST>(in.txzo[q] * xi + 2.0 * m * e, 1.0 + xi);
     }
     out.txz[q] = t;
   }
@@ -59,7 +70,7 @@ __device__ __forceinline__ void edges_point(const Box& b, const Coef& c, const E
       const double m = 0.25 * (in.mu[q - px - pxy] + in.mu[q - pxy] + in.mu[q - px] + in.mu[q]);
       const double xi = m * c.rGdtS;
       const double e = 0.5 * ((in.Vy[q] - in.Vy[q - pxy]) * c.rdz + (in.Vz[q] - in.Vz[q - px]) * c.rdy);
-      t = (in.tyzo[q] * xi + 2.0 * m * e) / (1.0 + xi);
+      t = ref_div<FAST>(in.tyzo[q] * xi + 2.0 * m * e, 1.0 + xi);
     }
     out.tyz[q] = t;
   }
@@ -67,6 +78,7 @@ __device__ __forceinline__ void edges_point(const Box& b, const Coef& c, const E
 
 // phi^{k+1} = 1 - exp(L),  L = Lo - dt [beta_phi ((Pf1 - Pfo) - (Pt1 - Pto)) / dt
 //                                       + (Pf1 - Pt1) / eta + V . grad(1 - phi) / (1 - phi)]
+template <bool FAST = false>
 __device__ __forceinline__ void porosity_point(const Box& b, const Coef& c, const double* __restrict__ Vx,
                                                const double* __restrict__ Vy, const double* __restrict__ Vz,
                                                const double* __restrict__ phi, const double* __restrict__ Pt1,
@@ -84,9 +96,9 @@ __device__ __forceinline__ void porosity_point(const Box& b, const Coef& c, cons
   if (j < b.ny - 1) ay += Vy[q + b.px] * ((1.0 - phi[q + b.px]) - omc) * c.rdy;
   if (k > 0) az += Vz[q] * (omc - (1.0 - phi[q - b.pxy])) * c.rdz;
   if (k < b.nz - 1) az += Vz[q + b.pxy] * ((1.0 - phi[q + b.pxy]) - omc) * c.rdz;
-  const double adv = 0.5 * (ax + ay + az) / omc;
+  const double adv = ref_div<FAST>(0.5 * (ax + ay + az), omc);
   const double pt1 = Pt1[q], pf1 = Pf1[q];
-  const double comp = c.compaction_on ? (pf1 - pt1) / eta[q] : 0.0;
+  const double comp = c.compaction_on ? ref_div<FAST>(pf1 - pt1, eta[q]) : 0.0;
   const double L = Lo[q] - c.dt * (c.beta_phi * ((pf1 - Pfo[q]) - (pt1 - Pto[q])) * c.rdt + comp + adv);
   phi1[q] = 1.0 - exp(L);
 }
