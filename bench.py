@@ -85,7 +85,7 @@ PROFILED = {
     "k_lean_cells_df64": {"src": "847b74c5871329ee", "traffic": 260.0, "thread_inst": 1929.0},
     "k_lean_faces_df64": {"src": "847b74c5871329ee", "traffic": 164.3, "thread_inst": 724.9},
     # profiles/k_corr_iteration_fp32_255.md (255^3, one launch)
-    "k_corr_iteration": {"src": "61ab62a158d14081", "traffic": 106.5, "thread_inst": 720.8},
+    "k_corr_iteration": {"src": "642041b57f4bbbcc", "traffic": 106.3, "thread_inst": 720.8},
 }
 # The FP64 pipe's nominal issue capacity: 304 thread-instructions per GPU clock (2 per SM; ncu's
 # sm__inst_executed_pipe_fp64 peak on this machine's GB300), 629 G/s at 2.07 GHz.
