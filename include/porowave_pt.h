@@ -301,6 +301,14 @@ typedef struct {
 } pt_adj_vec;
 int pt_adjoint_apply(pt_ctx *ctx, const pt_adj_vec *lam, pt_adj_vec *out, void *workspace, size_t bytes);
 
+/* Test aid (host only): the multigrid transfer tables of one direction between nf fine and
+ * nc = ceil(nf / 2) coarse cells (pt_num.mg_levels; see pt_mixed.cuh MgAxis for the layout:
+ * box_i0[nc], box_w[3 nc], hat_i0[nc + 1], hat_w[4 (nc + 1)], lin_ab[2 nf], lin_w[2 nf],
+ * fl_n0[nf + 1], fl_t[nf + 1], as 4-byte words, integers and FP32 values). Writes
+ * pt_mg_axis_words(nf) words to out (PT_ESPACE if `words` is smaller; PT_EINVAL for nf < 2). */
+size_t pt_mg_axis_words(int32_t nf);
+int pt_mg_axis_tables(int32_t nf, uint32_t *out, size_t words);
+
 /* ---- Batched ensemble --------------------------------------------------------------------
  * ninst independent instances (each its own grid, parameters, fields and numerics), all
  * PT_FP64 or all PT_FP32 (mixing returns PT_EINVAL), advanced together by one persistent engine:

@@ -1867,6 +1867,16 @@ int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
   return any_nan ? PT_ENAN : (any_nc ? PT_ENOTCONV : PT_OK);
 }
 
+size_t pt_mg_axis_words(int32_t nf) { return nf >= 2 ? mg_axis_words(nf, (nf + 1) / 2) : 0; }
+
+int pt_mg_axis_tables(int32_t nf, uint32_t* out, size_t words) {
+  if (nf < 2 || !out) return PT_EINVAL;
+  const std::vector<uint32_t> t = mg_axis_tables(nf, (nf + 1) / 2);
+  if (words < t.size()) return PT_ESPACE;
+  std::memcpy(out, t.data(), t.size() * sizeof(uint32_t));
+  return PT_OK;
+}
+
 int pt_batch_config(const pt_batch* B, int32_t* tile_x, int32_t* tile_y, int32_t* ipg) {
   if (!B) return PT_EINVAL;
   if (tile_x) *tile_x = B->mixed ? corr_tile_x() : B->bx;

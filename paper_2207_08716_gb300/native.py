@@ -215,6 +215,8 @@ SIGNATURES = {
     "pt_batch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pt_batch_config_fp32": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int32)]),
+    "pt_mg_axis_words": (C.c_size_t, [C.c_int32]),
+    "pt_mg_axis_tables": (C.c_int, [C.c_int32, C.c_void_p, C.c_size_t]),
     "pt_batch_destroy": (None, [C.c_void_p]),
     "pt_destroy": (None, [C.c_void_p]),
     "pt_strerror": (C.c_char_p, [C.c_int]),
