@@ -2,7 +2,8 @@
 on the GPU against the FP64 oracle: same iteration count -> fields within 1e-10 (max-rel,
 normwise), for the FP64-lean and step-by-step forms, over two physical steps (the second uses
 the old stresses of the first, wall edges included); the mixed-precision form's converged step
-within the porosity bar 1e-5; the sub-domain form bitwise equal to the undivided grid."""
+within the porosity bar 1e-5, with plain and with multigrid correction solves; the sub-domain
+form bitwise equal to the undivided grid."""
 import numpy as np
 import pytest
 
@@ -62,6 +63,25 @@ def test_shear_mixed_precision_step_matches_oracle():
     r = s.step(raise_on_notconv=True)
     assert r["status"] == 0
     assert rel(s.get("phi"), st["phi"]) <= 1e-5
+    s.close()
+
+
+def test_shear_multigrid_step_matches_oracle():
+    """The background strain rate enters the FP64 residuals only: multigrid correction solves
+    (three levels, 12 x 12 x 20 -> 6 x 6 x 10 -> 3 x 3 x 5) reach the oracle's converged step."""
+    PTSolver = _solver()
+    p = I.shear_params(12, 12, 20)
+    p["tol"] = 1e-8
+    phi = I.ellipsoid_porosity(p, centre=(0.5, 0.5, 0.3), axes=(14.0, 14.0, 8.0))
+    st = O.make_state(p, phi)
+    rc, iters, res = O.step(st)
+    assert rc == 0, res
+    s = PTSolver(dict(p, precision=1, mg_levels=3), phi)
+    r = s.step(raise_on_notconv=True)
+    assert r["status"] == 0
+    assert rel(s.get("phi"), st["phi"]) <= 1e-5
+    for name in ("Pt", "Pf", "Vx"):
+        assert rel(s.get(name), st[name]) <= 1e-4, name
     s.close()
 
 
