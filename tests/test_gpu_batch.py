@@ -119,6 +119,32 @@ def test_fp32_ensemble_instances_equal_single_fp32_runs():
     b.close()
 
 
+@pytest.mark.parametrize("fp32", (False, True))
+def test_ensemble_members_with_log_permeability_fields_equal_single_runs(fp32):
+    """Members carrying their own log-permeability prefactor fields (Eq. 23), next to one
+    without: each member's converged step equals its single run with the same field."""
+    PTBatch, PTSolver = _mods()
+    from paper_2207_08716_gb300 import native as N
+    prec = N.PT_FP32 if fp32 else N.PT_FP64
+    mem = I.ensemble(seed=9, n_inst=3, sizes=(12, 16), max_iter=60000)
+    for m in (0, 2):
+        p, phi = mem[m]
+        lk = I.gaussian_random_field((p["nz"], p["ny"], p["nx"]), seed=20 + m, corr_len=0.2, std=0.4)
+        mem[m] = (p, phi, lk)
+    b = PTBatch(mem, precision=prec)
+    reps, _ = b.step()
+    for m, member in enumerate(mem):
+        p, phi = member[0], member[1]
+        s = PTSolver(dict(p, precision=prec), phi, logk=member[2] if len(member) > 2 else None)
+        r = s.step()
+        assert reps[m]["status"] == r["status"] == 0 and reps[m]["iters"] == r["iters"], (m, reps[m], r)
+        bar = 1e-5 if fp32 else 1e-12
+        for name in FIELDS:
+            assert rel(b.get(m, name), s.get(name)) <= bar, (m, name, rel(b.get(m, name), s.get(name)))
+        s.close()
+    b.close()
+
+
 def test_fp32_ensemble_of_uneven_members_converges_like_single_runs():
     """Members of several sizes and parameter sets converging after different numbers of outer
     iterations: each stops at its own outer check, with the single run's iteration count."""

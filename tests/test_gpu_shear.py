@@ -1,6 +1,6 @@
 """The background-shear workload (thesis Art. 1 Section 3.1, Eqs. 32-33; Table 2 scaled down)
 on the GPU against the FP64 oracle: same iteration count -> fields within 1e-10 (max-rel,
-normwise), for the FP64-lean and step-by-step forms, over two physical steps (the second uses
+normwise), for the FP64-lean, step-by-step and double-float forms, over two physical steps (the second uses
 the old stresses of the first, wall edges included); the mixed-precision form's converged step
 within the porosity bar 1e-5, with plain and with multigrid correction solves; the sub-domain
 form bitwise equal to the undivided grid."""
@@ -27,7 +27,7 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("mode", (0, 2))
+@pytest.mark.parametrize("mode", (0, 2, 3))
 @pytest.mark.parametrize("dims, niter", [((16, 14, 24), 450), ((9, 11, 13), 300)])
 def test_shear_iterations_match_oracle(dims, niter, mode):
     PTSolver = _solver()
