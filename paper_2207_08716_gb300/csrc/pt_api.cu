@@ -1571,6 +1571,16 @@ int mix_active(pt_batch* B, int* nactive) {
   return PT_OK;
 }
 
+// The two timing events of a tuner, destroyed on every return path.
+struct TunerEvents {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool create() { return cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess; }
+  ~TunerEvents() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
 // FP32 ensemble step: every member's step begin (host, as pt_step), then graph replays until
 // every member is done; the first step times one replay of each candidate configuration
 // (correction tile depth, CTAs per SM, rounds per replay) and keeps the fastest per round.
@@ -1596,8 +1606,8 @@ int batch_step_mixed(pt_batch* B, pt_report* reps, double* ttc_ms) {
   Cfg best = {B->zchunk, B->minb, B->mult, B->groups};
   long long rounds = 0;
   int nactive = B->ninst;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (ncand && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) return PT_ECUDA;
+  TunerEvents ev;
+  if (ncand && !ev.create()) return PT_ECUDA;
   for (int t = 0; t < ncand && nactive > 0 && rounds < max_rounds; ++t) {
     B->zchunk = cands[t].zchunk;
     B->minb = cands[t].minb;
@@ -1606,22 +1616,20 @@ int batch_step_mixed(pt_batch* B, pt_report* reps, double* ttc_ms) {
     if (upload_mix(B) != cudaSuccess) return PT_ECUDA;
     rc = build_mix_graph(B);
     if (rc != PT_OK) return rc;
-    cudaEventRecord(e0, B->stream);
+    cudaEventRecord(ev.e0, B->stream);
     if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return PT_ECUDA;
-    cudaEventRecord(e1, B->stream);
+    cudaEventRecord(ev.e1, B->stream);
     rounds += B->mult;
     rc = mix_active(B, &nactive);
     if (rc != PT_OK) return rc;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, ev.e0, ev.e1);
     if (ms / B->mult < best_ms) {
       best_ms = ms / B->mult;
       best = cands[t];
     }
   }
   if (ncand) {
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     B->zchunk = best.zchunk;
     B->minb = best.minb;
     B->mult = best.mult;
@@ -1802,11 +1810,8 @@ int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
   float best_ms = 1e30f;
   Cfg best = {B->bx, B->by, B->ipg / (2 * B->nup)};
   int done = 0, nactive = B->ninst;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (ncand) {
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-  }
+  TunerEvents ev;
+  if (ncand && !ev.create()) return PT_ECUDA;
   for (int t = 0; t < ncand && nactive > 0 && done < cap; ++t) {
     B->bx = cands[t].bx;
     B->by = cands[t].by;
@@ -1814,22 +1819,20 @@ int pt_batch_step(pt_batch* B, pt_report* reps, double* ttc_ms) {
     if (upload_batch(B) != cudaSuccess) return PT_ECUDA;
     rc = build_batch_graph(B);
     if (rc != PT_OK) return rc;
-    cudaEventRecord(e0, B->stream);
+    cudaEventRecord(ev.e0, B->stream);
     if (cudaGraphLaunch(B->exec, B->stream) != cudaSuccess) return PT_ECUDA;
-    cudaEventRecord(e1, B->stream);
+    cudaEventRecord(ev.e1, B->stream);
     done += B->ipg;
     rc = batch_active(B, &nactive);
     if (rc != PT_OK) return rc;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, ev.e0, ev.e1);
     if (ms / B->ipg < best_ms) {
       best_ms = ms / B->ipg;
       best = cands[t];
     }
   }
   if (ncand) {
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     B->bx = best.bx;
     B->by = best.by;
     B->ipg = best.mult * 2 * B->nup;
